@@ -1,0 +1,307 @@
+"""FP64 CPU oracle for the static polarizability -> P~_GG' -> eps -> eps^-1 path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module.  It shares no code with the CUDA library: it has
+its own G-sphere ordering, its own twiddles (through numpy's FFT), its own units and its own
+linear algebra.
+
+Every function follows a passage of Kim et al., "Scalable GW software for quasiparticle
+properties using OpenAtom" (arXiv 1810.07772), at q = 0 and a single k-point, in Hartree atomic
+units with e^2 = 1:
+
+* Eq. (Pstatic), Sec. 2 -- the static polarizability in real space.
+* Eq. (fdef), Sec. 4.1 -- the energy-weighted pair densities f_vc(r).
+* The outer-product equation right after Eq. (fdef) -- P as a sum of f f^H.
+* The row and column FFT equations of Sec. 4.1 -- P(r,r') -> P^(G,r') -> P~(G,G').
+* Eq. (gpsaceP), Sec. 4.1 -- the Adler-Wiser g-space sum over states (the second route).
+* Sec. 5.1 (static inverse dielectric matrix) -- eps = I - sqrt(V) P~ sqrt(V), V = 4 pi/(Omega |G|^2),
+  and the Newton iteration X <- X (2I - A X) the paper uses to invert it.
+
+Readings of the paper taken here (where it is silent or inconsistent):
+
+1. Orientation.  Eq. (Pstatic) pairs psi_c(x) psi_v^*(x) with psi_c^*(x') psi_v(x'); Eq. (fdef) and
+   the outer product built from it give the transpose.  The oracle follows Eq. (Pstatic):
+   P(r,r') = -sum_k f_k(r) conj(f_k(r')) with f_vc = conj(psi_v) psi_c sqrt(2/(E_c-E_v)).  The
+   g-space matrix element is then M_vc(G) = sum_r exp(-i G.r) conj(psi_v(r)) psi_c(r).
+2. The factor 2 of Eq. (Pstatic) is the whole spin/time-ordering factor; no extra spin sum.
+3. Transform signs: exp(-i G.r) on the row index r and exp(+i G'.r') on the column index r',
+   unnormalised (the states are orthonormal on the discrete grid, which absorbs the paper's
+   1/sqrt(Omega) factors).
+4. Units: energies arrive in eV and are divided by 27.211386245988; the cell is cubic with edge L
+   (bohr), Omega = L^3, G = 2 pi m / L for integer m in FFT order.
+5. Sphere: all m with |m|^2 <= gcut, ordered by (|m|^2, m1, m2, m3) ascending, so G = 0 is first.
+6. Head at q = 0: V(G=0) is set to 0, so eps has a unit head and zero wings.
+7. Newton start: alpha = 1 / max_i sum_j |(A A^H)_ij| (the paper's A^T read as A^H for complex A,
+   with absolute values so the row sums bound the spectral radius).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HARTREE_EV = 27.211386245988
+
+
+# ----------------------------------------------------------------------------- energies
+
+
+def to_hartree(E_eV):
+    return np.asarray(E_eV, dtype=np.float64) / HARTREE_EV
+
+
+def pair_weights(E_eV, nv):
+    """w_vc = 2 / (E_c - E_v) in 1/Hartree: the energy factor of Eq. (fdef), before the root."""
+    E = to_hartree(E_eV)
+    return 2.0 / (E[None, nv:] - E[:nv, None])
+
+
+# ----------------------------------------------------------------------------- real space
+
+
+def pair_density(psi, E_eV, nv):
+    """Eq. (fdef) at q = 0: f_vc(r) = conj(psi_v(r)) psi_c(r) sqrt(2/(E_c - E_v)), row k = v*N_c + c."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    nb, nr = psi.shape
+    nc = nb - nv
+    w = pair_weights(E_eV, nv)
+    f = np.conj(psi[:nv])[:, None, :] * psi[nv:][None, :, :] * np.sqrt(w)[:, :, None]
+    return f.reshape(nv * nc, nr)
+
+
+def P_from_f(f):
+    """The outer product after Eq. (fdef), in the orientation of Eq. (Pstatic):
+    P(r, r') = -sum_k f_k(r) conj(f_k(r')).  (The matmul is the only library step.)"""
+    f = np.asarray(f, dtype=np.complex128)
+    return -(f.T @ np.conj(f))
+
+
+def P_rspace(psi, E_eV, nv):
+    """P(r, r') from the states through f (Eq. fdef and the outer product)."""
+    return P_from_f(pair_density(psi, E_eV, nv))
+
+
+_clib = None
+
+
+def _load_clib():
+    global _clib
+    if _clib is None:
+        from . import build as _b
+        path = _b.build()
+        lib = ctypes.CDLL(path)
+        lib.oracle_P_rows.restype = ctypes.c_int
+        lib.oracle_P_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _clib = lib
+    return _clib
+
+
+def clib_threads() -> int:
+    return int(_load_clib().oracle_num_threads())
+
+
+def P_rows_loop(psi, E_eV, nv, r0, r1):
+    """Rows [r0, r1) of Eq. (Pstatic) by the plain FP64 C loop over r, r', v, c."""
+    lib = _load_clib()
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    nb, nr = psi.shape
+    E = np.ascontiguousarray(to_hartree(E_eV))
+    out = np.zeros((r1 - r0, nr), dtype=np.complex128)
+    rc = lib.oracle_P_rows(nr, nv, nb - nv, psi.ctypes.data, E.ctypes.data, r0, r1, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_P_rows rejected its arguments")
+    return out
+
+
+def P_quadruple_loop(psi, E_eV, nv):
+    """Eq. (Pstatic) as a pure-Python loop over v, c, r, r' (tiny inputs only)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    E = to_hartree(E_eV)
+    nb, nr = psi.shape
+    P = np.zeros((nr, nr), dtype=np.complex128)
+    for v in range(nv):
+        for c in range(nv, nb):
+            for r in range(nr):
+                for rp in range(nr):
+                    P[r, rp] += (2.0 * np.conj(psi[v, r]) * psi[c, r] * np.conj(psi[c, rp]) * psi[v, rp]
+                                 / (E[v] - E[c]))
+    return P
+
+
+# ----------------------------------------------------------------------------- G sphere
+
+
+def sphere(dims, gcut):
+    """Integer G-vectors m (FFT order, each component in [-n/2, n - n/2)) with |m|^2 <= gcut,
+    sorted by (|m|^2, m1, m2, m3).  Returns an int64 array of shape (N_g, 3)."""
+    ranges = [range(-(n // 2), n - n // 2) for n in dims]
+    pts = []
+    for a in ranges[0]:
+        for b in ranges[1]:
+            for c in ranges[2]:
+                if a * a + b * b + c * c <= gcut:
+                    pts.append((a * a + b * b + c * c, a, b, c))
+    pts.sort()
+    return np.array([p[1:] for p in pts], dtype=np.int64).reshape(-1, 3)
+
+
+def _flat_index(dims, m):
+    n1, n2, n3 = dims
+    return ((m[:, 0] % n1) * n2 + (m[:, 1] % n2)) * n3 + (m[:, 2] % n3)
+
+
+def P_to_G(P, dims, gvec):
+    """The two FFT phases of Sec. 4.1 restricted to the sphere:
+    P^(G, r') = sum_r exp(-i G.r) P(r, r');  P~(G, G') = sum_r' P^(G, r') exp(+i G'.r').
+    numpy's forward FFT carries exp(-i...) and its inverse exp(+i...)/N, undone by the factor N_r."""
+    n1, n2, n3 = dims
+    nr = n1 * n2 * n3
+    idx = _flat_index(dims, gvec)
+    Phat = np.fft.fftn(np.asarray(P).reshape(n1, n2, n3, nr), axes=(0, 1, 2)).reshape(nr, nr)[idx]
+    Pt = np.fft.ifftn(Phat.reshape(-1, n1, n2, n3), axes=(1, 2, 3)).reshape(-1, nr)[:, idx]
+    return Pt * nr
+
+
+def dft_matrix(dims, gvec):
+    """D[g, r] = exp(-i 2 pi (m1 j1/n1 + m2 j2/n2 + m3 j3/n3)) written out element by element."""
+    n1, n2, n3 = dims
+    j1, j2, j3 = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    j1, j2, j3 = j1.reshape(-1), j2.reshape(-1), j3.reshape(-1)
+    ph = (np.outer(gvec[:, 0], j1) / n1 + np.outer(gvec[:, 1], j2) / n2
+          + np.outer(gvec[:, 2], j3) / n3)
+    return np.exp(-2j * np.pi * ph)
+
+
+def P_to_G_direct(P, dims, gvec):
+    """Same transform as P_to_G as explicit sums, P~ = D P D^H (tiny inputs)."""
+    D = dft_matrix(dims, gvec)
+    return D @ np.asarray(P) @ np.conj(D.T)
+
+
+def matrix_elements(psi, nv, dims, gvec, v_list=None):
+    """M_vc(G) = sum_r exp(-i G.r) conj(psi_v(r)) psi_c(r) for the listed v (Eq. gpsaceP's M, read
+    in the orientation of Eq. Pstatic).  Returns [len(v_list) * N_c][N_g]."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    n1, n2, n3 = dims
+    nb = psi.shape[0]
+    nc = nb - nv
+    idx = _flat_index(dims, gvec)
+    if v_list is None:
+        v_list = range(nv)
+    out = []
+    for v in v_list:
+        rho = np.conj(psi[v])[None, :] * psi[nv:]
+        out.append(np.fft.fftn(rho.reshape(nc, n1, n2, n3), axes=(1, 2, 3)).reshape(nc, -1)[:, idx])
+    return np.concatenate(out, axis=0)
+
+
+def P_gspace(psi, E_eV, nv, dims, gvec, v_chunk=4):
+    """Eq. (gpsaceP): P~(G, G') = sum_vc 2 M_vc(G) conj(M_vc(G')) / (E_v - E_c)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    E = to_hartree(E_eV)
+    nc = psi.shape[0] - nv
+    ng = gvec.shape[0]
+    Pt = np.zeros((ng, ng), dtype=np.complex128)
+    for v0 in range(0, nv, v_chunk):
+        vs = list(range(v0, min(nv, v0 + v_chunk)))
+        M = matrix_elements(psi, nv, dims, gvec, vs)
+        d = np.concatenate([2.0 / (E[v] - E[nv:]) for v in vs])
+        Pt += (M.T * d[None, :]) @ np.conj(M)
+    return Pt
+
+
+def P_gspace_truncated(psi, E_eV, nv, nc_keep, dims, gvec):
+    """Eq. (gpsaceP) with the unoccupied sum cut to the nc_keep lowest states (band truncation)."""
+    psi = np.asarray(psi)
+    keep = np.concatenate([psi[:nv], psi[nv:nv + nc_keep]])
+    E = np.asarray(E_eV)
+    Ek = np.concatenate([E[:nv], E[nv:nv + nc_keep]])
+    return P_gspace(keep, Ek, nv, dims, gvec)
+
+
+# ----------------------------------------------------------------------------- eps
+
+
+def coulomb(gvec, cell_L):
+    """V_c(G) = 4 pi / (Omega |G|^2) with G = 2 pi m / L, Omega = L^3 (Sec. 5.1); V_c(0) := 0."""
+    m2 = np.sum(np.asarray(gvec, dtype=np.float64) ** 2, axis=1)
+    G2 = (2.0 * np.pi / cell_L) ** 2 * m2
+    omega = cell_L ** 3
+    V = np.zeros_like(G2)
+    nz = m2 > 0
+    V[nz] = 4.0 * np.pi / (omega * G2[nz])
+    return V
+
+
+def eps_build(Pt, gvec, cell_L):
+    """eps_GG' = delta_GG' - sqrt(V(G)) P~_GG' sqrt(V(G')) (Sec. 5.1)."""
+    s = np.sqrt(coulomb(gvec, cell_L))
+    return np.eye(Pt.shape[0], dtype=np.complex128) - s[:, None] * np.asarray(Pt, np.complex128) * s[None, :]
+
+
+class NotPositiveDefinite(ArithmeticError):
+    pass
+
+
+def cholesky_lower(A):
+    """A = L L^H column by column (Cholesky-Crout), raising on a non-positive pivot."""
+    A = np.asarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    for j in range(n):
+        d = A[j, j].real - np.sum(np.abs(L[j, :j]) ** 2)
+        if not d > 0.0:
+            raise NotPositiveDefinite(f"pivot {j} is {d}")
+        L[j, j] = np.sqrt(d)
+        L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ np.conj(L[j, :j])) / L[j, j]
+    return L
+
+
+def forward_substitute(L, B):
+    """Solve L Y = B for lower-triangular L, one row at a time."""
+    L = np.asarray(L)
+    Y = np.zeros(np.shape(B), dtype=np.complex128)
+    for i in range(L.shape[0]):
+        Y[i] = (B[i] - L[i, :i] @ Y[:i]) / L[i, i]
+    return Y
+
+
+def inverse_cholesky(A):
+    """A^-1 = L^-H L^-1 from the Cholesky factor (the method fixed for eps^-1 in FP64)."""
+    L = cholesky_lower(A)
+    Y = forward_substitute(L, np.eye(L.shape[0], dtype=np.complex128))
+    return np.conj(Y.T) @ Y
+
+
+def inverse_newton(A, tol=1e-11, max_iter=100):
+    """Sec. 5.1: X_{n+1} = X_n (2I - A X_n), X_0 = alpha A^H, stopped when every entry moves < tol.
+    Returns (X, iterations)."""
+    A = np.asarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    alpha = 1.0 / np.max(np.sum(np.abs(A @ np.conj(A.T)), axis=1))
+    X = alpha * np.conj(A.T)
+    I2 = 2.0 * np.eye(n)
+    for it in range(1, max_iter + 1):
+        Xn = X @ (I2 - A @ X)
+        if np.max(np.abs(Xn - X)) < tol:
+            return Xn, it
+        X = Xn
+    return X, max_iter
+
+
+# ----------------------------------------------------------------------------- whole path
+
+
+def eps_inv_path(psi, E_eV, nv, dims, gcut, cell_L, route="gspace"):
+    """States -> P~ -> eps -> eps^-1.  route 'rspace' goes through P(r,r') (small grids),
+    'gspace' through Eq. (gpsaceP).  Returns dict(gvec, Pt, eps, epsinv)."""
+    gvec = sphere(dims, gcut)
+    if route == "rspace":
+        Pt = P_to_G(P_rspace(psi, E_eV, nv), dims, gvec)
+    else:
+        Pt = P_gspace(psi, E_eV, nv, dims, gvec)
+    eps = eps_build(Pt, gvec, cell_L)
+    return {"gvec": gvec, "Pt": Pt, "eps": eps, "epsinv": inverse_cholesky(eps)}

@@ -1,0 +1,118 @@
+"""Seeded synthetic inputs shaped like the plane-wave GW workloads of Kim et al. (arXiv 1810.07772).
+
+This module draws inputs only: random orthonormal complex states on a cubic real-space grid
+and sorted band energies.  It holds none of the polarizability arithmetic, so both the CUDA
+path and the FP64 oracle can be fed from it without sharing any of the method's code.
+
+Recipe (the paper's Si supercell states come from a DFT code that is not available here; these
+stand in for them with the same shapes):
+
+* ``A = N(0,1) + i N(0,1)`` of shape ``(N_r, N_v + N_c)`` from ``numpy.random.default_rng(seed)``
+  (real part drawn first, then the imaginary part), then a reduced QR.  The columns of ``Q``
+  are Haar-random and discretely orthonormal, ``sum_r conj(psi_m(r)) psi_n(r) = delta_mn``.
+  Columns ``[0, N_v)`` are the occupied states, the rest the unoccupied ones.
+* ``E_v ~ U[-10, 0] eV`` and ``E_c ~ U[0.5, 20] eV``, each sorted ascending, drawn after ``A``.
+* The real-space index is C order, ``r = (j1 * n2 + j2) * n3 + j3``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One synthetic system: an ``n^3`` grid, ``nv`` occupied and ``nc`` unoccupied states.
+
+    ``gcut`` is the integer sphere cut: the eps basis is every ``G = 2*pi*m/L`` with
+    ``|m|^2 <= gcut``.  ``cell_L`` is the cubic cell edge in bohr.
+    """
+
+    name: str
+    n: int
+    nv: int
+    nc: int
+    gcut: int
+    seed: int
+    cell_L: float = 1.0
+
+    @property
+    def nr(self) -> int:
+        return self.n ** 3
+
+    @property
+    def k(self) -> int:
+        return self.nv * self.nc
+
+    def herk_flop(self) -> float:
+        """LAPACK's complex Hermitian rank-k count over one triangle, 4 k N_r (N_r + 1)."""
+        return 4.0 * self.k * self.nr * (self.nr + 1)
+
+
+# The three single-system shapes: the small FP64-checkable case, the plain FP32 case and the
+# split-precision case.
+SMALL = Workload("grid12_nv4_nc28", 12, 4, 28, 8, 1)
+PLAIN = Workload("grid24_nv32_nc480", 24, 32, 480, 29, 2)
+SPLIT = Workload("grid36_nv64_nc1000", 36, 64, 1000, 61, 3)
+
+
+def batch_workloads() -> list[Workload]:
+    """Eight independent systems of uneven size (grids 16^3..32^3, N_v 8..48, N_c 100..800).
+
+    The sphere cut follows ``gcut = floor((n / 4.4)^2)`` so every system keeps about 5% of its
+    grid in the eps basis, as the single-system shapes do.
+    """
+    grids = [16, 18, 20, 24, 24, 27, 30, 32]
+    out = []
+    for i, n in enumerate(grids):
+        nv = int(round(8 + 40 * i / 7))
+        nc = 100 * (i + 1)
+        gcut = int((n / 4.4) ** 2)
+        out.append(Workload(f"batch{i}_grid{n}_nv{nv}_nc{nc}", n, nv, nc, gcut, 100 + i))
+    return out
+
+
+def learned_workload(nc: int, seed: int) -> Workload:
+    """The truncation-correction shape: a 24^3 grid with 32 occupied states and ``nc`` unoccupied."""
+    return Workload(f"grid24_nv32_nc{nc}_s{seed}", 24, 32, nc, 29, seed)
+
+
+def make_states(n: int, nv: int, nc: int, seed: int, dims: tuple[int, int, int] | None = None):
+    """Return ``(psi, E_eV)``: ``psi`` complex128 ``[nv + nc][N_r]``, ``E_eV`` float64 ``[nv + nc]``.
+
+    ``dims`` overrides the cubic ``(n, n, n)`` grid for non-cubic test grids.
+    """
+    if dims is None:
+        dims = (n, n, n)
+    nr = int(dims[0]) * int(dims[1]) * int(dims[2])
+    nb = nv + nc
+    if nb > nr:
+        raise ValueError("more states than grid points: they cannot be orthonormal")
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((nr, nb))
+    b = rng.standard_normal((nr, nb))
+    q, _ = np.linalg.qr(a + 1j * b, mode="reduced")
+    psi = np.ascontiguousarray(q.T)
+    ev = np.sort(rng.uniform(-10.0, 0.0, nv))
+    ec = np.sort(rng.uniform(0.5, 20.0, nc))
+    return psi, np.concatenate([ev, ec])
+
+
+def make_workload_states(w: Workload):
+    return make_states(w.n, w.nv, w.nc, w.seed)
+
+
+def plane_wave_states(dims, m_list, energies_eV):
+    """States ``psi_j(r) = exp(i 2 pi m_j . (j1/n1, j2/n2, j3/n3)) / sqrt(N_r)`` for integer ``m_j``.
+
+    Used for closed-form checks: distinct ``m_j`` (mod the grid) give exactly orthonormal states.
+    """
+    n1, n2, n3 = dims
+    j1, j2, j3 = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    nr = n1 * n2 * n3
+    rows = []
+    for m in m_list:
+        ph = 2.0 * np.pi * (m[0] * j1 / n1 + m[1] * j2 / n2 + m[2] * j3 / n3)
+        rows.append((np.exp(1j * ph) / np.sqrt(nr)).reshape(-1))
+    return np.array(rows), np.asarray(energies_eV, dtype=np.float64)

@@ -1,0 +1,253 @@
+"""Pins for the FP64 oracle: what the paper and the mathematics fix, independent of the oracle.
+
+Each test names the passage (Kim et al., arXiv 1810.07772) or the mathematical fact it checks and
+is chosen so that a plausible slip in the oracle (a dropped term, a flipped sign or exponent, a
+transposed operand, a wrong unit) fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_1810_07772_gb300 import inputs
+
+TINY = (3, 3, 2)
+
+
+def tiny_states(seed=7, nv=2, nc=3, dims=TINY):
+    return inputs.make_states(0, nv, nc, seed, dims=dims)
+
+
+# --------------------------------------------------------------------------- real-space P
+
+
+def test_quadruple_loop_equals_C_loop_and_outer_product():
+    """Eq. (Pstatic) three ways on a tiny grid: pure-Python loop, the C loop, and f f^H."""
+    psi, E = tiny_states()
+    nv = 2
+    P_py = O.P_quadruple_loop(psi, E, nv)
+    P_c = O.P_rows_loop(psi, E, nv, 0, psi.shape[1])
+    P_mm = O.P_rspace(psi, E, nv)
+    assert np.max(np.abs(P_c - P_py)) < 1e-14 * np.max(np.abs(P_py))
+    assert np.max(np.abs(P_mm - P_py)) < 1e-14 * np.max(np.abs(P_py))
+
+
+def test_C_loop_row_block_matches_full():
+    psi, E = inputs.make_states(4, 2, 5, 11)
+    P = O.P_rspace(psi, E, 2)
+    rows = O.P_rows_loop(psi, E, 2, 5, 17)
+    assert np.allclose(rows, P[5:17], rtol=0, atol=1e-15 * np.max(np.abs(P)))
+
+
+def test_hand_computed_single_pair():
+    """One occupied and one unoccupied state on a 2-point grid, evaluated by hand:
+    psi_v = (1, 1)/sqrt2, psi_c = (1, -1)/sqrt2, E_v = -1 Ha, E_c = +1 Ha.
+    rho = conj(psi_v) psi_c = (1, -1)/2, so P = 2/(E_v - E_c) rho rho^H = -(1/4) [[1, -1], [-1, 1]]."""
+    s = 1 / np.sqrt(2)
+    psi = np.array([[s, s], [s, -s]], dtype=np.complex128)
+    E = np.array([-1.0, 1.0]) * O.HARTREE_EV
+    P = O.P_rspace(psi, E, 1)
+    expect = -0.25 * np.array([[1, -1], [-1, 1]])
+    assert np.allclose(P, expect, atol=1e-15)
+    assert np.allclose(O.P_rows_loop(psi, E, 1, 0, 2), expect, atol=1e-15)
+
+
+def test_hand_computed_orientation_with_complex_states():
+    """Orientation of Eq. (Pstatic) on a 3-point grid, by hand: psi_v = (1, 1, 1)/sqrt3,
+    psi_c = (1, w, w^2)/sqrt3 with w = exp(2 pi i/3), E_c - E_v = 2 Ha.  Then
+    rho = conj(psi_v) psi_c = (1, w, w^2)/3 and P[a][b] = -(1/9) w^(a-b), so
+    P[0][1] = -(1/9) exp(-2 pi i/3) = (1 + i sqrt3)/18; the transposed orientation would give
+    (1 - i sqrt3)/18."""
+    s = 1 / np.sqrt(3)
+    w = np.exp(2j * np.pi / 3)
+    psi = np.array([[s, s, s], [s, s * w, s * w * w]], dtype=np.complex128)
+    E = np.array([-1.0, 1.0]) * O.HARTREE_EV
+    for P in (O.P_rspace(psi, E, 1), O.P_rows_loop(psi, E, 1, 0, 3)):
+        assert abs(P[0, 1] - (1 + 1j * np.sqrt(3)) / 18) < 1e-15
+        assert abs(P[1, 0] - (1 - 1j * np.sqrt(3)) / 18) < 1e-15
+        assert abs(P[2, 2] - (-1 / 9)) < 1e-15
+
+
+def test_paper_outer_product_orientation_is_transpose():
+    """Reading 1: the form -sum f^*(x) f(x') printed after Eq. (fdef) is P^T of Eq. (Pstatic)."""
+    psi, E = tiny_states(seed=3)
+    f = O.pair_density(psi, E, 2)
+    P = O.P_from_f(f)
+    P_paper = -(np.conj(f).T @ f)
+    assert np.allclose(P_paper, P.T, atol=1e-15)
+
+
+def test_P_hermitian_negative_semidefinite_rank():
+    psi, E = inputs.make_states(6, 3, 9, 5)
+    P = O.P_rspace(psi, E, 3)
+    assert np.max(np.abs(P - np.conj(P.T))) < 1e-16
+    lam = np.linalg.eigvalsh(P)
+    assert lam.max() < 1e-15 * np.abs(lam).max()
+    assert np.sum(np.abs(lam) > 1e-12 * np.abs(lam).max()) == 27     # rank k = nv * nc
+
+
+def test_phase_invariance_and_partition_linearity():
+    psi, E = inputs.make_states(4, 2, 6, 9)
+    P = O.P_rspace(psi, E, 2)
+    ph = np.exp(1j * np.linspace(0.1, 5.0, psi.shape[0]))
+    assert np.allclose(O.P_rspace(psi * ph[:, None], E, 2), P, atol=1e-16)
+    A = np.r_[0:2, 2:5]
+    B = np.r_[0:2, 5:8]
+    PA = O.P_rspace(psi[A], E[A], 2)
+    PB = O.P_rspace(psi[B], E[B], 2)
+    assert np.allclose(PA + PB, P, atol=1e-16)
+
+
+def test_pair_weights_units():
+    """eV -> Hartree with 27.211386245988 eV/Ha, and w = 2/(E_c - E_v) > 0."""
+    E = np.array([-O.HARTREE_EV, 0.0, O.HARTREE_EV])
+    w = O.pair_weights(E, 1)
+    assert np.allclose(w, [[2.0 / 1.0, 2.0 / 2.0]])
+
+
+# --------------------------------------------------------------------------- sphere and FFTs
+
+
+def test_sphere_counts_and_order():
+    """Lattice points with |m|^2 <= K: 1 + r3(1) + ... ; r3 = 6, 12, 8, 6, 24, 24, 0, 12 for 1..8."""
+    g = O.sphere((12, 12, 12), 8)
+    assert g.shape == (93, 3)
+    assert tuple(g[0]) == (0, 0, 0)
+    m2 = np.sum(g * g, axis=1)
+    assert np.all(np.diff(m2) >= 0)
+    assert len(O.sphere((24, 24, 24), 29)) == 691
+    assert len(O.sphere((36, 36, 36), 61)) == 2007
+    # even grid: -n/2 is in range, +n/2 is not
+    g4 = O.sphere((4, 4, 4), 4)
+    assert (-2, 0, 0) in map(tuple, g4) and (2, 0, 0) not in map(tuple, g4)
+
+
+def test_fft_route_equals_explicit_dft():
+    psi, E = inputs.make_states(0, 2, 4, 21, dims=(4, 3, 5))
+    dims = (4, 3, 5)
+    P = O.P_rspace(psi, E, 2)
+    g = O.sphere(dims, 3)
+    assert np.allclose(O.P_to_G(P, dims, g), O.P_to_G_direct(P, dims, g), atol=1e-14)
+
+
+def test_plane_wave_closed_form():
+    """Plane waves psi = exp(i G.r)/sqrt(N_r): rho_vc = exp(i (G_c - G_v).r)/N_r, so
+    M_vc(G) = delta(G, G_c - G_v) and P~ is 2/(E_v - E_c) at (G_c - G_v, G_c - G_v) only.
+    Pins the sign of both exponents, the orientation, the factor 2 and the unit conversion."""
+    dims = (6, 6, 6)
+    mv = [(0, 0, 0), (1, 0, 0)]
+    mc = [(0, 1, 0), (1, 1, 1), (-1, 0, 2)]
+    Ev = [-5.0, -2.0]
+    Ec = [3.0, 7.0, 11.0]
+    psi, E = inputs.plane_wave_states(dims, mv + mc, Ev + Ec)
+    g = O.sphere(dims, 9)
+    expect = np.zeros((len(g), len(g)), dtype=np.complex128)
+    pos = {tuple(x): i for i, x in enumerate(g)}
+    for iv, a in enumerate(mv):
+        for ic, b in enumerate(mc):
+            d = tuple(np.array(b) - np.array(a))
+            i = pos[d]
+            expect[i, i] += 2.0 / ((Ev[iv] - Ec[ic]) / O.HARTREE_EV)
+    Pr = O.P_to_G(O.P_rspace(psi, E, 2), dims, g)
+    Pg = O.P_gspace(psi, E, 2, dims, g)
+    assert np.max(np.abs(Pr - expect)) < 1e-12
+    assert np.max(np.abs(Pg - expect)) < 1e-12
+    # closed-form eps^-1 on those entries (V = 4 pi/(|G|^2 Omega), L = 1)
+    eps = O.eps_build(expect, g, 1.0)
+    inv = O.inverse_cholesky(eps)
+    for iv, a in enumerate(mv):
+        for ic, b in enumerate(mc):
+            d = np.array(b) - np.array(a)
+            i = pos[tuple(d)]
+            V = 4 * np.pi / ((2 * np.pi) ** 2 * np.sum(d * d))
+            assert abs(inv[i, i] - 1.0 / (1.0 - V * expect[i, i].real)) < 1e-13
+
+
+def test_parseval_on_full_grid():
+    """With every G of the grid kept, P~ = D P D^H with D unitary up to sqrt(N_r):
+    tr P~ = N_r tr P and ||P~||_F = N_r ||P||_F."""
+    dims = (4, 4, 3)
+    psi, E = inputs.make_states(0, 2, 5, 4, dims=dims)
+    P = O.P_rspace(psi, E, 2)
+    g = O.sphere(dims, 10 ** 6)
+    assert len(g) == 48
+    Pt = O.P_to_G(P, dims, g)
+    nr = 48
+    assert abs(np.trace(Pt) - nr * np.trace(P)) < 1e-13
+    assert abs(np.linalg.norm(Pt) - nr * np.linalg.norm(P)) < 1e-13
+
+
+def test_head_row_vanishes_by_orthogonality():
+    """G = 0 row and column of P~ vanish at q = 0 because occupied and unoccupied states are
+    orthogonal: M_vc(0) = <psi_v|psi_c> = 0."""
+    psi, E = inputs.make_states(8, 3, 10, 13)
+    g = O.sphere((8, 8, 8), 6)
+    Pt = O.P_gspace(psi, E, 3, (8, 8, 8), g)
+    scale = np.max(np.abs(Pt))
+    assert np.max(np.abs(Pt[0])) < 1e-14 * scale
+    assert np.max(np.abs(Pt[:, 0])) < 1e-14 * scale
+
+
+def test_rspace_route_equals_gspace_route():
+    """Sec. 4.1: the r-space route (P then row/column FFTs) and Eq. (gpsaceP) agree exactly on a
+    grid that holds the states (a discrete identity)."""
+    dims = (6, 5, 4)
+    psi, E = inputs.make_states(0, 3, 7, 17, dims=dims)
+    g = O.sphere(dims, 5)
+    Pr = O.P_to_G(O.P_rspace(psi, E, 3), dims, g)
+    Pg = O.P_gspace(psi, E, 3, dims, g)
+    assert np.linalg.norm(Pr - Pg) < 1e-14 * np.linalg.norm(Pg)
+
+
+# --------------------------------------------------------------------------- eps and inverse
+
+
+def test_coulomb_values():
+    g = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [1, 1, 1]])
+    V = O.coulomb(g, 2.0)
+    # G = 2 pi m / 2 = pi m, Omega = 8: V = 4 pi / (8 pi^2 |m|^2) = 1/(2 pi |m|^2)
+    assert V[0] == 0.0
+    assert np.allclose(V[1:], [1 / (2 * np.pi), 1 / (4 * np.pi), 1 / (6 * np.pi)])
+
+
+def test_eps_hpd_and_inverse_against_library():
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    res = O.eps_inv_path(psi, E, w.nv, (w.n,) * 3, w.gcut, w.cell_L)
+    eps = res["eps"]
+    assert eps.shape == (93, 93)
+    assert np.max(np.abs(eps - np.conj(eps.T))) < 1e-14
+    lam = np.linalg.eigvalsh(eps)
+    assert lam.min() > 1 - 1e-12            # -sqrt(V) P~ sqrt(V) is PSD, so eps >= I
+    assert abs(eps[0, 0] - 1) < 1e-15 and np.max(np.abs(eps[0, 1:])) < 1e-15
+    inv = res["epsinv"]
+    assert np.max(np.abs(inv @ eps - np.eye(93))) < 1e-12
+    assert np.max(np.abs(inv - np.linalg.inv(eps))) < 1e-12
+    L = O.cholesky_lower(eps)
+    assert np.max(np.abs(L - np.linalg.cholesky(eps))) < 1e-13
+
+
+def test_newton_iteration_matches_cholesky():
+    """Sec. 5.1 Newton iteration X <- X(2I - AX) converges to the same inverse."""
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    res = O.eps_inv_path(psi, E, w.nv, (w.n,) * 3, w.gcut, w.cell_L)
+    X, it = O.inverse_newton(res["eps"], tol=1e-11)
+    assert it < 40
+    assert np.max(np.abs(X - res["epsinv"])) < 1e-11
+
+
+def test_cholesky_rejects_indefinite():
+    A = np.array([[1.0, 2.0], [2.0, 1.0]], dtype=np.complex128)
+    with pytest.raises(O.NotPositiveDefinite):
+        O.cholesky_lower(A)
+
+
+def test_small_workload_rspace_vs_gspace():
+    """The 12^3 workload end to end: both routes agree to FP64 rounding."""
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    dims = (w.n,) * 3
+    a = O.eps_inv_path(psi, E, w.nv, dims, w.gcut, w.cell_L, route="rspace")
+    b = O.eps_inv_path(psi, E, w.nv, dims, w.gcut, w.cell_L, route="gspace")
+    assert np.linalg.norm(a["Pt"] - b["Pt"]) < 1e-13 * np.linalg.norm(b["Pt"])
+    assert np.max(np.abs(a["epsinv"] - b["epsinv"])) < 1e-13

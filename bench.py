@@ -1,0 +1,377 @@
+"""Benchmark of the static-polarizability path (Kim et al., arXiv 1810.07772) on one GB300.
+
+One step = one pass of the whole path over the 24^3 workload (N_r = 13824, N_v = 32, N_c = 480,
+k = 15360, N_g = 691): load the states (resident in HBM), pair densities, the Hermitian rank-k
+update P(r,r'), the row/column transforms to P~_GG', eps and its FP64 Cholesky inverse.
+
+Printed metric: P-build TFLOP/s = 4 k N_r (N_r + 1) / step time (the HERK's algorithmic flops over
+the time from resident states to eps^-1), with seconds per eps^-1, the error against the FP64
+oracle, and the rank-k update's fraction of the tensor-core peak.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
+
+Under torchrun with N > 1 each rank runs the same workload on its own GPU (independent replicas;
+the path has no exchange step at this size), timing is the max over ranks and `value` the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1810_07772_gb300 import inputs  # noqa: E402
+
+METRIC = "P-build TFLOP/s (4kN_r(N_r+1) per step, states resident -> eps^-1)"
+PRECISION = "fp16x3"
+WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
+             "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41)}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gw", "reference"], default="gw")
+    ap.add_argument("--precision", default=PRECISION)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the same-GPU precision comparison")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain",
+                    help="plain = the 24^3 configuration the metric is quoted on; the others are smaller "
+                         "configurations for profiling")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def aggregate(local_ms: float, local_units: float, world: int):
+    """Whole-job numbers: the slowest rank's time and the sum of the units all ranks processed."""
+    if world <= 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        pmax = max(r[2] for r in rows)
+        loaded = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded), "power_w_max": pmax}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+
+def cpu_baseline(w, psi, E, target_s=15.0):
+    """The FP64 oracle (plain C loop of Eq. Pstatic) on a bounded sample of rows of P for the same
+    workload, timed on the host cores; plus the oracle's P~ and eps^-1 (Eq. gpsaceP route) that the
+    GPU result is compared with."""
+    from oracle import gw_oracle as O
+    nr, k = w.nr, w.k
+    t0 = time.perf_counter()
+    O.P_rows_loop(psi, E, w.nv, 0, 16)
+    t16 = time.perf_counter() - t0
+    rows = int(max(16, min(nr, 16 * target_s / max(t16, 1e-3))))
+    rows = (rows // 16) * 16
+    t0 = time.perf_counter()
+    O.P_rows_loop(psi, E, w.nv, 16, 16 + rows)
+    t = time.perf_counter() - t0
+    flops = 8.0 * k * rows * nr          # 8 real flops per complex multiply-add, each element once
+    dims = (w.n,) * 3
+    g = O.sphere(dims, w.gcut)
+    Pt = O.P_gspace(psi, E, w.nv, dims, g)
+    inv = O.inverse_cholesky(O.eps_build(Pt, g, w.cell_L))
+    return ({"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": O.clib_threads(), "kind": "oracle",
+             "sample": f"{rows} rows of P(r,r') of {w.name} by the FP64 C loop of Eq. (Pstatic) "
+                       f"({rows * nr} of {nr * nr} elements, {t:.1f} s)"},
+            {"gvec": g, "Pt": Pt, "epsinv": inv})
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import gw_oracle as O
+    w = WORKLOADS[args.workload]
+    psi, E = inputs.make_workload_states(w)
+    rows = max(1, O.clib_threads())      # one row per host thread: every core busy, bounded step
+    for _ in range(args.warmup):
+        O.P_rows_loop(psi, E, w.nv, 0, rows)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r0 = (s * rows) % (w.nr - rows)
+        O.P_rows_loop(psi, E, w.nv, r0, r0 + rows)
+    t = time.perf_counter() - t0
+    value = 8.0 * w.k * rows * w.nr * args.steps / t / 1e12
+    sample = f"{rows} rows of P(r,r') per step of {w.name} by the FP64 C loop of Eq. (Pstatic)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.n] * 3, "nv": w.nv, "nc": w.nc, "gcut": w.gcut},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": O.clib_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_gw(args):
+    import torch
+    from paper_1810_07772_gb300 import gw
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    dims = (w.n,) * 3
+    psi, E = inputs.make_workload_states(w)
+    psi32 = psi.astype(np.complex64)
+    psi_d = torch.from_numpy(psi32).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gw.Context(local, stream)
+    flop_step = w.herk_flop()
+
+    def step():
+        ctx.load_states(psi_d, E, dims, w.nv)
+        ctx.build_P(args.precision)
+        ctx.P_to_G(w.gcut)
+        ctx.eps_inv("cholesky")
+
+    ctx.set_timing(True)
+    for _ in range(args.warmup):
+        step()
+    ng = ctx.ng
+    torch.cuda.synchronize()
+    ctx.reset_times()
+    launches0 = ctx.stats()["kernel_launches"]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    local_ms = ev0.elapsed_time(ev1)
+    st = ctx.stats()
+    launches = int(st["kernel_launches"] - launches0)
+    herk_ms = st["herk_ms_mean"]
+    times = ctx.times()
+    total_ms, total_flop = aggregate(local_ms, flop_step * args.steps, world)
+    value = total_flop / (total_ms * 1e-3) / 1e12
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the same calls with host buffers (pinned), copies inside the timed region
+    psi_h = torch.from_numpy(psi32).pin_memory()
+    inv_h = torch.empty((ng, ng), dtype=torch.complex128).pin_memory()
+
+    def step_e2e():
+        ctx.load_states(psi_h, E, dims, w.nv)
+        ctx.build_P(args.precision)
+        ctx.P_to_G(w.gcut)
+        ctx.eps_inv("cholesky", epsinv_out=inv_h)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    e_steps = max(3, args.steps // 3)
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+    e2e_ms, e2e_flop = aggregate(e2e_ms, flop_step, world)
+    h2d = psi32.nbytes
+    d2h = ng * ng * 16
+
+    # results of the last step for the error check
+    PG = torch.empty((ng, ng), dtype=torch.complex64, device=dev)
+    inv = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+    ctx.build_P(args.precision)
+    ctx.P_to_G(w.gcut, PG_out=PG)
+    ctx.eps_inv("cholesky", epsinv_out=inv)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    PGh, invh = PG.cpu().numpy(), inv.cpu().numpy()
+
+    # the same pass with the other arithmetic choices on this GPU (time per step and P~)
+    variants = {}
+    if not args.no_variants and world == 1:
+        for prec in ("fp32_simt", "tf32x3", "bf16x3"):
+            ctx.load_states(psi_d, E, dims, w.nv)
+            ctx.build_P(prec)
+            ctx.P_to_G(w.gcut)
+            ctx.eps_inv("cholesky")
+            torch.cuda.synchronize()
+            n = 3
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                ctx.load_states(psi_d, E, dims, w.nv)
+                ctx.build_P(prec)
+                ctx.P_to_G(w.gcut)
+                ctx.eps_inv("cholesky")
+            b.record(stream)
+            torch.cuda.synchronize()
+            PGv = torch.empty((ng, ng), dtype=torch.complex64, device=dev)
+            ctx.P_to_G(w.gcut, PG_out=PGv)
+            torch.cuda.synchronize()
+            variants[prec] = {"ms_per_step": a.elapsed_time(b) / n, "PG": PGv.cpu().numpy()}
+    ctx.close()
+
+    peaks, peak_src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))     # FP16 dense = BF16 dense rate
+    achieved = flop_step / (herk_ms * 1e-3) / 1e12 if herk_ms > 0 else None
+    # tensor-pipe work actually issued: 12 MMAs of 2*128*128*16 per 16-k chunk per tile
+    kpad = (w.k + 15) // 16 * 16
+    tensor_flop = st["herk_tiles"] * (kpad // 16) * 12 * 2.0 * 128 * 128 * 16
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "herk16_kernel<fp16> (tcgen05 kind::f16, 128x128 tiles, promoted TMEM windows)",
+                "peak_source": f"{peak_src} bf16_tflops_sustained (FP16:BF16 nominal ratio 1)",
+                "tensor_pipe_frac": (tensor_flop / (herk_ms * 1e-3) / 1e12 / peak) if herk_ms > 0 else None,
+                "herk_ms": herk_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16x3", "data": "synthetic",
+            "config": {"workload": w.name, "grid": [w.n] * 3, "N_r": w.nr, "nv": w.nv, "nc": w.nc, "k": w.k,
+                       "gcut": w.gcut, "N_g": ng, "precision": f"{args.precision}: FP16 hi+lo split, 3 products, "
+                       "FP32 accumulation (TMEM windows promoted to FP32); eps and eps^-1 in FP64",
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2: the operand planes (1.7 GB) and P (1.5 GB) stream "
+                             "through each step"},
+            "s_per_eps_inv": ms_per_step / 1e3,
+            "kernel_ms": times,
+            "roofline": roofline,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}
+    clocks = clk.summary()
+    line["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_baseline:
+        base, ref = cpu_baseline(w, psi, E)
+        line["cpu_baseline"] = base
+        assert np.array_equal(ref["gvec"], ctx.gvec)
+        line["err_vs_fp64"] = {
+            "P_G_rel_frobenius": float(np.linalg.norm(PGh - ref["Pt"]) / np.linalg.norm(ref["Pt"])),
+            "epsinv_head_abs": float(abs(invh[0, 0] - ref["epsinv"][0, 0])),
+            "epsinv_diag_max_abs": float(np.max(np.abs(np.diag(invh) - np.diag(ref["epsinv"])))),
+            "epsinv_max_abs": float(np.max(np.abs(invh - ref["epsinv"])))}
+        for prec, v in variants.items():
+            v["P_G_rel_frobenius"] = float(np.linalg.norm(v.pop("PG") - ref["Pt"]) / np.linalg.norm(ref["Pt"]))
+    for v in variants.values():
+        v.pop("PG", None)
+    if variants:
+        line["same_gpu_variants"] = variants
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gw(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * gw.h -- C ABI of the GB300 static-polarizability library (libgw.so).
+ *
+ * The library computes, on one GPU, the O(N^4) hot path of plane-wave GW as stated by Kim et
+ * al., "Scalable GW software for quasiparticle properties using OpenAtom" (arXiv 1810.07772):
+ *
+ *   states psi_n(r), energies E_n
+ *     -> pair densities f_vc(r) = conj(psi_v(r)) psi_c(r) sqrt(2/(E_c - E_v))      Eq. (fdef)
+ *     -> P(r,r') = -sum_vc f_vc(r) conj(f_vc(r'))   (Hermitian rank-k update)     Eq. (Pstatic)
+ *     -> P~(G,G') = sum_{r,r'} exp(-iG.r) P(r,r') exp(+iG'.r')  inside the sphere    Sec. 4.1
+ *     -> eps = I - sqrt(V) P~ sqrt(V),  V(G) = 4 pi / (Omega |G|^2), V(0) = 0        Sec. 5.1
+ *     -> eps^-1 (FP64)                                                             Sec. 5.1
+ *
+ * at q = 0 and one k-point, in Hartree atomic units.  Conventions shared by every call:
+ *
+ *   - Grid: n1 x n2 x n3 points, N_r = n1 n2 n3, index r = (j1 n2 + j2) n3 + j3 (C order).
+ *     The cell is cubic with edge cell_L bohr (Omega = cell_L^3); position r = cell_L (j1/n1,
+ *     j2/n2, j3/n3).
+ *   - G-vectors: G = 2 pi m / cell_L for integers m in FFT range ([-n/2, n - n/2) per axis).
+ *     The eps basis is every m with |m|^2 <= gcut, ordered by (|m|^2, m1, m2, m3) ascending,
+ *     so G = 0 is entry 0.
+ *   - Complex numbers are interleaved (re, im): complex64 = 2 x float, complex128 = 2 x double.
+ *     Matrices are row-major and dense (leading dimension = number of columns).
+ *
+ * Calls are asynchronous on the context's CUDA stream unless stated; device pointers must be
+ * valid on the context's device.  Every call returns a gw_status and never aborts, throws or
+ * traps.  Errors raised inside kernels (a wait that ran out, a non-positive Cholesky pivot) are
+ * recorded in a device status word and reported by the next synchronising call (gw_eps_inv,
+ * gw_sync).  One context must not be used by two host threads at once.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GW_API __attribute__((visibility("default")))
+#else
+#define GW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gw_status {
+    GW_OK = 0,
+    GW_E_INVALID = 1,     /* bad argument: size, pointer, NaN/Inf, E_v >= E_c, ...           */
+    GW_E_NOMEM = 2,       /* device allocation failed                                        */
+    GW_E_CUDA = 3,        /* a CUDA runtime call failed (message in gw_last_error)           */
+    GW_E_NOT_READY = 4,   /* call-order violation: e.g. gw_build_P before gw_load_states      */
+    GW_E_NUMERIC = 5,     /* eps is not Hermitian positive definite (Cholesky pivot <= 0)    */
+    GW_E_TIMEOUT = 6,     /* a bounded device-side wait ran out; the kernel returned early   */
+    GW_E_UNSUPPORTED = 7  /* valid request this build does not provide                       */
+} gw_status;
+
+/* Arithmetic used for the Hermitian rank-k update P = -F^T conj(F).                         */
+typedef enum gw_precision {
+    GW_PREC_TF32X3 = 0,    /* tcgen05 kind::tf32; every FP32 operand split x = hi + lo, both   */
+                           /* rounded to TF32; hi*hi + hi*lo + lo*hi, one TMEM accumulation over */
+                           /* all k (its truncating FP32 sum limits accuracy to ~1e-8 * k/8)    */
+    GW_PREC_BF16X3 = 1,    /* tcgen05 kind::f16 (BF16); same split and promotion as FP16X3       */
+    GW_PREC_TF32X1 = 2,    /* tcgen05 kind::tf32, one product (diagnostic, ~1e-4 relative)      */
+    GW_PREC_FP32_SIMT = 3, /* plain FP32 FMA on the CUDA cores (the same-GPU FP32 comparison)   */
+    GW_PREC_FP16X3 = 4     /* tcgen05 kind::f16 (FP16) with one global power-of-two scale; the   */
+                           /* three-product split, short TMEM windows promoted to FP32 registers */
+} gw_precision;
+
+typedef enum gw_inv_method {
+    GW_INV_CHOLESKY = 0,   /* FP64 blocked Cholesky eps = L L^H, then eps^-1 = L^-H L^-1        */
+    GW_INV_NEWTON = 1      /* FP64 Newton iteration X <- X (2I - eps X) of Sec. 5.1, from        */
+                           /* X0 = eps^H / max_i sum_j |(eps eps^H)_ij|, until max |dX| < 1e-11  */
+} gw_inv_method;
+
+typedef enum gw_dtype { GW_C64 = 0, GW_C128 = 1 } gw_dtype;
+
+typedef struct gw_ctx gw_ctx;
+
+/* Static string for a status code (never NULL). */
+GW_API const char *gw_status_str(int status);
+
+/* ABI version of this header: 1. */
+GW_API int gw_version(void);
+
+/*
+ * Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The context owns every internal device buffer; they are freed by
+ * gw_destroy.  *out is set to NULL on failure.
+ */
+GW_API gw_status gw_create(gw_ctx **out, int device, void *stream);
+GW_API gw_status gw_destroy(gw_ctx *ctx);
+GW_API gw_status gw_set_stream(gw_ctx *ctx, void *stream);
+
+/* Copy the last error message of this context into buf (NUL-terminated, at most n bytes). */
+GW_API gw_status gw_last_error(const gw_ctx *ctx, char *buf, size_t n);
+
+/*
+ * Load the states and energies (Sec. 3 item 1: the DFT input).  Eq. (fdef) at q = 0.
+ *   psi          [nv + nc][N_r] complex, occupied states first, r contiguous.  Stored on the
+ *                device as complex64 (complex128 input is rounded).  psi_on_device != 0 means
+ *                a device pointer, else a host pointer (copied synchronously to the stream).
+ *   energies_eV  host array [nv + nc] in eV (divided by 27.211386245988 to Hartree); the
+ *                weights 2 / (E_c - E_v) are formed in FP64 on the device.
+ * Requires nv, nc >= 1, n1, n2, n3 in [2, 64], nv + nc <= N_r, cell_L > 0, finite energies and
+ * max(E_v) < min(E_c); otherwise GW_E_INVALID.  The buffers are borrowed for the call only.
+ * Invalidates any P, P~ or eps of an earlier load.
+ */
+GW_API gw_status gw_load_states(gw_ctx *ctx, int n1, int n2, int n3, double cell_L, int nv, int nc,
+                         const void *psi, int psi_dtype, int psi_on_device,
+                         const double *energies_eV);
+
+/*
+ * Form the pair densities and the Hermitian rank-k update (Eq. fdef and the outer product of
+ * Sec. 4.1; Eq. Pstatic):  P(r,r') = -sum_{v,c} f_vc(r) conj(f_vc(r')).
+ *   precision  a gw_precision.
+ *   P_out      NULL, or a device buffer of N_r x N_r complex64 that receives a copy of P.
+ * P itself stays in the context (full Hermitian matrix, both triangles written, real diagonal)
+ * and can be read with gw_get_buffer(GW_BUF_P).  Requires gw_load_states.
+ */
+GW_API gw_status gw_build_P(gw_ctx *ctx, int precision, void *P_out);
+
+/*
+ * The row and column transforms of Sec. 4.1, restricted to the sphere |m|^2 <= gcut:
+ *   P^(G, r') = sum_r exp(-i G.r) P(r, r'),  P~(G, G') = sum_r' P^(G, r') exp(+i G'.r').
+ *   ng_out    host int, receives N_g.
+ *   gvec_out  NULL or host int array [N_g][3] receiving the integer vectors m in basis order
+ *             (up to max_ng entries are written when gvec_out != NULL; GW_E_INVALID if
+ *             N_g > max_ng).
+ *   PG_out    NULL or a device buffer of N_g x N_g complex64 receiving P~.
+ * Requires gw_build_P.  gcut must keep the sphere inside the grid: 4 gcut < min(n_i)^2.
+ */
+GW_API gw_status gw_P_to_G(gw_ctx *ctx, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out);
+
+/*
+ * eps_GG' = delta_GG' - sqrt(V(G)) P~_GG' sqrt(V(G')) and its inverse, both complex128 and
+ * formed in FP64 (Sec. 5.1).  eps_out / epsinv_out: NULL, or N_g x N_g complex128 buffers on
+ * the device or the host (host buffers are filled before the call returns).  This call
+ * synchronises the stream and returns any device-side status (GW_E_NUMERIC if a Cholesky
+ * pivot is <= 0, GW_E_TIMEOUT if a kernel wait ran out).  Requires gw_P_to_G.
+ */
+GW_API gw_status gw_eps_inv(gw_ctx *ctx, int method, void *eps_out, void *epsinv_out);
+
+/* Synchronise the context stream and return the device-side status word (then clear it). */
+GW_API gw_status gw_sync(gw_ctx *ctx);
+
+/* Internal buffers, exposed read-only for inspection and tests.                               */
+typedef enum gw_buffer {
+    GW_BUF_P = 0,        /* N_r x N_r complex64, P(r, r')                                      */
+    GW_BUF_F = 1,        /* pair-density operand planes, layout described below                */
+    GW_BUF_PG = 2,       /* N_g x N_g complex64, P~                                             */
+    GW_BUF_EPS = 3,      /* N_g x N_g complex128, eps                                           */
+    GW_BUF_EPSINV = 4,   /* N_g x N_g complex128, eps^-1                                        */
+    GW_BUF_WEIGHTS = 5   /* [nv][nc] float, sqrt(2 / (E_c - E_v)) in Hartree^-1/2              */
+} gw_buffer;
+
+/*
+ * Return the device pointer and byte size of an internal buffer (GW_E_NOT_READY if it has not
+ * been produced yet).  Pointers stay valid until the next gw_load_states or gw_destroy.
+ *
+ * GW_BUF_F layout (precisions TF32X3 / TF32X1): float planes, k = v * nc + c padded with zeros
+ * to a multiple of 8 (kpad), rows padded with zeros to a multiple of 256 (nr_pad).  For chunk
+ * kc = k / 8 and plane p (0 = Re hi, 1 = Re lo, 2 = Im hi, 3 = Im lo; TF32X1 keeps only
+ * p = 0 and 2, stored as planes 0 and 1), the element (r, k) sits at float offset
+ *   ((kc * nplanes + p) * nr_pad + (r / 8) * 8) * 8 + ((k % 8) / 4) * 32 + (r % 8) * 4 + k % 4.
+ * For GW_PREC_FP32_SIMT it is [kpad][nr_pad] complex64 (f itself, r contiguous).
+ * For GW_PREC_FP16X3 / GW_PREC_BF16X3 it is four 16-bit planes (FP16 or BF16 bit patterns; FP16
+ * values carry the factor 2^e of the scale), k padded to a multiple of 16: for kc = k / 16 the
+ * element (r, k) of plane p sits at 16-bit offset
+ *   ((kc * 4 + p) * nr_pad + (r / 8) * 8) * 16 + ((k % 16) / 8) * 64 + (r % 8) * 8 + k % 8.
+ */
+GW_API gw_status gw_get_buffer(gw_ctx *ctx, int which, void **ptr, size_t *bytes);
+
+/* Sizes of the loaded problem: dims[0..7] = n1, n2, n3, N_r, nv, nc, N_g (0 before gw_P_to_G),
+ * nr_pad. */
+GW_API gw_status gw_get_dims(gw_ctx *ctx, int *dims8);
+
+/*
+ * Per-kernel device times (ms) of the most recent gw_build_P / gw_P_to_G / gw_eps_inv, taken
+ * with CUDA events on the context stream when timing is enabled (gw_set_timing(ctx, 1)); the
+ * events never block the calls, they are read at the next synchronisation.  times[0] = pair
+ * densities, [1] = rank-k update, [2] = row transform, [3] = conjugate transpose, column
+ * transform and Hermitian part, [4] = eps build, [5] = eps inverse.  Synchronises the stream.
+ * gw_reset_times clears the running means reported by gw_get_stats.
+ */
+GW_API gw_status gw_set_timing(gw_ctx *ctx, int enable);
+GW_API gw_status gw_get_times(gw_ctx *ctx, float *times6);
+GW_API gw_status gw_reset_times(gw_ctx *ctx);
+
+/*
+ * Counters (synchronises the stream): stats8[0] = kernels this library has launched in this
+ * process, [1] = Newton iterations of the last GW_INV_NEWTON inverse, [2] = mean rank-k update
+ * time in ms over the timed calls since gw_reset_times, [3] = number of those calls, [4] = the
+ * FP16 scale exponent e of the last 16-bit build, [5] = rank-k update tiles, [6] and [7] = the
+ * window and flush lengths of the 16-bit update.
+ */
+GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
+
+/*
+ * Window length of the 16-bit rank-k update: the tensor core accumulates `window_chunks` chunks
+ * of 16 k (1..64, default 2) in TMEM before they are added into FP32 registers, and every
+ * `flush_windows` windows (1..4096, default 16) the registers are added into P.  Shorter windows
+ * and flushes mean smaller accumulation error.
+ */
+GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_windows);
+
+/* Upper bound, in milliseconds, of any single device-side wait (default 2000).  A wait that
+ * runs out makes its kernel record GW_E_TIMEOUT and return early. */
+GW_API gw_status gw_set_wait_limit(gw_ctx *ctx, double ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_H */

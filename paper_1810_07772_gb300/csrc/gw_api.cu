@@ -1,0 +1,835 @@
+// C ABI of libgw: context management, argument checks and the host-side orchestration of the
+// kernels of the static-polarizability path (Kim et al., arXiv 1810.07772, Sec. 4.1 and 5.1).
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gw_internal.cuh"
+
+using namespace gw;
+
+namespace gw {
+void count_launches(int n);
+}
+
+struct gw_ctx {
+    Ctx c;
+};
+
+namespace {
+
+constexpr double HARTREE_EV = 27.211386245988;
+constexpr double PI = 3.14159265358979323846;
+constexpr int CHOL_NB = 32;
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+}
+
+gw_status fail(Ctx &c, gw_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c.last_error = buf;
+    return st;
+}
+
+gw_status cuda_fail(Ctx &c, cudaError_t e, const char *where)
+{
+    cudaGetLastError();  // clear a sticky-free error so the context stays usable
+    if (e == cudaErrorMemoryAllocation)
+        return fail(c, GW_E_NOMEM, "%s: out of device memory", where);
+    return fail(c, GW_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define GW_CUDA(call, where)                \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess)              \
+            return cuda_fail(c, e_, where); \
+    } while (0)
+
+#define GW_TRY(expr)                \
+    do {                            \
+        gw_status s_ = (expr);      \
+        if (s_ != GW_OK)            \
+            return s_;              \
+    } while (0)
+
+// (Re)allocate a device buffer if its capacity is below `bytes`; contents are not kept.
+template <typename T>
+gw_status ensure(Ctx &c, T *&p, size_t &cap, size_t bytes, const char *what)
+{
+    if (p && cap >= bytes)
+        return GW_OK;
+    dfree(p);
+    cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return cuda_fail(c, e, what);
+    }
+    cap = bytes;
+    return GW_OK;
+}
+
+std::atomic<unsigned long long> g_launches{0};
+
+// Kernel-boundary events: build_P 0..2, P_to_G 3..5, eps_inv 6..8.  Recording never blocks; the
+// elapsed times are read at the next synchronisation (gw_eps_inv, gw_get_times).
+void record(Ctx &c, int i)
+{
+    if (c.timing) {
+        cudaEventRecord(c.ev[i], c.stream);
+        c.ev_mask |= 1u << i;
+    }
+}
+
+void resolve_times(Ctx &c)
+{
+    static const int pairs[6][2] = {{0, 1}, {1, 2}, {3, 4}, {4, 5}, {6, 7}, {7, 8}};
+    unsigned used = 0;
+    for (int t = 0; t < 6; ++t) {
+        const unsigned need = (1u << pairs[t][0]) | (1u << pairs[t][1]);
+        if ((c.ev_mask & need) == need) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c.ev[pairs[t][0]], c.ev[pairs[t][1]]) == cudaSuccess) {
+                c.times[t] = ms;
+                c.times_sum[t] += ms;
+                c.times_n[t] += 1;
+            }
+            used |= need;
+        }
+    }
+    c.ev_mask &= ~used;  // events shared by two pairs are cleared only after both were read
+    cudaGetLastError();
+}
+
+// Device status word -> gw_status (the word is cleared).
+gw_status read_device_status(Ctx &c)
+{
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream synchronize");
+    uint32_t word = 0;
+    e = cudaMemcpy(&word, c.d_err, sizeof word, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "status readback");
+    if (word == 0)
+        return GW_OK;
+    cudaMemset(c.d_err, 0, sizeof(uint32_t));
+    const uint32_t code = word & 0xFF, site = (word >> 8) & 0xFF, detail = word >> 16;
+    static const char *sites[] = {"?",
+                                  "rank-k update producer",
+                                  "rank-k update MMA issuer",
+                                  "rank-k update epilogue",
+                                  "rank-k update drain",
+                                  "Cholesky pivot",
+                                  "input check"};
+    const char *sname = site < sizeof(sites) / sizeof(sites[0]) ? sites[site] : "?";
+    if (code == GW_E_NUMERIC)
+        return fail(c, GW_E_NUMERIC, "eps is not positive definite: Cholesky pivot %u <= 0", detail);
+    if (code == GW_E_INVALID)
+        return fail(c, GW_E_INVALID, "non-finite value in the states (%s)", sname);
+    return fail(c, static_cast<gw_status>(code), "device wait ran out in the %s (block %u)", sname, detail);
+}
+
+// Upper-triangle tiles of the rank-k update (128-row blocks i of r, 256-row blocks j of r'),
+// kept when the tile reaches the diagonal or above: 256 j + 255 >= 128 i.  Ordered in groups of
+// 8 column blocks so that CTAs resident at the same time share operand rows in L2.
+std::vector<int2> herk_tiles(int nr_pad, int bm, int bn)
+{
+    const int nrb = nr_pad / bm, ncb = nr_pad / bn;
+    std::vector<int2> t;
+    const int GROUP = 8;
+    for (int j0 = 0; j0 < ncb; j0 += GROUP)
+        for (int i = 0; i < nrb; ++i)
+            for (int j = j0; j < std::min(ncb, j0 + GROUP); ++j)
+                if (bn * j + bn - 1 >= bm * i)
+                    t.push_back(make_int2(i, j));
+    return t;
+}
+
+// The eps basis: integer m in FFT range with |m|^2 <= gcut, ordered by (|m|^2, m1, m2, m3).
+std::vector<std::array<int, 3>> sphere_vectors(const int n[3], int gcut)
+{
+    std::vector<std::array<int, 4>> pts;
+    for (int a = -(n[0] / 2); a < n[0] - n[0] / 2; ++a)
+        for (int b = -(n[1] / 2); b < n[1] - n[1] / 2; ++b)
+            for (int d = -(n[2] / 2); d < n[2] - n[2] / 2; ++d) {
+                const int q = a * a + b * b + d * d;
+                if (q <= gcut)
+                    pts.push_back({q, a, b, d});
+            }
+    std::sort(pts.begin(), pts.end());
+    std::vector<std::array<int, 3>> out;
+    out.reserve(pts.size());
+    for (auto &p : pts)
+        out.push_back({p[1], p[2], p[3]});
+    return out;
+}
+
+int mod(int a, int n)
+{
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+gw_status build_plan(Ctx &c, int gcut)
+{
+    const int n[3] = {c.n1, c.n2, c.n3};
+    const auto g = sphere_vectors(n, gcut);
+    const int ng = static_cast<int>(g.size());
+    std::vector<int> m3vals;
+    for (auto &v : g)
+        m3vals.push_back(v[2]);
+    std::sort(m3vals.begin(), m3vals.end());
+    m3vals.erase(std::unique(m3vals.begin(), m3vals.end()), m3vals.end());
+    std::vector<std::array<int, 2>> dpairs;
+    for (auto &v : g)
+        dpairs.push_back({v[1], v[2]});
+    std::sort(dpairs.begin(), dpairs.end());
+    dpairs.erase(std::unique(dpairs.begin(), dpairs.end()), dpairs.end());
+    const int c3 = static_cast<int>(m3vals.size()), cd = static_cast<int>(dpairs.size());
+
+    std::vector<int> m3list(c3), disk(2 * cd), gmap(2 * ng);
+    for (int i = 0; i < c3; ++i)
+        m3list[i] = mod(m3vals[i], n[2]);
+    for (int d = 0; d < cd; ++d) {
+        disk[2 * d] = mod(dpairs[d][0], n[1]);
+        disk[2 * d + 1] = static_cast<int>(std::lower_bound(m3vals.begin(), m3vals.end(), dpairs[d][1]) - m3vals.begin());
+    }
+    for (int i = 0; i < ng; ++i) {
+        gmap[2 * i] = mod(g[i][0], n[0]);
+        const std::array<int, 2> key = {g[i][1], g[i][2]};
+        gmap[2 * i + 1] = static_cast<int>(std::lower_bound(dpairs.begin(), dpairs.end(), key) - dpairs.begin());
+    }
+    std::vector<float2> tw;
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < n[a]; ++t) {
+            const double ph = 2.0 * PI * t / n[a];
+            tw.push_back(make_float2(static_cast<float>(std::cos(ph)), static_cast<float>(std::sin(ph))));
+        }
+    const size_t ints = (size_t)c3 + 2 * cd + 2 * ng;
+    const size_t int_bytes = ((ints * sizeof(int) + 15) / 16) * 16;
+    const size_t bytes = int_bytes + tw.size() * sizeof(float2);
+    GW_TRY(ensure(c, c.d_plan_mem, c.cap.plan, bytes, "plan buffer"));
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data(), m3list.data(), c3 * sizeof(int));
+    std::memcpy(host.data() + c3 * sizeof(int), disk.data(), 2 * cd * sizeof(int));
+    std::memcpy(host.data() + (c3 + 2 * cd) * sizeof(int), gmap.data(), 2 * ng * sizeof(int));
+    std::memcpy(host.data() + int_bytes, tw.data(), tw.size() * sizeof(float2));
+    GW_CUDA(cudaMemcpy(c.d_plan_mem, host.data(), bytes, cudaMemcpyHostToDevice), "plan upload");
+    DftPlan &p = c.plan;
+    p.n[0] = n[0];
+    p.n[1] = n[1];
+    p.n[2] = n[2];
+    p.ng = ng;
+    p.c3 = c3;
+    p.cd = cd;
+    p.m3list = c.d_plan_mem;
+    p.disk = c.d_plan_mem + c3;
+    p.gmap = c.d_plan_mem + c3 + 2 * cd;
+    p.tw = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(c.d_plan_mem) + int_bytes);
+
+    c.gvec.assign(3 * ng, 0);
+    std::vector<double> sv(ng, 0.0);
+    const double omega = c.cell_L * c.cell_L * c.cell_L;
+    const double gunit = 2.0 * PI / c.cell_L;
+    for (int i = 0; i < ng; ++i) {
+        c.gvec[3 * i] = g[i][0];
+        c.gvec[3 * i + 1] = g[i][1];
+        c.gvec[3 * i + 2] = g[i][2];
+        const double m2 = (double)g[i][0] * g[i][0] + (double)g[i][1] * g[i][1] + (double)g[i][2] * g[i][2];
+        sv[i] = m2 > 0 ? std::sqrt(4.0 * PI / (omega * gunit * gunit * m2)) : 0.0;  // V(0) := 0
+    }
+    GW_TRY(ensure(c, c.d_sv, c.cap.sv, ng * sizeof(double), "sqrt(V) buffer"));
+    GW_CUDA(cudaMemcpy(c.d_sv, sv.data(), ng * sizeof(double), cudaMemcpyHostToDevice), "sqrt(V) upload");
+    c.gcut = gcut;
+    c.ng = ng;
+    return GW_OK;
+}
+
+// eps^-1 by blocked Cholesky (eps = L L^H, Y = L^-1, eps^-1 = Y^H Y).
+gw_status inverse_cholesky(Ctx &c)
+{
+    const int N = c.ng, NB = CHOL_NB;
+    const int nblk = (N + NB - 1) / NB;
+    // workspace: A (N*N) | Y (N*N) | T (NB*N) | W (N*NB) | Dinv (nblk*NB*NB)
+    const size_t need = (size_t)2 * N * N + 2 * (size_t)NB * N + (size_t)nblk * NB * NB;
+    GW_TRY(ensure(c, c.d_work, c.cap.work, need * sizeof(double2), "inverse workspace"));
+    double2 *A = c.d_work, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)NB * N,
+            *Dinv = W + (size_t)N * NB;
+    cudaStream_t s = c.stream;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+    GW_CUDA(cudaMemcpyAsync(A, c.d_eps, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s), "copy eps");
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int k0 = kb * NB, kn = std::min(NB, N - k0), rest = N - k0 - kn;
+        double2 *Dk = Dinv + (size_t)kb * NB * NB;
+        GW_CUDA(launch_chol_diag(A + (size_t)k0 * N + k0, N, kn, Dk, NB, k0, c.d_err, s), "Cholesky diagonal block");
+        if (rest > 0) {
+            double2 *panel = A + (size_t)(k0 + kn) * N + k0;
+            GW_CUDA(launch_zgemm(rest, kn, kn, one, panel, N, 0, Dk, NB, 1, zero, W, NB, s), "panel solve");
+            GW_CUDA(launch_copy_block(W, NB, panel, N, rest, kn, s), "panel store");
+            GW_CUDA(launch_zgemm(rest, rest, kn, mone, W, NB, 0, W, NB, 1, one, A + (size_t)(k0 + kn) * N + k0 + kn,
+                                 N, s),
+                    "trailing update");
+        }
+    }
+    GW_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * N * sizeof(double2), s), "clear Y");
+    for (int ib = 0; ib < nblk; ++ib) {
+        const int i0 = ib * NB, in = std::min(NB, N - i0);
+        const double2 *Di = Dinv + (size_t)ib * NB * NB;
+        GW_CUDA(launch_copy_block(Di, NB, Y + (size_t)i0 * N + i0, N, in, in, s), "diagonal inverse store");
+        if (ib > 0) {
+            GW_CUDA(launch_zgemm(in, i0, i0, one, A + (size_t)i0 * N, N, 0, Y, N, 0, zero, T, N, s), "L Y product");
+            GW_CUDA(launch_zgemm(in, i0, in, mone, Di, NB, 0, T, N, 0, zero, Y + (size_t)i0 * N, N, s),
+                    "off-diagonal inverse");
+        }
+    }
+    GW_CUDA(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, c.d_epsinv, N, s), "Y^H Y");
+    return GW_OK;
+}
+
+// eps^-1 by the Newton iteration of Sec. 5.1: X0 = eps^H / max_i sum_j |(eps eps^H)_ij|,
+// X <- X (2I - eps X) until every entry moves by less than 1e-11.
+gw_status inverse_newton(Ctx &c)
+{
+    const int N = c.ng;
+    const size_t nn = (size_t)N * N;
+    GW_TRY(ensure(c, c.d_work, c.cap.work, 3 * nn * sizeof(double2), "Newton workspace"));
+    GW_TRY(ensure(c, c.d_scal, c.cap.scal, 4 * sizeof(double), "Newton scalars"));
+    double2 *X = c.d_work, *T = X + nn, *Xn = T + nn;
+    cudaStream_t s = c.stream;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    GW_CUDA(launch_zgemm(N, N, N, one, c.d_eps, N, 0, c.d_eps, N, 1, zero, T, N, s), "eps eps^H");
+    GW_CUDA(launch_row_abs_sum_max(T, N, c.d_scal, s), "row sums");
+    GW_CUDA(launch_scaled_adjoint(c.d_eps, N, c.d_scal, X, s), "X0");
+    int it = 0;
+    for (it = 1; it <= 100; ++it) {
+        GW_CUDA(launch_zgemm(N, N, N, one, c.d_eps, N, 0, X, N, 0, zero, T, N, s), "eps X");
+        GW_CUDA(launch_two_minus(T, N, s), "2I - eps X");
+        GW_CUDA(launch_zgemm(N, N, N, one, X, N, 0, T, N, 0, zero, Xn, N, s), "X (2I - eps X)");
+        GW_CUDA(launch_max_absdiff(Xn, X, nn, c.d_scal + 1, s), "max |dX|");
+        double diff = 0;
+        GW_CUDA(cudaMemcpyAsync(&diff, c.d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "dX readback");
+        GW_CUDA(cudaStreamSynchronize(s), "Newton sync");
+        std::swap(X, Xn);
+        if (diff < 1e-11)
+            break;
+    }
+    c.newton_iters = it;
+    GW_CUDA(cudaMemcpyAsync(c.d_epsinv, X, nn * sizeof(double2), cudaMemcpyDeviceToDevice, s), "store eps^-1");
+    return GW_OK;
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+void gw::count_launches(int n)
+{
+    g_launches += (unsigned long long)n;
+}
+
+void Ctx::release()
+{
+    dfree(d_err);
+    dfree(d_psiT);
+    dfree(d_E);
+    dfree(d_sw);
+    dfree(d_F);
+    dfree(d_P);
+    dfree(d_tiles);
+    dfree(d_plan_mem);
+    dfree(d_Q);
+    dfree(d_QT);
+    dfree(d_PG);
+    dfree(d_sv);
+    dfree(d_eps);
+    dfree(d_epsinv);
+    dfree(d_work);
+    dfree(d_scal);
+    dfree(d_psi);
+    dfree(d_psi128);
+    dfree(d_small);
+    for (auto &e : ev)
+        if (e)
+            cudaEventDestroy(e);
+}
+
+extern "C" {
+
+const char *gw_status_str(int st)
+{
+    switch (st) {
+    case GW_OK: return "ok";
+    case GW_E_INVALID: return "invalid argument";
+    case GW_E_NOMEM: return "out of device memory";
+    case GW_E_CUDA: return "CUDA error";
+    case GW_E_NOT_READY: return "call-order violation";
+    case GW_E_NUMERIC: return "eps not positive definite";
+    case GW_E_TIMEOUT: return "device wait ran out";
+    case GW_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+int gw_version(void)
+{
+    return 1;
+}
+
+gw_status gw_create(gw_ctx **out, int device, void *stream)
+{
+    if (!out)
+        return GW_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GW_E_INVALID;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return GW_E_CUDA;
+    if (prop.major != 10 || prop.minor != 3)
+        return GW_E_UNSUPPORTED;  // the kernels are built for sm_103a only
+    gw_ctx *h = new (std::nothrow) gw_ctx;
+    if (!h)
+        return GW_E_NOMEM;
+    Ctx &c = h->c;
+    c.device = device;
+    c.stream = static_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c.d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c.d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        c.release();
+        delete h;
+        return GW_E_CUDA;
+    }
+    for (auto &e : c.ev)
+        cudaEventCreate(&e);
+    *out = h;
+    return GW_OK;
+}
+
+gw_status gw_destroy(gw_ctx *h)
+{
+    if (!h)
+        return GW_E_INVALID;
+    cudaSetDevice(h->c.device);
+    cudaStreamSynchronize(h->c.stream);
+    h->c.release();
+    delete h;
+    return GW_OK;
+}
+
+gw_status gw_set_stream(gw_ctx *h, void *stream)
+{
+    if (!h)
+        return GW_E_INVALID;
+    h->c.stream = static_cast<cudaStream_t>(stream);
+    return GW_OK;
+}
+
+gw_status gw_last_error(const gw_ctx *h, char *buf, size_t n)
+{
+    if (!h || !buf || n == 0)
+        return GW_E_INVALID;
+    std::snprintf(buf, n, "%s", h->c.last_error.c_str());
+    return GW_OK;
+}
+
+gw_status gw_set_wait_limit(gw_ctx *h, double ms)
+{
+    if (!h || !(ms > 0.0) || ms > 600000.0)
+        return GW_E_INVALID;
+    h->c.wait_limit_ms = ms;
+    return GW_OK;
+}
+
+gw_status gw_set_herk_window(gw_ctx *h, int window_chunks, int flush_windows)
+{
+    if (!h || window_chunks < 1 || window_chunks > 64 || flush_windows < 1 || flush_windows > 4096)
+        return GW_E_INVALID;
+    h->c.herk_W = window_chunks;
+    h->c.herk_L = flush_windows;
+    return GW_OK;
+}
+
+gw_status gw_set_timing(gw_ctx *h, int enable)
+{
+    if (!h)
+        return GW_E_INVALID;
+    h->c.timing = enable != 0;
+    return GW_OK;
+}
+
+gw_status gw_get_times(gw_ctx *h, float *t6)
+{
+    if (!h || !t6)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    GW_CUDA(cudaStreamSynchronize(c.stream), "timing sync");
+    resolve_times(c);
+    for (int i = 0; i < 6; ++i)
+        t6[i] = c.times[i];
+    return GW_OK;
+}
+
+gw_status gw_get_stats(gw_ctx *h, double *s8)
+{
+    if (!h || !s8)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    GW_CUDA(cudaStreamSynchronize(c.stream), "stats sync");
+    resolve_times(c);
+    s8[0] = (double)g_launches.load();
+    s8[1] = c.newton_iters;
+    s8[2] = c.times_n[1] ? c.times_sum[1] / c.times_n[1] : 0.0;
+    s8[3] = c.times_n[1];
+    int e = 0;
+    if (c.d_small && (c.F_prec == GW_PREC_FP16X3 || c.F_prec == GW_PREC_BF16X3))
+        cudaMemcpy(&e, c.d_small + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    s8[4] = e;
+    s8[5] = c.n_tiles;
+    s8[6] = c.herk_W;
+    s8[7] = c.herk_L;
+    return GW_OK;
+}
+
+gw_status gw_reset_times(gw_ctx *h)
+{
+    if (!h)
+        return GW_E_INVALID;
+    for (int i = 0; i < 6; ++i) {
+        h->c.times_sum[i] = 0.0;
+        h->c.times_n[i] = 0;
+    }
+    return GW_OK;
+}
+
+gw_status gw_load_states(gw_ctx *h, int n1, int n2, int n3, double cell_L, int nv, int nc, const void *psi,
+                         int psi_dtype, int psi_on_device, const double *energies_eV)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (n1 < 2 || n2 < 2 || n3 < 2 || n1 > 64 || n2 > 64 || n3 > 64)
+        return fail(c, GW_E_INVALID, "grid %d x %d x %d outside [2, 64]^3", n1, n2, n3);
+    const int nr = n1 * n2 * n3;
+    if (nv < 1 || nc < 1 || (long long)nv + nc > nr)
+        return fail(c, GW_E_INVALID, "need nv, nc >= 1 and nv + nc <= N_r (got %d, %d, %d)", nv, nc, nr);
+    if ((long long)nv * nc > (1LL << 30))
+        return fail(c, GW_E_INVALID, "nv * nc too large");
+    if (!(cell_L > 0.0) || !std::isfinite(cell_L))
+        return fail(c, GW_E_INVALID, "cell_L must be positive and finite");
+    if (!psi || !energies_eV)
+        return fail(c, GW_E_INVALID, "null psi or energies");
+    if (psi_dtype != GW_C64 && psi_dtype != GW_C128)
+        return fail(c, GW_E_INVALID, "psi_dtype must be GW_C64 or GW_C128");
+    const int nb = nv + nc;
+    double emax_v = -INFINITY, emin_c = INFINITY;
+    std::vector<double> Eh(nb);
+    for (int i = 0; i < nb; ++i) {
+        if (!std::isfinite(energies_eV[i]))
+            return fail(c, GW_E_INVALID, "energy %d is not finite", i);
+        Eh[i] = energies_eV[i] / HARTREE_EV;
+        if (i < nv)
+            emax_v = std::max(emax_v, energies_eV[i]);
+        else
+            emin_c = std::min(emin_c, energies_eV[i]);
+    }
+    if (!(emax_v < emin_c))
+        return fail(c, GW_E_INVALID, "need max(E_v) < min(E_c) (got %g >= %g eV)", emax_v, emin_c);
+    if (psi_on_device && !is_device_pointer(psi))
+        return fail(c, GW_E_INVALID, "psi_on_device set but psi is not a device pointer");
+
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    c.loaded = c.P_ready = c.PG_ready = c.eps_ready = false;
+    c.n1 = n1;
+    c.n2 = n2;
+    c.n3 = n3;
+    c.nr = nr;
+    c.nv = nv;
+    c.nc = nc;
+    c.nb = nb;
+    c.cell_L = cell_L;
+    c.k = nv * nc;
+    c.kpad = ((c.k + HERK_KC - 1) / HERK_KC) * HERK_KC;
+    c.sw_max = static_cast<float>(std::sqrt(2.0 / ((emin_c - emax_v) / HARTREE_EV)));
+    c.nr_pad = ((nr + HERK_BN - 1) / HERK_BN) * HERK_BN;
+    c.gcut = -1;
+    c.ng = 0;
+    const size_t n = (size_t)nb * nr;
+    cudaStream_t s = c.stream;
+    GW_TRY(ensure(c, c.d_psiT, c.cap.psiT, n * sizeof(float2), "transposed states"));
+    GW_TRY(ensure(c, c.d_E, c.cap.E, nb * sizeof(double), "energies"));
+    GW_TRY(ensure(c, c.d_sw, c.cap.sw, (size_t)c.k * sizeof(float), "weights"));
+    const float2 *src = nullptr;
+    if (psi_dtype == GW_C64 && psi_on_device) {
+        src = static_cast<const float2 *>(psi);
+    } else {
+        GW_TRY(ensure(c, c.d_psi, c.cap.psi, n * sizeof(float2), "state staging"));
+        if (psi_dtype == GW_C64) {
+            GW_CUDA(cudaMemcpyAsync(c.d_psi, psi, n * sizeof(float2), cudaMemcpyHostToDevice, s), "copy states");
+        } else {
+            const double2 *p128 = static_cast<const double2 *>(psi);
+            if (!psi_on_device) {
+                GW_TRY(ensure(c, c.d_psi128, c.cap.psi128, n * sizeof(double2), "complex128 staging"));
+                GW_CUDA(cudaMemcpyAsync(c.d_psi128, psi, n * sizeof(double2), cudaMemcpyHostToDevice, s),
+                        "copy states");
+                p128 = c.d_psi128;
+            }
+            GW_CUDA(launch_c128_to_c64(p128, n, c.d_psi, s), "round states");
+        }
+        src = c.d_psi;
+    }
+    GW_CUDA(launch_check_finite(src, n, c.d_err, s), "check states");
+    GW_CUDA(launch_transpose_states(src, nb, nr, c.d_psiT, s), "transpose states");
+    GW_CUDA(cudaMemcpyAsync(c.d_E, Eh.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s), "copy energies");
+    GW_CUDA(launch_weights(c.d_E, nv, nc, c.d_sw, s), "weights");
+    // Eh is a local: make sure the copy has consumed it before returning.
+    GW_CUDA(cudaStreamSynchronize(s), "load sync");
+    c.loaded = true;
+    return GW_OK;
+}
+
+gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.loaded)
+        return fail(c, GW_E_NOT_READY, "gw_build_P before gw_load_states");
+    if (precision != GW_PREC_TF32X3 && precision != GW_PREC_TF32X1 && precision != GW_PREC_FP32_SIMT &&
+        precision != GW_PREC_FP16X3 && precision != GW_PREC_BF16X3)
+        return fail(c, GW_E_INVALID, "unknown precision %d", precision);
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    cudaStream_t s = c.stream;
+    const bool p16 = precision == GW_PREC_FP16X3 || precision == GW_PREC_BF16X3;
+    const int kchunk = p16 ? HERK16_KC : HERK_KC;
+    c.kpad = ((c.k + kchunk - 1) / kchunk) * kchunk;
+    size_t Fbytes;
+    if (precision == GW_PREC_FP32_SIMT)
+        Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float2);
+    else if (p16)
+        Fbytes = (size_t)c.kpad * c.nr_pad * 2 * 4;
+    else
+        Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float) * (precision == GW_PREC_TF32X3 ? 4 : 2);
+    GW_TRY(ensure(c, c.d_F, c.cap.F, Fbytes, "pair-density operand"));
+    if (!c.d_small)
+        GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");
+    c.F_bytes = Fbytes;
+    c.P_bytes = (size_t)c.nr * c.nr * sizeof(float2);
+    GW_TRY(ensure(c, c.d_P, c.cap.P, c.P_bytes, "P(r,r')"));
+    c.P_ready = c.PG_ready = c.eps_ready = false;
+
+    const int tile_kind = p16 ? 1 : 0;
+    if (precision != GW_PREC_FP32_SIMT && (c.tiles_nr_pad != c.nr_pad || c.tiles_kind != tile_kind)) {
+        const auto t = p16 ? herk_tiles(c.nr_pad, HERK16_T, HERK16_T) : herk_tiles(c.nr_pad, HERK_BM, HERK_BN);
+        GW_TRY(ensure(c, c.d_tiles, c.cap.tiles, t.size() * sizeof(int2), "tile list"));
+        GW_CUDA(cudaMemcpy(c.d_tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice), "tile upload");
+        c.n_tiles = static_cast<int>(t.size());
+        c.tiles_nr_pad = c.nr_pad;
+        c.tiles_kind = tile_kind;
+    }
+    const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+    int *scale_exp = reinterpret_cast<int *>(c.d_small + 1);
+
+    record(c, 0);
+    if (p16)
+        GW_CUDA(launch_pair_density16(c.d_psiT, c.d_sw, c.sw_max, c.nr, c.nb, c.nv, c.nc, c.kpad, c.nr_pad,
+                                      precision == GW_PREC_BF16X3, c.d_small, scale_exp,
+                                      reinterpret_cast<uint16_t *>(c.d_F), s),
+                "pair densities (16-bit)");
+    else
+        GW_CUDA(launch_pair_density(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, c.kpad, c.nr_pad, precision, c.d_F, s),
+                "pair densities");
+    c.F_prec = precision;
+    record(c, 1);
+    if (precision == GW_PREC_FP32_SIMT) {
+        GW_CUDA(launch_herk_simt(reinterpret_cast<float2 *>(c.d_F), c.kpad, c.nr, c.nr_pad, c.d_P, s),
+                "rank-k update (CUDA cores)");
+    } else if (p16) {
+        GW_CUDA(launch_herk16(reinterpret_cast<uint16_t *>(c.d_F), precision == GW_PREC_BF16X3, c.kpad, c.nr,
+                              c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L,
+                              s),
+                "rank-k update (tcgen05, 16-bit)");
+    } else {
+        GW_CUDA(launch_herk_tc(c.d_F, precision, c.kpad, c.nr, c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, c.d_err, wait_ns,
+                               s),
+                "rank-k update (tcgen05, TF32)");
+    }
+    record(c, 2);
+    if (P_out)
+        GW_CUDA(cudaMemcpyAsync(P_out, c.d_P, c.P_bytes, cudaMemcpyDefault, s), "copy P out");
+    c.P_ready = true;
+    return GW_OK;
+}
+
+gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.P_ready)
+        return fail(c, GW_E_NOT_READY, "gw_P_to_G before gw_build_P");
+    const int nmin = std::min(c.n1, std::min(c.n2, c.n3));
+    if (gcut < 0 || 4LL * gcut >= (long long)nmin * nmin)
+        return fail(c, GW_E_INVALID, "gcut %d must satisfy 0 <= 4 gcut < min(n)^2 = %d", gcut, nmin * nmin);
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    if (gcut != c.gcut)
+        GW_TRY(build_plan(c, gcut));
+    const int ng = c.ng;
+    if (gvec_out && ng > max_ng)
+        return fail(c, GW_E_INVALID, "N_g = %d exceeds max_ng = %d", ng, max_ng);
+    if (dft_smem_bytes(c.plan, 1) > 220 * 1024)
+        return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform's shared memory");
+    cudaStream_t s = c.stream;
+    GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
+    GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
+    GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+    c.PG_ready = c.eps_ready = false;
+    record(c, 3);
+    // Q[r'][G] = sum_r P[r'][r] e^{+iG.r} = conj(P^(G, r')) since P is Hermitian
+    GW_CUDA(launch_dft_rows(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, s), "row transform");
+    record(c, 4);
+    // QT[G][r'] = conj(Q[r'][G]) = P^(G, r');  P~[G][G'] = sum_r' QT[G][r'] e^{+iG'.r'}
+    GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
+    GW_CUDA(launch_dft_rows(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, s), "column transform");
+    GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
+    record(c, 5);
+    if (PG_out)
+        GW_CUDA(cudaMemcpyAsync(PG_out, c.d_PG, (size_t)ng * ng * sizeof(float2), cudaMemcpyDefault, s),
+                "copy P~ out");
+    if (ng_out)
+        *ng_out = ng;
+    if (gvec_out)
+        std::memcpy(gvec_out, c.gvec.data(), (size_t)3 * ng * sizeof(int));
+    c.PG_ready = true;
+    return GW_OK;
+}
+
+gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.PG_ready)
+        return fail(c, GW_E_NOT_READY, "gw_eps_inv before gw_P_to_G");
+    if (method != GW_INV_CHOLESKY && method != GW_INV_NEWTON)
+        return fail(c, GW_E_INVALID, "unknown inversion method %d", method);
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    const int ng = c.ng;
+    const size_t bytes = (size_t)ng * ng * sizeof(double2);
+    GW_TRY(ensure(c, c.d_eps, c.cap.eps, bytes, "eps"));
+    GW_TRY(ensure(c, c.d_epsinv, c.cap.epsinv, bytes, "eps^-1"));
+    cudaStream_t s = c.stream;
+    record(c, 6);
+    GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
+    record(c, 7);
+    GW_TRY(method == GW_INV_CHOLESKY ? inverse_cholesky(c) : inverse_newton(c));
+    record(c, 8);
+    if (eps_out)
+        GW_CUDA(cudaMemcpyAsync(eps_out, c.d_eps, bytes, cudaMemcpyDefault, s), "copy eps out");
+    if (epsinv_out)
+        GW_CUDA(cudaMemcpyAsync(epsinv_out, c.d_epsinv, bytes, cudaMemcpyDefault, s), "copy eps^-1 out");
+    gw_status st = read_device_status(c);
+    resolve_times(c);
+    c.eps_ready = st == GW_OK;
+    return st;
+}
+
+gw_status gw_sync(gw_ctx *h)
+{
+    if (!h)
+        return GW_E_INVALID;
+    return read_device_status(h->c);
+}
+
+gw_status gw_get_buffer(gw_ctx *h, int which, void **ptr, size_t *bytes)
+{
+    if (!h || !ptr || !bytes)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    *ptr = nullptr;
+    *bytes = 0;
+    switch (which) {
+    case GW_BUF_P:
+        if (!c.P_ready)
+            return GW_E_NOT_READY;
+        *ptr = c.d_P;
+        *bytes = c.P_bytes;
+        return GW_OK;
+    case GW_BUF_F:
+        if (c.F_prec < 0 || !c.P_ready)
+            return GW_E_NOT_READY;
+        *ptr = c.d_F;
+        *bytes = c.F_bytes;
+        return GW_OK;
+    case GW_BUF_PG:
+        if (!c.PG_ready)
+            return GW_E_NOT_READY;
+        *ptr = c.d_PG;
+        *bytes = (size_t)c.ng * c.ng * sizeof(float2);
+        return GW_OK;
+    case GW_BUF_EPS:
+    case GW_BUF_EPSINV:
+        if (!c.eps_ready)
+            return GW_E_NOT_READY;
+        *ptr = which == GW_BUF_EPS ? (void *)c.d_eps : (void *)c.d_epsinv;
+        *bytes = (size_t)c.ng * c.ng * sizeof(double2);
+        return GW_OK;
+    case GW_BUF_WEIGHTS:
+        if (!c.loaded)
+            return GW_E_NOT_READY;
+        *ptr = c.d_sw;
+        *bytes = (size_t)c.k * sizeof(float);
+        return GW_OK;
+    default:
+        return GW_E_INVALID;
+    }
+}
+
+gw_status gw_get_dims(gw_ctx *h, int *d)
+{
+    if (!h || !d)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.loaded)
+        return GW_E_NOT_READY;
+    d[0] = c.n1;
+    d[1] = c.n2;
+    d[2] = c.n3;
+    d[3] = c.nr;
+    d[4] = c.nv;
+    d[5] = c.nc;
+    d[6] = c.PG_ready ? c.ng : 0;
+    d[7] = c.nr_pad;
+    return GW_OK;
+}
+
+}  // extern "C"

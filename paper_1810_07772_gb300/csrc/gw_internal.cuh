@@ -1,0 +1,167 @@
+// Internal declarations shared by the translation units of libgw.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gw.h"
+
+namespace gw {
+
+// Device status word layout: low byte = gw_status code, bits 8..15 = site, bits 16..31 =
+// detail (tile or pivot index, saturated).  First error wins (atomicCAS from 0).
+enum ErrSite : uint32_t {
+    SITE_HERK_PRODUCER = 1,
+    SITE_HERK_MMA = 2,
+    SITE_HERK_EPILOGUE = 3,
+    SITE_HERK_DRAIN = 4,
+    SITE_CHOL_PIVOT = 5,
+    SITE_INPUT = 6,
+};
+
+__device__ __forceinline__ void record_error(uint32_t *err, uint32_t code, uint32_t site, uint32_t detail)
+{
+    const uint32_t word = (code & 0xFFu) | ((site & 0xFFu) << 8) | ((detail > 0xFFFFu ? 0xFFFFu : detail) << 16);
+    atomicCAS(err, 0u, word);
+}
+
+// Sphere/transform plan for one grid and one gcut (built on the host by this library).
+struct DftPlan {
+    int n[3];
+    int ng;        // sphere size
+    int c3;        // distinct m3 values used by the sphere
+    int cd;        // distinct (m2, m3) pairs used by the sphere
+    int *m3list;   // [c3]   m3 values (device)
+    int *disk;     // [cd*2] (m2, index into m3list) (device)
+    int *gmap;     // [ng*2] (m1, index into disk) (device)
+    float2 *tw;    // [n1 + n2 + n3] exp(+2 pi i t / n_a), FP64-derived (device)
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    double wait_limit_ms = 2000.0;
+    bool timing = false;
+    cudaEvent_t ev[9] = {};
+    unsigned ev_mask = 0;
+    float times[6] = {};
+    double times_sum[6] = {};
+    long long times_n[6] = {};
+
+    // problem
+    bool loaded = false;
+    int n1 = 0, n2 = 0, n3 = 0, nr = 0, nv = 0, nc = 0, nb = 0;
+    double cell_L = 1.0;
+    int k = 0, kpad = 0, nr_pad = 0;
+
+    // device buffers (owned)
+    uint32_t *d_err = nullptr;      // device status word
+    float2 *d_psiT = nullptr;       // [nr][nb] complex64 (transposed states)
+    double *d_E = nullptr;          // [nb] Hartree
+    float *d_sw = nullptr;          // [nv][nc] sqrt(2/(Ec-Ev))
+    float *d_F = nullptr;           // operand planes
+    size_t F_bytes = 0;
+    int F_prec = -1;
+    float2 *d_P = nullptr;          // [nr][nr]
+    size_t P_bytes = 0;
+    bool P_ready = false;
+    int2 *d_tiles = nullptr;        // HERK tile list
+    int n_tiles = 0, tiles_rb = 0;
+
+    // G space
+    int gcut = -1, ng = 0;
+    std::vector<int> gvec;          // host [ng*3]
+    DftPlan plan = {};
+    int *d_plan_mem = nullptr;
+    float2 *d_Q = nullptr;          // [nr][ng]  row transform
+    float2 *d_QT = nullptr;         // [ng][nr]  conj-transposed
+    float2 *d_PG = nullptr;         // [ng][ng]
+    double *d_sv = nullptr;         // [ng] sqrt(V(G))
+    size_t G_cap = 0;               // ng capacity of the G-space buffers
+    bool PG_ready = false;
+
+    // eps
+    double2 *d_eps = nullptr;       // [ng][ng]
+    double2 *d_epsinv = nullptr;    // [ng][ng]
+    double2 *d_work = nullptr;      // workspace for the inverse
+    double *d_scal = nullptr;       // FP64 scalars of the Newton iteration
+    bool eps_ready = false;
+    int newton_iters = 0;
+
+    // staging for gw_load_states
+    float2 *d_psi = nullptr;        // [nb][nr] complex64
+    double2 *d_psi128 = nullptr;    // complex128 input staging
+
+    // allocation capacities in bytes (buffers are reused while large enough)
+    struct {
+        size_t psi, psi128, psiT, E, sw, F, P, tiles, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
+    } cap = {};
+    int tiles_nr_pad = -1, tiles_kind = -1;
+    float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
+    unsigned *d_small = nullptr;    // [0] |f| bound bits, [1] FP16 scale exponent
+    int herk_W = 2, herk_L = 16;
+
+    void release();
+};
+
+// Process-wide count of kernels this library has launched (reported by gw_get_stats).
+void count_launches(int n);
+
+// ---- launchers (each returns cudaGetLastError() of its launches) ----
+
+// k_pair.cu
+cudaError_t launch_transpose_states(const float2 *psi, int nb, int nr, float2 *psiT, cudaStream_t s);
+cudaError_t launch_c128_to_c64(const double2 *in, size_t n, float2 *out, cudaStream_t s);
+cudaError_t launch_check_finite(const float2 *x, size_t n, uint32_t *err, cudaStream_t s);
+cudaError_t launch_weights(const double *E, int nv, int nc, float *sw, cudaStream_t s);
+// prec: 0 = TF32X3 planes, 2 = TF32X1 planes, 3 = plain complex64 [kpad][nr_pad]
+cudaError_t launch_pair_density(const float2 *psiT, const float *sw, int nr, int nb, int nv, int nc,
+                                int kpad, int nr_pad, int prec, float *F, cudaStream_t s);
+
+// k_herk.cu
+size_t herk_smem_bytes(int prec);
+cudaError_t launch_herk_tc(const float *F, int prec, int kpad, int nr, int nr_pad, const int2 *tiles,
+                           int n_tiles, float2 *P, uint32_t *err, uint64_t wait_ns, cudaStream_t s);
+cudaError_t launch_herk_simt(const float2 *F, int kpad, int nr, int nr_pad, float2 *P, cudaStream_t s);
+constexpr int HERK_BM = 128;
+constexpr int HERK_BN = 256;
+constexpr int HERK_KC = 8;
+constexpr int HERK16_KC = 16;
+constexpr int HERK16_T = 128;
+
+// k_herk16.cu
+size_t herk16_smem_bytes();
+cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
+                                  int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,
+                                  cudaStream_t s);
+cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
+                          float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
+                          cudaStream_t s);
+
+// k_dft.cu
+size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
+cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
+                            const DftPlan &p, cudaStream_t s);
+cudaError_t launch_conj_transpose(const float2 *in, int rows, int cols, float2 *out, cudaStream_t s);
+cudaError_t launch_hermitize(float2 *A, int n, cudaStream_t s);  // A <- (A + A^H) / 2
+
+// k_eps.cu
+cudaError_t launch_eps_build(const float2 *PG, const double *sv, int ng, double2 *eps, cudaStream_t s);
+// C = alpha * op(A) * op(B) + beta * C, complex128 row-major; op: 0 = N, 1 = conj-transpose.
+cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA,
+                         const double2 *B, int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s);
+cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
+                             cudaStream_t s);
+cudaError_t launch_copy_block(const double2 *src, int lds, double2 *dst, int ldd, int rows, int cols,
+                              cudaStream_t s);
+cudaError_t launch_set_identity(double2 *A, int lda, int n, double scale, cudaStream_t s);
+cudaError_t launch_two_minus(double2 *T, int n, cudaStream_t s);  // T <- 2I - T
+cudaError_t launch_scaled_adjoint(const double2 *A, int n, const double *d_den, double2 *X, cudaStream_t s);
+cudaError_t launch_max_absdiff(const double2 *A, const double2 *B, size_t n, double *out, cudaStream_t s);
+cudaError_t launch_row_abs_sum_max(const double2 *A, int n, double *out, cudaStream_t s);
+
+}  // namespace gw

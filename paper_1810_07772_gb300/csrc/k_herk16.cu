@@ -1,0 +1,498 @@
+// Hermitian rank-k update P(r, r') = -sum_k f_k(r) conj(f_k(r')) (Eq. Pstatic; the outer product of
+// Sec. 4.1) on 16-bit tensor cores with accumulation accurate to FP32 over very long k.
+//
+// Why this kernel exists: tcgen05 accumulates in TMEM with FP32 truncation, so the error of one
+// long accumulation grows linearly with the number of MMAs into it (about 2e-8 per MMA; 1.7e-4
+// at k = 15360).  Here the tensor core only ever accumulates a short window (W chunks of 16 k,
+// 12 MMAs per chunk) into a fresh TMEM buffer; eight warps then add the window into FP32
+// registers with round-to-nearest, and every L windows the registers are added into the tile's
+// own region of P in global memory.  TMEM holds two window buffers so the tensor core keeps
+// running while the previous window is promoted.
+//
+// Operands: every FP32 pair-density value x (scaled by a global power of two s for FP16) is split
+// as hi = rn16(x s), lo = rn16(x s - hi); each real product is hi*hi + hi*lo + lo*hi.  FP16 keeps
+// 11 significant bits per part (22 together, like the TF32 split) at twice the TF32 MMA rate;
+// BF16 keeps 8 + 8.  Complex products: Re = Ar Br^T + Ai Bi^T, Im = Ai Br^T - Ar Bi^T.
+//
+// Tiles are 128 x 128, upper triangle only (i <= j); direct and mirrored stores as in the TF32
+// kernel, so every element of P is written exactly once at the end.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gw_internal.cuh"
+#include "ptx.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
+constexpr uint32_t A_BYTES = TM * KC16 * 2;  // 4 KB per plane
+constexpr uint32_t B_BYTES = TN * KC16 * 2;  // 4 KB per plane
+constexpr uint32_t NPL = 4;
+constexpr uint32_t STAGE_BYTES = NPL * (A_BYTES + B_BYTES);  // 32 KB
+constexpr int STAGES = 6;
+constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;  // 192 KB
+constexpr uint32_t LBO = 128, SBO = 256;
+constexpr int EPI_PITCH = 129;
+static_assert(PIPE_BYTES >= TM * EPI_PITCH * 8, "epilogue staging must fit");
+constexpr size_t SMEM = PIPE_BYTES + 256;
+constexpr int NPROMO_WARPS = 8;                  // warps 0..7
+constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
+constexpr int NTHREADS = 320;
+constexpr uint64_t DRAIN_NS = 2000000000ull;
+
+__device__ __forceinline__ void named_bar(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+template <bool BF16>
+__global__ void __maxnreg__(200)
+    herk16_kernel(const uint16_t *__restrict__ F, int kpad, int nr, int nr_pad, const int2 *__restrict__ tiles,
+                  float2 *__restrict__ P, const int *__restrict__ scale_exp, uint32_t *err, uint64_t wait_ns, int W,
+                  int L)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + PIPE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;   // [2] window ready in TMEM buffer b
+    uint64_t *acce = accf + 2;         // [2] TMEM buffer b promoted (free)
+    uint64_t *done = acce + 2;         // every MMA finished
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *n_issued = abort_flag + 1;
+    volatile int *n_consumed = abort_flag + 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 tile = tiles[blockIdx.x];  // x: 128-row block of r, y: 128-row block of r'
+    const int nkc = kpad / KC16;
+    const int nwin = (nkc + W - 1) / W;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], NPROMO_WARPS);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        *n_issued = 0;
+        *n_consumed = 0;
+        fence_barrier_init();
+    }
+    if (warp == MMA_WARP)
+        tmem_alloc(tmem_slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == PRODUCER_WARP) {
+        if (lane == 0) {
+            const size_t per_chunk = (size_t)nr_pad * KC16;  // 16-bit elements per (chunk, plane)
+            const size_t a_off = (size_t)tile.x * TM * KC16, b_off = (size_t)tile.y * TN * KC16;
+            for (int kc = 0; kc < nkc; ++kc) {
+                const int s = kc % STAGES;
+                const uint32_t ph = (kc / STAGES) & 1;
+                if (kc >= STAGES && !mbar_wait(&empty[s], ph ^ 1, wait_ns)) {
+                    record_error(err, GW_E_TIMEOUT, SITE_HERK_PRODUCER, blockIdx.x);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*abort_flag)
+                    break;
+                uint8_t *st = smem + s * STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll
+                for (int p = 0; p < (int)NPL; ++p) {
+                    const uint16_t *region = F + ((size_t)kc * NPL + p) * per_chunk;
+                    bulk_g2s(st + p * A_BYTES, region + a_off, A_BYTES, &full[s]);
+                    bulk_g2s(st + NPL * A_BYTES + p * B_BYTES, region + b_off, B_BYTES, &full[s]);
+                }
+                *n_issued = kc + 1;
+            }
+        }
+        __syncwarp();
+    } else if (warp == MMA_WARP) {
+        if (lane == 0) {
+            constexpr uint32_t FMT = BF16 ? 1u : 0u;
+            constexpr uint32_t ID = mma_idesc(FMT, TM, TN, false);
+            constexpr uint32_t IDN = mma_idesc(FMT, TM, TN, true);
+            const uint32_t sbase = smem_u32(smem);
+            int kc = 0;
+            bool ok = true;
+            for (int win = 0; win < nwin && ok; ++win) {
+                const int b = win & 1;
+                if (win >= 2 && !mbar_wait(&acce[b], ((win >> 1) - 1) & 1, wait_ns)) {
+                    record_error(err, GW_E_TIMEOUT, SITE_HERK_MMA, blockIdx.x);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_re = tmem + b * 256, d_im = d_re + 128;
+                const int kend = min(nkc, kc + W);
+                for (int c = 0; kc < kend; ++kc, ++c) {
+                    const int s = kc % STAGES;
+                    if (!mbar_wait(&full[s], (kc / STAGES) & 1, wait_ns)) {
+                        record_error(err, GW_E_TIMEOUT, SITE_HERK_MMA, blockIdx.x);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * STAGE_BYTES;
+                    uint64_t a[NPL], bd[NPL];
+#pragma unroll
+                    for (int p = 0; p < (int)NPL; ++p) {
+                        a[p] = smem_desc(st + p * A_BYTES, LBO, SBO);
+                        bd[p] = smem_desc(st + NPL * A_BYTES + p * B_BYTES, LBO, SBO);
+                    }
+                    const uint32_t acc = c > 0 ? 1u : 0u;
+                    // planes: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo
+                    mma_f16(d_re, a[0], bd[0], ID, acc);
+                    mma_f16(d_re, a[0], bd[1], ID, 1);
+                    mma_f16(d_re, a[1], bd[0], ID, 1);
+                    mma_f16(d_re, a[2], bd[2], ID, 1);
+                    mma_f16(d_re, a[2], bd[3], ID, 1);
+                    mma_f16(d_re, a[3], bd[2], ID, 1);
+                    mma_f16(d_im, a[2], bd[0], ID, acc);
+                    mma_f16(d_im, a[2], bd[1], ID, 1);
+                    mma_f16(d_im, a[3], bd[0], ID, 1);
+                    mma_f16(d_im, a[0], bd[2], IDN, 1);
+                    mma_f16(d_im, a[0], bd[3], IDN, 1);
+                    mma_f16(d_im, a[1], bd[2], IDN, 1);
+                    mma_commit(&empty[s]);
+                    *n_consumed = kc + 1;
+                }
+                if (ok)
+                    mma_commit(&accf[b]);
+            }
+            mma_commit(done);  // arrives once every MMA issued above has completed
+        }
+        __syncwarp();
+    } else {
+        // ---------------- promotion warps 0..7: TMEM windows -> FP32 registers -> P tile
+        const int q = warp & 3;          // TMEM lane quarter
+        const int h = warp >> 2;         // column half: 64 h .. 64 h + 63
+        const int m = q * 32 + lane;     // tile row
+        const int r = tile.x * TM + m;
+        const int cbase = tile.y * TN + h * 64;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        float are[64], aim[64];
+        int flushed = 0;
+        const bool vec_ok = (nr & 1) == 0;  // rows of P start 16-byte aligned
+        const int nseg = (nwin + L - 1) / L;
+        bool stop = false;
+        // Segments of L windows: the registers restart from zero in every segment (a fresh start
+        // rather than a conditional reset keeps all 128 sums in registers) and every segment but
+        // the last is added into this tile's own region of P.
+        for (int seg = 0; seg < nseg && !stop; ++seg) {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                are[i] = 0.f;
+                aim[i] = 0.f;
+            }
+            const int wend = min(nwin, (seg + 1) * L);
+            for (int win = seg * L; win < wend; ++win) {
+                const int b = win & 1;
+                // warp-uniform outcome: the TMEM loads below are warp-collective
+                if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (win >> 1) & 1, wait_ns))) {
+                    if (lane == 0)
+                        record_error(err, GW_E_TIMEOUT, SITE_HERK_EPILOGUE, blockIdx.x);
+                    *abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + lane_addr + b * 256 + h * 64;
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(base + c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        are[c0 + i] += v[i];
+                    tmem_ld16(base + 128 + c0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        aim[c0 + i] += v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&acce[b]);
+            }
+            if (stop || seg + 1 == nseg)
+                break;
+            // second level: add the registers into this tile's own region of P
+            if (r < nr) {
+                float2 *row = P + (size_t)r * nr + cbase;
+                const int avail = nr - cbase;
+                if (vec_ok && avail >= 64) {
+                    float4 *r4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        float4 o[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = flushed ? r4[g * 4 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int i = g * 8 + 2 * j;
+                            r4[g * 4 + j] = make_float4(o[j].x + are[i], o[j].y + aim[i], o[j].z + are[i + 1],
+                                                        o[j].w + aim[i + 1]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        if (i < avail) {
+                            const float2 o = flushed ? row[i] : make_float2(0.f, 0.f);
+                            row[i] = make_float2(o.x + are[i], o.y + aim[i]);
+                        }
+                }
+            }
+            flushed = 1;
+        }
+        // final sums -> shared staging (the operand pipeline is idle once every window is in)
+        named_bar(1, NPROMO_WARPS * 32);
+        const bool write = *abort_flag == 0 && nkc > 0;
+        if (write) {
+            const float inv_s2 = ldexpf(1.0f, -2 * (*scale_exp));
+            float2 *stage = reinterpret_cast<float2 *>(smem);
+            if (flushed && r < nr) {
+                const float2 *row = P + (size_t)r * nr + cbase;
+                const int avail = nr - cbase;
+                if (vec_ok && avail >= 64) {
+                    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        float4 o[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = r4[g * 4 + j];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int i = g * 8 + 2 * j;
+                            are[i] += o[j].x;
+                            aim[i] += o[j].y;
+                            are[i + 1] += o[j].z;
+                            aim[i + 1] += o[j].w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        if (i < avail) {
+                            const float2 o = row[i];
+                            are[i] += o.x;
+                            aim[i] += o.y;
+                        }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                stage[m * EPI_PITCH + h * 64 + i] = make_float2(-are[i] * inv_s2, -aim[i] * inv_s2);
+        }
+        named_bar(1, NPROMO_WARPS * 32);
+        if (write) {
+            const float2 *stage = reinterpret_cast<const float2 *>(smem);
+            const int t = threadIdx.x;  // 0..255
+            const int r0 = tile.x * TM, c0 = tile.y * TN;
+            // direct: P[r][c] for c >= r (real diagonal); two rows per pass
+            for (int mm = (t >> 7); mm < TM; mm += 2) {
+                const int rr = r0 + mm, cc = c0 + (t & 127);
+                if (rr < nr && cc < nr && cc >= rr) {
+                    float2 v = stage[mm * EPI_PITCH + (t & 127)];
+                    if (cc == rr)
+                        v.y = 0.f;
+                    P[(size_t)rr * nr + cc] = v;
+                }
+            }
+            // mirror: P[c][r] = conj(P[r][c]) for c > r
+            for (int cc = (t >> 7); cc < TN; cc += 2) {
+                const int cm = c0 + cc, rr = r0 + (t & 127);
+                if (cm < nr && rr < nr && rr < cm) {
+                    const float2 v = stage[(t & 127) * EPI_PITCH + cc];
+                    P[(size_t)cm * nr + rr] = make_float2(v.x, -v.y);
+                }
+            }
+        }
+    }
+
+    // ---------------- drain before releasing TMEM and shared memory
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait(done, 0, DRAIN_NS))
+            record_error(err, GW_E_TIMEOUT, SITE_HERK_DRAIN, blockIdx.x);
+        const int issued = *n_issued, consumed = *n_consumed;
+        for (int kc = consumed; kc < issued; ++kc)
+            if (!mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1, DRAIN_NS)) {
+                record_error(err, GW_E_TIMEOUT, SITE_HERK_DRAIN, blockIdx.x);
+                break;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------- operands
+// Bound on max |f| for the FP16 scale: per r, max_v |psi_v(r)| * max_c |psi_c(r)|.
+__global__ void f_bound_kernel(const float2 *__restrict__ psiT, int nr, int nb, int nv, unsigned *bound_bits)
+{
+    float best = 0.f;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        float mv = 0.f, mc = 0.f;
+        for (int n = 0; n < nb; ++n) {
+            const float2 z = psiT[(size_t)r * nb + n];
+            const float a = sqrtf(z.x * z.x + z.y * z.y);
+            if (n < nv)
+                mv = fmaxf(mv, a);
+            else
+                mc = fmaxf(mc, a);
+        }
+        best = fmaxf(best, mv * mc);
+    }
+    atomicMax(bound_bits, __float_as_uint(best));  // non-negative floats order like their bits
+}
+
+// scale exponent e with (bound * sw_max) * 2^e <= 2^14 (FP16 max is 65504, so a factor of four
+// of headroom covers any rounding in the bound); 0 for BF16, which has FP32's exponent range.
+__global__ void scale_exp_kernel(const unsigned *bound_bits, float sw_max, int bf16, int *scale_exp)
+{
+    const float b = __uint_as_float(*bound_bits) * sw_max * 1.001f;
+    int e = 0;
+    if (!bf16 && b > 0.f && isfinite(b))
+        e = (int)floorf(14.0f - log2f(b));
+    *scale_exp = max(-100, min(100, e));
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t to16(float x)
+{
+    if (BF16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        return *reinterpret_cast<uint16_t *>(&h);
+    } else {
+        __half h = __float2half_rn(x);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ float from16(uint16_t u)
+{
+    if (BF16) {
+        __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&u);
+        return __bfloat162float(h);
+    } else {
+        __half h = *reinterpret_cast<__half *>(&u);
+        return __half2float(h);
+    }
+}
+
+template <bool BF16>
+__global__ void pair_density16_kernel(const float2 *__restrict__ psiT, const float *__restrict__ sw, int nr, int nb,
+                                      int nv, int nc, int kpad, int nr_pad, const int *__restrict__ scale_exp,
+                                      uint16_t *__restrict__ F)
+{
+    const float s = ldexpf(1.0f, *scale_exp);
+    const size_t per_chunk = (size_t)nr_pad * KC16;
+    const size_t total = (size_t)(kpad / KC16) * per_chunk;
+    const int k_valid = nv * nc;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t kc = i / per_chunk;
+        const int rem = static_cast<int>(i - kc * per_chunk);
+        const int r8 = rem >> 7;         // 8-row group (128 elements)
+        const int w = rem & 127;
+        const int k8 = w >> 6;           // which 16-byte core matrix along k
+        const int rr = (w & 63) >> 3;    // row in the group
+        const int e = w & 7;             // element in the 16-byte row
+        const int r = r8 * 8 + rr;
+        const int k = static_cast<int>(kc) * KC16 + k8 * 8 + e;
+        float fr = 0.f, fi = 0.f;
+        if (r < nr && k < k_valid) {
+            const int v = k / nc, c = k - v * nc;
+            const float2 a = psiT[(size_t)r * nb + v];
+            const float2 b = psiT[(size_t)r * nb + nv + c];
+            const float wv = sw[k] * s;
+            fr = fmaf(a.x, b.x, a.y * b.y) * wv;   // conj(psi_v) psi_c
+            fi = fmaf(a.x, b.y, -a.y * b.x) * wv;
+        }
+        const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi);
+        uint16_t *base = F + kc * NPL * per_chunk + rem;
+        base[0] = rh;
+        base[per_chunk] = to16<BF16>(fr - from16<BF16>(rh));
+        base[2 * per_chunk] = ih;
+        base[3 * per_chunk] = to16<BF16>(fi - from16<BF16>(ih));
+    }
+}
+
+int grid_for(size_t n)
+{
+    size_t g = (n + 255) / 256;
+    if (g > 152 * 16)
+        g = 152 * 16;
+    return g < 1 ? 1 : static_cast<int>(g);
+}
+
+}  // namespace
+
+size_t herk16_smem_bytes()
+{
+    return SMEM;
+}
+
+cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
+                                  int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,
+                                  cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bound_bits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    f_bound_kernel<<<grid_for(nr), 256, 0, s>>>(psiT, nr, nb, nv, bound_bits);
+    count_launches(1);
+    scale_exp_kernel<<<1, 1, 0, s>>>(bound_bits, sw_max, bf16 ? 1 : 0, scale_exp);
+    count_launches(1);
+    const size_t total = (size_t)kpad * nr_pad;
+    if (bf16)
+        pair_density16_kernel<true><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+    else
+        pair_density16_kernel<false><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
+                          float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
+                          cudaStream_t s)
+{
+    if (n_tiles <= 0)
+        return cudaSuccess;
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(herk16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (e != cudaSuccess)
+            return e;
+        herk16_kernel<true><<<n_tiles, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, P, scale_exp, err, wait_ns, W, L);
+        count_launches(1);
+    } else {
+        e = cudaFuncSetAttribute(herk16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (e != cudaSuccess)
+            return e;
+        herk16_kernel<false><<<n_tiles, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, P, scale_exp, err, wait_ns, W,
+                                                             L);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gw

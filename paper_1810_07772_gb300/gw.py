@@ -1,0 +1,235 @@
+"""Python binding of libgw (ctypes).  Argument marshalling only: every step runs in the CUDA
+library, which must be built (``__graft_entry__.build()``); there is no CPU fallback.
+
+The names follow the C ABI in ``include/gw.h``: ``load_states``, ``build_P``, ``P_to_G``,
+``eps_inv``.  Device buffers are passed as ``torch.Tensor`` (``data_ptr()``) or raw integers; host
+buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+GW_OK, GW_E_INVALID, GW_E_NOMEM, GW_E_CUDA, GW_E_NOT_READY, GW_E_NUMERIC, GW_E_TIMEOUT, GW_E_UNSUPPORTED = range(8)
+PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
+INV_METHOD = {"cholesky": 0, "newton": 1}
+GW_C64, GW_C128 = 0, 1
+BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5}
+
+# Every symbol include/gw.h declares, with its ctypes signature.
+_c = ctypes
+_vp, _i, _d, _sz = _c.c_void_p, _c.c_int, _c.c_double, _c.c_size_t
+SIGNATURES = {
+    "gw_status_str": (_c.c_char_p, [_i]),
+    "gw_version": (_i, []),
+    "gw_create": (_i, [_c.POINTER(_vp), _i, _vp]),
+    "gw_destroy": (_i, [_vp]),
+    "gw_set_stream": (_i, [_vp, _vp]),
+    "gw_last_error": (_i, [_vp, _c.c_char_p, _sz]),
+    "gw_load_states": (_i, [_vp, _i, _i, _i, _d, _i, _i, _vp, _i, _i, _vp]),
+    "gw_build_P": (_i, [_vp, _i, _vp]),
+    "gw_P_to_G": (_i, [_vp, _i, _c.POINTER(_i), _vp, _i, _vp]),
+    "gw_eps_inv": (_i, [_vp, _i, _vp, _vp]),
+    "gw_sync": (_i, [_vp]),
+    "gw_get_buffer": (_i, [_vp, _i, _c.POINTER(_vp), _c.POINTER(_sz)]),
+    "gw_get_dims": (_i, [_vp, _c.POINTER(_i)]),
+    "gw_set_timing": (_i, [_vp, _i]),
+    "gw_get_times": (_i, [_vp, _c.POINTER(_c.c_float)]),
+    "gw_set_wait_limit": (_i, [_vp, _d]),
+    "gw_set_herk_window": (_i, [_vp, _i, _i]),
+    "gw_reset_times": (_i, [_vp]),
+    "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libgw.so (raises if it has not been built: the product path has no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgw.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GwError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{lib().gw_status_str(status).decode()} ({status}): {message}")
+        self.status = status
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor, numpy array or integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a buffer")
+
+
+def _is_device(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class DeviceView:
+    """Read-only view of a device buffer through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Context:
+    """One problem on one GPU; wraps a gw_ctx.  ``stream``: torch.cuda.Stream, raw handle or None
+    (torch's current stream at creation)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._h = ctypes.c_void_p()
+        st = lib().gw_create(ctypes.byref(self._h), device, handle)
+        if st != GW_OK:
+            raise GwError(st, "gw_create failed")
+        self.device = device
+        self.dims = None
+        self.ng = 0
+        self.gvec = None
+        self._gbuf = np.zeros((1 << 18, 3), dtype=np.int32)  # G-vector output, reused by P_to_G
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gw_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != GW_OK:
+            buf = ctypes.create_string_buffer(512)
+            lib().gw_last_error(self._h, buf, 512)
+            raise GwError(st, buf.value.decode())
+
+    # ------------------------------------------------------------------ the four calls
+    def load_states(self, psi, energies_eV, dims, nv, cell_L=1.0):
+        """psi: [nv + nc][N_r] complex (torch cuda tensor or numpy host array, complex64/128)."""
+        n1, n2, n3 = (int(d) for d in dims)
+        nb = psi.shape[0]
+        E = np.ascontiguousarray(np.asarray(energies_eV, dtype=np.float64))
+        if E.shape != (nb,):
+            raise ValueError("energies must have one entry per state")
+        dt = str(psi.dtype)
+        dtype = GW_C128 if "complex128" in dt else GW_C64
+        if "complex" not in dt:
+            raise TypeError("psi must be complex64 or complex128")
+        self._check(lib().gw_load_states(self._h, n1, n2, n3, float(cell_L), int(nv), nb - int(nv), _ptr(psi),
+                                         dtype, 1 if _is_device(psi) else 0, E.ctypes.data))
+        self.dims = (n1, n2, n3)
+        self.nv, self.nc = int(nv), nb - int(nv)
+        self._E_keep = E
+
+    def build_P(self, precision="fp16x3", P_out=None):
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self._check(lib().gw_build_P(self._h, prec, _ptr(P_out)))
+
+    def P_to_G(self, gcut, PG_out=None):
+        """Returns the integer G-vectors (N_g x 3, basis order)."""
+        ng = ctypes.c_int(0)
+        g = self._gbuf
+        self._check(lib().gw_P_to_G(self._h, int(gcut), ctypes.byref(ng), g.ctypes.data, g.shape[0], _ptr(PG_out)))
+        self.ng = ng.value
+        self.gvec = g[: ng.value].copy()
+        return self.gvec
+
+    def eps_inv(self, method="cholesky", eps_out=None, epsinv_out=None):
+        m = INV_METHOD[method] if isinstance(method, str) else int(method)
+        self._check(lib().gw_eps_inv(self._h, m, _ptr(eps_out), _ptr(epsinv_out)))
+
+    # ------------------------------------------------------------------ helpers
+    def sync(self):
+        self._check(lib().gw_sync(self._h))
+
+    def set_timing(self, on=True):
+        self._check(lib().gw_set_timing(self._h, 1 if on else 0))
+
+    def times(self):
+        t = (ctypes.c_float * 6)()
+        self._check(lib().gw_get_times(self._h, t))
+        return {"pair": t[0], "herk": t[1], "row_dft": t[2], "col_dft": t[3], "eps_build": t[4], "eps_inv": t[5]}
+
+    def reset_times(self):
+        self._check(lib().gw_reset_times(self._h))
+
+    def stats(self):
+        d = (ctypes.c_double * 8)()
+        self._check(lib().gw_get_stats(self._h, d))
+        keys = ["kernel_launches", "newton_iters", "herk_ms_mean", "herk_calls", "fp16_scale_exp", "herk_tiles",
+                "window_chunks", "flush_windows"]
+        return dict(zip(keys, list(d)))
+
+    def set_herk_window(self, window_chunks, flush_windows):
+        self._check(lib().gw_set_herk_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def set_wait_limit(self, ms):
+        self._check(lib().gw_set_wait_limit(self._h, float(ms)))
+
+    def buffer(self, which):
+        p = ctypes.c_void_p()
+        n = ctypes.c_size_t()
+        self._check(lib().gw_get_buffer(self._h, BUF[which], ctypes.byref(p), ctypes.byref(n)))
+        return p.value, n.value
+
+    def dims8(self):
+        d = (ctypes.c_int * 8)()
+        self._check(lib().gw_get_dims(self._h, d))
+        return list(d)
+
+    def view(self, which, dtype=None):
+        """torch tensor sharing an internal device buffer (no copy)."""
+        import torch
+        ptr, nbytes = self.buffer(which)
+        d = self.dims8()
+        nr, ng, nr_pad = d[3], d[6], d[7]
+        if which == "P":
+            shape, ts = (nr, nr), "<c8"
+        elif which == "PG":
+            shape, ts = (ng, ng), "<c8"
+        elif which in ("eps", "epsinv"):
+            shape, ts = (ng, ng), "<c16"
+        elif which == "weights":
+            shape, ts = (nbytes // 4,), "<f4"
+        else:
+            shape, ts = (nbytes // 4,), "<f4"
+        return torch.as_tensor(DeviceView(ptr, shape, ts), device=f"cuda:{self.device}")

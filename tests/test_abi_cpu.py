@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU and exports every symbol the
+header declares; host-side argument checks that need no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1810_07772_gb300 import build as gbuild
+from paper_1810_07772_gb300 import gw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    gbuild.build()
+    return gw.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "gw.h")).read()
+    return sorted(set(re.findall(r"^GW_API[^;(]*?\b(gw_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_path_calls():
+    names = declared_symbols()
+    for call in ("gw_load_states", "gw_build_P", "gw_P_to_G", "gw_eps_inv", "gw_create", "gw_destroy"):
+        assert call in names
+    assert len(names) == 19
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+        assert name in gw.SIGNATURES, f"binding has no signature for {name}"
+    assert set(gw.SIGNATURES) == set(declared_symbols())
+
+
+def test_status_strings(L):
+    assert L.gw_version() == 1
+    assert L.gw_status_str(0) == b"ok"
+    assert L.gw_status_str(5) == b"eps not positive definite"
+    assert L.gw_status_str(99) == b"unknown status"
+
+
+def test_null_handles_are_rejected(L):
+    assert L.gw_destroy(None) == gw.GW_E_INVALID
+    assert L.gw_build_P(None, 0, None) == gw.GW_E_INVALID
+    assert L.gw_sync(None) == gw.GW_E_INVALID
+    assert L.gw_create(None, 0, None) == gw.GW_E_INVALID
+
+
+def test_create_without_gpu_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = L.gw_create(ctypes.byref(h), 0, None)
+    assert st in (gw.GW_E_INVALID, gw.GW_E_CUDA)
+    assert not h.value
+
+
+def test_only_sm103a_code():
+    """The build targets sm_103a only (no PTX for other archs, no multi-arch fat binary)."""
+    assert gbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

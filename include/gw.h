@@ -199,7 +199,7 @@ GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
 /*
  * Window length of the 16-bit rank-k update: the tensor core accumulates `window_chunks` chunks
  * of 16 k (1..64, default 2) in TMEM before they are added into FP32 registers, and every
- * `flush_windows` windows (1..4096, default 16) the registers are added into P.  Shorter windows
+ * `flush_windows` windows (1..4096, default 256) the registers are added into P.  Shorter windows
  * and flushes mean smaller accumulation error.
  */
 GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_windows);

@@ -284,8 +284,9 @@ gw_status inverse_cholesky(Ctx &c)
             double2 *panel = A + (size_t)(k0 + kn) * N + k0;
             GW_CUDA(launch_zgemm(rest, kn, kn, one, panel, N, 0, Dk, NB, 1, zero, W, NB, s), "panel solve");
             GW_CUDA(launch_copy_block(W, NB, panel, N, rest, kn, s), "panel store");
+            // only the lower triangle of the trailing matrix is read later
             GW_CUDA(launch_zgemm(rest, rest, kn, mone, W, NB, 0, W, NB, 1, one, A + (size_t)(k0 + kn) * N + k0 + kn,
-                                 N, s),
+                                 N, s, ZG_C_LOWER),
                     "trailing update");
         }
     }
@@ -295,12 +296,18 @@ gw_status inverse_cholesky(Ctx &c)
         const double2 *Di = Dinv + (size_t)ib * NB * NB;
         GW_CUDA(launch_copy_block(Di, NB, Y + (size_t)i0 * N + i0, N, in, in, s), "diagonal inverse store");
         if (ib > 0) {
-            GW_CUDA(launch_zgemm(in, i0, i0, one, A + (size_t)i0 * N, N, 0, Y, N, 0, zero, T, N, s), "L Y product");
+            // Y is lower triangular: column block j only meets rows k >= j
+            GW_CUDA(launch_zgemm(in, i0, i0, one, A + (size_t)i0 * N, N, 0, Y, N, 0, zero, T, N, s, ZG_B_LOWER),
+                    "L Y product");
             GW_CUDA(launch_zgemm(in, i0, in, mone, Di, NB, 0, T, N, 0, zero, Y + (size_t)i0 * N, N, s),
                     "off-diagonal inverse");
         }
     }
-    GW_CUDA(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, c.d_epsinv, N, s), "Y^H Y");
+    // (Y^H Y)[i][j] = sum_{k >= max(i, j)} conj(Y[k][i]) Y[k][j]; Hermitian, so the lower half is
+    // computed and mirrored
+    GW_CUDA(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, c.d_epsinv, N, s,
+                         ZG_A_UPPER | ZG_B_LOWER | ZG_C_LOWER | ZG_C_MIRROR),
+            "Y^H Y");
     return GW_OK;
 }
 
@@ -706,8 +713,8 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
     const int ng = c.ng;
     if (gvec_out && ng > max_ng)
         return fail(c, GW_E_INVALID, "N_g = %d exceeds max_ng = %d", ng, max_ng);
-    if (dft_smem_bytes(c.plan, 1) > 220 * 1024)
-        return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform's shared memory");
+    if (!dft_supported(c.plan))
+        return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", ng);
     cudaStream_t s = c.stream;
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));

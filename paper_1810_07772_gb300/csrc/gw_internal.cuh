@@ -103,7 +103,7 @@ struct Ctx {
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
     unsigned *d_small = nullptr;    // [0] |f| bound bits, [1] FP16 scale exponent
-    int herk_W = 2, herk_L = 16;
+    int herk_W = 2, herk_L = 256;
 
     void release();
 };
@@ -144,6 +144,7 @@ cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr
 
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
+bool dft_supported(const DftPlan &p);  // sphere small enough for the transform kernel
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                             const DftPlan &p, cudaStream_t s);
 cudaError_t launch_conj_transpose(const float2 *in, int rows, int cols, float2 *out, cudaStream_t s);
@@ -152,8 +153,13 @@ cudaError_t launch_hermitize(float2 *A, int n, cudaStream_t s);  // A <- (A + A^
 // k_eps.cu
 cudaError_t launch_eps_build(const float2 *PG, const double *sv, int ng, double2 *eps, cudaStream_t s);
 // C = alpha * op(A) * op(B) + beta * C, complex128 row-major; op: 0 = N, 1 = conj-transpose.
+// flags: ZG_B_LOWER  op(B)[k][j] = 0 for k < j (skip those k);  ZG_A_UPPER  op(A)[i][k] = 0 for
+// k < i;  ZG_C_LOWER  compute and store only C[i][j] with j <= i;  ZG_C_MIRROR  with ZG_C_LOWER,
+// also store C[j][i] = conj(C[i][j]) (beta must be 0).
+enum { ZG_B_LOWER = 1, ZG_A_UPPER = 2, ZG_C_LOWER = 4, ZG_C_MIRROR = 8 };
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA,
-                         const double2 *B, int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s);
+                         const double2 *B, int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s,
+                         int flags = 0);
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
                              cudaStream_t s);
 cudaError_t launch_copy_block(const double2 *src, int lds, double2 *dst, int ldd, int rows, int cols,

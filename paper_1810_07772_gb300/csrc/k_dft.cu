@@ -19,6 +19,9 @@ namespace gw {
 
 namespace {
 
+constexpr int DFT_THREADS = 256;
+constexpr int GPT = 16;  // stage-3 outputs (row, G) per thread kept in registers
+
 struct SmemLayout {
     size_t tw, m3, disk, gmap, X, A1, A2, total;
 };
@@ -41,11 +44,11 @@ __host__ __device__ inline SmemLayout layout_for(const int n[3], int ng, int c3,
     L.gmap = o;
     o = align16(o + sizeof(int) * 2 * ng);
     L.X = o;
-    o = align16(o + sizeof(float2) * R * n[1] * n[2]);
+    o = align16(o + sizeof(float2) * 2 * R * n[1] * n[2]);  // double-buffered j1-plane
     L.A1 = o;
     o = align16(o + sizeof(float2) * R * n[1] * c3);
     L.A2 = o;
-    o = align16(o + sizeof(float2) * R * n[0] * cd);
+    o = align16(o + sizeof(float2) * R * cd);  // current plane only
     L.total = o;
     return L;
 }
@@ -56,11 +59,30 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 x, float2 w)
     acc.y = fmaf(x.x, w.y, fmaf(x.y, w.x, acc.y));
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(
+                     dst_smem))),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int R>
+__global__ void __launch_bounds__(DFT_THREADS)
     dft_rows_kernel(const float2 *__restrict__ X, long long ldx, int rows, float2 *__restrict__ Y, long long ldy,
                     int n1, int n2, int n3, int ng, int c3, int cd, const int *__restrict__ g_m3,
-                    const int *__restrict__ g_disk, const int *__restrict__ g_gmap, const float2 *__restrict__ g_tw,
-                    int R)
+                    const int *__restrict__ g_disk, const int *__restrict__ g_gmap, const float2 *__restrict__ g_tw)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nn[3] = {n1, n2, n3};
@@ -74,78 +96,123 @@ __global__ void __launch_bounds__(256)
     float2 *A2 = reinterpret_cast<float2 *>(smem + L.A2);
     const float2 *tw1 = tw, *tw2 = tw + n1, *tw3 = tw + n1 + n2;
 
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < n1 + n2 + n3; t += nt)
+    const int tid = threadIdx.x;
+    for (int t = tid; t < n1 + n2 + n3; t += DFT_THREADS)
         tw[t] = g_tw[t];
-    for (int t = tid; t < c3; t += nt)
+    for (int t = tid; t < c3; t += DFT_THREADS)
         m3[t] = g_m3[t];
-    for (int t = tid; t < 2 * cd; t += nt)
+    for (int t = tid; t < 2 * cd; t += DFT_THREADS)
         disk[t] = g_disk[t];
-    for (int t = tid; t < 2 * ng; t += nt)
+    for (int t = tid; t < 2 * ng; t += DFT_THREADS)
         gmap[t] = g_gmap[t];
 
     const int row0 = blockIdx.x * R;
     const int plane = n2 * n3;
-    for (int j1 = 0; j1 < n1; ++j1) {
-        __syncthreads();
-        // plane j1 of R rows -> shared (zero for rows past the end)
-        for (int t = tid; t < R * plane; t += nt) {
+    // plane j1 of the R rows -> Xs[buf] (asynchronous 8-byte copies; zeros past the last row)
+    auto issue_plane = [&](int j1, int buf) {
+        float2 *dst = Xs + (size_t)buf * R * plane;
+        for (int t = tid; t < R * plane; t += DFT_THREADS) {
             const int rho = t / plane, q = t - rho * plane;
             const int row = row0 + rho;
-            Xs[t] = row < rows ? X[(size_t)row * ldx + (size_t)j1 * plane + q] : make_float2(0.f, 0.f);
+            if (row < rows)
+                cp_async8(dst + t, X + (size_t)row * ldx + (size_t)j1 * plane + q);
+            else
+                dst[t] = make_float2(0.f, 0.f);
+        }
+        cp_async_commit();
+    };
+
+    // stage-3 outputs owned by this thread: items u = tid + 256 * s over (rho, g)
+    float2 acc3[GPT];
+    int idx3[GPT];
+#pragma unroll
+    for (int s = 0; s < GPT; ++s) {
+        acc3[s] = make_float2(0.f, 0.f);
+        idx3[s] = 0;
+    }
+    const int n3items = R * ng;
+
+    __syncthreads();  // tables visible
+    issue_plane(0, 0);
+    for (int j1 = 0; j1 < n1; ++j1) {
+        const int buf = j1 & 1;
+        if (j1 + 1 < n1) {
+            issue_plane(j1 + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        // stage 1: A1[rho][j2][i3] = sum_j3 X[rho][j2][j3] e(m3 j3 / n3)
-        for (int t = tid; t < R * n2 * c3; t += nt) {
-            const int i3 = t % c3;
-            const int rj = t / c3;  // rho * n2 + j2
-            const float2 *x = Xs + (size_t)rj * n3;
+        const float2 *xb = Xs + (size_t)buf * R * plane;
+        // stage 1: A1[rho][j2][i3] = sum_j3 X[rho][j2][j3] e(m3 j3 / n3); one twiddle serves R rows
+        for (int t = tid; t < n2 * c3; t += DFT_THREADS) {
+            const int j2 = t / c3, i3 = t - j2 * c3;
             const int step = m3[i3];
+            float2 acc[R];
+#pragma unroll
+            for (int rho = 0; rho < R; ++rho)
+                acc[rho] = make_float2(0.f, 0.f);
             int idx = 0;
-            float2 acc = make_float2(0.f, 0.f);
+            const float2 *x = xb + j2 * n3;
             for (int j3 = 0; j3 < n3; ++j3) {
-                cmac(acc, x[j3], tw3[idx]);
+                const float2 w = tw3[idx];
+#pragma unroll
+                for (int rho = 0; rho < R; ++rho)
+                    cmac(acc[rho], x[rho * plane + j3], w);
                 idx += step;
                 if (idx >= n3)
                     idx -= n3;
             }
-            A1[t] = acc;
+#pragma unroll
+            for (int rho = 0; rho < R; ++rho)
+                A1[(rho * n2 + j2) * c3 + i3] = acc[rho];
         }
         __syncthreads();
-        // stage 2: A2[rho][j1][d] = sum_j2 A1[rho][j2][i3(d)] e(m2(d) j2 / n2)
-        for (int t = tid; t < R * cd; t += nt) {
-            const int rho = t / cd, d = t - rho * cd;
+        // stage 2: A2[rho][d] = sum_j2 A1[rho][j2][i3(d)] e(m2(d) j2 / n2)
+        for (int d = tid; d < cd; d += DFT_THREADS) {
             const int step = disk[2 * d], i3 = disk[2 * d + 1];
-            const float2 *a = A1 + (size_t)rho * n2 * c3 + i3;
+            float2 acc[R];
+#pragma unroll
+            for (int rho = 0; rho < R; ++rho)
+                acc[rho] = make_float2(0.f, 0.f);
             int idx = 0;
-            float2 acc = make_float2(0.f, 0.f);
             for (int j2 = 0; j2 < n2; ++j2) {
-                cmac(acc, a[(size_t)j2 * c3], tw2[idx]);
+                const float2 w = tw2[idx];
+#pragma unroll
+                for (int rho = 0; rho < R; ++rho)
+                    cmac(acc[rho], A1[(rho * n2 + j2) * c3 + i3], w);
                 idx += step;
                 if (idx >= n2)
                     idx -= n2;
             }
-            A2[((size_t)rho * n1 + j1) * cd + d] = acc;
+#pragma unroll
+            for (int rho = 0; rho < R; ++rho)
+                A2[rho * cd + d] = acc[rho];
         }
+        __syncthreads();
+        // stage 3 (this plane's term): y[rho][g] += A2[rho][d(g)] e(m1(g) j1 / n1)
+#pragma unroll
+        for (int s = 0; s < GPT; ++s) {
+            const int u = tid + DFT_THREADS * s;
+            if (u < n3items) {
+                const int rho = u / ng, g = u - rho * ng;
+                cmac(acc3[s], A2[rho * cd + gmap[2 * g + 1]], tw1[idx3[s]]);
+                idx3[s] += gmap[2 * g];
+                if (idx3[s] >= n1)
+                    idx3[s] -= n1;
+            }
+        }
+        // the next iteration's wait + __syncthreads orders these reads before A1/A2 are rewritten
     }
-    __syncthreads();
-    // stage 3: y[rho][g] = sum_j1 A2[rho][j1][d(g)] e(m1(g) j1 / n1)
-    for (int t = tid; t < R * ng; t += nt) {
-        const int rho = t / ng, g = t - rho * ng;
-        const int row = row0 + rho;
-        if (row >= rows)
-            continue;
-        const int step = gmap[2 * g], d = gmap[2 * g + 1];
-        const float2 *a = A2 + (size_t)rho * n1 * cd + d;
-        int idx = 0;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int j1 = 0; j1 < n1; ++j1) {
-            cmac(acc, a[(size_t)j1 * cd], tw1[idx]);
-            idx += step;
-            if (idx >= n1)
-                idx -= n1;
+#pragma unroll
+    for (int s = 0; s < GPT; ++s) {
+        const int u = tid + DFT_THREADS * s;
+        if (u < n3items) {
+            const int rho = u / ng, g = u - rho * ng;
+            const int row = row0 + rho;
+            if (row < rows)
+                Y[(size_t)row * ldy + g] = acc3[s];
         }
-        Y[(size_t)row * ldy + g] = acc;
     }
 }
 
@@ -188,13 +255,13 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
     A[(size_t)h * n + g] = make_float2(m.x, -m.y);
 }
 
-constexpr size_t DFT_SMEM_TARGET = 100 * 1024;
+constexpr size_t DFT_SMEM_TARGET = 56 * 1024;  // four CTAs per SM
 constexpr size_t DFT_SMEM_MAX = 220 * 1024;
 
 int rows_per_cta(const DftPlan &p)
 {
-    for (int R = 8; R > 1; --R)
-        if (layout_for(p.n, p.ng, p.c3, p.cd, R).total <= DFT_SMEM_TARGET)
+    for (int R : {4, 2})
+        if (layout_for(p.n, p.ng, p.c3, p.cd, R).total <= DFT_SMEM_TARGET && R * p.ng <= DFT_THREADS * GPT)
             return R;
     return 1;
 }
@@ -208,22 +275,41 @@ size_t dft_smem_bytes(const DftPlan &p, int R)
     return layout_for(p.n, p.ng, p.c3, p.cd, R).total;
 }
 
+bool dft_supported(const DftPlan &p)
+{
+    return p.ng <= DFT_THREADS * GPT && layout_for(p.n, p.ng, p.c3, p.cd, 1).total <= DFT_SMEM_MAX;
+}
+
+template <int R>
+static cudaError_t launch_dft_R(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
+                                cudaStream_t s)
+{
+    const size_t smem = layout_for(p.n, p.ng, p.c3, p.cd, R).total;
+    cudaError_t e = cudaFuncSetAttribute(dft_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dft_rows_kernel<R><<<(rows + R - 1) / R, DFT_THREADS, smem, s>>>(X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2],
+                                                                      p.ng, p.c3, p.cd, p.m3list, p.disk, p.gmap,
+                                                                      p.tw);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
                             cudaStream_t s)
 {
     if (rows <= 0)
         return cudaSuccess;
-    const int R = rows_per_cta(p);
-    const size_t smem = layout_for(p.n, p.ng, p.c3, p.cd, R).total;
-    if (smem > DFT_SMEM_MAX)
+    if (!dft_supported(p))
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(dft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    dft_rows_kernel<<<(rows + R - 1) / R, 256, smem, s>>>(X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2], p.ng, p.c3,
-                                                          p.cd, p.m3list, p.disk, p.gmap, p.tw, R);
-    count_launches(1);
-    return cudaGetLastError();
+    switch (rows_per_cta(p)) {
+    case 4:
+        return launch_dft_R<4>(X, ldx, rows, Y, ldy, p, s);
+    case 2:
+        return launch_dft_R<2>(X, ldx, rows, Y, ldy, p, s);
+    default:
+        return launch_dft_R<1>(X, ldx, rows, Y, ldy, p, s);
+    }
 }
 
 cudaError_t launch_hermitize(float2 *A, int n, cudaStream_t s)

@@ -36,13 +36,19 @@ __global__ void eps_build_kernel(const float2 *__restrict__ PG, const double *__
 constexpr int ZT = 32;   // output tile
 constexpr int ZK = 16;   // k chunk
 
+// C = alpha op(A) op(B) + beta C with optional triangular structure (flags, see gw_internal.cuh):
+// known-zero k ranges of a triangular operand are skipped, and with ZG_C_LOWER only tiles that
+// reach the diagonal or below are computed (ZG_C_MIRROR also stores the conjugate transpose).
 __global__ void __launch_bounds__(256)
     zgemm_kernel(int M, int N, int K, double2 alpha, const double2 *__restrict__ A, int lda, int opA,
-                 const double2 *__restrict__ B, int ldb, int opB, double2 beta, double2 *__restrict__ C, int ldc)
+                 const double2 *__restrict__ B, int ldb, int opB, double2 beta, double2 *__restrict__ C, int ldc,
+                 int flags)
 {
     __shared__ double2 As[ZK][ZT + 1];
     __shared__ double2 Bs[ZK][ZT + 1];
     const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
+    if ((flags & ZG_C_LOWER) && j0 > i0 + ZT - 1)
+        return;  // tile strictly above the diagonal
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double2 acc[2][2];
 #pragma unroll
@@ -50,7 +56,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
             acc[a][b] = make_double2(0.0, 0.0);
-    for (int k0 = 0; k0 < K; k0 += ZK) {
+    int kbeg = 0;
+    if (flags & ZG_B_LOWER)
+        kbeg = max(kbeg, j0);  // op(B)[k][j] = 0 for k < j
+    if (flags & ZG_A_UPPER)
+        kbeg = max(kbeg, i0);  // op(A)[i][k] = 0 for k < i
+    kbeg = (kbeg / ZK) * ZK;
+    for (int k0 = kbeg; k0 < K; k0 += ZK) {
         for (int t = threadIdx.x; t < ZK * ZT; t += 256) {
             int i, kk;
             if (opA == 0) {
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
-            if (gi < M && gj < N) {
+            if (gi < M && gj < N && (!(flags & ZG_C_LOWER) || gj <= gi)) {
                 double2 v = cmul(alpha, acc[a][b]);
                 if (use_beta) {
                     const double2 c = cmul(beta, C[(size_t)gi * ldc + gj]);
@@ -109,19 +121,23 @@ __global__ void __launch_bounds__(256)
                     v.y += c.y;
                 }
                 C[(size_t)gi * ldc + gj] = v;
+                if ((flags & ZG_C_MIRROR) && gj < gi)
+                    C[(size_t)gj * ldc + gi] = cconj(v);
             }
         }
 }
 
 // ---------------------------------------------------------------------------- diagonal block
 // Factor the n x n (n <= 32) Hermitian block A = L L^H in place (lower triangle; the strict
-// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.
-__global__ void __launch_bounds__(64)
+// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.  FP64 division
+// and square root are slow on this GPU, so each pivot's reciprocal is formed once.
+__global__ void __launch_bounds__(256)
     chol_diag_kernel(double2 *__restrict__ A, int lda, int n, double2 *__restrict__ Linv, int ldl, int pivot0,
                      uint32_t *err)
 {
     __shared__ double2 S[32][33];
     __shared__ double2 T[32][33];
+    __shared__ double rd[32];
     __shared__ int bad;
     const int tid = threadIdx.x;
     if (tid == 0)
@@ -134,17 +150,20 @@ __global__ void __launch_bounds__(64)
     for (int j = 0; j < n; ++j) {
         if (tid == 0) {
             const double d = S[j][j].x;
+            double sq;
             if (!(d > 0.0) || !isfinite(d)) {
                 if (!bad)
                     record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
                 bad = 1;
-                S[j][j] = make_double2(1.0, 0.0);
+                sq = 1.0;
             } else {
-                S[j][j] = make_double2(sqrt(d), 0.0);
+                sq = sqrt(d);
             }
+            S[j][j] = make_double2(sq, 0.0);
+            rd[j] = 1.0 / sq;
         }
         __syncthreads();
-        const double inv = 1.0 / S[j][j].x;
+        const double inv = rd[j];
         if (tid > j && tid < n) {
             S[tid][j].x *= inv;
             S[tid][j].y *= inv;
@@ -175,8 +194,7 @@ __global__ void __launch_bounds__(64)
                 s.x -= p.x;
                 s.y -= p.y;
             }
-            const double inv = 1.0 / S[i][i].x;
-            T[i][c] = make_double2(s.x * inv, s.y * inv);
+            T[i][c] = make_double2(s.x * rd[i], s.y * rd[i]);
         }
     }
     __syncthreads();
@@ -294,12 +312,12 @@ cudaError_t launch_eps_build(const float2 *PG, const double *sv, int ng, double2
 }
 
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA, const double2 *B,
-                         int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s)
+                         int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s, int flags)
 {
     if (M <= 0 || N <= 0)
         return cudaSuccess;
     dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT);
-    zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc);
+    zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -307,7 +325,7 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, i
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
                              cudaStream_t s)
 {
-    chol_diag_kernel<<<1, 64, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
+    chol_diag_kernel<<<1, 256, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -48,7 +48,7 @@ __device__ __forceinline__ void named_bar(int id, int n)
 }
 
 template <bool BF16>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(NTHREADS, 1)
     herk16_kernel(const uint16_t *__restrict__ F, int kpad, int nr, int nr_pad, const int2 *__restrict__ tiles,
                   float2 *__restrict__ P, const int *__restrict__ scale_exp, uint32_t *err, uint64_t wait_ns, int W,
                   int L)

@@ -268,10 +268,10 @@ gw_status inverse_cholesky(Ctx &c)
 {
     const int N = c.ng, NB = CHOL_NB;
     const int nblk = (N + NB - 1) / NB;
-    // workspace: A (N*N) | Y (N*N) | T (NB*N) | W (N*NB) | Dinv (nblk*NB*NB)
-    const size_t need = (size_t)2 * N * N + 2 * (size_t)NB * N + (size_t)nblk * NB * NB;
+    // workspace: A (N*N) | Y (N*N) | T (N*N) | W (N*NB) | Dinv (nblk*NB*NB)
+    const size_t need = (size_t)3 * N * N + (size_t)NB * N + (size_t)nblk * NB * NB;
     GW_TRY(ensure(c, c.d_work, c.cap.work, need * sizeof(double2), "inverse workspace"));
-    double2 *A = c.d_work, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)NB * N,
+    double2 *A = c.d_work, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)N * N,
             *Dinv = W + (size_t)N * NB;
     cudaStream_t s = c.stream;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
@@ -290,18 +290,40 @@ gw_status inverse_cholesky(Ctx &c)
                     "trailing update");
         }
     }
+    // Y = L^-1 by recursive halving at multiples of 32, so every leaf is one diagonal block whose
+    // inverse chol_diag already formed:  [L11 0; L21 L22]^-1 = [Y11 0; -Y22 L21 Y11  Y22].
+    // The two products per level are large GEMMs that fill the GPU, unlike a row-by-row sweep.
     GW_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * N * sizeof(double2), s), "clear Y");
-    for (int ib = 0; ib < nblk; ++ib) {
-        const int i0 = ib * NB, in = std::min(NB, N - i0);
-        const double2 *Di = Dinv + (size_t)ib * NB * NB;
-        GW_CUDA(launch_copy_block(Di, NB, Y + (size_t)i0 * N + i0, N, in, in, s), "diagonal inverse store");
-        if (ib > 0) {
-            // Y is lower triangular: column block j only meets rows k >= j
-            GW_CUDA(launch_zgemm(in, i0, i0, one, A + (size_t)i0 * N, N, 0, Y, N, 0, zero, T, N, s, ZG_B_LOWER),
-                    "L Y product");
-            GW_CUDA(launch_zgemm(in, i0, in, mone, Di, NB, 0, T, N, 0, zero, Y + (size_t)i0 * N, N, s),
-                    "off-diagonal inverse");
+    struct Frame {
+        int n0, n;
+    };
+    std::vector<Frame> todo = {{0, N}}, order;
+    while (!todo.empty()) {  // post-order: children before their parent
+        Frame f = todo.back();
+        todo.pop_back();
+        order.push_back(f);
+        if (f.n > NB) {
+            const int n1 = std::max(NB, ((f.n / 2 + NB - 1) / NB) * NB);
+            todo.push_back({f.n0, n1});
+            todo.push_back({f.n0 + n1, f.n - n1});
         }
+    }
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        const int n0 = it->n0, n = it->n;
+        if (n <= NB) {
+            GW_CUDA(launch_copy_block(Dinv + (size_t)(n0 / NB) * NB * NB, NB, Y + (size_t)n0 * N + n0, N, n, n, s),
+                    "diagonal inverse store");
+            continue;
+        }
+        const int n1 = std::max(NB, ((n / 2 + NB - 1) / NB) * NB), n2 = n - n1;
+        // T = L21 Y11 (Y11 lower triangular)
+        GW_CUDA(launch_zgemm(n2, n1, n1, one, A + (size_t)(n0 + n1) * N + n0, N, 0, Y + (size_t)n0 * N + n0, N, 0,
+                             zero, T, n1, s, ZG_B_LOWER),
+                "L21 Y11");
+        // Y21 = -Y22 T (Y22 lower triangular)
+        GW_CUDA(launch_zgemm(n2, n1, n2, mone, Y + (size_t)(n0 + n1) * N + n0 + n1, N, 0, T, n1, 0, zero,
+                             Y + (size_t)(n0 + n1) * N + n0, N, s, ZG_A_LOWER),
+                "-Y22 L21 Y11");
     }
     // (Y^H Y)[i][j] = sum_{k >= max(i, j)} conj(Y[k][i]) Y[k][j]; Hermitian, so the lower half is
     // computed and mirrored

@@ -155,8 +155,8 @@ cudaError_t launch_eps_build(const float2 *PG, const double *sv, int ng, double2
 // C = alpha * op(A) * op(B) + beta * C, complex128 row-major; op: 0 = N, 1 = conj-transpose.
 // flags: ZG_B_LOWER  op(B)[k][j] = 0 for k < j (skip those k);  ZG_A_UPPER  op(A)[i][k] = 0 for
 // k < i;  ZG_C_LOWER  compute and store only C[i][j] with j <= i;  ZG_C_MIRROR  with ZG_C_LOWER,
-// also store C[j][i] = conj(C[i][j]) (beta must be 0).
-enum { ZG_B_LOWER = 1, ZG_A_UPPER = 2, ZG_C_LOWER = 4, ZG_C_MIRROR = 8 };
+// also store C[j][i] = conj(C[i][j]) (beta must be 0);  ZG_A_LOWER  op(A)[i][k] = 0 for k > i.
+enum { ZG_B_LOWER = 1, ZG_A_UPPER = 2, ZG_C_LOWER = 4, ZG_C_MIRROR = 8, ZG_A_LOWER = 16 };
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA,
                          const double2 *B, int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s,
                          int flags = 0);

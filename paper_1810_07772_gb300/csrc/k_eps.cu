@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256)
     if (flags & ZG_A_UPPER)
         kbeg = max(kbeg, i0);  // op(A)[i][k] = 0 for k < i
     kbeg = (kbeg / ZK) * ZK;
-    for (int k0 = kbeg; k0 < K; k0 += ZK) {
+    const int kend = (flags & ZG_A_LOWER) ? min(K, i0 + ZT) : K;  // op(A)[i][k] = 0 for k > i
+    for (int k0 = kbeg; k0 < kend; k0 += ZK) {
         for (int t = threadIdx.x; t < ZK * ZT; t += 256) {
             int i, kk;
             if (opA == 0) {
@@ -128,9 +129,26 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------- diagonal block
+// 1/sqrt(d) by the Newton-Raphson iteration y <- y (3 - d y^2) / 2 started from the FP32 estimate:
+// each step doubles the number of correct bits (24 -> 48 -> FP64 rounding).  On this GPU an FP64
+// FMA has a 64-cycle latency and a correctly rounded FP64 sqrt plus division cost more than 1000
+// cycles, so two short Newton steps are the faster route to a pivot and its reciprocal.
+__device__ __forceinline__ double rsqrt_newton(double d)
+{
+    const float df = static_cast<float>(d);
+    if (!(df > 1e-30f) || !(df < 1e30f))
+        return 1.0 / sqrt(d);
+    double y = static_cast<double>(rsqrtf(df));
+    const double hd = 0.5 * d;
+    y = y * fma(-hd * y, y, 1.5);
+    y = y * fma(-hd * y, y, 1.5);
+    return y;
+}
+
 // Factor the n x n (n <= 32) Hermitian block A = L L^H in place (lower triangle; the strict
-// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.  FP64 division
-// and square root are slow on this GPU, so each pivot's reciprocal is formed once.
+// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.  The inverse is
+// built row by row with each dot product split over eight lanes, so its critical path is 32
+// short reductions rather than 32-term serial sums.
 __global__ void __launch_bounds__(256)
     chol_diag_kernel(double2 *__restrict__ A, int lda, int n, double2 *__restrict__ Linv, int ldl, int pivot0,
                      uint32_t *err)
@@ -150,17 +168,18 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < n; ++j) {
         if (tid == 0) {
             const double d = S[j][j].x;
-            double sq;
+            double y;
             if (!(d > 0.0) || !isfinite(d)) {
                 if (!bad)
                     record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
                 bad = 1;
-                sq = 1.0;
+                y = 1.0;
+                S[j][j] = make_double2(1.0, 0.0);
             } else {
-                sq = sqrt(d);
+                y = rsqrt_newton(d);
+                S[j][j] = make_double2(d * y, 0.0);
             }
-            S[j][j] = make_double2(sq, 0.0);
-            rd[j] = 1.0 / sq;
+            rd[j] = y;
         }
         __syncthreads();
         const double inv = rd[j];
@@ -180,24 +199,32 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
     }
-    // Linv by forward substitution, one column per thread: L X = I.
-    if (tid < n) {
-        const int c = tid;
-        for (int i = 0; i < n; ++i) {
-            if (i < c) {
-                T[i][c] = make_double2(0.0, 0.0);
-                continue;
-            }
-            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            for (int l = c; l < i; ++l) {
+    // L X = I row by row: X[i][c] = (delta_ic - sum_{c <= l < i} L[i][l] X[l][c]) / L[i][i].
+    const int c = tid >> 3, part = tid & 7;
+    for (int i = 0; i < n; ++i) {
+        double2 s = make_double2(0.0, 0.0);
+        if (c < i)
+            for (int l = c + part; l < i; l += 8) {
                 const double2 p = cmul(S[i][l], T[l][c]);
-                s.x -= p.x;
-                s.y -= p.y;
+                s.x += p.x;
+                s.y += p.y;
             }
-            T[i][c] = make_double2(s.x * rd[i], s.y * rd[i]);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
         }
+        if (part == 0 && c < 32) {
+            if (c > i)
+                T[i][c] = make_double2(0.0, 0.0);
+            else
+                T[i][c] = make_double2(((c == i) ? 1.0 : 0.0) - s.x, -s.y);
+        }
+        __syncthreads();
+        if (part == 0 && c <= i)
+            T[i][c] = make_double2(T[i][c].x * rd[i], T[i][c].y * rd[i]);
+        __syncthreads();
     }
-    __syncthreads();
     for (int t = tid; t < n * n; t += blockDim.x) {
         const int i = t / n, j = t % n;
         A[(size_t)i * lda + j] = j <= i ? S[i][j] : make_double2(0.0, 0.0);

@@ -197,6 +197,25 @@ GW_API gw_status gw_reset_times(gw_ctx *ctx);
 GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
 
 /*
+ * Allocation-free inverse of a Hermitian positive-definite complex128 matrix, by the same FP64
+ * blocked Cholesky that gw_eps_inv uses.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- code running while a stream is captured into a
+ * CUDA graph, applications whose device memory belongs to another allocator, and loops that must
+ * not pay cudaFree's device-wide synchronisation.
+ *   eps     device pointer, n x n complex128, row-major (only its lower triangle is read)
+ *   n       1 <= n <= 512; larger orders return GW_E_INVALID
+ *   epsinv  device pointer, n x n complex128, receives eps^-1 (both triangles written)
+ *   stream  cudaStream_t to enqueue on (NULL = legacy default stream); the call synchronises it
+ *           and returns GW_E_NUMERIC if a Cholesky pivot was <= 0
+ * Both pointers must be on the calling thread's current device.  No context is needed and no
+ * device memory is allocated: the workspace is one static device array of 12.9 MB, which every
+ * GPU that loads the library keeps until the process exits.  The first call on a device looks up
+ * that array's device address; make that first call before any stream capture.  All calls share
+ * the array, so calls that overlap on the GPU (other threads, other streams) race: serialise them.
+ */
+GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *stream);
+
+/*
  * Window length of the 16-bit rank-k update: the tensor core accumulates `window_chunks` chunks
  * of 16 k (1..64, default 2) in TMEM before they are added into FP32 registers, and every
  * `flush_windows` windows (1..4096, default 256) the registers are added into P.  Shorter windows

@@ -45,6 +45,7 @@ SIGNATURES = {
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
+    "gw_eps_inv_noalloc": (_i, [_vp, _i, _vp, _vp]),
 }
 
 _lib = None

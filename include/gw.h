@@ -197,6 +197,42 @@ GW_API gw_status gw_reset_times(gw_ctx *ctx);
 GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
 
 /*
+ * Batch of independent systems (several q-points or supercells of uneven size), each held by its
+ * own context with its states loaded.  A batch pass computes, for every instance, the same results
+ * as gw_build_P (16-bit precisions) + gw_P_to_G + gw_eps_inv(GW_INV_CHOLESKY):
+ *   - pair densities per instance;
+ *   - ONE persistent launch of the rank-k update over the tiles of every instance (one CTA per SM
+ *     walks a static tile list ordered by decreasing k), bit-identical to the per-instance kernel
+ *     for the same window settings;
+ *   - per-instance transforms, eps and FP64 inverse.
+ * Results are read from each context (gw_get_buffer GW_BUF_PG / GW_BUF_EPSINV, or gw_eps_inv-style
+ * buffers via gw_get_buffer).  All contexts must share one device and one stream.
+ *
+ * gw_batch_create   ctxs[n] loaded contexts, gcuts[n] their sphere cuts, precision GW_PREC_FP16X3
+ *                   or GW_PREC_BF16X3 (else GW_E_UNSUPPORTED).  Allocates every buffer the pass
+ *                   needs, builds the sphere plans and the tile table.  The contexts must outlive
+ *                   the batch and must not be reloaded while it is in use.
+ * gw_batch_run      one pass.  use_graph != 0: the first call runs eagerly, the second captures the
+ *                   whole pass into a CUDA graph, later calls replay it (recaptured after
+ *                   gw_batch_set_window).  Synchronises the stream and returns the first error
+ *                   of any instance (message: gw_batch_last_error).
+ * gw_batch_autotune picks the window / flush lengths of the rank-k update by timing the candidates
+ *                   whose measured FP16-split error is within target_error (e.g. 1e-6); the choice is
+ *                   appended to cache_path (JSON lines keyed by the instance shapes; NULL = no cache)
+ *                   and reused from it when the same batch is tuned again.
+ * gw_batch_stats    stats4[0] = last pass's rank-k update time in ms, [1] = window, [2] = flush,
+ *                   [3] = number of tiles.
+ */
+typedef struct gw_batch gw_batch;
+GW_API gw_status gw_batch_create(gw_batch **out, gw_ctx *const *ctxs, int n, const int *gcuts, int precision);
+GW_API gw_status gw_batch_destroy(gw_batch *batch);
+GW_API gw_status gw_batch_run(gw_batch *batch, int use_graph);
+GW_API gw_status gw_batch_set_window(gw_batch *batch, int window_chunks, int flush_windows);
+GW_API gw_status gw_batch_autotune(gw_batch *batch, const char *cache_path, double target_error);
+GW_API gw_status gw_batch_stats(gw_batch *batch, double *stats4);
+GW_API gw_status gw_batch_last_error(const gw_batch *batch, char *buf, size_t n);
+
+/*
  * Allocation-free inverse of a Hermitian positive-definite complex128 matrix, by the same FP64
  * blocked Cholesky that gw_eps_inv uses.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- code running while a stream is captured into a

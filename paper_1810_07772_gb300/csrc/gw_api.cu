@@ -264,7 +264,7 @@ gw_status build_plan(Ctx &c, int gcut)
 }
 
 // eps^-1 by blocked Cholesky (eps = L L^H, Y = L^-1, eps^-1 = Y^H Y).
-gw_status inverse_cholesky(Ctx &c)
+gw_status inverse_cholesky(Ctx &c, cudaStream_t s)
 {
     const int N = c.ng, NB = CHOL_NB;
     const int nblk = (N + NB - 1) / NB;
@@ -273,7 +273,6 @@ gw_status inverse_cholesky(Ctx &c)
     GW_TRY(ensure(c, c.d_work, c.cap.work, need * sizeof(double2), "inverse workspace"));
     double2 *A = c.d_work, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)N * N,
             *Dinv = W + (size_t)N * NB;
-    cudaStream_t s = c.stream;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
     GW_CUDA(cudaMemcpyAsync(A, c.d_eps, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s), "copy eps");
     for (int kb = 0; kb < nblk; ++kb) {
@@ -780,7 +779,7 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     record(c, 6);
     GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
     record(c, 7);
-    GW_TRY(method == GW_INV_CHOLESKY ? inverse_cholesky(c) : inverse_newton(c));
+    GW_TRY(method == GW_INV_CHOLESKY ? inverse_cholesky(c, c.stream) : inverse_newton(c));
     record(c, 8);
     if (eps_out)
         GW_CUDA(cudaMemcpyAsync(eps_out, c.d_eps, bytes, cudaMemcpyDefault, s), "copy eps out");
@@ -858,6 +857,466 @@ gw_status gw_get_dims(gw_ctx *h, int *d)
     d[5] = c.nc;
     d[6] = c.PG_ready ? c.ng : 0;
     d[7] = c.nr_pad;
+    return GW_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================= batch
+// Independent systems of uneven size (q-points, supercells) in one pass: per-instance pair
+// densities, ONE persistent launch of the rank-k update over every instance's tiles, then each
+// instance's transforms, eps and FP64 inverse.  The whole pass can be captured once in a CUDA
+// graph and replayed.  Every instance keeps its own context (buffers, status word, results).
+
+struct gw_batch {
+    std::vector<gw_ctx *> ctxs;
+    std::vector<int> gcut;
+    int precision = GW_PREC_FP16X3;
+    int device = 0;
+    cudaStream_t stream = nullptr;  // the batch's own non-blocking stream
+    bool own_stream = false;
+    HerkJob *d_jobs = nullptr;
+    int4 *d_tiles = nullptr;
+    int n_tiles = 0, grid = 0;
+    int W = 2, L = 256;
+    uint32_t *d_err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float herk_ms = 0.f;
+    int runs = 0;
+    std::string last_error;
+};
+
+namespace {
+
+gw_status vbfail(gw_batch &b, gw_status st, const char *fmt, va_list ap)
+{
+    char buf[512];
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    b.last_error = buf;
+    return st;
+}
+
+gw_status bfail(gw_batch &b, gw_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    const gw_status r = vbfail(b, st, fmt, ap);
+    va_end(ap);
+    return r;
+}
+
+gw_status bfail(gw_batch *b, gw_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    const gw_status r = vbfail(*b, st, fmt, ap);
+    va_end(ap);
+    return r;
+}
+
+#define GW_BCUDA(call, where)                                                                  \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            cudaGetLastError();                                                                \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? GW_E_NOMEM : GW_E_CUDA, "%s: %s", \
+                         where, cudaGetErrorString(e_));                                       \
+        }                                                                                      \
+    } while (0)
+
+void drop_graph(gw_batch &b)
+{
+    if (b.exec)
+        cudaGraphExecDestroy(b.exec);
+    if (b.graph)
+        cudaGraphDestroy(b.graph);
+    b.exec = nullptr;
+    b.graph = nullptr;
+}
+
+// Allocate every buffer the pass needs (graph capture must not allocate) and build the plans.
+gw_status batch_prepare(gw_batch &b)
+{
+    const bool bf16 = b.precision == GW_PREC_BF16X3;
+    std::vector<HerkJob> jobs;
+    std::vector<int4> tiles;
+    for (size_t i = 0; i < b.ctxs.size(); ++i) {
+        Ctx &c = b.ctxs[i]->c;
+        const int kpad = ((c.k + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
+        c.kpad = kpad;
+        const size_t Fbytes = (size_t)kpad * c.nr_pad * 2 * 4;
+        GW_TRY(ensure(c, c.d_F, c.cap.F, Fbytes, "pair-density operand"));
+        if (!c.d_small)
+            GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");
+        c.F_bytes = Fbytes;
+        c.P_bytes = (size_t)c.nr * c.nr * sizeof(float2);
+        GW_TRY(ensure(c, c.d_P, c.cap.P, c.P_bytes, "P(r,r')"));
+        if (b.gcut[i] != c.gcut)
+            GW_TRY(build_plan(c, b.gcut[i]));
+        if (!dft_supported(c.plan))
+            return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", c.ng);
+        const int ng = c.ng, NB = CHOL_NB, nblk = (ng + NB - 1) / NB;
+        GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
+        GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
+        GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+        GW_TRY(ensure(c, c.d_eps, c.cap.eps, (size_t)ng * ng * sizeof(double2), "eps"));
+        GW_TRY(ensure(c, c.d_epsinv, c.cap.epsinv, (size_t)ng * ng * sizeof(double2), "eps^-1"));
+        const size_t work = (size_t)3 * ng * ng + (size_t)NB * ng + (size_t)nblk * NB * NB;
+        GW_TRY(ensure(c, c.d_work, c.cap.work, work * sizeof(double2), "inverse workspace"));
+        jobs.push_back({reinterpret_cast<const uint16_t *>(c.d_F), c.d_P, reinterpret_cast<const int *>(c.d_small + 1),
+                        c.nr, c.nr_pad, kpad, 0});
+        for (const int2 t : herk_tiles(c.nr_pad, HERK16_T, HERK16_T))
+            tiles.push_back(make_int4((int)i, t.x, t.y, 0));
+    }
+    // longest tiles first: with the static round-robin schedule every CTA gets a similar load
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [&](const int4 &a, const int4 &c2) { return jobs[a.x].kpad > jobs[c2.x].kpad; });
+    if (b.d_jobs)
+        cudaFree(b.d_jobs);
+    if (b.d_tiles)
+        cudaFree(b.d_tiles);
+    b.d_jobs = nullptr;
+    b.d_tiles = nullptr;
+    GW_BCUDA(cudaMalloc(&b.d_jobs, jobs.size() * sizeof(HerkJob)), "job table");
+    GW_BCUDA(cudaMalloc(&b.d_tiles, tiles.size() * sizeof(int4)), "tile table");
+    GW_BCUDA(cudaMemcpy(b.d_jobs, jobs.data(), jobs.size() * sizeof(HerkJob), cudaMemcpyHostToDevice), "job upload");
+    GW_BCUDA(cudaMemcpy(b.d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice), "tile upload");
+    b.n_tiles = static_cast<int>(tiles.size());
+    int sms = 0;
+    GW_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device), "SM count");
+    b.grid = std::min(b.n_tiles, sms);
+    (void)bf16;
+    return GW_OK;
+}
+
+gw_status batch_pair_densities(gw_batch &b)
+{
+    for (gw_ctx *h : b.ctxs) {
+        Ctx &c = h->c;
+        GW_CUDA(launch_pair_density16(c.d_psiT, c.d_sw, c.sw_max, c.nr, c.nb, c.nv, c.nc, c.kpad, c.nr_pad,
+                                      b.precision == GW_PREC_BF16X3, c.d_small, reinterpret_cast<int *>(c.d_small + 1),
+                                      reinterpret_cast<uint16_t *>(c.d_F), b.stream),
+                "pair densities (batch)");
+        c.F_prec = b.precision;
+    }
+    return GW_OK;
+}
+
+gw_status batch_herk(gw_batch &b)
+{
+    const uint64_t wait_ns = static_cast<uint64_t>(b.ctxs[0]->c.wait_limit_ms * 1e6);
+    GW_BCUDA(cudaEventRecord(b.e0, b.stream), "event");
+    GW_BCUDA(launch_herk16p(b.d_jobs, b.d_tiles, b.n_tiles, b.grid, b.precision == GW_PREC_BF16X3, b.d_err, wait_ns,
+                            b.W, b.L, b.stream),
+             "rank-k update (persistent, batch)");
+    GW_BCUDA(cudaEventRecord(b.e1, b.stream), "event");
+    return GW_OK;
+}
+
+// The whole pass, launches only (no allocation, no host synchronisation): safe to capture.
+gw_status batch_enqueue(gw_batch &b)
+{
+    GW_TRY(batch_pair_densities(b));
+    GW_TRY(batch_herk(b));
+    for (gw_ctx *h : b.ctxs) {
+        Ctx &c = h->c;
+        const int ng = c.ng;
+        cudaStream_t s = b.stream;
+        GW_CUDA(launch_dft_rows(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, s), "row transform");
+        GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
+        GW_CUDA(launch_dft_rows(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, s), "column transform");
+        GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
+        GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
+        GW_TRY(inverse_cholesky(c, s));
+    }
+    return GW_OK;
+}
+
+gw_status batch_status(gw_batch &b)
+{
+    GW_BCUDA(cudaStreamSynchronize(b.stream), "batch synchronize");
+    uint32_t word = 0;
+    GW_BCUDA(cudaMemcpy(&word, b.d_err, sizeof word, cudaMemcpyDeviceToHost), "status readback");
+    if (word != 0) {
+        cudaMemset(b.d_err, 0, sizeof(uint32_t));
+        return bfail(b, static_cast<gw_status>(word & 0xFF), "rank-k update: device wait ran out (block %u)",
+                     word >> 16);
+    }
+    gw_status first = GW_OK;
+    for (gw_ctx *h : b.ctxs) {
+        Ctx &c = h->c;
+        const gw_status st = read_device_status(c);
+        c.P_ready = c.PG_ready = c.eps_ready = st == GW_OK;
+        if (st != GW_OK && first == GW_OK) {
+            first = st;
+            b.last_error = c.last_error;
+        }
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b.e0, b.e1) == cudaSuccess)
+        b.herk_ms = ms;
+    cudaGetLastError();
+    return first;
+}
+
+// Measured error of the FP16 split against FP64 on the 24^3 workload (k = 15360) for window
+// lengths W (chunks of 16 k): the truncating TMEM sum of one window dominates and does not grow
+// with k.  BF16 keeps 8 + 8 bits and sits near 4e-6 for any W.
+double predicted_error(int precision, int W)
+{
+    if (precision == GW_PREC_BF16X3)
+        return 4e-6;
+    static const int ws[] = {1, 2, 3, 4, 6, 8, 16};
+    static const double es[] = {2.6e-7, 4.9e-7, 5.7e-7, 6.8e-7, 1.2e-6, 1.3e-6, 2.6e-6};
+    for (int i = 0; i < 7; ++i)
+        if (W <= ws[i])
+            return es[i];
+    return 1e-5;
+}
+
+std::string batch_key(const gw_batch &b)
+{
+    std::string k = "prec" + std::to_string(b.precision);
+    for (size_t i = 0; i < b.ctxs.size(); ++i) {
+        const Ctx &c = b.ctxs[i]->c;
+        k += "|" + std::to_string(c.n1) + "x" + std::to_string(c.n2) + "x" + std::to_string(c.n3) + ",v" +
+             std::to_string(c.nv) + ",c" + std::to_string(c.nc) + ",g" + std::to_string(b.gcut[i]);
+    }
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_batch_create(gw_batch **out, gw_ctx *const *ctxs, int n, const int *gcuts, int precision)
+{
+    if (!out || !ctxs || !gcuts || n < 1 || n > 4096)
+        return GW_E_INVALID;
+    *out = nullptr;
+    if (precision != GW_PREC_FP16X3 && precision != GW_PREC_BF16X3)
+        return GW_E_UNSUPPORTED;
+    gw_batch *b = new (std::nothrow) gw_batch;
+    if (!b)
+        return GW_E_NOMEM;
+    b->precision = precision;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !ctxs[i]->c.loaded) {
+            delete b;
+            return GW_E_NOT_READY;
+        }
+        const Ctx &c = ctxs[i]->c;
+        const int nmin = std::min(c.n1, std::min(c.n2, c.n3));
+        if (i > 0 && (c.device != ctxs[0]->c.device || c.stream != ctxs[0]->c.stream)) {
+            delete b;
+            return GW_E_INVALID;  // one device and one stream for the whole batch
+        }
+        if (gcuts[i] < 0 || 4LL * gcuts[i] >= (long long)nmin * nmin) {
+            delete b;
+            return GW_E_INVALID;
+        }
+        b->ctxs.push_back(ctxs[i]);
+        b->gcut.push_back(gcuts[i]);
+    }
+    b->device = ctxs[0]->c.device;
+    // the pass runs on a stream of its own: the contexts' stream may be the legacy default
+    // stream, which cannot be captured into a graph
+    if (cudaSetDevice(b->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return GW_E_CUDA;
+    }
+    b->own_stream = true;
+    if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc(&b->d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, sizeof(uint32_t)) != cudaSuccess || cudaEventCreate(&b->e0) != cudaSuccess ||
+        cudaEventCreate(&b->e1) != cudaSuccess) {
+        cudaGetLastError();
+        gw_batch_destroy(b);
+        return GW_E_CUDA;
+    }
+    const gw_status st = batch_prepare(*b);
+    if (st != GW_OK) {
+        gw_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return GW_OK;
+}
+
+gw_status gw_batch_destroy(gw_batch *b)
+{
+    if (!b)
+        return GW_E_INVALID;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(*b);
+    if (b->d_jobs)
+        cudaFree(b->d_jobs);
+    if (b->d_tiles)
+        cudaFree(b->d_tiles);
+    if (b->d_err)
+        cudaFree(b->d_err);
+    if (b->e0)
+        cudaEventDestroy(b->e0);
+    if (b->e1)
+        cudaEventDestroy(b->e1);
+    if (b->own_stream && b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+    return GW_OK;
+}
+
+gw_status gw_batch_set_window(gw_batch *b, int window_chunks, int flush_windows)
+{
+    if (!b || window_chunks < 1 || window_chunks > 64 || flush_windows < 1 || flush_windows > 4096)
+        return GW_E_INVALID;
+    if (b->W != window_chunks || b->L != flush_windows)
+        drop_graph(*b);  // the captured launch carries the old lengths
+    b->W = window_chunks;
+    b->L = flush_windows;
+    return GW_OK;
+}
+
+gw_status gw_batch_run(gw_batch *b, int use_graph)
+{
+    if (!b)
+        return GW_E_INVALID;
+    gw_batch &bb = *b;
+    cudaSetDevice(bb.device);
+    for (gw_ctx *h : bb.ctxs)
+        if (!h->c.loaded)
+            return bfail(bb, GW_E_NOT_READY, "a context lost its states");
+    // work queued earlier on the contexts' stream comes first
+    GW_BCUDA(cudaStreamSynchronize(bb.ctxs[0]->c.stream), "context stream synchronize");
+    if (!use_graph || bb.runs == 0) {
+        // eager pass (the first pass is always eager, so every lazy setup happens outside capture)
+        const gw_status st = batch_enqueue(bb);
+        if (st != GW_OK) {
+            cudaStreamSynchronize(bb.stream);
+            return st;
+        }
+    } else {
+        if (!bb.exec) {
+            cudaStreamCaptureStatus cs;
+            if (cudaStreamIsCapturing(bb.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+                return bfail(bb, GW_E_INVALID, "the batch stream is already being captured");
+            if (cudaStreamBeginCapture(bb.stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(bb, GW_E_CUDA, "stream capture could not start");
+            }
+            const gw_status st = batch_enqueue(bb);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(bb.stream, &g);
+            if (st != GW_OK || ec != cudaSuccess || !g) {
+                cudaGetLastError();
+                if (g)
+                    cudaGraphDestroy(g);
+                return st != GW_OK ? st : bfail(bb, GW_E_CUDA, "stream capture failed");
+            }
+            bb.graph = g;
+            if (cudaGraphInstantiate(&bb.exec, bb.graph, 0) != cudaSuccess) {
+                cudaGetLastError();
+                drop_graph(bb);
+                return bfail(bb, GW_E_CUDA, "graph instantiation failed");
+            }
+        }
+        GW_BCUDA(cudaGraphLaunch(bb.exec, bb.stream), "graph launch");
+    }
+    ++bb.runs;
+    return batch_status(bb);
+}
+
+gw_status gw_batch_autotune(gw_batch *b, const char *cache_path, double target_error)
+{
+    if (!b || !(target_error > 0.0))
+        return GW_E_INVALID;
+    gw_batch &bb = *b;
+    cudaSetDevice(bb.device);
+    const std::string key = batch_key(bb);
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "r")) {
+            char line[8192];
+            int W = 0, L = 0;
+            while (std::fgets(line, sizeof line, f)) {
+                const std::string s(line);
+                const std::string want = "{\"key\": \"" + key + "\"";
+                if (s.compare(0, want.size(), want) == 0) {
+                    const size_t pw = s.find("\"W\": "), pl = s.find("\"L\": ");
+                    if (pw != std::string::npos && pl != std::string::npos) {
+                        W = std::atoi(s.c_str() + pw + 5);
+                        L = std::atoi(s.c_str() + pl + 5);
+                    }
+                }
+            }
+            std::fclose(f);
+            if (W >= 1 && L >= 1)
+                return gw_batch_set_window(b, W, L);
+        }
+    }
+    struct Cand {
+        int W, L;
+    };
+    const Cand cands[] = {{1, 4096}, {2, 256}, {2, 4096}, {3, 4096}, {4, 4096}, {6, 4096}, {8, 4096}};
+    GW_TRY(batch_pair_densities(bb));
+    int bestW = 0, bestL = 0;
+    float best = 1e30f;
+    for (const Cand &cd : cands) {
+        if (predicted_error(bb.precision, cd.W) * 1.25 > target_error)
+            continue;
+        bb.W = cd.W;
+        bb.L = cd.L;
+        GW_TRY(batch_herk(bb));  // warm-up
+        float tot = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            GW_TRY(batch_herk(bb));
+            GW_BCUDA(cudaEventSynchronize(bb.e1), "autotune sync");
+            float ms = 0.f;
+            GW_BCUDA(cudaEventElapsedTime(&ms, bb.e0, bb.e1), "autotune timing");
+            tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            bestW = cd.W;
+            bestL = cd.L;
+        }
+    }
+    const gw_status st = batch_status(bb);
+    if (st != GW_OK)
+        return st;
+    if (bestW == 0)
+        return bfail(bb, GW_E_UNSUPPORTED, "no window length meets error target %g", target_error);
+    drop_graph(bb);
+    bb.W = bestW;
+    bb.L = bestL;
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "{\"key\": \"%s\", \"W\": %d, \"L\": %d, \"herk_ms\": %.4f, \"target_error\": %g}\n",
+                         key.c_str(), bestW, bestL, best / 2.f, target_error);
+            std::fclose(f);
+        }
+    }
+    return GW_OK;
+}
+
+gw_status gw_batch_stats(gw_batch *b, double *stats4)
+{
+    if (!b || !stats4)
+        return GW_E_INVALID;
+    stats4[0] = b->herk_ms;
+    stats4[1] = b->W;
+    stats4[2] = b->L;
+    stats4[3] = b->n_tiles;
+    return GW_OK;
+}
+
+gw_status gw_batch_last_error(const gw_batch *b, char *buf, size_t n)
+{
+    if (!b || !buf || n == 0)
+        return GW_E_INVALID;
+    std::snprintf(buf, n, "%s", b->last_error.c_str());
     return GW_OK;
 }
 

@@ -142,6 +142,18 @@ cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
                           cudaStream_t s);
 
+// k_herk16p.cu: persistent multi-instance rank-k update.  One job per instance; tiles are
+// (job, 128-row block of r, 128-row block of r', 0) in the order CTAs take them (tile t goes to
+// CTA t mod grid).
+struct HerkJob {
+    const uint16_t *F;
+    float2 *P;
+    const int *scale_exp;
+    int nr, nr_pad, kpad, pad;
+};
+cudaError_t launch_herk16p(const HerkJob *jobs, const int4 *tiles, int n_tiles, int grid, bool bf16, uint32_t *err,
+                           uint64_t wait_ns, int W, int L, cudaStream_t s);
+
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
 bool dft_supported(const DftPlan &p);  // sphere small enough for the transform kernel

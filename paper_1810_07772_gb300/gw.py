@@ -46,6 +46,13 @@ SIGNATURES = {
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
     "gw_eps_inv_noalloc": (_i, [_vp, _i, _vp, _vp]),
+    "gw_batch_create": (_i, [_c.POINTER(_vp), _c.POINTER(_vp), _i, _c.POINTER(_i), _i]),
+    "gw_batch_destroy": (_i, [_vp]),
+    "gw_batch_run": (_i, [_vp, _i]),
+    "gw_batch_set_window": (_i, [_vp, _i, _i]),
+    "gw_batch_autotune": (_i, [_vp, _c.c_char_p, _d]),
+    "gw_batch_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
+    "gw_batch_last_error": (_i, [_vp, _c.c_char_p, _sz]),
 }
 
 _lib = None
@@ -223,14 +230,74 @@ class Context:
         ptr, nbytes = self.buffer(which)
         d = self.dims8()
         nr, ng, nr_pad = d[3], d[6], d[7]
+        raw = torch.as_tensor(DeviceView(ptr, (nbytes,), "|u1"), device=f"cuda:{self.device}")
         if which == "P":
-            shape, ts = (nr, nr), "<c8"
-        elif which == "PG":
-            shape, ts = (ng, ng), "<c8"
-        elif which in ("eps", "epsinv"):
-            shape, ts = (ng, ng), "<c16"
-        elif which == "weights":
-            shape, ts = (nbytes // 4,), "<f4"
-        else:
-            shape, ts = (nbytes // 4,), "<f4"
-        return torch.as_tensor(DeviceView(ptr, shape, ts), device=f"cuda:{self.device}")
+            return raw.view(torch.complex64).view(nr, nr)
+        if which == "PG":
+            return raw[: ng * ng * 8].view(torch.complex64).view(ng, ng)
+        if which in ("eps", "epsinv"):
+            return raw[: ng * ng * 16].view(torch.complex128).view(ng, ng)
+        return raw.view(torch.float32) if nbytes % 4 == 0 else raw
+
+
+class Batch:
+    """Independent systems in one pass (gw_batch_*): contexts with loaded states and their gcuts."""
+
+    def __init__(self, contexts, gcuts, precision="fp16x3"):
+        n = len(contexts)
+        hs = (ctypes.c_void_p * n)(*[c._h.value for c in contexts])
+        gc = (ctypes.c_int * n)(*[int(g) for g in gcuts])
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self._h = ctypes.c_void_p()
+        st = lib().gw_batch_create(ctypes.byref(self._h), hs, n, gc, prec)
+        if st != GW_OK:
+            msg = ""
+            for c in contexts:
+                buf = ctypes.create_string_buffer(512)
+                lib().gw_last_error(c._h, buf, 512)
+                msg = msg or buf.value.decode()
+            raise GwError(st, "gw_batch_create failed " + msg)
+        self.contexts = list(contexts)
+        self.gcuts = list(gcuts)
+
+    def _check(self, st):
+        if st != GW_OK:
+            buf = ctypes.create_string_buffer(512)
+            lib().gw_batch_last_error(self._h, buf, 512)
+            raise GwError(st, buf.value.decode())
+
+    def run(self, use_graph=True):
+        self._check(lib().gw_batch_run(self._h, 1 if use_graph else 0))
+        for c in self.contexts:   # each context now holds P~, eps and eps^-1 of its instance
+            d = c.dims8()
+            c.ng = d[6]
+
+    def set_window(self, window_chunks, flush_windows):
+        self._check(lib().gw_batch_set_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def autotune(self, cache_path=None, target_error=1e-6):
+        p = cache_path.encode() if cache_path else None
+        self._check(lib().gw_batch_autotune(self._h, p, float(target_error)))
+        return self.stats()
+
+    def stats(self):
+        d = (ctypes.c_double * 4)()
+        self._check(lib().gw_batch_stats(self._h, d))
+        return {"herk_ms": d[0], "window_chunks": int(d[1]), "flush_windows": int(d[2]), "tiles": int(d[3])}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gw_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

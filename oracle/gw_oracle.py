@@ -213,6 +213,28 @@ def P_gspace(psi, E_eV, nv, dims, gvec, v_chunk=4):
     return Pt
 
 
+def P_gspace_entries(psi, E_eV, nv, dims, gsel):
+    """Eq. (gpsaceP) on a chosen set of G only: P~(Ga, Gb) for Ga, Gb in gsel, with
+    M_vc(G) = sum_r exp(-i G.r) conj(psi_v(r)) psi_c(r) written as explicit phase sums (no FFT), so
+    single entries of large systems can be checked one by one."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    E = to_hartree(E_eV)
+    n1, n2, n3 = dims
+    j1, j2, j3 = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    j1, j2, j3 = j1.reshape(-1), j2.reshape(-1), j3.reshape(-1)
+    gsel = np.asarray(gsel).reshape(-1, 3)
+    phases = np.exp(-2j * np.pi * (np.outer(gsel[:, 0], j1) / n1 + np.outer(gsel[:, 1], j2) / n2
+                                   + np.outer(gsel[:, 2], j3) / n3))          # [ns][N_r]
+    ns = len(gsel)
+    out = np.zeros((ns, ns), dtype=np.complex128)
+    for v in range(nv):
+        weighted = phases * np.conj(psi[v])[None, :]                           # [ns][N_r]
+        M = weighted @ psi[nv:].T                                              # [ns][N_c]: M_vc(G)
+        d = 2.0 / (E[v] - E[nv:])
+        out += (M * d[None, :]) @ np.conj(M.T)
+    return out
+
+
 def P_gspace_truncated(psi, E_eV, nv, nc_keep, dims, gvec):
     """Eq. (gpsaceP) with the unoccupied sum cut to the nc_keep lowest states (band truncation)."""
     psi = np.asarray(psi)

@@ -251,3 +251,17 @@ def test_small_workload_rspace_vs_gspace():
     b = O.eps_inv_path(psi, E, w.nv, dims, w.gcut, w.cell_L, route="gspace")
     assert np.linalg.norm(a["Pt"] - b["Pt"]) < 1e-13 * np.linalg.norm(b["Pt"])
     assert np.max(np.abs(a["epsinv"] - b["epsinv"])) < 1e-13
+
+
+def test_selected_entries_equal_full_gspace_route():
+    """P_gspace_entries (explicit phase sums on chosen G) equals the FFT-based Eq. (gpsaceP) on the
+    same entries, and the r-space route on a tiny grid."""
+    dims = (6, 5, 4)
+    psi, E = inputs.make_states(0, 3, 8, 23, dims=dims)
+    g = O.sphere(dims, 5)
+    sel = np.array([0, 3, 7, len(g) - 1])
+    full = O.P_gspace(psi, E, 3, dims, g)
+    part = O.P_gspace_entries(psi, E, 3, dims, g[sel])
+    assert np.max(np.abs(part - full[np.ix_(sel, sel)])) < 1e-15 * np.max(np.abs(full)) * 10
+    Pr = O.P_to_G(O.P_rspace(psi, E, 3), dims, g)
+    assert np.max(np.abs(part - Pr[np.ix_(sel, sel)])) < 1e-13

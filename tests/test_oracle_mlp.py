@@ -1,0 +1,57 @@
+"""Pins for the oracle of the learned truncation correction: the analytic gradient against central
+finite differences, a one-layer case against the closed-form least-squares gradient, and the
+features against a hand-made 2-vector system."""
+import numpy as np
+
+from oracle import mlp as M
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    n_in, hidden, B = 5, 7, 9
+    theta = rng.standard_normal(M.n_params(n_in, hidden)) * 0.4
+    X = rng.standard_normal((B, n_in))
+    T = rng.standard_normal((B, 2))
+    loss, grads = M.loss_and_grad(M.unpack(theta, n_in, hidden), X, T)
+    g = M.flatten(grads)
+    eps = 1e-6
+    for i in rng.choice(theta.size, 40, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        lp, _ = M.loss_and_grad(M.unpack(tp, n_in, hidden), X, T)
+        lm, _ = M.loss_and_grad(M.unpack(tm, n_in, hidden), X, T)
+        assert abs((lp - lm) / (2 * eps) - g[i]) < 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_output_layer_gradient_is_least_squares_gradient():
+    """With all hidden layers fixed, dL/dW4 = (1/B) (y - t)^T h3 and dL/db4 = mean(y - t): the
+    closed form of linear least squares."""
+    rng = np.random.default_rng(5)
+    n_in, hidden, B = 3, 4, 11
+    params = M.unpack(rng.standard_normal(M.n_params(n_in, hidden)), n_in, hidden)
+    X = rng.standard_normal((B, n_in))
+    T = rng.standard_normal((B, 2))
+    y, acts = M.forward(params, X)
+    _, grads = M.loss_and_grad(params, X, T)
+    h3 = acts[-1]
+    assert np.allclose(grads[-1][0], (y - T).T @ h3 / B, atol=1e-14)
+    assert np.allclose(grads[-1][1], np.mean(y - T, axis=0), atol=1e-14)
+    # and h3 really is tanh of the previous layer
+    W3, b3 = params[2]
+    assert np.allclose(h3, np.tanh(acts[2] @ W3.T + b3))
+
+
+def test_features_by_hand():
+    """Two G-vectors m0 = 0, m1 = (1, 0, 0), gcut = 1, P~_lo = [[0, 1+2i], [1-2i, 4]]:
+    s = 1/4 (mean |diagonal| over G != 0), three upper-triangle rows (0,0), (0,1), (1,1)."""
+    PG = np.array([[0.0, 1 + 2j], [1 - 2j, 4.0]])
+    g = np.array([[0, 0, 0], [1, 0, 0]])
+    X, s = M.features(PG, g, 1, 3.0, 6.0)
+    assert s == 0.25
+    assert X.shape == (3, M.N_FEATURES)
+    assert np.allclose(X[1], [0, 1, 0.25, 0.25, 0.5, 0, 1, 0, 0.5, 1])
+    assert np.allclose(X[0], [0, 0, 0, 0, 0, 0, 0, 1, 0.5, 1])
+    assert np.allclose(X[2], [1, 1, 0, 1, 0, 1, 1, 1, 0.5, 0])
+    T = M.targets(PG, PG + np.array([[0, 4j], [-4j, 8]]))
+    assert np.allclose(T, [[0, 0], [0, 1], [2, 0]])

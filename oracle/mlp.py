@@ -116,3 +116,31 @@ def to_fp16_weights(theta, n_in, hidden):
         out[o:o + r * c] = out[o:o + r * c].astype(np.float16).astype(np.float64)
         o += r * c + r
     return out
+
+
+def apply_correction(PG_lo, Y, s):
+    """P~ = P~_lo + (y0 + i y1) / s on the upper triangle, mirrored as the conjugate below it.
+    The diagonal takes y0 only (a Hermitian matrix has a real diagonal) and the G = 0 row and
+    column are left unchanged (they vanish exactly, because occupied and unoccupied states are
+    orthogonal, at any N_c)."""
+    P = np.array(PG_lo, dtype=np.complex128)
+    ng = P.shape[0]
+    gi, hi = np.triu_indices(ng)
+    d = (np.asarray(Y[:, 0], dtype=np.float64) + 1j * np.asarray(Y[:, 1], dtype=np.float64)) / s
+    keep = (gi != 0) & (hi != 0)
+    gi, hi, d = gi[keep], hi[keep], d[keep]
+    on = gi == hi
+    P[gi[on], gi[on]] += np.real(d[on])
+    P[gi[~on], hi[~on]] += d[~on]
+    P[hi[~on], gi[~on]] += np.conj(d[~on])
+    return P
+
+
+def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Adam (Kingma and Ba, 2015): moment updates, bias correction by 1 - beta^t, then
+    theta -= lr * m_hat / (sqrt(v_hat) + eps).  Returns new (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

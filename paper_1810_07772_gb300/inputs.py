@@ -116,3 +116,36 @@ def plane_wave_states(dims, m_list, energies_eV):
         ph = 2.0 * np.pi * (m[0] * j1 / n1 + m[1] * j2 / n2 + m[2] * j3 / n3)
         rows.append((np.exp(1j * ph) / np.sqrt(nr)).reshape(-1))
     return np.array(rows), np.asarray(energies_eV, dtype=np.float64)
+
+
+def mlp_init(n_in: int, hidden: int, seed: int, n_out: int = 2) -> np.ndarray:
+    """Initial parameters of the correction network, flat FP32 ``[W1, b1, W2, b2, W3, b3, W4, b4]``
+    with each ``W_l`` of shape ``(out, in)`` row-major: Glorot-uniform weights
+    ``U(-a, a), a = sqrt(6 / (fan_in + fan_out))`` and zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for r, c in [(hidden, n_in), (hidden, hidden), (hidden, hidden), (n_out, hidden)]:
+        a = np.sqrt(6.0 / (r + c))
+        parts.append(rng.uniform(-a, a, r * c))
+        parts.append(np.zeros(r))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def make_states_device(n: int, nv: int, nc: int, seed: int, device):
+    """Device-drawn variant of :func:`make_states` for workloads that need many large systems:
+    ``A`` from torch's seeded CUDA generator (complex64, real and imaginary parts N(0, 1/2)),
+    a reduced QR on the device, energies drawn exactly as in :func:`make_states` but from
+    ``default_rng(seed)`` directly.  Returns ``(psi [nv + nc][N_r] complex64 on device, E_eV)``."""
+    import torch
+
+    nr = n ** 3
+    nb = nv + nc
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    a = torch.randn((nr, nb), dtype=torch.complex64, device=device, generator=gen)
+    q, _ = torch.linalg.qr(a, mode="reduced")
+    psi = q.transpose(0, 1).contiguous()
+    rng = np.random.default_rng(seed)
+    ev = np.sort(rng.uniform(-10.0, 0.0, nv))
+    ec = np.sort(rng.uniform(0.5, 20.0, nc))
+    return psi, np.concatenate([ev, ec])

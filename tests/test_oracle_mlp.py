@@ -55,3 +55,22 @@ def test_features_by_hand():
     assert np.allclose(X[2], [1, 1, 0, 1, 0, 1, 1, 1, 0.5, 0])
     T = M.targets(PG, PG + np.array([[0, 4j], [-4j, 8]]))
     assert np.allclose(T, [[0, 0], [0, 1], [2, 0]])
+
+
+def test_apply_correction_by_hand():
+    """3x3 P~_lo = 0, three upper-triangle predictions per row: head row/column untouched,
+    diagonal takes the real part only, (1,2) and (2,1) are conjugates; s = 2 halves everything."""
+    Y = np.array([[9, 9], [9, 9], [9, 9], [2, 4], [4, 6], [6, 8]], dtype=float)
+    P = M.apply_correction(np.zeros((3, 3)), Y, 2.0)
+    want = np.array([[0, 0, 0], [0, 1, 2 + 3j], [0, 2 - 3j, 3]])
+    assert np.array_equal(P, want)
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    """From zero moments the bias-corrected first step is lr * g / (|g| + eps): lr * sign(g) up to
+    eps; a second identical gradient repeats it exactly (m_hat = g, v_hat = g^2 again)."""
+    g = np.array([3.0, -0.5, 2e-3, -7.0])
+    th, m, v = M.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 0.01, eps=0.0)
+    assert np.allclose(th, -0.01 * np.sign(g), rtol=0, atol=1e-15)
+    th2, _, _ = M.adam_step(th, g, m, v, 2, 0.01, eps=0.0)
+    assert np.allclose(th2, -0.02 * np.sign(g), rtol=0, atol=1e-15)

@@ -263,6 +263,104 @@ GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_wi
  * runs out makes its kernel record GW_E_TIMEOUT and return early. */
 GW_API gw_status gw_set_wait_limit(gw_ctx *ctx, double ms);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned truncation correction.
+ *
+ * In practice the sum over unoccupied states c in Eq. (Pstatic) is cut at N_c = nc_keep, and
+ * Sec. 2 counts this band truncation among the method's costs.  The paper gives no correction;
+ * this library adds a learned one.  A multilayer perceptron
+ *     h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3), y = W4 h3 + b4
+ * (n_in -> hidden -> hidden -> hidden -> 2) maps features x of one upper-triangle entry
+ * (g, h), g <= h, of the truncated P~ to y ~ s (P~_all - P~_keep)(g, h) as (Re, Im).
+ *
+ * Weights are used in FP16 (rounded from an FP32 master copy), biases and accumulation in FP32.
+ *
+ * Upper-triangle entries are stored row-major: entry (g, h) is row t = g ng - g (g - 1)/2 + (h - g),
+ * and there are ng (ng + 1)/2 rows.
+ *
+ * Scale s = 1 / mean_{g >= 1} |Re P~_keep(g, g)|.  It makes features and targets O(1) for any
+ * system.
+ *
+ * Features (float32, 10 per row):
+ *   [ |m_g|^2/gcut, |m_h|^2/gcut, |m_g - m_h|^2/(4 gcut), s Re P~(g,h), s Im P~(g,h), s Re P~(g,g),
+ *     s Re P~(h,h), [g == h], ratio, [g == 0 or h == 0] ]
+ * Here m are the integer G-vectors and ratio is the per-system scalar from gw_corr_weight_ratio.
+ *
+ * Parameters are one flat float32 vector [W1, b1, W2, b2, W3, b3, W4, b4], each W_l row-major
+ * (out x in).  The loss is L = (1/(2B)) sum over the batch and both outputs of (y - t)^2.
+ *
+ * All data pointers are device pointers on the handle's (or the current) device.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct gw_mlp gw_mlp;
+
+/* Number of parameters of an n_in -> hidden x 3 -> 2 network. */
+GW_API gw_status gw_mlp_num_params(int n_in, int hidden, size_t *n);
+
+/* Network with zero parameters and Adam state.
+ *   n_in       1..64
+ *   hidden     1..1024
+ *   max_batch  largest batch of gw_mlp_grad / gw_mlp_train_step, and the chunk of gw_mlp_forward;
+ *              1..2^22
+ *   stream     cudaStream_t for every call on the handle (NULL = legacy default stream)
+ * Device memory: 4 P floats, P halves, 5 max_batch x hidden floats, and a split-K workspace
+ * of 64 x hidden x (hidden + 1) floats. */
+GW_API gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_batch, void *stream);
+GW_API gw_status gw_mlp_destroy(gw_mlp *m);
+GW_API gw_status gw_mlp_last_error(gw_mlp *m, char *buf, size_t n);
+
+/* Copy the flat parameters in (this resets Adam's moments and step count) or out.  theta is a
+ * host pointer (on_device = 0; the call then synchronises) or a device pointer (1). */
+GW_API gw_status gw_mlp_set_params(gw_mlp *m, const float *theta, int on_device);
+GW_API gw_status gw_mlp_get_params(gw_mlp *m, float *theta, int on_device);
+
+/* Inference: Y[n][2] = network(X[n][n_in]), in chunks of max_batch rows. */
+GW_API gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y);
+
+/* Loss and gradient of a batch, without an update.
+ *   rows    NULL, or batch sample indices into X[.][n_in] and T[.][2] (a minibatch gather)
+ *   grad    receives dL/dtheta (P floats, same flat order as the parameters)
+ *   loss    receives L (one float)
+ * Weights enter as their FP16 values, so the exact gradient is that of the network whose W_l
+ * are rounded to FP16. */
+GW_API gw_status gw_mlp_grad(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, float *grad,
+                             float *loss);
+
+/* One Adam step (Kingma and Ba, 2015) on a batch:
+ *     m <- b1 m + (1 - b1) g
+ *     v <- b2 v + (1 - b2) g^2
+ *     theta <- theta - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * followed by re-rounding of the FP16 weights.
+ *   loss_accum  NULL, or a device float to which this batch's L is added. */
+GW_API gw_status gw_mlp_train_step(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, double lr,
+                                   double beta1, double beta2, double adam_eps, float *loss_accum);
+
+/* ratio = sum_{c >= nc_keep} sum_v 2/(E_c - E_v) / sum_{c < nc_keep} sum_v 2/(E_c - E_v), in FP64,
+ * from device energies E_eV[nv + nc_all] (occupied first, as gw_load_states).  This is the
+ * weight of the omitted pairs in Eq. (Pstatic) relative to the kept ones; it needs only the
+ * energies of the omitted states, not their orbitals.  Output: one device float. */
+GW_API gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_all, float *ratio,
+                                      void *stream);
+
+/* Features of every upper-triangle entry of a truncated P~.
+ *   PG     complex64, ng x ng, as written by gw_P_to_G
+ *   ng     >= 2
+ *   gvec   int32 [ng][3] integer G-vectors in basis order
+ *   ratio  device float from gw_corr_weight_ratio
+ *   X      float [ng (ng + 1)/2][10]
+ *   scale  device float, receives s */
+GW_API gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, float *X,
+                                  float *scale, void *stream);
+
+/* Training targets T[t][2] = s (P~_all - P~_keep)(g, h), with s from gw_corr_features on P~_keep. */
+GW_API gw_status gw_corr_targets(const void *PG_keep, const void *PG_all, int ng, const float *scale, float *T,
+                                 void *stream);
+
+/* In place, P~(g,h) += (y0 + i y1)/s and P~(h,g) = its conjugate, for g < h.
+ * The diagonal takes y0/s only.  Row and column 0 are left unchanged: they vanish exactly at any
+ * N_c, because occupied and unoccupied states are orthogonal.
+ *   Y  float [ng (ng + 1)/2][2], from gw_mlp_forward */
+GW_API gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

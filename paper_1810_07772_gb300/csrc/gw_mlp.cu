@@ -1,0 +1,752 @@
+// Learned truncation correction of P~(G,G').
+//
+// The sum over unoccupied states c in Eq. (Pstatic) is cut at some N_c in practice, and the paper
+// lists this band truncation among the costs of the method (Sec. 2) without prescribing a cure.
+// This file adds one: a multilayer perceptron maps per-entry features of the truncated P~ to the
+// missing part P~(N_c = all) - P~(N_c = kept).  Everything runs on the device:
+//
+//   features / targets / apply   element-wise kernels over the upper triangle of P~
+//   forward / backward           a tiled SIMT GEMM with FP16 weights and FP32 accumulation,
+//                                fused bias + tanh (forward) and tanh' (backward) epilogues,
+//                                deterministic split-K for the weight gradients, with the bias
+//                                gradient taken as one more column of ones
+//   loss                         L = (1 / (2B)) sum (y - t)^2 and dL/dy = (y - t) / B
+//   optimiser                    Adam on an FP32 master copy; the FP16 weights are rounded from it
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+void count_launches(int n);
+}
+
+namespace {
+
+constexpr int NF = 10;        // features per P~ entry
+constexpr int NOUT = 2;       // (Re, Im) of the predicted correction
+constexpr int GT_M = 64, GT_N = 64, GT_K = 16;
+constexpr int SPLIT_MAX = 64;
+
+// Position of entry (g, h), g <= h, in the row-major upper triangle of an ng x ng matrix.
+__device__ __forceinline__ long tri_index(int g, int h, int ng)
+{
+    return (long)g * ng - (long)g * (g - 1) / 2 + (h - g);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-system scalars
+
+// ratio = sum_{c >= keep} sum_v 2/(E_c - E_v)  /  sum_{c < keep} sum_v 2/(E_c - E_v)   (FP64)
+__global__ void __launch_bounds__(256) weight_ratio_kernel(const double *E, int nv, int keep, int nc_all,
+                                                           float *ratio)
+{
+    __shared__ double s_om[256], s_in[256];
+    double om = 0, in = 0;
+    const long total = (long)nv * nc_all;
+    for (long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int v = (int)(i / nc_all), c = (int)(i % nc_all);
+        const double w = 2.0 / (E[nv + c] - E[v]);
+        if (c < keep)
+            in += w;
+        else
+            om += w;
+    }
+    s_om[threadIdx.x] = om;
+    s_in[threadIdx.x] = in;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_om[threadIdx.x] += s_om[threadIdx.x + o];
+            s_in[threadIdx.x] += s_in[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *ratio = (float)(s_om[0] / s_in[0]);
+}
+
+// s = 1 / mean_{g >= 1} |Re P~(g, g)|  (FP64 sum)
+__global__ void __launch_bounds__(256) entry_scale_kernel(const float2 *PG, int ng, float *scale)
+{
+    __shared__ double red[256];
+    double acc = 0;
+    for (int g = 1 + threadIdx.x; g < ng; g += blockDim.x)
+        acc += fabs((double)PG[(long)g * ng + g].x);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *scale = red[0] > 0 ? (float)((double)(ng - 1) / red[0]) : 0.f;
+}
+
+// One block per row g; threads over h in [g, ng).
+__global__ void __launch_bounds__(128) features_kernel(const float2 *PG, int ng, const int *gvec, float inv_gcut,
+                                                       const float *ratio, const float *scale, float *X)
+{
+    const int g = blockIdx.x;
+    const float s = *scale, rt = *ratio;
+    const int g1 = gvec[3 * g], g2 = gvec[3 * g + 1], g3 = gvec[3 * g + 2];
+    const float m2g = (float)(g1 * g1 + g2 * g2 + g3 * g3);
+    const float dg = PG[(long)g * ng + g].x;
+    for (int h = g + (int)threadIdx.x; h < ng; h += blockDim.x) {
+        const int h1 = gvec[3 * h], h2 = gvec[3 * h + 1], h3 = gvec[3 * h + 2];
+        const int d1 = g1 - h1, d2 = g2 - h2, d3 = g3 - h3;
+        const float2 p = PG[(long)g * ng + h];
+        float *x = X + tri_index(g, h, ng) * NF;
+        x[0] = m2g * inv_gcut;
+        x[1] = (float)(h1 * h1 + h2 * h2 + h3 * h3) * inv_gcut;
+        x[2] = (float)(d1 * d1 + d2 * d2 + d3 * d3) * (0.25f * inv_gcut);
+        x[3] = s * p.x;
+        x[4] = s * p.y;
+        x[5] = s * dg;
+        x[6] = s * PG[(long)h * ng + h].x;
+        x[7] = g == h ? 1.f : 0.f;
+        x[8] = rt;
+        x[9] = (g == 0 || h == 0) ? 1.f : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(128) targets_kernel(const float2 *lo, const float2 *hi, int ng, const float *scale,
+                                                      float *T)
+{
+    const int g = blockIdx.x;
+    const float s = *scale;
+    for (int h = g + (int)threadIdx.x; h < ng; h += blockDim.x) {
+        const long e = (long)g * ng + h;
+        float *t = T + tri_index(g, h, ng) * NOUT;
+        t[0] = s * (hi[e].x - lo[e].x);
+        t[1] = s * (hi[e].y - lo[e].y);
+    }
+}
+
+// P~(g,h) += (y0 + i y1)/s and P~(h,g) = its conjugate; diagonal: real part only; row and
+// column 0 untouched.
+__global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const float *Y, const float *scale)
+{
+    const int g = blockIdx.x;
+    if (g == 0)
+        return;
+    const float inv = 1.f / *scale;
+    for (int h = g + (int)threadIdx.x; h < ng; h += blockDim.x) {
+        const float *y = Y + tri_index(g, h, ng) * NOUT;
+        const float dr = y[0] * inv, di = y[1] * inv;
+        if (h == g) {
+            PG[(long)g * ng + g].x += dr;
+        } else {
+            float2 &a = PG[(long)g * ng + h];
+            float2 &b = PG[(long)h * ng + g];
+            a.x += dr;
+            a.y += di;
+            b.x += dr;
+            b.y -= di;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// SIMT GEMM: C(m, n) = sum_k A(m, k) B(n, k), 64 x 64 x 16 tiles, 256 threads, 4 x 4 outputs per
+// thread, FP32 accumulation.  A is FP32 (activations or deltas); B is FP16 (weights) or FP32.
+//   A_KC: A(m,k) = A[row(m) * lda + k]   else A(m,k) = A[k * lda + m]
+//   B_KC: B(n,k) = B[n * ldb + k]        else B(n,k) = B[row(k) * ldb + n]
+// row() is an optional gather of sample rows (a minibatch drawn from a larger set).
+
+enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_TANH = 2, EPI_DTANH = 3 };
+
+struct GemmArgs {
+    const float *A;
+    long lda;
+    const int *arow;  // A_KC only
+    const void *B;
+    long ldb;
+    const int *brow;  // !B_KC only
+    int M, N, K;
+    int ones_col;     // B(ones_col, k) = 1: the bias-gradient column
+    const float *bias;
+    const float *H;   // EPI_DTANH: C = acc * (1 - H^2)
+    long ldh;
+    float *C;
+    long ldc;
+    int kps;          // K range of one split (multiple of GT_K)
+    long split_stride;
+};
+
+__device__ __forceinline__ float ld_elem(const float *p) { return *p; }
+__device__ __forceinline__ float ld_elem(const __half *p) { return __half2float(*p); }
+
+template <bool A_KC, bool B_KC, typename TB, int EPI>
+__global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs a)
+{
+    __shared__ __align__(16) float As[GT_K][GT_M + 4];
+    __shared__ __align__(16) float Bs[GT_K][GT_N + 4];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.y * GT_M, n0 = blockIdx.x * GT_N;
+    const int kbeg = blockIdx.z * a.kps, kend = min(a.K, kbeg + a.kps);
+    const TB *B = static_cast<const TB *>(a.B);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[i][j] = 0.f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += GT_K) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = tid + e * 256;
+            const int mm = A_KC ? i / GT_K : i % GT_M, kk = A_KC ? i % GT_K : i / GT_M;
+            const int m = m0 + mm, k = k0 + kk;
+            float v = 0.f;
+            if (m < a.M && k < kend) {
+                if (A_KC)
+                    v = a.A[(long)(a.arow ? a.arow[m] : m) * a.lda + k];
+                else
+                    v = a.A[(long)k * a.lda + m];
+            }
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = tid + e * 256;
+            const int nn = B_KC ? i / GT_K : i % GT_N, kk = B_KC ? i % GT_K : i / GT_N;
+            const int n = n0 + nn, k = k0 + kk;
+            float v = 0.f;
+            if (n < a.N && k < kend) {
+                if (n == a.ones_col)
+                    v = 1.f;
+                else if (B_KC)
+                    v = ld_elem(B + (long)n * a.ldb + k);
+                else
+                    v = ld_elem(B + (long)(a.brow ? a.brow[k] : k) * a.ldb + n);
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GT_K; ++kk) {
+            const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    float *C = a.C + blockIdx.z * a.split_stride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= a.M)
+            continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= a.N)
+                continue;
+            float v = acc[i][j];
+            if (EPI == EPI_BIAS)
+                v += a.bias[n];
+            else if (EPI == EPI_BIAS_TANH)
+                v = tanhf(v + a.bias[n]);
+            else if (EPI == EPI_DTANH) {
+                const float h = a.H[(long)m * a.ldh + n];
+                v *= 1.f - h * h;
+            }
+            C[(long)m * a.ldc + n] = v;
+        }
+    }
+}
+
+// Sum of the split-K partials of a weight gradient; column n_w of the partials is the bias.
+__global__ void splitk_reduce_kernel(const float *part, int S, long stride, int M, int n_w, float *gW, float *gb)
+{
+    const long total = (long)M * (n_w + 1);
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z)
+            s += part[z * stride + e];
+        const int m = (int)(e / (n_w + 1)), n = (int)(e % (n_w + 1));
+        if (n < n_w)
+            gW[(long)m * n_w + n] = s;
+        else
+            gb[m] = s;
+    }
+}
+
+// D = (Y - T) / B; loss += (1 / (2B)) sum (Y - T)^2.
+__global__ void __launch_bounds__(256) mse_delta_kernel(const float *Y, const float *T, const int *trow, int B,
+                                                        float invB, float *D, float *loss)
+{
+    __shared__ float red[256];
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    if (b < B) {
+        const long r = trow ? trow[b] : b;
+        const float r0 = Y[2 * b] - T[2 * r], r1 = Y[2 * b + 1] - T[2 * r + 1];
+        D[2 * b] = r0 * invB;
+        D[2 * b + 1] = r1 * invB;
+        acc = r0 * r0 + r1 * r1;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss)
+        atomicAdd(loss, 0.5f * invB * red[0]);
+}
+
+__global__ void adam_kernel(float *theta, __half *theta16, const float *g, float *m, float *v, long P, float lr,
+                            float b1, float b2, float c1, float c2, float eps)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float t = theta[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        theta[i] = t;
+        theta16[i] = __float2half_rn(t);
+    }
+}
+
+__global__ void to_half_kernel(const float *x, __half *y, long n)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        y[i] = __float2half_rn(x[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Network state and host orchestration
+
+struct gw_mlp {
+    int device = 0, n_in = 0, hidden = 0, max_batch = 0, num_sms = 0;
+    long P = 0;
+    long off_w[4] = {}, off_b[4] = {};
+    cudaStream_t stream = nullptr;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __half *theta16 = nullptr;
+    float *H[3] = {}, *Da = nullptr, *Db = nullptr, *D4 = nullptr, *Y = nullptr, *part = nullptr;
+    long step = 0;
+    std::string last_error;
+};
+
+namespace {
+
+gw_status mfail(gw_mlp *m, gw_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (m)
+        m->last_error = buf;
+    return st;
+}
+
+gw_status mcuda(gw_mlp *m, cudaError_t e, const char *where)
+{
+    cudaGetLastError();
+    return mfail(m, e == cudaErrorMemoryAllocation ? GW_E_NOMEM : GW_E_CUDA, "%s: %s", where,
+                 cudaGetErrorString(e));
+}
+
+#define MLP_TRY(expr)               \
+    do {                            \
+        gw_status s_ = (expr);      \
+        if (s_ != GW_OK)            \
+            return s_;              \
+    } while (0)
+
+#define MLP_CUDA(call, where)            \
+    do {                                 \
+        cudaError_t e_ = (call);         \
+        if (e_ != cudaSuccess)           \
+            return mcuda(m, e_, where);  \
+    } while (0)
+
+long num_params(int n_in, int hidden)
+{
+    return (long)hidden * n_in + hidden + 2L * ((long)hidden * hidden + hidden) + (long)NOUT * hidden + NOUT;
+}
+
+template <bool A_KC, bool B_KC, typename TB, int EPI>
+cudaError_t gemm(cudaStream_t s, GemmArgs a, int splits)
+{
+    dim3 grid((a.N + GT_N - 1) / GT_N, (a.M + GT_M - 1) / GT_M, splits);
+    if (splits == 1)
+        a.kps = ((a.K + GT_K - 1) / GT_K) * GT_K;
+    mlp_gemm_kernel<A_KC, B_KC, TB, EPI><<<grid, 256, 0, s>>>(a);
+    gw::count_launches(1);
+    return cudaGetLastError();
+}
+
+// dW_l (out x in) and db_l from deltas D (batch x out) and the layer input Ain (batch x in):
+// dW = D^T Ain with K = batch split across blockIdx.z, then a deterministic reduction.
+cudaError_t weight_grad(gw_mlp *m, const float *D, int out, const float *Ain, long ld_in, const int *brow, int in,
+                        int batch, int layer)
+{
+    GemmArgs a{};
+    a.A = D;
+    a.lda = out;
+    a.B = Ain;
+    a.ldb = ld_in;
+    a.brow = brow;
+    a.M = out;
+    a.N = in + 1;
+    a.K = batch;
+    a.ones_col = in;
+    a.C = m->part;
+    a.ldc = in + 1;
+    a.split_stride = (long)out * (in + 1);
+    const int tiles = ((a.N + GT_N - 1) / GT_N) * ((a.M + GT_M - 1) / GT_M);
+    int S = std::max(1, std::min({(2 * m->num_sms + tiles - 1) / tiles, (batch + GT_K - 1) / GT_K, SPLIT_MAX}));
+    const int per = (batch + S - 1) / S;
+    a.kps = ((per + GT_K - 1) / GT_K) * GT_K;
+    S = (batch + a.kps - 1) / a.kps;
+    cudaError_t e = gemm<false, false, float, EPI_STORE>(m->stream, a, S);
+    if (e != cudaSuccess)
+        return e;
+    const long total = (long)out * (in + 1);
+    const int blocks = (int)std::min<long>((total + 255) / 256, 4L * m->num_sms);
+    splitk_reduce_kernel<<<blocks, 256, 0, m->stream>>>(m->part, S, a.split_stride, out, in,
+                                                         m->grad + m->off_w[layer], m->grad + m->off_b[layer]);
+    gw::count_launches(1);
+    return cudaGetLastError();
+}
+
+// Forward of `batch` rows of X (gathered by rows if given) into H[0..2] and Yout.
+cudaError_t forward_batch(gw_mlp *m, const float *X, const int *rows, int batch, float *Yout)
+{
+    const int Hd = m->hidden;
+    GemmArgs a{};
+    a.ones_col = -1;
+    a.A = X;
+    a.lda = m->n_in;
+    a.arow = rows;
+    a.B = m->theta16 + m->off_w[0];
+    a.ldb = m->n_in;
+    a.M = batch;
+    a.N = Hd;
+    a.K = m->n_in;
+    a.bias = m->theta + m->off_b[0];
+    a.C = m->H[0];
+    a.ldc = Hd;
+    cudaError_t e = gemm<true, true, __half, EPI_BIAS_TANH>(m->stream, a, 1);
+    for (int l = 1; l < 3 && e == cudaSuccess; ++l) {
+        a.A = m->H[l - 1];
+        a.lda = Hd;
+        a.arow = nullptr;
+        a.B = m->theta16 + m->off_w[l];
+        a.ldb = Hd;
+        a.K = Hd;
+        a.bias = m->theta + m->off_b[l];
+        a.C = m->H[l];
+        e = gemm<true, true, __half, EPI_BIAS_TANH>(m->stream, a, 1);
+    }
+    if (e != cudaSuccess)
+        return e;
+    a.A = m->H[2];
+    a.B = m->theta16 + m->off_w[3];
+    a.N = NOUT;
+    a.bias = m->theta + m->off_b[3];
+    a.C = Yout;
+    a.ldc = NOUT;
+    return gemm<true, true, __half, EPI_BIAS>(m->stream, a, 1);
+}
+
+// Loss and the gradient of every parameter into m->grad.
+cudaError_t loss_grad(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, float *loss)
+{
+    const int Hd = m->hidden;
+    cudaError_t e = forward_batch(m, X, rows, batch, m->Y);
+    if (e != cudaSuccess)
+        return e;
+    mse_delta_kernel<<<(batch + 255) / 256, 256, 0, m->stream>>>(m->Y, T, rows, batch, 1.f / batch, m->D4, loss);
+    gw::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    // output layer
+    if ((e = weight_grad(m, m->D4, NOUT, m->H[2], Hd, nullptr, Hd, batch, 3)) != cudaSuccess)
+        return e;
+    // hidden layers 3, 2, 1: dH_l = D_{l+1} W_{l+1}, D_l = dH_l (1 - H_l^2), then dW_l
+    const float *Dnext = m->D4;
+    int out_next = NOUT;
+    float *bufs[2] = {m->Da, m->Db};
+    for (int l = 2; l >= 0; --l) {
+        float *Dl = bufs[l & 1];
+        GemmArgs a{};
+        a.ones_col = -1;
+        a.A = Dnext;
+        a.lda = out_next;
+        a.B = m->theta16 + m->off_w[l + 1];
+        a.ldb = Hd;
+        a.M = batch;
+        a.N = Hd;
+        a.K = out_next;
+        a.H = m->H[l];
+        a.ldh = Hd;
+        a.C = Dl;
+        a.ldc = Hd;
+        if ((e = gemm<true, false, __half, EPI_DTANH>(m->stream, a, 1)) != cudaSuccess)
+            return e;
+        const float *Ain = l > 0 ? m->H[l - 1] : X;
+        const long ld_in = l > 0 ? Hd : m->n_in;
+        const int in = l > 0 ? Hd : m->n_in;
+        if ((e = weight_grad(m, Dl, Hd, Ain, ld_in, l > 0 ? nullptr : rows, in, batch, l)) != cudaSuccess)
+            return e;
+        Dnext = Dl;
+        out_next = Hd;
+    }
+    return cudaSuccess;
+}
+
+gw_status check_mlp(gw_mlp *m)
+{
+    if (!m)
+        return GW_E_INVALID;
+    const cudaError_t e = cudaSetDevice(m->device);
+    if (e != cudaSuccess)
+        return mcuda(m, e, "cudaSetDevice");
+    return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_mlp_num_params(int n_in, int hidden, size_t *n)
+{
+    if (!n || n_in < 1 || hidden < 1)
+        return GW_E_INVALID;
+    *n = (size_t)num_params(n_in, hidden);
+    return GW_OK;
+}
+
+gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_batch, void *stream)
+{
+    if (!out)
+        return GW_E_INVALID;
+    *out = nullptr;
+    if (n_in < 1 || n_in > 64 || hidden < 1 || hidden > 1024 || max_batch < 1 || max_batch > (1 << 22))
+        return GW_E_INVALID;
+    gw_mlp *m = new (std::nothrow) gw_mlp;
+    if (!m)
+        return GW_E_NOMEM;
+    m->device = device;
+    m->n_in = n_in;
+    m->hidden = hidden;
+    m->max_batch = max_batch;
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->P = num_params(n_in, hidden);
+    const long sizes[4][2] = {{hidden, n_in}, {hidden, hidden}, {hidden, hidden}, {NOUT, hidden}};
+    long o = 0;
+    for (int l = 0; l < 4; ++l) {
+        m->off_w[l] = o;
+        o += sizes[l][0] * sizes[l][1];
+        m->off_b[l] = o;
+        o += sizes[l][0];
+    }
+    auto cleanup = [&](gw_status st) {
+        gw_mlp_destroy(m);
+        return st;
+    };
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount,
+                                                                       device) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(GW_E_CUDA);
+    }
+    const size_t P = (size_t)m->P, act = (size_t)max_batch * hidden;
+    const size_t part = (size_t)SPLIT_MAX * hidden * (std::max(hidden, n_in) + 1);
+    float **fbufs[] = {&m->theta, &m->grad, &m->m, &m->v};
+    for (float **p : fbufs)
+        if (cudaMalloc(p, P * sizeof(float)) != cudaSuccess)
+            return cleanup(GW_E_NOMEM);
+    if (cudaMalloc(&m->theta16, P * sizeof(__half)) != cudaSuccess)
+        return cleanup(GW_E_NOMEM);
+    float **abufs[] = {&m->H[0], &m->H[1], &m->H[2], &m->Da, &m->Db};
+    for (float **p : abufs)
+        if (cudaMalloc(p, act * sizeof(float)) != cudaSuccess)
+            return cleanup(GW_E_NOMEM);
+    if (cudaMalloc(&m->D4, (size_t)max_batch * NOUT * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&m->Y, (size_t)max_batch * NOUT * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&m->part, part * sizeof(float)) != cudaSuccess)
+        return cleanup(GW_E_NOMEM);
+    if (cudaMemsetAsync(m->theta, 0, P * sizeof(float), m->stream) != cudaSuccess ||
+        cudaMemsetAsync(m->theta16, 0, P * sizeof(__half), m->stream) != cudaSuccess ||
+        cudaMemsetAsync(m->m, 0, P * sizeof(float), m->stream) != cudaSuccess ||
+        cudaMemsetAsync(m->v, 0, P * sizeof(float), m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(GW_E_CUDA);
+    }
+    *out = m;
+    return GW_OK;
+}
+
+gw_status gw_mlp_destroy(gw_mlp *m)
+{
+    if (!m)
+        return GW_OK;
+    cudaSetDevice(m->device);
+    if (m->stream)
+        cudaStreamSynchronize(m->stream);
+    else
+        cudaDeviceSynchronize();
+    void *ptrs[] = {m->theta, m->grad, m->m, m->v, m->theta16, m->H[0], m->H[1], m->H[2],
+                    m->Da,    m->Db,   m->D4, m->Y, m->part};
+    for (void *p : ptrs)
+        if (p)
+            cudaFree(p);
+    cudaGetLastError();
+    delete m;
+    return GW_OK;
+}
+
+gw_status gw_mlp_last_error(gw_mlp *m, char *buf, size_t len)
+{
+    if (!m || !buf || !len)
+        return GW_E_INVALID;
+    snprintf(buf, len, "%s", m->last_error.c_str());
+    return GW_OK;
+}
+
+gw_status gw_mlp_set_params(gw_mlp *m, const float *theta, int on_device)
+{
+    MLP_TRY(check_mlp(m));
+    if (!theta)
+        return mfail(m, GW_E_INVALID, "gw_mlp_set_params: null parameter pointer");
+    const size_t bytes = (size_t)m->P * sizeof(float);
+    MLP_CUDA(cudaMemcpyAsync(m->theta, theta, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             m->stream),
+             "gw_mlp_set_params copy");
+    MLP_CUDA(cudaMemsetAsync(m->m, 0, bytes, m->stream), "gw_mlp_set_params reset");
+    MLP_CUDA(cudaMemsetAsync(m->v, 0, bytes, m->stream), "gw_mlp_set_params reset");
+    to_half_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(m->theta, m->theta16,
+                                                                                                   m->P);
+    gw::count_launches(1);
+    MLP_CUDA(cudaGetLastError(), "gw_mlp_set_params convert");
+    m->step = 0;
+    if (!on_device)
+        MLP_CUDA(cudaStreamSynchronize(m->stream), "gw_mlp_set_params sync");
+    return GW_OK;
+}
+
+gw_status gw_mlp_get_params(gw_mlp *m, float *theta, int on_device)
+{
+    MLP_TRY(check_mlp(m));
+    if (!theta)
+        return mfail(m, GW_E_INVALID, "gw_mlp_get_params: null parameter pointer");
+    MLP_CUDA(cudaMemcpyAsync(theta, m->theta, (size_t)m->P * sizeof(float),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream),
+             "gw_mlp_get_params copy");
+    if (!on_device)
+        MLP_CUDA(cudaStreamSynchronize(m->stream), "gw_mlp_get_params sync");
+    return GW_OK;
+}
+
+gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y)
+{
+    MLP_TRY(check_mlp(m));
+    if (!X || !Y || n < 0)
+        return mfail(m, GW_E_INVALID, "gw_mlp_forward: null pointer or negative size");
+    for (long b0 = 0; b0 < n; b0 += m->max_batch) {
+        const int b = (int)std::min<long>(m->max_batch, n - b0);
+        MLP_CUDA(forward_batch(m, X + b0 * m->n_in, nullptr, b, Y + b0 * NOUT), "gw_mlp_forward");
+    }
+    return GW_OK;
+}
+
+gw_status gw_mlp_grad(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, float *grad, float *loss)
+{
+    MLP_TRY(check_mlp(m));
+    if (!X || !T || !grad || !loss || batch < 1 || batch > m->max_batch)
+        return mfail(m, GW_E_INVALID, "gw_mlp_grad: null pointer or batch outside [1, max_batch]");
+    MLP_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), m->stream), "gw_mlp_grad loss reset");
+    MLP_CUDA(loss_grad(m, X, T, rows, batch, loss), "gw_mlp_grad");
+    MLP_CUDA(cudaMemcpyAsync(grad, m->grad, (size_t)m->P * sizeof(float), cudaMemcpyDeviceToDevice, m->stream),
+             "gw_mlp_grad copy");
+    return GW_OK;
+}
+
+gw_status gw_mlp_train_step(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, double lr,
+                            double beta1, double beta2, double adam_eps, float *loss_accum)
+{
+    MLP_TRY(check_mlp(m));
+    if (!X || !T || batch < 1 || batch > m->max_batch)
+        return mfail(m, GW_E_INVALID, "gw_mlp_train_step: null pointer or batch outside [1, max_batch]");
+    if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(adam_eps >= 0))
+        return mfail(m, GW_E_INVALID, "gw_mlp_train_step: bad optimiser constants");
+    MLP_CUDA(loss_grad(m, X, T, rows, batch, loss_accum), "gw_mlp_train_step");
+    m->step += 1;
+    const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
+    const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
+    adam_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(
+        m->theta, m->theta16, m->grad, m->m, m->v, m->P, (float)lr, (float)beta1, (float)beta2, (float)c1, (float)c2,
+        (float)adam_eps);
+    gw::count_launches(1);
+    MLP_CUDA(cudaGetLastError(), "gw_mlp_train_step adam");
+    return GW_OK;
+}
+
+gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_all, float *ratio, void *stream)
+{
+    if (!E_eV || !ratio || nv < 1 || nc_keep < 1 || nc_all <= nc_keep)
+        return GW_E_INVALID;
+    weight_ratio_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(E_eV, nv, nc_keep, nc_all, ratio);
+    gw::count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
+}
+
+gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, float *X,
+                           float *scale, void *stream)
+{
+    if (!PG || !gvec || !ratio || !X || !scale || ng < 2 || gcut < 1)
+        return GW_E_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2 *P = static_cast<const float2 *>(PG);
+    entry_scale_kernel<<<1, 256, 0, s>>>(P, ng, scale);
+    features_kernel<<<ng, 128, 0, s>>>(P, ng, gvec, 1.f / (float)gcut, ratio, scale, X);
+    gw::count_launches(2);
+    return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
+}
+
+gw_status gw_corr_targets(const void *PG_lo, const void *PG_hi, int ng, const float *scale, float *T, void *stream)
+{
+    if (!PG_lo || !PG_hi || !scale || !T || ng < 1)
+        return GW_E_INVALID;
+    targets_kernel<<<ng, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const float2 *>(PG_lo), static_cast<const float2 *>(PG_hi), ng, scale, T);
+    gw::count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
+}
+
+gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, void *stream)
+{
+    if (!PG || !Y || !scale || ng < 1)
+        return GW_E_INVALID;
+    apply_kernel<<<ng, 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<float2 *>(PG), ng, Y, scale);
+    gw::count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
+}
+
+}  // extern "C"

@@ -53,6 +53,19 @@ SIGNATURES = {
     "gw_batch_autotune": (_i, [_vp, _c.c_char_p, _d]),
     "gw_batch_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
     "gw_batch_last_error": (_i, [_vp, _c.c_char_p, _sz]),
+    "gw_mlp_num_params": (_i, [_i, _i, _c.POINTER(_sz)]),
+    "gw_mlp_create": (_i, [_c.POINTER(_vp), _i, _i, _i, _i, _vp]),
+    "gw_mlp_destroy": (_i, [_vp]),
+    "gw_mlp_last_error": (_i, [_vp, _c.c_char_p, _sz]),
+    "gw_mlp_set_params": (_i, [_vp, _vp, _i]),
+    "gw_mlp_get_params": (_i, [_vp, _vp, _i]),
+    "gw_mlp_forward": (_i, [_vp, _vp, _c.c_long, _vp]),
+    "gw_mlp_grad": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp]),
+    "gw_mlp_train_step": (_i, [_vp, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp]),
+    "gw_corr_weight_ratio": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "gw_corr_features": (_i, [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]),
+    "gw_corr_targets": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "gw_corr_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -301,3 +314,133 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---------------------------------------------------------------------------------------------- learned correction
+N_FEATURES = 10
+
+
+def _stream_handle(device, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _status(st, where):
+    if st != GW_OK:
+        raise GwError(st, where)
+
+
+class Mlp:
+    """The correction network (gw_mlp_*): n_in -> hidden -> hidden -> hidden -> 2, tanh, FP16 weights."""
+
+    def __init__(self, n_in=N_FEATURES, hidden=256, max_batch=8192, device=0, stream=None):
+        import torch
+        self.device, self.n_in, self.hidden, self.max_batch = int(device), int(n_in), int(hidden), int(max_batch)
+        self.stream = _stream_handle(device, stream)
+        n = ctypes.c_size_t()
+        _status(lib().gw_mlp_num_params(self.n_in, self.hidden, ctypes.byref(n)), "gw_mlp_num_params")
+        self.P = n.value
+        self._h = ctypes.c_void_p()
+        _status(lib().gw_mlp_create(ctypes.byref(self._h), self.device, self.n_in, self.hidden, self.max_batch,
+                                    self.stream), "gw_mlp_create")
+        self._dev = torch.device(f"cuda:{self.device}")
+        self._loss = torch.zeros(1, dtype=torch.float32, device=self._dev)
+
+    def _check(self, st):
+        if st != GW_OK:
+            buf = ctypes.create_string_buffer(512)
+            lib().gw_mlp_last_error(self._h, buf, 512)
+            raise GwError(st, buf.value.decode())
+
+    def set_params(self, theta):
+        if _is_device(theta):
+            self._check(lib().gw_mlp_set_params(self._h, _ptr(theta), 1))
+        else:
+            th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+            if th.size != self.P:
+                raise ValueError(f"expected {self.P} parameters, got {th.size}")
+            self._check(lib().gw_mlp_set_params(self._h, th.ctypes.data, 0))
+
+    def get_params(self):
+        th = np.empty(self.P, dtype=np.float32)
+        self._check(lib().gw_mlp_get_params(self._h, th.ctypes.data, 0))
+        return th
+
+    def forward(self, X, Y=None):
+        import torch
+        n = X.shape[0]
+        if Y is None:
+            Y = torch.empty((n, 2), dtype=torch.float32, device=self._dev)
+        self._check(lib().gw_mlp_forward(self._h, _ptr(X), n, _ptr(Y)))
+        return Y
+
+    def grad(self, X, T, rows=None, batch=None):
+        """(dL/dtheta as a device tensor, L) for one batch."""
+        import torch
+        b = int(rows.shape[0]) if rows is not None else (int(batch) if batch else X.shape[0])
+        g = torch.empty(self.P, dtype=torch.float32, device=self._dev)
+        self._check(lib().gw_mlp_grad(self._h, _ptr(X), _ptr(T), _ptr(rows), b, _ptr(g), _ptr(self._loss)))
+        torch.cuda.synchronize(self._dev)
+        return g, float(self._loss.item())
+
+    def train_step(self, X, T, rows, lr, beta1=0.9, beta2=0.999, eps=1e-8, loss_accum=None):
+        self._check(lib().gw_mlp_train_step(self._h, _ptr(X), _ptr(T), _ptr(rows), int(rows.shape[0]), float(lr),
+                                            float(beta1), float(beta2), float(eps), _ptr(loss_accum)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gw_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def corr_weight_ratio(E_eV, nv, nc_keep, device=0, stream=None):
+    """Device float: weight of the omitted pairs relative to the kept ones (gw_corr_weight_ratio)."""
+    import torch
+    dev = torch.device(f"cuda:{device}")
+    E = torch.as_tensor(np.asarray(E_eV, dtype=np.float64)).to(dev)
+    out = torch.empty(1, dtype=torch.float32, device=dev)
+    _status(lib().gw_corr_weight_ratio(_ptr(E), int(nv), int(nc_keep), E.shape[0] - int(nv), _ptr(out),
+                                       _stream_handle(device, stream)), "gw_corr_weight_ratio")
+    return out
+
+
+def corr_features(PG, gvec, gcut, ratio, stream=None):
+    """(X [ng(ng+1)/2][10], scale) for a truncated P~ (complex64 ng x ng device tensor)."""
+    import torch
+    dev = PG.device
+    ng = PG.shape[0]
+    g = torch.as_tensor(np.ascontiguousarray(np.asarray(gvec, dtype=np.int32))).to(dev)
+    X = torch.empty((ng * (ng + 1) // 2, N_FEATURES), dtype=torch.float32, device=dev)
+    scale = torch.empty(1, dtype=torch.float32, device=dev)
+    _status(lib().gw_corr_features(_ptr(PG), ng, _ptr(g), int(gcut), _ptr(ratio), _ptr(X), _ptr(scale),
+                                   _stream_handle(dev.index, stream)), "gw_corr_features")
+    return X, scale
+
+
+def corr_targets(PG_keep, PG_all, scale, stream=None):
+    import torch
+    ng = PG_keep.shape[0]
+    T = torch.empty((ng * (ng + 1) // 2, 2), dtype=torch.float32, device=PG_keep.device)
+    _status(lib().gw_corr_targets(_ptr(PG_keep), _ptr(PG_all), ng, _ptr(scale), _ptr(T),
+                                  _stream_handle(PG_keep.device.index, stream)), "gw_corr_targets")
+    return T
+
+
+def corr_apply(PG, Y, scale, stream=None):
+    """In place: PG += the predicted correction (gw_corr_apply)."""
+    _status(lib().gw_corr_apply(_ptr(PG), PG.shape[0], _ptr(Y), _ptr(scale), _stream_handle(PG.device.index, stream)),
+            "gw_corr_apply")

@@ -1,0 +1,98 @@
+"""Learned truncation correction of P~(G,G'): training data from the plain method and the
+training loop, driving the library's kernels (gw_corr_*, gw_mlp_*).
+
+The arithmetic runs in the library.  This module calls the C ABI in order, draws the minibatch
+order, and sets the learning-rate schedule:
+
+1. For every seeded system, run the plain method twice: P~ with the nc_keep lowest unoccupied
+   states, and P~ with all of them.  The sum over unoccupied states c is the one in
+   Eq. (Pstatic).
+2. Compute the per-entry features of the truncated P~ and the targets s (P~_all - P~_keep)
+   (gw_corr_features, gw_corr_targets).
+3. Run Adam on minibatches drawn without replacement from all systems' entries
+   (gw_mlp_train_step), with a cosine learning-rate decay.
+4. Inference: features of a new truncated P~, the forward pass, then add the prediction into P~
+   (gw_corr_apply).  eps and eps^-1 then follow as for any P~.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import gw
+
+
+def truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3"):
+    """(P~_keep, P~_all, gvec) of one system.  psi: [nv + nc_all][N_r] device tensor."""
+    E = np.asarray(E_eV, dtype=np.float64)
+    ctx.load_states(psi[: nv + nc_keep], E[: nv + nc_keep], dims, nv)
+    ctx.build_P(precision)
+    gvec = ctx.P_to_G(gcut)
+    PG_keep = ctx.view("PG").clone()
+    ctx.load_states(psi, E, dims, nv)
+    ctx.build_P(precision)
+    ctx.P_to_G(gcut)
+    PG_all = ctx.view("PG").clone()
+    return PG_keep, PG_all, gvec
+
+
+def system_samples(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3"):
+    """Features, targets and the pieces needed to judge a prediction, for one system."""
+    PG_keep, PG_all, gvec = truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision)
+    ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
+    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
+    T = gw.corr_targets(PG_keep, PG_all, scale)
+    return {"X": X, "T": T, "scale": scale, "ratio": ratio, "PG_keep": PG_keep, "PG_all": PG_all, "gvec": gvec}
+
+
+def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp16x3"):
+    """Concatenated (X, T) over the seeded systems; make_states(seed) -> (psi on device, E_eV)."""
+    import torch
+
+    Xs, Ts = [], []
+    for s in seeds:
+        psi, E = make_states(s)
+        d = system_samples(ctx, psi, E, nv, nc_keep, dims, gcut, precision)
+        Xs.append(d["X"])
+        Ts.append(d["T"])
+        del psi, d
+    return torch.cat(Xs), torch.cat(Ts)
+
+
+def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Adam over `epochs` passes of minibatches without replacement (the last ragged minibatch of
+    each pass is dropped).  Learning rate: cosine decay from lr to lr_final.  Returns the mean
+    loss of each pass."""
+    import torch
+
+    dev = X.device
+    S = X.shape[0]
+    steps = S // batch
+    if steps < 1:
+        raise ValueError("fewer samples than one minibatch")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    acc = torch.zeros(1, dtype=torch.float32, device=dev)
+    total, t, losses = epochs * steps, 0, []
+    for _ in range(epochs):
+        perm = torch.randperm(S, generator=gen, device=dev).to(torch.int32)
+        acc.zero_()
+        for i in range(steps):
+            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * t / total))
+            mlp.train_step(X, T, perm[i * batch:(i + 1) * batch], lr_t, beta1, beta2, eps, loss_accum=acc)
+            t += 1
+        losses.append(float(acc.item()) / steps)
+    return losses
+
+
+def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, out=None):
+    """Learned form: P~_keep plus the predicted correction (in `out`, or a new tensor)."""
+    ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
+    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
+    Y = mlp.forward(X)
+    P = PG_keep.clone() if out is None else out
+    if out is not None and out.data_ptr() != PG_keep.data_ptr():
+        P.copy_(PG_keep)
+    gw.corr_apply(P, Y, scale)
+    return P

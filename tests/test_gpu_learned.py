@@ -1,0 +1,192 @@
+"""Learned truncation correction on the GPU.
+
+* The network's gradient, loss and forward pass (the library's kernels, FP16 weights, FP32
+  accumulation) against the FP64 oracle network evaluated with the same FP16-rounded weights.
+* One Adam step against the oracle's Adam.
+* The per-entry features, targets and the correction rule against the oracle, on a seeded
+  synthetic Hermitian P~.
+* End to end on the 24^3 workload: 64 systems with N_v = 32 and N_c = 200 of 2000 kept, trained
+  on the GPU and judged on held-out systems against the full N_c = 2000 sum of the plain method.
+  It must gain over truncation alone and come close to the analytic closure estimate; the full
+  sum is itself checked against the FP64 oracle at sampled entries.
+"""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from oracle import mlp as M
+from paper_1810_07772_gb300 import gw, inputs, learned
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N_IN, HID = M.N_FEATURES, 256
+
+
+def _blocks(vec):
+    """Split a flat parameter vector into its 8 blocks (W1, b1, ..., W4, b4)."""
+    out, o = [], 0
+    for r, c in [(HID, N_IN), (HID, HID), (HID, HID), (2, HID)]:
+        out.append(vec[o:o + r * c])
+        o += r * c
+        out.append(vec[o:o + r])
+        o += r
+    return out
+
+
+def _theta(seed):
+    th = inputs.mlp_init(N_IN, HID, seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 1)
+    for blk in _blocks(th)[1::2]:        # non-zero biases so their paths are exercised
+        blk[:] = 0.1 * rng.standard_normal(blk.size)
+    return th.astype(np.float32)
+
+
+def test_gradient_and_forward_match_oracle():
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(11)
+    S, B = 1000, 300                      # ragged: neither is a multiple of the 64-row tile
+    X = rng.standard_normal((S, N_IN)).astype(np.float32)
+    T = rng.standard_normal((S, 2)).astype(np.float32)
+    rows = rng.permutation(S)[:B].astype(np.int32)
+    th = _theta(5)
+    params = M.unpack(M.to_fp16_weights(th.astype(np.float64), N_IN, HID), N_IN, HID)
+    loss_ref, grads = M.loss_and_grad(params, X[rows].astype(np.float64), T[rows].astype(np.float64))
+    g_ref = M.flatten(grads)
+    y_ref, _ = M.forward(params, X.astype(np.float64))
+    with gw.Mlp(N_IN, HID, max_batch=384, device=0) as net:
+        net.set_params(th)
+        assert np.array_equal(net.get_params(), th)
+        g, loss = net.grad(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev))
+        Y = net.forward(torch.from_numpy(X).to(dev)).cpu().numpy()   # 1000 rows in chunks of 384
+    g = g.cpu().numpy().astype(np.float64)
+    # FP32 accumulation over at most 300 terms in each of the 8 GEMM stages: about sqrt(300) u_32
+    # = 1e-6 relative per stage, compounded over the stages.
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    for gb, rb in zip(_blocks(g), _blocks(g_ref)):
+        assert np.linalg.norm(gb - rb) <= 2e-5 * np.linalg.norm(rb)
+    assert np.linalg.norm(Y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+
+
+def test_adam_step_matches_oracle():
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((512, N_IN)).astype(np.float32)
+    T = rng.standard_normal((512, 2)).astype(np.float32)
+    th = _theta(6)
+    params = M.unpack(M.to_fp16_weights(th.astype(np.float64), N_IN, HID), N_IN, HID)
+    _, grads = M.loss_and_grad(params, X.astype(np.float64), T.astype(np.float64))
+    g = M.flatten(grads)
+    lr = 1e-3
+    want, _, _ = M.adam_step(th.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr)
+    rows = torch.arange(512, dtype=torch.int32, device=dev)
+    with gw.Mlp(N_IN, HID, max_batch=512, device=0) as net:
+        net.set_params(th)
+        net.train_step(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), rows, lr)
+        got = net.get_params().astype(np.float64)
+    # The first step moves every parameter by ~lr sign(g); where |g| is within rounding of 0 the
+    # sign is not fixed by FP32 arithmetic, so those entries are excluded.
+    firm = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert firm.mean() > 0.9
+    assert np.max(np.abs(got - want)[firm]) <= 1e-6
+
+
+def _synthetic_PG(ng, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((ng, 3 * ng)) + 1j * rng.standard_normal((ng, 3 * ng))
+    P = -(A @ A.conj().T) / (3 * ng)
+    P = 0.5 * (P + P.conj().T)
+    P[np.diag_indices(ng)] = P.diagonal().real
+    P[0, :] = 0
+    P[:, 0] = 0
+    return P.astype(np.complex64)
+
+
+def test_features_targets_apply_match_oracle():
+    dev = torch.device("cuda:0")
+    dims, gcut = (12, 12, 12), 8
+    g = O.sphere(dims, gcut)
+    ng = len(g)                           # 93: one full 64-row block and a ragged one
+    lo, hi = _synthetic_PG(ng, 21), _synthetic_PG(ng, 22)
+    hi = lo + 0.3 * hi
+    psi, E = inputs.make_states(12, 4, 40, 3)
+    nv, keep = 4, 10
+    w_om, w_in = M.omitted_weights(E, nv, keep)
+    X_ref, s_ref = M.features(lo.astype(np.complex128), g, gcut, w_om, w_in)
+    T_ref = M.targets(lo.astype(np.complex128), hi.astype(np.complex128))
+    Y = np.random.default_rng(23).standard_normal((ng * (ng + 1) // 2, 2)).astype(np.float32)
+    P_ref = M.apply_correction(lo.astype(np.complex128), Y.astype(np.float64), s_ref)
+
+    lo_d, hi_d = torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev)
+    ratio = gw.corr_weight_ratio(E, nv, keep)
+    X, scale = gw.corr_features(lo_d, g, gcut, ratio)
+    T = gw.corr_targets(lo_d, hi_d, scale)
+    P = lo_d.clone()
+    gw.corr_apply(P, torch.from_numpy(Y).to(dev), scale)
+    X, T, P = X.cpu().numpy(), T.cpu().numpy(), P.cpu().numpy()
+    assert abs(float(ratio.item()) - w_om / w_in) <= 1e-7 * (w_om / w_in)
+    assert abs(float(scale.item()) - s_ref) <= 1e-6 * s_ref
+    assert X.shape == X_ref.shape and T.shape == T_ref.shape
+    for j in range(M.N_FEATURES):
+        assert np.allclose(X[:, j], X_ref[:, j], rtol=2e-6, atol=2e-7 * max(1.0, np.abs(X_ref[:, j]).max())), j
+    assert np.array_equal(X[:, [7, 9]], X_ref[:, [7, 9]])
+    assert np.allclose(T, T_ref, rtol=0, atol=2e-6 * np.abs(T_ref).max())
+    assert np.allclose(P, P_ref, rtol=0, atol=2e-6 * np.abs(P_ref).max())
+    assert np.array_equal(P[0], lo[0]) and np.array_equal(P[:, 0], lo[:, 0])
+    assert np.array_equal(P, P.conj().T)
+
+
+def _rel(A, B):
+    return float(torch.linalg.norm(A - B) / torch.linalg.norm(B))
+
+
+@pytest.mark.slow
+def test_learned_correction_gain_24cubed():
+    """24^3, N_v = 32, N_c = 200 kept of 2000; 64 training systems, 8 held-out systems."""
+    dev = torch.device("cuda:0")
+    n, nv, keep, nc_all, gcut = 24, 32, 200, 2000, 29
+    dims = (n,) * 3
+    nr = n ** 3
+
+    def states(seed):
+        return inputs.make_states_device(n, nv, nc_all, seed, dev)
+
+    with gw.Context(0) as ctx:
+        X, T = learned.training_set(ctx, states, range(1000, 1064), nv, keep, dims, gcut)
+        assert X.shape[0] == 64 * 691 * 692 // 2
+        with gw.Mlp(N_IN, HID, max_batch=8192, device=0) as net:
+            net.set_params(inputs.mlp_init(N_IN, HID, 7))
+            losses = learned.train(net, X, T, epochs=3, batch=8192, lr=1e-3, seed=0)
+            del X, T
+            e_trunc, e_mlp, e_clos = [], [], []
+            for seed in range(2000, 2008):
+                psi, E = states(seed)
+                d = learned.system_samples(ctx, psi, E, nv, keep, dims, gcut)
+                P_ml = learned.correct(net, d["PG_keep"], d["gvec"], gcut, E, nv, keep)
+                w_om, _ = M.omitted_weights(E, nv, keep)
+                clos = d["PG_keep"].clone()
+                idx = torch.arange(1, clos.shape[0], device=dev)
+                clos[idx, idx] -= w_om / (nr - (nv + keep))
+                e_trunc.append(_rel(d["PG_keep"], d["PG_all"]))
+                e_mlp.append(_rel(P_ml, d["PG_all"]))
+                e_clos.append(_rel(clos, d["PG_all"]))
+                if seed == 2000:
+                    # the learned form goes on to eps^-1 like any P~
+                    ctx.view("PG").copy_(P_ml)
+                    ng = P_ml.shape[0]
+                    eps = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+                    inv = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+                    ctx.eps_inv("cholesky", eps_out=eps, epsinv_out=inv)
+                    I = torch.eye(ng, dtype=torch.complex128, device=dev)
+                    assert float((inv @ eps - I).abs().max()) <= 1e-12
+                    # the judge, P~ of the full sum, against the FP64 oracle at sampled entries
+                    sel = np.array([0, 1, 7, 100, 350, 690])
+                    ref = O.P_gspace_entries(psi.cpu().numpy().astype(np.complex128), E, nv, dims, d["gvec"][sel])
+                    sub = d["PG_all"][sel][:, sel].cpu().numpy()
+                    assert np.linalg.norm(sub - ref) / np.linalg.norm(ref) <= 1e-6
+    e_trunc, e_mlp, e_clos = map(np.mean, (e_trunc, e_mlp, e_clos))
+    print(f"losses {losses}  rel. error of P~: truncated {e_trunc:.4f}  learned {e_mlp:.4f}  closure {e_clos:.4f}")
+    assert losses[-1] < losses[0]
+    assert e_mlp < 0.3 * e_trunc
+    assert e_mlp < 1.25 * e_clos

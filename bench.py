@@ -36,7 +36,7 @@ METRIC = "P-build TFLOP/s (4kN_r(N_r+1) per step, states resident -> eps^-1)"
 PRECISION = "fp16x3"
 WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
              "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41),
-             "split": inputs.SPLIT, "batch": None}
+             "split": inputs.SPLIT, "batch": None, "learned": None}
 
 
 def parse_args(argv=None):
@@ -48,6 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default=PRECISION)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the same-GPU precision comparison")
+    ap.add_argument("--epochs", type=int, default=6, help="training passes of the learned workload")
+    ap.add_argument("--diag-repeat", type=int, default=32, help="diagonal entries' multiplicity in training")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain",
                     help="plain = the 24^3 configuration the metric is quoted on; the others are smaller "
                          "configurations for profiling")
@@ -177,7 +179,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import gw_oracle as O
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS[args.workload] or inputs.PLAIN   # multi-system workloads: the oracle on the 24^3 system
     psi, E = inputs.make_workload_states(w)
     rows = max(1, O.clib_threads())      # one row per host thread: every core busy, bounded step
     for _ in range(args.warmup):
@@ -454,12 +456,155 @@ def run_batch(args):
     return 0
 
 
+# flops of one training sample of the 10 -> 256 x 3 -> 2 network: forward, the three hidden-layer
+# deltas and the four weight gradients (with their bias columns)
+def mlp_sample_flop(n_in=10, h=256, n_out=2):
+    fwd = 2 * (n_in * h + 2 * h * h + h * n_out)
+    dh = 2 * (n_out * h + 2 * h * h)
+    dw = 2 * (h * (n_in + 1) + 2 * h * (h + 1) + n_out * (h + 1))
+    return fwd, fwd + dh + dw
+
+
+def run_learned(args):
+    """Learned truncation correction on the 24^3 workload: N_v = 32, the sum over unoccupied states
+    cut at N_c = 200 of 2000, a 10 -> 256 x 3 -> 2 network trained on 64 seeded systems.  Times
+    the learned form to eps^-1 against the plain full-N_c method on the same GPU, and reports the
+    error of both truncated and learned P~ against the full sum on 8 held-out systems."""
+    import torch
+    from paper_1810_07772_gb300 import gw, learned
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n, nv, keep, nc_all, gcut = 24, 32, 200, 2000, 29
+    dims, nr = (n,) * 3, n ** 3
+    stream = torch.cuda.current_stream(dev)
+    ctx = gw.Context(0, stream)
+
+    def states(seed):
+        return inputs.make_states_device(n, nv, nc_all, seed, dev)
+
+    t0 = time.perf_counter()
+    X, T = learned.training_set(ctx, states, range(1000, 1064), nv, keep, dims, gcut, args.precision)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    S = X.shape[0]
+    net = gw.Mlp(10, 256, max_batch=8192, device=0, stream=stream)
+    net.set_params(inputs.mlp_init(10, 256, 7))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record(stream)
+    losses = learned.train(net, X, T, epochs=args.epochs, batch=8192, lr=1e-3, seed=0, diag_repeat=args.diag_repeat)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    fwd_flop, train_flop = mlp_sample_flop()
+    n_train = args.epochs * ((S + (args.diag_repeat - 1) * 64 * 691) // 8192) * 8192
+    # inference alone on one system's entries (the dominant kernel of the correction)
+    Xs = X[: 691 * 692 // 2].contiguous()
+    Y = net.forward(Xs)
+    ev[2].record(stream)
+    for _ in range(10):
+        net.forward(Xs, Y)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev[2].elapsed_time(ev[3]) / 10
+    del X, T
+
+    # held-out systems: errors of the truncated and learned P~ against the full sum
+    e_tr, e_ml, e_cl, e_inv, e_inv_tr = [], [], [], [], []
+    for seed in range(2000, 2008):
+        psi, E = states(seed)
+        d = learned.system_samples(ctx, psi, E, nv, keep, dims, gcut, args.precision)
+        P_ml = learned.correct(net, d["PG_keep"], d["gvec"], gcut, E, nv, keep)
+        w_om = float(np.sum(2.0 * 27.211386245988 / (E[None, nv + keep:] - E[:nv, None])))   # Hartree
+        clos = d["PG_keep"].clone()
+        ix = torch.arange(1, clos.shape[0], device=dev)
+        clos[ix, ix] -= w_om / (nr - nv - keep)
+        rel = lambda A, B: float(torch.linalg.norm(A - B) / torch.linalg.norm(B))  # noqa: E731
+        e_tr.append(rel(d["PG_keep"], d["PG_all"]))
+        e_ml.append(rel(P_ml, d["PG_all"]))
+        e_cl.append(rel(clos, d["PG_all"]))
+        if seed == 2000:
+            ng = P_ml.shape[0]
+            invs = []
+            for P in (d["PG_all"], P_ml, d["PG_keep"]):
+                ctx.view("PG").copy_(P)
+                inv = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+                ctx.eps_inv("cholesky", epsinv_out=inv)
+                invs.append(inv)
+            e_inv.append(rel(invs[1], invs[0]))
+            e_inv_tr.append(rel(invs[2], invs[0]))
+            held = (psi, E)
+
+    # time to eps^-1: learned form against the plain full sum, on one held-out system
+    psi, E = held
+
+    def step_learned():
+        ctx.load_states(psi[: nv + keep], E[: nv + keep], dims, nv)
+        ctx.build_P(args.precision)
+        g = ctx.P_to_G(gcut)
+        PG = ctx.view("PG")
+        learned.correct(net, PG, g, gcut, E, nv, keep, out=PG)
+        ctx.eps_inv("cholesky")
+
+    def step_full():
+        ctx.load_states(psi, E, dims, nv)
+        ctx.build_P(args.precision)
+        ctx.P_to_G(gcut)
+        ctx.eps_inv("cholesky")
+
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, fn in (("learned", step_learned), ("full", step_full)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            l0 = ctx.stats()["kernel_launches"]
+            ev[4].record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev[5].record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"ms": ev[4].elapsed_time(ev[5]) / args.steps,
+                         "launches": int(ctx.stats()["kernel_launches"] - l0)}
+    ctx.close()
+    net.close()
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
+    line = {"metric": "seconds per eps^-1, learned truncation correction", "value": res["learned"]["ms"] / 1e3,
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["learned"]["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16-weights/f32",
+            "data": "synthetic",
+            "config": {"workload": f"grid24_nv32_nc{keep}_of_{nc_all}_learned", "grid": [n] * 3, "nv": nv,
+                       "nc_keep": keep, "nc_all": nc_all, "gcut": gcut, "N_g": 691,
+                       "network": "10 -> 256 -> 256 -> 256 -> 2, tanh, FP16 weights, FP32 accumulation",
+                       "train_systems": 64, "held_out_systems": 8, "precision_of_P": args.precision,
+                       "diag_repeat": args.diag_repeat},
+            "plain_full_nc": {"s_per_eps_inv": res["full"]["ms"] / 1e3, "gpu_launches": res["full"]["launches"]},
+            "speedup_vs_full": res["full"]["ms"] / res["learned"]["ms"],
+            "err_vs_full_sum": {"P_G_rel_truncated": float(np.mean(e_tr)), "P_G_rel_learned": float(np.mean(e_ml)),
+                                "P_G_rel_closure_estimate": float(np.mean(e_cl)),
+                                "epsinv_rel_learned": float(np.mean(e_inv)),
+                                "epsinv_rel_truncated": float(np.mean(e_inv_tr))},
+            "training": {"samples": S, "epochs": args.epochs, "losses": losses, "ms": train_ms,
+                         "samples_per_s": n_train / (train_ms * 1e-3),
+                         "tflops": n_train * train_flop / (train_ms * 1e-3) / 1e12,
+                         "data_generation_s": gen_s},
+            "roofline": {"bound": "alu", "kernel": "mlp_gemm_kernel (forward, SIMT FP32 FMA)",
+                         "achieved": Xs.shape[0] * fwd_flop / (fwd_ms * 1e-3) / 1e12, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": Xs.shape[0] * fwd_flop / (fwd_ms * 1e-3) / 1e12 / alu_peak,
+                         "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                         "forward_ms_per_system": fwd_ms},
+            "gpu_launches": res["learned"]["launches"], "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_gw(args)
 
 

@@ -60,14 +60,23 @@ def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp
     return torch.cat(Xs), torch.cat(Ts)
 
 
-def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1=0.9, beta2=0.999, eps=1e-8):
+def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1=0.9, beta2=0.999, eps=1e-8,
+          diag_repeat=1):
     """Adam over `epochs` passes of minibatches without replacement (the last ragged minibatch of
     each pass is dropped).  Learning rate: cosine decay from lr to lr_final.  Returns the mean
-    loss of each pass."""
+    loss of each pass.
+
+    diag_repeat > 1 puts every diagonal entry (feature 7 set) that many times into the pool a
+    pass draws from.  Diagonal entries carry most of the correction's norm but are 1 in ng(ng+1)/2
+    of the entries, so without this their fit is left to few, noisy updates."""
     import torch
 
     dev = X.device
-    S = X.shape[0]
+    pool = torch.arange(X.shape[0], dtype=torch.int64, device=dev)
+    if diag_repeat > 1:
+        diag = torch.nonzero(X[:, 7] == 1).flatten()
+        pool = torch.cat([pool, diag.repeat(diag_repeat - 1)])
+    S = pool.shape[0]
     steps = S // batch
     if steps < 1:
         raise ValueError("fewer samples than one minibatch")
@@ -76,7 +85,7 @@ def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1
     acc = torch.zeros(1, dtype=torch.float32, device=dev)
     total, t, losses = epochs * steps, 0, []
     for _ in range(epochs):
-        perm = torch.randperm(S, generator=gen, device=dev).to(torch.int32)
+        perm = pool[torch.randperm(S, generator=gen, device=dev)].to(torch.int32)
         acc.zero_()
         for i in range(steps):
             lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * t / total))

@@ -157,7 +157,7 @@ def test_learned_correction_gain_24cubed():
         assert X.shape[0] == 64 * 691 * 692 // 2
         with gw.Mlp(N_IN, HID, max_batch=8192, device=0) as net:
             net.set_params(inputs.mlp_init(N_IN, HID, 7))
-            losses = learned.train(net, X, T, epochs=3, batch=8192, lr=1e-3, seed=0)
+            losses = learned.train(net, X, T, epochs=6, batch=8192, lr=1e-3, seed=0, diag_repeat=32)
             del X, T
             e_trunc, e_mlp, e_clos = [], [], []
             for seed in range(2000, 2008):
@@ -189,4 +189,4 @@ def test_learned_correction_gain_24cubed():
     print(f"losses {losses}  rel. error of P~: truncated {e_trunc:.4f}  learned {e_mlp:.4f}  closure {e_clos:.4f}")
     assert losses[-1] < losses[0]
     assert e_mlp < 0.3 * e_trunc
-    assert e_mlp < 1.25 * e_clos
+    assert e_mlp < 1.05 * e_clos

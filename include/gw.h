@@ -217,9 +217,10 @@ GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
  *                   gw_batch_set_window).  Synchronises the stream and returns the first error
  *                   of any instance (message: gw_batch_last_error).
  * gw_batch_autotune picks the window / flush lengths of the rank-k update by timing the candidates
- *                   whose measured FP16-split error is within target_error (e.g. 1e-6); the choice is
- *                   appended to cache_path (JSON lines keyed by the instance shapes; NULL = no cache)
- *                   and reused from it when the same batch is tuned again.
+ *                   whose measured FP16-split error x 1.25 is within target_error (e.g. 1e-6); the
+ *                   choice is appended to cache_path (JSON lines keyed by the instance shapes and the
+ *                   target; NULL = no cache) and reused from it when the same batch is tuned again
+ *                   for the same target.
  * gw_batch_stats    stats4[0] = last pass's rank-k update time in ms, [1] = window, [2] = flush,
  *                   [3] = number of tiles.
  */

@@ -1235,7 +1235,10 @@ gw_status gw_batch_autotune(gw_batch *b, const char *cache_path, double target_e
         return GW_E_INVALID;
     gw_batch &bb = *b;
     cudaSetDevice(bb.device);
-    const std::string key = batch_key(bb);
+    // the choice depends on the error target as well as on the shapes
+    char tgt[32];
+    std::snprintf(tgt, sizeof tgt, "|target%.3g", target_error);
+    const std::string key = batch_key(bb) + tgt;
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "r")) {
             char line[8192];

@@ -33,23 +33,27 @@ __global__ void eps_build_kernel(const float2 *__restrict__ PG, const double *__
 }
 
 // ---------------------------------------------------------------------------- zgemm
-constexpr int ZT = 32;   // output tile
 constexpr int ZK = 16;   // k chunk
 
 // C = alpha op(A) op(B) + beta C with optional triangular structure (flags, see gw_internal.cuh):
 // known-zero k ranges of a triangular operand are skipped, and with ZG_C_LOWER only tiles that
 // reach the diagonal or below are computed (ZG_C_MIRROR also stores the conjugate transpose).
-__global__ void __launch_bounds__(256)
+// ZT x ZT output tiles, (ZT/2)^2 threads with 2 x 2 outputs each.  The FP64 pipe, not shared
+// memory, bounds this kernel; ZT = 16 gives four times as many CTAs for the small and triangular
+// products of the inverse, whose few 32-wide tiles left most SMs idle.
+template <int ZT>
+__global__ void __launch_bounds__((ZT / 2) * (ZT / 2))
     zgemm_kernel(int M, int N, int K, double2 alpha, const double2 *__restrict__ A, int lda, int opA,
                  const double2 *__restrict__ B, int ldb, int opB, double2 beta, double2 *__restrict__ C, int ldc,
                  int flags)
 {
+    constexpr int H = ZT / 2, NT = H * H;
     __shared__ double2 As[ZK][ZT + 1];
     __shared__ double2 Bs[ZK][ZT + 1];
     const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
     if ((flags & ZG_C_LOWER) && j0 > i0 + ZT - 1)
         return;  // tile strictly above the diagonal
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x % H, ty = threadIdx.x / H;
     double2 acc[2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(256)
     kbeg = (kbeg / ZK) * ZK;
     const int kend = (flags & ZG_A_LOWER) ? min(K, i0 + ZT) : K;  // op(A)[i][k] = 0 for k > i
     for (int k0 = kbeg; k0 < kend; k0 += ZK) {
-        for (int t = threadIdx.x; t < ZK * ZT; t += 256) {
+        for (int t = threadIdx.x; t < ZK * ZT; t += NT) {
             int i, kk;
             if (opA == 0) {
                 i = t / ZK;
@@ -95,8 +99,8 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < ZK; ++kk) {
-            const double2 a0 = As[kk][ty], a1 = As[kk][ty + 16];
-            const double2 b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            const double2 a0 = As[kk][ty], a1 = As[kk][ty + H];
+            const double2 b0 = Bs[kk][tx], b1 = Bs[kk][tx + H];
             acc[0][0].x = fma(a0.x, b0.x, fma(-a0.y, b0.y, acc[0][0].x));
             acc[0][0].y = fma(a0.x, b0.y, fma(a0.y, b0.x, acc[0][0].y));
             acc[0][1].x = fma(a0.x, b1.x, fma(-a0.y, b1.y, acc[0][1].x));
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(256)
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+            const int gi = i0 + ty + H * a, gj = j0 + tx + H * b;
             if (gi < M && gj < N && (!(flags & ZG_C_LOWER) || gj <= gi)) {
                 double2 v = cmul(alpha, acc[a][b]);
                 if (use_beta) {
@@ -146,89 +150,81 @@ __device__ __forceinline__ double rsqrt_newton(double d)
 }
 
 // Factor the n x n (n <= 32) Hermitian block A = L L^H in place (lower triangle; the strict
-// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.  The inverse is
-// built row by row with each dot product split over eight lanes, so its critical path is 32
-// short reductions rather than 32-term serial sums.
-__global__ void __launch_bounds__(256)
+// upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.
+//
+// One warp per block.  The FP64 pipe of an SM retires about 1.7 DFMA per clock, so a whole-warp
+// FP64 instruction costs ~19 clocks whether or not its lanes are masked.  Both phases therefore
+// spread the entries that are active at each step evenly over the 32 lanes, instead of giving each
+// lane a fixed row:
+//  * factorisation, pivot j: the entries (i, l) with j < l <= i are a prefix of a list ordered by
+//    column l descending, so lane t takes list entries t, t + 32, ...;
+//  * inverse, step i (forward substitution on the columns of I): row i of X is scaled by
+//    1/L_ii, then the (k, c) entries with k > i, c <= i take X[k][c] -= L[k][i] X[i][c].
+__global__ void __launch_bounds__(32)
     chol_diag_kernel(double2 *__restrict__ A, int lda, int n, double2 *__restrict__ Linv, int ldl, int pivot0,
                      uint32_t *err)
 {
     __shared__ double2 S[32][33];
-    __shared__ double2 T[32][33];
+    __shared__ double2 X[32][33];
+    __shared__ unsigned short ent[528];
     __shared__ double rd[32];
-    __shared__ int bad;
-    const int tid = threadIdx.x;
-    if (tid == 0)
-        bad = 0;
-    for (int t = tid; t < 32 * 32; t += blockDim.x) {
-        const int i = t / 32, j = t % 32;
-        S[i][j] = (i < n && j < n && j <= i) ? A[(size_t)i * lda + j] : make_double2(0.0, 0.0);
+    const int lane = threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    for (int t = lane; t < 32 * 32; t += 32) {
+        const int i = t >> 5, l = t & 31;
+        S[i][l] = (i < n && l < n && l <= i) ? A[(size_t)i * lda + l] : make_double2(0.0, 0.0);
+        X[i][l] = make_double2(i == l && i < n ? 1.0 : 0.0, 0.0);
+        if (l >= 1 && l <= i)  // position of (i, l): all entries of the columns right of l come first
+            ent[(31 - l) * (32 - l) / 2 + (i - l)] = (unsigned short)((i << 8) | l);
     }
-    __syncthreads();
+    __syncwarp(FULL);
+    bool bad = false;
     for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            const double d = S[j][j].x;
-            double y;
-            if (!(d > 0.0) || !isfinite(d)) {
-                if (!bad)
-                    record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
-                bad = 1;
-                y = 1.0;
-                S[j][j] = make_double2(1.0, 0.0);
-            } else {
-                y = rsqrt_newton(d);
-                S[j][j] = make_double2(d * y, 0.0);
-            }
+        const double d = S[j][j].x;
+        const bool ok = d > 0.0 && isfinite(d);
+        const double y = ok ? rsqrt_newton(d) : 1.0;
+        if (!ok && !bad && lane == 0)
+            record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
+        bad = bad || !ok;
+        __syncwarp(FULL);  // every lane has read the pivot before it is overwritten
+        if (lane == j)
+            S[j][j] = make_double2(ok ? d * y : 1.0, 0.0);
+        else if (lane > j && lane < n)
+            S[lane][j] = make_double2(S[lane][j].x * y, S[lane][j].y * y);
+        if (lane == 0)
             rd[j] = y;
+        __syncwarp(FULL);
+        // S[i][l] -= S[i][j] conj(S[l][j]) for j < l <= i
+        const int cnt = (31 - j) * (32 - j) / 2;
+        for (int p = lane; p < cnt; p += 32) {
+            const int e = ent[p], i = e >> 8, l = e & 255;
+            const double2 a = S[i][j], b = S[l][j];
+            double2 v = S[i][l];
+            v.x = fma(-a.x, b.x, fma(-a.y, b.y, v.x));
+            v.y = fma(-a.y, b.x, fma(a.x, b.y, v.y));
+            S[i][l] = v;
         }
-        __syncthreads();
-        const double inv = rd[j];
-        if (tid > j && tid < n) {
-            S[tid][j].x *= inv;
-            S[tid][j].y *= inv;
-        }
-        __syncthreads();
-        // trailing update of the lower triangle: S[i][l] -= S[i][j] conj(S[l][j]), j < l <= i
-        for (int t = tid; t < 32 * 32; t += blockDim.x) {
-            const int i = t / 32, l = t % 32;
-            if (i < n && l > j && l <= i) {
-                const double2 p = cmul(S[i][j], cconj(S[l][j]));
-                S[i][l].x -= p.x;
-                S[i][l].y -= p.y;
-            }
-        }
-        __syncthreads();
+        __syncwarp(FULL);
     }
-    // L X = I row by row: X[i][c] = (delta_ic - sum_{c <= l < i} L[i][l] X[l][c]) / L[i][i].
-    const int c = tid >> 3, part = tid & 7;
     for (int i = 0; i < n; ++i) {
-        double2 s = make_double2(0.0, 0.0);
-        if (c < i)
-            for (int l = c + part; l < i; l += 8) {
-                const double2 p = cmul(S[i][l], T[l][c]);
-                s.x += p.x;
-                s.y += p.y;
-            }
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        if (lane <= i)
+            X[i][lane] = make_double2(X[i][lane].x * rd[i], X[i][lane].y * rd[i]);
+        __syncwarp(FULL);
+        const int w = i + 1, cnt = (n - 1 - i) * w;
+        for (int p = lane; p < cnt; p += 32) {
+            const int k = i + 1 + p / w, c = p - (p / w) * w;
+            const double2 a = S[k][i], b = X[i][c];
+            double2 v = X[k][c];
+            v.x = fma(-a.x, b.x, fma(a.y, b.y, v.x));
+            v.y = fma(-a.x, b.y, fma(-a.y, b.x, v.y));
+            X[k][c] = v;
         }
-        if (part == 0 && c < 32) {
-            if (c > i)
-                T[i][c] = make_double2(0.0, 0.0);
-            else
-                T[i][c] = make_double2(((c == i) ? 1.0 : 0.0) - s.x, -s.y);
-        }
-        __syncthreads();
-        if (part == 0 && c <= i)
-            T[i][c] = make_double2(T[i][c].x * rd[i], T[i][c].y * rd[i]);
-        __syncthreads();
+        __syncwarp(FULL);
     }
-    for (int t = tid; t < n * n; t += blockDim.x) {
+    for (int t = lane; t < n * n; t += 32) {
         const int i = t / n, j = t % n;
         A[(size_t)i * lda + j] = j <= i ? S[i][j] : make_double2(0.0, 0.0);
-        Linv[(size_t)i * ldl + j] = T[i][j];
+        Linv[(size_t)i * ldl + j] = j <= i ? X[i][j] : make_double2(0.0, 0.0);
     }
 }
 
@@ -343,8 +339,15 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, i
 {
     if (M <= 0 || N <= 0)
         return cudaSuccess;
-    dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT);
-    zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
+    // 32-wide tiles only when they alone make two full waves on 152 SMs
+    const long t32 = (long)((N + 31) / 32) * ((M + 31) / 32) / ((flags & ZG_C_LOWER) ? 2 : 1);
+    if (t32 >= 2 * 152) {
+        dim3 grid((N + 31) / 32, (M + 31) / 32);
+        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
+    } else {
+        dim3 grid((N + 15) / 16, (M + 15) / 16);
+        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -352,7 +355,7 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, i
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
                              cudaStream_t s)
 {
-    chol_diag_kernel<<<1, 256, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
+    chol_diag_kernel<<<1, 32, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -314,9 +314,7 @@ cudaError_t launch_herk_tc(const float *F, int prec, int kpad, int nr, int nr_pa
 {
     if (n_tiles <= 0)
         return cudaSuccess;
-    uint32_t lbo = LBO, sbo = SBO;
-    if (const char *e = getenv("GW_DEBUG_SWAP_LBO_SBO"); e && e[0] == '1')
-        std::swap(lbo, sbo);
+    const uint32_t lbo = LBO, sbo = SBO;
     cudaError_t e;
     if (prec == GW_PREC_TF32X3) {
         e = cudaFuncSetAttribute(herk_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -273,62 +273,7 @@ gw_status inverse_cholesky(Ctx &c, cudaStream_t s)
     GW_TRY(ensure(c, c.d_work, c.cap.work, need * sizeof(double2), "inverse workspace"));
     double2 *A = c.d_work, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)N * N,
             *Dinv = W + (size_t)N * NB;
-    const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
-    GW_CUDA(cudaMemcpyAsync(A, c.d_eps, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s), "copy eps");
-    for (int kb = 0; kb < nblk; ++kb) {
-        const int k0 = kb * NB, kn = std::min(NB, N - k0), rest = N - k0 - kn;
-        double2 *Dk = Dinv + (size_t)kb * NB * NB;
-        GW_CUDA(launch_chol_diag(A + (size_t)k0 * N + k0, N, kn, Dk, NB, k0, c.d_err, s), "Cholesky diagonal block");
-        if (rest > 0) {
-            double2 *panel = A + (size_t)(k0 + kn) * N + k0;
-            GW_CUDA(launch_zgemm(rest, kn, kn, one, panel, N, 0, Dk, NB, 1, zero, W, NB, s), "panel solve");
-            GW_CUDA(launch_copy_block(W, NB, panel, N, rest, kn, s), "panel store");
-            // only the lower triangle of the trailing matrix is read later
-            GW_CUDA(launch_zgemm(rest, rest, kn, mone, W, NB, 0, W, NB, 1, one, A + (size_t)(k0 + kn) * N + k0 + kn,
-                                 N, s, ZG_C_LOWER),
-                    "trailing update");
-        }
-    }
-    // Y = L^-1 by recursive halving at multiples of 32, so every leaf is one diagonal block whose
-    // inverse chol_diag already formed:  [L11 0; L21 L22]^-1 = [Y11 0; -Y22 L21 Y11  Y22].
-    // The two products per level are large GEMMs that fill the GPU, unlike a row-by-row sweep.
-    GW_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * N * sizeof(double2), s), "clear Y");
-    struct Frame {
-        int n0, n;
-    };
-    std::vector<Frame> todo = {{0, N}}, order;
-    while (!todo.empty()) {  // post-order: children before their parent
-        Frame f = todo.back();
-        todo.pop_back();
-        order.push_back(f);
-        if (f.n > NB) {
-            const int n1 = std::max(NB, ((f.n / 2 + NB - 1) / NB) * NB);
-            todo.push_back({f.n0, n1});
-            todo.push_back({f.n0 + n1, f.n - n1});
-        }
-    }
-    for (auto it = order.rbegin(); it != order.rend(); ++it) {
-        const int n0 = it->n0, n = it->n;
-        if (n <= NB) {
-            GW_CUDA(launch_copy_block(Dinv + (size_t)(n0 / NB) * NB * NB, NB, Y + (size_t)n0 * N + n0, N, n, n, s),
-                    "diagonal inverse store");
-            continue;
-        }
-        const int n1 = std::max(NB, ((n / 2 + NB - 1) / NB) * NB), n2 = n - n1;
-        // T = L21 Y11 (Y11 lower triangular)
-        GW_CUDA(launch_zgemm(n2, n1, n1, one, A + (size_t)(n0 + n1) * N + n0, N, 0, Y + (size_t)n0 * N + n0, N, 0,
-                             zero, T, n1, s, ZG_B_LOWER),
-                "L21 Y11");
-        // Y21 = -Y22 T (Y22 lower triangular)
-        GW_CUDA(launch_zgemm(n2, n1, n2, mone, Y + (size_t)(n0 + n1) * N + n0 + n1, N, 0, T, n1, 0, zero,
-                             Y + (size_t)(n0 + n1) * N + n0, N, s, ZG_A_LOWER),
-                "-Y22 L21 Y11");
-    }
-    // (Y^H Y)[i][j] = sum_{k >= max(i, j)} conj(Y[k][i]) Y[k][j]; Hermitian, so the lower half is
-    // computed and mirrored
-    GW_CUDA(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, c.d_epsinv, N, s,
-                         ZG_A_UPPER | ZG_B_LOWER | ZG_C_LOWER | ZG_C_MIRROR),
-            "Y^H Y");
+    GW_CUDA(chol_inverse_enqueue(c.d_eps, N, c.d_epsinv, A, Y, T, W, Dinv, c.d_err, s), "Cholesky inverse");
     return GW_OK;
 }
 

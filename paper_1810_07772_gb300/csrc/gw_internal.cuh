@@ -172,8 +172,16 @@ enum { ZG_B_LOWER = 1, ZG_A_UPPER = 2, ZG_C_LOWER = 4, ZG_C_MIRROR = 8, ZG_A_LOW
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA,
                          const double2 *B, int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s,
                          int flags = 0);
+// The same for `batch` independent products; problem z uses A + z sA, B + z sB, C + z sC.
+cudaError_t launch_zgemm_batched(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA, long sA,
+                                 const double2 *B, int ldb, int opB, long sB, double2 beta, double2 *C, int ldc,
+                                 long sC, int batch, cudaStream_t s, int flags = 0);
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
                              cudaStream_t s);
+// Enqueue eps^-1 = (L L^H)^-1 in FP64 (Cholesky, recursive-doubling triangular inverse, Y^H Y).
+// Workspace: A, Y, T of N^2 complex128 each, W of 32 N, Dinv of ceil(N/32) 32^2.
+cudaError_t chol_inverse_enqueue(const double2 *eps, int N, double2 *epsinv, double2 *A, double2 *Y, double2 *T,
+                                 double2 *W, double2 *Dinv, uint32_t *err, cudaStream_t s);
 cudaError_t launch_copy_block(const double2 *src, int lds, double2 *dst, int ldd, int rows, int cols,
                               cudaStream_t s);
 cudaError_t launch_set_identity(double2 *A, int lda, int n, double scale, cudaStream_t s);

@@ -73,60 +73,15 @@ extern "C" gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, vo
     if (st != GW_OK)
         return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int N = n, nblk = (N + NB - 1) / NB;
+    const int N = n;
     double2 *A = base, *Y = A + (size_t)N * N, *T = Y + (size_t)N * N, *W = T + (size_t)N * N,
             *Dinv = W + (size_t)N * NB;
     uint32_t *status = reinterpret_cast<uint32_t *>(base + SCRATCH_ELEMS - 1);
-    const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
 
-    // The array keeps the previous call's contents: clear the status word and Y, copy the input.
+    // The array keeps the previous call's contents: clear the status word (the enqueue clears Y).
     NA_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
-    NA_CUDA(cudaMemcpyAsync(A, eps, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    for (int kb = 0; kb < nblk; ++kb) {
-        const int k0 = kb * NB, kn = std::min(NB, N - k0), rest = N - k0 - kn;
-        double2 *Dk = Dinv + (size_t)kb * NB * NB;
-        NA_CUDA(launch_chol_diag(A + (size_t)k0 * N + k0, N, kn, Dk, NB, k0, status, s));
-        if (rest > 0) {
-            double2 *panel = A + (size_t)(k0 + kn) * N + k0;
-            NA_CUDA(launch_zgemm(rest, kn, kn, one, panel, N, 0, Dk, NB, 1, zero, W, NB, s));
-            NA_CUDA(launch_copy_block(W, NB, panel, N, rest, kn, s));
-            NA_CUDA(launch_zgemm(rest, rest, kn, mone, W, NB, 0, W, NB, 1, one, A + (size_t)(k0 + kn) * N + k0 + kn,
-                                 N, s, ZG_C_LOWER));
-        }
-    }
-    NA_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * N * sizeof(double2), s));
-    // Y = L^-1 by recursive halving (children before parents), leaves are the 32x32 inverses.
-    struct Frame {
-        int n0, n;
-    };
-    Frame order[2 * NOALLOC_MAX_N / NB + 8];
-    int norder = 0;
-    Frame stack[2 * NOALLOC_MAX_N / NB + 8];
-    int nstack = 0;
-    stack[nstack++] = {0, N};
-    while (nstack > 0) {
-        const Frame f = stack[--nstack];
-        order[norder++] = f;
-        if (f.n > NB) {
-            const int n1 = std::max(NB, ((f.n / 2 + NB - 1) / NB) * NB);
-            stack[nstack++] = {f.n0, n1};
-            stack[nstack++] = {f.n0 + n1, f.n - n1};
-        }
-    }
-    for (int i = norder - 1; i >= 0; --i) {
-        const int n0 = order[i].n0, nn = order[i].n;
-        if (nn <= NB) {
-            NA_CUDA(launch_copy_block(Dinv + (size_t)(n0 / NB) * NB * NB, NB, Y + (size_t)n0 * N + n0, N, nn, nn, s));
-            continue;
-        }
-        const int n1 = std::max(NB, ((nn / 2 + NB - 1) / NB) * NB), n2 = nn - n1;
-        NA_CUDA(launch_zgemm(n2, n1, n1, one, A + (size_t)(n0 + n1) * N + n0, N, 0, Y + (size_t)n0 * N + n0, N, 0, zero,
-                             T, n1, s, ZG_B_LOWER));
-        NA_CUDA(launch_zgemm(n2, n1, n2, mone, Y + (size_t)(n0 + n1) * N + n0 + n1, N, 0, T, n1, 0, zero,
-                             Y + (size_t)(n0 + n1) * N + n0, N, s, ZG_A_LOWER));
-    }
-    NA_CUDA(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, static_cast<double2 *>(epsinv), N, s,
-                         ZG_A_UPPER | ZG_B_LOWER | ZG_C_LOWER | ZG_C_MIRROR));
+    NA_CUDA(chol_inverse_enqueue(static_cast<const double2 *>(eps), N, static_cast<double2 *>(epsinv), A, Y, T, W,
+                                 Dinv, status, s));
     uint32_t word = 0;
     NA_CUDA(cudaMemcpyAsync(&word, status, sizeof word, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));

@@ -4,6 +4,8 @@
 // eps^-1 = Y^H Y with Y = L^-1, assembled from one small kernel that factors and inverts a
 // 32 x 32 diagonal block in shared memory and a complex128 GEMM kernel.  The same GEMM drives
 // the paper's Newton iteration X <- X (2I - eps X) when that method is requested.
+#include <algorithm>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -45,9 +47,12 @@ template <int ZT>
 __global__ void __launch_bounds__((ZT / 2) * (ZT / 2))
     zgemm_kernel(int M, int N, int K, double2 alpha, const double2 *__restrict__ A, int lda, int opA,
                  const double2 *__restrict__ B, int ldb, int opB, double2 beta, double2 *__restrict__ C, int ldc,
-                 int flags)
+                 int flags, long sA, long sB, long sC)
 {
     constexpr int H = ZT / 2, NT = H * H;
+    A += blockIdx.z * sA;  // batched products: one independent problem per blockIdx.z
+    B += blockIdx.z * sB;
+    C += blockIdx.z * sC;
     __shared__ double2 As[ZK][ZT + 1];
     __shared__ double2 Bs[ZK][ZT + 1];
     const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
@@ -149,82 +154,104 @@ __device__ __forceinline__ double rsqrt_newton(double d)
     return y;
 }
 
+// 1/d by the Newton-Raphson iteration y <- y + y (1 - d y) from the FP32 reciprocal: each step
+// doubles the number of correct bits (24 -> 48 -> FP64 rounding), two dependent FMAs per step.
+__device__ __forceinline__ double rcp_newton(double d)
+{
+    const float df = static_cast<float>(d);
+    if (!(fabsf(df) > 1e-30f) || !(fabsf(df) < 1e30f))
+        return 1.0 / d;
+    double y = static_cast<double>(__frcp_rn(df));
+    y = fma(y, fma(-d, y, 1.0), y);
+    y = fma(y, fma(-d, y, 1.0), y);
+    return y;
+}
+
 // Factor the n x n (n <= 32) Hermitian block A = L L^H in place (lower triangle; the strict
 // upper triangle is zeroed) and write Linv = L^-1 (lower, zero above) to Linv.
 //
-// One warp per block.  The FP64 pipe of an SM retires about 1.7 DFMA per clock, so a whole-warp
-// FP64 instruction costs ~19 clocks whether or not its lanes are masked.  Both phases therefore
-// spread the entries that are active at each step evenly over the 32 lanes, instead of giving each
-// lane a fixed row:
-//  * factorisation, pivot j: the entries (i, l) with j < l <= i are a prefix of a list ordered by
-//    column l descending, so lane t takes list entries t, t + 32, ...;
-//  * inverse, step i (forward substitution on the columns of I): row i of X is scaled by
-//    1/L_ii, then the (k, c) entries with k > i, c <= i take X[k][c] -= L[k][i] X[i][c].
-__global__ void __launch_bounds__(32)
+// The block is factored as A = L~ D L~^H (L~ unit lower, D real), and L = L~ D^1/2 is formed at
+// the end.  The chain of dependent operations from one pivot to the next is then one reciprocal
+// and one update; the square roots, the column scalings and the inverse of the unit-lower L~
+// (no divisions) are off that chain or parallel over the block:
+//  * pivot j (one barrier): every thread forms r = 1/d_j; the entries (i, l), j < l <= i, take
+//    S[i][l] -= S[i][j] conj(S[l][j]) r, with column j left unscaled (it holds L~_ij d_j).  They
+//    are a prefix of a list ordered by column l descending, at most 2 per thread;
+//  * L~_ij = S[i][j] r_j; X = L~^-1 by forward substitution on the columns of I, one entry
+//    (k, c), k > i >= c, per thread and step;
+//  * L = L~ diag(sqrt d), Linv = diag(1/sqrt d) X.
+__global__ void __launch_bounds__(256)
     chol_diag_kernel(double2 *__restrict__ A, int lda, int n, double2 *__restrict__ Linv, int ldl, int pivot0,
                      uint32_t *err)
 {
     __shared__ double2 S[32][33];
     __shared__ double2 X[32][33];
-    __shared__ unsigned short ent[528];
-    __shared__ double rd[32];
-    const int lane = threadIdx.x;
-    const unsigned FULL = 0xffffffffu;
-    for (int t = lane; t < 32 * 32; t += 32) {
+    __shared__ unsigned short ent[496];
+    __shared__ double dv[32], rdv[32], qv[32];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < 32 * 32; t += blockDim.x) {
         const int i = t >> 5, l = t & 31;
         S[i][l] = (i < n && l < n && l <= i) ? A[(size_t)i * lda + l] : make_double2(0.0, 0.0);
         X[i][l] = make_double2(i == l && i < n ? 1.0 : 0.0, 0.0);
         if (l >= 1 && l <= i)  // position of (i, l): all entries of the columns right of l come first
             ent[(31 - l) * (32 - l) / 2 + (i - l)] = (unsigned short)((i << 8) | l);
     }
-    __syncwarp(FULL);
+    __syncthreads();
     bool bad = false;
     for (int j = 0; j < n; ++j) {
         const double d = S[j][j].x;
         const bool ok = d > 0.0 && isfinite(d);
-        const double y = ok ? rsqrt_newton(d) : 1.0;
-        if (!ok && !bad && lane == 0)
-            record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
+        const double r = ok ? rcp_newton(d) : 1.0;
+        if (tid == 0) {
+            if (!ok && !bad)
+                record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
+            dv[j] = ok ? d : 1.0;
+            rdv[j] = r;
+        }
         bad = bad || !ok;
-        __syncwarp(FULL);  // every lane has read the pivot before it is overwritten
-        if (lane == j)
-            S[j][j] = make_double2(ok ? d * y : 1.0, 0.0);
-        else if (lane > j && lane < n)
-            S[lane][j] = make_double2(S[lane][j].x * y, S[lane][j].y * y);
-        if (lane == 0)
-            rd[j] = y;
-        __syncwarp(FULL);
-        // S[i][l] -= S[i][j] conj(S[l][j]) for j < l <= i
         const int cnt = (31 - j) * (32 - j) / 2;
-        for (int p = lane; p < cnt; p += 32) {
+        for (int p = tid; p < cnt; p += blockDim.x) {
             const int e = ent[p], i = e >> 8, l = e & 255;
             const double2 a = S[i][j], b = S[l][j];
-            double2 v = S[i][l];
-            v.x = fma(-a.x, b.x, fma(-a.y, b.y, v.x));
-            v.y = fma(-a.y, b.x, fma(a.x, b.y, v.y));
-            S[i][l] = v;
+            const double tr = fma(a.x, b.x, a.y * b.y) * r, ti = fma(a.y, b.x, -a.x * b.y) * r;
+            S[i][l] = make_double2(S[i][l].x - tr, S[i][l].y - ti);
         }
-        __syncwarp(FULL);
+        __syncthreads();
     }
-    for (int i = 0; i < n; ++i) {
-        if (lane <= i)
-            X[i][lane] = make_double2(X[i][lane].x * rd[i], X[i][lane].y * rd[i]);
-        __syncwarp(FULL);
-        const int w = i + 1, cnt = (n - 1 - i) * w;
-        for (int p = lane; p < cnt; p += 32) {
-            const int k = i + 1 + p / w, c = p - (p / w) * w;
+    // L~ in place below the diagonal; 1/sqrt(d) per column
+    for (int t = tid; t < n * n; t += blockDim.x) {
+        const int i = t / n, j = t % n;
+        if (i > j)
+            S[i][j] = make_double2(S[i][j].x * rdv[j], S[i][j].y * rdv[j]);
+    }
+    if (tid < n)
+        qv[tid] = rsqrt_newton(dv[tid]);
+    __syncthreads();
+    for (int i = 0; i + 1 < n; ++i) {
+        const int w = i + 1;
+        if (tid < (n - 1 - i) * w) {
+            const int k = i + 1 + tid / w, c = tid - (tid / w) * w;
             const double2 a = S[k][i], b = X[i][c];
             double2 v = X[k][c];
             v.x = fma(-a.x, b.x, fma(a.y, b.y, v.x));
             v.y = fma(-a.x, b.y, fma(-a.y, b.x, v.y));
             X[k][c] = v;
         }
-        __syncwarp(FULL);
+        __syncthreads();
     }
-    for (int t = lane; t < n * n; t += 32) {
+    for (int t = tid; t < n * n; t += blockDim.x) {
         const int i = t / n, j = t % n;
-        A[(size_t)i * lda + j] = j <= i ? S[i][j] : make_double2(0.0, 0.0);
-        Linv[(size_t)i * ldl + j] = j <= i ? X[i][j] : make_double2(0.0, 0.0);
+        double2 l = make_double2(0.0, 0.0), x = make_double2(0.0, 0.0);
+        if (j < i) {
+            const double sq = dv[j] * qv[j];
+            l = make_double2(S[i][j].x * sq, S[i][j].y * sq);
+        } else if (j == i) {
+            l = make_double2(dv[j] * qv[j], 0.0);
+        }
+        if (j <= i)
+            x = make_double2(X[i][j].x * qv[i], X[i][j].y * qv[i]);
+        A[(size_t)i * lda + j] = l;
+        Linv[(size_t)i * ldl + j] = x;
     }
 }
 
@@ -317,6 +344,17 @@ __global__ void row_abs_sum_max_kernel(const double2 *__restrict__ A, int n, dou
         *out = red[0];
 }
 
+// The nblk inverses of the 32x32 diagonal blocks (Dinv, leading dimension 32) onto the diagonal of
+// Y (leading dimension N); blockIdx.x = block.
+__global__ void scatter_diag_blocks_kernel(const double2 *__restrict__ Dinv, int N, double2 *__restrict__ Y)
+{
+    const int b = blockIdx.x, n0 = 32 * b, nb = min(32, N - n0);
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int i = t / nb, j = t % nb;
+        Y[(size_t)(n0 + i) * N + n0 + j] = Dinv[(size_t)b * 32 * 32 + i * 32 + j];
+    }
+}
+
 int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
@@ -343,10 +381,10 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, i
     const long t32 = (long)((N + 31) / 32) * ((M + 31) / 32) / ((flags & ZG_C_LOWER) ? 2 : 1);
     if (t32 >= 2 * 152) {
         dim3 grid((N + 31) / 32, (M + 31) / 32);
-        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
+        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, 0, 0, 0);
     } else {
         dim3 grid((N + 15) / 16, (M + 15) / 16);
-        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags);
+        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, 0, 0, 0);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -355,7 +393,7 @@ cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, i
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
                              cudaStream_t s)
 {
-    chol_diag_kernel<<<1, 32, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
+    chol_diag_kernel<<<1, 256, 0, s>>>(A, lda, n, Linv, ldl, pivot0, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -403,6 +441,95 @@ cudaError_t launch_row_abs_sum_max(const double2 *A, int n, double *out, cudaStr
     row_abs_sum_max_kernel<<<1, 256, 0, s>>>(A, n, out);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm_batched(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA, long sA,
+                                 const double2 *B, int ldb, int opB, long sB, double2 beta, double2 *C, int ldc,
+                                 long sC, int batch, cudaStream_t s, int flags)
+{
+    if (M <= 0 || N <= 0 || batch <= 0)
+        return cudaSuccess;
+    const long t32 = (long)batch * ((N + 31) / 32) * ((M + 31) / 32) / ((flags & ZG_C_LOWER) ? 2 : 1);
+    if (t32 >= 2 * 152) {
+        dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
+        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, sA, sB,
+                                                sC);
+    } else {
+        dim3 grid((N + 15) / 16, (M + 15) / 16, batch);
+        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, sA, sB,
+                                               sC);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// eps^-1 of a Hermitian positive-definite N x N complex128 matrix, in FP64 (Sec. 5.1 asks for the
+// inverse; the factorisation route is this library's):
+//  1. blocked right-looking Cholesky eps = L L^H with 32-wide panels; each diagonal block is
+//     factored and inverted by chol_diag_kernel, the panel below it is solved as a product with
+//     that inverse, and the trailing lower triangle takes the rank-32 update;
+//  2. Y = L^-1 by recursive doubling: with the inverted blocks of size b on the diagonal of Y,
+//     each pair of neighbours becomes one block of size 2b through
+//     [L11 0; L21 L22]^-1 = [Y11 0; -Y22 L21 Y11  Y22],
+//     and all pairs of one size go in one batched product (a trailing pair with a short second
+//     block in one more);
+//  3. eps^-1 = Y^H Y, lower half computed and mirrored.
+// Workspace: A, Y, T (N^2 each), W (N x 32), Dinv (ceil(N/32) x 32 x 32).  Status words for a
+// non-positive pivot go to err.
+cudaError_t chol_inverse_enqueue(const double2 *eps, int N, double2 *epsinv, double2 *A, double2 *Y, double2 *T,
+                                 double2 *W, double2 *Dinv, uint32_t *err, cudaStream_t s)
+{
+    constexpr int NB = 32;
+    const int nblk = (N + NB - 1) / NB;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+    cudaError_t e;
+#define ENQ(x)                         \
+    do {                               \
+        if ((e = (x)) != cudaSuccess)  \
+            return e;                  \
+    } while (0)
+    ENQ(cudaMemcpyAsync(A, eps, (size_t)N * N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int k0 = kb * NB, kn = std::min(NB, N - k0), rest = N - k0 - kn;
+        double2 *Dk = Dinv + (size_t)kb * NB * NB;
+        ENQ(launch_chol_diag(A + (size_t)k0 * N + k0, N, kn, Dk, NB, k0, err, s));
+        if (rest > 0) {
+            double2 *panel = A + (size_t)(k0 + kn) * N + k0;
+            ENQ(launch_zgemm(rest, kn, kn, one, panel, N, 0, Dk, NB, 1, zero, W, NB, s));
+            ENQ(launch_copy_block(W, NB, panel, N, rest, kn, s));
+            // only the lower triangle of the trailing matrix is read later
+            ENQ(launch_zgemm(rest, rest, kn, mone, W, NB, 0, W, NB, 1, one, A + (size_t)(k0 + kn) * N + k0 + kn, N,
+                             s, ZG_C_LOWER));
+        }
+    }
+    ENQ(cudaMemsetAsync(Y, 0, (size_t)N * N * sizeof(double2), s));
+    scatter_diag_blocks_kernel<<<nblk, 256, 0, s>>>(Dinv, N, Y);
+    count_launches(1);
+    ENQ(cudaGetLastError());
+    const long diag = (long)N + 1;
+    for (int b = NB; b < N; b *= 2) {
+        const int F = N / (2 * b);  // pairs of two full blocks
+        if (F > 0) {
+            // T_p = L21 Y11, then Y21 = -Y22 T_p, for the pairs starting at 2 p b
+            ENQ(launch_zgemm_batched(b, b, b, one, A + (size_t)b * N, N, 0, 2 * b * diag, Y, N, 0, 2 * b * diag, zero,
+                                     T, b, (long)b * b, F, s, ZG_B_LOWER));
+            ENQ(launch_zgemm_batched(b, b, b, mone, Y + (size_t)b * diag, N, 0, 2 * b * diag, T, b, 0, (long)b * b,
+                                     zero, Y + (size_t)b * N, N, 2 * b * diag, F, s, ZG_A_LOWER));
+        }
+        const int n0 = 2 * b * F, n2 = N - n0 - b;  // a last pair with a short second block
+        if (n2 > 0) {
+            ENQ(launch_zgemm(n2, b, b, one, A + (size_t)(n0 + b) * N + n0, N, 0, Y + (size_t)n0 * diag, N, 0, zero, T,
+                             b, s, ZG_B_LOWER));
+            ENQ(launch_zgemm(n2, b, n2, mone, Y + (size_t)(n0 + b) * diag, N, 0, T, b, 0, zero,
+                             Y + (size_t)(n0 + b) * N + n0, N, s, ZG_A_LOWER));
+        }
+    }
+    // (Y^H Y)[i][j] = sum_{k >= max(i, j)} conj(Y[k][i]) Y[k][j]; Hermitian, so the lower half is
+    // computed and mirrored
+    ENQ(launch_zgemm(N, N, N, one, Y, N, 1, Y, N, 0, zero, epsinv, N, s,
+                     ZG_A_UPPER | ZG_B_LOWER | ZG_C_LOWER | ZG_C_MIRROR));
+#undef ENQ
+    return cudaSuccess;
 }
 
 }  // namespace gw

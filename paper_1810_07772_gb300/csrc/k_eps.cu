@@ -35,56 +35,56 @@ __global__ void eps_build_kernel(const float2 *__restrict__ PG, const double *__
 }
 
 // ---------------------------------------------------------------------------- zgemm
-constexpr int ZK = 16;   // k chunk
+constexpr int ZT = 16;    // output tile (ZT x ZT, one complex output per thread)
+constexpr int ZKC = 32;   // k chunk staged in shared memory
 
 // C = alpha op(A) op(B) + beta C with optional triangular structure (flags, see gw_internal.cuh):
 // known-zero k ranges of a triangular operand are skipped, and with ZG_C_LOWER only tiles that
 // reach the diagonal or below are computed (ZG_C_MIRROR also stores the conjugate transpose).
-// ZT x ZT output tiles, (ZT/2)^2 threads with 2 x 2 outputs each.  The FP64 pipe, not shared
-// memory, bounds this kernel; ZT = 16 gives four times as many CTAs for the small and triangular
-// products of the inverse, whose few 32-wide tiles left most SMs idle.
-template <int ZT>
-__global__ void __launch_bounds__((ZT / 2) * (ZT / 2))
+//
+// FP64 on this GPU: each SM sub-partition retires about 0.42 lane-FMAs per clock, so one
+// warp-wide DFMA holds its sub-partition for ~77 clocks and the kernel is bound by how many
+// DFMAs each warp issues and on how many sub-partitions they run.  Each thread therefore owns a
+// single output (4 DFMAs per k), a CTA is 8 warps (two per sub-partition) on a 16 x 16 tile, and
+// even the small products of the factorisation spread over hundreds of warps.  Shared-memory and
+// global traffic are minor next to that.  Batched products: problem blockIdx.z uses A + z sA,
+// B + z sB, C + z sC.
+__global__ void __launch_bounds__(256)
     zgemm_kernel(int M, int N, int K, double2 alpha, const double2 *__restrict__ A, int lda, int opA,
                  const double2 *__restrict__ B, int ldb, int opB, double2 beta, double2 *__restrict__ C, int ldc,
                  int flags, long sA, long sB, long sC)
 {
-    constexpr int H = ZT / 2, NT = H * H;
-    A += blockIdx.z * sA;  // batched products: one independent problem per blockIdx.z
+    __shared__ double2 As[ZKC][ZT + 1];
+    __shared__ double2 Bs[ZKC][ZT + 1];
+    A += blockIdx.z * sA;
     B += blockIdx.z * sB;
     C += blockIdx.z * sC;
-    __shared__ double2 As[ZK][ZT + 1];
-    __shared__ double2 Bs[ZK][ZT + 1];
     const int i0 = blockIdx.y * ZT, j0 = blockIdx.x * ZT;
     if ((flags & ZG_C_LOWER) && j0 > i0 + ZT - 1)
         return;  // tile strictly above the diagonal
-    const int tx = threadIdx.x % H, ty = threadIdx.x / H;
-    double2 acc[2][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-            acc[a][b] = make_double2(0.0, 0.0);
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     int kbeg = 0;
     if (flags & ZG_B_LOWER)
         kbeg = max(kbeg, j0);  // op(B)[k][j] = 0 for k < j
     if (flags & ZG_A_UPPER)
         kbeg = max(kbeg, i0);  // op(A)[i][k] = 0 for k < i
-    kbeg = (kbeg / ZK) * ZK;
     const int kend = (flags & ZG_A_LOWER) ? min(K, i0 + ZT) : K;  // op(A)[i][k] = 0 for k > i
-    for (int k0 = kbeg; k0 < kend; k0 += ZK) {
-        for (int t = threadIdx.x; t < ZK * ZT; t += NT) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k0 = kbeg; k0 < kend; k0 += ZKC) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int t = tid + 256 * e;
             int i, kk;
             if (opA == 0) {
-                i = t / ZK;
-                kk = t % ZK;
+                i = t / ZKC;
+                kk = t % ZKC;
             } else {
                 kk = t / ZT;
                 i = t % ZT;
             }
             const int gi = i0 + i, gk = k0 + kk;
             double2 v = make_double2(0.0, 0.0);
-            if (gi < M && gk < K)
+            if (gi < M && gk < kend)
                 v = opA == 0 ? A[(size_t)gi * lda + gk] : cconj(A[(size_t)gk * lda + gi]);
             As[kk][i] = v;
             int j, kb;
@@ -92,49 +92,37 @@ __global__ void __launch_bounds__((ZT / 2) * (ZT / 2))
                 kb = t / ZT;
                 j = t % ZT;
             } else {
-                j = t / ZK;
-                kb = t % ZK;
+                j = t / ZKC;
+                kb = t % ZKC;
             }
             const int gj = j0 + j, gk2 = k0 + kb;
             double2 w = make_double2(0.0, 0.0);
-            if (gj < N && gk2 < K)
+            if (gj < N && gk2 < kend)
                 w = opB == 0 ? B[(size_t)gk2 * ldb + gj] : cconj(B[(size_t)gj * ldb + gk2]);
             Bs[kb][j] = w;
         }
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < ZK; ++kk) {
-            const double2 a0 = As[kk][ty], a1 = As[kk][ty + H];
-            const double2 b0 = Bs[kk][tx], b1 = Bs[kk][tx + H];
-            acc[0][0].x = fma(a0.x, b0.x, fma(-a0.y, b0.y, acc[0][0].x));
-            acc[0][0].y = fma(a0.x, b0.y, fma(a0.y, b0.x, acc[0][0].y));
-            acc[0][1].x = fma(a0.x, b1.x, fma(-a0.y, b1.y, acc[0][1].x));
-            acc[0][1].y = fma(a0.x, b1.y, fma(a0.y, b1.x, acc[0][1].y));
-            acc[1][0].x = fma(a1.x, b0.x, fma(-a1.y, b0.y, acc[1][0].x));
-            acc[1][0].y = fma(a1.x, b0.y, fma(a1.y, b0.x, acc[1][0].y));
-            acc[1][1].x = fma(a1.x, b1.x, fma(-a1.y, b1.y, acc[1][1].x));
-            acc[1][1].y = fma(a1.x, b1.y, fma(a1.y, b1.x, acc[1][1].y));
+        const int kn = min(ZKC, kend - k0);
+#pragma unroll 8
+        for (int kk = 0; kk < kn; ++kk) {
+            const double2 a = As[kk][ty], b = Bs[kk][tx];
+            acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+            acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
         }
         __syncthreads();
     }
-    const bool use_beta = beta.x != 0.0 || beta.y != 0.0;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int gi = i0 + ty + H * a, gj = j0 + tx + H * b;
-            if (gi < M && gj < N && (!(flags & ZG_C_LOWER) || gj <= gi)) {
-                double2 v = cmul(alpha, acc[a][b]);
-                if (use_beta) {
-                    const double2 c = cmul(beta, C[(size_t)gi * ldc + gj]);
-                    v.x += c.x;
-                    v.y += c.y;
-                }
-                C[(size_t)gi * ldc + gj] = v;
-                if ((flags & ZG_C_MIRROR) && gj < gi)
-                    C[(size_t)gj * ldc + gi] = cconj(v);
-            }
+    const int gi = i0 + ty, gj = j0 + tx;
+    if (gi < M && gj < N && (!(flags & ZG_C_LOWER) || gj <= gi)) {
+        double2 v = cmul(alpha, acc);
+        if (beta.x != 0.0 || beta.y != 0.0) {
+            const double2 c = cmul(beta, C[(size_t)gi * ldc + gj]);
+            v.x += c.x;
+            v.y += c.y;
         }
+        C[(size_t)gi * ldc + gj] = v;
+        if ((flags & ZG_C_MIRROR) && gj < gi)
+            C[(size_t)gj * ldc + gi] = cconj(v);
+    }
 }
 
 // ---------------------------------------------------------------------------- diagonal block
@@ -174,9 +162,10 @@ __device__ __forceinline__ double rcp_newton(double d)
 // the end.  The chain of dependent operations from one pivot to the next is then one reciprocal
 // and one update; the square roots, the column scalings and the inverse of the unit-lower L~
 // (no divisions) are off that chain or parallel over the block:
-//  * pivot j (one barrier): every thread forms r = 1/d_j; the entries (i, l), j < l <= i, take
-//    S[i][l] -= S[i][j] conj(S[l][j]) r, with column j left unscaled (it holds L~_ij d_j).  They
-//    are a prefix of a list ordered by column l descending, at most 2 per thread;
+//  * pivot j (one barrier): the entries (i, l), j < l <= i, take S[i][l] -= S[i][j] conj(S[l][j]) r
+//    with r = 1/d_j, column j left unscaled (it holds L~_ij d_j).  They are a prefix of a list
+//    ordered by column l descending, at most 2 per thread.  The thread that updates (j+1, j+1)
+//    forms the next reciprocal at once, so no other warp repeats it;
 //  * L~_ij = S[i][j] r_j; X = L~^-1 by forward substitution on the columns of I, one entry
 //    (k, c), k > i >= c, per thread and step;
 //  * L = L~ diag(sqrt d), Linv = diag(1/sqrt d) X.
@@ -196,25 +185,34 @@ __global__ void __launch_bounds__(256)
         if (l >= 1 && l <= i)  // position of (i, l): all entries of the columns right of l come first
             ent[(31 - l) * (32 - l) / 2 + (i - l)] = (unsigned short)((i << 8) | l);
     }
-    __syncthreads();
-    bool bad = false;
-    for (int j = 0; j < n; ++j) {
-        const double d = S[j][j].x;
+    // pivot 0's reciprocal; every later one is formed by the thread that finishes its diagonal entry
+    if (tid == 0 && n > 0) {
+        const double d = S[0][0].x;
         const bool ok = d > 0.0 && isfinite(d);
-        const double r = ok ? rcp_newton(d) : 1.0;
-        if (tid == 0) {
-            if (!ok && !bad)
-                record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + j));
-            dv[j] = ok ? d : 1.0;
-            rdv[j] = r;
-        }
-        bad = bad || !ok;
+        if (!ok)
+            record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)pivot0);
+        dv[0] = ok ? d : 1.0;
+        rdv[0] = ok ? rcp_newton(d) : 1.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const double r = rdv[j];
         const int cnt = (31 - j) * (32 - j) / 2;
         for (int p = tid; p < cnt; p += blockDim.x) {
             const int e = ent[p], i = e >> 8, l = e & 255;
             const double2 a = S[i][j], b = S[l][j];
-            const double tr = fma(a.x, b.x, a.y * b.y) * r, ti = fma(a.y, b.x, -a.x * b.y) * r;
-            S[i][l] = make_double2(S[i][l].x - tr, S[i][l].y - ti);
+            const double cx = a.x * r, cy = a.y * r;
+            double2 v = S[i][l];
+            v.x = fma(-cx, b.x, fma(-cy, b.y, v.x));
+            v.y = fma(-cy, b.x, fma(cx, b.y, v.y));
+            S[i][l] = v;
+            if (i == j + 1 && l == j + 1 && l < n) {  // the next pivot is final: its reciprocal now
+                const bool ok = v.x > 0.0 && isfinite(v.x);
+                if (!ok)
+                    record_error(err, GW_E_NUMERIC, SITE_CHOL_PIVOT, (uint32_t)(pivot0 + l));
+                dv[l] = ok ? v.x : 1.0;
+                rdv[l] = ok ? rcp_newton(v.x) : 1.0;
+            }
         }
         __syncthreads();
     }
@@ -375,19 +373,7 @@ cudaError_t launch_eps_build(const float2 *PG, const double *sv, int ng, double2
 cudaError_t launch_zgemm(int M, int N, int K, double2 alpha, const double2 *A, int lda, int opA, const double2 *B,
                          int ldb, int opB, double2 beta, double2 *C, int ldc, cudaStream_t s, int flags)
 {
-    if (M <= 0 || N <= 0)
-        return cudaSuccess;
-    // 32-wide tiles only when they alone make two full waves on 152 SMs
-    const long t32 = (long)((N + 31) / 32) * ((M + 31) / 32) / ((flags & ZG_C_LOWER) ? 2 : 1);
-    if (t32 >= 2 * 152) {
-        dim3 grid((N + 31) / 32, (M + 31) / 32);
-        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, 0, 0, 0);
-    } else {
-        dim3 grid((N + 15) / 16, (M + 15) / 16);
-        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, 0, 0, 0);
-    }
-    count_launches(1);
-    return cudaGetLastError();
+    return launch_zgemm_batched(M, N, K, alpha, A, lda, opA, 0, B, ldb, opB, 0, beta, C, ldc, 0, 1, s, flags);
 }
 
 cudaError_t launch_chol_diag(double2 *A, int lda, int n, double2 *Linv, int ldl, int pivot0, uint32_t *err,
@@ -449,16 +435,8 @@ cudaError_t launch_zgemm_batched(int M, int N, int K, double2 alpha, const doubl
 {
     if (M <= 0 || N <= 0 || batch <= 0)
         return cudaSuccess;
-    const long t32 = (long)batch * ((N + 31) / 32) * ((M + 31) / 32) / ((flags & ZG_C_LOWER) ? 2 : 1);
-    if (t32 >= 2 * 152) {
-        dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
-        zgemm_kernel<32><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, sA, sB,
-                                                sC);
-    } else {
-        dim3 grid((N + 15) / 16, (M + 15) / 16, batch);
-        zgemm_kernel<16><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, sA, sB,
-                                               sC);
-    }
+    dim3 grid((N + ZT - 1) / ZT, (M + ZT - 1) / ZT, batch);
+    zgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, flags, sA, sB, sC);
     count_launches(1);
     return cudaGetLastError();
 }

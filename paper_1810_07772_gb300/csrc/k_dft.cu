@@ -20,7 +20,7 @@ namespace gw {
 namespace {
 
 constexpr int DFT_THREADS = 256;
-constexpr int GPT = 16;  // stage-3 outputs (row, G) per thread kept in registers
+constexpr int GPT_MAX = 16;  // stage-3 outputs (row, G) per thread kept in registers, at most
 
 struct SmemLayout {
     size_t tw, m3, disk, gmap, X, A1, A2, total;
@@ -78,8 +78,11 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int R>
-__global__ void __launch_bounds__(DFT_THREADS)
+// GPT (stage-3 outputs per thread) is sized to R N_g at launch: registers, not shared memory,
+// decide how many CTAs share an SM, and every CTA more hides more of the barrier waits between
+// the three stages.
+template <int R, int GPT>
+__global__ void __launch_bounds__(DFT_THREADS, GPT <= 12 ? 3 : 2)
     dft_rows_kernel(const float2 *__restrict__ X, long long ldx, int rows, float2 *__restrict__ Y, long long ldy,
                     int n1, int n2, int n3, int ng, int c3, int cd, const int *__restrict__ g_m3,
                     const int *__restrict__ g_disk, const int *__restrict__ g_gmap, const float2 *__restrict__ g_tw)
@@ -168,26 +171,21 @@ __global__ void __launch_bounds__(DFT_THREADS)
                 A1[(rho * n2 + j2) * c3 + i3] = acc[rho];
         }
         __syncthreads();
-        // stage 2: A2[rho][d] = sum_j2 A1[rho][j2][i3(d)] e(m2(d) j2 / n2)
-        for (int d = tid; d < cd; d += DFT_THREADS) {
+        // stage 2: A2[rho][d] = sum_j2 A1[rho][j2][i3(d)] e(m2(d) j2 / n2), one (row, d) per item:
+        // the disk has about a hundred points, so items over rows keep more threads busy
+        for (int t = tid; t < R * cd; t += DFT_THREADS) {
+            const int rho = t / cd, d = t - rho * cd;
             const int step = disk[2 * d], i3 = disk[2 * d + 1];
-            float2 acc[R];
-#pragma unroll
-            for (int rho = 0; rho < R; ++rho)
-                acc[rho] = make_float2(0.f, 0.f);
+            float2 acc = make_float2(0.f, 0.f);
             int idx = 0;
+            const float2 *a1 = A1 + rho * n2 * c3 + i3;
             for (int j2 = 0; j2 < n2; ++j2) {
-                const float2 w = tw2[idx];
-#pragma unroll
-                for (int rho = 0; rho < R; ++rho)
-                    cmac(acc[rho], A1[(rho * n2 + j2) * c3 + i3], w);
+                cmac(acc, a1[j2 * c3], tw2[idx]);
                 idx += step;
                 if (idx >= n2)
                     idx -= n2;
             }
-#pragma unroll
-            for (int rho = 0; rho < R; ++rho)
-                A2[rho * cd + d] = acc[rho];
+            A2[rho * cd + d] = acc;
         }
         __syncthreads();
         // stage 3 (this plane's term): y[rho][g] += A2[rho][d(g)] e(m1(g) j1 / n1)
@@ -261,7 +259,7 @@ constexpr size_t DFT_SMEM_MAX = 220 * 1024;
 int rows_per_cta(const DftPlan &p)
 {
     for (int R : {4, 2})
-        if (layout_for(p.n, p.ng, p.c3, p.cd, R).total <= DFT_SMEM_TARGET && R * p.ng <= DFT_THREADS * GPT)
+        if (layout_for(p.n, p.ng, p.c3, p.cd, R).total <= DFT_SMEM_TARGET && R * p.ng <= DFT_THREADS * GPT_MAX)
             return R;
     return 1;
 }
@@ -277,22 +275,36 @@ size_t dft_smem_bytes(const DftPlan &p, int R)
 
 bool dft_supported(const DftPlan &p)
 {
-    return p.ng <= DFT_THREADS * GPT && layout_for(p.n, p.ng, p.c3, p.cd, 1).total <= DFT_SMEM_MAX;
+    return p.ng <= DFT_THREADS * GPT_MAX && layout_for(p.n, p.ng, p.c3, p.cd, 1).total <= DFT_SMEM_MAX;
+}
+
+template <int R, int GPT>
+static cudaError_t launch_dft_RG(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
+                                 cudaStream_t s)
+{
+    const size_t smem = layout_for(p.n, p.ng, p.c3, p.cd, R).total;
+    cudaError_t e =
+        cudaFuncSetAttribute(dft_rows_kernel<R, GPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dft_rows_kernel<R, GPT><<<(rows + R - 1) / R, DFT_THREADS, smem, s>>>(
+        X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2], p.ng, p.c3, p.cd, p.m3list, p.disk, p.gmap, p.tw);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_dft_R(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
                                 cudaStream_t s)
 {
-    const size_t smem = layout_for(p.n, p.ng, p.c3, p.cd, R).total;
-    cudaError_t e = cudaFuncSetAttribute(dft_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    dft_rows_kernel<R><<<(rows + R - 1) / R, DFT_THREADS, smem, s>>>(X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2],
-                                                                      p.ng, p.c3, p.cd, p.m3list, p.disk, p.gmap,
-                                                                      p.tw);
-    count_launches(1);
-    return cudaGetLastError();
+    const int need = (R * p.ng + DFT_THREADS - 1) / DFT_THREADS;  // stage-3 outputs per thread
+    if (need <= 4)
+        return launch_dft_RG<R, 4>(X, ldx, rows, Y, ldy, p, s);
+    if (need <= 8)
+        return launch_dft_RG<R, 8>(X, ldx, rows, Y, ldy, p, s);
+    if (need <= 12)
+        return launch_dft_RG<R, 12>(X, ldx, rows, Y, ldy, p, s);
+    return launch_dft_RG<R, 16>(X, ldx, rows, Y, ldy, p, s);
 }
 
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,

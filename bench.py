@@ -323,6 +323,26 @@ def run_gw(args):
             ctx.P_to_G(w.gcut, PG_out=PGv)
             torch.cuda.synchronize()
             variants[prec] = {"ms_per_step": a.elapsed_time(b) / n, "PG": PGv.cpu().numpy()}
+        # the g-space route: sphere transforms of the pair densities and an N_g x N_g update (no P)
+        ctx.load_states(psi_d, E, dims, w.nv)
+        ctx.build_PG(w.gcut, args.precision)
+        ctx.eps_inv("cholesky")
+        torch.cuda.synchronize()
+        n = 5
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            ctx.load_states(psi_d, E, dims, w.nv)
+            ctx.build_PG(w.gcut, args.precision)
+            ctx.eps_inv("cholesky")
+        b.record(stream)
+        torch.cuda.synchronize()
+        PGv = torch.empty((ng, ng), dtype=torch.complex64, device=dev)
+        ctx.build_PG(w.gcut, args.precision, PG_out=PGv)
+        torch.cuda.synchronize()
+        variants["gspace_" + args.precision] = {"ms_per_step": a.elapsed_time(b) / n, "PG": PGv.cpu().numpy(),
+                                                "route": "gw_build_PG: sphere transforms of the pair densities, "
+                                                         "N_g x N_g rank-k update, no P(r,r')"}
     ctx.close()
 
     peaks, peak_src = load_peaks()

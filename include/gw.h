@@ -133,6 +133,24 @@ GW_API gw_status gw_build_P(gw_ctx *ctx, int precision, void *P_out);
 GW_API gw_status gw_P_to_G(gw_ctx *ctx, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out);
 
 /*
+ * P~ without P(r,r'): the g-space route of Sec. 4.1 (Eq. gpsaceP), written with the pair
+ * densities of Eq. (fdef):
+ *   M_k(G) = sum_r exp(-i G.r) f_k(r)       (sphere transform of each pair density),
+ *   P~(G, G') = -sum_k M_k(G) conj(M_k(G'))  (Hermitian rank-k update of N_g x N_g).
+ * It equals gw_build_P followed by gw_P_to_G in exact arithmetic, and needs about
+ * N_g^2 / N_r^2 of its rank-k work (plus k sphere transforms).
+ *   precision  GW_PREC_FP16X3 or GW_PREC_BF16X3: the update runs on the 16-bit tensor-core kernel
+ *              with the operand scaled by a power of two from max |M|.
+ *   gcut, ng_out, gvec_out, max_ng, PG_out  as gw_P_to_G.
+ * Requires gw_load_states; afterwards gw_eps_inv may be called, while P (GW_BUF_P) is not
+ * available until gw_build_P.  Device memory: k N_r + k N_g complex64 and the 16-bit planes.
+ * Timing slots (gw_get_times): [0] pair densities, [2] their sphere transforms, [3] the N_g
+ * update.
+ */
+GW_API gw_status gw_build_PG(gw_ctx *ctx, int precision, int gcut, int *ng_out, int *gvec_out, int max_ng,
+                             void *PG_out);
+
+/*
  * eps_GG' = delta_GG' - sqrt(V(G)) P~_GG' sqrt(V(G')) and its inverse, both complex128 and
  * formed in FP64 (Sec. 5.1).  eps_out / epsinv_out: NULL, or N_g x N_g complex128 buffers on
  * the device or the host (host buffers are filled before the call returns).  This call

@@ -217,12 +217,15 @@ gw_status build_plan(Ctx &c, int gcut)
         const std::array<int, 2> key = {g[i][1], g[i][2]};
         gmap[2 * i + 1] = static_cast<int>(std::lower_bound(dpairs.begin(), dpairs.end(), key) - dpairs.begin());
     }
-    std::vector<float2> tw;
+    std::vector<float2> tw;  // exp(+2 pi i t / n_a) for the three axes, then the conjugated copy
     for (int a = 0; a < 3; ++a)
         for (int t = 0; t < n[a]; ++t) {
             const double ph = 2.0 * PI * t / n[a];
             tw.push_back(make_float2(static_cast<float>(std::cos(ph)), static_cast<float>(std::sin(ph))));
         }
+    const size_t ntw = tw.size();
+    for (size_t t = 0; t < ntw; ++t)
+        tw.push_back(make_float2(tw[t].x, -tw[t].y));
     const size_t ints = (size_t)c3 + 2 * cd + 2 * ng;
     const size_t int_bytes = ((ints * sizeof(int) + 15) / 16) * 16;
     const size_t bytes = int_bytes + tw.size() * sizeof(float2);
@@ -244,6 +247,7 @@ gw_status build_plan(Ctx &c, int gcut)
     p.disk = c.d_plan_mem + c3;
     p.gmap = c.d_plan_mem + c3 + 2 * cd;
     p.tw = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(c.d_plan_mem) + int_bytes);
+    p.twc = p.tw + ntw;
 
     c.gvec.assign(3 * ng, 0);
     std::vector<double> sv(ng, 0.0);
@@ -335,6 +339,7 @@ void Ctx::release()
     dfree(d_F);
     dfree(d_P);
     dfree(d_tiles);
+    dfree(d_tiles_g);
     dfree(d_plan_mem);
     dfree(d_Q);
     dfree(d_QT);
@@ -694,6 +699,79 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
     GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
     GW_CUDA(launch_dft_rows(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, s), "column transform");
     GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
+    record(c, 5);
+    if (PG_out)
+        GW_CUDA(cudaMemcpyAsync(PG_out, c.d_PG, (size_t)ng * ng * sizeof(float2), cudaMemcpyDefault, s),
+                "copy P~ out");
+    if (ng_out)
+        *ng_out = ng;
+    if (gvec_out)
+        std::memcpy(gvec_out, c.gvec.data(), (size_t)3 * ng * sizeof(int));
+    c.PG_ready = true;
+    return GW_OK;
+}
+
+// P~ by the g-space route (Eq. gpsaceP): M_k(G) = sum_r exp(-iG.r) f_k(r) for every pair density
+// f_k, then P~(G, G') = -sum_k M_k(G) conj(M_k(G')) as a rank-k update of N_g x N_g.  P(r,r') is
+// never formed.
+gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.loaded)
+        return fail(c, GW_E_NOT_READY, "gw_build_PG before gw_load_states");
+    if (precision != GW_PREC_FP16X3 && precision != GW_PREC_BF16X3)
+        return fail(c, GW_E_INVALID, "gw_build_PG takes GW_PREC_FP16X3 or GW_PREC_BF16X3, not %d", precision);
+    const int nmin = std::min(c.n1, std::min(c.n2, c.n3));
+    if (gcut < 0 || 4LL * gcut >= (long long)nmin * nmin)
+        return fail(c, GW_E_INVALID, "gcut %d must satisfy 0 <= 4 gcut < min(n)^2 = %d", gcut, nmin * nmin);
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    if (gcut != c.gcut)
+        GW_TRY(build_plan(c, gcut));
+    const int ng = c.ng;
+    if (gvec_out && ng > max_ng)
+        return fail(c, GW_E_INVALID, "N_g = %d exceeds max_ng = %d", ng, max_ng);
+    if (!dft_supported(c.plan))
+        return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", ng);
+    cudaStream_t s = c.stream;
+    const bool bf16 = precision == GW_PREC_BF16X3;
+    const int k = c.k, kpad = ((k + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
+    const int ng_pad = ((ng + 255) / 256) * 256;
+    // buffers: pair densities [k][nr_pad] complex64 in F, their transforms [k][ng] in Q, the 16-bit
+    // planes of the transforms in QT, the result in PG
+    GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
+    GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k * ng * sizeof(float2), "pair-density transforms"));
+    GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad * ng_pad * 2 * 4, "transform planes"));
+    GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+    if (!c.d_small)
+        GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");
+    if (c.tiles_g_pad != ng_pad) {
+        const auto t = herk_tiles(ng_pad, HERK16_T, HERK16_T);
+        GW_TRY(ensure(c, c.d_tiles_g, c.cap.tiles_g, t.size() * sizeof(int2), "tile list (N_g)"));
+        GW_CUDA(cudaMemcpy(c.d_tiles_g, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice), "tile upload");
+        c.n_tiles_g = static_cast<int>(t.size());
+        c.tiles_g_pad = ng_pad;
+    }
+    c.F_prec = -1;  // F now holds plain pair densities, not the operand of gw_build_P
+    c.P_ready = c.PG_ready = c.eps_ready = false;
+    const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+    int *scale_exp = reinterpret_cast<int *>(c.d_small + 1);
+    float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
+
+    record(c, 0);
+    GW_CUDA(launch_pair_density(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, GW_PREC_FP32_SIMT, c.d_F, s),
+            "pair densities");
+    record(c, 1);
+    record(c, 3);
+    GW_CUDA(launch_dft_rows(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, s, true), "pair-density transforms");
+    record(c, 4);
+    GW_CUDA(launch_planes16_from_c64(c.d_Q, k, ng, ng, kpad, ng_pad, bf16, c.d_small, scale_exp,
+                                     reinterpret_cast<uint16_t *>(c.d_QT), s),
+            "transform planes");
+    GW_CUDA(launch_herk16(reinterpret_cast<const uint16_t *>(c.d_QT), bf16, kpad, ng, ng_pad, c.d_tiles_g,
+                          c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s),
+            "rank-k update in G space");
     record(c, 5);
     if (PG_out)
         GW_CUDA(cudaMemcpyAsync(PG_out, c.d_PG, (size_t)ng * ng * sizeof(float2), cudaMemcpyDefault, s),

@@ -38,6 +38,7 @@ struct DftPlan {
     int *disk;     // [cd*2] (m2, index into m3list) (device)
     int *gmap;     // [ng*2] (m1, index into disk) (device)
     float2 *tw;    // [n1 + n2 + n3] exp(+2 pi i t / n_a), FP64-derived (device)
+    float2 *twc;   // the same table conjugated: exp(-2 pi i t / n_a)
 };
 
 struct Ctx {
@@ -71,6 +72,8 @@ struct Ctx {
     bool P_ready = false;
     int2 *d_tiles = nullptr;        // HERK tile list
     int n_tiles = 0, tiles_rb = 0;
+    int2 *d_tiles_g = nullptr;      // tile list of the N_g x N_g update (g-space route)
+    int n_tiles_g = 0, tiles_g_pad = -1;
 
     // G space
     int gcut = -1, ng = 0;
@@ -98,7 +101,7 @@ struct Ctx {
 
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
-        size_t psi, psi128, psiT, E, sw, F, P, tiles, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
+        size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -141,6 +144,10 @@ cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_
 cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
                           cudaStream_t s);
+// 16-bit hi/lo operand planes of a complex64 matrix M[k][j] (k < rows, j < cols, row stride ld)
+// for launch_herk16 with nr = cols, nr_pad = cols_pad; the scale exponent comes from max |M|.
+cudaError_t launch_planes16_from_c64(const float2 *M, int rows, int cols, long ld, int kpad, int cols_pad, bool bf16,
+                                     unsigned *bound_bits, int *scale_exp, uint16_t *F, cudaStream_t s);
 
 // k_herk16p.cu: persistent multi-instance rank-k update.  One job per instance; tiles are
 // (job, 128-row block of r, 128-row block of r', 0) in the order CTAs take them (tile t goes to
@@ -157,8 +164,9 @@ cudaError_t launch_herk16p(const HerkJob *jobs, const int4 *tiles, int n_tiles, 
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
 bool dft_supported(const DftPlan &p);  // sphere small enough for the transform kernel
+// negative_exponent: exp(-iG.r) instead of exp(+iG.r) (the conjugated twiddle table)
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
-                            const DftPlan &p, cudaStream_t s);
+                            const DftPlan &p, cudaStream_t s, bool negative_exponent = false);
 cudaError_t launch_conj_transpose(const float2 *in, int rows, int cols, float2 *out, cudaStream_t s);
 cudaError_t launch_hermitize(float2 *A, int n, cudaStream_t s);  // A <- (A + A^H) / 2
 

@@ -280,7 +280,7 @@ bool dft_supported(const DftPlan &p)
 
 template <int R, int GPT>
 static cudaError_t launch_dft_RG(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const float2 *tw)
 {
     const size_t smem = layout_for(p.n, p.ng, p.c3, p.cd, R).total;
     cudaError_t e =
@@ -288,39 +288,40 @@ static cudaError_t launch_dft_RG(const float2 *X, long long ldx, int rows, float
     if (e != cudaSuccess)
         return e;
     dft_rows_kernel<R, GPT><<<(rows + R - 1) / R, DFT_THREADS, smem, s>>>(
-        X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2], p.ng, p.c3, p.cd, p.m3list, p.disk, p.gmap, p.tw);
+        X, ldx, rows, Y, ldy, p.n[0], p.n[1], p.n[2], p.ng, p.c3, p.cd, p.m3list, p.disk, p.gmap, tw);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_dft_R(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                                cudaStream_t s)
+                                cudaStream_t s, const float2 *tw)
 {
     const int need = (R * p.ng + DFT_THREADS - 1) / DFT_THREADS;  // stage-3 outputs per thread
     if (need <= 4)
-        return launch_dft_RG<R, 4>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_RG<R, 4>(X, ldx, rows, Y, ldy, p, s, tw);
     if (need <= 8)
-        return launch_dft_RG<R, 8>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_RG<R, 8>(X, ldx, rows, Y, ldy, p, s, tw);
     if (need <= 12)
-        return launch_dft_RG<R, 12>(X, ldx, rows, Y, ldy, p, s);
-    return launch_dft_RG<R, 16>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_RG<R, 12>(X, ldx, rows, Y, ldy, p, s, tw);
+    return launch_dft_RG<R, 16>(X, ldx, rows, Y, ldy, p, s, tw);
 }
 
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                            cudaStream_t s)
+                            cudaStream_t s, bool negative_exponent)
 {
+    const float2 *tw = negative_exponent ? p.twc : p.tw;
     if (rows <= 0)
         return cudaSuccess;
     if (!dft_supported(p))
         return cudaErrorInvalidValue;
     switch (rows_per_cta(p)) {
     case 4:
-        return launch_dft_R<4>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_R<4>(X, ldx, rows, Y, ldy, p, s, tw);
     case 2:
-        return launch_dft_R<2>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_R<2>(X, ldx, rows, Y, ldy, p, s, tw);
     default:
-        return launch_dft_R<1>(X, ldx, rows, Y, ldy, p, s);
+        return launch_dft_R<1>(X, ldx, rows, Y, ldy, p, s, tw);
     }
 }
 

@@ -436,6 +436,52 @@ __global__ void pair_density16_kernel(const float2 *__restrict__ psiT, const flo
     }
 }
 
+// max |M[k][j]| over a complex64 matrix (rows x cols, row stride ld), as float bits.
+__global__ void absmax_c64_kernel(const float2 *__restrict__ M, int rows, int cols, long ld, unsigned *bound_bits)
+{
+    float best = 0.f;
+    const size_t total = (size_t)rows * cols;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = static_cast<int>(i / cols), j = static_cast<int>(i - (size_t)k * cols);
+        const float2 z = M[(size_t)k * ld + j];
+        best = fmaxf(best, sqrtf(z.x * z.x + z.y * z.y));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(bound_bits, __float_as_uint(best));
+}
+
+// The 16-bit hi/lo planes of a complex64 matrix M[k][j] (k < rows, j < cols), in the operand
+// layout of herk16_kernel with the column index j in the place of r: row k of M is one "pair
+// density" of the rank-k update, scaled by 2^scale_exp and split as pair_density16_kernel does.
+template <bool BF16>
+__global__ void planes16_from_c64_kernel(const float2 *__restrict__ M, int rows, int cols, long ld, int kpad,
+                                         int cols_pad, const int *__restrict__ scale_exp, uint16_t *__restrict__ F)
+{
+    const float s = ldexpf(1.0f, *scale_exp);
+    const size_t per_chunk = (size_t)cols_pad * KC16;
+    const size_t total = (size_t)(kpad / KC16) * per_chunk;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t kc = i / per_chunk;
+        const int rem = static_cast<int>(i - kc * per_chunk);
+        const int j = (rem >> 7) * 8 + ((rem & 63) >> 3);
+        const int k = static_cast<int>(kc) * KC16 + ((rem & 127) >> 6) * 8 + (rem & 7);
+        float fr = 0.f, fi = 0.f;
+        if (j < cols && k < rows) {
+            const float2 z = M[(size_t)k * ld + j];
+            fr = z.x * s;
+            fi = z.y * s;
+        }
+        const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi);
+        uint16_t *base = F + kc * NPL * per_chunk + rem;
+        base[0] = rh;
+        base[per_chunk] = to16<BF16>(fr - from16<BF16>(rh));
+        base[2 * per_chunk] = ih;
+        base[3 * per_chunk] = to16<BF16>(fi - from16<BF16>(ih));
+    }
+}
+
 int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
@@ -467,6 +513,26 @@ cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_
         pair_density16_kernel<true><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
     else
         pair_density16_kernel<false><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes16_from_c64(const float2 *M, int rows, int cols, long ld, int kpad, int cols_pad, bool bf16,
+                                     unsigned *bound_bits, int *scale_exp, uint16_t *F, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bound_bits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    absmax_c64_kernel<<<grid_for((size_t)rows * cols), 256, 0, s>>>(M, rows, cols, ld, bound_bits);
+    count_launches(1);
+    scale_exp_kernel<<<1, 1, 0, s>>>(bound_bits, 1.0f, bf16 ? 1 : 0, scale_exp);
+    count_launches(1);
+    const size_t total = (size_t)kpad * cols_pad;
+    if (bf16)
+        planes16_from_c64_kernel<true><<<grid_for(total), 256, 0, s>>>(M, rows, cols, ld, kpad, cols_pad, scale_exp, F);
+    else
+        planes16_from_c64_kernel<false><<<grid_for(total), 256, 0, s>>>(M, rows, cols, ld, kpad, cols_pad, scale_exp,
+                                                                        F);
     count_launches(1);
     return cudaGetLastError();
 }

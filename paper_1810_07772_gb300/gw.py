@@ -35,6 +35,7 @@ SIGNATURES = {
     "gw_load_states": (_i, [_vp, _i, _i, _i, _d, _i, _i, _vp, _i, _i, _vp]),
     "gw_build_P": (_i, [_vp, _i, _vp]),
     "gw_P_to_G": (_i, [_vp, _i, _c.POINTER(_i), _vp, _i, _vp]),
+    "gw_build_PG": (_i, [_vp, _i, _i, _c.POINTER(_i), _vp, _i, _vp]),
     "gw_eps_inv": (_i, [_vp, _i, _vp, _vp]),
     "gw_sync": (_i, [_vp]),
     "gw_get_buffer": (_i, [_vp, _i, _c.POINTER(_vp), _c.POINTER(_sz)]),
@@ -190,6 +191,17 @@ class Context:
         ng = ctypes.c_int(0)
         g = self._gbuf
         self._check(lib().gw_P_to_G(self._h, int(gcut), ctypes.byref(ng), g.ctypes.data, g.shape[0], _ptr(PG_out)))
+        self.ng = ng.value
+        self.gvec = g[: ng.value].copy()
+        return self.gvec
+
+    def build_PG(self, gcut, precision="fp16x3", PG_out=None):
+        """P~ by the g-space route (no P(r,r')); returns the integer G-vectors like P_to_G."""
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        ng = ctypes.c_int(0)
+        g = self._gbuf
+        self._check(lib().gw_build_PG(self._h, prec, int(gcut), ctypes.byref(ng), g.ctypes.data, g.shape[0],
+                                      _ptr(PG_out)))
         self.ng = ng.value
         self.gvec = g[: ng.value].copy()
         return self.gvec

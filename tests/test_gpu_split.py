@@ -50,3 +50,19 @@ def test_split_workload(split_case, prec, tol):
     assert np.linalg.norm(sub - ref) / np.linalg.norm(ref) <= tol
     assert np.linalg.norm(rows - s["Prows"]) / np.linalg.norm(s["Prows"]) <= tol
     assert resid <= 1e-12
+
+
+def test_split_workload_gspace_route(split_case):
+    """The same system by the g-space route (no 17 GB P(r,r')): FP16X3 within 1e-6 at the sampled
+    entries."""
+    s = split_case
+    w = s["w"]
+    dev = torch.device("cuda:0")
+    with gw.Context(0) as ctx:
+        ctx.load_states(torch.from_numpy(s["psi"].astype(np.complex64)).to(dev), s["E"], s["dims"], w.nv)
+        g = ctx.build_PG(w.gcut, "fp16x3")
+        assert np.array_equal(g, s["g"])
+        sub = ctx.view("PG")[s["sel"]][:, s["sel"]].cpu().numpy()
+        ctx.eps_inv("cholesky")
+    ref = s["ref"]
+    assert np.linalg.norm(sub - ref) / np.linalg.norm(ref) <= 1e-6

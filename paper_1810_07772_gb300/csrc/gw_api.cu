@@ -340,6 +340,7 @@ void Ctx::release()
     dfree(d_P);
     dfree(d_tiles);
     dfree(d_tiles_g);
+    dfree(d_PG_parts);
     dfree(d_plan_mem);
     dfree(d_Q);
     dfree(d_QT);
@@ -760,8 +761,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
 
     record(c, 0);
-    GW_CUDA(launch_pair_density(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, GW_PREC_FP32_SIMT, c.d_F, s),
-            "pair densities");
+    GW_CUDA(launch_pair_density_rows(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, Fc, s), "pair densities");
     record(c, 1);
     record(c, 3);
     GW_CUDA(launch_dft_rows(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, s, true), "pair-density transforms");
@@ -769,8 +769,15 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     GW_CUDA(launch_planes16_from_c64(c.d_Q, k, ng, ng, kpad, ng_pad, bf16, c.d_small, scale_exp,
                                      reinterpret_cast<uint16_t *>(c.d_QT), s),
             "transform planes");
+    // one CTA per SM: split k so that tiles x splits fills the GPU
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device);
+    const int splits = std::max(1, std::min(kpad / HERK16_KC, nsm / std::max(1, c.n_tiles_g)));
+    if (splits > 1)
+        GW_TRY(ensure(c, c.d_PG_parts, c.cap.PG_parts, (size_t)splits * ng * ng * sizeof(float2), "split-k partials"));
     GW_CUDA(launch_herk16(reinterpret_cast<const uint16_t *>(c.d_QT), bf16, kpad, ng, ng_pad, c.d_tiles_g,
-                          c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s),
+                          c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s, splits,
+                          c.d_PG_parts),
             "rank-k update in G space");
     record(c, 5);
     if (PG_out)

@@ -74,6 +74,7 @@ struct Ctx {
     int n_tiles = 0, tiles_rb = 0;
     int2 *d_tiles_g = nullptr;      // tile list of the N_g x N_g update (g-space route)
     int n_tiles_g = 0, tiles_g_pad = -1;
+    float2 *d_PG_parts = nullptr;   // split-k partials of the N_g x N_g update
 
     // G space
     int gcut = -1, ng = 0;
@@ -101,7 +102,7 @@ struct Ctx {
 
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
-        size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
+        size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -122,6 +123,10 @@ cudaError_t launch_c128_to_c64(const double2 *in, size_t n, float2 *out, cudaStr
 cudaError_t launch_check_finite(const float2 *x, size_t n, uint32_t *err, cudaStream_t s);
 cudaError_t launch_weights(const double *E, int nv, int nc, float *sw, cudaStream_t s);
 // prec: 0 = TF32X3 planes, 2 = TF32X1 planes, 3 = plain complex64 [kpad][nr_pad]
+// Plain complex64 pair densities f [rows][nr_pad] (rows >= nv nc; extra rows and columns zero),
+// written with r contiguous through a shared-memory transpose.
+cudaError_t launch_pair_density_rows(const float2 *psiT, const float *sw, int nr, int nb, int nv, int nc, int rows,
+                                     int nr_pad, float2 *F, cudaStream_t s);
 cudaError_t launch_pair_density(const float2 *psiT, const float *sw, int nr, int nb, int nv, int nc,
                                 int kpad, int nr_pad, int prec, float *F, cudaStream_t s);
 
@@ -141,9 +146,11 @@ size_t herk16_smem_bytes();
 cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
                                   int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,
                                   cudaStream_t s);
+// splits > 1 (with a workspace P_parts of splits x nr^2 complex64): split-k over blockIdx.y, for
+// updates with too few tiles to fill the GPU; the partials are summed in a fixed order into P.
 cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
-                          cudaStream_t s);
+                          cudaStream_t s, int splits = 1, float2 *P_parts = nullptr);
 // 16-bit hi/lo operand planes of a complex64 matrix M[k][j] (k < rows, j < cols, row stride ld)
 // for launch_herk16 with nr = cols, nr_pad = cols_pad; the scale exponent comes from max |M|.
 cudaError_t launch_planes16_from_c64(const float2 *M, int rows, int cols, long ld, int kpad, int cols_pad, bool bf16,

@@ -51,7 +51,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(NTHREADS, 1)
     herk16_kernel(const uint16_t *__restrict__ F, int kpad, int nr, int nr_pad, const int2 *__restrict__ tiles,
                   float2 *__restrict__ P, const int *__restrict__ scale_exp, uint32_t *err, uint64_t wait_ns, int W,
-                  int L)
+                  int L, int split_chunks, long long P_split)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + PIPE_BYTES);
@@ -66,7 +66,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 tile = tiles[blockIdx.x];  // x: 128-row block of r, y: 128-row block of r'
-    const int nkc = kpad / KC16;
+    // split-k: blockIdx.y takes chunks [y split_chunks, (y + 1) split_chunks) and writes its own
+    // partial P at P + y P_split (the launcher sizes the splits so that none is empty)
+    const int kc_begin = blockIdx.y * split_chunks;
+    const int nkc = max(0, min(split_chunks, kpad / KC16 - kc_begin));
+    F += (size_t)kc_begin * NPL * nr_pad * KC16;
+    P += (size_t)blockIdx.y * P_split;
     const int nwin = (nkc + W - 1) / W;
 
     if (threadIdx.x == 0) {
@@ -537,27 +542,54 @@ cudaError_t launch_planes16_from_c64(const float2 *M, int rows, int cols, long l
     return cudaGetLastError();
 }
 
+// Sum of the split-k partials of the rank-k update, in a fixed order.
+__global__ void sum_parts_kernel(const float2 *__restrict__ parts, int nparts, size_t n, float2 *__restrict__ out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 a = parts[i];
+        for (int p = 1; p < nparts; ++p) {
+            const float2 b = parts[(size_t)p * n + i];
+            a.x += b.x;
+            a.y += b.y;
+        }
+        out[i] = a;
+    }
+}
+
 cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
-                          cudaStream_t s)
+                          cudaStream_t s, int splits, float2 *P_parts)
 {
     if (n_tiles <= 0)
         return cudaSuccess;
+    const int nkc = kpad / KC16;
+    if (splits < 1 || !P_parts || nkc < 2)
+        splits = 1;
+    const int per = (nkc + splits - 1) / splits;
+    splits = (nkc + per - 1) / per;  // every split has at least one chunk
+    float2 *dst = splits > 1 ? P_parts : P;
+    const long long pstride = (long long)nr * nr;
     cudaError_t e;
+    dim3 grid(n_tiles, splits);
     if (bf16) {
         e = cudaFuncSetAttribute(herk16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess)
             return e;
-        herk16_kernel<true><<<n_tiles, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, P, scale_exp, err, wait_ns, W, L);
-        count_launches(1);
+        herk16_kernel<true><<<grid, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W, L,
+                                                         per, pstride);
     } else {
         e = cudaFuncSetAttribute(herk16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess)
             return e;
-        herk16_kernel<false><<<n_tiles, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, P, scale_exp, err, wait_ns, W,
-                                                             L);
-        count_launches(1);
+        herk16_kernel<false><<<grid, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W,
+                                                          L, per, pstride);
     }
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess || splits == 1)
+        return e;
+    const size_t n = (size_t)nr * nr;
+    sum_parts_kernel<<<grid_for(n), 256, 0, s>>>(P_parts, splits, n, P);
+    count_launches(1);
     return cudaGetLastError();
 }
 

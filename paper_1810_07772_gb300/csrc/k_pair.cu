@@ -126,7 +126,49 @@ __global__ void pair_density_plain_kernel(const float2 *__restrict__ psiT, const
     }
 }
 
+// Plain complex64 f [rows][nr_pad] by 32 x 32 tiles: threads along k read 32 consecutive psi_c(r)
+// of one r (psiT rows hold every state of one grid point), the tile is transposed in shared
+// memory, and rows of F are written with r contiguous.
+__global__ void __launch_bounds__(256) pair_density_tiled_kernel(const float2 *__restrict__ psiT,
+                                                                 const float *__restrict__ sw, int nr, int nb, int nv,
+                                                                 int nc, int rows, int nr_pad,
+                                                                 float2 *__restrict__ F)
+{
+    __shared__ float2 T[32][33];
+    const int k0 = blockIdx.y * 32, r0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int k = k0 + tx;
+    const bool kin = k < nv * nc;
+    const int v = kin ? k / nc : 0, c = kin ? k - v * nc : 0;
+    const float w = kin ? sw[k] : 0.f;
+    for (int dy = ty; dy < 32; dy += 8) {
+        const int r = r0 + dy;
+        float2 f = make_float2(0.f, 0.f);
+        if (kin && r < nr) {
+            const float2 a = psiT[(size_t)r * nb + v];
+            const float2 b = psiT[(size_t)r * nb + nv + c];
+            f = make_float2(fmaf(a.x, b.x, a.y * b.y) * w, fmaf(a.x, b.y, -a.y * b.x) * w);  // conj(a) b
+        }
+        T[dy][tx] = f;
+    }
+    __syncthreads();
+    for (int dy = ty; dy < 32; dy += 8) {
+        const int kk = k0 + dy, r = r0 + tx;
+        if (kk < rows && r < nr_pad)
+            F[(size_t)kk * nr_pad + r] = T[tx][dy];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pair_density_rows(const float2 *psiT, const float *sw, int nr, int nb, int nv, int nc, int rows,
+                                     int nr_pad, float2 *F, cudaStream_t s)
+{
+    dim3 grid((nr_pad + 31) / 32, (rows + 31) / 32);
+    pair_density_tiled_kernel<<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, rows, nr_pad, F);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_transpose_states(const float2 *psi, int nb, int nr, float2 *psiT, cudaStream_t s)
 {

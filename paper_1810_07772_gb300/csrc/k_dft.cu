@@ -147,8 +147,11 @@ __global__ void __launch_bounds__(DFT_THREADS, GPT <= 12 ? 3 : 2)
         }
         __syncthreads();
         const float2 *xb = Xs + (size_t)buf * R * plane;
-        // stage 1: A1[rho][j2][i3] = sum_j3 X[rho][j2][j3] e(m3 j3 / n3); one twiddle serves R rows
-        for (int t = tid; t < n2 * c3; t += DFT_THREADS) {
+        // stage 1: A1[rho][j2][i3] = sum_j3 X[rho][j2][j3] e(m3 j3 / n3).  Whole rounds of items take
+        // all R rows (one twiddle serves R rows); the items left over after the last whole round go
+        // one row each, so that round does not leave most threads waiting at the barrier.
+        const int nfull = n2 * c3, whole = (nfull / DFT_THREADS) * DFT_THREADS;
+        for (int t = tid; t < whole; t += DFT_THREADS) {
             const int j2 = t / c3, i3 = t - j2 * c3;
             const int step = m3[i3];
             float2 acc[R];
@@ -169,6 +172,21 @@ __global__ void __launch_bounds__(DFT_THREADS, GPT <= 12 ? 3 : 2)
 #pragma unroll
             for (int rho = 0; rho < R; ++rho)
                 A1[(rho * n2 + j2) * c3 + i3] = acc[rho];
+        }
+        for (int t = tid; t < (nfull - whole) * R; t += DFT_THREADS) {
+            const int item = whole + t / R, rho = t - (t / R) * R;
+            const int j2 = item / c3, i3 = item - j2 * c3;
+            const int step = m3[i3];
+            float2 acc = make_float2(0.f, 0.f);
+            int idx = 0;
+            const float2 *x = xb + rho * plane + j2 * n3;
+            for (int j3 = 0; j3 < n3; ++j3) {
+                cmac(acc, x[j3], tw3[idx]);
+                idx += step;
+                if (idx >= n3)
+                    idx -= n3;
+            }
+            A1[(rho * n2 + j2) * c3 + i3] = acc;
         }
         __syncthreads();
         // stage 2: A2[rho][d] = sum_j2 A1[rho][j2][i3(d)] e(m2(d) j2 / n2), one (row, d) per item:

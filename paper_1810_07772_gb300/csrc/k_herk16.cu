@@ -17,6 +17,7 @@
 // Tiles are 128 x 128, upper triangle only (i <= j); direct and mirrored stores as in the TF32
 // kernel, so every element of P is written exactly once at the end.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_fp16.h>
 
 #include "gw_internal.cuh"
@@ -404,40 +405,53 @@ __device__ __forceinline__ float from16(uint16_t u)
     }
 }
 
+// The 16-bit operand planes of the pair densities.  blockIdx.y is one 16-wide chunk of k, whose
+// (v, c) pairs and weights are resolved once in shared memory; threads run over the chunk in the
+// order it is stored (32-bit index arithmetic, no division per element), so every warp writes
+// 64 contiguous bytes per plane and reads psi_c(r) for 8 consecutive c of each r.
 template <bool BF16>
-__global__ void pair_density16_kernel(const float2 *__restrict__ psiT, const float *__restrict__ sw, int nr, int nb,
-                                      int nv, int nc, int kpad, int nr_pad, const int *__restrict__ scale_exp,
-                                      uint16_t *__restrict__ F)
+__global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__restrict__ psiT,
+                                                             const float *__restrict__ sw, int nr, int nb, int nv,
+                                                             int nc, int kpad, int nr_pad,
+                                                             const int *__restrict__ scale_exp,
+                                                             uint16_t *__restrict__ F)
 {
-    const float s = ldexpf(1.0f, *scale_exp);
-    const size_t per_chunk = (size_t)nr_pad * KC16;
-    const size_t total = (size_t)(kpad / KC16) * per_chunk;
-    const int k_valid = nv * nc;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t kc = i / per_chunk;
-        const int rem = static_cast<int>(i - kc * per_chunk);
-        const int r8 = rem >> 7;         // 8-row group (128 elements)
-        const int w = rem & 127;
-        const int k8 = w >> 6;           // which 16-byte core matrix along k
-        const int rr = (w & 63) >> 3;    // row in the group
-        const int e = w & 7;             // element in the 16-byte row
-        const int r = r8 * 8 + rr;
-        const int k = static_cast<int>(kc) * KC16 + k8 * 8 + e;
+    __shared__ int s_v[KC16], s_c[KC16];
+    __shared__ float s_w[KC16];
+    const int kc = blockIdx.y;
+    if (threadIdx.x < KC16) {
+        const int k = kc * KC16 + threadIdx.x;
+        const float s = ldexpf(1.0f, *scale_exp);
+        if (k < nv * nc) {
+            const int v = k / nc;
+            s_v[threadIdx.x] = v;
+            s_c[threadIdx.x] = nv + (k - v * nc);
+            s_w[threadIdx.x] = sw[k] * s;
+        } else {
+            s_v[threadIdx.x] = 0;
+            s_c[threadIdx.x] = 0;
+            s_w[threadIdx.x] = 0.f;  // padding k: zero operand
+        }
+    }
+    __syncthreads();
+    const int per_chunk = nr_pad * KC16;
+    uint16_t *Fc = F + (size_t)kc * NPL * per_chunk;
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < per_chunk; rem += gridDim.x * blockDim.x) {
+        const int r = (rem >> 7) * 8 + ((rem & 63) >> 3);  // 8-row group, row in the group
+        const int kk = ((rem & 127) >> 6) * 8 + (rem & 7);  // 16-byte core matrix along k, element
         float fr = 0.f, fi = 0.f;
-        if (r < nr && k < k_valid) {
-            const int v = k / nc, c = k - v * nc;
-            const float2 a = psiT[(size_t)r * nb + v];
-            const float2 b = psiT[(size_t)r * nb + nv + c];
-            const float wv = sw[k] * s;
-            fr = fmaf(a.x, b.x, a.y * b.y) * wv;   // conj(psi_v) psi_c
-            fi = fmaf(a.x, b.y, -a.y * b.x) * wv;
+        const float w = s_w[kk];
+        if (r < nr && w != 0.f) {
+            const float2 a = psiT[(size_t)r * nb + s_v[kk]];
+            const float2 b = psiT[(size_t)r * nb + s_c[kk]];
+            fr = fmaf(a.x, b.x, a.y * b.y) * w;   // conj(psi_v) psi_c
+            fi = fmaf(a.x, b.y, -a.y * b.x) * w;
         }
         const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi);
-        uint16_t *base = F + kc * NPL * per_chunk + rem;
-        base[0] = rh;
-        base[per_chunk] = to16<BF16>(fr - from16<BF16>(rh));
-        base[2 * per_chunk] = ih;
-        base[3 * per_chunk] = to16<BF16>(fi - from16<BF16>(ih));
+        Fc[rem] = rh;
+        Fc[per_chunk + rem] = to16<BF16>(fr - from16<BF16>(rh));
+        Fc[2 * per_chunk + rem] = ih;
+        Fc[3 * per_chunk + rem] = to16<BF16>(fi - from16<BF16>(ih));
     }
 }
 
@@ -513,11 +527,12 @@ cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_
     count_launches(1);
     scale_exp_kernel<<<1, 1, 0, s>>>(bound_bits, sw_max, bf16 ? 1 : 0, scale_exp);
     count_launches(1);
-    const size_t total = (size_t)kpad * nr_pad;
+    const int nchunks = kpad / KC16, per_chunk = nr_pad * KC16;
+    dim3 grid(std::max(1, std::min((per_chunk + 255) / 256, (152 * 16 + nchunks - 1) / nchunks)), nchunks);
     if (bf16)
-        pair_density16_kernel<true><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+        pair_density16_kernel<true><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
     else
-        pair_density16_kernel<false><<<grid_for(total), 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+        pair_density16_kernel<false><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
     count_launches(1);
     return cudaGetLastError();
 }

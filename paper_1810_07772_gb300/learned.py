@@ -6,7 +6,8 @@ order, and sets the learning-rate schedule:
 
 1. For every seeded system, run the plain method twice: P~ with the nc_keep lowest unoccupied
    states, and P~ with all of them.  The sum over unoccupied states c is the one in
-   Eq. (Pstatic).
+   Eq. (Pstatic).  Both go by the g-space route (gw_build_PG) unless route="rspace" asks for
+   P(r,r') and its transforms.
 2. Compute the per-entry features of the truncated P~ and the targets s (P~_all - P~_keep)
    (gw_corr_features, gw_corr_targets).
 3. Run Adam on minibatches drawn without replacement from all systems' entries
@@ -23,37 +24,43 @@ import numpy as np
 from . import gw
 
 
-def truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3"):
+def build_PG(ctx, gcut, precision="fp16x3", route="gspace"):
+    """P~ of the loaded states by either route; returns the G-vectors."""
+    if route == "gspace":
+        return ctx.build_PG(gcut, precision)
+    ctx.build_P(precision)
+    return ctx.P_to_G(gcut)
+
+
+def truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
     """(P~_keep, P~_all, gvec) of one system.  psi: [nv + nc_all][N_r] device tensor."""
     E = np.asarray(E_eV, dtype=np.float64)
     ctx.load_states(psi[: nv + nc_keep], E[: nv + nc_keep], dims, nv)
-    ctx.build_P(precision)
-    gvec = ctx.P_to_G(gcut)
+    gvec = build_PG(ctx, gcut, precision, route)
     PG_keep = ctx.view("PG").clone()
     ctx.load_states(psi, E, dims, nv)
-    ctx.build_P(precision)
-    ctx.P_to_G(gcut)
+    build_PG(ctx, gcut, precision, route)
     PG_all = ctx.view("PG").clone()
     return PG_keep, PG_all, gvec
 
 
-def system_samples(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3"):
+def system_samples(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
     """Features, targets and the pieces needed to judge a prediction, for one system."""
-    PG_keep, PG_all, gvec = truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision)
+    PG_keep, PG_all, gvec = truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision, route)
     ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
     X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
     T = gw.corr_targets(PG_keep, PG_all, scale)
     return {"X": X, "T": T, "scale": scale, "ratio": ratio, "PG_keep": PG_keep, "PG_all": PG_all, "gvec": gvec}
 
 
-def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp16x3"):
+def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
     """Concatenated (X, T) over the seeded systems; make_states(seed) -> (psi on device, E_eV)."""
     import torch
 
     Xs, Ts = [], []
     for s in seeds:
         psi, E = make_states(s)
-        d = system_samples(ctx, psi, E, nv, nc_keep, dims, gcut, precision)
+        d = system_samples(ctx, psi, E, nv, nc_keep, dims, gcut, precision, route)
         Xs.append(d["X"])
         Ts.append(d["T"])
         del psi, d

@@ -144,3 +144,15 @@ def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def forward_f16act(params, X):
+    """Inference arithmetic of the tensor-core path: the outputs of layers 1 and 2 (the inputs of
+    the two 256 x 256 products, FP16 operands on both sides) are rounded to FP16; layer 3's output
+    feeds the last layer unrounded.  params should hold FP16-rounded weights (to_fp16_weights)."""
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = params
+    f16 = lambda a: a.astype(np.float16).astype(np.float64)  # noqa: E731
+    h1 = f16(np.tanh(np.asarray(X, dtype=np.float64) @ W1.T + b1))
+    h2 = f16(np.tanh(h1 @ W2.T + b2))
+    h3 = np.tanh(h2 @ W3.T + b3)
+    return h3 @ W4.T + b4

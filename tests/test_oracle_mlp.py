@@ -74,3 +74,22 @@ def test_adam_first_step_is_signed_learning_rate():
     assert np.allclose(th, -0.01 * np.sign(g), rtol=0, atol=1e-15)
     th2, _, _ = M.adam_step(th, g, m, v, 2, 0.01, eps=0.0)
     assert np.allclose(th2, -0.02 * np.sign(g), rtol=0, atol=1e-15)
+
+
+def test_f16_activation_forward_equals_forward_when_activations_are_exact():
+    """With W1 = W2 = 0 and biases atanh(1/2), atanh(1/4), the activations feeding the 256-wide
+    products are 1/2 and 1/4, exact in FP16: both forwards then agree bit for bit; with a random
+    network they differ by FP16 rounding only (2^-11 relative per activation)."""
+    rng = np.random.default_rng(8)
+    n_in, hidden = 4, 16
+    params = M.unpack(rng.standard_normal(M.n_params(n_in, hidden)) * 0.3, n_in, hidden)
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = params
+    W1[:] = 0
+    b1[:] = np.arctanh(0.5)
+    W2[:] = 0
+    b2[:] = np.arctanh(0.25)
+    X = rng.standard_normal((7, n_in))
+    assert np.array_equal(M.forward_f16act(params, X), M.forward(params, X)[0])
+    params = M.unpack(rng.standard_normal(M.n_params(n_in, hidden)) * 0.3, n_in, hidden)
+    a, b = M.forward_f16act(params, X), M.forward(params, X)[0]
+    assert 0 < np.abs(a - b).max() <= 2.0 ** -9 * np.abs(b).max()

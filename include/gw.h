@@ -335,6 +335,17 @@ GW_API gw_status gw_mlp_get_params(gw_mlp *m, float *theta, int on_device);
 /* Inference: Y[n][2] = network(X[n][n_in]), in chunks of max_batch rows. */
 GW_API gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y);
 
+/* Inference on the tensor cores: the same network with FP16 weights and FP32 accumulation, and
+ * the activations that enter the two 256 x 256 products (outputs of layers 1 and 2) rounded to
+ * FP16 - they are FP16 operands of tcgen05.mma kind::f16.  Layer 1 (n_in inputs) and the output
+ * layer run on CUDA cores inside the same two kernels.  Requires hidden = 256 and n_in <= 16
+ * (else GW_E_UNSUPPORTED).  Asynchronous; device-side waits are bounded and report through
+ * gw_mlp_check.  Y[n][2] as gw_mlp_forward. */
+GW_API gw_status gw_mlp_infer(gw_mlp *m, const float *X, long n, float *Y);
+
+/* Synchronise the handle's stream and return the status of its tensor-core kernels. */
+GW_API gw_status gw_mlp_check(gw_mlp *m);
+
 /* Loss and gradient of a batch, without an update.
  *   rows    NULL, or batch sample indices into X[.][n_in] and T[.][2] (a minibatch gather)
  *   grad    receives dL/dtheta (P floats, same flat order as the parameters)

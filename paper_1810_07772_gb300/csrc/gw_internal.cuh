@@ -1,5 +1,6 @@
 // Internal declarations shared by the translation units of libgw.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -167,6 +168,14 @@ struct HerkJob {
 };
 cudaError_t launch_herk16p(const HerkJob *jobs, const int4 *tiles, int n_tiles, int grid, bool bf16, uint32_t *err,
                            uint64_t wait_ns, int W, int L, cudaStream_t s);
+
+// k_mlp_tc.cu: tensor-core inference of the correction network (hidden width 256, n_in <= 16)
+size_t mlp_tc_h2_bytes(int rows);
+cudaError_t launch_mlp_tile_weights(const __half *W, uint8_t *Wt, cudaStream_t s);
+cudaError_t launch_mlp_tc_forward(const float *X, int n, int n_in, const __half *W1, const float *b1,
+                                  const uint8_t *W2t, const float *b2, const uint8_t *W3t, const float *b3,
+                                  const __half *W4, const float *b4, uint8_t *H2, float *Y, int num_sms,
+                                  uint32_t *err, uint64_t wait_ns, cudaStream_t s);
 
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);

@@ -347,6 +347,11 @@ struct gw_mlp {
     __half *theta16 = nullptr;
     float *H[3] = {}, *Da = nullptr, *Db = nullptr, *D4 = nullptr, *Y = nullptr, *part = nullptr;
     long step = 0;
+    // tensor-core inference: W2, W3 in the operand layout (valid while tiled == true), the FP16
+    // hidden layer between its two kernels, and a status word for their bounded waits
+    uint8_t *W2t = nullptr, *W3t = nullptr, *H2 = nullptr;
+    bool tiled = false;
+    uint32_t *d_err = nullptr;
     std::string last_error;
 };
 
@@ -613,7 +618,7 @@ gw_status gw_mlp_destroy(gw_mlp *m)
     else
         cudaDeviceSynchronize();
     void *ptrs[] = {m->theta, m->grad, m->m, m->v, m->theta16, m->H[0], m->H[1], m->H[2],
-                    m->Da,    m->Db,   m->D4, m->Y, m->part};
+                    m->Da,    m->Db,   m->D4, m->Y, m->part,  m->W2t, m->W3t, m->H2, m->d_err};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -646,6 +651,7 @@ gw_status gw_mlp_set_params(gw_mlp *m, const float *theta, int on_device)
     gw::count_launches(1);
     MLP_CUDA(cudaGetLastError(), "gw_mlp_set_params convert");
     m->step = 0;
+    m->tiled = false;
     if (!on_device)
         MLP_CUDA(cudaStreamSynchronize(m->stream), "gw_mlp_set_params sync");
     return GW_OK;
@@ -676,6 +682,54 @@ gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y)
     return GW_OK;
 }
 
+gw_status gw_mlp_infer(gw_mlp *m, const float *X, long n, float *Y)
+{
+    MLP_TRY(check_mlp(m));
+    if (!X || !Y || n < 0)
+        return mfail(m, GW_E_INVALID, "gw_mlp_infer: null pointer or negative size");
+    if (m->hidden != 256 || m->n_in > 16)
+        return mfail(m, GW_E_UNSUPPORTED, "gw_mlp_infer: the tensor-core path takes hidden = 256 and n_in <= 16");
+    if (n == 0)
+        return GW_OK;
+    if (!m->W2t) {
+        MLP_CUDA(cudaMalloc(&m->W2t, 256 * 256 * 2), "gw_mlp_infer weights");
+        MLP_CUDA(cudaMalloc(&m->W3t, 256 * 256 * 2), "gw_mlp_infer weights");
+        MLP_CUDA(cudaMalloc(&m->H2, gw::mlp_tc_h2_bytes(m->max_batch)), "gw_mlp_infer hidden layer");
+        MLP_CUDA(cudaMalloc(&m->d_err, sizeof(uint32_t)), "gw_mlp_infer status");
+        MLP_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(uint32_t), m->stream), "gw_mlp_infer status");
+    }
+    if (!m->tiled) {
+        MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[1], m->W2t, m->stream), "gw_mlp_infer tile W2");
+        MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[2], m->W3t, m->stream), "gw_mlp_infer tile W3");
+        m->tiled = true;
+    }
+    const uint64_t wait_ns = 2000000000ull;
+    for (long b0 = 0; b0 < n; b0 += m->max_batch) {
+        const int b = (int)std::min<long>(m->max_batch, n - b0);
+        MLP_CUDA(gw::launch_mlp_tc_forward(X + b0 * m->n_in, b, m->n_in, m->theta16 + m->off_w[0], m->theta + m->off_b[0],
+                                       m->W2t, m->theta + m->off_b[1], m->W3t, m->theta + m->off_b[2],
+                                       m->theta16 + m->off_w[3], m->theta + m->off_b[3], m->H2, Y + b0 * NOUT,
+                                       m->num_sms, m->d_err, wait_ns, m->stream),
+                 "gw_mlp_infer");
+    }
+    return GW_OK;
+}
+
+gw_status gw_mlp_check(gw_mlp *m)
+{
+    MLP_TRY(check_mlp(m));
+    MLP_CUDA(cudaStreamSynchronize(m->stream), "gw_mlp_check sync");
+    if (!m->d_err)
+        return GW_OK;
+    uint32_t word = 0;
+    MLP_CUDA(cudaMemcpy(&word, m->d_err, sizeof word, cudaMemcpyDeviceToHost), "gw_mlp_check readback");
+    if (word == 0)
+        return GW_OK;
+    cudaMemset(m->d_err, 0, sizeof(uint32_t));
+    return mfail(m, static_cast<gw_status>(word & 0xFF), "gw_mlp_infer: a device-side wait ran out (code %u)",
+                 word & 0xFF);
+}
+
 gw_status gw_mlp_grad(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, float *grad, float *loss)
 {
     MLP_TRY(check_mlp(m));
@@ -698,6 +752,7 @@ gw_status gw_mlp_train_step(gw_mlp *m, const float *X, const float *T, const int
         return mfail(m, GW_E_INVALID, "gw_mlp_train_step: bad optimiser constants");
     MLP_CUDA(loss_grad(m, X, T, rows, batch, loss_accum), "gw_mlp_train_step");
     m->step += 1;
+    m->tiled = false;
     const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
     const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
     adam_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(

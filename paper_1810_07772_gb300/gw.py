@@ -61,6 +61,8 @@ SIGNATURES = {
     "gw_mlp_set_params": (_i, [_vp, _vp, _i]),
     "gw_mlp_get_params": (_i, [_vp, _vp, _i]),
     "gw_mlp_forward": (_i, [_vp, _vp, _c.c_long, _vp]),
+    "gw_mlp_infer": (_i, [_vp, _vp, _c.c_long, _vp]),
+    "gw_mlp_check": (_i, [_vp]),
     "gw_mlp_grad": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp]),
     "gw_mlp_train_step": (_i, [_vp, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp]),
     "gw_corr_weight_ratio": (_i, [_vp, _i, _i, _i, _vp, _vp]),
@@ -387,6 +389,18 @@ class Mlp:
             Y = torch.empty((n, 2), dtype=torch.float32, device=self._dev)
         self._check(lib().gw_mlp_forward(self._h, _ptr(X), n, _ptr(Y)))
         return Y
+
+    def infer(self, X, Y=None):
+        """Tensor-core inference (FP16 activations into the 256-wide products)."""
+        import torch
+        n = X.shape[0]
+        if Y is None:
+            Y = torch.empty((n, 2), dtype=torch.float32, device=self._dev)
+        self._check(lib().gw_mlp_infer(self._h, _ptr(X), n, _ptr(Y)))
+        return Y
+
+    def check(self):
+        self._check(lib().gw_mlp_check(self._h))
 
     def grad(self, X, T, rows=None, batch=None):
         """(dL/dtheta as a device tensor, L) for one batch."""

@@ -102,11 +102,13 @@ def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1
     return losses
 
 
-def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, out=None):
-    """Learned form: P~_keep plus the predicted correction (in `out`, or a new tensor)."""
+def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, out=None, tensor_cores=True):
+    """Learned form: P~_keep plus the predicted correction (in `out`, or a new tensor).  The
+    prediction runs on the tensor cores (gw_mlp_infer) unless tensor_cores=False asks for the
+    FP32 forward of training (gw_mlp_forward)."""
     ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
     X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
-    Y = mlp.forward(X)
+    Y = mlp.infer(X) if tensor_cores else mlp.forward(X)
     P = PG_keep.clone() if out is None else out
     if out is not None and out.data_ptr() != PG_keep.data_ptr():
         P.copy_(PG_keep)

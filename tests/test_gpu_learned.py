@@ -69,6 +69,34 @@ def test_gradient_and_forward_match_oracle():
     assert np.linalg.norm(Y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
 
 
+def test_tensor_core_inference_matches_oracle():
+    """gw_mlp_infer (tcgen05 kind::f16, FP16 activations into the 256-wide products) against the
+    oracle forward with the same roundings; 1000 rows = several 128-row tiles, a ragged last tile,
+    and three chunks of 384 rows.  Tolerance: FP32 accumulation plus the odd activation that lands
+    on the other side of an FP16 rounding boundary (2^-11 of one term)."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((1000, N_IN)).astype(np.float32)
+    th = _theta(9)
+    params = M.unpack(M.to_fp16_weights(th.astype(np.float64), N_IN, HID), N_IN, HID)
+    y_ref = M.forward_f16act(params, X.astype(np.float64))
+    y_fp32 = M.forward(params, X.astype(np.float64))[0]
+    with gw.Mlp(N_IN, HID, max_batch=384, device=0) as net:
+        net.set_params(th)
+        Y = net.infer(torch.from_numpy(X).to(dev))
+        net.check()
+        Y = Y.cpu().numpy()
+        # a parameter update invalidates the tiled weights: inference must follow it
+        th2 = th.copy()
+        th2[: HID * N_IN] *= -1.0
+        net.set_params(th2)
+        Y2 = net.infer(torch.from_numpy(X).to(dev)).cpu().numpy()
+    assert np.linalg.norm(Y - y_ref) <= 1e-3 * np.linalg.norm(y_ref)
+    assert np.linalg.norm(Y - y_fp32) <= 1e-2 * np.linalg.norm(y_fp32)
+    p2 = M.unpack(M.to_fp16_weights(th2.astype(np.float64), N_IN, HID), N_IN, HID)
+    assert np.linalg.norm(Y2 - M.forward_f16act(p2, X.astype(np.float64))) <= 1e-3 * np.linalg.norm(Y2)
+
+
 def test_adam_step_matches_oracle():
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(12)

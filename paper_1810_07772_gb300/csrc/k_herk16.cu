@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_commit(&empty[s]);
                     *n_consumed = kc + 1;
                 }
-                if (ok)
+                // With W < STAGES the commit to the empty barrier of the window's last chunk already
+                // tells the promotion warps that the window is complete (a commit arrives once every
+                // earlier tcgen05 op has finished), and each such commit costs the tensor pipe ~100
+                // clocks; a separate window commit is kept only for W >= STAGES (see below).
+                if (ok && W >= STAGES)
                     mma_commit(&accf[b]);
             }
             mma_commit(done);  // arrives once every MMA issued above has completed
@@ -205,8 +209,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int wend = min(nwin, (seg + 1) * L);
             for (int win = seg * L; win < wend; ++win) {
                 const int b = win & 1;
+                // Window complete: with W < STAGES the empty barrier of its last chunk; that barrier
+                // cannot complete its next phase before this window is promoted (the chunk STAGES later
+                // lies in window win + 2 or later, whose MMAs wait for this promotion), so its parity is
+                // unambiguous.  With W >= STAGES the window has its own commit on accf[b].
+                const int kc_last = min(nkc, (win + 1) * W) - 1;
+                uint64_t *wbar = W < STAGES ? &empty[kc_last % STAGES] : &accf[b];
+                const uint32_t wpar = W < STAGES ? (uint32_t)((kc_last / STAGES) & 1) : (uint32_t)((win >> 1) & 1);
                 // warp-uniform outcome: the TMEM loads below are warp-collective
-                if (!__all_sync(0xffffffffu, mbar_wait(&accf[b], (win >> 1) & 1, wait_ns))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(wbar, wpar, wait_ns))) {
                     if (lane == 0)
                         record_error(err, GW_E_TIMEOUT, SITE_HERK_EPILOGUE, blockIdx.x);
                     *abort_flag = 1;

@@ -343,6 +343,7 @@ void Ctx::release()
     dfree(d_PG_parts);
     dfree(d_plan_mem);
     dfree(d_Q);
+    dfree(d_dftw);
     dfree(d_QT);
     dfree(d_PG);
     dfree(d_sv);
@@ -691,14 +692,15 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
     GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+    GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, std::max(c.nr, ng)), "transform workspace"));
     c.PG_ready = c.eps_ready = false;
     record(c, 3);
     // Q[r'][G] = sum_r P[r'][r] e^{+iG.r} = conj(P^(G, r')) since P is Hermitian
-    GW_CUDA(launch_dft_rows(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, s), "row transform");
+    GW_CUDA(launch_dft_rows_ws(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, c.d_dftw, s), "row transform");
     record(c, 4);
     // QT[G][r'] = conj(Q[r'][G]) = P^(G, r');  P~[G][G'] = sum_r' QT[G][r'] e^{+iG'.r'}
     GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
-    GW_CUDA(launch_dft_rows(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, s), "column transform");
+    GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
     GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
     record(c, 5);
     if (PG_out)
@@ -745,6 +747,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k * ng * sizeof(float2), "pair-density transforms"));
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad * ng_pad * 2 * 4, "transform planes"));
     GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+    GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, k), "transform workspace"));
     if (!c.d_small)
         GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");
     if (c.tiles_g_pad != ng_pad) {
@@ -764,7 +767,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     GW_CUDA(launch_pair_density_rows(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, Fc, s), "pair densities");
     record(c, 1);
     record(c, 3);
-    GW_CUDA(launch_dft_rows(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, s, true), "pair-density transforms");
+    GW_CUDA(launch_dft_rows_ws(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, c.d_dftw, s, true), "pair-density transforms");
     record(c, 4);
     GW_CUDA(launch_planes16_from_c64(c.d_Q, k, ng, ng, kpad, ng_pad, bf16, c.d_small, scale_exp,
                                      reinterpret_cast<uint16_t *>(c.d_QT), s),
@@ -991,6 +994,7 @@ gw_status batch_prepare(gw_batch &b)
         GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
         GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
         GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
+        GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, std::max(c.nr, ng)), "transform workspace"));
         GW_TRY(ensure(c, c.d_eps, c.cap.eps, (size_t)ng * ng * sizeof(double2), "eps"));
         GW_TRY(ensure(c, c.d_epsinv, c.cap.epsinv, (size_t)ng * ng * sizeof(double2), "eps^-1"));
         const size_t work = (size_t)3 * ng * ng + (size_t)NB * ng + (size_t)nblk * NB * NB;
@@ -1054,9 +1058,9 @@ gw_status batch_enqueue(gw_batch &b)
         Ctx &c = h->c;
         const int ng = c.ng;
         cudaStream_t s = b.stream;
-        GW_CUDA(launch_dft_rows(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, s), "row transform");
+        GW_CUDA(launch_dft_rows_ws(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, c.d_dftw, s), "row transform");
         GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
-        GW_CUDA(launch_dft_rows(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, s), "column transform");
+        GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
         GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
         GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
         GW_TRY(inverse_cholesky(c, s));

@@ -85,6 +85,7 @@ struct Ctx {
     float2 *d_Q = nullptr;          // [nr][ng]  row transform
     float2 *d_QT = nullptr;         // [ng][nr]  conj-transposed
     float2 *d_PG = nullptr;         // [ng][ng]
+    float2 *d_dftw = nullptr;       // sphere-transform workspace [rows][n1][cd]
     double *d_sv = nullptr;         // [ng] sqrt(V(G))
     size_t G_cap = 0;               // ng capacity of the G-space buffers
     bool PG_ready = false;
@@ -103,7 +104,8 @@ struct Ctx {
 
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
-        size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, sv, eps, epsinv, work, scal;
+        size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, dftw, sv, eps, epsinv, work,
+            scal;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -180,6 +182,11 @@ cudaError_t launch_mlp_tc_forward(const float *X, int n, int n_in, const __half 
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
 bool dft_supported(const DftPlan &p);  // sphere small enough for the transform kernel
+// Two-kernel form with a workspace of dft_work_bytes(p, rows) (stages 1 and 2 per plane, stage 3
+// per row).
+size_t dft_work_bytes(const DftPlan &p, int rows);
+cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
+                               float2 *work, cudaStream_t s, bool negative_exponent = false);
 // negative_exponent: exp(-iG.r) instead of exp(+iG.r) (the conjugated twiddle table)
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                             const DftPlan &p, cudaStream_t s, bool negative_exponent = false);

@@ -13,6 +13,8 @@
 // The path applies it twice: to the rows of P (P is Hermitian, so the conjugate of a row
 // transform with exp(+iG.r) is the column transform with exp(-iG.r)), and, after a conjugate
 // transpose, to the rows of that intermediate, which yields P~(G, G').
+#include <algorithm>
+
 #include "gw_internal.cuh"
 
 namespace gw {
@@ -271,6 +273,125 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
     A[(size_t)h * n + g] = make_float2(m.x, -m.y);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Two-kernel form.  Stages 1 and 2 of one (row, j1) plane are independent of every other plane, so
+// one warp takes one plane at a time: it stages the n2 x n3 plane in its own shared memory,
+// forms the c3 stage-1 lines and the cd stage-2 disk values with __syncwarp only, and writes
+// the cd values to a workspace [rows][n1][cd].  A second kernel does stage 3 per row (one CTA
+// per row: the row's n1 x cd values in shared memory, the N_g outputs over the threads).  The
+// sums run in the same order with the same twiddles as in dft_rows_kernel.
+constexpr int P12_WARPS = 8;
+
+__host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3)
+{
+    return align16(sizeof(float2) * ((size_t)n2 * n3 + (size_t)n2 * c3)) / sizeof(float2);
+}
+
+__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd)
+{
+    const size_t tables = align16(sizeof(float2) * (n[0] + n[1] + n[2]) + sizeof(int) * (c3 + 2 * cd));
+    return tables + P12_WARPS * p12_warp_floats2(n[1], n[2], c3) * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(P12_WARPS * 32)
+    dft_plane12_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int n2, int n3, int c3,
+                       int cd, const int *__restrict__ g_m3, const int *__restrict__ g_disk,
+                       const float2 *__restrict__ g_tw, float2 *__restrict__ Y2)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    float2 *tw = reinterpret_cast<float2 *>(smem);  // [n1 | n2 | n3]
+    int *m3 = reinterpret_cast<int *>(tw + n1 + n2 + n3);
+    int *disk = m3 + c3;
+    float2 *wbase = reinterpret_cast<float2 *>(
+        smem + align16(sizeof(float2) * (n1 + n2 + n3) + sizeof(int) * (c3 + 2 * cd)));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < n1 + n2 + n3; t += blockDim.x)
+        tw[t] = g_tw[t];
+    for (int t = tid; t < c3; t += blockDim.x)
+        m3[t] = g_m3[t];
+    for (int t = tid; t < 2 * cd; t += blockDim.x)
+        disk[t] = g_disk[t];
+    __syncthreads();
+    const float2 *tw2 = tw + n1, *tw3 = tw + n1 + n2;
+    const int plane = n2 * n3;
+    float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3);
+    float2 *a1 = xp + plane;
+    const long long ntasks = (long long)rows * n1;
+    for (long long task = (long long)blockIdx.x * P12_WARPS + warp; task < ntasks;
+         task += (long long)gridDim.x * P12_WARPS) {
+        const long long row = task / n1;
+        const int j1 = (int)(task - row * n1);
+        const float2 *src = X + row * ldx + (size_t)j1 * plane;
+        for (int q = lane; q < plane; q += 32)
+            xp[q] = src[q];
+        __syncwarp();
+        // stage 1: a1[j2][i3] = sum_j3 x[j2][j3] e(m3 j3 / n3)
+        for (int o = lane; o < n2 * c3; o += 32) {
+            const int j2 = o / c3, i3 = o - j2 * c3, step = m3[i3];
+            const float2 *x = xp + j2 * n3;
+            float2 acc = make_float2(0.f, 0.f);
+            int idx = 0;
+            for (int j3 = 0; j3 < n3; ++j3) {
+                cmac(acc, x[j3], tw3[idx]);
+                idx += step;
+                if (idx >= n3)
+                    idx -= n3;
+            }
+            a1[o] = acc;
+        }
+        __syncwarp();
+        // stage 2: y2[d] = sum_j2 a1[j2][i3(d)] e(m2(d) j2 / n2)
+        float2 *dst = Y2 + task * cd;
+        for (int d = lane; d < cd; d += 32) {
+            const int step = disk[2 * d], i3 = disk[2 * d + 1];
+            float2 acc = make_float2(0.f, 0.f);
+            int idx = 0;
+            for (int j2 = 0; j2 < n2; ++j2) {
+                cmac(acc, a1[j2 * c3 + i3], tw2[idx]);
+                idx += step;
+                if (idx >= n2)
+                    idx -= n2;
+            }
+            dst[d] = acc;
+        }
+        __syncwarp();  // the plane buffer is rewritten by the next task
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    dft_stage3_kernel(const float2 *__restrict__ Y2, int rows, int n1, int cd, int ng, const int *__restrict__ g_gmap,
+                      const float2 *__restrict__ g_tw, float2 *__restrict__ Y, long long ldy)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    float2 *ys = reinterpret_cast<float2 *>(smem);      // [n1][cd]
+    float2 *tw1 = ys + (size_t)n1 * cd;                 // [n1]
+    int *gmap = reinterpret_cast<int *>(tw1 + n1);      // [ng][2]
+    const int tid = threadIdx.x;
+    for (int t = tid; t < n1; t += blockDim.x)
+        tw1[t] = g_tw[t];
+    for (int t = tid; t < 2 * ng; t += blockDim.x)
+        gmap[t] = g_gmap[t];
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        __syncthreads();  // tables ready / previous row's reads done
+        const float2 *src = Y2 + row * n1 * cd;
+        for (int t = tid; t < n1 * cd; t += blockDim.x)
+            ys[t] = src[t];
+        __syncthreads();
+        for (int g = tid; g < ng; g += blockDim.x) {
+            const int step = gmap[2 * g], d = gmap[2 * g + 1];
+            float2 acc = make_float2(0.f, 0.f);
+            int idx = 0;
+            for (int j1 = 0; j1 < n1; ++j1) {
+                cmac(acc, ys[j1 * cd + d], tw1[idx]);
+                idx += step;
+                if (idx >= n1)
+                    idx -= n1;
+            }
+            Y[row * ldy + g] = acc;
+        }
+    }
+}
+
 constexpr size_t DFT_SMEM_TARGET = 56 * 1024;  // four CTAs per SM
 constexpr size_t DFT_SMEM_MAX = 220 * 1024;
 
@@ -323,6 +444,45 @@ static cudaError_t launch_dft_R(const float2 *X, long long ldx, int rows, float2
     if (need <= 12)
         return launch_dft_RG<R, 12>(X, ldx, rows, Y, ldy, p, s, tw);
     return launch_dft_RG<R, 16>(X, ldx, rows, Y, ldy, p, s, tw);
+}
+
+// The plane-per-warp form reads about two shared-memory words per complex FMA and the row-block
+// kernel 1.25 (one twiddle serves R rows), so the latter is the faster one for the long transforms
+// (the rows of P, the pair densities); the plane-per-warp form wins where rows are too few for
+// the row-block kernel to fill the GPU (the column pass, N_g rows).
+constexpr int WS_MAX_ROWS = 4096;
+
+size_t dft_work_bytes(const DftPlan &p, int rows)
+{
+    return (size_t)std::min(rows, WS_MAX_ROWS) * p.n[0] * p.cd * sizeof(float2);
+}
+
+cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
+                               float2 *work, cudaStream_t s, bool negative_exponent)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (rows > WS_MAX_ROWS || !work)
+        return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
+    const float2 *tw = negative_exponent ? p.twc : p.tw;
+    const size_t sm12 = p12_smem(p.n, p.c3, p.cd);
+    const size_t sm3 = sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
+    if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
+        return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
+    cudaError_t e = cudaFuncSetAttribute(dft_plane12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    if (e != cudaSuccess)
+        return e;
+    const long long ntasks = (long long)rows * p.n[0];
+    const int g12 = (int)std::min<long long>((ntasks + P12_WARPS - 1) / P12_WARPS, 152LL * 16);
+    dft_plane12_kernel<<<g12, P12_WARPS * 32, sm12, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.cd, p.m3list,
+                                                         p.disk, tw, work);
+    const int g3 = std::min(rows, 152 * 8);
+    dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,

@@ -116,3 +116,17 @@ def test_plain_workload_full_size():
     inv_ref = O.inverse_cholesky(O.eps_build(Pt, gref, w.cell_L))
     assert np.max(np.abs(inv - inv_ref)) <= 1e-6
     assert resid <= 1e-12
+
+
+@pytest.mark.slow
+def test_largest_grid_gspace_route():
+    """The largest grid gw_load_states takes, 64^3 (N_r = 262144), by the g-space route: P(r,r')
+    would be 550 GB, the route needs k N_r complex64 (0.14 GB here).  N_v = 4, N_c = 32, gcut 40
+    (about a thousand G): all of P~ against Eq. (gpsaceP), then eps^-1."""
+    dims, nv, nc, gcut = (64, 64, 64), 4, 32, 40
+    psi, E = inputs.make_states(64, nv, nc, 29)
+    gref = O.sphere(dims, gcut)
+    g, PG, inv, resid = gspace(psi, E, nv, dims, gcut)
+    assert np.array_equal(g, gref) and len(g) > 1000
+    assert rel(PG, O.P_gspace(psi, E, nv, dims, gref)) <= 1e-6
+    assert resid <= 1e-12

@@ -272,7 +272,7 @@ GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *
 
 /*
  * Window length of the 16-bit rank-k update: the tensor core accumulates `window_chunks` chunks
- * of 16 k (1..64, default 2) in TMEM before they are added into FP32 registers, and every
+ * of 16 k (1..64, default 3) in TMEM before they are added into FP32 registers, and every
  * `flush_windows` windows (1..4096, default 256) the registers are added into P.  Shorter windows
  * and flushes mean smaller accumulation error.
  */

@@ -30,7 +30,10 @@ Readings of the paper taken here (where it is silent or inconsistent):
 4. Units: energies arrive in eV and are divided by 27.211386245988; the cell is cubic with edge L
    (bohr), Omega = L^3, G = 2 pi m / L for integer m in FFT order.
 5. Sphere: all m with |m|^2 <= gcut, ordered by (|m|^2, m1, m2, m3) ascending, so G = 0 is first.
-6. Head at q = 0: V(G=0) is set to 0, so eps has a unit head and zero wings.
+6. Head at q = 0: V(G=0) is set to 0, so eps has a unit head and zero wings.  For q != 0 (given
+   in units of 2 pi / L) V(q + G) = 4 pi / (Omega |q + G|^2) for every G; the states are then the
+   periodic parts u_{v,k+q} (occupied rows) and u_{c,k} (unoccupied rows) of Sec. 4.1, and the
+   transforms are the same as at q = 0.
 7. Newton start: alpha = 1 / max_i sum_j |(A A^H)_ij| (the paper's A^T read as A^H for complex A,
    with absolute values so the row sums bound the spectral radius).
 """
@@ -247,9 +250,13 @@ def P_gspace_truncated(psi, E_eV, nv, nc_keep, dims, gvec):
 # ----------------------------------------------------------------------------- eps
 
 
-def coulomb(gvec, cell_L):
-    """V_c(G) = 4 pi / (Omega |G|^2) with G = 2 pi m / L, Omega = L^3 (Sec. 5.1); V_c(0) := 0."""
-    m2 = np.sum(np.asarray(gvec, dtype=np.float64) ** 2, axis=1)
+def coulomb(gvec, cell_L, q=None):
+    """V_c(q + G) = 4 pi / (Omega |q + G|^2) with G = 2 pi m / L, q = 2 pi q_frac / L and
+    Omega = L^3 (Sec. 5.1); V_c := 0 where q + G = 0 (the head at q = 0)."""
+    m = np.asarray(gvec, dtype=np.float64)
+    if q is not None:
+        m = m + np.asarray(q, dtype=np.float64)[None, :]
+    m2 = np.sum(m ** 2, axis=1)
     G2 = (2.0 * np.pi / cell_L) ** 2 * m2
     omega = cell_L ** 3
     V = np.zeros_like(G2)
@@ -258,9 +265,9 @@ def coulomb(gvec, cell_L):
     return V
 
 
-def eps_build(Pt, gvec, cell_L):
-    """eps_GG' = delta_GG' - sqrt(V(G)) P~_GG' sqrt(V(G')) (Sec. 5.1)."""
-    s = np.sqrt(coulomb(gvec, cell_L))
+def eps_build(Pt, gvec, cell_L, q=None):
+    """eps^q_GG' = delta_GG' - sqrt(V(q + G)) P~^q_GG' sqrt(V(q + G')) (Sec. 5.1)."""
+    s = np.sqrt(coulomb(gvec, cell_L, q))
     return np.eye(Pt.shape[0], dtype=np.complex128) - s[:, None] * np.asarray(Pt, np.complex128) * s[None, :]
 
 
@@ -317,13 +324,15 @@ def inverse_newton(A, tol=1e-11, max_iter=100):
 # ----------------------------------------------------------------------------- whole path
 
 
-def eps_inv_path(psi, E_eV, nv, dims, gcut, cell_L, route="gspace"):
+def eps_inv_path(psi, E_eV, nv, dims, gcut, cell_L, route="gspace", q=None):
     """States -> P~ -> eps -> eps^-1.  route 'rspace' goes through P(r,r') (small grids),
-    'gspace' through Eq. (gpsaceP).  Returns dict(gvec, Pt, eps, epsinv)."""
+    'gspace' through Eq. (gpsaceP).  For q != 0 the occupied rows of psi are u_{v,k+q} and the
+    unoccupied ones u_{c,k} (Sec. 4.1); the transforms are unchanged.  Returns dict(gvec, Pt, eps,
+    epsinv)."""
     gvec = sphere(dims, gcut)
     if route == "rspace":
         Pt = P_to_G(P_rspace(psi, E_eV, nv), dims, gvec)
     else:
         Pt = P_gspace(psi, E_eV, nv, dims, gvec)
-    eps = eps_build(Pt, gvec, cell_L)
+    eps = eps_build(Pt, gvec, cell_L, q)
     return {"gvec": gvec, "Pt": Pt, "eps": eps, "epsinv": inverse_cholesky(eps)}

@@ -265,3 +265,33 @@ def test_selected_entries_equal_full_gspace_route():
     assert np.max(np.abs(part - full[np.ix_(sel, sel)])) < 1e-15 * np.max(np.abs(full)) * 10
     Pr = O.P_to_G(O.P_rspace(psi, E, 3), dims, g)
     assert np.max(np.abs(part - Pr[np.ix_(sel, sel)])) < 1e-13
+
+
+def test_finite_q_closed_forms():
+    """q != 0 (Sec. 4.1 and 5.1).  (a) u_v = u_c = 1/sqrt(N_r), allowed when the two sets belong to
+    k + q and k: M(G) is a Kronecker delta at G = 0, so P~ has only a head entry 2/(E_v - E_c) and
+    eps^q_00 = 1 + 4 pi * 2 / (Omega |q|^2 (E_c - E_v)), with V(q) = 4 pi / (Omega |2 pi q / L|^2).
+    (b) plane waves m_a, m_b: the single entry sits at G = m_b - m_a with V(q + G)."""
+    dims, L, q = (6, 6, 6), 1.7, (0.25, -0.1, 0.05)
+    Eh = lambda e: e / 27.211386245988  # noqa: E731
+    psi, E = inputs.plane_wave_states(dims, [(0, 0, 0), (0, 0, 0)], [-2.0, 3.0])
+    r = O.eps_inv_path(psi, E, 1, dims, 3, L, route="gspace", q=q)
+    g = r["gvec"]
+    assert np.array_equal(g[0], [0, 0, 0])
+    want_P = 2.0 / (Eh(E[0]) - Eh(E[1]))
+    assert abs(r["Pt"][0, 0] - want_P) <= 1e-12 * abs(want_P)
+    assert np.abs(r["Pt"]).sum() - abs(r["Pt"][0, 0]) <= 1e-12 * abs(want_P)
+    q2 = (2 * np.pi / L) ** 2 * np.sum(np.asarray(q) ** 2)
+    e00 = 1.0 + 4 * np.pi * 2.0 / (L ** 3 * q2 * (Eh(E[1]) - Eh(E[0])))
+    assert abs(r["eps"][0, 0] - e00) <= 1e-12 * e00
+    assert abs(r["epsinv"][0, 0] - 1.0 / e00) <= 1e-12
+    # (b) plane waves at distinct m: entry at m_b - m_a, with |q + G|
+    psi, E = inputs.plane_wave_states(dims, [(1, 0, 0), (0, 1, 1)], [-1.0, 4.0])
+    r = O.eps_inv_path(psi, E, 1, dims, 3, L, route="gspace", q=q)
+    i = int(np.flatnonzero((r["gvec"] == [-1, 1, 1]).all(axis=1))[0])
+    qg2 = (2 * np.pi / L) ** 2 * np.sum((np.array([-1, 1, 1]) + np.asarray(q)) ** 2)
+    eii = 1.0 + 4 * np.pi * 2.0 / (L ** 3 * qg2 * (Eh(E[1]) - Eh(E[0])))
+    assert abs(r["epsinv"][i, i] - 1.0 / eii) <= 1e-12
+    # and the q -> 0 limit of V keeps the q = 0 convention (head 0) only at q = 0 itself
+    assert O.coulomb(np.array([[0, 0, 0]]), L)[0] == 0.0
+    assert O.coulomb(np.array([[0, 0, 0]]), L, q)[0] > 0.0

@@ -278,6 +278,18 @@ GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *
  */
 GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_windows);
 
+/*
+ * Wave vector q of eps^q (Sec. 4.1 and 5.1), in units of 2 pi / cell_L per axis (default 0).
+ * eps^q_GG' = delta_GG' - sqrt(V(q+G)) P~^q_GG' sqrt(V(q+G')), V(q+G) = 4 pi / (Omega |q+G|^2); only
+ * where q + G = 0 (the head at q = 0) is V set to 0.  For q != 0 the states passed to
+ * gw_load_states are periodic parts: the occupied rows u_{v,k+q} with energies E_{v,k+q}, the
+ * unoccupied rows u_{c,k} with E_{c,k}; the pair densities and transforms are the same as at q = 0
+ * (they need no orthogonality between the two sets).  V is recomputed at once for the current
+ * sphere (the call synchronises the context's stream), so the next gw_eps_inv uses it; P~ depends
+ * on q only through the states the caller loads.
+ */
+GW_API gw_status gw_set_q(gw_ctx *ctx, const double *q);
+
 /* Upper bound, in milliseconds, of any single device-side wait (default 2000).  A wait that
  * runs out makes its kernel record GW_E_TIMEOUT and return early. */
 GW_API gw_status gw_set_wait_limit(gw_ctx *ctx, double ms);

@@ -188,6 +188,23 @@ int mod(int a, int n)
     return r < 0 ? r + n : r;
 }
 
+// sqrt(V(q + G)) for the sphere in c.gvec: V = 4 pi / (Omega |q + G|^2), 0 where q + G = 0.
+gw_status upload_sqrt_v(Ctx &c)
+{
+    const int ng = c.ng;
+    std::vector<double> sv(ng, 0.0);
+    const double omega = c.cell_L * c.cell_L * c.cell_L;
+    const double gunit = 2.0 * PI / c.cell_L;
+    for (int i = 0; i < ng; ++i) {
+        const double a = c.gvec[3 * i] + c.q[0], b = c.gvec[3 * i + 1] + c.q[1], d = c.gvec[3 * i + 2] + c.q[2];
+        const double m2 = a * a + b * b + d * d;  // |q + G|^2 in units of (2 pi / L)^2
+        sv[i] = m2 > 0 ? std::sqrt(4.0 * PI / (omega * gunit * gunit * m2)) : 0.0;  // V(0) := 0 at q = 0
+    }
+    GW_TRY(ensure(c, c.d_sv, c.cap.sv, ng * sizeof(double), "sqrt(V) buffer"));
+    GW_CUDA(cudaMemcpy(c.d_sv, sv.data(), ng * sizeof(double), cudaMemcpyHostToDevice), "sqrt(V) upload");
+    return GW_OK;
+}
+
 gw_status build_plan(Ctx &c, int gcut)
 {
     const int n[3] = {c.n1, c.n2, c.n3};
@@ -250,18 +267,13 @@ gw_status build_plan(Ctx &c, int gcut)
     p.twc = p.tw + ntw;
 
     c.gvec.assign(3 * ng, 0);
-    std::vector<double> sv(ng, 0.0);
-    const double omega = c.cell_L * c.cell_L * c.cell_L;
-    const double gunit = 2.0 * PI / c.cell_L;
     for (int i = 0; i < ng; ++i) {
         c.gvec[3 * i] = g[i][0];
         c.gvec[3 * i + 1] = g[i][1];
         c.gvec[3 * i + 2] = g[i][2];
-        const double m2 = (double)g[i][0] * g[i][0] + (double)g[i][1] * g[i][1] + (double)g[i][2] * g[i][2];
-        sv[i] = m2 > 0 ? std::sqrt(4.0 * PI / (omega * gunit * gunit * m2)) : 0.0;  // V(0) := 0
     }
-    GW_TRY(ensure(c, c.d_sv, c.cap.sv, ng * sizeof(double), "sqrt(V) buffer"));
-    GW_CUDA(cudaMemcpy(c.d_sv, sv.data(), ng * sizeof(double), cudaMemcpyHostToDevice), "sqrt(V) upload");
+    c.ng = ng;
+    GW_TRY(upload_sqrt_v(c));
     c.gcut = gcut;
     c.ng = ng;
     return GW_OK;
@@ -447,6 +459,22 @@ gw_status gw_set_wait_limit(gw_ctx *h, double ms)
     if (!h || !(ms > 0.0) || ms > 600000.0)
         return GW_E_INVALID;
     h->c.wait_limit_ms = ms;
+    return GW_OK;
+}
+
+gw_status gw_set_q(gw_ctx *h, const double *q)
+{
+    if (!h || !q || !std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]))
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    for (int a = 0; a < 3; ++a)
+        c.q[a] = q[a];
+    c.eps_ready = false;
+    if (c.ng > 0 && c.gcut >= 0) {  // a sphere exists: the next gw_eps_inv uses V(q + G)
+        GW_CUDA(cudaSetDevice(c.device), "set device");
+        GW_CUDA(cudaStreamSynchronize(c.stream), "sync before sqrt(V) update");
+        GW_TRY(upload_sqrt_v(c));
+    }
     return GW_OK;
 }
 

@@ -58,6 +58,7 @@ struct Ctx {
     bool loaded = false;
     int n1 = 0, n2 = 0, n3 = 0, nr = 0, nv = 0, nc = 0, nb = 0;
     double cell_L = 1.0;
+    double q[3] = {0.0, 0.0, 0.0};  // wave vector of eps^q, in units of 2 pi / cell_L
     int k = 0, kpad = 0, nr_pad = 0;
 
     // device buffers (owned)

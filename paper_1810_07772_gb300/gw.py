@@ -43,6 +43,7 @@ SIGNATURES = {
     "gw_set_timing": (_i, [_vp, _i]),
     "gw_get_times": (_i, [_vp, _c.POINTER(_c.c_float)]),
     "gw_set_wait_limit": (_i, [_vp, _d]),
+    "gw_set_q": (_i, [_vp, _c.POINTER(_d)]),
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
@@ -236,6 +237,11 @@ class Context:
 
     def set_herk_window(self, window_chunks, flush_windows):
         self._check(lib().gw_set_herk_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def set_q(self, q):
+        """Wave vector of eps^q in units of 2 pi / cell_L (gw_set_q)."""
+        arr = (ctypes.c_double * 3)(*[float(x) for x in q])
+        self._check(lib().gw_set_q(self._h, arr))
 
     def set_wait_limit(self, ms):
         self._check(lib().gw_set_wait_limit(self._h, float(ms)))

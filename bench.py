@@ -461,6 +461,7 @@ def run_batch(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     herk = []
+    launches0 = ctxs[0].stats()["kernel_launches"]   # the library's launch counter is process-wide
     with ClockSampler(0) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -469,6 +470,7 @@ def run_batch(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
+    launches = int(ctxs[0].stats()["kernel_launches"] - launches0)  # graph replays count their kernels
     # sampled rows of the largest system's P against the FP64 loop (oracle)
     err = None
     if not args.no_baseline:
@@ -491,7 +493,7 @@ def run_batch(args):
             "roofline": {"bound": "tensor", "achieved": flop / (herk_ms * 1e-3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "frac": flop / (herk_ms * 1e-3) / 1e12 / peak, "traffic": None,
                          "kernel": "herk16p_kernel (persistent, all instances)", "herk_ms": herk_ms},
-            "P_rows_rel_err_largest": err, "clocks": clk.summary()}
+            "P_rows_rel_err_largest": err, "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(line))
     b.close()
     for c in ctxs:

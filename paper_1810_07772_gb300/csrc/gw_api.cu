@@ -946,6 +946,7 @@ struct gw_batch {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float herk_ms = 0.f;
     int runs = 0;
+    int graph_kernels = 0;          // kernel nodes of the captured pass (launches per replay)
     std::string last_error;
 };
 
@@ -1269,7 +1270,9 @@ gw_status gw_batch_run(gw_batch *b, int use_graph)
                 cudaGetLastError();
                 return bfail(bb, GW_E_CUDA, "stream capture could not start");
             }
+            const unsigned long long counted = g_launches.load();
             const gw_status st = batch_enqueue(bb);
+            g_launches.store(counted);  // captured launches run at replay time, where they are counted
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(bb.stream, &g);
             if (st != GW_OK || ec != cudaSuccess || !g) {
@@ -1284,8 +1287,21 @@ gw_status gw_batch_run(gw_batch *b, int use_graph)
                 drop_graph(bb);
                 return bfail(bb, GW_E_CUDA, "graph instantiation failed");
             }
+            size_t nn = 0;
+            bb.graph_kernels = 0;
+            if (cudaGraphGetNodes(bb.graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+                std::vector<cudaGraphNode_t> nodes(nn);
+                if (cudaGraphGetNodes(bb.graph, nodes.data(), &nn) == cudaSuccess)
+                    for (size_t i = 0; i < nn; ++i) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            ++bb.graph_kernels;
+                    }
+            }
+            cudaGetLastError();
         }
         GW_BCUDA(cudaGraphLaunch(bb.exec, bb.stream), "graph launch");
+        count_launches(bb.graph_kernels);
     }
     ++bb.runs;
     return batch_status(bb);

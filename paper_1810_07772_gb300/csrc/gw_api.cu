@@ -644,7 +644,7 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     if (precision == GW_PREC_FP32_SIMT)
         Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float2);
     else if (p16)
-        Fbytes = (size_t)c.kpad * c.nr_pad * 2 * 4;
+        Fbytes = (size_t)c.kpad * c.nr_pad * 2 * HERK16_NPL;
     else
         Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float) * (precision == GW_PREC_TF32X3 ? 4 : 2);
     GW_TRY(ensure(c, c.d_F, c.cap.F, Fbytes, "pair-density operand"));
@@ -773,7 +773,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     // planes of the transforms in QT, the result in PG
     GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k * ng * sizeof(float2), "pair-density transforms"));
-    GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad * ng_pad * 2 * 4, "transform planes"));
+    GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad * ng_pad * 2 * HERK16_NPL, "transform planes"));
     GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
     GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, k), "transform workspace"));
     if (!c.d_small)
@@ -1008,7 +1008,7 @@ gw_status batch_prepare(gw_batch &b)
         Ctx &c = b.ctxs[i]->c;
         const int kpad = ((c.k + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
         c.kpad = kpad;
-        const size_t Fbytes = (size_t)kpad * c.nr_pad * 2 * 4;
+        const size_t Fbytes = (size_t)kpad * c.nr_pad * 2 * HERK16_NPL;
         GW_TRY(ensure(c, c.d_F, c.cap.F, Fbytes, "pair-density operand"));
         if (!c.d_small)
             GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");

@@ -20,11 +20,13 @@ namespace gw {
 namespace {
 
 constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
-constexpr uint32_t A_BYTES = TM * KC16 * 2;
-constexpr uint32_t B_BYTES = TN * KC16 * 2;
-constexpr uint32_t NPL = 4;
-constexpr uint32_t STAGE_BYTES = NPL * (A_BYTES + B_BYTES);  // 32 KB
-constexpr int STAGES = 6;
+constexpr uint32_t PL = TM * KC16 * 2;  // 4 KB: one plane of one 128-row block
+constexpr uint32_t NPL = HERK16_NPL;
+// stage as in herk16_kernel: A planes Re hi, Re lo, Im hi, Im lo, then B regions [Im | Re | -Im]
+// of the hi part and of the lo part, so one N = 256 MMA fills the Re and Im columns of a window
+constexpr uint32_t B_OFF = 4 * PL;
+constexpr uint32_t STAGE_BYTES = 10 * PL;  // 40 KB
+constexpr int STAGES = 5;
 constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;
 constexpr uint32_t LBO = 128, SBO = 256;
 constexpr size_t SMEM = PIPE_BYTES + 256;
@@ -118,12 +120,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         break;
                     }
                     uint8_t *st = smem + s * STAGE_BYTES;
+                    const uint16_t *chunk = jb.F + (size_t)kc * NPL * per_chunk;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
-                    for (int p = 0; p < (int)NPL; ++p) {
-                        const uint16_t *region = jb.F + ((size_t)kc * NPL + p) * per_chunk;
-                        bulk_g2s(st + p * A_BYTES, region + a_off, A_BYTES, &full[s]);
-                        bulk_g2s(st + NPL * A_BYTES + p * B_BYTES, region + b_off, B_BYTES, &full[s]);
+                    for (int p = 0; p < 4; ++p)
+                        bulk_g2s(st + p * PL, chunk + p * per_chunk + a_off, PL, &full[s]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint8_t *bb = st + B_OFF + h * 3 * PL;
+                        bulk_g2s(bb, chunk + (2 + h) * per_chunk + b_off, PL, &full[s]);
+                        bulk_g2s(bb + PL, chunk + (0 + h) * per_chunk + b_off, PL, &full[s]);
+                        bulk_g2s(bb + 2 * PL, chunk + (4 + h) * per_chunk + b_off, PL, &full[s]);
                     }
                     *n_issued = g + 1;
                 }
@@ -133,8 +140,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
             constexpr uint32_t FMT = BF16 ? 1u : 0u;
-            constexpr uint32_t ID = mma_idesc(FMT, TM, TN, false);
-            constexpr uint32_t IDN = mma_idesc(FMT, TM, TN, true);
+            constexpr uint32_t ID = mma_idesc(FMT, TM, 2 * TN, false);
             const uint32_t sbase = smem_u32(smem);
             long long g = 0, gw = 0;  // chunks and windows consumed by this CTA
             bool ok = true;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d_re = tmem + b * 256, d_im = d_re + 128;
+                    const uint32_t d = tmem + b * 256;
                     const int kend = min(nkc, kc + W);
                     for (int c = 0; kc < kend; ++kc, ++c, ++g) {
                         const int s = (int)(g % STAGES);
@@ -164,25 +170,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                         tc_fence_after();
                         const uint32_t st = sbase + s * STAGE_BYTES;
-                        uint64_t a[NPL], bd[NPL];
-#pragma unroll
-                        for (int p = 0; p < (int)NPL; ++p) {
-                            a[p] = smem_desc(st + p * A_BYTES, LBO, SBO);
-                            bd[p] = smem_desc(st + NPL * A_BYTES + p * B_BYTES, LBO, SBO);
-                        }
+                        const uint64_t a_rh = smem_desc(st, LBO, SBO), a_rl = smem_desc(st + PL, LBO, SBO);
+                        const uint64_t a_ih = smem_desc(st + 2 * PL, LBO, SBO);
+                        const uint64_t a_il = smem_desc(st + 3 * PL, LBO, SBO);
+                        const uint64_t b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
+                        const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO);
+                        const uint64_t b_rl = smem_desc(st + B_OFF + 4 * PL, LBO, SBO);
+                        const uint64_t b_il = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
                         const uint32_t acc = c > 0 ? 1u : 0u;
-                        mma_f16(d_re, a[0], bd[0], ID, acc);
-                        mma_f16(d_re, a[0], bd[1], ID, 1);
-                        mma_f16(d_re, a[1], bd[0], ID, 1);
-                        mma_f16(d_re, a[2], bd[2], ID, 1);
-                        mma_f16(d_re, a[2], bd[3], ID, 1);
-                        mma_f16(d_re, a[3], bd[2], ID, 1);
-                        mma_f16(d_im, a[2], bd[0], ID, acc);
-                        mma_f16(d_im, a[2], bd[1], ID, 1);
-                        mma_f16(d_im, a[3], bd[0], ID, 1);
-                        mma_f16(d_im, a[0], bd[2], IDN, 1);
-                        mma_f16(d_im, a[0], bd[3], IDN, 1);
-                        mma_f16(d_im, a[1], bd[2], IDN, 1);
+                        mma_f16(d, a_rh, b_rh, ID, acc);  // Re += Ar Br, Im -= Ar Bi
+                        mma_f16(d, a_rh, b_rl, ID, 1);
+                        mma_f16(d, a_rl, b_rh, ID, 1);
+                        mma_f16(d, a_ih, b_ih, ID, 1);    // Re += Ai Bi, Im += Ai Br
+                        mma_f16(d, a_ih, b_il, ID, 1);
+                        mma_f16(d, a_il, b_ih, ID, 1);
                         mma_commit(&empty[s]);
                         *n_consumed = g + 1;
                     }

@@ -34,6 +34,7 @@ from paper_1810_07772_gb300 import inputs  # noqa: E402
 
 METRIC = "P-build TFLOP/s (4kN_r(N_r+1) per step, states resident -> eps^-1)"
 PRECISION = "fp16x3"
+INV_METHOD = "cholesky"
 WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
              "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41),
              "split": inputs.SPLIT, "batch": None, "learned": None}
@@ -48,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default=PRECISION)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the same-GPU precision comparison")
+    ap.add_argument("--inv", choices=["cholesky", "newton_tc"], default=INV_METHOD,
+                    help="eps^-1 method of the timed step")
     ap.add_argument("--epochs", type=int, default=6, help="training passes of the learned workload")
     ap.add_argument("--diag-repeat", type=int, default=32, help="diagonal entries' multiplicity in training")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain",
@@ -259,7 +262,7 @@ def run_gw(args):
         ctx.load_states(psi_d, E, dims, w.nv)
         ctx.build_P(args.precision)
         ctx.P_to_G(w.gcut)
-        ctx.eps_inv("cholesky")
+        ctx.eps_inv(args.inv)
 
     ctx.set_timing(True)
     for _ in range(args.warmup):
@@ -297,7 +300,7 @@ def run_gw(args):
         ctx.load_states(psi_h, E, dims, w.nv)
         ctx.build_P(args.precision)
         ctx.P_to_G(w.gcut)
-        ctx.eps_inv("cholesky", epsinv_out=inv_h)
+        ctx.eps_inv(args.inv, epsinv_out=inv_h)
 
     step_e2e()
     torch.cuda.synchronize()
@@ -316,10 +319,33 @@ def run_gw(args):
     inv = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
     ctx.build_P(args.precision)
     ctx.P_to_G(w.gcut, PG_out=PG)
-    ctx.eps_inv("cholesky", epsinv_out=inv)
+    ctx.eps_inv(args.inv, epsinv_out=inv)
     torch.cuda.synchronize()
     st = ctx.stats()
     PGh, invh = PG.cpu().numpy(), inv.cpu().numpy()
+
+    # the two inverses on this step's eps: time per call and their difference
+    inverses = {}
+    if world == 1:
+        res = {}
+        for m in ("cholesky", "newton_tc"):
+            ctx.eps_inv(m)
+            torch.cuda.synchronize()
+            n = 5
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                ctx.eps_inv(m)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
+            ctx.eps_inv(m, epsinv_out=out)
+            inverses[m + "_ms"] = a.elapsed_time(b) / n
+            res[m] = out
+            if m == "newton_tc":
+                inverses["newton_tc_report"] = ctx.newton_tc_report()
+        inverses["max_abs_diff"] = float((res["cholesky"] - res["newton_tc"]).abs().max())
+        del res
 
     # the same pass with the other arithmetic choices on this GPU (time per step and P~)
     variants = {}
@@ -369,9 +395,9 @@ def run_gw(args):
     peaks, peak_src = load_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))     # FP16 dense = BF16 dense rate
     achieved = flop_step / (herk_ms * 1e-3) / 1e12 if herk_ms > 0 else None
-    # tensor-pipe work actually issued: 12 MMAs of 2*128*128*16 per 16-k chunk per tile
+    # tensor-pipe work actually issued: 6 MMAs of 2*128*256*16 per 16-k chunk per tile
     kpad = (w.k + 15) // 16 * 16
-    tensor_flop = st["herk_tiles"] * (kpad // 16) * 12 * 2.0 * 128 * 128 * 16
+    tensor_flop = st["herk_tiles"] * (kpad // 16) * 6 * 2.0 * 128 * 256 * 16
     traffic = herk_traffic(w.name, args.precision, (int(st["window_chunks"]), int(st["flush_windows"])))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -427,6 +453,8 @@ def run_gw(args):
         v.pop("PG", None)
     if variants:
         line["same_gpu_variants"] = variants
+    if inverses:
+        line["eps_inv_methods"] = inverses
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

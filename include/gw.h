@@ -69,8 +69,14 @@ typedef enum gw_precision {
 
 typedef enum gw_inv_method {
     GW_INV_CHOLESKY = 0,   /* FP64 blocked Cholesky eps = L L^H, then eps^-1 = L^-H L^-1        */
-    GW_INV_NEWTON = 1      /* FP64 Newton iteration X <- X (2I - eps X) of Sec. 5.1, from        */
+    GW_INV_NEWTON = 1,     /* FP64 Newton iteration X <- X (2I - eps X) of Sec. 5.1, from        */
                            /* X0 = eps^H / max_i sum_j |(eps eps^H)_ij|, until max |dX| < 1e-11  */
+    GW_INV_NEWTON_TC = 2   /* the Newton iteration of Sec. 5.1 on the 16-bit tensor cores, for a  */
+                           /* Hermitian positive definite eps: FP16X3 steps from X0 = 2/(1+u) I   */
+                           /* (u = max row sum of |eps|) to max |I - eps X| < 3e-5, then two      */
+                           /* refinements R = I - eps X, X <- X + X R with R exact to FP64 from   */
+                           /* integer slices (see gw_zgemm_tc); GW_E_NUMERIC if the residual      */
+                           /* before the last refinement exceeds 1e-8                             */
 } gw_inv_method;
 
 typedef enum gw_dtype { GW_C64 = 0, GW_C128 = 1 } gw_dtype;
@@ -208,7 +214,8 @@ GW_API gw_status gw_reset_times(gw_ctx *ctx);
 
 /*
  * Counters (synchronises the stream): stats8[0] = kernels this library has launched in this
- * process, [1] = Newton iterations of the last GW_INV_NEWTON inverse, [2] = mean rank-k update
+ * process, [1] = Newton iterations of the last GW_INV_NEWTON inverse (FP16X3 steps for
+ * GW_INV_NEWTON_TC and gw_zinv_tc), [2] = mean rank-k update
  * time in ms over the timed calls since gw_reset_times, [3] = number of those calls, [4] = the
  * FP16 scale exponent e of the last 16-bit build, [5] = rank-k update tiles, [6] and [7] = the
  * window and flush lengths of the 16-bit update.
@@ -270,6 +277,39 @@ GW_API gw_status gw_batch_last_error(const gw_batch *batch, char *buf, size_t n)
  * the array, so calls that overlap on the GPU (other threads, other streams) race: serialise them.
  */
 GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *stream);
+
+/*
+ * Complex GEMM C = A B from FP64 operands on the 16-bit tensor cores (the products of the
+ * GW_INV_NEWTON_TC inverse).  Each operand is scaled by one power of two 2^e (max |Re|, |Im| <
+ * 2^e) and sliced:
+ *   mode 0  FP16X3: y = x 2^(14 - e), hi = rn16(y), lo = rn16(y - hi); hi*hi + hi*lo + lo*hi
+ *           accumulated in FP32 (about 1e-6 relative, normwise);
+ *   mode 1  integer slices (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012): x 2^-e =
+ *           sum_t a_t 2^(-6(t+1)) + r with a_0 in [-64, 64], a_t in [-32, 32], nine slices; every
+ *           slice product and every partial sum of a work slot is an integer below 2^24, so the
+ *           tensor cores sum exactly and the result has FP64 accuracy (error about
+ *           K 2^-54 max|A| max|B| per entry; integer-valued inputs below 2^6 give exact results).
+ *   A, B, C   device pointers, complex128, row-major: A is M x K with row stride lda, B is K x N
+ *             with row stride ldb, C is M x N with row stride N (written, not read)
+ *   1 <= M, N, K <= 16384.  Uses the context's stream and workspace and synchronises it.
+ */
+GW_API gw_status gw_zgemm_tc(gw_ctx *ctx, int mode, int M, int N, int K, const void *A, int lda, const void *B,
+                             int ldb, void *C);
+
+/*
+ * Inverse of a Hermitian positive definite complex128 matrix by the GW_INV_NEWTON_TC iteration.
+ *   A  device pointer, n x n complex128, row-major; X receives A^-1 (device, n x n)
+ *   1 <= n <= 16384.  Returns GW_E_NUMERIC when the iteration does not reach the FP64 refinement
+ * (A not positive definite, or too ill-conditioned for 16 FP16X3 steps).  The number of FP16X3
+ * steps taken is reported by gw_get_stats (stats8[1]).
+ */
+GW_API gw_status gw_zinv_tc(gw_ctx *ctx, int n, const void *A, void *X);
+
+/* Report of the last GW_INV_NEWTON_TC inverse or gw_zinv_tc call on this context (-1 before
+ * any): out4[0] = FP16X3 Newton steps of phase 1 (16 = the limit, reached without converging),
+ * [1] = max |I - A X| after phase 1 (measured to FP64 accuracy), [2] = the last measured residual
+ * (the one before the last correction), [3] = refinements that ran (1..3). */
+GW_API gw_status gw_newton_tc_report(gw_ctx *ctx, double *out4);
 
 /*
  * Window length of the 16-bit rank-k update: the tensor core accumulates `window_chunks` chunks

@@ -138,8 +138,13 @@ gw_status read_device_status(Ctx &c)
                                   "rank-k update epilogue",
                                   "rank-k update drain",
                                   "Cholesky pivot",
-                                  "input check"};
+                                  "input check",
+                                  "sliced complex GEMM",
+                                  "tensor-core Newton iteration"};
     const char *sname = site < sizeof(sites) / sizeof(sites[0]) ? sites[site] : "?";
+    if (code == GW_E_NUMERIC && site == SITE_NS)
+        return fail(c, GW_E_NUMERIC, "tensor-core Newton iteration: residual above 1e-8 before the last "
+                                     "refinement (matrix not positive definite or too ill-conditioned)");
     if (code == GW_E_NUMERIC)
         return fail(c, GW_E_NUMERIC, "eps is not positive definite: Cholesky pivot %u <= 0", detail);
     if (code == GW_E_INVALID)
@@ -325,6 +330,40 @@ gw_status inverse_newton(Ctx &c)
     return GW_OK;
 }
 
+int sm_count(int device)
+{
+    int nsm = 152;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    return nsm;
+}
+
+// The tensor-core Newton iteration (Sec. 5.1) for the inverse of A (n x n, device) into X.
+gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X)
+{
+    const int nsm = sm_count(c.device);
+    GW_TRY(ensure(c, c.d_tcw, c.cap.tcw, ns_work_bytes(n, nsm), "tensor-core Newton workspace"));
+    GW_TRY(ensure(c, c.d_scal, c.cap.scal, 4 * sizeof(double), "Newton scalars"));
+    const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+    GW_CUDA(ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.stream),
+            "tensor-core Newton inverse");
+    return GW_OK;
+}
+
+// Report of the last tensor-core Newton inverse of order n (after the stream has been
+// synchronised): FP16X3 steps, residual after phase 1, last measured residual, refinements.
+void newton_tc_record(Ctx &c, int n)
+{
+    double r[4] = {-1, -1, -1, -1};
+    if (ns_report(c.d_tcw, n, sm_count(c.device), r) != cudaSuccess)
+        cudaGetLastError();
+    c.newton_iters = static_cast<int>(r[0]);
+    for (int i = 0; i < 4; ++i)
+        c.tc_report[i] = r[i];
+}
+
 bool is_device_pointer(const void *p)
 {
     cudaPointerAttributes a;
@@ -363,6 +402,7 @@ void Ctx::release()
     dfree(d_epsinv);
     dfree(d_work);
     dfree(d_scal);
+    dfree(d_tcw);
     dfree(d_psi);
     dfree(d_psi128);
     dfree(d_small);
@@ -829,7 +869,7 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     Ctx &c = h->c;
     if (!c.PG_ready)
         return fail(c, GW_E_NOT_READY, "gw_eps_inv before gw_P_to_G");
-    if (method != GW_INV_CHOLESKY && method != GW_INV_NEWTON)
+    if (method != GW_INV_CHOLESKY && method != GW_INV_NEWTON && method != GW_INV_NEWTON_TC)
         return fail(c, GW_E_INVALID, "unknown inversion method %d", method);
     GW_CUDA(cudaSetDevice(c.device), "set device");
     const int ng = c.ng;
@@ -840,7 +880,12 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     record(c, 6);
     GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
     record(c, 7);
-    GW_TRY(method == GW_INV_CHOLESKY ? inverse_cholesky(c, c.stream) : inverse_newton(c));
+    if (method == GW_INV_CHOLESKY)
+        GW_TRY(inverse_cholesky(c, c.stream));
+    else if (method == GW_INV_NEWTON)
+        GW_TRY(inverse_newton(c));
+    else
+        GW_TRY(inverse_newton_tc(c, c.d_eps, ng, c.d_epsinv));
     record(c, 8);
     if (eps_out)
         GW_CUDA(cudaMemcpyAsync(eps_out, c.d_eps, bytes, cudaMemcpyDefault, s), "copy eps out");
@@ -848,8 +893,58 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
         GW_CUDA(cudaMemcpyAsync(epsinv_out, c.d_epsinv, bytes, cudaMemcpyDefault, s), "copy eps^-1 out");
     gw_status st = read_device_status(c);
     resolve_times(c);
+    if (method == GW_INV_NEWTON_TC)
+        newton_tc_record(c, ng);
     c.eps_ready = st == GW_OK;
     return st;
+}
+
+gw_status gw_zgemm_tc(gw_ctx *h, int mode, int M, int N, int K, const void *A, int lda, const void *B, int ldb,
+                      void *C)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (mode != 0 && mode != 1)
+        return fail(c, GW_E_INVALID, "gw_zgemm_tc: mode %d (0 = FP16X3, 1 = integer slices)", mode);
+    if (M < 1 || N < 1 || K < 1 || M > 16384 || N > 16384 || K > 16384 || lda < K || ldb < N)
+        return fail(c, GW_E_INVALID, "gw_zgemm_tc: sizes M %d N %d K %d lda %d ldb %d", M, N, K, lda, ldb);
+    if (!A || !B || !C || !is_device_pointer(A) || !is_device_pointer(B) || !is_device_pointer(C))
+        return fail(c, GW_E_INVALID, "gw_zgemm_tc: A, B and C must be device pointers");
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    ZPlan p;
+    p.build(mode, M, N, K, sm_count(c.device));
+    GW_TRY(ensure(c, c.d_tcw, c.cap.tcw, zgemm_work_bytes(p), "zgemm workspace"));
+    const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+    GW_CUDA(zgemm_enqueue(p, static_cast<const double2 *>(A), lda, static_cast<const double2 *>(B), ldb,
+                          static_cast<double2 *>(C), c.d_tcw, c.d_err, wait_ns, c.stream),
+            "tensor-core zgemm");
+    return read_device_status(c);
+}
+
+gw_status gw_zinv_tc(gw_ctx *h, int n, const void *A, void *X)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (n < 1 || n > 16384)
+        return fail(c, GW_E_INVALID, "gw_zinv_tc: order %d", n);
+    if (!A || !X || !is_device_pointer(A) || !is_device_pointer(X))
+        return fail(c, GW_E_INVALID, "gw_zinv_tc: A and X must be device pointers");
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    GW_TRY(inverse_newton_tc(c, static_cast<const double2 *>(A), n, static_cast<double2 *>(X)));
+    const gw_status st = read_device_status(c);
+    newton_tc_record(c, n);
+    return st;
+}
+
+gw_status gw_newton_tc_report(gw_ctx *h, double *out4)
+{
+    if (!h || !out4)
+        return GW_E_INVALID;
+    for (int i = 0; i < 4; ++i)
+        out4[i] = h->c.tc_report[i];
+    return GW_OK;
 }
 
 gw_status gw_sync(gw_ctx *h)

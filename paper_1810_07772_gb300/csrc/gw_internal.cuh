@@ -21,6 +21,8 @@ enum ErrSite : uint32_t {
     SITE_HERK_DRAIN = 4,
     SITE_CHOL_PIVOT = 5,
     SITE_INPUT = 6,
+    SITE_ZGEMM = 7,
+    SITE_NS = 8,
 };
 
 __device__ __forceinline__ void record_error(uint32_t *err, uint32_t code, uint32_t site, uint32_t detail)
@@ -96,8 +98,10 @@ struct Ctx {
     double2 *d_epsinv = nullptr;    // [ng][ng]
     double2 *d_work = nullptr;      // workspace for the inverse
     double *d_scal = nullptr;       // FP64 scalars of the Newton iteration
+    void *d_tcw = nullptr;          // workspace of the tensor-core Newton iteration / gw_zgemm_tc
     bool eps_ready = false;
     int newton_iters = 0;
+    double tc_report[4] = {-1, -1, -1, -1};  // last tensor-core Newton inverse (gw_newton_tc_report)
 
     // staging for gw_load_states
     float2 *d_psi = nullptr;        // [nb][nr] complex64
@@ -106,7 +110,7 @@ struct Ctx {
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
         size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, dftw, sv, eps, epsinv, work,
-            scal;
+            scal, tcw;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -224,5 +228,28 @@ cudaError_t launch_two_minus(double2 *T, int n, cudaStream_t s);  // T <- 2I - T
 cudaError_t launch_scaled_adjoint(const double2 *A, int n, const double *d_den, double2 *X, cudaStream_t s);
 cudaError_t launch_max_absdiff(const double2 *A, const double2 *B, size_t n, double *out, cudaStream_t s);
 cudaError_t launch_row_abs_sum_max(const double2 *A, int n, double *out, cudaStream_t s);
+
+// k_zgemm16.cu: complex GEMM from sliced FP64 operands on the 16-bit tensor cores, and the
+// tensor-core Newton iteration for eps^-1.
+struct ZPlan {
+    int mode = 0;  // 0 = FP16X3 split, 1 = integer slices (FP64 accuracy)
+    int M = 0, N = 0, K = 0, Mpad = 0, Npad = 0, nkc = 0, ntiles = 0, ns = 0, nslots = 0, npairs = 0;
+    std::vector<int2> host_pairs;
+    std::vector<int> host_slots, host_wexp;
+    int2 *d_pairs = nullptr;
+    int *d_slots = nullptr, *d_wexp = nullptr;
+    void build(int mode, int M, int N, int K, int nsm);
+    size_t table_bytes() const;
+    size_t planes_bytes(bool a_operand) const;
+    size_t T_bytes() const;
+    cudaError_t upload(void *tab, cudaStream_t s);
+};
+size_t zgemm_work_bytes(const ZPlan &p);
+cudaError_t zgemm_enqueue(ZPlan &p, const double2 *A, long lda, const double2 *B, long ldb, double2 *C, void *work,
+                          uint32_t *err, uint64_t wait_ns, cudaStream_t s);
+size_t ns_work_bytes(int N, int nsm);
+cudaError_t ns_report(const void *work, int N, int nsm, double *out4);
+cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
+                               uint64_t wait_ns, int nsm, cudaStream_t s);
 
 }  // namespace gw

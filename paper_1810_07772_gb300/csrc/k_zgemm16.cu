@@ -1,0 +1,980 @@
+// Complex GEMM C = A B on the 16-bit tensor cores from sliced FP64 operands, and the Newton
+// iteration X <- X (2I - eps X) of Sec. 5.1 for eps^-1 built on it.
+//
+// FP64 runs at about 1 TFLOP/s on this GPU and FP16 tensor MMAs at about 2 PFLOP/s, so the
+// inverse is carried by the tensor cores:
+//  * Phase 1: Newton iterations whose products use the FP16X3 split (22 significant bits), from
+//    X0 = 2 / (1 + u) I with u = max_i sum_j |eps_ij| >= lambda_max, until max |I - eps X| < 3e-5.
+//    For a Hermitian positive definite eps (lambda_min >= 1 for the eps of this library) the error
+//    e = I - eps X squares each step from e0 <= (u - 1) / (u + 1).
+//  * Phase 2: up to three refinement steps R = I - eps X, X <- X + X R.  R is computed to FP64 accuracy
+//    from integer slices (the error-free splitting of Ozaki, Ogita, Oishi and Rump, Numer.
+//    Algorithms 59, 2012): every entry scaled into [-1, 1] is a sum of slices a_t 2^(-6(t+1))
+//    with integer a_0 in [-64, 64] and a_t in [-32, 32] (t >= 1); nine slices keep 54 bits.  The
+//    slice products a_t b_u are exact in FP16 and their sums over one work slot stay below 2^24,
+//    so the FP32 tensor-core accumulation is exact; the slots are scaled by 2^(-6(t+u+2)) and
+//    added in FP64.  X R only needs the relative accuracy of the FP16X3 split, because R is small.
+//    Each refinement squares the residual (plus the FP16X3 error of X R, ~4e-6 |R|); once a
+//    measured residual is <= 1e-9 its correction is the last one (the result then sits near 4e-15).
+//    If three refinements end with a last measured residual above 1e-8 (or a non-finite one), the
+//    inverse is reported as GW_E_NUMERIC.
+//
+// Operand planes (K-major, 8-row x 16-byte core matrices, as in the rank-k update): element
+// (r, k) of plane p sits at 16-bit offset ((kc NP + p) Rpad + (r/8) 8) 16 + ((k%16)/8) 64 +
+// (r%8) 8 + k%8 with kc = k / 16.  A operand (row i of A, k along the row): planes 2t (Re) and
+// 2t + 1 (Im) of slice t.  B operand (row j = column j of B, k down the column): planes 3t (-Im),
+// 3t + 1 (Re), 3t + 2 (Im), so the 256 rows starting at Re are [Re; Im] and those starting at -Im
+// are [-Im; Re].  Then one M = 128, N = 256 MMA with A = Re(A) adds Re A Re B into the Re columns
+// of the accumulator and Re A Im B into its Im columns, and one with A = Im(A) from the -Im plane
+// adds -Im A Im B and Im A Re B: C = A B with two MMAs per slice pair and 16-wide chunk.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "gw_internal.cuh"
+#include "ptx.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int ZT = 128;
+constexpr uint32_t ZPL = ZT * 16 * 2;       // 4 KB: one plane of one 128-row block, one chunk
+constexpr uint32_t ZSTAGE = 5 * ZPL;        // A Re, A Im, B -Im, B Re, B Im
+constexpr int ZSTAGES = 4;
+constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 80 KB: two CTAs per SM
+static_assert(128 * 65 * 8 <= ZPIPE, "epilogue staging must fit in the pipeline buffers");
+constexpr size_t ZSMEM = ZPIPE + 128;
+constexpr int ZTHREADS = 192;               // warp 0 copies, warp 1 MMAs, warps 2..5 epilogue
+constexpr uint32_t LBO = 128, SBO = 256;
+constexpr uint64_t DRAIN_NS = 2000000000ull;
+
+constexpr int MODE_FP16X3 = 0, MODE_SLICES = 1;
+constexpr int OZ_SLICES = 9;
+constexpr double NS_TOL = 3e-5;     // phase 1 stops below this max |I - eps X|
+constexpr double NS_LAST = 1e-9;    // a refinement whose residual is below this is the last one
+constexpr double NS_ACCEPT = 1e-8;  // largest residual before the last correction
+constexpr int NS_MAX = 16, NS_REFINE = 3;
+
+// Scale exponent e of a matrix from the bits of max(|Re|, |Im|): max < 2^e (0 for an all-zero or
+// non-finite matrix; a non-finite residual is caught by the final check).
+__device__ __forceinline__ int exp_of(const unsigned long long *w)
+{
+    const double m = __longlong_as_double((long long)*w);
+    if (!(m > 0.0) || !isfinite(m))
+        return 0;
+    int e;
+    frexp(m, &e);
+    return e;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Named barrier over n threads that also ORs a predicate, so the participants agree on it.
+__device__ __forceinline__ bool named_bar_or(int id, int n, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(pred ? 1u : 0u), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ uint16_t h16(float x)
+{
+    __half h = __float2half_rn(x);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+
+// max(|Re|, |Im|) over a rows x cols complex128 matrix into *w (as the bits of a non-negative
+// double, which order like unsigned integers).  *w must be zero (or smaller) beforehand.
+__global__ void zmaxabs_kernel(const double2 *__restrict__ M, int rows, int cols, long ld, unsigned long long *w)
+{
+    double best = 0.0;
+    const size_t total = (size_t)rows * cols;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / cols, c = i - r * cols;
+        const double2 z = M[r * ld + c];
+        best = fmax(best, fmax(fabs(z.x), fabs(z.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(w, (unsigned long long)__double_as_longlong(best));
+}
+
+// Slice a complex128 matrix into operand planes (layouts above).  One block per (16-wide chunk
+// kc, 128-row block rb of the operand): the 16 x 128 tile goes through shared memory, so both
+// orientations read contiguous runs of M and every plane is written in 4 KB runs.  transpose = 0:
+// operand row r is row r of M (A operand, element (r, k) = M[r][k]); transpose = 1: operand row r
+// is column r of M (B operand, element (r, k) = M[k][r]).  npl = 2 (A: Re, Im) or 3 (B: -Im, Re,
+// Im) planes per slice.  Entries outside rows x K are zero.
+//   FP16X3: y = float(x) 2^(14 - e), hi = rn16(y), lo = rn16(y - hi).
+//   slices: n = rint(x 2^(54 - e)) (|n| <= 2^54) written in balanced base 64,
+//           n = sum_t a_t 2^(6 (8 - t)): a_8 .. a_1 in [-32, 31] from the low end, a_0 = the rest,
+//           |a_0| <= 64; so x 2^-e = sum_t a_t 2^(-6 (t + 1)) up to 2^-55.
+__global__ void __launch_bounds__(256) zslice_kernel(const double2 *__restrict__ M, long ld, int rows, int K,
+                                                     int transpose, int Rpad, int mode, int ns, int npl,
+                                                     const unsigned long long *maxw, uint16_t *__restrict__ planes,
+                                                     const int *skip)
+{
+    if (skip && *skip)
+        return;
+    __shared__ double2 tile[16][129];
+    const int kc = blockIdx.x, rb = blockIdx.y;
+    const int k0 = kc * 16, r0 = rb * 128;
+    const double2 zero = make_double2(0.0, 0.0);
+    if (transpose) {
+        for (int q = threadIdx.x; q < 2048; q += 256) {
+            const int kk = q >> 7, rr = q & 127, r = r0 + rr, k = k0 + kk;
+            tile[kk][rr] = (r < rows && k < K) ? M[(size_t)k * ld + r] : zero;
+        }
+    } else {
+        for (int q = threadIdx.x; q < 2048; q += 256) {
+            const int rr = q >> 4, kk = q & 15, r = r0 + rr, k = k0 + kk;
+            tile[kk][rr] = (r < rows && k < K) ? M[(size_t)r * ld + k] : zero;
+        }
+    }
+    __syncthreads();
+    const int e = exp_of(maxw);
+    const int NP = ns * npl;
+    const size_t per = (size_t)Rpad * 16;
+    uint16_t *base0 = planes + (size_t)kc * NP * per + (size_t)rb * 2048;
+    const float scf = ldexpf(1.0f, 14 - e);
+    const double scd = ldexp(1.0, 54 - e);
+    for (int rem = threadIdx.x; rem < 2048; rem += 256) {
+        const int rr = (rem >> 7) * 8 + ((rem & 63) >> 3);
+        const int kk = ((rem & 127) >> 6) * 8 + (rem & 7);
+        const double2 z = tile[kk][rr];
+        uint16_t *b = base0 + rem;
+        if (mode == MODE_FP16X3) {
+            const float yr = (float)z.x * scf, yi = (float)z.y * scf;
+            const uint16_t rh = h16(yr), ih = h16(yi);
+            const uint16_t rl = h16(yr - __half2float(*reinterpret_cast<const __half *>(&rh)));
+            const uint16_t il = h16(yi - __half2float(*reinterpret_cast<const __half *>(&ih)));
+            const uint16_t re[2] = {rh, rl}, im[2] = {ih, il};
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (npl == 2) {
+                    b[(size_t)(2 * t) * per] = re[t];
+                    b[(size_t)(2 * t + 1) * per] = im[t];
+                } else {
+                    b[(size_t)(3 * t) * per] = im[t] ^ 0x8000u;
+                    b[(size_t)(3 * t + 1) * per] = re[t];
+                    b[(size_t)(3 * t + 2) * per] = im[t];
+                }
+            }
+        } else {
+            long long nr = __double2ll_rn(z.x * scd), ni = __double2ll_rn(z.y * scd);
+            for (int t = ns - 1; t >= 0; --t) {
+                long long ar, ai;
+                if (t > 0) {
+                    ar = ((nr + 32) & 63) - 32;
+                    ai = ((ni + 32) & 63) - 32;
+                    nr = (nr - ar) >> 6;  // exact: nr - ar is a multiple of 64
+                    ni = (ni - ai) >> 6;
+                } else {
+                    ar = nr;
+                    ai = ni;
+                }
+                const uint16_t hr = h16((float)ar), hi = h16((float)ai);  // |a| <= 64: exact
+                if (npl == 2) {
+                    b[(size_t)(2 * t) * per] = hr;
+                    b[(size_t)(2 * t + 1) * per] = hi;
+                } else {
+                    b[(size_t)(3 * t) * per] = hi ^ 0x8000u;
+                    b[(size_t)(3 * t + 1) * per] = hr;
+                    b[(size_t)(3 * t + 2) * per] = hi;
+                }
+            }
+        }
+    }
+}
+
+// One work slot of the sliced product: slice pairs [p0, p1) of the pair list over chunks
+// [kc0, kc1); the slot's result is one FP32 complex tile per output tile, T[slot][Mpad][Npad].
+struct ZSlot {
+    int p0, p1, kc0, kc1;
+};
+
+__global__ void __launch_bounds__(ZTHREADS, 2)
+    zgemm16_kernel(const uint16_t *__restrict__ Ap, int npA, int Mpad, const uint16_t *__restrict__ Bp, int npB,
+                   int Npad, const int2 *__restrict__ pairs, const ZSlot *__restrict__ slots, int ntj,
+                   float2 *__restrict__ T, uint32_t *err, uint64_t wait_ns, const int *skip)
+{
+    if (skip && *skip)
+        return;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + ZPIPE);
+    uint64_t *empty = full + ZSTAGES;
+    uint64_t *done = empty + ZSTAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *n_issued = abort_flag + 1;
+    volatile int *n_consumed = abort_flag + 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ti = blockIdx.x / ntj, tj = blockIdx.x - (blockIdx.x / ntj) * ntj;
+    const ZSlot sl = slots[blockIdx.y];
+    const int np = sl.p1 - sl.p0;
+    const int nunits = np * (sl.kc1 - sl.kc0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ZSTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        *n_issued = 0;
+        *n_consumed = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1)
+        tmem_alloc(tmem_slot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const size_t perA = (size_t)Mpad * 16, perB = (size_t)Npad * 16;
+            const size_t aoff = (size_t)ti * ZT * 16, boff = (size_t)tj * ZT * 16;
+            for (int u = 0; u < nunits; ++u) {
+                const int s = u % ZSTAGES;
+                const uint32_t ph = (uint32_t)(u / ZSTAGES) & 1u;
+                if (u >= ZSTAGES && !mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
+                    record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*abort_flag)
+                    break;
+                const int kc = sl.kc0 + u / np;  // chunk-major: every pair of a chunk in turn
+                const int2 pr = pairs[sl.p0 + u % np];
+                uint8_t *st = smem + s * ZSTAGE;
+                mbar_arrive_expect_tx(&full[s], ZSTAGE);
+                const uint16_t *a = Ap + ((size_t)kc * npA + 2 * pr.x) * perA + aoff;
+                bulk_g2s(st, a, ZPL, &full[s]);
+                bulk_g2s(st + ZPL, a + perA, ZPL, &full[s]);
+                const uint16_t *b = Bp + ((size_t)kc * npB + 3 * pr.y) * perB + boff;
+                bulk_g2s(st + 2 * ZPL, b, ZPL, &full[s]);
+                bulk_g2s(st + 3 * ZPL, b + perB, ZPL, &full[s]);
+                bulk_g2s(st + 4 * ZPL, b + 2 * perB, ZPL, &full[s]);
+                *n_issued = u + 1;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t ID = mma_idesc(0u, ZT, 2 * ZT, false);  // FP16, N = 256: Re | Im
+            const uint32_t sbase = smem_u32(smem);
+            for (int u = 0; u < nunits; ++u) {
+                const int s = u % ZSTAGES;
+                if (!mbar_wait(&full[s], (uint32_t)(u / ZSTAGES) & 1u, wait_ns)) {
+                    record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + s * ZSTAGE;
+                const uint64_t a_re = smem_desc(st, LBO, SBO), a_im = smem_desc(st + ZPL, LBO, SBO);
+                const uint64_t b_neg = smem_desc(st + 2 * ZPL, LBO, SBO);  // rows [-Im B; Re B]
+                const uint64_t b_re = smem_desc(st + 3 * ZPL, LBO, SBO);   // rows [Re B; Im B]
+                mma_f16(tmem, a_re, b_re, ID, u > 0 ? 1u : 0u);
+                mma_f16(tmem, a_im, b_neg, ID, 1u);
+                mma_commit(&empty[s]);
+                *n_consumed = u + 1;
+            }
+            mma_commit(done);  // arrives once every MMA issued above has completed
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps 2..5: TMEM lane quarter warp % 4, one output row per thread
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const bool waited = __all_sync(0xffffffffu, mbar_wait(done, 0, wait_ns));
+        if (!waited) {
+            if (lane == 0)
+                record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
+            *abort_flag = 1;
+        }
+        // one decision for the four epilogue warps (the staging below has barriers among them)
+        if (!named_bar_or(1, 128, !waited || *abort_flag != 0)) {
+            // every copy has landed and every MMA has read it, so the pipeline buffers stage the
+            // tile: two halves of 64 columns, each written back as 512-byte row runs
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16);
+            float2 *stage = reinterpret_cast<float2 *>(smem);  // [128][65]
+            const int et = threadIdx.x - 64;                   // 0..127 over the epilogue warps
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float re[16], im[16];
+                    tmem_ld16x2(base + h * 64 + c0, base + ZT + h * 64 + c0, re, im);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        stage[row * 65 + c0 + i] = make_float2(re[i], im[i]);
+                }
+                named_bar_sync(1, 128);
+                float2 *out = T + ((size_t)blockIdx.y * Mpad + (size_t)ti * ZT) * Npad + (size_t)tj * ZT + h * 64;
+                for (int rr = et >> 5; rr < ZT; rr += 4) {
+                    const int c = (et & 31) * 2;
+                    const float2 a = stage[rr * 65 + c], b2 = stage[rr * 65 + c + 1];
+                    *reinterpret_cast<float4 *>(out + (size_t)rr * Npad + c) = make_float4(a.x, a.y, b2.x, b2.y);
+                }
+                named_bar_sync(1, 128);
+            }
+        }
+        tc_fence_before();
+    }
+
+    // ---------------- drain before releasing TMEM and shared memory
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait(done, 0, DRAIN_NS))
+            record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
+        const int issued = *n_issued, consumed = *n_consumed;
+        for (int u = consumed; u < issued; ++u)
+            if (!mbar_wait(&full[u % ZSTAGES], (uint32_t)(u / ZSTAGES) & 1u, DRAIN_NS)) {
+                record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
+                break;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// Words of the scalar area (unsigned long long each), zeroed at the start of an inverse.
+enum NsWord : int {
+    W_EPS = 0,   // max of eps
+    W_X,         // max of the current X
+    W_XN,        // max of the X being written (moved to W_X by the last block)
+    W_Z,         // max of the current Z (2I - eps X) or R
+    W_ZN,
+    W_DEVN,      // max |out - ref I| being accumulated
+    W_RES0,      // residual max |I - eps X| measured by refinement 1 (after phase 1)
+    W_RLAST,     // residual measured by the last refinement that ran
+    W_NREF,      // refinements that ran
+    W_ITERS,     // Newton iterations of phase 1
+    W_COUNT,     // completed blocks of the running combine
+    W_DISCARD,   // deviations nobody reads
+    W_U,         // row-sum bound of lambda_max
+    W_TOTAL
+};
+static_assert(W_TOTAL <= 64, "scalar area");
+
+// What the last block of a combine does with the deviation d = max |out - ref I|.
+enum DevUse : int {
+    DEV_STORE = 0,   // words[dev_to] = d
+    DEV_PHASE1 = 1,  // d < tol: set flags[0] (phase 1 done) and store the iteration count
+    DEV_REFINE = 2,  // words[dev_to] = W_RLAST = d, ++W_NREF; d <= tol: set flags[iter + 1 ..]
+};
+
+// Block and grid reduction of a combine's two maxima (max(|Re|, |Im|) of out into
+// words[acc_max]; deviation into W_DEVN); the last block to finish moves acc_max -> fin_max and
+// acts on the deviation as `use` says.
+__device__ void combine_tail(float best, float dev, unsigned long long *words, int acc_max, int fin_max, int dev_to,
+                             int use, double tol, int iter, int *flags)
+{
+    __shared__ float red[2][32];
+    __shared__ bool last;
+    for (int o = 16; o > 0; o >>= 1) {
+        best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][warp] = best;
+        red[1][warp] = dev;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // one atomic per block and word: same-address atomics serialise
+        for (int w = 1; w < nw; ++w) {
+            best = fmaxf(best, red[0][w]);
+            dev = fmaxf(dev, red[1][w]);
+        }
+        atomicMax(&words[acc_max], (unsigned long long)__double_as_longlong((double)best));
+        atomicMax(&words[W_DEVN], (unsigned long long)__double_as_longlong((double)dev));
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last = atomicAdd(&words[W_COUNT], 1ull) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        volatile unsigned long long *vw = words;
+        vw[fin_max] = vw[acc_max];
+        vw[acc_max] = 0ull;
+        const unsigned long long d = vw[W_DEVN];
+        const double dv = __longlong_as_double((long long)d);
+        vw[W_DEVN] = 0ull;
+        vw[W_COUNT] = 0ull;
+        if (use == DEV_STORE) {
+            vw[dev_to] = d;
+        } else if (use == DEV_PHASE1) {
+            if (dv < tol) {
+                flags[0] = 1;
+                vw[W_ITERS] = (unsigned long long)iter;
+            }
+        } else {
+            vw[dev_to] = d;
+            vw[W_RLAST] = d;
+            vw[W_NREF] = vw[W_NREF] + 1ull;
+            if (dv <= tol)
+                for (int j = iter + 1; j <= NS_REFINE; ++j)
+                    reinterpret_cast<volatile int *>(flags)[j] = 1;
+        }
+    }
+}
+
+__device__ __forceinline__ float finite_or_inf(float d)
+{
+    return d <= 3.0e38f ? d : __int_as_float(0x7f800000);  // NaN or inf: +inf, which fmaxf keeps
+}
+
+// FP16X3 products: out = cI I + cC 2^(eA + eB - 28) sum_slot T[slot] + cD D, the K-range slots
+// summed in FP32 (their own rounding is below the split's 2^-22), the rest in FP64.
+__global__ void zcombine16_kernel(const float2 *__restrict__ T, int nslots, int Mpad, int Npad,
+                                  const unsigned long long *wA, const unsigned long long *wB, int M, int N, double cI,
+                                  double cC, const double2 *D, double cD, double2 *out, double ref,
+                                  unsigned long long *words, int acc_max, int fin_max, int dev_to, int use, double tol,
+                                  int iter, const int *skip, int *flags)
+{
+    if (skip && *skip)
+        return;
+    const double sc = cC * ldexp(1.0, exp_of(wA) + exp_of(wB) - 28);
+    float best = 0.f, dev = 0.f;
+    const size_t total = (size_t)M * N, plane = (size_t)Mpad * Npad;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = static_cast<int>(i / N), c = static_cast<int>(i - (size_t)r * N);
+        const float2 *t = T + (size_t)r * Npad + c;
+        float sr = 0.f, si = 0.f;
+        for (int s = 0; s < nslots; ++s) {
+            const float2 v = t[s * plane];
+            sr += v.x;
+            si += v.y;
+        }
+        double xr = sc * (double)sr, xi = sc * (double)si;
+        if (r == c)
+            xr += cI;
+        if (D) {
+            const double2 d = D[i];
+            xr = fma(cD, d.x, xr);
+            xi = fma(cD, d.y, xi);
+        }
+        out[i] = make_double2(xr, xi);
+        const float fr = (float)xr, fi = (float)xi;
+        best = fmaxf(best, fmaxf(fabsf(fr), fabsf(fi)));
+        const float dr = r == c ? (float)(xr - ref) : fr;
+        dev = fmaxf(dev, finite_or_inf(sqrtf(dr * dr + fi * fi)));
+    }
+    combine_tail(best, dev, words, acc_max, fin_max, dev_to, use, tol, iter, flags);
+}
+
+// Exact 128-bit integer -> double (one rounding in each half; the halves do not cancel).
+__device__ __forceinline__ double i128_to_double(__int128 a)
+{
+    const bool neg = a < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-a) : (unsigned __int128)a;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const double v = hi ? fma((double)hi, 18446744073709551616.0, (double)lo) : (double)lo;
+    return neg ? -v : v;
+}
+
+// Integer-slice products: every slot tile is an exact integer below 2^24 with weight
+// 2^(wexp - 60 + 60) = 2^(-6(d + 2)); sum_slot T 2^(wexp + 60) is added up exactly in 128-bit
+// integers, so out = sign (2^(eA + eB - 60) (that sum)) (+ I when identity = 1, added in the same
+// integer units, which keeps I - eps X exact) is rounded once.
+__global__ void zcombine_int_kernel(const float2 *__restrict__ T, int nslots, const int *__restrict__ wexp, int Mpad,
+                                    int Npad, const unsigned long long *wA, const unsigned long long *wB, int M, int N,
+                                    int identity, int negate, double2 *out, double ref, unsigned long long *words,
+                                    int acc_max, int fin_max, int dev_to, int use, double tol, int iter,
+                                    const int *skip, int *flags)
+{
+    if (skip && *skip)
+        return;
+    __shared__ int shift[256];
+    for (int s = threadIdx.x; s < nslots && s < 256; s += blockDim.x)
+        shift[s] = wexp[s] + 60;  // 6 (8 - d) in [0, 48]
+    __syncthreads();
+    const int eab = exp_of(wA) + exp_of(wB);
+    const int ish = 60 - eab;  // I in units of 2^(eab - 60)
+    const bool exact_i = ish >= 0 && ish <= 120;
+    const double sc = ldexp(1.0, eab - 60);
+    float best = 0.f, dev = 0.f;
+    const size_t total = (size_t)M * N, plane = (size_t)Mpad * Npad;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = static_cast<int>(i / N), c = static_cast<int>(i - (size_t)r * N);
+        const float2 *t = T + (size_t)r * Npad + c;
+        __int128 ar = 0, ai = 0;
+        for (int s = 0; s < nslots; ++s) {
+            const float2 v = t[s * plane];
+            ar += (__int128)__float2int_rn(v.x) << shift[s];
+            ai += (__int128)__float2int_rn(v.y) << shift[s];
+        }
+        if (negate) {
+            ar = -ar;
+            ai = -ai;
+        }
+        const bool diag = identity && r == c;
+        if (diag && exact_i)
+            ar += (__int128)1 << ish;
+        double xr = i128_to_double(ar) * sc, xi = i128_to_double(ai) * sc;
+        if (diag && !exact_i)
+            xr += 1.0;
+        out[i] = make_double2(xr, xi);
+        const float fr = (float)xr, fi = (float)xi;
+        best = fmaxf(best, fmaxf(fabsf(fr), fabsf(fi)));
+        const float dr = r == c ? (float)(xr - ref) : fr;
+        dev = fmaxf(dev, finite_or_inf(sqrtf(dr * dr + fi * fi)));
+    }
+    combine_tail(best, dev, words, acc_max, fin_max, dev_to, use, tol, iter, flags);
+}
+
+// u = max_i sum_j (|Re a_ij| + |Im a_ij|) >= max_i sum_j |a_ij| >= lambda_max, one warp per row,
+// into words[W_U] (the bits of a non-negative double; zero beforehand).
+__global__ void row_sum_bound_kernel(const double2 *__restrict__ A, int n, unsigned long long *words)
+{
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double2 a = A[(size_t)i * n + j];
+            s += fabs(a.x) + fabs(a.y);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0)
+            atomicMax(&words[W_U], (unsigned long long)__double_as_longlong(s));
+    }
+}
+
+// X0 = c I with c = 2 / (1 + u), u >= lambda_max from row_sum_bound_kernel.
+__global__ void ns_init_kernel(double2 *X, int N, unsigned long long *words, int *flags)
+{
+    const double c = 2.0 / (1.0 + __longlong_as_double((long long)words[W_U]));
+    const size_t total = (size_t)N * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / N, col = i - r * N;
+        X[i] = make_double2(r == col ? c : 0.0, 0.0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        words[W_X] = (unsigned long long)__double_as_longlong(fabs(c));
+        words[W_ITERS] = (unsigned long long)NS_MAX;
+        for (int j = 0; j <= NS_REFINE + 1; ++j)
+            flags[j] = 0;
+    }
+}
+
+__global__ void ns_final_kernel(const unsigned long long *words, uint32_t *err)
+{
+    const double r = __longlong_as_double((long long)words[W_RLAST]);
+    if (!(r <= NS_ACCEPT))
+        record_error(err, GW_E_NUMERIC, SITE_NS, 0);
+}
+
+int grid_for(size_t n)
+{
+    size_t g = (n + 255) / 256;
+    if (g > 152 * 8)
+        g = 152 * 8;
+    return g < 1 ? 1 : static_cast<int>(g);
+}
+
+int round_up(int x, int m)
+{
+    return ((x + m - 1) / m) * m;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- host side
+
+// Work slots of one product shape: FP16X3 = one slot of the three split pairs per K range (the
+// K range split so that tiles x slots fills the GPU); slices = the pairs (t, u) with t + u <= 8,
+// grouped by t + u into slots whose exact-sum bound sum 2 m_t m_u K_range stays below 2^24
+// (m_0 = 64, m_t = 32) and that hold at most five pairs.
+void ZPlan::build(int mode_, int M_, int N_, int K_, int nsm)
+{
+    mode = mode_;
+    M = M_;
+    N = N_;
+    K = K_;
+    Mpad = round_up(std::max(M, 1), ZT);
+    Npad = round_up(std::max(N, 1), ZT);
+    nkc = round_up(std::max(K, 1), 16) / 16;
+    ntiles = (Mpad / ZT) * (Npad / ZT);
+    ns = mode == MODE_FP16X3 ? 2 : OZ_SLICES;
+    std::vector<int2> pr;
+    std::vector<int> sl, we;  // slot: p0, p1, kc0, kc1
+    auto add_slot = [&](int p0, int p1, int kc0, int kc1, int w) {
+        sl.insert(sl.end(), {p0, p1, kc0, kc1});
+        we.push_back(w);
+    };
+    if (mode == MODE_FP16X3) {
+        pr = {make_int2(0, 0), make_int2(0, 1), make_int2(1, 0)};
+        int ks = std::max(1, std::min(std::max(1, nkc / 4), (nsm + ntiles - 1) / ntiles));
+        const int per = (nkc + ks - 1) / ks;
+        ks = (nkc + per - 1) / per;
+        for (int s = 0; s < ks; ++s)
+            add_slot(0, 3, s * per, std::min(nkc, (s + 1) * per), -28);
+    } else {
+        const int ks = (nkc + 127) / 128;  // K range <= 2048: the pair (0, 0) alone stays exact
+        const int per = (nkc + ks - 1) / ks;
+        const double limit = 16777216.0;
+        for (int s = 0; s < ks; ++s) {
+            const int kc0 = s * per, kc1 = std::min(nkc, (s + 1) * per);
+            const double krange = 16.0 * (kc1 - kc0);
+            for (int d = 0; d < ns; ++d) {
+                int p0 = static_cast<int>(pr.size());
+                double bound = 0.0;
+                for (int t = 0; t <= d; ++t) {
+                    const int u = d - t;
+                    const double b = 2.0 * (t == 0 ? 64 : 32) * (u == 0 ? 64 : 32) * krange;
+                    const int cnt = static_cast<int>(pr.size()) - p0;
+                    if (cnt > 0 && (bound + b >= limit || cnt == 5)) {
+                        add_slot(p0, static_cast<int>(pr.size()), kc0, kc1, -6 * (d + 2));
+                        p0 = static_cast<int>(pr.size());
+                        bound = 0.0;
+                    }
+                    pr.push_back(make_int2(t, u));
+                    bound += b;
+                }
+                add_slot(p0, static_cast<int>(pr.size()), kc0, kc1, -6 * (d + 2));
+            }
+        }
+    }
+    nslots = static_cast<int>(we.size());
+    npairs = static_cast<int>(pr.size());
+    host_pairs = pr;
+    host_slots = sl;
+    host_wexp = we;
+}
+
+size_t ZPlan::table_bytes() const
+{
+    return host_pairs.size() * sizeof(int2) + host_slots.size() * sizeof(int) + host_wexp.size() * sizeof(int);
+}
+
+size_t ZPlan::planes_bytes(bool a_operand) const
+{
+    const int npl = a_operand ? 2 : 3;
+    return (size_t)nkc * ns * npl * (a_operand ? Mpad : Npad) * 16 * sizeof(uint16_t);
+}
+
+size_t ZPlan::T_bytes() const
+{
+    return (size_t)nslots * Mpad * Npad * sizeof(float2);
+}
+
+// Copy the slot tables into `tab` (device, table_bytes() long) on stream s.
+cudaError_t ZPlan::upload(void *tab, cudaStream_t s)
+{
+    uint8_t *p = static_cast<uint8_t *>(tab);
+    d_pairs = reinterpret_cast<int2 *>(p);
+    d_slots = reinterpret_cast<int *>(p + host_pairs.size() * sizeof(int2));
+    d_wexp = d_slots + host_slots.size();
+    cudaError_t e = cudaMemcpyAsync(d_pairs, host_pairs.data(), host_pairs.size() * sizeof(int2),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_slots, host_slots.data(), host_slots.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_wexp, host_wexp.data(), host_wexp.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    return e;
+}
+
+cudaError_t launch_zmaxabs(const double2 *M, int rows, int cols, long ld, unsigned long long *w, cudaStream_t s)
+{
+    zmaxabs_kernel<<<grid_for((size_t)rows * cols), 256, 0, s>>>(M, rows, cols, ld, w);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zslice(const ZPlan &p, bool a_operand, const double2 *Mx, long ld, const unsigned long long *maxw,
+                          uint16_t *planes, const int *skip, cudaStream_t s)
+{
+    const int rows = a_operand ? p.M : p.N, Rpad = a_operand ? p.Mpad : p.Npad;
+    zslice_kernel<<<dim3(p.nkc, Rpad / ZT), 256, 0, s>>>(Mx, ld, rows, p.K, a_operand ? 0 : 1, Rpad, p.mode, p.ns,
+                                                         a_operand ? 2 : 3, maxw, planes, skip);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm16(const ZPlan &p, const uint16_t *Ap, const uint16_t *Bp, float2 *T, uint32_t *err,
+                           uint64_t wait_ns, const int *skip, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(zgemm16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZSMEM);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid(p.ntiles, p.nslots);
+    zgemm16_kernel<<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.ns, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+                                                 reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT, T, err,
+                                                 wait_ns, skip);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// out = cI I + cC (A B) + cD D from the slot tiles of plan p.  With integer slices only
+// cI in {0, 1}, cC = +-1 and no D are taken (the exact forms the inverse needs).
+cudaError_t launch_zcombine(const ZPlan &p, const float2 *T, const unsigned long long *wA,
+                            const unsigned long long *wB, double cI, double cC, const double2 *D, double cD,
+                            double2 *out, double ref, unsigned long long *words, int acc_max, int fin_max, int dev_to,
+                            int use, double tol, int iter, const int *skip, int *flags, cudaStream_t s)
+{
+    const int grid = grid_for((size_t)p.M * p.N);
+    if (p.mode == MODE_FP16X3) {
+        zcombine16_kernel<<<grid, 256, 0, s>>>(T, p.nslots, p.Mpad, p.Npad, wA, wB, p.M, p.N, cI, cC, D, cD, out, ref,
+                                               words, acc_max, fin_max, dev_to, use, tol, iter, skip, flags);
+    } else {
+        if (D || (cI != 0.0 && cI != 1.0) || (cC != 1.0 && cC != -1.0) || p.nslots > 256)
+            return cudaErrorInvalidValue;
+        zcombine_int_kernel<<<grid, 256, 0, s>>>(T, p.nslots, p.d_wexp, p.Mpad, p.Npad, wA, wB, p.M, p.N,
+                                                 cI == 1.0 ? 1 : 0, cC < 0 ? 1 : 0, out, ref, words, acc_max, fin_max,
+                                                 dev_to, use, tol, iter, skip, flags);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+// Carves a workspace into 256-byte aligned pieces; with base == nullptr it only counts.
+struct Carver {
+    uint8_t *base;
+    size_t used = 0;
+    explicit Carver(void *b) : base(static_cast<uint8_t *>(b)) {}
+    void *take(size_t bytes)
+    {
+        void *r = base ? base + used : nullptr;
+        used += (bytes + 255) / 256 * 256;
+        return r;
+    }
+};
+
+struct GemmWork {
+    uint16_t *Ap, *Bp;
+    float2 *T;
+    unsigned long long *words;
+    void *tab;
+};
+
+GemmWork carve_gemm(const ZPlan &p, Carver &c)
+{
+    GemmWork g;
+    g.Ap = static_cast<uint16_t *>(c.take(p.planes_bytes(true)));
+    g.Bp = static_cast<uint16_t *>(c.take(p.planes_bytes(false)));
+    g.T = static_cast<float2 *>(c.take(p.T_bytes()));
+    g.words = static_cast<unsigned long long *>(c.take(64 * 8));
+    g.tab = c.take(p.table_bytes());
+    return g;
+}
+}  // namespace
+
+// C = A B for M x K and K x N complex128 matrices (row-major, device), by the sliced tensor-core
+// product of plan p (mode FP16X3 or integer slices); the workspace holds both operands' planes,
+// the slot tiles T, the scalar words and the tables (zgemm_work_bytes).
+size_t zgemm_work_bytes(const ZPlan &p)
+{
+    Carver c(nullptr);
+    carve_gemm(p, c);
+    return c.used;
+}
+
+cudaError_t zgemm_enqueue(ZPlan &p, const double2 *A, long lda, const double2 *B, long ldb, double2 *C, void *work,
+                          uint32_t *err, uint64_t wait_ns, cudaStream_t s)
+{
+    Carver c(work);
+    const GemmWork g = carve_gemm(p, c);
+    uint16_t *Ap = g.Ap, *Bp = g.Bp;
+    float2 *T = g.T;
+    unsigned long long *words = g.words;
+    cudaError_t e = p.upload(g.tab, s);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(words, 0, 64 * 8, s)) != cudaSuccess)
+        return e;
+    // words[0], [1]: max of A and B; [2]: max of C (unused), [3]: scratch
+    if ((e = launch_zmaxabs(A, p.M, p.K, lda, &words[0], s)) != cudaSuccess)
+        return e;
+    if ((e = launch_zmaxabs(B, p.K, p.N, ldb, &words[1], s)) != cudaSuccess)
+        return e;
+    if ((e = launch_zslice(p, true, A, lda, &words[0], Ap, nullptr, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_zslice(p, false, B, ldb, &words[1], Bp, nullptr, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_zgemm16(p, Ap, Bp, T, err, wait_ns, nullptr, s)) != cudaSuccess)
+        return e;
+    // C = 2^(eA + eB) sum_slot 2^wexp T; words[0] and [1] are W_EPS and W_X, untouched here
+    return launch_zcombine(p, T, &words[0], &words[1], 0.0, 1.0, nullptr, 0.0, C, 0.0, words, W_ZN, W_Z,
+                           W_DISCARD, DEV_STORE, 0.0, 0, nullptr, nullptr, s);
+}
+
+namespace {
+struct NsWork {
+    uint16_t *A16, *AOZ, *XA16, *XB16, *ZB16, *XBOZ;
+    float2 *T;
+    double2 *X, *Z;
+    unsigned long long *words;
+    int *skip;
+    void *tab16, *taboz;
+};
+
+NsWork carve_ns(const ZPlan &p16, const ZPlan &poz, int N, Carver &c)
+{
+    NsWork w;
+    const size_t nn = (size_t)N * N;
+    w.A16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(true)));
+    w.AOZ = static_cast<uint16_t *>(c.take(poz.planes_bytes(true)));
+    w.XA16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(true)));
+    w.XB16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(false)));
+    w.ZB16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(false)));
+    w.XBOZ = static_cast<uint16_t *>(c.take(poz.planes_bytes(false)));
+    w.T = static_cast<float2 *>(c.take(std::max(p16.T_bytes(), poz.T_bytes())));
+    w.X = static_cast<double2 *>(c.take(nn * sizeof(double2)));
+    w.Z = static_cast<double2 *>(c.take(nn * sizeof(double2)));
+    w.words = static_cast<unsigned long long *>(c.take(64 * 8));
+    w.skip = static_cast<int *>(c.take(64));
+    w.tab16 = c.take(p16.table_bytes());
+    w.taboz = c.take(poz.table_bytes());
+    return w;
+}
+}  // namespace
+
+// eps^-1 by the tensor-core Newton iteration (header comment).  A is eps (N x N, device).
+size_t ns_work_bytes(int N, int nsm)
+{
+    ZPlan p16, poz;
+    p16.build(MODE_FP16X3, N, N, N, nsm);
+    poz.build(MODE_SLICES, N, N, N, nsm);
+    Carver c(nullptr);
+    carve_ns(p16, poz, N, c);
+    return c.used;
+}
+
+// Report of the last inverse run on workspace `work` (synchronous read after the stream is idle):
+// out[0] FP16X3 steps of phase 1, [1] residual max |I - eps X| after phase 1, [2] the last measured
+// residual, [3] refinements that ran.
+cudaError_t ns_report(const void *work, int N, int nsm, double *out4)
+{
+    ZPlan p16, poz;
+    p16.build(MODE_FP16X3, N, N, N, nsm);
+    poz.build(MODE_SLICES, N, N, N, nsm);
+    Carver c(const_cast<void *>(work));
+    const NsWork w = carve_ns(p16, poz, N, c);
+    unsigned long long h[W_TOTAL];
+    const cudaError_t e = cudaMemcpy(h, w.words, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return e;
+    out4[0] = (double)h[W_ITERS];
+    out4[1] = __builtin_bit_cast(double, h[W_RES0]);
+    out4[2] = __builtin_bit_cast(double, h[W_RLAST]);
+    out4[3] = (double)h[W_NREF];
+    return cudaSuccess;
+}
+
+namespace {
+// Host read of a device flag (waits for the stream); a failed read counts as "not set".
+bool flag_set(const int *d_flag, cudaStream_t s)
+{
+    int h = 0;
+    if (cudaMemcpyAsync(&h, d_flag, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return h != 0;
+}
+}  // namespace
+
+// The kernels of every step check the device flags, so the result does not depend on the host
+// reads below: they only stop queuing steps that would return at once (after phase-1 steps 3, 5,
+// 7, ... and before the third refinement), at the price of one stream synchronisation each.
+cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
+                               uint64_t wait_ns, int nsm, cudaStream_t s)
+{
+    ZPlan p16, poz;
+    p16.build(MODE_FP16X3, N, N, N, nsm);
+    poz.build(MODE_SLICES, N, N, N, nsm);
+    Carver cv(work);
+    const NsWork nw = carve_ns(p16, poz, N, cv);
+    uint16_t *A16 = nw.A16, *AOZ = nw.AOZ, *XA16 = nw.XA16, *XB16 = nw.XB16, *ZB16 = nw.ZB16, *XBOZ = nw.XBOZ;
+    float2 *T = nw.T;
+    double2 *X = nw.X, *Z = nw.Z;
+    unsigned long long *words = nw.words;
+    int *skip = nw.skip;
+    void *tab16 = nw.tab16, *taboz = nw.taboz;
+    const size_t nn = (size_t)N * N;
+    cudaError_t e;
+#define NS_TRY(x)                      \
+    do {                               \
+        if ((e = (x)) != cudaSuccess)  \
+            return e;                  \
+    } while (0)
+    NS_TRY(p16.upload(tab16, s));
+    NS_TRY(poz.upload(taboz, s));
+    NS_TRY(cudaMemsetAsync(words, 0, 64 * 8, s));
+    // eps: its max, both slicings, and the row-sum bound for X0
+    NS_TRY(launch_zmaxabs(A, N, N, N, &words[W_EPS], s));
+    NS_TRY(launch_zslice(p16, true, A, N, &words[W_EPS], A16, nullptr, s));
+    NS_TRY(launch_zslice(poz, true, A, N, &words[W_EPS], AOZ, nullptr, s));
+    (void)rowsum;
+    row_sum_bound_kernel<<<std::max(1, std::min(152 * 4, (N + 7) / 8)), 256, 0, s>>>(A, N, words);
+    count_launches(1);
+    ns_init_kernel<<<grid_for(nn), 256, 0, s>>>(X, N, words, skip);  // skip[0]: phase 1, [1 + j]: refinement j
+    count_launches(1);
+    NS_TRY(cudaGetLastError());
+    // phase 1: X <- X (2I - eps X) with FP16X3 products, stopped on device below NS_TOL
+    for (int it = 0; it < NS_MAX; ++it) {
+        NS_TRY(launch_zslice(p16, false, X, N, &words[W_X], XB16, skip, s));
+        NS_TRY(launch_zgemm16(p16, A16, XB16, T, err, wait_ns, skip, s));
+        // Z = 2I - eps X; deviation |Z - I| = |I - eps X|
+        NS_TRY(launch_zcombine(p16, T, &words[W_EPS], &words[W_X], 2.0, -1.0, nullptr, 0.0, Z, 1.0, words, W_ZN, W_Z,
+                               W_DISCARD, DEV_PHASE1, NS_TOL, it, skip, skip, s));
+        NS_TRY(launch_zslice(p16, true, X, N, &words[W_X], XA16, skip, s));
+        NS_TRY(launch_zslice(p16, false, Z, N, &words[W_Z], ZB16, skip, s));
+        NS_TRY(launch_zgemm16(p16, XA16, ZB16, T, err, wait_ns, skip, s));
+        NS_TRY(launch_zcombine(p16, T, &words[W_X], &words[W_Z], 0.0, 1.0, nullptr, 0.0, X, 0.0, words, W_XN, W_X,
+                               W_DISCARD, DEV_STORE, 0.0, it, skip, nullptr, s));
+        if (it >= 3 && (it & 1) && flag_set(skip, s))
+            break;
+    }
+    // phase 2: R = I - eps X to FP64 accuracy (integer slices), X <- X + X R (FP16X3); refinement
+    // j runs unless an earlier one measured a residual <= NS_LAST (flag skip[1 + j])
+    for (int j = 0; j < NS_REFINE; ++j) {
+        const int *sk = skip + 1 + j;
+        if (j == 2 && flag_set(sk, s))
+            break;
+        NS_TRY(launch_zslice(poz, false, X, N, &words[W_X], XBOZ, sk, s));
+        NS_TRY(launch_zslice(p16, true, X, N, &words[W_X], XA16, sk, s));
+        NS_TRY(launch_zgemm16(poz, AOZ, XBOZ, T, err, wait_ns, sk, s));
+        NS_TRY(launch_zcombine(poz, T, &words[W_EPS], &words[W_X], 1.0, -1.0, nullptr, 0.0, Z, 0.0, words, W_ZN, W_Z,
+                               j == 0 ? W_RES0 : W_DISCARD, DEV_REFINE, NS_LAST, j, sk, skip + 1, s));
+        NS_TRY(launch_zslice(p16, false, Z, N, &words[W_Z], ZB16, sk, s));
+        NS_TRY(launch_zgemm16(p16, XA16, ZB16, T, err, wait_ns, sk, s));
+        NS_TRY(launch_zcombine(p16, T, &words[W_X], &words[W_Z], 0.0, 1.0, X, 1.0, X, 0.0, words, W_XN, W_X,
+                               W_DISCARD, DEV_STORE, 0.0, j, sk, nullptr, s));
+    }
+    NS_TRY(cudaMemcpyAsync(Xout, X, nn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    ns_final_kernel<<<1, 1, 0, s>>>(words, err);
+    count_launches(1);
+#undef NS_TRY
+    return cudaGetLastError();
+}
+
+}  // namespace gw

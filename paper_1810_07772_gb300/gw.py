@@ -18,7 +18,8 @@ LIB_PATH = _build.LIB_PATH
 
 GW_OK, GW_E_INVALID, GW_E_NOMEM, GW_E_CUDA, GW_E_NOT_READY, GW_E_NUMERIC, GW_E_TIMEOUT, GW_E_UNSUPPORTED = range(8)
 PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
-INV_METHOD = {"cholesky": 0, "newton": 1}
+INV_METHOD = {"cholesky": 0, "newton": 1, "newton_tc": 2}
+ZGEMM_MODE = {"fp16x3": 0, "slices": 1}
 GW_C64, GW_C128 = 0, 1
 BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5}
 
@@ -48,6 +49,9 @@ SIGNATURES = {
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
     "gw_eps_inv_noalloc": (_i, [_vp, _i, _vp, _vp]),
+    "gw_zgemm_tc": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _vp, _i, _vp]),
+    "gw_zinv_tc": (_i, [_vp, _i, _vp, _vp]),
+    "gw_newton_tc_report": (_i, [_vp, _c.POINTER(_c.c_double)]),
     "gw_batch_create": (_i, [_c.POINTER(_vp), _c.POINTER(_vp), _i, _c.POINTER(_i), _i]),
     "gw_batch_destroy": (_i, [_vp]),
     "gw_batch_run": (_i, [_vp, _i]),
@@ -212,6 +216,41 @@ class Context:
     def eps_inv(self, method="cholesky", eps_out=None, epsinv_out=None):
         m = INV_METHOD[method] if isinstance(method, str) else int(method)
         self._check(lib().gw_eps_inv(self._h, m, _ptr(eps_out), _ptr(epsinv_out)))
+
+    def zgemm_tc(self, A, B, mode="slices", C=None):
+        """C = A B for device complex128 tensors (A: M x K, B: K x N, rows may be strided) on the
+        tensor cores: mode "slices" has FP64 accuracy, "fp16x3" about 1e-6 (gw_zgemm_tc)."""
+        import torch
+        M, K = A.shape
+        K2, N = B.shape
+        if K2 != K or A.dtype != torch.complex128 or B.dtype != torch.complex128 or A.stride(1) != 1 or B.stride(1) != 1:
+            raise GwError(GW_E_INVALID, "zgemm_tc: complex128 A (M x K), B (K x N) with unit column stride")
+        if C is None:
+            C = torch.empty((M, N), dtype=torch.complex128, device=A.device)
+        m = ZGEMM_MODE[mode] if isinstance(mode, str) else int(mode)
+        # rows may be strided (unit column stride checked above), so pass the addresses directly
+        self._check(lib().gw_zgemm_tc(self._h, m, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                      _ptr(C)))
+        return C
+
+    def zinv_tc(self, A, X=None):
+        """A^-1 of a Hermitian positive definite device complex128 matrix by the tensor-core Newton
+        iteration (gw_zinv_tc)."""
+        import torch
+        n = A.shape[0]
+        if A.shape != (n, n) or A.dtype != torch.complex128 or not A.is_contiguous():
+            raise GwError(GW_E_INVALID, "zinv_tc: contiguous complex128 n x n")
+        if X is None:
+            X = torch.empty_like(A)
+        self._check(lib().gw_zinv_tc(self._h, n, _ptr(A), _ptr(X)))
+        return X
+
+    def newton_tc_report(self):
+        """Phase-1 steps, residual after phase 1, last measured residual and refinements of the
+        last tensor-core Newton inverse (gw_newton_tc_report)."""
+        d = (ctypes.c_double * 4)()
+        self._check(lib().gw_newton_tc_report(self._h, d))
+        return {"steps": int(d[0]), "res_phase1": d[1], "res_last": d[2], "refinements": int(d[3])}
 
     # ------------------------------------------------------------------ helpers
     def sync(self):

@@ -1,0 +1,148 @@
+"""The tensor-core Newton inverse of Sec. 5.1 (gw_eps_inv with GW_INV_NEWTON_TC, gw_zinv_tc) and
+the sliced complex GEMM under it (gw_zgemm_tc): integer slices against exact integer products and
+FP64 products, the FP16X3 split, and eps^-1 against the oracle's FP64 Cholesky inverse."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_1810_07772_gb300 import gw, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).to(DEV)
+
+
+def crand(rng, m, n):
+    return rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+
+
+def exact_product(Ar, Ai, Br, Bi):
+    """(Ar + i Ai)(Br + i Bi) for int64 matrices, in int64 (no rounding anywhere)."""
+    return Ar @ Br - Ai @ Bi, Ar @ Bi + Ai @ Br
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 77, 45), (257, 300, 691), (64, 40, 2100)])
+def test_slices_exact_on_small_integers(M, N, K):
+    """Entries with |Re|, |Im| <= 31 are one slice each, every product and partial sum is an
+    integer below 2^24, so C equals the integer product exactly (K = 2100 uses two K ranges)."""
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    Ar, Ai = rng.integers(-31, 32, (M, K)), rng.integers(-31, 32, (M, K))
+    Br, Bi = rng.integers(-31, 32, (K, N)), rng.integers(-31, 32, (K, N))
+    Cr, Ci = exact_product(Ar, Ai, Br, Bi)
+    with gw.Context(0) as ctx:
+        C = ctx.zgemm_tc(dev(Ar + 1j * Ai), dev(Br + 1j * Bi), "slices").cpu().numpy()
+    assert np.array_equal(C.real, Cr.astype(np.float64))
+    assert np.array_equal(C.imag, Ci.astype(np.float64))
+
+
+def test_slices_fp64_accuracy_and_strided_rows():
+    """Random FP64 operands (one with rows spread over 2^-20 .. 1): error per entry within
+    K 2^-52 max|A| max|B| of the FP64 product, as the slicing bounds it."""
+    rng = np.random.default_rng(5)
+    M, N, K = 300, 200, 517
+    A = crand(rng, M, K) * 2.0 ** rng.uniform(-20, 0, (M, 1))
+    Bfull = crand(rng, K, N + 9)
+    B = dev(Bfull)[:, :N]                      # row stride N + 9
+    with gw.Context(0) as ctx:
+        C = ctx.zgemm_tc(dev(A), B, "slices").cpu().numpy()
+    ref = A @ Bfull[:, :N]
+    bound = K * 2.0 ** -52 * np.abs(A).max() * np.abs(Bfull).max()
+    assert np.max(np.abs(C - ref)) <= bound
+    assert np.max(np.abs(C - ref)) / np.max(np.abs(ref)) < 1e-14
+
+
+def test_fp16x3_split():
+    rng = np.random.default_rng(6)
+    A, B = crand(rng, 200, 333), crand(rng, 333, 150)
+    with gw.Context(0) as ctx:
+        C = ctx.zgemm_tc(dev(A), dev(B), "fp16x3").cpu().numpy()
+    ref = A @ B
+    assert np.max(np.abs(C - ref)) / np.max(np.abs(ref)) < 1e-5
+
+
+def test_arguments_rejected():
+    with gw.Context(0) as ctx:
+        A = dev(np.eye(4))
+        with pytest.raises(gw.GwError):
+            ctx.zgemm_tc(A, A, mode=3)
+        with pytest.raises(gw.GwError):
+            ctx.zgemm_tc(A.cpu(), A.cpu())        # host pointers
+        with pytest.raises(gw.GwError):
+            ctx.zinv_tc(A.cpu())
+
+
+def hpd(rng, n, lo, hi):
+    Q, _ = np.linalg.qr(crand(rng, n, n))
+    lam = rng.uniform(lo, hi, n)
+    return (Q * lam) @ Q.conj().T
+
+
+@pytest.mark.parametrize("n", [1, 93, 200, 517])
+def test_zinv_tc_random_hpd(n):
+    rng = np.random.default_rng(n)
+    A = hpd(rng, n, 1.0, 10.0)
+    with gw.Context(0) as ctx:
+        try:
+            X = ctx.zinv_tc(dev(A)).cpu().numpy()
+        finally:
+            print(n, ctx.newton_tc_report())
+        iters = ctx.stats()["newton_iters"]
+        rep = ctx.newton_tc_report()
+    ref = np.linalg.inv(A)
+    assert np.max(np.abs(X - ref)) <= 1e-12
+    assert np.max(np.abs(X @ A - np.eye(n))) <= 1e-12
+    assert 0 <= iters < 16 and iters == rep["steps"]
+    assert 1 <= rep["refinements"] <= 3 and rep["res_last"] <= 1e-8
+
+
+def test_zinv_tc_indefinite_is_numeric_error():
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(crand(rng, 64, 64))
+    lam = np.concatenate([rng.uniform(-1.0, -0.5, 8), rng.uniform(1.0, 2.0, 56)])
+    A = (Q * lam) @ Q.conj().T
+    with gw.Context(0) as ctx:
+        with pytest.raises(gw.GwError) as e:
+            ctx.zinv_tc(dev(A))
+        assert e.value.status == gw.GW_E_NUMERIC
+        # the context stays usable
+        X = ctx.zinv_tc(dev(np.eye(8) * 2.0)).cpu().numpy()
+    assert np.allclose(X, np.eye(8) * 0.5, rtol=0, atol=1e-15)
+
+
+def eps_pair(w, route):
+    psi, E = inputs.make_workload_states(w)
+    dims = (w.n,) * 3
+    with gw.Context(0) as ctx:
+        ctx.load_states(torch.from_numpy(psi.astype(np.complex64)).to(DEV), E, dims, w.nv)
+        if route == "gspace":
+            g = ctx.build_PG(w.gcut)
+        else:
+            ctx.build_P("fp16x3")
+            g = ctx.P_to_G(w.gcut)
+        ng = len(g)
+        out = {}
+        for m in ("cholesky", "newton_tc"):
+            eps = torch.empty((ng, ng), dtype=torch.complex128, device=DEV)
+            inv = torch.empty_like(eps)
+            ctx.eps_inv(m, eps_out=eps, epsinv_out=inv)
+            resid = float((inv @ eps - torch.eye(ng, dtype=torch.complex128, device=DEV)).abs().max())
+            out[m] = (eps.cpu().numpy(), inv.cpu().numpy(), resid, ctx.stats()["newton_iters"])
+    return out
+
+
+@pytest.mark.parametrize("w,route", [(inputs.SMALL, "rspace"), (inputs.PLAIN, "gspace")])
+def test_eps_inv_newton_tc_matches_cholesky(w, route):
+    out = eps_pair(w, route)
+    eps, inv_c, res_c, _ = out["cholesky"]
+    eps2, inv_t, res_t, iters = out["newton_tc"]
+    assert np.array_equal(eps, eps2)
+    ref = O.inverse_cholesky(eps)
+    assert np.max(np.abs(inv_t - ref)) <= 1e-12
+    assert np.max(np.abs(inv_t - inv_c)) <= 1e-12
+    assert res_t <= 1e-12
+    assert 0 <= iters < 16

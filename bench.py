@@ -34,7 +34,7 @@ from paper_1810_07772_gb300 import inputs  # noqa: E402
 
 METRIC = "P-build TFLOP/s (4kN_r(N_r+1) per step, states resident -> eps^-1)"
 PRECISION = "fp16x3"
-INV_METHOD = "cholesky"
+INV_METHOD = "newton_tc"
 WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
              "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41),
              "split": inputs.SPLIT, "batch": None, "learned": None}
@@ -354,7 +354,7 @@ def run_gw(args):
             ctx.load_states(psi_d, E, dims, w.nv)
             ctx.build_P(prec)
             ctx.P_to_G(w.gcut)
-            ctx.eps_inv("cholesky")
+            ctx.eps_inv(args.inv)
             torch.cuda.synchronize()
             n = 3
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -363,7 +363,7 @@ def run_gw(args):
                 ctx.load_states(psi_d, E, dims, w.nv)
                 ctx.build_P(prec)
                 ctx.P_to_G(w.gcut)
-                ctx.eps_inv("cholesky")
+                ctx.eps_inv(args.inv)
             b.record(stream)
             torch.cuda.synchronize()
             PGv = torch.empty((ng, ng), dtype=torch.complex64, device=dev)
@@ -373,7 +373,7 @@ def run_gw(args):
         # the g-space route: sphere transforms of the pair densities and an N_g x N_g update (no P)
         ctx.load_states(psi_d, E, dims, w.nv)
         ctx.build_PG(w.gcut, args.precision)
-        ctx.eps_inv("cholesky")
+        ctx.eps_inv(args.inv)
         torch.cuda.synchronize()
         n = 5
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -381,7 +381,7 @@ def run_gw(args):
         for _ in range(n):
             ctx.load_states(psi_d, E, dims, w.nv)
             ctx.build_PG(w.gcut, args.precision)
-            ctx.eps_inv("cholesky")
+            ctx.eps_inv(args.inv)
         b.record(stream)
         torch.cuda.synchronize()
         PGv = torch.empty((ng, ng), dtype=torch.complex64, device=dev)
@@ -408,8 +408,11 @@ def run_gw(args):
                 "herk_ms": herk_ms}
 
     part = {"fp16x3": "FP16", "bf16x3": "BF16"}.get(args.precision)
+    inv_note = ("eps in FP64; eps^-1 by the Newton iteration of Sec. 5.1 on the tensor cores, refined with "
+                "residuals exact to FP64 from integer slices (FP64 accuracy)" if args.inv == "newton_tc"
+                else "eps and eps^-1 (Cholesky) in FP64")
     prec_note = (f"{args.precision}: {part} hi+lo split, 3 products, FP32 accumulation (TMEM windows promoted to "
-                 "FP32); eps and eps^-1 in FP64" if part else f"{args.precision}; eps and eps^-1 in FP64")
+                 f"FP32); {inv_note}" if part else f"{args.precision}; {inv_note}")
     f_gb = (w.k + 15) // 16 * 16 * ((w.nr + 255) // 256 * 256) * 8 / 1e9
     p_gb = w.nr * w.nr * 8 / 1e9
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -609,7 +612,7 @@ def run_learned(args):
             for P in (d["PG_all"], P_ml, d["PG_keep"]):
                 ctx.view("PG").copy_(P)
                 inv = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
-                ctx.eps_inv("cholesky", epsinv_out=inv)
+                ctx.eps_inv(args.inv, epsinv_out=inv)
                 invs.append(inv)
             e_inv.append(rel(invs[1], invs[0]))
             e_inv_tr.append(rel(invs[2], invs[0]))
@@ -623,18 +626,18 @@ def run_learned(args):
         g = ctx.build_PG(gcut, args.precision)
         PG = ctx.view("PG")
         learned.correct(net, PG, g, gcut, E, nv, keep, out=PG)
-        ctx.eps_inv("cholesky")
+        ctx.eps_inv(args.inv)
 
     def step_full():          # the full sum by the faster plain route (g-space)
         ctx.load_states(psi, E, dims, nv)
         ctx.build_PG(gcut, args.precision)
-        ctx.eps_inv("cholesky")
+        ctx.eps_inv(args.inv)
 
     def step_full_rspace():   # the full sum through P(r,r')
         ctx.load_states(psi, E, dims, nv)
         ctx.build_P(args.precision)
         ctx.P_to_G(gcut)
-        ctx.eps_inv("cholesky")
+        ctx.eps_inv(args.inv)
 
     res = {}
     with ClockSampler(0) as clk:

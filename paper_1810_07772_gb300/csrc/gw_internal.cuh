@@ -233,12 +233,14 @@ cudaError_t launch_row_abs_sum_max(const double2 *A, int n, double *out, cudaStr
 // tensor-core Newton iteration for eps^-1.
 struct ZPlan {
     int mode = 0;  // 0 = FP16X3 split, 1 = integer slices (FP64 accuracy)
-    int M = 0, N = 0, K = 0, Mpad = 0, Npad = 0, nkc = 0, ntiles = 0, ns = 0, nslots = 0, npairs = 0;
+    int M = 0, N = 0, K = 0, Mpad = 0, Npad = 0, nkc = 0, ntiles = 0, nslots = 0, npairs = 0;
+    int ns = 0;   // slices of B (and the pairs t + u < ns); FP16X3: 2 (hi, lo)
+    int nsA = 0;  // slices held in the A planes (>= ns; the refinement reuses eps's nine)
     std::vector<int2> host_pairs;
     std::vector<int> host_slots, host_wexp;
     int2 *d_pairs = nullptr;
     int *d_slots = nullptr, *d_wexp = nullptr;
-    void build(int mode, int M, int N, int K, int nsm);
+    void build(int mode, int M, int N, int K, int nsm, int slices = 0, int slicesA = 0);
     size_t table_bytes() const;
     size_t planes_bytes(bool a_operand) const;
     size_t T_bytes() const;

@@ -43,8 +43,8 @@ namespace {
 constexpr int ZT = 128;
 constexpr uint32_t ZPL = ZT * 16 * 2;       // 4 KB: one plane of one 128-row block, one chunk
 constexpr uint32_t ZSTAGE = 5 * ZPL;        // A Re, A Im, B -Im, B Re, B Im
-constexpr int ZSTAGES = 4;
-constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 80 KB: two CTAs per SM
+constexpr int ZSTAGES = 5;                  // ten stages in flight per SM cover the copy latency
+constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 100 KB: two CTAs per SM
 static_assert(128 * 65 * 8 <= ZPIPE, "epilogue staging must fit in the pipeline buffers");
 constexpr size_t ZSMEM = ZPIPE + 128;
 constexpr int ZTHREADS = 192;               // warp 0 copies, warp 1 MMAs, warps 2..5 epilogue
@@ -58,15 +58,16 @@ constexpr double NS_LAST = 1e-9;    // a refinement whose residual is below this
 constexpr double NS_ACCEPT = 1e-8;  // largest residual before the last correction
 constexpr int NS_MAX = 16, NS_REFINE = 3;
 
-// Scale exponent e of a matrix from the bits of max(|Re|, |Im|): max < 2^e (0 for an all-zero or
-// non-finite matrix; a non-finite residual is caught by the final check).
+// Scale exponent e of a matrix from the bits of max(|Re|, |Im|): m (1 + 2^-20) < 2^e, so a max
+// taken in FP32 (relative error 2^-24) still bounds every entry (0 for an all-zero or non-finite
+// matrix; a non-finite residual is caught by the final check).
 __device__ __forceinline__ int exp_of(const unsigned long long *w)
 {
     const double m = __longlong_as_double((long long)*w);
     if (!(m > 0.0) || !isfinite(m))
         return 0;
     int e;
-    frexp(m, &e);
+    frexp(m * (1.0 + 0x1p-20), &e);
     return e;
 }
 
@@ -100,17 +101,23 @@ __device__ __forceinline__ uint16_t h16(float x)
 // double, which order like unsigned integers).  *w must be zero (or smaller) beforehand.
 __global__ void zmaxabs_kernel(const double2 *__restrict__ M, int rows, int cols, long ld, unsigned long long *w)
 {
+    __shared__ double red[32];
     double best = 0.0;
-    const size_t total = (size_t)rows * cols;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = i / cols, c = i - r * cols;
-        const double2 z = M[r * ld + c];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = blockIdx.y; r < rows && c < cols; r += gridDim.y) {
+        const double2 z = M[(size_t)r * ld + c];
         best = fmax(best, fmax(fabs(z.x), fabs(z.y)));
     }
     for (int o = 16; o > 0; o >>= 1)
         best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+            best = fmax(best, red[i]);
         atomicMax(w, (unsigned long long)__double_as_longlong(best));
+    }
 }
 
 // Slice a complex128 matrix into operand planes (layouts above).  One block per (16-wide chunk
@@ -120,10 +127,10 @@ __global__ void zmaxabs_kernel(const double2 *__restrict__ M, int rows, int cols
 // is column r of M (B operand, element (r, k) = M[k][r]).  npl = 2 (A: Re, Im) or 3 (B: -Im, Re,
 // Im) planes per slice.  Entries outside rows x K are zero.
 //   FP16X3: y = float(x) 2^(14 - e), hi = rn16(y), lo = rn16(y - hi).
-//   slices: n = rint(x 2^(54 - e)) (|n| <= 2^54) written in balanced base 64,
-//           n = sum_t a_t 2^(6 (8 - t)): a_8 .. a_1 in [-32, 31] from the low end, a_0 = the rest,
-//           |a_0| <= 64; so x 2^-e = sum_t a_t 2^(-6 (t + 1)) up to 2^-55.
-__global__ void __launch_bounds__(256) zslice_kernel(const double2 *__restrict__ M, long ld, int rows, int K,
+//   slices: n = rint(x 2^(6 ns - e)) (|n| <= 2^(6 ns)) written in balanced base 64,
+//           n = sum_t a_t 2^(6 (ns - 1 - t)): a_(ns-1) .. a_1 in [-32, 31] from the low end, a_0 =
+//           the rest, |a_0| <= 64; so x 2^-e = sum_t a_t 2^(-6 (t + 1)) up to 2^(-6 ns - 1).
+__global__ void __launch_bounds__(512) zslice_kernel(const double2 *__restrict__ M, long ld, int rows, int K,
                                                      int transpose, int Rpad, int mode, int ns, int npl,
                                                      const unsigned long long *maxw, uint16_t *__restrict__ planes,
                                                      const int *skip)
@@ -135,24 +142,31 @@ __global__ void __launch_bounds__(256) zslice_kernel(const double2 *__restrict__
     const int k0 = kc * 16, r0 = rb * 128;
     const double2 zero = make_double2(0.0, 0.0);
     if (transpose) {
-        for (int q = threadIdx.x; q < 2048; q += 256) {
+        for (int q = threadIdx.x; q < 2048; q += blockDim.x) {
             const int kk = q >> 7, rr = q & 127, r = r0 + rr, k = k0 + kk;
             tile[kk][rr] = (r < rows && k < K) ? M[(size_t)k * ld + r] : zero;
         }
     } else {
-        for (int q = threadIdx.x; q < 2048; q += 256) {
+        for (int q = threadIdx.x; q < 2048; q += blockDim.x) {
             const int rr = q >> 4, kk = q & 15, r = r0 + rr, k = k0 + kk;
             tile[kk][rr] = (r < rows && k < K) ? M[(size_t)r * ld + k] : zero;
         }
     }
+    // the scales once per block: FP64 work per thread would rival the slicing itself here
+    __shared__ float s_scf;
+    __shared__ double s_scd;
+    if (threadIdx.x == 0) {
+        const int e = exp_of(maxw);
+        s_scf = ldexpf(1.0f, 14 - e);
+        s_scd = ldexp(1.0, 6 * ns - e);
+    }
     __syncthreads();
-    const int e = exp_of(maxw);
     const int NP = ns * npl;
     const size_t per = (size_t)Rpad * 16;
     uint16_t *base0 = planes + (size_t)kc * NP * per + (size_t)rb * 2048;
-    const float scf = ldexpf(1.0f, 14 - e);
-    const double scd = ldexp(1.0, 54 - e);
-    for (int rem = threadIdx.x; rem < 2048; rem += 256) {
+    const float scf = s_scf;
+    const double scd = s_scd;
+    for (int rem = threadIdx.x; rem < 2048; rem += blockDim.x) {
         const int rr = (rem >> 7) * 8 + ((rem & 63) >> 3);
         const int kk = ((rem & 127) >> 6) * 8 + (rem & 7);
         const double2 z = tile[kk][rr];
@@ -415,7 +429,7 @@ __device__ void combine_tail(float best, float dev, unsigned long long *words, i
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0)
-        last = atomicAdd(&words[W_COUNT], 1ull) == gridDim.x - 1;
+        last = atomicAdd(&words[W_COUNT], 1ull) == (unsigned long long)gridDim.x * gridDim.y - 1;
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
@@ -459,11 +473,19 @@ __global__ void zcombine16_kernel(const float2 *__restrict__ T, int nslots, int 
 {
     if (skip && *skip)
         return;
-    const double sc = cC * ldexp(1.0, exp_of(wA) + exp_of(wB) - 28);
+    // FP64 runs at 1/64 of the FP32 rate here, so the product part stays in FP32 (it carries the
+    // split's 22 bits only) and each entry takes one conversion plus the FP64 terms it needs
+    __shared__ float s_sc;
+    if (threadIdx.x == 0)
+        s_sc = (float)(cC * ldexp(1.0, exp_of(wA) + exp_of(wB) - 28));
+    __syncthreads();
+    const float sc = s_sc;
+    const float cIf = (float)cI, cIref = (float)(cI - ref), cDf = (float)cD;
     float best = 0.f, dev = 0.f;
-    const size_t total = (size_t)M * N, plane = (size_t)Mpad * Npad;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = static_cast<int>(i / N), c = static_cast<int>(i - (size_t)r * N);
+    const size_t plane = (size_t)Mpad * Npad;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = blockIdx.y; r < M && c < N; r += gridDim.y) {
+        const size_t i = (size_t)r * N + c;
         const float2 *t = T + (size_t)r * Npad + c;
         float sr = 0.f, si = 0.f;
         for (int s = 0; s < nslots; ++s) {
@@ -471,18 +493,24 @@ __global__ void zcombine16_kernel(const float2 *__restrict__ T, int nslots, int 
             sr += v.x;
             si += v.y;
         }
-        double xr = sc * (double)sr, xi = sc * (double)si;
-        if (r == c)
+        const float pr = sr * sc, pi = si * sc;  // the product term, exact scaling by 2^k
+        double xr = (double)pr, xi = (double)pi;
+        float fr = pr, fi = pi, dr = pr;
+        if (r == c) {
             xr += cI;
+            fr += cIf;
+            dr += cIref;
+        }
         if (D) {
             const double2 d = D[i];
             xr = fma(cD, d.x, xr);
             xi = fma(cD, d.y, xi);
+            fr += cDf * (float)d.x;
+            fi += cDf * (float)d.y;
+            dr = fr - (r == c ? (float)ref : 0.f);
         }
         out[i] = make_double2(xr, xi);
-        const float fr = (float)xr, fi = (float)xi;
         best = fmaxf(best, fmaxf(fabsf(fr), fabsf(fi)));
-        const float dr = r == c ? (float)(xr - ref) : fr;
         dev = fmaxf(dev, finite_or_inf(sqrtf(dr * dr + fi * fi)));
     }
     combine_tail(best, dev, words, acc_max, fin_max, dev_to, use, tol, iter, flags);
@@ -511,17 +539,24 @@ __global__ void zcombine_int_kernel(const float2 *__restrict__ T, int nslots, co
     if (skip && *skip)
         return;
     __shared__ int shift[256];
+    __shared__ int s_eab;
+    __shared__ double s_sc;
     for (int s = threadIdx.x; s < nslots && s < 256; s += blockDim.x)
         shift[s] = wexp[s] + 60;  // 6 (8 - d) in [0, 48]
+    if (threadIdx.x == 0) {
+        s_eab = exp_of(wA) + exp_of(wB);
+        s_sc = ldexp(1.0, s_eab - 60);
+    }
     __syncthreads();
-    const int eab = exp_of(wA) + exp_of(wB);
+    const int eab = s_eab;
     const int ish = 60 - eab;  // I in units of 2^(eab - 60)
     const bool exact_i = ish >= 0 && ish <= 120;
-    const double sc = ldexp(1.0, eab - 60);
+    const double sc = s_sc;
     float best = 0.f, dev = 0.f;
-    const size_t total = (size_t)M * N, plane = (size_t)Mpad * Npad;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = static_cast<int>(i / N), c = static_cast<int>(i - (size_t)r * N);
+    const size_t plane = (size_t)Mpad * Npad;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = blockIdx.y; r < M && c < N; r += gridDim.y) {
+        const size_t i = (size_t)r * N + c;
         const float2 *t = T + (size_t)r * Npad + c;
         __int128 ar = 0, ai = 0;
         for (int s = 0; s < nslots; ++s) {
@@ -570,12 +605,10 @@ __global__ void row_sum_bound_kernel(const double2 *__restrict__ A, int n, unsig
 __global__ void ns_init_kernel(double2 *X, int N, unsigned long long *words, int *flags)
 {
     const double c = 2.0 / (1.0 + __longlong_as_double((long long)words[W_U]));
-    const size_t total = (size_t)N * N;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = i / N, col = i - r * N;
-        X[i] = make_double2(r == col ? c : 0.0, 0.0);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = blockIdx.y; r < N && col < N; r += gridDim.y)
+        X[(size_t)r * N + col] = make_double2(r == col ? c : 0.0, 0.0);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         words[W_X] = (unsigned long long)__double_as_longlong(fabs(c));
         words[W_ITERS] = (unsigned long long)NS_MAX;
         for (int j = 0; j <= NS_REFINE + 1; ++j)
@@ -590,12 +623,13 @@ __global__ void ns_final_kernel(const unsigned long long *words, uint32_t *err)
         record_error(err, GW_E_NUMERIC, SITE_NS, 0);
 }
 
-int grid_for(size_t n)
+// Grid of the element-wise kernels over an M x N matrix: x covers the columns in 256-thread blocks,
+// y strides over the rows, about eight blocks per SM in all.
+dim3 grid2d(int M, int N)
 {
-    size_t g = (n + 255) / 256;
-    if (g > 152 * 8)
-        g = 152 * 8;
-    return g < 1 ? 1 : static_cast<int>(g);
+    const int gx = std::max(1, (N + 255) / 256);
+    const int gy = std::max(1, std::min(M, std::max(1, 152 * 8 / gx)));
+    return dim3(gx, gy);
 }
 
 int round_up(int x, int m)
@@ -611,7 +645,7 @@ int round_up(int x, int m)
 // K range split so that tiles x slots fills the GPU); slices = the pairs (t, u) with t + u <= 8,
 // grouped by t + u into slots whose exact-sum bound sum 2 m_t m_u K_range stays below 2^24
 // (m_0 = 64, m_t = 32) and that hold at most five pairs.
-void ZPlan::build(int mode_, int M_, int N_, int K_, int nsm)
+void ZPlan::build(int mode_, int M_, int N_, int K_, int nsm, int slices, int slicesA)
 {
     mode = mode_;
     M = M_;
@@ -621,7 +655,8 @@ void ZPlan::build(int mode_, int M_, int N_, int K_, int nsm)
     Npad = round_up(std::max(N, 1), ZT);
     nkc = round_up(std::max(K, 1), 16) / 16;
     ntiles = (Mpad / ZT) * (Npad / ZT);
-    ns = mode == MODE_FP16X3 ? 2 : OZ_SLICES;
+    ns = mode == MODE_FP16X3 ? 2 : std::max(1, std::min(OZ_SLICES, slices > 0 ? slices : OZ_SLICES));
+    nsA = std::max(ns, slicesA > 0 ? std::min(OZ_SLICES, slicesA) : ns);  // planes in the A operand
     std::vector<int2> pr;
     std::vector<int> sl, we;  // slot: p0, p1, kc0, kc1
     auto add_slot = [&](int p0, int p1, int kc0, int kc1, int w) {
@@ -676,7 +711,7 @@ size_t ZPlan::table_bytes() const
 size_t ZPlan::planes_bytes(bool a_operand) const
 {
     const int npl = a_operand ? 2 : 3;
-    return (size_t)nkc * ns * npl * (a_operand ? Mpad : Npad) * 16 * sizeof(uint16_t);
+    return (size_t)nkc * (a_operand ? nsA : ns) * npl * (a_operand ? Mpad : Npad) * 16 * sizeof(uint16_t);
 }
 
 size_t ZPlan::T_bytes() const
@@ -702,7 +737,7 @@ cudaError_t ZPlan::upload(void *tab, cudaStream_t s)
 
 cudaError_t launch_zmaxabs(const double2 *M, int rows, int cols, long ld, unsigned long long *w, cudaStream_t s)
 {
-    zmaxabs_kernel<<<grid_for((size_t)rows * cols), 256, 0, s>>>(M, rows, cols, ld, w);
+    zmaxabs_kernel<<<grid2d(rows, cols), 256, 0, s>>>(M, rows, cols, ld, w);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -711,7 +746,8 @@ cudaError_t launch_zslice(const ZPlan &p, bool a_operand, const double2 *Mx, lon
                           uint16_t *planes, const int *skip, cudaStream_t s)
 {
     const int rows = a_operand ? p.M : p.N, Rpad = a_operand ? p.Mpad : p.Npad;
-    zslice_kernel<<<dim3(p.nkc, Rpad / ZT), 256, 0, s>>>(Mx, ld, rows, p.K, a_operand ? 0 : 1, Rpad, p.mode, p.ns,
+    zslice_kernel<<<dim3(p.nkc, Rpad / ZT), 512, 0, s>>>(Mx, ld, rows, p.K, a_operand ? 0 : 1, Rpad, p.mode,
+                                                         a_operand ? p.nsA : p.ns,
                                                          a_operand ? 2 : 3, maxw, planes, skip);
     count_launches(1);
     return cudaGetLastError();
@@ -724,7 +760,7 @@ cudaError_t launch_zgemm16(const ZPlan &p, const uint16_t *Ap, const uint16_t *B
     if (e != cudaSuccess)
         return e;
     dim3 grid(p.ntiles, p.nslots);
-    zgemm16_kernel<<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.ns, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+    zgemm16_kernel<<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
                                                  reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT, T, err,
                                                  wait_ns, skip);
     count_launches(1);
@@ -738,7 +774,7 @@ cudaError_t launch_zcombine(const ZPlan &p, const float2 *T, const unsigned long
                             double2 *out, double ref, unsigned long long *words, int acc_max, int fin_max, int dev_to,
                             int use, double tol, int iter, const int *skip, int *flags, cudaStream_t s)
 {
-    const int grid = grid_for((size_t)p.M * p.N);
+    const dim3 grid(grid2d(p.M, p.N));
     if (p.mode == MODE_FP16X3) {
         zcombine16_kernel<<<grid, 256, 0, s>>>(T, p.nslots, p.Mpad, p.Npad, wA, wB, p.M, p.N, cI, cC, D, cD, out, ref,
                                                words, acc_max, fin_max, dev_to, use, tol, iter, skip, flags);
@@ -832,10 +868,22 @@ struct NsWork {
     double2 *X, *Z;
     unsigned long long *words;
     int *skip;
-    void *tab16, *taboz;
+    void *tab16, *taboz, *taboz7;
 };
 
-NsWork carve_ns(const ZPlan &p16, const ZPlan &poz, int N, Carver &c)
+// The first refinement only has to bring max |I - eps X| from the FP16X3 floor (~1e-6) to where
+// the second can finish, so its residual uses seven slices (2^-42 relative, 28 slice pairs) of X
+// against the nine of eps; the second uses nine (45 pairs).
+constexpr int NS_SLICES_FIRST = 7;
+
+void ns_plans(int N, int nsm, ZPlan &p16, ZPlan &poz, ZPlan &poz7)
+{
+    p16.build(MODE_FP16X3, N, N, N, nsm);
+    poz.build(MODE_SLICES, N, N, N, nsm);
+    poz7.build(MODE_SLICES, N, N, N, nsm, NS_SLICES_FIRST, OZ_SLICES);
+}
+
+NsWork carve_ns(const ZPlan &p16, const ZPlan &poz, const ZPlan &poz7, int N, Carver &c)
 {
     NsWork w;
     const size_t nn = (size_t)N * N;
@@ -845,13 +893,14 @@ NsWork carve_ns(const ZPlan &p16, const ZPlan &poz, int N, Carver &c)
     w.XB16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(false)));
     w.ZB16 = static_cast<uint16_t *>(c.take(p16.planes_bytes(false)));
     w.XBOZ = static_cast<uint16_t *>(c.take(poz.planes_bytes(false)));
-    w.T = static_cast<float2 *>(c.take(std::max(p16.T_bytes(), poz.T_bytes())));
+    w.T = static_cast<float2 *>(c.take(std::max(p16.T_bytes(), std::max(poz.T_bytes(), poz7.T_bytes()))));
     w.X = static_cast<double2 *>(c.take(nn * sizeof(double2)));
     w.Z = static_cast<double2 *>(c.take(nn * sizeof(double2)));
     w.words = static_cast<unsigned long long *>(c.take(64 * 8));
     w.skip = static_cast<int *>(c.take(64));
     w.tab16 = c.take(p16.table_bytes());
     w.taboz = c.take(poz.table_bytes());
+    w.taboz7 = c.take(poz7.table_bytes());
     return w;
 }
 }  // namespace
@@ -859,11 +908,10 @@ NsWork carve_ns(const ZPlan &p16, const ZPlan &poz, int N, Carver &c)
 // eps^-1 by the tensor-core Newton iteration (header comment).  A is eps (N x N, device).
 size_t ns_work_bytes(int N, int nsm)
 {
-    ZPlan p16, poz;
-    p16.build(MODE_FP16X3, N, N, N, nsm);
-    poz.build(MODE_SLICES, N, N, N, nsm);
+    ZPlan p16, poz, poz7;
+    ns_plans(N, nsm, p16, poz, poz7);
     Carver c(nullptr);
-    carve_ns(p16, poz, N, c);
+    carve_ns(p16, poz, poz7, N, c);
     return c.used;
 }
 
@@ -872,11 +920,10 @@ size_t ns_work_bytes(int N, int nsm)
 // residual, [3] refinements that ran.
 cudaError_t ns_report(const void *work, int N, int nsm, double *out4)
 {
-    ZPlan p16, poz;
-    p16.build(MODE_FP16X3, N, N, N, nsm);
-    poz.build(MODE_SLICES, N, N, N, nsm);
+    ZPlan p16, poz, poz7;
+    ns_plans(N, nsm, p16, poz, poz7);
     Carver c(const_cast<void *>(work));
-    const NsWork w = carve_ns(p16, poz, N, c);
+    const NsWork w = carve_ns(p16, poz, poz7, N, c);
     unsigned long long h[W_TOTAL];
     const cudaError_t e = cudaMemcpy(h, w.words, sizeof h, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
@@ -908,17 +955,16 @@ bool flag_set(const int *d_flag, cudaStream_t s)
 cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
                                uint64_t wait_ns, int nsm, cudaStream_t s)
 {
-    ZPlan p16, poz;
-    p16.build(MODE_FP16X3, N, N, N, nsm);
-    poz.build(MODE_SLICES, N, N, N, nsm);
+    ZPlan p16, poz, poz7;
+    ns_plans(N, nsm, p16, poz, poz7);
     Carver cv(work);
-    const NsWork nw = carve_ns(p16, poz, N, cv);
+    const NsWork nw = carve_ns(p16, poz, poz7, N, cv);
     uint16_t *A16 = nw.A16, *AOZ = nw.AOZ, *XA16 = nw.XA16, *XB16 = nw.XB16, *ZB16 = nw.ZB16, *XBOZ = nw.XBOZ;
     float2 *T = nw.T;
     double2 *X = nw.X, *Z = nw.Z;
     unsigned long long *words = nw.words;
     int *skip = nw.skip;
-    void *tab16 = nw.tab16, *taboz = nw.taboz;
+    void *tab16 = nw.tab16, *taboz = nw.taboz, *taboz7 = nw.taboz7;
     const size_t nn = (size_t)N * N;
     cudaError_t e;
 #define NS_TRY(x)                      \
@@ -928,6 +974,7 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
     } while (0)
     NS_TRY(p16.upload(tab16, s));
     NS_TRY(poz.upload(taboz, s));
+    NS_TRY(poz7.upload(taboz7, s));
     NS_TRY(cudaMemsetAsync(words, 0, 64 * 8, s));
     // eps: its max, both slicings, and the row-sum bound for X0
     NS_TRY(launch_zmaxabs(A, N, N, N, &words[W_EPS], s));
@@ -936,7 +983,7 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
     (void)rowsum;
     row_sum_bound_kernel<<<std::max(1, std::min(152 * 4, (N + 7) / 8)), 256, 0, s>>>(A, N, words);
     count_launches(1);
-    ns_init_kernel<<<grid_for(nn), 256, 0, s>>>(X, N, words, skip);  // skip[0]: phase 1, [1 + j]: refinement j
+    ns_init_kernel<<<grid2d(N, N), 256, 0, s>>>(X, N, words, skip);  // skip[0]: phase 1, [1 + j]: refinement j
     count_launches(1);
     NS_TRY(cudaGetLastError());
     // phase 1: X <- X (2I - eps X) with FP16X3 products, stopped on device below NS_TOL
@@ -960,10 +1007,11 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
         const int *sk = skip + 1 + j;
         if (j == 2 && flag_set(sk, s))
             break;
-        NS_TRY(launch_zslice(poz, false, X, N, &words[W_X], XBOZ, sk, s));
+        const ZPlan &pr = j == 0 ? poz7 : poz;
+        NS_TRY(launch_zslice(pr, false, X, N, &words[W_X], XBOZ, sk, s));
         NS_TRY(launch_zslice(p16, true, X, N, &words[W_X], XA16, sk, s));
-        NS_TRY(launch_zgemm16(poz, AOZ, XBOZ, T, err, wait_ns, sk, s));
-        NS_TRY(launch_zcombine(poz, T, &words[W_EPS], &words[W_X], 1.0, -1.0, nullptr, 0.0, Z, 0.0, words, W_ZN, W_Z,
+        NS_TRY(launch_zgemm16(pr, AOZ, XBOZ, T, err, wait_ns, sk, s));
+        NS_TRY(launch_zcombine(pr, T, &words[W_EPS], &words[W_X], 1.0, -1.0, nullptr, 0.0, Z, 0.0, words, W_ZN, W_Z,
                                j == 0 ? W_RES0 : W_DISCARD, DEV_REFINE, NS_LAST, j, sk, skip + 1, s));
         NS_TRY(launch_zslice(p16, false, Z, N, &words[W_Z], ZB16, sk, s));
         NS_TRY(launch_zgemm16(p16, XA16, ZB16, T, err, wait_ns, sk, s));

@@ -175,7 +175,8 @@ typedef enum gw_buffer {
     GW_BUF_PG = 2,       /* N_g x N_g complex64, P~                                             */
     GW_BUF_EPS = 3,      /* N_g x N_g complex128, eps                                           */
     GW_BUF_EPSINV = 4,   /* N_g x N_g complex128, eps^-1                                        */
-    GW_BUF_WEIGHTS = 5   /* [nv][nc] float, sqrt(2 / (E_c - E_v)) in Hartree^-1/2              */
+    GW_BUF_WEIGHTS = 5,  /* [nv][nc] float, sqrt(2 / (E_c - E_v)) in Hartree^-1/2              */
+    GW_BUF_PSIT = 6      /* [N_r][nv + nc] complex64, the loaded states transposed (r major)     */
 } gw_buffer;
 
 /*
@@ -277,6 +278,34 @@ GW_API gw_status gw_batch_last_error(const gw_batch *batch, char *buf, size_t n)
  * the array, so calls that overlap on the GPU (other threads, other streams) race: serialise them.
  */
 GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *stream);
+
+/*
+ * States given as plane-wave coefficients (the DFT input of Sec. 4.1, u_nk(x) =
+ * sum_g u~_nk(g) e^{i g.x} / sqrt(Omega)).  The library transforms them to the grid,
+ *     psi_n(r_j) = N_r^(-1/2) sum_p coef[n][p] exp(+2 pi i (m1 j1/n1 + m2 j2/n2 + m3 j3/n3)),
+ * (m = gvec_psi[p], taken modulo the grid; unit-norm coefficient vectors give unit-norm states),
+ * in FP32 on the GPU, then loads them exactly as gw_load_states does.
+ *   npw        number of plane waves, 1 <= npw <= N_r
+ *   gvec_psi   host int [npw][3] Miller indices; two that coincide modulo the grid are
+ *              GW_E_INVALID (they would alias)
+ *   coef       [nv + nc][npw] complex (GW_C64 or GW_C128), host or device (coef_on_device)
+ *   other arguments as gw_load_states (the grid also bounds the transform: n1, n2, n3 <= 64).
+ * The call synchronises the stream.
+ */
+GW_API gw_status gw_load_states_g(gw_ctx *ctx, int n1, int n2, int n3, double cell_L, int nv, int nc, int npw,
+                                  const int *gvec_psi, const void *coef, int coef_dtype, int coef_on_device,
+                                  const double *energies_eV);
+
+/*
+ * Sums over k-points (Sec. 4.1: P^q = (1/N_k) sum_k of the one-k-point sums).  The P~ that the
+ * next gw_P_to_G or gw_build_PG forms is multiplied by `weight` (e.g. 1/N_k) and, with accumulate
+ * = 1, added to the P~ the previous of those calls left (the running sum); gw_eps_inv then uses the
+ * sum.  With accumulate = 1 the sphere must be the one of that previous P~ (GW_E_INVALID
+ * otherwise; GW_E_NOT_READY if there is none).  For each k-point the caller loads the states
+ * (u_{v,k+q} occupied, u_{c,k} unoccupied) and sets q as for one k-point.  The setting persists
+ * until changed; the default is weight 1, accumulate 0.  Non-finite weights are GW_E_INVALID.
+ */
+GW_API gw_status gw_set_kweight(gw_ctx *ctx, double weight, int accumulate);
 
 /*
  * Complex GEMM C = A B from FP64 operands on the 16-bit tensor cores (the products of the

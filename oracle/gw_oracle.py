@@ -16,6 +16,8 @@ units with e^2 = 1:
 * Eq. (gpsaceP), Sec. 4.1 -- the Adler-Wiser g-space sum over states (the second route).
 * Sec. 5.1 (static inverse dielectric matrix) -- eps = I - sqrt(V) P~ sqrt(V), V = 4 pi/(Omega |G|^2),
   and the Newton iteration X <- X (2I - A X) the paper uses to invert it.
+* Sec. 4.1, u_nk(x) = FFT[u~_nk(g)] -- states given as plane-wave coefficients, transformed to
+  the grid (`states_from_g`), and the (1/N_k) sum over k-points of P^q (`P_gspace_ksum`).
 
 Readings of the paper taken here (where it is silent or inconsistent):
 
@@ -36,6 +38,9 @@ Readings of the paper taken here (where it is silent or inconsistent):
    transforms are the same as at q = 0.
 7. Newton start: alpha = 1 / max_i sum_j |(A A^H)_ij| (the paper's A^T read as A^H for complex A,
    with absolute values so the row sums bound the spectral radius).
+8. Plane-wave states: u(r_j) = N_r^(-1/2) sum_g c(g) exp(+i g.r_j), the discrete form of the
+   paper's 1/sqrt(Omega) normalisation (unit-norm coefficients give unit-norm grid states); a
+   Miller index m and m + n (per axis) are the same grid function.
 """
 from __future__ import annotations
 
@@ -149,6 +154,29 @@ def sphere(dims, gcut):
                     pts.append((a * a + b * b + c * c, a, b, c))
     pts.sort()
     return np.array([p[1:] for p in pts], dtype=np.int64).reshape(-1, 3)
+
+
+def states_from_g(coef, gvec, dims):
+    """Sec. 4.1's u_nk(x) = sum_g u~_nk(g) e^{i g.x} / sqrt(Omega) on the grid (reading 8):
+    u[n][j] = N_r^(-1/2) sum_p coef[n][p] exp(+2 pi i sum_a m_pa j_a / n_a), j in C order.  A plain
+    phase sum in FP64 (an [npw x N_r] phase matrix: small grids only)."""
+    n1, n2, n3 = dims
+    j = np.indices((n1, n2, n3)).reshape(3, -1).astype(np.float64)
+    m = np.asarray(gvec, dtype=np.float64)
+    phase = np.outer(m[:, 0], j[0] / n1) + np.outer(m[:, 1], j[1] / n2) + np.outer(m[:, 2], j[2] / n3)
+    return (np.asarray(coef, dtype=np.complex128) @ np.exp(2j * np.pi * phase)) / np.sqrt(n1 * n2 * n3)
+
+
+def P_gspace_ksum(kpoints, nv, dims, gvec, weights=None):
+    """Sec. 4.1's (1/N_k) sum over k of the one-k-point P~^q: kpoints is a list of (psi, E_eV),
+    each psi holding u_{v,k+q} (occupied rows) and u_{c,k}; weights default to 1/N_k."""
+    if weights is None:
+        weights = [1.0 / len(kpoints)] * len(kpoints)
+    out = None
+    for (psi, E), w in zip(kpoints, weights):
+        t = w * P_gspace(psi, E, nv, dims, gvec)
+        out = t if out is None else out + t
+    return out
 
 
 def _flat_index(dims, m):

@@ -403,6 +403,11 @@ void Ctx::release()
     dfree(d_work);
     dfree(d_scal);
     dfree(d_tcw);
+    dfree(d_PGsum);
+    dfree(d_coef);
+    dfree(d_gidx);
+    dfree(d_gtw);
+    dfree(d_psig);
     dfree(d_psi);
     dfree(d_psi128);
     dfree(d_small);
@@ -738,6 +743,23 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     return GW_OK;
 }
 
+// The k-point weight and running sum (gw_set_kweight) applied to the P~ just formed in d_PG.
+gw_status finish_PG(Ctx &c, cudaStream_t s)
+{
+    const int ng = c.ng;
+    const size_t n = (size_t)ng * ng;
+    if (c.kaccumulate && c.PGsum_ng != ng)
+        return fail(c, c.PGsum_ng < 0 ? GW_E_NOT_READY : GW_E_INVALID,
+                    "k-point accumulation needs an earlier P~ on the same sphere (N_g %d, sum has %d)", ng,
+                    c.PGsum_ng);
+    if (c.kaccumulate || c.kweight != 1.0)
+        GW_CUDA(launch_kweight(c.d_PG, c.d_PGsum, n, static_cast<float>(c.kweight), c.kaccumulate, s), "k weight");
+    GW_TRY(ensure(c, c.d_PGsum, c.cap.PGsum, n * sizeof(float2), "P~ sum over k"));
+    GW_CUDA(cudaMemcpyAsync(c.d_PGsum, c.d_PG, n * sizeof(float2), cudaMemcpyDeviceToDevice, s), "keep P~ sum");
+    c.PGsum_ng = ng;
+    return GW_OK;
+}
+
 gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out)
 {
     if (!h)
@@ -770,6 +792,7 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
     GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
     GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
     GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
+    GW_TRY(finish_PG(c, s));
     record(c, 5);
     if (PG_out)
         GW_CUDA(cudaMemcpyAsync(PG_out, c.d_PG, (size_t)ng * ng * sizeof(float2), cudaMemcpyDefault, s),
@@ -850,6 +873,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
                           c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s, splits,
                           c.d_PG_parts),
             "rank-k update in G space");
+    GW_TRY(finish_PG(c, s));
     record(c, 5);
     if (PG_out)
         GW_CUDA(cudaMemcpyAsync(PG_out, c.d_PG, (size_t)ng * ng * sizeof(float2), cudaMemcpyDefault, s),
@@ -897,6 +921,97 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
         newton_tc_record(c, ng);
     c.eps_ready = st == GW_OK;
     return st;
+}
+
+gw_status gw_set_kweight(gw_ctx *h, double weight, int accumulate)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!std::isfinite(weight))
+        return fail(c, GW_E_INVALID, "k-point weight must be finite");
+    c.kweight = weight;
+    c.kaccumulate = accumulate != 0;
+    return GW_OK;
+}
+
+gw_status gw_load_states_g(gw_ctx *h, int n1, int n2, int n3, double cell_L, int nv, int nc, int npw,
+                           const int *gvec_psi, const void *coef, int coef_dtype, int coef_on_device,
+                           const double *energies_eV)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (n1 < 2 || n2 < 2 || n3 < 2 || n1 > 64 || n2 > 64 || n3 > 64)
+        return fail(c, GW_E_INVALID, "grid %d x %d x %d outside [2, 64]^3", n1, n2, n3);
+    const int nr = n1 * n2 * n3;
+    const int nb = nv + nc;
+    if (nv < 1 || nc < 1 || (long long)nv + nc > nr)
+        return fail(c, GW_E_INVALID, "need nv, nc >= 1 and nv + nc <= N_r (got %d, %d, %d)", nv, nc, nr);
+    if (npw < 1 || npw > nr)
+        return fail(c, GW_E_INVALID, "npw = %d plane waves: need 1 <= npw <= N_r = %d", npw, nr);
+    if (!gvec_psi || !coef || !energies_eV)
+        return fail(c, GW_E_INVALID, "null gvec, coefficients or energies");
+    if (coef_dtype != GW_C64 && coef_dtype != GW_C128)
+        return fail(c, GW_E_INVALID, "coef_dtype must be GW_C64 or GW_C128");
+    if (coef_on_device && !is_device_pointer(coef))
+        return fail(c, GW_E_INVALID, "coef_on_device set but coef is not a device pointer");
+    // Miller indices modulo the grid; two plane waves on one grid point would alias
+    std::vector<int> idx(npw);
+    std::vector<char> seen(nr, 0);
+    const int nn[3] = {n1, n2, n3};
+    for (int p = 0; p < npw; ++p) {
+        int j[3];
+        for (int a = 0; a < 3; ++a)
+            j[a] = ((gvec_psi[3 * p + a] % nn[a]) + nn[a]) % nn[a];
+        const int lin = (j[0] * n2 + j[1]) * n3 + j[2];
+        if (seen[lin])
+            return fail(c, GW_E_INVALID, "plane wave %d (%d, %d, %d) aliases an earlier one on the %d x %d x %d grid",
+                        p, gvec_psi[3 * p], gvec_psi[3 * p + 1], gvec_psi[3 * p + 2], n1, n2, n3);
+        seen[lin] = 1;
+        idx[p] = lin;
+    }
+    std::vector<float2> tw(n1 + n2 + n3);
+    for (int a = 0, o = 0; a < 3; o += nn[a], ++a)
+        for (int t = 0; t < nn[a]; ++t) {
+            const double ph = 6.283185307179586476925 * t / nn[a];
+            tw[o + t] = make_float2(static_cast<float>(std::cos(ph)), static_cast<float>(std::sin(ph)));
+        }
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    cudaStream_t s = c.stream;
+    const size_t ncoef = (size_t)nb * npw, n = (size_t)nb * nr;
+    GW_TRY(ensure(c, c.d_gidx, c.cap.gidx, npw * sizeof(int), "plane-wave indices"));
+    GW_TRY(ensure(c, c.d_gtw, c.cap.gtw, tw.size() * sizeof(float2), "axis twiddles"));
+    GW_TRY(ensure(c, c.d_psig, c.cap.psig, n * sizeof(float2), "state transform workspace"));
+    GW_TRY(ensure(c, c.d_psi, c.cap.psi, n * sizeof(float2), "state staging"));
+    GW_CUDA(cudaMemcpyAsync(c.d_gidx, idx.data(), npw * sizeof(int), cudaMemcpyHostToDevice, s), "copy indices");
+    GW_CUDA(cudaMemcpyAsync(c.d_gtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s),
+            "copy twiddles");
+    const float2 *coef64 = nullptr;
+    if (coef_dtype == GW_C64 && coef_on_device) {
+        coef64 = static_cast<const float2 *>(coef);
+    } else {
+        GW_TRY(ensure(c, c.d_coef, c.cap.coef, ncoef * sizeof(float2), "coefficient staging"));
+        if (coef_dtype == GW_C64) {
+            GW_CUDA(cudaMemcpyAsync(c.d_coef, coef, ncoef * sizeof(float2), cudaMemcpyHostToDevice, s),
+                    "copy coefficients");
+        } else {
+            const double2 *p128 = static_cast<const double2 *>(coef);
+            if (!coef_on_device) {
+                GW_TRY(ensure(c, c.d_psi128, c.cap.psi128, ncoef * sizeof(double2), "complex128 staging"));
+                GW_CUDA(cudaMemcpyAsync(c.d_psi128, coef, ncoef * sizeof(double2), cudaMemcpyHostToDevice, s),
+                        "copy coefficients");
+                p128 = c.d_psi128;
+            }
+            GW_CUDA(launch_c128_to_c64(p128, ncoef, c.d_coef, s), "round coefficients");
+        }
+        coef64 = c.d_coef;
+    }
+    GW_CUDA(launch_states_from_g(coef64, nb, npw, c.d_gidx, n1, n2, n3, c.d_gtw, c.d_psig, c.d_psi, s),
+            "states to the grid");
+    // host vectors idx and tw are read by the copies above: finish them before they go out of scope
+    GW_CUDA(cudaStreamSynchronize(s), "transform sync");
+    return gw_load_states(h, n1, n2, n3, cell_L, nv, nc, c.d_psi, GW_C64, 1, energies_eV);
 }
 
 gw_status gw_zgemm_tc(gw_ctx *h, int mode, int M, int N, int K, const void *A, int lda, const void *B, int ldb,
@@ -992,6 +1107,12 @@ gw_status gw_get_buffer(gw_ctx *h, int which, void **ptr, size_t *bytes)
             return GW_E_NOT_READY;
         *ptr = c.d_sw;
         *bytes = (size_t)c.k * sizeof(float);
+        return GW_OK;
+    case GW_BUF_PSIT:
+        if (!c.loaded)
+            return GW_E_NOT_READY;
+        *ptr = c.d_psiT;
+        *bytes = (size_t)c.nr * c.nb * sizeof(float2);
         return GW_OK;
     default:
         return GW_E_INVALID;

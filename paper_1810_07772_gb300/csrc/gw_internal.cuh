@@ -88,6 +88,10 @@ struct Ctx {
     float2 *d_Q = nullptr;          // [nr][ng]  row transform
     float2 *d_QT = nullptr;         // [ng][nr]  conj-transposed
     float2 *d_PG = nullptr;         // [ng][ng]
+    float2 *d_PGsum = nullptr;      // running sum over k-points (gw_set_kweight)
+    int PGsum_ng = -1;              // N_g of that sum (-1: none)
+    double kweight = 1.0;           // weight of the next P~ (Sec. 4.1's 1/N_k)
+    bool kaccumulate = false;       // add the next P~ to the running sum
     float2 *d_dftw = nullptr;       // sphere-transform workspace [rows][n1][cd]
     double *d_sv = nullptr;         // [ng] sqrt(V(G))
     size_t G_cap = 0;               // ng capacity of the G-space buffers
@@ -106,11 +110,15 @@ struct Ctx {
     // staging for gw_load_states
     float2 *d_psi = nullptr;        // [nb][nr] complex64
     double2 *d_psi128 = nullptr;    // complex128 input staging
+    float2 *d_coef = nullptr;       // plane-wave coefficients [nb][npw] (gw_load_states_g)
+    int *d_gidx = nullptr;          // their grid indices
+    float2 *d_gtw = nullptr;        // twiddles of the three axes
+    float2 *d_psig = nullptr;       // transform workspace [nb][nr]
 
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
         size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, dftw, sv, eps, epsinv, work,
-            scal, tcw;
+            scal, tcw, PGsum, coef, gidx, gtw, psig;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -247,6 +255,10 @@ struct ZPlan {
     cudaError_t upload(void *tab, cudaStream_t s);
 };
 size_t zgemm_work_bytes(const ZPlan &p);
+// k_states.cu
+cudaError_t launch_states_from_g(const float2 *coef, int nb, int npw, const int *idx, int n1, int n2, int n3,
+                                 const float2 *tw, float2 *work, float2 *out, cudaStream_t s);
+cudaError_t launch_kweight(float2 *PG, const float2 *sum, size_t n, float w, bool acc, cudaStream_t s);
 cudaError_t zgemm_enqueue(ZPlan &p, const double2 *A, long lda, const double2 *B, long ldb, double2 *C, void *work,
                           uint32_t *err, uint64_t wait_ns, cudaStream_t s);
 size_t ns_work_bytes(int N, int nsm);

@@ -21,7 +21,7 @@ PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
 INV_METHOD = {"cholesky": 0, "newton": 1, "newton_tc": 2}
 ZGEMM_MODE = {"fp16x3": 0, "slices": 1}
 GW_C64, GW_C128 = 0, 1
-BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5}
+BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5, "psiT": 6}
 
 # Every symbol include/gw.h declares, with its ctypes signature.
 _c = ctypes
@@ -34,6 +34,8 @@ SIGNATURES = {
     "gw_set_stream": (_i, [_vp, _vp]),
     "gw_last_error": (_i, [_vp, _c.c_char_p, _sz]),
     "gw_load_states": (_i, [_vp, _i, _i, _i, _d, _i, _i, _vp, _i, _i, _vp]),
+    "gw_load_states_g": (_i, [_vp, _i, _i, _i, _d, _i, _i, _i, _vp, _vp, _i, _i, _vp]),
+    "gw_set_kweight": (_i, [_vp, _d, _i]),
     "gw_build_P": (_i, [_vp, _i, _vp]),
     "gw_P_to_G": (_i, [_vp, _i, _c.POINTER(_i), _vp, _i, _vp]),
     "gw_build_PG": (_i, [_vp, _i, _i, _c.POINTER(_i), _vp, _i, _vp]),
@@ -189,6 +191,30 @@ class Context:
         self.nv, self.nc = int(nv), nb - int(nv)
         self._E_keep = E
 
+    def load_states_g(self, coef, gvec, energies_eV, dims, nv, cell_L=1.0):
+        """States as plane-wave coefficients: coef [nv + nc][npw] complex (torch cuda tensor or numpy
+        host array), gvec [npw][3] integer Miller indices (gw_load_states_g)."""
+        n1, n2, n3 = (int(d) for d in dims)
+        nb, npw = coef.shape
+        E = np.ascontiguousarray(np.asarray(energies_eV, dtype=np.float64))
+        g = np.ascontiguousarray(np.asarray(gvec, dtype=np.int32))
+        if E.shape != (nb,) or g.shape != (npw, 3):
+            raise ValueError("energies need one entry per state and gvec one row per plane wave")
+        dt = str(coef.dtype)
+        if "complex" not in dt:
+            raise TypeError("coefficients must be complex64 or complex128")
+        dtype = GW_C128 if "complex128" in dt else GW_C64
+        self._check(lib().gw_load_states_g(self._h, n1, n2, n3, float(cell_L), int(nv), nb - int(nv), npw,
+                                           g.ctypes.data, _ptr(coef), dtype, 1 if _is_device(coef) else 0,
+                                           E.ctypes.data))
+        self.dims = (n1, n2, n3)
+        self.nv, self.nc = int(nv), nb - int(nv)
+        self._E_keep = E
+
+    def set_kweight(self, weight, accumulate=False):
+        """Weight of the next P~ and whether it adds to the running sum over k-points (gw_set_kweight)."""
+        self._check(lib().gw_set_kweight(self._h, float(weight), 1 if accumulate else 0))
+
     def build_P(self, precision="fp16x3", P_out=None):
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
         self._check(lib().gw_build_P(self._h, prec, _ptr(P_out)))
@@ -309,6 +335,8 @@ class Context:
             return raw[: ng * ng * 8].view(torch.complex64).view(ng, ng)
         if which in ("eps", "epsinv"):
             return raw[: ng * ng * 16].view(torch.complex128).view(ng, ng)
+        if which == "psiT":
+            return raw.view(torch.complex64).view(nr, self.nv + self.nc)
         return raw.view(torch.float32) if nbytes % 4 == 0 else raw
 
 

@@ -99,6 +99,35 @@ def make_states(n: int, nv: int, nc: int, seed: int, dims: tuple[int, int, int] 
     return psi, np.concatenate([ev, ec])
 
 
+def psi_sphere(dims, gcut_psi):
+    """Plane-wave basis of the states: integer Miller indices m with |m|^2 <= gcut_psi, each
+    component in [-n/2, n - n/2), in the order (m1, m2, m3) ascending.  Returns int32 (npw, 3)."""
+    pts = [(a, b, c)
+           for a in range(-(dims[0] // 2), dims[0] - dims[0] // 2)
+           for b in range(-(dims[1] // 2), dims[1] - dims[1] // 2)
+           for c in range(-(dims[2] // 2), dims[2] - dims[2] // 2)
+           if a * a + b * b + c * c <= gcut_psi]
+    return np.array(pts, dtype=np.int32).reshape(-1, 3)
+
+
+def make_states_g(dims, gcut_psi: int, nv: int, nc: int, seed: int):
+    """Return ``(coef, gvec, E_eV)``: random orthonormal plane-wave coefficient sets
+    ``coef [nv + nc][npw]`` (complex128; a reduced QR of ``N(0,1) + i N(0,1)`` of shape
+    ``(npw, nv + nc)``, real part first), the basis ``gvec`` of :func:`psi_sphere` and energies drawn
+    as in :func:`make_states`."""
+    gvec = psi_sphere(dims, gcut_psi)
+    npw, nb = len(gvec), nv + nc
+    if nb > npw:
+        raise ValueError("more states than plane waves: they cannot be orthonormal")
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((npw, nb))
+    b = rng.standard_normal((npw, nb))
+    q, _ = np.linalg.qr(a + 1j * b, mode="reduced")
+    ev = np.sort(rng.uniform(-10.0, 0.0, nv))
+    ec = np.sort(rng.uniform(0.5, 20.0, nc))
+    return np.ascontiguousarray(q.T), gvec, np.concatenate([ev, ec])
+
+
 def make_workload_states(w: Workload):
     return make_states(w.n, w.nv, w.nc, w.seed)
 

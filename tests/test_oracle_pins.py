@@ -295,3 +295,49 @@ def test_finite_q_closed_forms():
     # and the q -> 0 limit of V keeps the q = 0 convention (head 0) only at q = 0 itself
     assert O.coulomb(np.array([[0, 0, 0]]), L)[0] == 0.0
     assert O.coulomb(np.array([[0, 0, 0]]), L, q)[0] > 0.0
+
+
+def test_states_from_g_plane_wave_translation():
+    """One coefficient at m: the grid state has constant modulus N_r^-1/2 and picks up
+    exp(2 pi i m_a / n_a) under a one-point shift along axis a (this fixes the sign, the axis order
+    and the C-order index), and it sums to zero over the grid unless m = 0 (mod n)."""
+    dims = (6, 5, 4)
+    nr = 6 * 5 * 4
+    for m in [(1, 0, 0), (0, -2, 1), (2, 1, -1), (0, 0, 0)]:
+        u = O.states_from_g(np.array([[1.0 + 0j]]), np.array([m]), dims)[0].reshape(dims)
+        assert np.allclose(np.abs(u), nr ** -0.5, atol=1e-15)
+        for a in range(3):
+            shifted = np.roll(u, -1, axis=a)     # u at j + e_a
+            assert np.allclose(shifted, u * np.exp(2j * np.pi * m[a] / dims[a]), atol=1e-14)
+        assert abs(u.sum()) < 1e-12 or m == (0, 0, 0)
+
+
+def test_states_from_g_unitary_and_equals_inverse_fft():
+    """Orthonormal coefficient rows give orthonormal grid states (Parseval), and the phase sum
+    equals N_r^(1/2) times numpy's inverse FFT of the coefficients scattered on the grid (an
+    independent route: library FFT, modular index placement); m and m + n alias."""
+    dims = (8, 6, 5)
+    coef, gvec, _ = inputs.make_states_g(dims, 5, 3, 9, 4)
+    u = O.states_from_g(coef, gvec, dims)
+    assert np.allclose(u.conj() @ u.T, np.eye(12), atol=1e-13)
+    grid = np.zeros((12,) + dims, dtype=np.complex128)
+    for p, m in enumerate(gvec):
+        grid[:, m[0] % dims[0], m[1] % dims[1], m[2] % dims[2]] = coef[:, p]
+    ref = np.sqrt(np.prod(dims)) * np.fft.ifftn(grid, axes=(1, 2, 3)).reshape(12, -1)
+    assert np.allclose(u, ref, atol=1e-13)
+    shifted = gvec + np.array(dims) * np.array([1, -1, 2])
+    assert np.allclose(O.states_from_g(coef, shifted, dims), u, atol=1e-12)
+
+
+def test_ksum_identical_points_and_linearity():
+    """The (1/N_k) sum over k of identical k-points is the one-point result; with two different
+    point sets it is linear in the weights."""
+    w = inputs.SMALL
+    dims = (w.n,) * 3
+    g = O.sphere(dims, w.gcut)
+    a = inputs.make_states(w.n, w.nv, w.nc, 5)
+    b = inputs.make_states(w.n, w.nv, w.nc, 6)
+    Pa = O.P_gspace(a[0], a[1], w.nv, dims, g)
+    assert np.allclose(O.P_gspace_ksum([a, a, a], w.nv, dims, g), Pa, atol=1e-15)
+    Pb = O.P_gspace(b[0], b[1], w.nv, dims, g)
+    assert np.allclose(O.P_gspace_ksum([a, b], w.nv, dims, g, [0.25, 0.75]), 0.25 * Pa + 0.75 * Pb, atol=1e-15)

@@ -308,6 +308,31 @@ GW_API gw_status gw_load_states_g(gw_ctx *ctx, int n1, int n2, int n3, double ce
 GW_API gw_status gw_set_kweight(gw_ctx *ctx, double weight, int accumulate);
 
 /*
+ * The plasmon-pole model of Sec. 5.2 (von der Linden-Horsch form) from the last gw_eps_inv:
+ *   S = sqrt(V) (eps^-1 - I) sqrt(V) (Hermitian, negative semidefinite since eps >= I), its nmodes
+ *   most negative eigenvalues sigma_a (ascending) and orthonormal eigenvectors A[:, a]
+ *   (Eq. eigdecomp), by block subspace iteration with Rayleigh-Ritz in FP64 until every
+ *   || S a - sigma_a a || <= tol |sigma_0|;
+ *   the mode frequencies of the Johnson sum rule (Eq. ppfreq),
+ *     omega_a^2 = -(1/sigma_a) sum_{g,g'} conj(A_ga) V(q+g) V(q+g') ((q+g).(q+g')) rho(g - g') A_g'a,
+ *   Hartree^2, with rho(G) = sum_r e^{-iG.r} 2 sum_v |psi_v(r)|^2 the density of the loaded
+ *   occupied states (rho(0) = 2 N_v electrons per cell); g - g' is taken modulo the grid.  The
+ *   minus sign makes omega^2 > 0 (sigma < 0, the density form is positive semidefinite).
+ *   nmodes 1..16 (and <= N_g); tol > 0.  Outputs may be NULL: sigma, omega2, resid [nmodes] on the
+ *   host, A_out [N_g][nmodes] complex128 (host or device).  Needs gw_eps_inv and the states it was
+ *   built from; GW_E_NUMERIC if the iteration does not converge (400 iterations).
+ */
+GW_API gw_status gw_pp_modes(gw_ctx *ctx, int nmodes, double tol, double *sigma, double *omega2, double *resid,
+                             void *A_out);
+
+/*
+ * S(omega) = sum_{a < nuse} A_a sigma_a omega_a^2 / (omega_a^2 - omega^2) A_a^H (Eq. ppform) from
+ * the last gw_pp_modes (nuse <= its nmodes); omega in Hartree; S_out N_g x N_g complex128, host or
+ * device.  With every mode at omega = 0 it is S itself.
+ */
+GW_API gw_status gw_pp_eval(gw_ctx *ctx, double omega, int nuse, void *S_out);
+
+/*
  * Complex GEMM C = A B from FP64 operands on the 16-bit tensor cores (the products of the
  * GW_INV_NEWTON_TC inverse).  Each operand is scaled by one power of two 2^e (max |Re|, |Im| <
  * 2^e) and sliced:

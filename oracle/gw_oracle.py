@@ -18,6 +18,8 @@ units with e^2 = 1:
   and the Newton iteration X <- X (2I - A X) the paper uses to invert it.
 * Sec. 4.1, u_nk(x) = FFT[u~_nk(g)] -- states given as plane-wave coefficients, transformed to
   the grid (`states_from_g`), and the (1/N_k) sum over k-points of P^q (`P_gspace_ksum`).
+* Sec. 5.2, Eqs. (eigdecomp), (ppform), (ppfreq) -- the plasmon-pole model: S = sqrt(V)(eps^-1 - I)
+  sqrt(V), its eigenpairs, the Johnson-sum-rule frequencies and S(omega) (`pp_*`).
 
 Readings of the paper taken here (where it is silent or inconsistent):
 
@@ -41,6 +43,13 @@ Readings of the paper taken here (where it is silent or inconsistent):
 8. Plane-wave states: u(r_j) = N_r^(-1/2) sum_g c(g) exp(+i g.r_j), the discrete form of the
    paper's 1/sqrt(Omega) normalisation (unit-norm coefficients give unit-norm grid states); a
    Miller index m and m + n (per axis) are the same grid function.
+9. Plasmon-pole frequencies: omega_a^2 = -(1/sigma_a) A_a^H Omega A_a.  The paper prints the
+   quotient without the minus sign; with sigma_a < 0 (S is negative semidefinite) and Omega positive
+   semidefinite that would give omega^2 < 0.  The sign follows from the sum rule with the pole form
+   of Eq. (ppform): int_0^inf w Im S(w) dw = (pi/2) sum_a A sigma omega^2 A^H = -(pi/2) Omega.  The
+   density is rho(G) = sum_r e^{-iG.r} rho(r) with rho(r) = 2 sum_v |psi_v(r)|^2 per grid point, so
+   rho(0) = 2 N_v is the number of electrons per cell; with it a single-pole eps^-1 = 1 - wp^2/w~^2
+   (wp^2 = 4 pi rho(0)/Omega) returns omega = w~ exactly.  g - g' is taken modulo the grid.
 """
 from __future__ import annotations
 
@@ -177,6 +186,50 @@ def P_gspace_ksum(kpoints, nv, dims, gvec, weights=None):
         t = w * P_gspace(psi, E, nv, dims, gvec)
         out = t if out is None else out + t
     return out
+
+
+def density_g(psi, nv, dims):
+    """rho(G) on the whole grid (reading 9): numpy's forward FFT (e^{-iG.r}) of
+    rho(r) = 2 sum_v |psi_v(r)|^2, indexed by m modulo the grid."""
+    rho = 2.0 * np.sum(np.abs(np.asarray(psi)[:nv]) ** 2, axis=0).reshape(dims)
+    return np.fft.fftn(rho)
+
+
+def pp_S(epsinv, gvec, cell_L, q=None):
+    """Sec. 5.2: S = sqrt(V) (eps^-1 - I) sqrt(V) (Hermitian part)."""
+    sv = np.sqrt(coulomb(gvec, cell_L, q))
+    S = sv[:, None] * (np.asarray(epsinv) - np.eye(len(gvec))) * sv[None, :]
+    return 0.5 * (S + S.conj().T)
+
+
+def pp_omega_matrix(gvec, cell_L, rhoG, dims, q=None):
+    """Omega_gg' = V(q+g) V(q+g') ((q+g).(q+g')) rho(g - g') of Eq. (ppfreq)."""
+    V = coulomb(gvec, cell_L, q)
+    m = np.asarray(gvec, dtype=np.float64) + (np.zeros(3) if q is None else np.asarray(q, dtype=np.float64))
+    k = (2.0 * np.pi / cell_L) * m
+    g = np.asarray(gvec)
+    d = g[:, None, :] - g[None, :, :]
+    rho = rhoG[d[..., 0] % dims[0], d[..., 1] % dims[1], d[..., 2] % dims[2]]
+    return V[:, None] * V[None, :] * (k @ k.T) * rho
+
+
+def pp_modes(epsinv, gvec, cell_L, rhoG, dims, nmodes, q=None):
+    """Eq. (eigdecomp) by LAPACK (numpy.linalg.eigh, ascending) and Eq. (ppfreq) with reading 9:
+    returns (sigma[:nmodes], omega2[:nmodes], A[:, :nmodes])."""
+    S = pp_S(epsinv, gvec, cell_L, q)
+    w, A = np.linalg.eigh(S)
+    A = A[:, :nmodes]
+    Om = pp_omega_matrix(gvec, cell_L, rhoG, dims, q)
+    quad = np.real(np.einsum("ga,gh,ha->a", A.conj(), Om, A))
+    sig = w[:nmodes]
+    # a mode with sigma = 0 (the G = 0 row at q = 0) screens nothing and has no pole: omega^2 := 0
+    return sig, np.where(sig != 0, -quad / np.where(sig != 0, sig, 1.0), 0.0), A
+
+
+def pp_S_omega(sigma, omega2, A, w):
+    """Eq. (ppform): S(w) = sum_a A_a sigma_a omega_a^2 / (omega_a^2 - w^2) A_a^H."""
+    f = sigma * omega2 / (omega2 - w * w)
+    return (A * f) @ A.conj().T
 
 
 def _flat_index(dims, m):

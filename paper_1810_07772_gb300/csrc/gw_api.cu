@@ -408,6 +408,7 @@ void Ctx::release()
     dfree(d_gidx);
     dfree(d_gtw);
     dfree(d_psig);
+    dfree(d_ppw);
     dfree(d_psi);
     dfree(d_psi128);
     dfree(d_small);
@@ -1012,6 +1013,81 @@ gw_status gw_load_states_g(gw_ctx *h, int n1, int n2, int n3, double cell_L, int
     // host vectors idx and tw are read by the copies above: finish them before they go out of scope
     GW_CUDA(cudaStreamSynchronize(s), "transform sync");
     return gw_load_states(h, n1, n2, n3, cell_L, nv, nc, c.d_psi, GW_C64, 1, energies_eV);
+}
+
+gw_status gw_pp_modes(gw_ctx *h, int nmodes, double tol, double *sigma, double *omega2, double *resid, void *A_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.eps_ready || !c.loaded)
+        return fail(c, GW_E_NOT_READY, "gw_pp_modes needs gw_eps_inv (and the states it came from)");
+    const int ng = c.ng;
+    int b = std::min(40, std::max(2 * nmodes + 8, 16));
+    b = std::min(b, ng - (ng & 1));  // even, at most N_g
+    if (nmodes < 1 || nmodes > 16 || nmodes > b)
+        return fail(c, GW_E_INVALID, "nmodes %d: need 1 <= nmodes <= min(16, N_g) (N_g = %d)", nmodes, ng);
+    if (!(tol > 0.0) || !std::isfinite(tol))
+        return fail(c, GW_E_INVALID, "tol must be positive");
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    cudaStream_t s = c.stream;
+    c.pp_ready = false;
+    const size_t bytes = PPWork::carve(nullptr, ng, b, c.nr).bytes;
+    GW_TRY(ensure(c, c.d_ppw, c.cap.ppw, bytes, "plasmon-pole workspace"));
+    c.pp = PPWork::carve(c.d_ppw, ng, b, c.nr);
+    const int dims[3] = {c.n1, c.n2, c.n3};
+    std::vector<int> g32(c.gvec.begin(), c.gvec.end());
+    GW_CUDA(pp_prepare(c.pp, c.d_epsinv, c.d_sv, c.d_psiT, ng, c.nr, c.nb, c.nv, dims, g32.data(), c.cell_L, c.q, s),
+            "plasmon-pole S, density and Omega");
+    int iters = 0;
+    GW_CUDA(pp_iterate(c.pp, ng, b, nmodes, tol, 400, &iters, s), "plasmon-pole subspace iteration");
+    std::vector<double> th(b), res(b), w2(b);
+    int flag = 0;
+    GW_CUDA(cudaMemcpyAsync(th.data(), c.pp.theta, b * sizeof(double), cudaMemcpyDeviceToHost, s), "read theta");
+    GW_CUDA(cudaMemcpyAsync(res.data(), c.pp.res, b * sizeof(double), cudaMemcpyDeviceToHost, s), "read residuals");
+    GW_CUDA(cudaMemcpyAsync(w2.data(), c.pp.omega2, b * sizeof(double), cudaMemcpyDeviceToHost, s), "read omega2");
+    GW_CUDA(cudaMemcpyAsync(&flag, c.pp.flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+    if (A_out)
+        GW_CUDA(cudaMemcpy2DAsync(A_out, nmodes * sizeof(double2), c.pp.X, b * sizeof(double2),
+                                  nmodes * sizeof(double2), ng, cudaMemcpyDefault, s),
+                "copy modes out");
+    GW_TRY(read_device_status(c));
+    for (int a = 0; a < nmodes; ++a) {
+        if (sigma)
+            sigma[a] = th[a];
+        if (omega2)
+            omega2[a] = w2[a];
+        if (resid)
+            resid[a] = res[a];
+    }
+    bool conv = flag == 0;
+    for (int a = 0; a < nmodes; ++a)
+        conv = conv && res[a] <= tol * std::fabs(th[0]);
+    if (!conv)
+        return fail(c, GW_E_NUMERIC, "plasmon-pole modes did not converge in %d iterations (residual %g)", iters,
+                    res[0]);
+    c.pp_b = b;
+    c.pp_nmodes = nmodes;
+    c.pp_ready = true;
+    return GW_OK;
+}
+
+gw_status gw_pp_eval(gw_ctx *h, double omega, int nuse, void *S_out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.pp_ready)
+        return fail(c, GW_E_NOT_READY, "gw_pp_eval before gw_pp_modes");
+    if (nuse < 1 || nuse > c.pp_nmodes || !S_out || !std::isfinite(omega))
+        return fail(c, GW_E_INVALID, "gw_pp_eval: nuse %d (1..%d), finite omega, non-null output", nuse,
+                    c.pp_nmodes);
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    cudaStream_t s = c.stream;
+    const int ng = c.ng;
+    GW_CUDA(pp_eval(c.pp, ng, c.pp_b, nuse, omega, c.pp.Om, s), "S(omega)");
+    GW_CUDA(cudaMemcpyAsync(S_out, c.pp.Om, (size_t)ng * ng * sizeof(double2), cudaMemcpyDefault, s), "copy S out");
+    return read_device_status(c);
 }
 
 gw_status gw_zgemm_tc(gw_ctx *h, int mode, int M, int N, int K, const void *A, int lda, const void *B, int ldb,

@@ -44,6 +44,15 @@ struct DftPlan {
     float2 *twc;   // the same table conjugated: exp(-2 pi i t / n_a)
 };
 
+// Plasmon-pole workspace pieces (k_pp.cu) for N_g = ng and block b <= 40.
+struct PPWork {
+    double2 *S, *Om, *X, *Y, *T, *G, *U, *parts, *rho, *rho2, *tw;
+    double *theta, *res, *omega2;
+    int *gvec, *flag;
+    size_t bytes;
+    static PPWork carve(void *base, int ng, int b, int nr);  // base == nullptr: sizes only
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -106,6 +115,10 @@ struct Ctx {
     bool eps_ready = false;
     int newton_iters = 0;
     double tc_report[4] = {-1, -1, -1, -1};  // last tensor-core Newton inverse (gw_newton_tc_report)
+    void *d_ppw = nullptr;          // plasmon-pole workspace
+    PPWork pp = {};                 // its pieces (valid while pp_ready)
+    int pp_b = 0, pp_nmodes = 0;
+    bool pp_ready = false;
 
     // staging for gw_load_states
     float2 *d_psi = nullptr;        // [nb][nr] complex64
@@ -118,7 +131,7 @@ struct Ctx {
     // allocation capacities in bytes (buffers are reused while large enough)
     struct {
         size_t psi, psi128, psiT, E, sw, F, P, tiles, tiles_g, PG_parts, plan, Q, QT, PG, dftw, sv, eps, epsinv, work,
-            scal, tcw, PGsum, coef, gidx, gtw, psig;
+            scal, tcw, PGsum, coef, gidx, gtw, psig, ppw;
     } cap = {};
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
@@ -255,6 +268,13 @@ struct ZPlan {
     cudaError_t upload(void *tab, cudaStream_t s);
 };
 size_t zgemm_work_bytes(const ZPlan &p);
+// k_pp.cu: the plasmon-pole model of Sec. 5.2 (workspace struct PPWork above).
+cudaError_t pp_prepare(const PPWork &w, const double2 *epsinv, const double *sv, const float2 *psiT, int ng, int nr,
+                       int nb, int nv, const int dims[3], const int *gvec_host, double cell_L, const double q[3],
+                       cudaStream_t s);
+cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max_iter, int *iters_out,
+                       cudaStream_t s);
+cudaError_t pp_eval(const PPWork &w, int ng, int b, int nuse, double omega, double2 *Sout, cudaStream_t s);
 // k_states.cu
 cudaError_t launch_states_from_g(const float2 *coef, int nb, int npw, const int *idx, int n1, int n2, int n3,
                                  const float2 *tw, float2 *work, float2 *out, cudaStream_t s);

@@ -36,6 +36,8 @@ SIGNATURES = {
     "gw_load_states": (_i, [_vp, _i, _i, _i, _d, _i, _i, _vp, _i, _i, _vp]),
     "gw_load_states_g": (_i, [_vp, _i, _i, _i, _d, _i, _i, _i, _vp, _vp, _i, _i, _vp]),
     "gw_set_kweight": (_i, [_vp, _d, _i]),
+    "gw_pp_modes": (_i, [_vp, _i, _d, _vp, _vp, _vp, _vp]),
+    "gw_pp_eval": (_i, [_vp, _d, _i, _vp]),
     "gw_build_P": (_i, [_vp, _i, _vp]),
     "gw_P_to_G": (_i, [_vp, _i, _c.POINTER(_i), _vp, _i, _vp]),
     "gw_build_PG": (_i, [_vp, _i, _i, _c.POINTER(_i), _vp, _i, _vp]),
@@ -270,6 +272,21 @@ class Context:
             X = torch.empty_like(A)
         self._check(lib().gw_zinv_tc(self._h, n, _ptr(A), _ptr(X)))
         return X
+
+    def pp_modes(self, nmodes, tol=1e-12):
+        """Plasmon-pole modes of Sec. 5.2 from the last eps^-1 (gw_pp_modes): sigma (ascending),
+        omega^2 (Hartree^2), residuals and the eigenvectors A [N_g][nmodes]."""
+        sig, w2, res = (np.zeros(nmodes) for _ in range(3))
+        A = np.zeros((self.ng, nmodes), dtype=np.complex128)
+        self._check(lib().gw_pp_modes(self._h, int(nmodes), float(tol), sig.ctypes.data, w2.ctypes.data,
+                                      res.ctypes.data, A.ctypes.data))
+        return {"sigma": sig, "omega2": w2, "resid": res, "A": A}
+
+    def pp_eval(self, omega, nuse, S_out=None):
+        """S(omega) from the first nuse plasmon-pole modes (gw_pp_eval); a host array unless S_out."""
+        out = S_out if S_out is not None else np.zeros((self.ng, self.ng), dtype=np.complex128)
+        self._check(lib().gw_pp_eval(self._h, float(omega), int(nuse), _ptr(out)))
+        return out
 
     def newton_tc_report(self):
         """Phase-1 steps, residual after phase 1, last measured residual and refinements of the

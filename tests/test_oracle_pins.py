@@ -341,3 +341,51 @@ def test_ksum_identical_points_and_linearity():
     assert np.allclose(O.P_gspace_ksum([a, a, a], w.nv, dims, g), Pa, atol=1e-15)
     Pb = O.P_gspace(b[0], b[1], w.nv, dims, g)
     assert np.allclose(O.P_gspace_ksum([a, b], w.nv, dims, g, [0.25, 0.75]), 0.25 * Pa + 0.75 * Pb, atol=1e-15)
+
+
+def test_pp_single_pole_closed_form():
+    """Sec. 5.2 with a diagonal single-pole eps^-1 = 1 - wp^2 / w_g^2 (wp^2 = 4 pi rho(0)/Omega) and
+    a constant density: every mode is one G and its Johnson-sum-rule frequency is w_g (this fixes
+    the sign of Eq. ppfreq, the V factors, |q+G|^2 and the density normalisation rho(0) = N_el)."""
+    dims, L = (8, 8, 8), 1.3
+    g = O.sphere(dims, 3)[1:]                     # no G = 0 (V(0) = 0 at q = 0)
+    n = len(g)
+    nel = 6.0
+    rhoG = np.zeros(dims, dtype=np.complex128)
+    rhoG[0, 0, 0] = nel
+    wp2 = 4 * np.pi * nel / L ** 3
+    wt2 = np.linspace(2.0, 9.0, n) * wp2          # distinct poles, eps^-1 - 1 in (-1, 0)
+    inv = np.diag(1.0 - wp2 / wt2).astype(np.complex128)
+    sig, w2, A = O.pp_modes(inv, g, L, rhoG, dims, n)
+    for a in range(n):
+        gi = int(np.argmax(np.abs(A[:, a])))
+        assert abs(abs(A[gi, a]) - 1) < 1e-12
+        assert abs(w2[a] - wt2[gi]) <= 1e-12 * wt2[gi]
+    assert np.all(sig < 0)
+
+
+def test_pp_density_and_S_omega_limits():
+    """Occupied plane waves give a constant density, rho(G) = 2 N_v at G = 0 only; S(w) from every
+    mode is S at w = 0 and vanishes as w grows; all-mode S(w) is Hermitian."""
+    dims = (6, 6, 6)
+    psi, E = inputs.plane_wave_states(dims, [(0, 0, 0), (1, 0, 0), (0, 1, 0)], [-3.0, -2.0, 4.0])
+    rhoG = O.density_g(psi, 2, dims)
+    assert abs(rhoG[0, 0, 0] - 4.0) < 1e-12
+    rhoG0 = rhoG.copy()
+    rhoG0[0, 0, 0] = 0
+    assert np.max(np.abs(rhoG0)) < 1e-12
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    d3 = (w.n,) * 3
+    r = O.eps_inv_path(psi, E, w.nv, d3, w.gcut, w.cell_L, route="gspace")
+    g = O.sphere(d3, w.gcut)
+    rho = O.density_g(psi, w.nv, d3)
+    assert abs(rho[0, 0, 0] - 2 * w.nv) < 1e-12
+    sig, w2, A = O.pp_modes(r["epsinv"], g, w.cell_L, rho, d3, len(g))
+    S = O.pp_S(r["epsinv"], g, w.cell_L)
+    keep = np.abs(sig) > 1e-14                    # the G = 0 null mode carries no pole
+    S0 = O.pp_S_omega(sig[keep], w2[keep], A[:, keep], 0.0)
+    assert np.max(np.abs(S0 - S)) < 1e-12 * np.max(np.abs(S))
+    Sinf = O.pp_S_omega(sig[keep], w2[keep], A[:, keep], 1e6)
+    assert np.max(np.abs(Sinf)) < 1e-6 * np.max(np.abs(S))
+    assert np.all(w2[keep] > 0)

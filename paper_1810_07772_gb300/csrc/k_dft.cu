@@ -280,19 +280,34 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
 // the cd values to a workspace [rows][n1][cd].  A second kernel does stage 3 per row (one CTA
 // per row: the row's n1 x cd values in shared memory, the N_g outputs over the threads).  The
 // sums run in the same order with the same twiddles as in dft_rows_kernel.
+//
+// Stage 1 (two thirds of the work) takes one line j2 per lane when n3 is a compiled size: the n3
+// inputs sit in registers and, output by output, every lane reads the same twiddle (one
+// broadcast shared-memory access per complex FMA of each lane) where the per-output form read the
+// input and the twiddle for every FMA.
 constexpr int P12_WARPS = 8;
 
+// Per warp: the plane [n2][n3 + 1] (rows padded: one lane per row reads them) and a1 [n2][c3].
 __host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3)
 {
-    return align16(sizeof(float2) * ((size_t)n2 * n3 + (size_t)n2 * c3)) / sizeof(float2);
+    return align16(sizeof(float2) * ((size_t)n2 * (n3 + 1) + (size_t)n2 * c3)) / sizeof(float2);
+}
+
+// Twiddle tables of the plane kernel, unrolled so the inner loops carry no index arithmetic:
+// tw3m[i3][j3] = e(m3(i3) j3 / n3) and tw2d[d][j2] = e(m2(d) j2 / n2), the latter with rows of
+// n2 + 1 so that lanes on neighbouring disk points hit different banks.
+__host__ __device__ inline size_t p12_tables(const int n[3], int c3, int cd)
+{
+    return align16(sizeof(float2) * ((size_t)c3 * n[2] + (size_t)cd * (n[1] + 1)));
 }
 
 __host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd)
 {
     const size_t tables = align16(sizeof(float2) * (n[0] + n[1] + n[2]) + sizeof(int) * (c3 + 2 * cd));
-    return tables + P12_WARPS * p12_warp_floats2(n[1], n[2], c3) * sizeof(float2);
+    return tables + p12_tables(n, c3, cd) + P12_WARPS * p12_warp_floats2(n[1], n[2], c3) * sizeof(float2);
 }
 
+template <int N3>  // 0: any n3 (one output per lane)
 __global__ void __launch_bounds__(P12_WARPS * 32)
     dft_plane12_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int n2, int n3, int c3,
                        int cd, const int *__restrict__ g_m3, const int *__restrict__ g_disk,
@@ -302,8 +317,11 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     float2 *tw = reinterpret_cast<float2 *>(smem);  // [n1 | n2 | n3]
     int *m3 = reinterpret_cast<int *>(tw + n1 + n2 + n3);
     int *disk = m3 + c3;
-    float2 *wbase = reinterpret_cast<float2 *>(
+    const int nn[3] = {n1, n2, n3};
+    float2 *tw3m = reinterpret_cast<float2 *>(
         smem + align16(sizeof(float2) * (n1 + n2 + n3) + sizeof(int) * (c3 + 2 * cd)));
+    float2 *tw2d = tw3m + (size_t)c3 * n3;
+    float2 *wbase = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(tw3m) + p12_tables(nn, c3, cd));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int t = tid; t < n1 + n2 + n3; t += blockDim.x)
         tw[t] = g_tw[t];
@@ -313,45 +331,79 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         disk[t] = g_disk[t];
     __syncthreads();
     const float2 *tw2 = tw + n1, *tw3 = tw + n1 + n2;
+    for (int t = tid; t < c3 * n3; t += blockDim.x) {
+        const int i3 = t / n3, j3 = t - i3 * n3;
+        tw3m[t] = tw3[(int)(((long long)m3[i3] * j3) % n3)];
+    }
+    for (int t = tid; t < cd * n2; t += blockDim.x) {
+        const int d = t / n2, j2 = t - d * n2;
+        tw2d[d * (n2 + 1) + j2] = tw2[(int)(((long long)disk[2 * d] * j2) % n2)];
+    }
+    __syncthreads();
     const int plane = n2 * n3;
     float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3);
-    float2 *a1 = xp + plane;
+    float2 *a1 = xp + (size_t)n2 * (n3 + 1);
+    const int ld3 = n3 + 1;
     const long long ntasks = (long long)rows * n1;
     for (long long task = (long long)blockIdx.x * P12_WARPS + warp; task < ntasks;
          task += (long long)gridDim.x * P12_WARPS) {
         const long long row = task / n1;
         const int j1 = (int)(task - row * n1);
         const float2 *src = X + row * ldx + (size_t)j1 * plane;
-        for (int q = lane; q < plane; q += 32)
-            xp[q] = src[q];
+        {
+            int j2 = lane / n3, j3 = lane - (lane / n3) * n3;  // q = lane + 32 i -> (j2, j3), no division in the loop
+            const int dj2 = 32 / n3, dj3 = 32 - (32 / n3) * n3;
+            for (int q = lane; q < plane; q += 32) {
+                xp[j2 * ld3 + j3] = src[q];
+                j2 += dj2;
+                j3 += dj3;
+                if (j3 >= n3) {
+                    j3 -= n3;
+                    ++j2;
+                }
+            }
+        }
         __syncwarp();
         // stage 1: a1[j2][i3] = sum_j3 x[j2][j3] e(m3 j3 / n3)
-        for (int o = lane; o < n2 * c3; o += 32) {
-            const int j2 = o / c3, i3 = o - j2 * c3, step = m3[i3];
-            const float2 *x = xp + j2 * n3;
-            float2 acc = make_float2(0.f, 0.f);
-            int idx = 0;
-            for (int j3 = 0; j3 < n3; ++j3) {
-                cmac(acc, x[j3], tw3[idx]);
-                idx += step;
-                if (idx >= n3)
-                    idx -= n3;
+        if (N3 > 0) {
+            for (int j2 = lane; j2 < n2; j2 += 32) {
+                float2 xr[N3 > 0 ? N3 : 1];
+#pragma unroll
+                for (int j3 = 0; j3 < N3; ++j3)
+                    xr[j3] = xp[j2 * (N3 + 1) + j3];
+                for (int i3 = 0; i3 < c3; ++i3) {
+                    const float2 *w = tw3m + i3 * N3;  // the same row for every lane: broadcast reads
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j3 = 0; j3 < N3; ++j3)
+                        cmac(acc, xr[j3], w[j3]);
+                    a1[j2 * c3 + i3] = acc;
+                }
             }
-            a1[o] = acc;
+        } else {
+            for (int o = lane; o < n2 * c3; o += 32) {
+                const int j2 = o / c3, i3 = o - j2 * c3, step = m3[i3];
+                const float2 *x = xp + j2 * ld3;
+                float2 acc = make_float2(0.f, 0.f);
+                int idx = 0;
+                for (int j3 = 0; j3 < n3; ++j3) {
+                    cmac(acc, x[j3], tw3[idx]);
+                    idx += step;
+                    if (idx >= n3)
+                        idx -= n3;
+                }
+                a1[o] = acc;
+            }
         }
         __syncwarp();
         // stage 2: y2[d] = sum_j2 a1[j2][i3(d)] e(m2(d) j2 / n2)
         float2 *dst = Y2 + task * cd;
         for (int d = lane; d < cd; d += 32) {
-            const int step = disk[2 * d], i3 = disk[2 * d + 1];
+            const int i3 = disk[2 * d + 1];
+            const float2 *w = tw2d + d * (n2 + 1), *a = a1 + i3;
             float2 acc = make_float2(0.f, 0.f);
-            int idx = 0;
-            for (int j2 = 0; j2 < n2; ++j2) {
-                cmac(acc, a1[j2 * c3 + i3], tw2[idx]);
-                idx += step;
-                if (idx >= n2)
-                    idx -= n2;
-            }
+            for (int j2 = 0; j2 < n2; ++j2)
+                cmac(acc, a[j2 * c3], w[j2]);
             dst[d] = acc;
         }
         __syncwarp();  // the plane buffer is rewritten by the next task
@@ -446,15 +498,39 @@ static cudaError_t launch_dft_R(const float2 *X, long long ldx, int rows, float2
     return launch_dft_RG<R, 16>(X, ldx, rows, Y, ldy, p, s, tw);
 }
 
-// The plane-per-warp form reads about two shared-memory words per complex FMA and the row-block
-// kernel 1.25 (one twiddle serves R rows), so the latter is the faster one for the long transforms
-// (the rows of P, the pair densities); the plane-per-warp form wins where rows are too few for
-// the row-block kernel to fill the GPU (the column pass, N_g rows).
-constexpr int WS_MAX_ROWS = 4096;
+// With the register stage 1 the plane-per-warp form is the faster one for every row count; its
+// workspace holds n1 cd values per row.  Grids whose n3 has no compiled stage 1 keep the
+// row-block kernel for long transforms (it reads 1.25 shared-memory words per complex FMA against
+// two for the generic plane-per-warp stage 1).
+constexpr int WS_MAX_ROWS_GENERIC = 4096;
+
+bool p12_compiled(int n3)
+{
+    switch (n3) {
+    case 12: case 16: case 18: case 20: case 24: case 27: case 30: case 32: case 36:
+        return true;
+    default:
+        return false;
+    }
+}
 
 size_t dft_work_bytes(const DftPlan &p, int rows)
 {
-    return (size_t)std::min(rows, WS_MAX_ROWS) * p.n[0] * p.cd * sizeof(float2);
+    const int r = p12_compiled(p.n[2]) ? rows : std::min(rows, WS_MAX_ROWS_GENERIC);
+    return (size_t)r * p.n[0] * p.cd * sizeof(float2);
+}
+
+template <int N3>
+static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
+                              const float2 *tw, float2 *work, cudaStream_t s)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(dft_plane12_kernel<N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dft_plane12_kernel<N3><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.cd,
+                                                               p.m3list, p.disk, tw, work);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
@@ -462,23 +538,32 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
 {
     if (rows <= 0)
         return cudaSuccess;
-    if (rows > WS_MAX_ROWS || !work)
+    if ((!p12_compiled(p.n[2]) && rows > WS_MAX_ROWS_GENERIC) || !work)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     const float2 *tw = negative_exponent ? p.twc : p.tw;
     const size_t sm12 = p12_smem(p.n, p.c3, p.cd);
     const size_t sm3 = sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
     if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
-    cudaError_t e = cudaFuncSetAttribute(dft_plane12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm12);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    cudaError_t e = cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
     if (e != cudaSuccess)
         return e;
     const long long ntasks = (long long)rows * p.n[0];
     const int g12 = (int)std::min<long long>((ntasks + P12_WARPS - 1) / P12_WARPS, 152LL * 16);
-    dft_plane12_kernel<<<g12, P12_WARPS * 32, sm12, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.cd, p.m3list,
-                                                         p.disk, tw, work);
+    switch (p.n[2]) {
+    case 12: e = launch_p12<12>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 16: e = launch_p12<16>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 18: e = launch_p12<18>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 20: e = launch_p12<20>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 24: e = launch_p12<24>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 27: e = launch_p12<27>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 30: e = launch_p12<30>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 32: e = launch_p12<32>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 36: e = launch_p12<36>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    default: e = launch_p12<0>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    }
+    if (e != cudaSuccess)
+        return e;
     const int g3 = std::min(rows, 152 * 8);
     dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
     count_launches(2);

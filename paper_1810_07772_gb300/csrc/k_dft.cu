@@ -287,10 +287,11 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
 // input and the twiddle for every FMA.
 constexpr int P12_WARPS = 8;
 
-// Per warp: the plane [n2][n3 + 1] (rows padded: one lane per row reads them) and a1 [n2][c3].
-__host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3)
+// Per warp: a1 [n2][c3] and, for the generic stage 1 only, the plane [n2][n3 + 1] (rows padded:
+// one lane per row reads them).  The compiled stage 1 loads each lane's line from global memory.
+__host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3, bool plane)
 {
-    return align16(sizeof(float2) * ((size_t)n2 * (n3 + 1) + (size_t)n2 * c3)) / sizeof(float2);
+    return align16(sizeof(float2) * ((plane ? (size_t)n2 * (n3 + 1) : 0) + (size_t)n2 * c3)) / sizeof(float2);
 }
 
 // Twiddle tables of the plane kernel, unrolled so the inner loops carry no index arithmetic:
@@ -301,10 +302,10 @@ __host__ __device__ inline size_t p12_tables(const int n[3], int c3, int cd)
     return align16(sizeof(float2) * ((size_t)c3 * n[2] + (size_t)cd * (n[1] + 1)));
 }
 
-__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd)
+__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, bool plane)
 {
     const size_t tables = align16(sizeof(float2) * (n[0] + n[1] + n[2]) + sizeof(int) * (c3 + 2 * cd));
-    return tables + p12_tables(n, c3, cd) + P12_WARPS * p12_warp_floats2(n[1], n[2], c3) * sizeof(float2);
+    return tables + p12_tables(n, c3, cd) + P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane) * sizeof(float2);
 }
 
 template <int N3>  // 0: any n3 (one output per lane)
@@ -341,16 +342,19 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     }
     __syncthreads();
     const int plane = n2 * n3;
-    float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3);
-    float2 *a1 = xp + (size_t)n2 * (n3 + 1);
+    constexpr bool kPlane = N3 == 0;
+    float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3, kPlane);
+    float2 *a1 = xp + (kPlane ? (size_t)n2 * (n3 + 1) : 0);
     const int ld3 = n3 + 1;
+    // 16-byte loads of the lines need an even n3, an even row stride and an aligned base
+    const bool vec = (N3 % 2 == 0) && (ldx % 2 == 0) && ((reinterpret_cast<size_t>(X) & 15) == 0);
     const long long ntasks = (long long)rows * n1;
     for (long long task = (long long)blockIdx.x * P12_WARPS + warp; task < ntasks;
          task += (long long)gridDim.x * P12_WARPS) {
         const long long row = task / n1;
         const int j1 = (int)(task - row * n1);
         const float2 *src = X + row * ldx + (size_t)j1 * plane;
-        {
+        if (kPlane) {
             int j2 = lane / n3, j3 = lane - (lane / n3) * n3;  // q = lane + 32 i -> (j2, j3), no division in the loop
             const int dj2 = 32 / n3, dj3 = 32 - (32 / n3) * n3;
             for (int q = lane; q < plane; q += 32) {
@@ -368,9 +372,19 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         if (N3 > 0) {
             for (int j2 = lane; j2 < n2; j2 += 32) {
                 float2 xr[N3 > 0 ? N3 : 1];
+                const float2 *line = src + (size_t)j2 * N3;  // the line from global memory (L1 keeps it)
+                if (vec) {
 #pragma unroll
-                for (int j3 = 0; j3 < N3; ++j3)
-                    xr[j3] = xp[j2 * (N3 + 1) + j3];
+                    for (int j3 = 0; j3 < N3; j3 += 2) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(line + j3));
+                        xr[j3] = make_float2(v.x, v.y);
+                        xr[j3 + 1 < N3 ? j3 + 1 : j3] = make_float2(v.z, v.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int j3 = 0; j3 < N3; ++j3)
+                        xr[j3] = __ldg(line + j3);
+                }
                 for (int i3 = 0; i3 < c3; ++i3) {
                     const float2 *w = tw3m + i3 * N3;  // the same row for every lane: broadcast reads
                     float2 acc = make_float2(0.f, 0.f);
@@ -541,7 +555,7 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
     if ((!p12_compiled(p.n[2]) && rows > WS_MAX_ROWS_GENERIC) || !work)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     const float2 *tw = negative_exponent ? p.twc : p.tw;
-    const size_t sm12 = p12_smem(p.n, p.c3, p.cd);
+    const size_t sm12 = p12_smem(p.n, p.c3, p.cd, !p12_compiled(p.n[2]));
     const size_t sm3 = sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
     if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);

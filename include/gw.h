@@ -258,6 +258,10 @@ GW_API gw_status gw_batch_run(gw_batch *batch, int use_graph);
 GW_API gw_status gw_batch_set_window(gw_batch *batch, int window_chunks, int flush_windows);
 GW_API gw_status gw_batch_autotune(gw_batch *batch, const char *cache_path, double target_error);
 GW_API gw_status gw_batch_stats(gw_batch *batch, double *stats4);
+/* eps^-1 of every instance: GW_INV_NEWTON_TC (the default; its steps are all queued and the
+ * unneeded ones return at once on the device, so the pass stays one CUDA graph) or
+ * GW_INV_CHOLESKY.  Re-prepares the batch's buffers; GW_E_INVALID for another method. */
+GW_API gw_status gw_batch_set_inverse(gw_batch *batch, int method);
 GW_API gw_status gw_batch_last_error(const gw_batch *batch, char *buf, size_t n);
 
 /*

@@ -1239,6 +1239,7 @@ struct gw_batch {
     float herk_ms = 0.f;
     int runs = 0;
     int graph_kernels = 0;          // kernel nodes of the captured pass (launches per replay)
+    int inv_method = GW_INV_NEWTON_TC;  // eps^-1 of every instance (gw_batch_set_inverse)
     std::string last_error;
 };
 
@@ -1318,8 +1319,15 @@ gw_status batch_prepare(gw_batch &b)
         GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, std::max(c.nr, ng)), "transform workspace"));
         GW_TRY(ensure(c, c.d_eps, c.cap.eps, (size_t)ng * ng * sizeof(double2), "eps"));
         GW_TRY(ensure(c, c.d_epsinv, c.cap.epsinv, (size_t)ng * ng * sizeof(double2), "eps^-1"));
-        const size_t work = (size_t)3 * ng * ng + (size_t)NB * ng + (size_t)nblk * NB * NB;
-        GW_TRY(ensure(c, c.d_work, c.cap.work, work * sizeof(double2), "inverse workspace"));
+        if (b.inv_method == GW_INV_NEWTON_TC) {
+            const int nsm = sm_count(c.device);
+            GW_TRY(ensure(c, c.d_tcw, c.cap.tcw, ns_work_bytes(ng, nsm), "tensor-core Newton workspace"));
+            GW_TRY(ensure(c, c.d_scal, c.cap.scal, 4 * sizeof(double), "Newton scalars"));
+            GW_CUDA(ns_prepare(c.d_tcw, ng, nsm, b.stream), "Newton tables");
+        } else {
+            const size_t work = (size_t)3 * ng * ng + (size_t)NB * ng + (size_t)nblk * NB * NB;
+            GW_TRY(ensure(c, c.d_work, c.cap.work, work * sizeof(double2), "inverse workspace"));
+        }
         jobs.push_back({reinterpret_cast<const uint16_t *>(c.d_F), c.d_P, reinterpret_cast<const int *>(c.d_small + 1),
                         c.nr, c.nr_pad, kpad, 0});
         for (const int2 t : herk_tiles(c.nr_pad, HERK16_T, HERK16_T))
@@ -1384,7 +1392,14 @@ gw_status batch_enqueue(gw_batch &b)
         GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
         GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
         GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
-        GW_TRY(inverse_cholesky(c, s));
+        if (b.inv_method == GW_INV_NEWTON_TC) {
+            const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+            GW_CUDA(ns_inverse_enqueue(c.d_eps, ng, c.d_epsinv, c.d_tcw, c.d_scal, c.d_err, wait_ns,
+                                       sm_count(c.device), s, true),
+                    "tensor-core Newton inverse");
+        } else {
+            GW_TRY(inverse_cholesky(c, s));
+        }
     }
     return GW_OK;
 }
@@ -1533,6 +1548,18 @@ gw_status gw_batch_set_window(gw_batch *b, int window_chunks, int flush_windows)
     b->W = window_chunks;
     b->L = flush_windows;
     return GW_OK;
+}
+
+gw_status gw_batch_set_inverse(gw_batch *b, int method)
+{
+    if (!b || (method != GW_INV_CHOLESKY && method != GW_INV_NEWTON_TC))
+        return GW_E_INVALID;
+    if (b->inv_method == method)
+        return GW_OK;
+    drop_graph(*b);  // the captured pass carries the old inverse
+    b->inv_method = method;
+    cudaSetDevice(b->device);
+    return batch_prepare(*b);  // the other inverse's workspace and tables, outside any capture
 }
 
 gw_status gw_batch_run(gw_batch *b, int use_graph)

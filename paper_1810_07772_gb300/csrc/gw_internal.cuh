@@ -283,7 +283,8 @@ cudaError_t zgemm_enqueue(ZPlan &p, const double2 *A, long lda, const double2 *B
                           uint32_t *err, uint64_t wait_ns, cudaStream_t s);
 size_t ns_work_bytes(int N, int nsm);
 cudaError_t ns_report(const void *work, int N, int nsm, double *out4);
+cudaError_t ns_prepare(void *work, int N, int nsm, cudaStream_t s);
 cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
-                               uint64_t wait_ns, int nsm, cudaStream_t s);
+                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe = false);
 
 }  // namespace gw

@@ -949,11 +949,31 @@ bool flag_set(const int *d_flag, cudaStream_t s)
 }
 }  // namespace
 
+// Upload the slot tables of order N into the workspace (done inside ns_inverse_enqueue unless
+// the caller did it beforehand, as a captured CUDA graph needs: no pageable copies in capture).
+cudaError_t ns_prepare(void *work, int N, int nsm, cudaStream_t s)
+{
+    ZPlan p16, poz, poz7;
+    ns_plans(N, nsm, p16, poz, poz7);
+    Carver cv(work);
+    const NsWork nw = carve_ns(p16, poz, poz7, N, cv);
+    cudaError_t e = p16.upload(nw.tab16, s);
+    if (e == cudaSuccess)
+        e = poz.upload(nw.taboz, s);
+    if (e == cudaSuccess)
+        e = poz7.upload(nw.taboz7, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // the host tables are locals
+    return e;
+}
+
 // The kernels of every step check the device flags, so the result does not depend on the host
 // reads below: they only stop queuing steps that would return at once (after phase-1 steps 3, 5,
 // 7, ... and before the third refinement), at the price of one stream synchronisation each.
+// With graph_safe the tables must have been uploaded by ns_prepare and every step is queued (no
+// host reads, no pageable copies), so the whole inverse can be captured into a CUDA graph.
 cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
-                               uint64_t wait_ns, int nsm, cudaStream_t s)
+                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe)
 {
     ZPlan p16, poz, poz7;
     ns_plans(N, nsm, p16, poz, poz7);
@@ -972,9 +992,22 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
         if ((e = (x)) != cudaSuccess)  \
             return e;                  \
     } while (0)
-    NS_TRY(p16.upload(tab16, s));
-    NS_TRY(poz.upload(taboz, s));
-    NS_TRY(poz7.upload(taboz7, s));
+    if (graph_safe) {  // the device pointers of the tables, uploaded earlier by ns_prepare
+        p16.d_pairs = static_cast<int2 *>(tab16);
+        p16.d_slots = reinterpret_cast<int *>(static_cast<uint8_t *>(tab16) + p16.host_pairs.size() * sizeof(int2));
+        p16.d_wexp = p16.d_slots + p16.host_slots.size();
+        poz.d_pairs = static_cast<int2 *>(taboz);
+        poz.d_slots = reinterpret_cast<int *>(static_cast<uint8_t *>(taboz) + poz.host_pairs.size() * sizeof(int2));
+        poz.d_wexp = poz.d_slots + poz.host_slots.size();
+        poz7.d_pairs = static_cast<int2 *>(taboz7);
+        poz7.d_slots =
+            reinterpret_cast<int *>(static_cast<uint8_t *>(taboz7) + poz7.host_pairs.size() * sizeof(int2));
+        poz7.d_wexp = poz7.d_slots + poz7.host_slots.size();
+    } else {
+        NS_TRY(p16.upload(tab16, s));
+        NS_TRY(poz.upload(taboz, s));
+        NS_TRY(poz7.upload(taboz7, s));
+    }
     NS_TRY(cudaMemsetAsync(words, 0, 64 * 8, s));
     // eps: its max, both slicings, and the row-sum bound for X0
     NS_TRY(launch_zmaxabs(A, N, N, N, &words[W_EPS], s));
@@ -998,14 +1031,14 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
         NS_TRY(launch_zgemm16(p16, XA16, ZB16, T, err, wait_ns, skip, s));
         NS_TRY(launch_zcombine(p16, T, &words[W_X], &words[W_Z], 0.0, 1.0, nullptr, 0.0, X, 0.0, words, W_XN, W_X,
                                W_DISCARD, DEV_STORE, 0.0, it, skip, nullptr, s));
-        if (it >= 3 && (it & 1) && flag_set(skip, s))
+        if (!graph_safe && it >= 3 && (it & 1) && flag_set(skip, s))
             break;
     }
     // phase 2: R = I - eps X to FP64 accuracy (integer slices), X <- X + X R (FP16X3); refinement
     // j runs unless an earlier one measured a residual <= NS_LAST (flag skip[1 + j])
     for (int j = 0; j < NS_REFINE; ++j) {
         const int *sk = skip + 1 + j;
-        if (j == 2 && flag_set(sk, s))
+        if (!graph_safe && j == 2 && flag_set(sk, s))
             break;
         const ZPlan &pr = j == 0 ? poz7 : poz;
         NS_TRY(launch_zslice(pr, false, X, N, &words[W_X], XBOZ, sk, s));

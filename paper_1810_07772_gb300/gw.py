@@ -62,6 +62,7 @@ SIGNATURES = {
     "gw_batch_set_window": (_i, [_vp, _i, _i]),
     "gw_batch_autotune": (_i, [_vp, _c.c_char_p, _d]),
     "gw_batch_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
+    "gw_batch_set_inverse": (_i, [_vp, _i]),
     "gw_batch_last_error": (_i, [_vp, _c.c_char_p, _sz]),
     "gw_mlp_num_params": (_i, [_i, _i, _c.POINTER(_sz)]),
     "gw_mlp_create": (_i, [_c.POINTER(_vp), _i, _i, _i, _i, _vp]),
@@ -388,6 +389,11 @@ class Batch:
         for c in self.contexts:   # each context now holds P~, eps and eps^-1 of its instance
             d = c.dims8()
             c.ng = d[6]
+
+    def set_inverse(self, method):
+        """eps^-1 of every instance: "newton_tc" (default) or "cholesky" (gw_batch_set_inverse)."""
+        m = INV_METHOD[method] if isinstance(method, str) else int(method)
+        self._check(lib().gw_batch_set_inverse(self._h, m))
 
     def set_window(self, window_chunks, flush_windows):
         self._check(lib().gw_batch_set_window(self._h, int(window_chunks), int(flush_windows)))

@@ -26,7 +26,7 @@ def load(dims, nv, nc, seed):
     return ctx, psi, E
 
 
-def single_path(dims, nv, nc, seed, gcut, W=2, L=256):
+def single_path(dims, nv, nc, seed, gcut, W=2, L=256, inv_method="newton_tc"):
     ctx, psi, E = load(dims, nv, nc, seed)
     ctx.set_herk_window(W, L)
     ctx.build_P("fp16x3")
@@ -35,7 +35,7 @@ def single_path(dims, nv, nc, seed, gcut, W=2, L=256):
     PG = torch.empty((ng, ng), dtype=torch.complex64, device="cuda:0")
     inv = torch.empty((ng, ng), dtype=torch.complex128, device="cuda:0")
     ctx.P_to_G(gcut, PG_out=PG)
-    ctx.eps_inv("cholesky", epsinv_out=inv)
+    ctx.eps_inv(inv_method, epsinv_out=inv)
     ctx.close()
     return PG.cpu().numpy(), inv.cpu().numpy(), g
 
@@ -65,6 +65,30 @@ def test_batch_equals_single_instance_path_bit_for_bit(batch_results):
         PGs, invs, _ = single_path(dims, nv, nc, seed, gcut)
         assert np.array_equal(PG, PGs)
         assert np.array_equal(inv, invs)
+
+
+def test_batch_cholesky_inverse_bit_for_bit():
+    """gw_batch_set_inverse(GW_INV_CHOLESKY): the replayed graph equals the single-instance
+    Cholesky path bit for bit, and switching back re-captures the Newton inverse."""
+    ctxs = [load(dims, nv, nc, seed)[0] for dims, nv, nc, gcut, seed in SYSTEMS]
+    b = gw.Batch(ctxs, [s[3] for s in SYSTEMS])
+    b.set_inverse("cholesky")
+    for _ in range(3):
+        b.run(use_graph=True)
+    chol = [c.view("epsinv").cpu().numpy() for c in ctxs]
+    b.set_inverse("newton_tc")
+    for _ in range(2):
+        b.run(use_graph=True)
+    tc = [c.view("epsinv").cpu().numpy() for c in ctxs]
+    with pytest.raises(gw.GwError):
+        b.set_inverse("newton")          # the FP64 Newton iteration is not offered in the batch
+    b.close()
+    for c in ctxs:
+        c.close()
+    for (dims, nv, nc, gcut, seed), inv_c, inv_t in zip(SYSTEMS, chol, tc):
+        _, ref, _ = single_path(dims, nv, nc, seed, gcut, inv_method="cholesky")
+        assert np.array_equal(inv_c, ref)
+        assert np.max(np.abs(inv_t - ref)) <= 1e-12
 
 
 def test_graph_replay_equals_eager(batch_results):

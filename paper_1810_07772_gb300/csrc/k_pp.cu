@@ -430,6 +430,7 @@ PPWork PPWork::carve(void *base, int ng, int b, int nr)
     w.G = static_cast<double2 *>(take((size_t)b * b * sizeof(double2)));
     w.U = static_cast<double2 *>(take((size_t)b * b * sizeof(double2)));
     w.parts = static_cast<double2 *>(take((size_t)nparts * b * b * sizeof(double2)));
+    w.partsY = static_cast<double2 *>(take((size_t)((ng + 63) / 64) * nb * sizeof(double2)));
     w.theta = static_cast<double *>(take(b * sizeof(double)));
     w.res = static_cast<double *>(take(b * sizeof(double)));
     w.omega2 = static_cast<double *>(take(b * sizeof(double)));
@@ -459,6 +460,26 @@ cudaError_t gram(const double2 *X, const double2 *Y, int ng, int ld, int b, doub
     if (e != cudaSuccess)
         return e;
     sum_parts64_kernel<<<blocks_for((size_t)b * b), 256, 0, s>>>(parts, nparts, b * b, C);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Y (ng x b) = A (ng x ng) X (ng x b): K split into 64-wide parts (a batched product, enough CTAs
+// for FP64 on every SM), the parts summed in order.
+cudaError_t prod_ksplit(const double2 *A, const double2 *X, int ng, int b, double2 *parts, double2 *Y, cudaStream_t s)
+{
+    const int kc = 64, nparts = (ng + kc - 1) / kc;
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    cudaError_t e = launch_zgemm_batched(ng, b, kc, one, A, ng, 0, kc, X, b, 0, (long)kc * b, zero, parts, b,
+                                         (long)ng * b, nparts - 1, s, 0);
+    if (e != cudaSuccess)
+        return e;
+    const int last = ng - (nparts - 1) * kc;
+    e = launch_zgemm(ng, b, last, one, A + (size_t)(nparts - 1) * kc, ng, 0, X + (size_t)(nparts - 1) * kc * b, b, 0,
+                     zero, parts + (size_t)(nparts - 1) * ng * b, b, s, 0);
+    if (e != cudaSuccess)
+        return e;
+    sum_parts64_kernel<<<blocks_for((size_t)ng * b), 256, 0, s>>>(parts, nparts, ng * b, Y);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -526,7 +547,7 @@ cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max
     // X0 = (c I - S) R with a deterministic R
     pp_random_kernel<<<blocks_for(nb), 256, 0, s>>>(w.T, nb);
     count_launches(1);
-    if ((e = launch_zgemm(ng, b, ng, one, w.S, ng, 0, w.T, b, 0, zero, w.X, b, s, 0)) != cudaSuccess)
+    if ((e = prod_ksplit(w.S, w.T, ng, b, w.partsY, w.X, s)) != cudaSuccess)
         return e;
     shift_step_kernel<<<blocks_for(nb), 256, 0, s>>>(w.T, w.X, c, nb);
     count_launches(1);
@@ -544,7 +565,7 @@ cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max
                 return e;
             std::swap(w.X, w.T);
         }
-        if ((e = launch_zgemm(ng, b, ng, one, w.S, ng, 0, w.X, b, 0, zero, w.Y, b, s, 0)) != cudaSuccess)
+        if ((e = prod_ksplit(w.S, w.X, ng, b, w.partsY, w.Y, s)) != cudaSuccess)
             return e;
         if (it % 4 != 3 && it + 1 < max_iter) {
             shift_step_kernel<<<blocks_for(nb), 256, 0, s>>>(w.X, w.Y, c, nb);  // next block: (c I - S) X
@@ -583,7 +604,7 @@ cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max
         }
     }
     // frequencies: T = Omega X, omega2 = -Re(x^H T x) / theta
-    if ((e = launch_zgemm(ng, b, ng, one, w.Om, ng, 0, w.X, b, 0, zero, w.T, b, s, 0)) != cudaSuccess)
+    if ((e = prod_ksplit(w.Om, w.X, ng, b, w.partsY, w.T, s)) != cudaSuccess)
         return e;
     pp_freq_kernel<<<b, 256, 0, s>>>(w.X, w.T, ng, b, w.theta, w.omega2);
     count_launches(1);

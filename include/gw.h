@@ -189,11 +189,10 @@ typedef enum gw_buffer {
  * p = 0 and 2, stored as planes 0 and 1), the element (r, k) sits at float offset
  *   ((kc * nplanes + p) * nr_pad + (r / 8) * 8) * 8 + ((k % 8) / 4) * 32 + (r % 8) * 4 + k % 4.
  * For GW_PREC_FP32_SIMT it is [kpad][nr_pad] complex64 (f itself, r contiguous).
- * For GW_PREC_FP16X3 / GW_PREC_BF16X3 it is six 16-bit planes (FP16 or BF16 bit patterns; FP16
- * values carry the factor 2^e of the scale): p = 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo, 4 -Im hi,
- * 5 -Im lo (planes 2 and 3 with the sign bit flipped), k padded to a multiple of 16: for
- * kc = k / 16 the element (r, k) of plane p sits at 16-bit offset
- *   ((kc * 6 + p) * nr_pad + (r / 8) * 8) * 16 + ((k % 16) / 8) * 64 + (r % 8) * 8 + k % 8.
+ * For GW_PREC_FP16X3 / GW_PREC_BF16X3 it is four 16-bit planes (FP16 or BF16 bit patterns; FP16
+ * values carry the factor 2^e of the scale): p = 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo, k padded
+ * to a multiple of 16: for kc = k / 16 the element (r, k) of plane p sits at 16-bit offset
+ *   ((kc * 4 + p) * nr_pad + (r / 8) * 8) * 16 + ((k % 16) / 8) * 64 + (r % 8) * 8 + k % 8.
  */
 GW_API gw_status gw_get_buffer(gw_ctx *ctx, int which, void **ptr, size_t *bytes);
 

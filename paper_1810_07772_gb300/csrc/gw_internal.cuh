@@ -168,9 +168,8 @@ constexpr int HERK_BM = 128;
 constexpr int HERK_BN = 256;
 constexpr int HERK_KC = 8;
 constexpr int HERK16_KC = 16;
-// 16-bit operand planes per k chunk: Re hi, Re lo, Im hi, Im lo, -Im hi, -Im lo.  The negated
-// imaginary planes let one N = 256 MMA produce the real and the imaginary half of a tile.
-constexpr int HERK16_NPL = 6;
+// 16-bit operand planes per k chunk: Re hi, Re lo, Im hi, Im lo.
+constexpr int HERK16_NPL = 4;
 constexpr int HERK16_T = 128;
 
 // k_herk16.cu

@@ -4,7 +4,7 @@
 // Why this kernel exists: tcgen05 accumulates in TMEM with FP32 truncation, so the error of one
 // long accumulation grows linearly with the number of MMAs into it (about 2e-8 per MMA; 1.7e-4
 // at k = 15360).  Here the tensor core only ever accumulates a short window (W chunks of 16 k,
-// 6 MMAs per chunk) into a fresh TMEM buffer; eight warps then add the window into FP32
+// 9 MMAs per chunk) into a fresh TMEM buffer; eight warps then add the window into FP32
 // registers with round-to-nearest, and every L windows the registers are added into the tile's
 // own region of P in global memory.  TMEM holds two window buffers so the tensor core keeps
 // running while the previous window is promoted.
@@ -14,12 +14,15 @@
 // 11 significant bits per part (22 together, like the TF32 split) at twice the TF32 MMA rate;
 // BF16 keeps 8 + 8.  Complex products: Re = Ar Br^T + Ai Bi^T, Im = Ai Br^T - Ar Bi^T.
 //
-// One MMA makes both halves: the B operand of a chunk sits in shared memory as three 128-row
-// regions [Bi | Br | -Bi] (per hi/lo part), so the 256 rows starting at Br are [Br; -Bi] and those
-// starting at Bi are [Bi; Br].  With A = Ar and A = Ai an M = 128, N = 256 MMA adds Ar Br^T and
-// Ai Bi^T into the Re columns of the window and -Ar Bi^T and Ai Br^T into its Im columns: six MMAs
-// per chunk instead of twelve of N = 128, and 112 KB of shared-memory operand traffic instead of
-// 128 KB (the stage is 40 KB written by the bulk copies, the MMAs read 6 x 12 KB).
+// The B operand of a chunk sits in shared memory as two adjacent 128-row regions [Bi | Br] per
+// hi/lo part, so the 256 rows starting at Bi are [Bi; Br]: one M = 128, N = 256 MMA from A = Ai
+// adds Ai Bi^T into the Re columns of the window and Ai Br^T into its Im columns; two N = 128 MMAs
+// from A = Ar add Ar Br^T into Re and, with the A-negate bit of the instruction descriptor,
+// -Ar Bi^T into Im.  Per chunk that is three N = 256 and six N = 128 MMAs (every output element
+// still takes six accumulations), a 32 KB stage of 8 bulk copies and no negated operand copies
+// in global memory.  A form with a third region -Bi and six N = 256 MMAs moves fewer bytes through
+// shared memory (112 KB per chunk against 116 KB here) but needs 40 KB stages and a fifth and
+// sixth plane in global memory; it measured 2-3% slower.
 //
 // Tiles are 128 x 128, upper triangle only (i <= j); direct and mirrored stores as in the TF32
 // kernel, so every element of P is written exactly once at the end.
@@ -38,11 +41,11 @@ constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
 constexpr uint32_t PL = TM * KC16 * 2;  // 4 KB: one plane of one 128-row block
 constexpr uint32_t NPL = HERK16_NPL;    // global planes per chunk
 // stage: A planes Re hi, Re lo, Im hi, Im lo of the row block (4 PL), then the B regions
-// [Im | Re | -Im] of the hi part and of the lo part (6 PL)
+// [Im | Re] of the hi part and of the lo part (4 PL)
 constexpr uint32_t B_OFF = 4 * PL;
-constexpr uint32_t STAGE_BYTES = 10 * PL;  // 40 KB
-constexpr int STAGES = 5;
-constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;  // 200 KB
+constexpr uint32_t STAGE_BYTES = 8 * PL;  // 32 KB
+constexpr int STAGES = 6;
+constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;  // 192 KB
 constexpr uint32_t LBO = 128, SBO = 256;
 constexpr int EPI_PITCH = 129;
 static_assert(PIPE_BYTES >= TM * EPI_PITCH * 8, "epilogue staging must fit");
@@ -127,11 +130,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int p = 0; p < 4; ++p)
                     bulk_g2s(st + p * PL, chunk + p * per_chunk + a_off, PL, &full[s]);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {  // hi, lo: [Im | Re | -Im]
-                    uint8_t *bb = st + B_OFF + h * 3 * PL;
+                for (int h = 0; h < 2; ++h) {  // hi, lo: [Im | Re]
+                    uint8_t *bb = st + B_OFF + h * 2 * PL;
                     bulk_g2s(bb, chunk + (2 + h) * per_chunk + b_off, PL, &full[s]);
                     bulk_g2s(bb + PL, chunk + (0 + h) * per_chunk + b_off, PL, &full[s]);
-                    bulk_g2s(bb + 2 * PL, chunk + (4 + h) * per_chunk + b_off, PL, &full[s]);
                 }
                 *n_issued = kc + 1;
             }
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             constexpr uint32_t FMT = BF16 ? 1u : 0u;
             constexpr uint32_t ID = mma_idesc(FMT, TM, 2 * TN, false);  // N = 256: Re | Im columns
+            constexpr uint32_t ID1 = mma_idesc(FMT, TM, TN, false), ID1N = mma_idesc(FMT, TM, TN, true);
             const uint32_t sbase = smem_u32(smem);
             int kc = 0;
             bool ok = true;
@@ -166,18 +169,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     const uint64_t a_rh = smem_desc(st, LBO, SBO), a_rl = smem_desc(st + PL, LBO, SBO);
                     const uint64_t a_ih = smem_desc(st + 2 * PL, LBO, SBO), a_il = smem_desc(st + 3 * PL, LBO, SBO);
-                    // B from Br: rows [Br; -Bi]; from Bi: rows [Bi; Br] (hi part, then lo part)
-                    const uint64_t b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
-                    const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO);
-                    const uint64_t b_rl = smem_desc(st + B_OFF + 4 * PL, LBO, SBO);
-                    const uint64_t b_il = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
+                    // B regions per part: [Bi | Br]; from Bi the 256 rows are [Bi; Br]
+                    const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO), b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
+                    const uint64_t b_il = smem_desc(st + B_OFF + 2 * PL, LBO, SBO);
+                    const uint64_t b_rl = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
                     const uint32_t acc = c > 0 ? 1u : 0u;
-                    mma_f16(d, a_rh, b_rh, ID, acc);  // Re += Ar Br, Im -= Ar Bi
-                    mma_f16(d, a_rh, b_rl, ID, 1);
-                    mma_f16(d, a_rl, b_rh, ID, 1);
-                    mma_f16(d, a_ih, b_ih, ID, 1);    // Re += Ai Bi, Im += Ai Br
+                    mma_f16(d, a_ih, b_ih, ID, acc);       // Re += Ai Bi, Im += Ai Br
                     mma_f16(d, a_ih, b_il, ID, 1);
                     mma_f16(d, a_il, b_ih, ID, 1);
+                    mma_f16(d, a_rh, b_rh, ID1, 1);        // Re += Ar Br
+                    mma_f16(d, a_rh, b_rl, ID1, 1);
+                    mma_f16(d, a_rl, b_rh, ID1, 1);
+                    mma_f16(d + 128, a_rh, b_ih, ID1N, 1);  // Im -= Ar Bi
+                    mma_f16(d + 128, a_rh, b_il, ID1N, 1);
+                    mma_f16(d + 128, a_rl, b_ih, ID1N, 1);
                     mma_commit(&empty[s]);
                     *n_consumed = kc + 1;
                 }
@@ -470,8 +475,6 @@ __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__res
         Fc[per_chunk + rem] = to16<BF16>(fr - from16<BF16>(rh));
         Fc[2 * per_chunk + rem] = ih;
         Fc[3 * per_chunk + rem] = il;
-        Fc[4 * per_chunk + rem] = ih ^ 0x8000u;  // -Im: the sign bit, exact in FP16 and BF16
-        Fc[5 * per_chunk + rem] = il ^ 0x8000u;
     }
 }
 
@@ -518,8 +521,6 @@ __global__ void planes16_from_c64_kernel(const float2 *__restrict__ M, int rows,
         base[per_chunk] = to16<BF16>(fr - from16<BF16>(rh));
         base[2 * per_chunk] = ih;
         base[3 * per_chunk] = il;
-        base[4 * per_chunk] = ih ^ 0x8000u;
-        base[5 * per_chunk] = il ^ 0x8000u;
     }
 }
 

@@ -22,11 +22,11 @@ namespace {
 constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
 constexpr uint32_t PL = TM * KC16 * 2;  // 4 KB: one plane of one 128-row block
 constexpr uint32_t NPL = HERK16_NPL;
-// stage as in herk16_kernel: A planes Re hi, Re lo, Im hi, Im lo, then B regions [Im | Re | -Im]
-// of the hi part and of the lo part, so one N = 256 MMA fills the Re and Im columns of a window
+// stage as in herk16_kernel: A planes Re hi, Re lo, Im hi, Im lo, then B regions [Im | Re] of the
+// hi part and of the lo part, so one N = 256 MMA from A = Im fills the Re and Im columns of a window
 constexpr uint32_t B_OFF = 4 * PL;
-constexpr uint32_t STAGE_BYTES = 10 * PL;  // 40 KB
-constexpr int STAGES = 5;
+constexpr uint32_t STAGE_BYTES = 8 * PL;  // 32 KB
+constexpr int STAGES = 6;
 constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;
 constexpr uint32_t LBO = 128, SBO = 256;
 constexpr size_t SMEM = PIPE_BYTES + 256;
@@ -127,10 +127,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         bulk_g2s(st + p * PL, chunk + p * per_chunk + a_off, PL, &full[s]);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        uint8_t *bb = st + B_OFF + h * 3 * PL;
+                        uint8_t *bb = st + B_OFF + h * 2 * PL;
                         bulk_g2s(bb, chunk + (2 + h) * per_chunk + b_off, PL, &full[s]);
                         bulk_g2s(bb + PL, chunk + (0 + h) * per_chunk + b_off, PL, &full[s]);
-                        bulk_g2s(bb + 2 * PL, chunk + (4 + h) * per_chunk + b_off, PL, &full[s]);
                     }
                     *n_issued = g + 1;
                 }
@@ -141,6 +140,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             constexpr uint32_t FMT = BF16 ? 1u : 0u;
             constexpr uint32_t ID = mma_idesc(FMT, TM, 2 * TN, false);
+            constexpr uint32_t ID1 = mma_idesc(FMT, TM, TN, false), ID1N = mma_idesc(FMT, TM, TN, true);
             const uint32_t sbase = smem_u32(smem);
             long long g = 0, gw = 0;  // chunks and windows consumed by this CTA
             bool ok = true;
@@ -173,17 +173,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint64_t a_rh = smem_desc(st, LBO, SBO), a_rl = smem_desc(st + PL, LBO, SBO);
                         const uint64_t a_ih = smem_desc(st + 2 * PL, LBO, SBO);
                         const uint64_t a_il = smem_desc(st + 3 * PL, LBO, SBO);
-                        const uint64_t b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
                         const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO);
-                        const uint64_t b_rl = smem_desc(st + B_OFF + 4 * PL, LBO, SBO);
-                        const uint64_t b_il = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
+                        const uint64_t b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
+                        const uint64_t b_il = smem_desc(st + B_OFF + 2 * PL, LBO, SBO);
+                        const uint64_t b_rl = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
                         const uint32_t acc = c > 0 ? 1u : 0u;
-                        mma_f16(d, a_rh, b_rh, ID, acc);  // Re += Ar Br, Im -= Ar Bi
-                        mma_f16(d, a_rh, b_rl, ID, 1);
-                        mma_f16(d, a_rl, b_rh, ID, 1);
-                        mma_f16(d, a_ih, b_ih, ID, 1);    // Re += Ai Bi, Im += Ai Br
+                        mma_f16(d, a_ih, b_ih, ID, acc);       // Re += Ai Bi, Im += Ai Br
                         mma_f16(d, a_ih, b_il, ID, 1);
                         mma_f16(d, a_il, b_ih, ID, 1);
+                        mma_f16(d, a_rh, b_rh, ID1, 1);        // Re += Ar Br
+                        mma_f16(d, a_rh, b_rl, ID1, 1);
+                        mma_f16(d, a_rl, b_rh, ID1, 1);
+                        mma_f16(d + 128, a_rh, b_ih, ID1N, 1);  // Im -= Ar Bi
+                        mma_f16(d + 128, a_rh, b_il, ID1N, 1);
+                        mma_f16(d + 128, a_rl, b_ih, ID1N, 1);
                         mma_commit(&empty[s]);
                         *n_consumed = g + 1;
                     }

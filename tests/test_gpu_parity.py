@@ -110,19 +110,14 @@ def _decode_16(F, nr_pad, nr, k, bf16):
     u = F.view(np.uint16)
     rr = np.arange(nr)[:, None]
     kk = np.arange(k)[None, :]
-    off = (((kk // 16) * 6) * nr_pad + (rr // 8) * 8) * 16 + ((kk % 16) // 8) * 64 + (rr % 8) * 8 + kk % 8
+    off = (((kk // 16) * 4) * nr_pad + (rr // 8) * 8) * 16 + ((kk % 16) // 8) * 64 + (rr % 8) * 8 + kk % 8
     per = nr_pad * 16
     if bf16:
         val = lambda x: (x.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     else:
         val = lambda x: x.view(np.float16).astype(np.float64)
     pl = [val(u[off + p * per]) for p in range(4)]
-    # planes 4 and 5 are -Im hi and -Im lo: the sign bit flipped, padding included
-    nplanes = len(u) // (per * ((k + 15) // 16))
-    assert nplanes == 6
-    u6 = u.reshape(-1, 6, per)
-    assert np.array_equal(u6[:, 4], u6[:, 2] ^ np.uint16(0x8000))
-    assert np.array_equal(u6[:, 5], u6[:, 3] ^ np.uint16(0x8000))
+    assert len(u) // (per * ((k + 15) // 16)) == 4
     return (pl[0] + pl[1]) + 1j * (pl[2] + pl[3]), u
 
 

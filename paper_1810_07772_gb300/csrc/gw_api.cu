@@ -228,6 +228,63 @@ gw_status build_plan(Ctx &c, int gcut)
     const int c3 = static_cast<int>(m3vals.size()), cd = static_cast<int>(dpairs.size());
 
     std::vector<int> m3list(c3), disk(2 * cd), gmap(2 * ng);
+    // stage-2 pairs: (m2, m3) with (-m2, m3), which share the sums over j2 and n2 - j2
+    std::vector<int4> pair2;
+    int k2 = 0;
+    for (int d = 0; d < cd; ++d) {
+        const int m2 = dpairs[d][0], m3 = dpairs[d][1];
+        k2 = std::max(k2, std::abs(m2));
+        if (m2 < 0)
+            continue;
+        const int i3 = static_cast<int>(std::lower_bound(m3vals.begin(), m3vals.end(), m3) - m3vals.begin());
+        const std::array<int, 2> key = {-m2, m3};
+        const auto it = std::lower_bound(dpairs.begin(), dpairs.end(), key);
+        if (m2 == 0)
+            pair2.push_back(make_int4(i3, 0, d, -1));
+        else if (it != dpairs.end() && *it == key)
+            pair2.push_back(make_int4(i3, m2, d, static_cast<int>(it - dpairs.begin())));
+        else {
+            pair2.clear();
+            break;
+        }
+    }
+    int covered = 0;
+    for (const int4 &e : pair2)
+        covered += e.w >= 0 ? 2 : 1;
+    if (2 * k2 >= n[1] || covered != cd)
+        pair2.clear();
+    // stage-3 pairs: (m1, m2, m3) with (-m1, m2, m3), which share the sums over j1 and n1 - j1
+    std::vector<int4> pair1;
+    int k1 = 0;
+    {
+        std::vector<std::pair<std::array<int, 3>, int>> idx(ng);
+        for (int i = 0; i < ng; ++i) {
+            idx[i] = {g[i], i};
+            k1 = std::max(k1, std::abs(g[i][0]));
+        }
+        std::sort(idx.begin(), idx.end());
+        int cov = 0;
+        for (int i = 0; i < ng && 2 * k1 < n[0]; ++i) {
+            const int m1 = g[i][0];
+            if (m1 < 0)
+                continue;
+            const int d = static_cast<int>(std::lower_bound(dpairs.begin(), dpairs.end(),
+                                                            std::array<int, 2>{g[i][1], g[i][2]}) - dpairs.begin());
+            if (m1 == 0) {
+                pair1.push_back(make_int4(d, 0, i, -1));
+                cov += 1;
+                continue;
+            }
+            const std::pair<std::array<int, 3>, int> key = {{-m1, g[i][1], g[i][2]}, -1};
+            const auto it = std::lower_bound(idx.begin(), idx.end(), key);
+            if (it == idx.end() || it->first != key.first)
+                break;
+            pair1.push_back(make_int4(d, m1, i, it->second));
+            cov += 2;
+        }
+        if (cov != ng)
+            pair1.clear();
+    }
     for (int i = 0; i < c3; ++i)
         m3list[i] = mod(m3vals[i], n[2]);
     for (int d = 0; d < cd; ++d) {
@@ -250,13 +307,19 @@ gw_status build_plan(Ctx &c, int gcut)
         tw.push_back(make_float2(tw[t].x, -tw[t].y));
     const size_t ints = (size_t)c3 + 2 * cd + 2 * ng;
     const size_t int_bytes = ((ints * sizeof(int) + 15) / 16) * 16;
-    const size_t bytes = int_bytes + tw.size() * sizeof(float2);
+    const size_t tw_bytes = tw.size() * sizeof(float2);
+    const size_t bytes = int_bytes + tw_bytes + (pair2.size() + pair1.size()) * sizeof(int4);
     GW_TRY(ensure(c, c.d_plan_mem, c.cap.plan, bytes, "plan buffer"));
     std::vector<unsigned char> host(bytes, 0);
     std::memcpy(host.data(), m3list.data(), c3 * sizeof(int));
     std::memcpy(host.data() + c3 * sizeof(int), disk.data(), 2 * cd * sizeof(int));
     std::memcpy(host.data() + (c3 + 2 * cd) * sizeof(int), gmap.data(), 2 * ng * sizeof(int));
-    std::memcpy(host.data() + int_bytes, tw.data(), tw.size() * sizeof(float2));
+    std::memcpy(host.data() + int_bytes, tw.data(), tw_bytes);
+    if (!pair2.empty())
+        std::memcpy(host.data() + int_bytes + tw_bytes, pair2.data(), pair2.size() * sizeof(int4));
+    if (!pair1.empty())
+        std::memcpy(host.data() + int_bytes + tw_bytes + pair2.size() * sizeof(int4), pair1.data(),
+                    pair1.size() * sizeof(int4));
     GW_CUDA(cudaMemcpy(c.d_plan_mem, host.data(), bytes, cudaMemcpyHostToDevice), "plan upload");
     DftPlan &p = c.plan;
     p.n[0] = n[0];
@@ -264,12 +327,22 @@ gw_status build_plan(Ctx &c, int gcut)
     p.n[2] = n[2];
     p.ng = ng;
     p.c3 = c3;
+    p.sym3 = (c3 % 2 == 1) ? (c3 - 1) / 2 : -1;
+    for (int i = 0; i < c3 && p.sym3 >= 0; ++i)
+        if (m3vals[i] != i - (c3 - 1) / 2)
+            p.sym3 = -1;
     p.cd = cd;
     p.m3list = c.d_plan_mem;
     p.disk = c.d_plan_mem + c3;
     p.gmap = c.d_plan_mem + c3 + 2 * cd;
     p.tw = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(c.d_plan_mem) + int_bytes);
     p.twc = p.tw + ntw;
+    p.np2 = static_cast<int>(pair2.size());
+    p.k2 = k2;
+    p.pair2 = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(c.d_plan_mem) + int_bytes + tw_bytes);
+    p.np1 = static_cast<int>(pair1.size());
+    p.k1 = k1;
+    p.pair1 = p.pair2 + pair2.size();
 
     c.gvec.assign(3 * ng, 0);
     for (int i = 0; i < ng; ++i) {

@@ -36,10 +36,17 @@ struct DftPlan {
     int n[3];
     int ng;        // sphere size
     int c3;        // distinct m3 values used by the sphere
+    int sym3;      // M when those values are exactly -M..M (in that order), else -1
     int cd;        // distinct (m2, m3) pairs used by the sphere
     int *m3list;   // [c3]   m3 values (device)
     int *disk;     // [cd*2] (m2, index into m3list) (device)
     int *gmap;     // [ng*2] (m1, index into disk) (device)
+    int np2;       // disk pairs {(m2, m3), (-m2, m3)} when the disk is symmetric in m2, else 0
+    int k2;        // max m2 of the disk
+    int4 *pair2;   // [np2] (index into m3list, m2 >= 0, disk index of m2, of -m2 or -1 at m2 = 0)
+    int np1;       // sphere pairs {(m1, m2, m3), (-m1, m2, m3)} (every sphere has them), else 0
+    int k1;        // max m1 of the sphere
+    int4 *pair1;   // [np1] (disk index, m1 >= 0, sphere index of m1, of -m1 or -1 at m1 = 0)
     float2 *tw;    // [n1 + n2 + n3] exp(+2 pi i t / n_a), FP64-derived (device)
     float2 *twc;   // the same table conjugated: exp(-2 pi i t / n_a)
 };

@@ -285,6 +285,18 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
 // inputs sit in registers and, output by output, every lane reads the same twiddle (one
 // broadcast shared-memory access per complex FMA of each lane) where the per-output form read the
 // input and the twiddle for every FMA.
+//
+// When the sphere's m3 values are exactly -M..M (every sphere |G|^2 < gcut is symmetric under
+// G -> -G), stage 1 pairs the inputs j3 and n3 - j3: with s = x_j + x_{n-j}, t = x_j - x_{n-j} and
+// e(m j / n) = c + i s_m,
+//     sum_j x_j e(+-m j / n) = x_0 + (-1)^m x_{n/2} + sum_{0<j<n/2} s_j c  +-  i sum_{0<j<n/2} t_j s_m,
+// so one cosine sum and one sine sum give the outputs m and -m: a quarter of the multiplies and
+// twiddle reads of the plain sums.  The table's sine carries the sign of the exponent, so the
+// same code serves both directions.  Stage 2 does the same over j2 for the disk points (m2, m3)
+// and (-m2, m3) (the disk of a sphere is symmetric in m2): a1[j2] + a1[n2 - j2] and
+// a1[j2] - a1[n2 - j2] are formed in place once per column, and one lane makes both outputs of
+// a pair.  Sums run in another order than in dft_rows_kernel; both are FP32 sums of the same
+// terms.
 constexpr int P12_WARPS = 8;
 
 // Per warp: a1 [n2][c3] and, for the generic stage 1 only, the plane [n2][n3 + 1] (rows padded:
@@ -296,23 +308,30 @@ __host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3, bool 
 
 // Twiddle tables of the plane kernel, unrolled so the inner loops carry no index arithmetic:
 // tw3m[i3][j3] = e(m3(i3) j3 / n3) and tw2d[d][j2] = e(m2(d) j2 / n2), the latter with rows of
-// n2 + 1 so that lanes on neighbouring disk points hit different banks.
-__host__ __device__ inline size_t p12_tables(const int n[3], int c3, int cd)
+// n2 + 1 so that lanes on neighbouring disk points hit different banks.  With stage-2 pairs
+// (np2 > 0) tw2d is replaced by the pair list and tw2m[m2][j2] = e(m2 j2 / n2) for m2 <= k2,
+// j2 <= n2 / 2, rows of p12_ld2 (odd) entries.
+__host__ __device__ inline int p12_ld2(int n2) { return (n2 / 2 + 1) | 1; }
+
+__host__ __device__ inline size_t p12_tables(const int n[3], int c3, int cd, int np2, int k2)
 {
-    return align16(sizeof(float2) * ((size_t)c3 * n[2] + (size_t)cd * (n[1] + 1)));
+    const size_t t2 = np2 > 0 ? (size_t)np2 * 2 + (size_t)(k2 + 1) * p12_ld2(n[1]) : (size_t)cd * (n[1] + 1);
+    return align16(sizeof(float2) * (size_t)c3 * n[2]) + align16(sizeof(float2) * t2);
 }
 
-__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, bool plane)
+__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, int np2, int k2, bool plane)
 {
     const size_t tables = align16(sizeof(float2) * (n[0] + n[1] + n[2]) + sizeof(int) * (c3 + 2 * cd));
-    return tables + p12_tables(n, c3, cd) + P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane) * sizeof(float2);
+    return tables + p12_tables(n, c3, cd, np2, k2) +
+           P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane) * sizeof(float2);
 }
 
 template <int N3>  // 0: any n3 (one output per lane)
 __global__ void __launch_bounds__(P12_WARPS * 32)
     dft_plane12_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int n2, int n3, int c3,
-                       int cd, const int *__restrict__ g_m3, const int *__restrict__ g_disk,
-                       const float2 *__restrict__ g_tw, float2 *__restrict__ Y2)
+                       int sym3, int cd, const int *__restrict__ g_m3, const int *__restrict__ g_disk,
+                       int np2, int k2, const int4 *__restrict__ g_pair2, const float2 *__restrict__ g_tw,
+                       float2 *__restrict__ Y2)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     float2 *tw = reinterpret_cast<float2 *>(smem);  // [n1 | n2 | n3]
@@ -321,8 +340,12 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     const int nn[3] = {n1, n2, n3};
     float2 *tw3m = reinterpret_cast<float2 *>(
         smem + align16(sizeof(float2) * (n1 + n2 + n3) + sizeof(int) * (c3 + 2 * cd)));
-    float2 *tw2d = tw3m + (size_t)c3 * n3;
-    float2 *wbase = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(tw3m) + p12_tables(nn, c3, cd));
+    float2 *tw2d = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(tw3m) + align16(sizeof(float2) * c3 * n3));
+    int4 *pair2 = reinterpret_cast<int4 *>(tw2d);  // np2 > 0: [np2] (16-byte aligned), then tw2m
+    const int ld2 = p12_ld2(n2), h2 = (n2 - 1) / 2;
+    float2 *tw2m = tw2d + (size_t)np2 * 2;
+    float2 *wbase =
+        reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(tw3m) + p12_tables(nn, c3, cd, np2, k2));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int t = tid; t < n1 + n2 + n3; t += blockDim.x)
         tw[t] = g_tw[t];
@@ -336,9 +359,18 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         const int i3 = t / n3, j3 = t - i3 * n3;
         tw3m[t] = tw3[(int)(((long long)m3[i3] * j3) % n3)];
     }
-    for (int t = tid; t < cd * n2; t += blockDim.x) {
-        const int d = t / n2, j2 = t - d * n2;
-        tw2d[d * (n2 + 1) + j2] = tw2[(int)(((long long)disk[2 * d] * j2) % n2)];
+    if (np2 > 0) {
+        for (int t = tid; t < np2; t += blockDim.x)
+            pair2[t] = g_pair2[t];
+        for (int t = tid; t < (k2 + 1) * ld2; t += blockDim.x) {
+            const int m2 = t / ld2, j2 = t - m2 * ld2;
+            tw2m[t] = tw2[(m2 * j2) % n2];
+        }
+    } else {
+        for (int t = tid; t < cd * n2; t += blockDim.x) {
+            const int d = t / n2, j2 = t - d * n2;
+            tw2d[d * (n2 + 1) + j2] = tw2[(int)(((long long)disk[2 * d] * j2) % n2)];
+        }
     }
     __syncthreads();
     const int plane = n2 * n3;
@@ -385,13 +417,45 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
                     for (int j3 = 0; j3 < N3; ++j3)
                         xr[j3] = __ldg(line + j3);
                 }
-                for (int i3 = 0; i3 < c3; ++i3) {
-                    const float2 *w = tw3m + i3 * N3;  // the same row for every lane: broadcast reads
-                    float2 acc = make_float2(0.f, 0.f);
+                if (sym3 >= 0) {
+                    constexpr int H = (N3 - 1) / 2;  // pairs (j, n3 - j), 0 < j < n3 / 2
+                    float2 a0 = xr[0];
 #pragma unroll
-                    for (int j3 = 0; j3 < N3; ++j3)
-                        cmac(acc, xr[j3], w[j3]);
-                    a1[j2 * c3 + i3] = acc;
+                    for (int j = 1; j <= H; ++j) {  // xr[j] <- s_j, xr[n3 - j] <- t_j
+                        const float2 u = xr[j], v = xr[N3 - j];
+                        xr[j] = make_float2(u.x + v.x, u.y + v.y);
+                        xr[N3 - j] = make_float2(u.x - v.x, u.y - v.y);
+                        a0.x += xr[j].x;
+                        a0.y += xr[j].y;
+                    }
+                    const float2 mid = (N3 % 2 == 0) ? xr[N3 / 2] : make_float2(0.f, 0.f);
+                    float2 *out = a1 + j2 * c3 + sym3;  // m3 = m sits at index sym3 + m
+                    out[0] = make_float2(a0.x + mid.x, a0.y + mid.y);
+                    for (int m = 1; m <= sym3; ++m) {
+                        const float2 *w = tw3m + (sym3 + m) * N3;  // e(m j / n3), j = 0..n3-1: broadcast
+                        const float sg = (m & 1) ? -1.f : 1.f;
+                        float2 A = make_float2(fmaf(sg, mid.x, xr[0].x), fmaf(sg, mid.y, xr[0].y));
+                        float2 B = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int j = 1; j <= H; ++j) {
+                            const float2 cs = w[j];
+                            A.x = fmaf(xr[j].x, cs.x, A.x);
+                            A.y = fmaf(xr[j].y, cs.x, A.y);
+                            B.x = fmaf(xr[N3 - j].x, cs.y, B.x);
+                            B.y = fmaf(xr[N3 - j].y, cs.y, B.y);
+                        }
+                        out[m] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
+                        out[-m] = make_float2(A.x + B.y, A.y - B.x);  // A - i B
+                    }
+                } else {
+                    for (int i3 = 0; i3 < c3; ++i3) {
+                        const float2 *w = tw3m + i3 * N3;  // the same row for every lane: broadcast reads
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int j3 = 0; j3 < N3; ++j3)
+                            cmac(acc, xr[j3], w[j3]);
+                        a1[j2 * c3 + i3] = acc;
+                    }
                 }
             }
         } else {
@@ -412,15 +476,112 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         __syncwarp();
         // stage 2: y2[d] = sum_j2 a1[j2][i3(d)] e(m2(d) j2 / n2)
         float2 *dst = Y2 + task * cd;
-        for (int d = lane; d < cd; d += 32) {
-            const int i3 = disk[2 * d + 1];
-            const float2 *w = tw2d + d * (n2 + 1), *a = a1 + i3;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int j2 = 0; j2 < n2; ++j2)
-                cmac(acc, a[j2 * c3], w[j2]);
-            dst[d] = acc;
+        if (np2 > 0) {
+            // a1[j2] <- a1[j2] + a1[n2 - j2], a1[n2 - j2] <- a1[j2] - a1[n2 - j2] for 0 < j2 < n2 / 2
+            for (int t = lane; t < h2 * c3; t += 32) {
+                const int j2 = 1 + t / c3, i3 = t - (j2 - 1) * c3;
+                const float2 u = a1[j2 * c3 + i3], v = a1[(n2 - j2) * c3 + i3];
+                a1[j2 * c3 + i3] = make_float2(u.x + v.x, u.y + v.y);
+                a1[(n2 - j2) * c3 + i3] = make_float2(u.x - v.x, u.y - v.y);
+            }
+            __syncwarp();
+            for (int e = lane; e < np2; e += 32) {
+                const int4 pr = pair2[e];  // (i3, m2, d of m2, d of -m2)
+                const float2 *a = a1 + pr.x, *w = tw2m + pr.y * ld2;
+                float2 A = a[0], B = make_float2(0.f, 0.f);
+                if ((n2 & 1) == 0) {
+                    const float sg = (pr.y & 1) ? -1.f : 1.f;
+                    A.x = fmaf(sg, a[(n2 / 2) * c3].x, A.x);
+                    A.y = fmaf(sg, a[(n2 / 2) * c3].y, A.y);
+                }
+                for (int j2 = 1; j2 <= h2; ++j2) {
+                    const float2 cs = w[j2], s = a[j2 * c3], t = a[(n2 - j2) * c3];
+                    A.x = fmaf(s.x, cs.x, A.x);
+                    A.y = fmaf(s.y, cs.x, A.y);
+                    B.x = fmaf(t.x, cs.y, B.x);
+                    B.y = fmaf(t.y, cs.y, B.y);
+                }
+                dst[pr.z] = make_float2(A.x - B.y, A.y + B.x);      // A + i B
+                if (pr.w >= 0)
+                    dst[pr.w] = make_float2(A.x + B.y, A.y - B.x);  // A - i B
+            }
+        } else {
+            for (int d = lane; d < cd; d += 32) {
+                const int i3 = disk[2 * d + 1];
+                const float2 *w = tw2d + d * (n2 + 1), *a = a1 + i3;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int j2 = 0; j2 < n2; ++j2)
+                    cmac(acc, a[j2 * c3], w[j2]);
+                dst[d] = acc;
+            }
         }
         __syncwarp();  // the plane buffer is rewritten by the next task
+    }
+}
+
+// Stage 3 with sphere pairs (np1 > 0): y(+-m1, d) = A +- i B from the sums of
+// ys[j1][d] + ys[n1 - j1][d] (times the cosine) and ys[j1][d] - ys[n1 - j1][d] (times the sine),
+// formed while the row is loaded; tw1m[m1][j1] = e(m1 j1 / n1), m1 <= k1, rows of p3_ld1 (odd).
+__host__ __device__ inline int p3_ld1(int n1) { return (n1 / 2 + 1) | 1; }
+
+__host__ __device__ inline size_t p3_smem_paired(int n1, int cd, int np1, int k1)
+{
+    return sizeof(float2) * ((size_t)n1 * cd + (size_t)(k1 + 1) * p3_ld1(n1)) + sizeof(int4) * np1;
+}
+
+__global__ void __launch_bounds__(256)
+    dft_stage3_paired_kernel(const float2 *__restrict__ Y2, int rows, int n1, int cd, int np1, int k1,
+                             const int4 *__restrict__ g_pair1, const float2 *__restrict__ g_tw,
+                             float2 *__restrict__ Y, long long ldy)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    int4 *pair1 = reinterpret_cast<int4 *>(smem);                // [np1]
+    float2 *tw1m = reinterpret_cast<float2 *>(pair1 + np1);     // [k1 + 1][ld1]
+    const int ld1 = p3_ld1(n1), h1 = (n1 - 1) / 2;
+    float2 *ys = tw1m + (size_t)(k1 + 1) * ld1;                  // [n1][cd]
+    const int tid = threadIdx.x;
+    for (int t = tid; t < np1; t += blockDim.x)
+        pair1[t] = g_pair1[t];
+    for (int t = tid; t < (k1 + 1) * ld1; t += blockDim.x) {
+        const int m1 = t / ld1, j1 = t - m1 * ld1;
+        tw1m[t] = g_tw[(m1 * j1) % n1];
+    }
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        __syncthreads();  // tables ready / previous row's reads done
+        const float2 *src = Y2 + row * n1 * cd;
+        for (int t = tid; t < cd; t += blockDim.x) {
+            ys[t] = src[t];
+            if ((n1 & 1) == 0)
+                ys[(n1 / 2) * cd + t] = src[(n1 / 2) * cd + t];
+        }
+        for (int t = tid; t < h1 * cd; t += blockDim.x) {
+            const int j1 = 1 + t / cd, d = t - (j1 - 1) * cd;
+            const float2 u = src[j1 * cd + d], v = src[(n1 - j1) * cd + d];
+            ys[j1 * cd + d] = make_float2(u.x + v.x, u.y + v.y);
+            ys[(n1 - j1) * cd + d] = make_float2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+        float2 *y = Y + row * ldy;
+        for (int e = tid; e < np1; e += blockDim.x) {
+            const int4 pr = pair1[e];  // (d, m1, g of m1, g of -m1)
+            const float2 *a = ys + pr.x, *w = tw1m + pr.y * ld1;
+            float2 A = a[0], B = make_float2(0.f, 0.f);
+            if ((n1 & 1) == 0) {
+                const float sg = (pr.y & 1) ? -1.f : 1.f;
+                A.x = fmaf(sg, a[(n1 / 2) * cd].x, A.x);
+                A.y = fmaf(sg, a[(n1 / 2) * cd].y, A.y);
+            }
+            for (int j1 = 1; j1 <= h1; ++j1) {
+                const float2 cs = w[j1], s = a[j1 * cd], t = a[(n1 - j1) * cd];
+                A.x = fmaf(s.x, cs.x, A.x);
+                A.y = fmaf(s.y, cs.x, A.y);
+                B.x = fmaf(t.x, cs.y, B.x);
+                B.y = fmaf(t.y, cs.y, B.y);
+            }
+            y[pr.z] = make_float2(A.x - B.y, A.y + B.x);      // A + i B
+            if (pr.w >= 0)
+                y[pr.w] = make_float2(A.x + B.y, A.y - B.x);  // A - i B
+        }
     }
 }
 
@@ -542,8 +703,9 @@ static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long 
         cudaFuncSetAttribute(dft_plane12_kernel<N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    dft_plane12_kernel<N3><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.cd,
-                                                               p.m3list, p.disk, tw, work);
+    dft_plane12_kernel<N3><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.sym3,
+                                                               p.cd, p.m3list, p.disk, p.np2, p.k2, p.pair2, tw,
+                                                               work);
     return cudaGetLastError();
 }
 
@@ -555,11 +717,16 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
     if ((!p12_compiled(p.n[2]) && rows > WS_MAX_ROWS_GENERIC) || !work)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     const float2 *tw = negative_exponent ? p.twc : p.tw;
-    const size_t sm12 = p12_smem(p.n, p.c3, p.cd, !p12_compiled(p.n[2]));
-    const size_t sm3 = sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
+    const size_t sm12 = p12_smem(p.n, p.c3, p.cd, p.np2, p.k2, !p12_compiled(p.n[2]));
+    const bool paired3 = p.np1 > 0 && p3_smem_paired(p.n[0], p.cd, p.np1, p.k1) <= DFT_SMEM_MAX;
+    const size_t sm3 = paired3 ? p3_smem_paired(p.n[0], p.cd, p.np1, p.k1)
+                               : sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
     if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
         return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
-    cudaError_t e = cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    cudaError_t e = paired3 ? cudaFuncSetAttribute(dft_stage3_paired_kernel,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)
+                            : cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sm3);
     if (e != cudaSuccess)
         return e;
     const long long ntasks = (long long)rows * p.n[0];
@@ -579,7 +746,10 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
     if (e != cudaSuccess)
         return e;
     const int g3 = std::min(rows, 152 * 8);
-    dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
+    if (paired3)
+        dft_stage3_paired_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.np1, p.k1, p.pair1, tw, Y, ldy);
+    else
+        dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -377,10 +377,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Bound on max |f| for the FP16 scale: per r, max_v |psi_v(r)| * max_c |psi_c(r)|.
 __global__ void f_bound_kernel(const float2 *__restrict__ psiT, int nr, int nb, int nv, unsigned *bound_bits)
 {
+    // one warp per r: the lanes read the row of psiT coalesced and reduce its two maxima
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     float best = 0.f;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nr; r += gridDim.x * wpb) {
         float mv = 0.f, mc = 0.f;
-        for (int n = 0; n < nb; ++n) {
+        for (int n = lane; n < nb; n += 32) {
             const float2 z = psiT[(size_t)r * nb + n];
             const float a = sqrtf(z.x * z.x + z.y * z.y);
             if (n < nv)
@@ -388,9 +390,14 @@ __global__ void f_bound_kernel(const float2 *__restrict__ psiT, int nr, int nb, 
             else
                 mc = fmaxf(mc, a);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+            mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        }
         best = fmaxf(best, mv * mc);
     }
-    atomicMax(bound_bits, __float_as_uint(best));  // non-negative floats order like their bits
+    if (lane == 0)
+        atomicMax(bound_bits, __float_as_uint(best));  // non-negative floats order like their bits
 }
 
 // scale exponent e with (bound * sw_max) * 2^e <= 2^14 (FP16 max is 65504, so a factor of four
@@ -431,7 +438,8 @@ __device__ __forceinline__ float from16(uint16_t u)
 // The 16-bit operand planes of the pair densities.  blockIdx.y is one 16-wide chunk of k, whose
 // (v, c) pairs and weights are resolved once in shared memory; threads run over the chunk in the
 // order it is stored (32-bit index arithmetic, no division per element), so every warp writes
-// 64 contiguous bytes per plane and reads psi_c(r) for 8 consecutive c of each r.
+// 64 contiguous bytes per plane and reads psi_c(r) for 8 consecutive c of each r.  Used when the
+// rows of psiT are too long for pair_density16_rows_kernel.
 template <bool BF16>
 __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__restrict__ psiT,
                                                              const float *__restrict__ sw, int nr, int nb, int nv,
@@ -475,6 +483,71 @@ __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__res
         Fc[per_chunk + rem] = to16<BF16>(fr - from16<BF16>(rh));
         Fc[2 * per_chunk + rem] = ih;
         Fc[3 * per_chunk + rem] = il;
+    }
+}
+
+// The same planes with the rows of psiT staged in shared memory: blockIdx.x is one 8-row group
+// (its 8 rows of psiT, nb states each, read from global memory once), blockIdx.y one of
+// gridDim.y parts of the k chunks.  Warp w takes chunks w, w + 8, ... of the part; each lane
+// makes four consecutive k of one r (the element values are those of pair_density16_kernel, bit
+// for bit) and stores 8 bytes per plane, so a warp writes the group's 256 contiguous bytes of
+// every plane of a chunk.
+constexpr int PD_LDP_PAD = 2;  // row pitch nb + 2 float2: lanes on 8 rows spread over the banks
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) pair_density16_rows_kernel(const float2 *__restrict__ psiT,
+                                                                  const float *__restrict__ sw, int nr, int nb,
+                                                                  int nv, int nc, int kpad, int nr_pad,
+                                                                  const int *__restrict__ scale_exp,
+                                                                  uint16_t *__restrict__ F)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    float2 *s_psi = reinterpret_cast<float2 *>(smem);  // [8][nb + PD_LDP_PAD]
+    const int ldp = nb + PD_LDP_PAD;
+    const int grp = blockIdx.x;
+    for (int t = threadIdx.x; t < 8 * nb; t += blockDim.x) {
+        const int rr = t / nb, n = t - rr * nb, r = grp * 8 + rr;
+        s_psi[rr * ldp + n] = r < nr ? psiT[(size_t)r * nb + n] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float s = ldexpf(1.0f, *scale_exp);
+    const int nk = nv * nc, nchunks = kpad / KC16, per_chunk = nr_pad * KC16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rem = 4 * lane;                                    // element offset in the group's 128
+    const int r8 = (rem & 63) >> 3, kk0 = ((rem & 127) >> 6) * 8 + (rem & 7);
+    const bool live = grp * 8 + r8 < nr;
+    const float2 *row = s_psi + r8 * ldp;
+    const int per_part = (nchunks + gridDim.y - 1) / gridDim.y;
+    const int kc_end = min(nchunks, (int)(blockIdx.y + 1) * per_part);
+    for (int kc = blockIdx.y * per_part + warp; kc < kc_end; kc += 8) {
+        const int k0 = kc * KC16 + kk0;
+        int v = k0 / nc, c = k0 - v * nc;
+        uint32_t p[4][2];  // planes Re hi, Re lo, Im hi, Im lo: two 16-bit values per word
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i;
+            float fr = 0.f, fi = 0.f;
+            const float w = k < nk ? sw[k] * s : 0.f;  // padding k: zero operand
+            if (live && w != 0.f) {
+                const float2 a = row[v];
+                const float2 b = row[nv + c];
+                fr = fmaf(a.x, b.x, a.y * b.y) * w;   // conj(psi_v) psi_c
+                fi = fmaf(a.x, b.y, -a.y * b.x) * w;
+            }
+            if (++c == nc) {
+                c = 0;
+                ++v;
+            }
+            const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi), il = to16<BF16>(fi - from16<BF16>(ih));
+            const uint32_t h[4] = {rh, to16<BF16>(fr - from16<BF16>(rh)), ih, il};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                p[q][i >> 1] = (i & 1) ? (p[q][i >> 1] | (h[q] << 16)) : h[q];
+        }
+        uint16_t *dst = F + (size_t)kc * NPL * per_chunk + (size_t)grp * 128 + rem;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint2 *>(dst + (size_t)q * per_chunk) = make_uint2(p[q][0], p[q][1]);
     }
 }
 
@@ -546,11 +619,32 @@ cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_
     cudaError_t e = cudaMemsetAsync(bound_bits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess)
         return e;
-    f_bound_kernel<<<grid_for(nr), 256, 0, s>>>(psiT, nr, nb, nv, bound_bits);
+    f_bound_kernel<<<std::max(1, std::min((nr + 7) / 8, 152 * 16)), 256, 0, s>>>(psiT, nr, nb, nv, bound_bits);
     count_launches(1);
     scale_exp_kernel<<<1, 1, 0, s>>>(bound_bits, sw_max, bf16 ? 1 : 0, scale_exp);
     count_launches(1);
     const int nchunks = kpad / KC16, per_chunk = nr_pad * KC16;
+    const size_t rows_smem = (size_t)8 * (nb + PD_LDP_PAD) * sizeof(float2);
+    if (rows_smem <= 100 * 1024) {
+        // parts of k per row group: about 4 blocks per SM-resident slot, at least one chunk per warp
+        const int ngrp = nr_pad / 8;
+        const int parts = std::max(1, std::min((nchunks + 7) / 8, (152 * 6 * 4 + ngrp - 1) / ngrp));
+        const dim3 g2(ngrp, parts);
+        e = bf16 ? cudaFuncSetAttribute(pair_density16_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)rows_smem)
+                 : cudaFuncSetAttribute(pair_density16_rows_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem);
+        if (e != cudaSuccess)
+            return e;
+        if (bf16)
+            pair_density16_rows_kernel<true><<<g2, 256, rows_smem, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad,
+                                                                        scale_exp, F);
+        else
+            pair_density16_rows_kernel<false><<<g2, 256, rows_smem, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad,
+                                                                         scale_exp, F);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     dim3 grid(std::max(1, std::min((per_chunk + 255) / 256, (152 * 16 + nchunks - 1) / nchunks)), nchunks);
     if (bf16)
         pair_density16_kernel<true><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);

@@ -179,7 +179,7 @@ constexpr int HERK16_KC = 16;
 constexpr int HERK16_NPL = 4;
 constexpr int HERK16_T = 128;
 
-// k_herk16.cu
+// k_herk16.cu, k_planes16.cu
 size_t herk16_smem_bytes();
 cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
                                   int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,

@@ -1,0 +1,51 @@
+"""The sphere transforms of Sec. 4.1 (e^{+iG.r} on rows of P in gw_P_to_G, e^{-iG.r} on the pair
+densities in gw_build_PG) on grids that reach every branch of the paired sums: odd and even axis
+lengths (with and without the middle term x_{n/2}), the register stage 1 (compiled n3: 24, 27)
+and the generic one (n3 = 11, 13), non-cubic grids.  Each P~ is compared with the oracle's FP64
+route of Eq. (gpsaceP), which shares nothing with the kernels."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_1810_07772_gb300 import gw, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+GRIDS = [
+    ((27, 27, 27), 40),   # compiled odd n3, odd n1 and n2: no middle term anywhere
+    ((9, 15, 27), 16),    # odd n1, n2 with the compiled odd stage 1
+    ((7, 9, 24), 12),     # compiled even n3 (middle term in stage 1 only)
+    ((12, 10, 13), 8),    # generic odd n3, even n1 and n2 (middle terms in stages 2 and 3)
+    ((11, 11, 11), 20),   # generic stage 1, all odd
+]
+
+
+@pytest.mark.parametrize("dims,gcut", GRIDS)
+@pytest.mark.parametrize("route", ["rspace", "gspace"])
+def test_paired_transforms_match_oracle(dims, gcut, route):
+    nv, nc = 3, 9
+    psi, E = inputs.make_states(0, nv, nc, 61 + sum(dims), dims=dims)
+    g_ref = O.sphere(dims, gcut)
+    Pt = O.P_gspace(psi, E, nv, dims, g_ref)
+    with gw.Context(0) as ctx:
+        ctx.load_states(torch.from_numpy(psi.astype(np.complex64)).to(DEV), E, dims, nv)
+        if route == "rspace":
+            ctx.build_P("fp16x3")
+            g = ctx.P_to_G(gcut)
+        else:
+            g = ctx.build_PG(gcut)
+        PG = ctx.view("PG").cpu().numpy()
+    assert np.array_equal(g, g_ref)
+    assert rel(PG, Pt) <= 1e-6
+    # the G = 0 row vanishes at q = 0 (occupied and unoccupied states are orthogonal)
+    i0 = int(np.flatnonzero((g_ref == 0).all(axis=1))[0])
+    assert np.max(np.abs(Pt[i0])) <= 1e-12 * np.linalg.norm(Pt)
+    assert np.max(np.abs(PG[i0])) <= 1e-6 * np.linalg.norm(Pt)

@@ -1511,9 +1511,9 @@ double predicted_error(int precision, int W)
 {
     if (precision == GW_PREC_BF16X3)
         return 4e-6;
-    static const int ws[] = {1, 2, 3, 4, 6, 8, 16};
-    static const double es[] = {2.6e-7, 4.9e-7, 5.7e-7, 6.8e-7, 1.2e-6, 1.3e-6, 2.6e-6};
-    for (int i = 0; i < 7; ++i)
+    static const int ws[] = {1, 2, 3, 4, 5, 6, 8, 16};
+    static const double es[] = {2.9e-7, 4.6e-7, 6.5e-7, 8.1e-7, 1.08e-6, 1.3e-6, 1.6e-6, 3.3e-6};
+    for (int i = 0; i < 8; ++i)
         if (W <= ws[i])
             return es[i];
     return 1e-5;
@@ -1705,9 +1705,10 @@ gw_status gw_batch_autotune(gw_batch *b, const char *cache_path, double target_e
         return GW_E_INVALID;
     gw_batch &bb = *b;
     cudaSetDevice(bb.device);
-    // the choice depends on the error target as well as on the shapes
-    char tgt[32];
-    std::snprintf(tgt, sizeof tgt, "|target%.3g", target_error);
+    // the choice depends on the error target as well as on the shapes, and on the error table
+    // of the update kernel (rule2: the three-N=256 + six-N=128 form)
+    char tgt[48];
+    std::snprintf(tgt, sizeof tgt, "|target%.3g|rule2", target_error);
     const std::string key = batch_key(bb) + tgt;
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "r")) {

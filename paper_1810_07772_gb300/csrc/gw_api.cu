@@ -906,9 +906,9 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     const bool bf16 = precision == GW_PREC_BF16X3;
     const int k = c.k, kpad = ((k + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
     const int ng_pad = ((ng + 255) / 256) * 256;
-    // buffers: pair densities [k][nr_pad] complex64 in F, their transforms [k][ng] in Q, the 16-bit
-    // planes of the transforms in QT, the result in PG
-    GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
+    // buffers: the pair-density transforms [k][ng] in Q, the 16-bit planes of the transforms in QT,
+    // the result in PG (pair densities [k][nr_pad] complex64 in F only where the transform kernel
+    // cannot form them itself)
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k * ng * sizeof(float2), "pair-density transforms"));
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad * ng_pad * 2 * HERK16_NPL, "transform planes"));
     GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
@@ -922,17 +922,28 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
         c.n_tiles_g = static_cast<int>(t.size());
         c.tiles_g_pad = ng_pad;
     }
-    c.F_prec = -1;  // F now holds plain pair densities, not the operand of gw_build_P
+    c.F_prec = -1;  // F no longer holds the operand of gw_build_P (nor its scale word)
     c.P_ready = c.PG_ready = c.eps_ready = false;
     const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
     int *scale_exp = reinterpret_cast<int *>(c.d_small + 1);
-    float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
 
     record(c, 0);
-    GW_CUDA(launch_pair_density_rows(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, Fc, s), "pair densities");
+    // The states back in [nb][N_r] order (psiT transposed), so that the transform kernel forms
+    // each pair density from two contiguous state lines; grids that need the row-block kernel
+    // store the pair densities first.
+    GW_TRY(ensure(c, c.d_psi, c.cap.psi, (size_t)c.nb * c.nr * sizeof(float2), "state staging"));
+    GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
     record(c, 1);
     record(c, 3);
-    GW_CUDA(launch_dft_rows_ws(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, c.d_dftw, s, true), "pair-density transforms");
+    cudaError_t fe = launch_dft_pairs_ws(c.d_psi, c.nr, c.d_sw, c.nv, c.nc, c.d_Q, ng, c.plan, c.d_dftw, s, true);
+    if (fe == cudaErrorNotSupported) {
+        GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
+        float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
+        GW_CUDA(launch_pair_density_rows(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, Fc, s),
+                "pair densities");
+        fe = launch_dft_rows_ws(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, c.d_dftw, s, true);
+    }
+    GW_CUDA(fe, "pair-density transforms");
     record(c, 4);
     GW_CUDA(launch_planes16_from_c64(c.d_Q, k, ng, ng, kpad, ng_pad, bf16, c.d_small, scale_exp,
                                      reinterpret_cast<uint16_t *>(c.d_QT), s),

@@ -222,6 +222,12 @@ bool dft_supported(const DftPlan &p);  // sphere small enough for the transform 
 size_t dft_work_bytes(const DftPlan &p, int rows);
 cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
                                float2 *work, cudaStream_t s, bool negative_exponent = false);
+// The same transform of the nv nc pair densities f_k = conj(psi_v) psi_c sw[k] (k = v nc + c),
+// formed from the states psi [nb][nr] inside the kernel; row k of Y is f_k's transform.
+// cudaErrorNotSupported (nothing launched) where the grid needs the row-block kernel.
+cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
+                                long long ldy, const DftPlan &p, float2 *work, cudaStream_t s,
+                                bool negative_exponent);
 // negative_exponent: exp(-iG.r) instead of exp(+iG.r) (the conjugated twiddle table)
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                             const DftPlan &p, cudaStream_t s, bool negative_exponent = false);

@@ -326,12 +326,28 @@ __host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, int n
            P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane) * sizeof(float2);
 }
 
-template <int N3>  // 0: any n3 (one output per lane)
+// Pair-density rows (PAIR): row k of the transform is f_k(r) = conj(psi_v(r)) psi_c(r) w_k with
+// k = v nc + c (Eq. fdef), formed while the lines are loaded from the states psi [nb][N_r] (X,
+// row stride ldx = N_r) instead of being read from a stored [k][N_r] array.  The products are
+// written with the same FP32 operations as in pair_density_tiled_kernel.  Tasks then run
+// j1-major, so the warps of a CTA share psi_v.
+struct PairSrc {
+    const float *sw;
+    int nv, nc;
+};
+
+template <bool PAIR>
+__device__ __forceinline__ float2 pair_or_x(float2 a, float2 b, float w)
+{
+    return PAIR ? make_float2(fmaf(a.x, b.x, a.y * b.y) * w, fmaf(a.x, b.y, -a.y * b.x) * w) : a;
+}
+
+template <int N3, bool PAIR>  // N3 = 0: any n3 (one output per lane)
 __global__ void __launch_bounds__(P12_WARPS * 32)
     dft_plane12_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int n2, int n3, int c3,
                        int sym3, int cd, const int *__restrict__ g_m3, const int *__restrict__ g_disk,
                        int np2, int k2, const int4 *__restrict__ g_pair2, const float2 *__restrict__ g_tw,
-                       float2 *__restrict__ Y2)
+                       float2 *__restrict__ Y2, PairSrc ps)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     float2 *tw = reinterpret_cast<float2 *>(smem);  // [n1 | n2 | n3]
@@ -383,14 +399,31 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     const long long ntasks = (long long)rows * n1;
     for (long long task = (long long)blockIdx.x * P12_WARPS + warp; task < ntasks;
          task += (long long)gridDim.x * P12_WARPS) {
-        const long long row = task / n1;
-        const int j1 = (int)(task - row * n1);
-        const float2 *src = X + row * ldx + (size_t)j1 * plane;
+        long long row;
+        int j1;
+        if (PAIR) {
+            j1 = (int)(task / rows);
+            row = task - (long long)j1 * rows;
+        } else {
+            row = task / n1;
+            j1 = (int)(task - row * n1);
+        }
+        // PAIR: src is the plane of psi_c and srcv that of psi_v, w the weight of the pair
+        const float2 *src, *srcv = nullptr;
+        float w = 0.f;
+        if (PAIR) {
+            const int kk = (int)row, v = kk / ps.nc;
+            src = X + (size_t)(ps.nv + kk - v * ps.nc) * ldx + (size_t)j1 * plane;
+            srcv = X + (size_t)v * ldx + (size_t)j1 * plane;
+            w = ps.sw[kk];
+        } else {
+            src = X + row * ldx + (size_t)j1 * plane;
+        }
         if (kPlane) {
             int j2 = lane / n3, j3 = lane - (lane / n3) * n3;  // q = lane + 32 i -> (j2, j3), no division in the loop
             const int dj2 = 32 / n3, dj3 = 32 - (32 / n3) * n3;
             for (int q = lane; q < plane; q += 32) {
-                xp[j2 * ld3 + j3] = src[q];
+                xp[j2 * ld3 + j3] = pair_or_x<PAIR>(PAIR ? srcv[q] : src[q], src[q], w);
                 j2 += dj2;
                 j3 += dj3;
                 if (j3 >= n3) {
@@ -412,10 +445,21 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
                         xr[j3] = make_float2(v.x, v.y);
                         xr[j3 + 1 < N3 ? j3 + 1 : j3] = make_float2(v.z, v.w);
                     }
+                    if (PAIR) {  // x <- conj(psi_v) psi_c w
+                        const float2 *lv = srcv + (size_t)j2 * N3;
+#pragma unroll
+                        for (int j3 = 0; j3 < N3; j3 += 2) {
+                            const float4 a = __ldg(reinterpret_cast<const float4 *>(lv + j3));
+                            xr[j3] = pair_or_x<PAIR>(make_float2(a.x, a.y), xr[j3], w);
+                            if (j3 + 1 < N3)
+                                xr[j3 + 1] = pair_or_x<PAIR>(make_float2(a.z, a.w), xr[j3 + 1], w);
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int j3 = 0; j3 < N3; ++j3)
-                        xr[j3] = __ldg(line + j3);
+                        xr[j3] = pair_or_x<PAIR>(PAIR ? __ldg(srcv + (size_t)j2 * N3 + j3) : __ldg(line + j3),
+                                                 __ldg(line + j3), w);
                 }
                 if (sym3 >= 0) {
                     constexpr int H = (N3 - 1) / 2;  // pairs (j, n3 - j), 0 < j < n3 / 2
@@ -475,7 +519,7 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         }
         __syncwarp();
         // stage 2: y2[d] = sum_j2 a1[j2][i3(d)] e(m2(d) j2 / n2)
-        float2 *dst = Y2 + task * cd;
+        float2 *dst = Y2 + (row * n1 + j1) * cd;
         if (np2 > 0) {
             // a1[j2] <- a1[j2] + a1[n2 - j2], a1[n2 - j2] <- a1[j2] - a1[n2 - j2] for 0 < j2 < n2 / 2
             for (int t = lane; t < h2 * c3; t += 32) {
@@ -695,34 +739,46 @@ size_t dft_work_bytes(const DftPlan &p, int rows)
     return (size_t)r * p.n[0] * p.cd * sizeof(float2);
 }
 
-template <int N3>
-static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
-                              const float2 *tw, float2 *work, cudaStream_t s)
+template <int N3, bool PAIR>
+static cudaError_t launch_p12_t(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
+                                const float2 *tw, float2 *work, PairSrc ps, cudaStream_t s)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(dft_plane12_kernel<N3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(dft_plane12_kernel<N3, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess)
         return e;
-    dft_plane12_kernel<N3><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3, p.sym3,
-                                                               p.cd, p.m3list, p.disk, p.np2, p.k2, p.pair2, tw,
-                                                               work);
+    dft_plane12_kernel<N3, PAIR><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.n[1], p.n[2], p.c3,
+                                                                     p.sym3, p.cd, p.m3list, p.disk, p.np2, p.k2,
+                                                                     p.pair2, tw, work, ps);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                               float2 *work, cudaStream_t s, bool negative_exponent)
+template <int N3>
+static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
+                              const float2 *tw, float2 *work, const PairSrc *ps, cudaStream_t s)
+{
+    return ps ? launch_p12_t<N3, true>(grid, smem, X, ldx, rows, p, tw, work, *ps, s)
+              : launch_p12_t<N3, false>(grid, smem, X, ldx, rows, p, tw, work, PairSrc{nullptr, 0, 1}, s);
+}
+
+// The two-kernel transform of `rows` rows: of X (ps == nullptr) or of the pair densities formed
+// from the states X = psi [nb][ldx] (ps != nullptr).  Returns cudaErrorNotSupported, with nothing
+// launched, when pair rows would need the row-block kernel.
+static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
+                                  const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent,
+                                  const PairSrc *ps)
 {
     if (rows <= 0)
         return cudaSuccess;
     if ((!p12_compiled(p.n[2]) && rows > WS_MAX_ROWS_GENERIC) || !work)
-        return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
+        return ps ? cudaErrorNotSupported : launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     const float2 *tw = negative_exponent ? p.twc : p.tw;
     const size_t sm12 = p12_smem(p.n, p.c3, p.cd, p.np2, p.k2, !p12_compiled(p.n[2]));
     const bool paired3 = p.np1 > 0 && p3_smem_paired(p.n[0], p.cd, p.np1, p.k1) <= DFT_SMEM_MAX;
     const size_t sm3 = paired3 ? p3_smem_paired(p.n[0], p.cd, p.np1, p.k1)
                                : sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
     if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
-        return launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
+        return ps ? cudaErrorNotSupported : launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     cudaError_t e = paired3 ? cudaFuncSetAttribute(dft_stage3_paired_kernel,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)
                             : cudaFuncSetAttribute(dft_stage3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -732,16 +788,16 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
     const long long ntasks = (long long)rows * p.n[0];
     const int g12 = (int)std::min<long long>((ntasks + P12_WARPS - 1) / P12_WARPS, 152LL * 16);
     switch (p.n[2]) {
-    case 12: e = launch_p12<12>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 16: e = launch_p12<16>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 18: e = launch_p12<18>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 20: e = launch_p12<20>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 24: e = launch_p12<24>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 27: e = launch_p12<27>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 30: e = launch_p12<30>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 32: e = launch_p12<32>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    case 36: e = launch_p12<36>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
-    default: e = launch_p12<0>(g12, sm12, X, ldx, rows, p, tw, work, s); break;
+    case 12: e = launch_p12<12>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 16: e = launch_p12<16>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 18: e = launch_p12<18>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 20: e = launch_p12<20>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 24: e = launch_p12<24>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 27: e = launch_p12<27>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 30: e = launch_p12<30>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 32: e = launch_p12<32>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    case 36: e = launch_p12<36>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
+    default: e = launch_p12<0>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
     }
     if (e != cudaSuccess)
         return e;
@@ -752,6 +808,19 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
         dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
     count_launches(2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
+                               float2 *work, cudaStream_t s, bool negative_exponent)
+{
+    return dft_two_kernel(X, ldx, rows, Y, ldy, p, work, s, negative_exponent, nullptr);
+}
+
+cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
+                                long long ldy, const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent)
+{
+    const PairSrc ps{sw, nv, nc};
+    return dft_two_kernel(psi, nr, nv * nc, Y, ldy, p, work, s, negative_exponent, &ps);
 }
 
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,

@@ -72,8 +72,9 @@ typedef enum gw_inv_method {
     GW_INV_NEWTON = 1,     /* FP64 Newton iteration X <- X (2I - eps X) of Sec. 5.1, from        */
                            /* X0 = eps^H / max_i sum_j |(eps eps^H)_ij|, until max |dX| < 1e-11  */
     GW_INV_NEWTON_TC = 2   /* the Newton iteration of Sec. 5.1 on the 16-bit tensor cores, for a  */
-                           /* Hermitian positive definite eps: FP16X3 steps from X0 = 2/(1+u) I   */
-                           /* (u = max row sum of |eps|) to max |I - eps X| < 3e-5, then two      */
+                           /* Hermitian positive definite eps: FP16X3 steps from the Jacobi-scaled */
+                           /* X0 = 2/(1+u) diag(eps)^-1 (u = max row sum of the scaled |eps|) to  */
+                           /* max |I - eps X| < 3e-5, then two                                     */
                            /* refinements R = I - eps X, X <- X + X R with R exact to FP64 from   */
                            /* integer slices (see gw_zgemm_tc); GW_E_NUMERIC if the residual      */
                            /* before the last refinement exceeds 1e-8                             */

@@ -3,10 +3,15 @@
 //
 // FP64 runs at about 1 TFLOP/s on this GPU and FP16 tensor MMAs at about 2 PFLOP/s, so the
 // inverse is carried by the tensor cores:
-//  * Phase 1: Newton iterations whose products use the FP16X3 split (22 significant bits), from
-//    X0 = 2 / (1 + u) I with u = max_i sum_j |eps_ij| >= lambda_max, until max |I - eps X| < 3e-5.
-//    For a Hermitian positive definite eps (lambda_min >= 1 for the eps of this library) the error
-//    e = I - eps X squares each step from e0 <= (u - 1) / (u + 1).
+//  * Phase 1: Newton iterations whose products use the FP16X3 split (22 significant bits), until
+//    max |I - eps X| < 3e-5, from the Jacobi-scaled start X0 = 2 / (1 + u) D^-1: D = diag(eps)
+//    (through rs_i = 1 / sqrt(eps_ii) in FP32, D^-1 = diag(rs^2)) and
+//    u = max_i rs_i sum_j |eps_ij| rs_j >= lambda_max(D^-1/2 eps D^-1/2).  eps X0 is similar to
+//    2 / (1 + u) D^-1/2 eps D^-1/2, whose eigenvalues lie in (0, 2) for a Hermitian positive
+//    definite eps, and the error e = I - eps X squares each step.  Scaling the rows and columns of
+//    eps by a positive diagonal leaves the scaled matrix, and so the step count, unchanged.  A
+//    diagonal entry that is not positive and finite falls back to X0 = 2 / (1 + u) I with the
+//    plain row-sum bound u = max_i sum_j |eps_ij|.
 //  * Phase 2: up to three refinement steps R = I - eps X, X <- X + X R.  R is computed to FP64 accuracy
 //    from integer slices (the error-free splitting of Ozaki, Ogita, Oishi and Rump, Numer.
 //    Algorithms 59, 2012): every entry scaled into [-1, 1] is a sum of slices a_t 2^(-6(t+1))
@@ -423,6 +428,9 @@ enum NsWord : int {
     W_COUNT,     // completed blocks of the running combine
     W_DISCARD,   // deviations nobody reads
     W_U,         // row-sum bound of lambda_max
+    W_UJ,        // the same bound of the Jacobi-scaled matrix
+    W_RS2,       // max rs_i^2 (the largest entry of X0 / alpha)
+    W_DBAD,      // nonzero: a diagonal entry is not positive and finite (identity start)
     W_TOTAL
 };
 static_assert(W_TOTAL <= 64, "scalar area");
@@ -617,33 +625,63 @@ __global__ void zcombine_int_kernel(const float2 *__restrict__ T, int nslots, co
     combine_tail(best, dev, words, acc_max, fin_max, dev_to, use, tol, iter, flags);
 }
 
-// u = max_i sum_j (|Re a_ij| + |Im a_ij|) >= max_i sum_j |a_ij| >= lambda_max, one warp per row,
-// into words[W_U] (the bits of a non-negative double; zero beforehand).
-__global__ void row_sum_bound_kernel(const double2 *__restrict__ A, int n, unsigned long long *words)
+// rs_i = 1 / sqrt(Re a_ii) (FP32 reciprocal square root, widened) for the Jacobi-scaled start;
+// words[W_RS2] = max rs_i^2, words[W_DBAD] set where a diagonal entry gives no positive finite rs.
+__global__ void jacobi_rs_kernel(const double2 *__restrict__ A, int n, double *__restrict__ rs,
+                                 unsigned long long *words)
 {
-    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
-        double s = 0.0;
-        for (int j = lane; j < n; j += 32) {
-            const double2 a = A[(size_t)i * n + j];
-            s += fabs(a.x) + fabs(a.y);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double d = A[(size_t)i * n + i].x;
+        const double r = (d > 0.0 && d < 1e30) ? (double)rsqrtf((float)d) : 0.0;
+        if (r > 0.0 && isfinite(r)) {
+            rs[i] = r;
+            atomicMax(&words[W_RS2], (unsigned long long)__double_as_longlong(r * r));
+        } else {
+            rs[i] = 0.0;
+            atomicOr(&words[W_DBAD], 1ull);
         }
-        for (int o = 16; o > 0; o >>= 1)
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0)
-            atomicMax(&words[W_U], (unsigned long long)__double_as_longlong(s));
     }
 }
 
-// X0 = c I with c = 2 / (1 + u), u >= lambda_max from row_sum_bound_kernel.
-__global__ void ns_init_kernel(double2 *X, int N, unsigned long long *words, int *flags)
+// u = max_i sum_j (|Re a_ij| + |Im a_ij|) >= max_i sum_j |a_ij| >= lambda_max, one warp per row,
+// into words[W_U], and the same bound of diag(rs) A diag(rs) into words[W_UJ] (the bits of
+// non-negative doubles; zero beforehand).
+__global__ void row_sum_bound_kernel(const double2 *__restrict__ A, int n, const double *__restrict__ rs,
+                                     unsigned long long *words)
 {
-    const double c = 2.0 / (1.0 + __longlong_as_double((long long)words[W_U]));
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
+        double s = 0.0, sj = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double2 a = A[(size_t)i * n + j];
+            const double m = fabs(a.x) + fabs(a.y);
+            s += m;
+            sj += m * rs[j];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sj += __shfl_xor_sync(0xffffffffu, sj, o);
+        }
+        if (lane == 0) {
+            atomicMax(&words[W_U], (unsigned long long)__double_as_longlong(s));
+            atomicMax(&words[W_UJ], (unsigned long long)__double_as_longlong(sj * rs[i]));
+        }
+    }
+}
+
+// X0 = c diag(rs)^2 with c = 2 / (1 + u_J) (the Jacobi-scaled start), or c I with c = 2 / (1 + u)
+// when words[W_DBAD] is set; both bounds from row_sum_bound_kernel.
+__global__ void ns_init_kernel(double2 *X, int N, const double *__restrict__ rs, unsigned long long *words,
+                               int *flags)
+{
+    const bool jac = words[W_DBAD] == 0;
+    const double c = 2.0 / (1.0 + __longlong_as_double((long long)words[jac ? W_UJ : W_U]));
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     for (int r = blockIdx.y; r < N && col < N; r += gridDim.y)
-        X[(size_t)r * N + col] = make_double2(r == col ? c : 0.0, 0.0);
+        X[(size_t)r * N + col] = make_double2(r == col ? (jac ? c * rs[r] * rs[r] : c) : 0.0, 0.0);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        words[W_X] = (unsigned long long)__double_as_longlong(fabs(c));
+        const double xmax = jac ? c * __longlong_as_double((long long)words[W_RS2]) : c;
+        words[W_X] = (unsigned long long)__double_as_longlong(fabs(xmax));
         words[W_ITERS] = (unsigned long long)NS_MAX;
         for (int j = 0; j <= NS_REFINE + 1; ++j)
             flags[j] = 0;
@@ -1057,9 +1095,11 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
     NS_TRY(launch_zslice(p16, true, A, N, &words[W_EPS], A16, nullptr, s));
     NS_TRY(launch_zslice(poz, true, A, N, &words[W_EPS], AOZ, nullptr, s));
     (void)rowsum;
-    row_sum_bound_kernel<<<std::max(1, std::min(152 * 4, (N + 7) / 8)), 256, 0, s>>>(A, N, words);
-    count_launches(1);
-    ns_init_kernel<<<grid2d(N, N), 256, 0, s>>>(X, N, words, skip);  // skip[0]: phase 1, [1 + j]: refinement j
+    double *rs = reinterpret_cast<double *>(Z);  // scratch: Z is first written by phase 1
+    jacobi_rs_kernel<<<std::max(1, std::min(152 * 4, (N + 255) / 256)), 256, 0, s>>>(A, N, rs, words);
+    row_sum_bound_kernel<<<std::max(1, std::min(152 * 4, (N + 7) / 8)), 256, 0, s>>>(A, N, rs, words);
+    count_launches(2);
+    ns_init_kernel<<<grid2d(N, N), 256, 0, s>>>(X, N, rs, words, skip);  // skip[0]: phase 1, [1 + j]: refinement j
     count_launches(1);
     NS_TRY(cudaGetLastError());
     // phase 1: X <- X (2I - eps X) with FP16X3 products, stopped on device below NS_TOL

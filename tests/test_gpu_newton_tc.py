@@ -100,6 +100,28 @@ def test_zinv_tc_random_hpd(n):
     assert 1 <= rep["refinements"] <= 3 and rep["res_last"] <= 1e-8
 
 
+def test_zinv_tc_jacobi_start():
+    """A = D^1/2 C D^1/2 with C of unit diagonal (eigenvalues 1..3 before the scaling) and D in
+    [1, 16]: the Jacobi-scaled start sees C's conditioning (3) instead of A's (21).  In FP64 the
+    iteration from 2/(1+u) I needs 9 steps to max |I - A X| < 3e-5 and from the Jacobi start 6;
+    the tensor-core phase 1 must stay within one step of the latter."""
+    rng = np.random.default_rng(23)
+    n = 300
+    Q, _ = np.linalg.qr(crand(rng, n, n))
+    C = (Q * rng.uniform(1.0, 3.0, n)) @ Q.conj().T
+    c = np.real(np.diag(C))
+    C = C / np.sqrt(c[:, None] * c[None, :])
+    d = rng.uniform(1, 16, n)
+    A = C * np.sqrt(d[:, None] * d[None, :])
+    with gw.Context(0) as ctx:
+        X = ctx.zinv_tc(dev(A)).cpu().numpy()
+        rep = ctx.newton_tc_report()
+    ref = np.linalg.inv(A)
+    assert rep["steps"] <= 7
+    assert np.max(np.abs(X - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(X @ A - np.eye(n))) <= 1e-11
+
+
 def test_zinv_tc_indefinite_is_numeric_error():
     rng = np.random.default_rng(11)
     Q, _ = np.linalg.qr(crand(rng, 64, 64))

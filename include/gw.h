@@ -378,6 +378,19 @@ GW_API gw_status gw_newton_tc_report(gw_ctx *ctx, double *out4);
 GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_windows);
 
 /*
+ * Error target of the 16-bit rank-k update, as the relative Frobenius error of P~ against FP64
+ * (0 = use the window of gw_set_herk_window, the default).  Each gw_build_P / gw_build_PG then
+ * takes the longest window of 16, 8, 6, 5, 4, 3, 2, 1 chunks whose predicted error x 1.25 meets
+ * the target at the call's precision; the predictions are errors measured at 24^3 (FP16X3:
+ * 2.9e-7 at 1 chunk, 6.5e-7 at 3, 3.3e-6 at 16; BF16X3 4e-6 above those).  The flush length
+ * stays that of gw_set_herk_window.  GW_E_INVALID for a negative or non-finite target,
+ * GW_E_UNSUPPORTED when no window meets it (below 3.6e-7); a build whose precision cannot meet
+ * it fails with GW_E_UNSUPPORTED.  gw_set_herk_window clears the target.  The window used is
+ * reported by gw_get_stats (stats8[6]).
+ */
+GW_API gw_status gw_set_error_target(gw_ctx *ctx, double target);
+
+/*
  * Wave vector q of eps^q (Sec. 4.1 and 5.1), in units of 2 pi / cell_L per axis (default 0).
  * eps^q_GG' = delta_GG' - sqrt(V(q+G)) P~^q_GG' sqrt(V(q+G')), V(q+G) = 4 pi / (Omega |q+G|^2); only
  * where q + G = 0 (the head at q = 0) is V set to 0.  For q != 0 the states passed to

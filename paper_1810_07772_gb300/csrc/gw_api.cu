@@ -152,6 +152,34 @@ gw_status read_device_status(Ctx &c)
     return fail(c, static_cast<gw_status>(code), "device wait ran out in the %s (block %u)", sname, detail);
 }
 
+// Measured error of the FP16 split against FP64 on the 24^3 workload (k = 15360) for window
+// lengths W (chunks of 16 k): the truncating TMEM sum of one window dominates and does not grow
+// with k.  BF16 keeps 8 + 8 bits (about 4e-6 at short windows); its window error is taken as
+// additive on top.
+double predicted_error(int precision, int W)
+{
+    static const int ws[] = {1, 2, 3, 4, 5, 6, 8, 16};
+    static const double es[] = {2.9e-7, 4.6e-7, 6.5e-7, 8.1e-7, 1.08e-6, 1.3e-6, 1.6e-6, 3.3e-6};
+    double e = 1e-5;
+    for (int i = 0; i < 8; ++i)
+        if (W <= ws[i]) {
+            e = es[i];
+            break;
+        }
+    return precision == GW_PREC_BF16X3 ? 4e-6 + e : e;
+}
+
+// The longest window among 16, 8, 6, 5, 4, 3, 2, 1 chunks whose predicted error, with a quarter
+// of margin, meets `target`; 0 when none does.
+int window_for_target(int precision, double target)
+{
+    static const int cand[] = {16, 8, 6, 5, 4, 3, 2, 1};
+    for (int W : cand)
+        if (predicted_error(precision, W) * 1.25 <= target)
+            return W;
+    return 0;
+}
+
 // Upper-triangle tiles of the rank-k update (128-row blocks i of r, 256-row blocks j of r'),
 // kept when the tile reaches the diagonal or above: 256 j + 255 >= 128 i.  Ordered in groups of
 // 8 column blocks so that CTAs resident at the same time share operand rows in L2.
@@ -603,6 +631,17 @@ gw_status gw_set_herk_window(gw_ctx *h, int window_chunks, int flush_windows)
         return GW_E_INVALID;
     h->c.herk_W = window_chunks;
     h->c.herk_L = flush_windows;
+    h->c.err_target = 0.0;
+    return GW_OK;
+}
+
+gw_status gw_set_error_target(gw_ctx *h, double target)
+{
+    if (!h || !(target >= 0.0) || !std::isfinite(target))
+        return GW_E_INVALID;
+    if (target > 0.0 && window_for_target(GW_PREC_FP16X3, target) == 0)
+        return fail(h->c, GW_E_UNSUPPORTED, "no window length meets the error target %g", target);
+    h->c.err_target = target;
     return GW_OK;
 }
 
@@ -642,7 +681,7 @@ gw_status gw_get_stats(gw_ctx *h, double *s8)
         cudaMemcpy(&e, c.d_small + 1, sizeof(int), cudaMemcpyDeviceToHost);
     s8[4] = e;
     s8[5] = c.n_tiles;
-    s8[6] = c.herk_W;
+    s8[6] = c.last_W;
     s8[7] = c.herk_L;
     return GW_OK;
 }
@@ -757,6 +796,12 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     GW_CUDA(cudaSetDevice(c.device), "set device");
     cudaStream_t s = c.stream;
     const bool p16 = precision == GW_PREC_FP16X3 || precision == GW_PREC_BF16X3;
+    if (p16) {
+        c.last_W = c.err_target > 0.0 ? window_for_target(precision, c.err_target) : c.herk_W;
+        if (c.last_W == 0)
+            return fail(c, GW_E_UNSUPPORTED, "no window length meets the error target %g at this precision",
+                        c.err_target);
+    }
     const int kchunk = p16 ? HERK16_KC : HERK_KC;
     c.kpad = ((c.k + kchunk - 1) / kchunk) * kchunk;
     size_t Fbytes;
@@ -802,7 +847,7 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
                 "rank-k update (CUDA cores)");
     } else if (p16) {
         GW_CUDA(launch_herk16(reinterpret_cast<uint16_t *>(c.d_F), precision == GW_PREC_BF16X3, c.kpad, c.nr,
-                              c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L,
+                              c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, scale_exp, c.d_err, wait_ns, c.last_W, c.herk_L,
                               s),
                 "rank-k update (tcgen05, 16-bit)");
     } else {
@@ -904,6 +949,10 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
         return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", ng);
     cudaStream_t s = c.stream;
     const bool bf16 = precision == GW_PREC_BF16X3;
+    c.last_W = c.err_target > 0.0 ? window_for_target(precision, c.err_target) : c.herk_W;
+    if (c.last_W == 0)
+        return fail(c, GW_E_UNSUPPORTED, "no window length meets the error target %g at this precision",
+                    c.err_target);
     const int k = c.k, kpad = ((k + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
     const int ng_pad = ((ng + 255) / 256) * 256;
     // buffers: the pair-density transforms [k][ng] in Q, the 16-bit planes of the transforms in QT,
@@ -955,7 +1004,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     if (splits > 1)
         GW_TRY(ensure(c, c.d_PG_parts, c.cap.PG_parts, (size_t)splits * ng * ng * sizeof(float2), "split-k partials"));
     GW_CUDA(launch_herk16(reinterpret_cast<const uint16_t *>(c.d_QT), bf16, kpad, ng, ng_pad, c.d_tiles_g,
-                          c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s, splits,
+                          c.n_tiles_g, c.d_PG, scale_exp, c.d_err, wait_ns, c.last_W, c.herk_L, s, splits,
                           c.d_PG_parts),
             "rank-k update in G space");
     GW_TRY(finish_PG(c, s));
@@ -1513,21 +1562,6 @@ gw_status batch_status(gw_batch &b)
         b.herk_ms = ms;
     cudaGetLastError();
     return first;
-}
-
-// Measured error of the FP16 split against FP64 on the 24^3 workload (k = 15360) for window
-// lengths W (chunks of 16 k): the truncating TMEM sum of one window dominates and does not grow
-// with k.  BF16 keeps 8 + 8 bits and sits near 4e-6 for any W.
-double predicted_error(int precision, int W)
-{
-    if (precision == GW_PREC_BF16X3)
-        return 4e-6;
-    static const int ws[] = {1, 2, 3, 4, 5, 6, 8, 16};
-    static const double es[] = {2.9e-7, 4.6e-7, 6.5e-7, 8.1e-7, 1.08e-6, 1.3e-6, 1.6e-6, 3.3e-6};
-    for (int i = 0; i < 8; ++i)
-        if (W <= ws[i])
-            return es[i];
-    return 1e-5;
 }
 
 std::string batch_key(const gw_batch &b)

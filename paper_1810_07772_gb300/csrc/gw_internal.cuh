@@ -143,7 +143,9 @@ struct Ctx {
     int tiles_nr_pad = -1, tiles_kind = -1;
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
     unsigned *d_small = nullptr;    // [0] |f| bound bits, [1] FP16 scale exponent
-    int herk_W = 3, herk_L = 256;   // 5.7e-7 against FP64 at 24^3; see gw_set_herk_window
+    int herk_W = 3, herk_L = 256;   // 6.5e-7 against FP64 at 24^3; see gw_set_herk_window
+    double err_target = 0.0;        // > 0: the window comes from gw_set_error_target's rule
+    int last_W = 3;                 // the window of the last 16-bit rank-k update
 
     void release();
 };

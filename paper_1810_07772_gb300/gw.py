@@ -50,6 +50,7 @@ SIGNATURES = {
     "gw_set_wait_limit": (_i, [_vp, _d]),
     "gw_set_q": (_i, [_vp, _c.POINTER(_d)]),
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
+    "gw_set_error_target": (_i, [_vp, ctypes.c_double]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
     "gw_eps_inv_noalloc": (_i, [_vp, _i, _vp, _vp]),
@@ -320,6 +321,10 @@ class Context:
 
     def set_herk_window(self, window_chunks, flush_windows):
         self._check(lib().gw_set_herk_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def set_error_target(self, target):
+        """P~ error target of the 16-bit update; the window follows from it (gw_set_error_target)."""
+        self._check(lib().gw_set_error_target(self._h, float(target)))
 
     def set_q(self, q):
         """Wave vector of eps^q in units of 2 pi / cell_L (gw_set_q)."""

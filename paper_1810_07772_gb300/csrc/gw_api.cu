@@ -442,14 +442,98 @@ int sm_count(int device)
 }
 
 // The tensor-core Newton iteration (Sec. 5.1) for the inverse of A (n x n, device) into X.
-gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X)
+void drop_ns_graph(Ctx &c)
+{
+    if (c.ns_exec)
+        cudaGraphExecDestroy(c.ns_exec);
+    if (c.ns_graph)
+        cudaGraphDestroy(c.ns_graph);
+    c.ns_exec = nullptr;
+    c.ns_graph = nullptr;
+    c.ns_key = Ctx::NsKey{};
+}
+
+// The tensor-core Newton inverse of A (n x n) into X.  With use_graph, every step is queued in its
+// graph-safe form (tables uploaded beforehand, device flags skip the unneeded steps, no host reads)
+// and captured once into a CUDA graph per (n, buffers, wait limit, stream), then replayed: the
+// eager form stops queuing on host reads of the convergence flag, which leave the GPU idle.
+gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X, bool use_graph = false)
 {
     const int nsm = sm_count(c.device);
     GW_TRY(ensure(c, c.d_tcw, c.cap.tcw, ns_work_bytes(n, nsm), "tensor-core Newton workspace"));
     GW_TRY(ensure(c, c.d_scal, c.cap.scal, 4 * sizeof(double), "Newton scalars"));
     const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
-    GW_CUDA(ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.stream),
-            "tensor-core Newton inverse");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (use_graph && (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)) {
+        cudaGetLastError();
+        use_graph = false;  // the caller is capturing this stream: queue into its capture instead
+        GW_CUDA(ns_prepare(c.d_tcw, n, nsm, c.stream), "Newton tables");
+        GW_CUDA(ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.stream, true),
+                "tensor-core Newton inverse");
+        return GW_OK;
+    }
+    if (!use_graph) {
+        // the eager form uploads the tables of order n into the workspace: a graph captured for
+        // another order would then read tables of the wrong layout
+        if (c.ns_exec && c.ns_key.n != n)
+            drop_ns_graph(c);
+        GW_CUDA(ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.stream),
+                "tensor-core Newton inverse");
+        return GW_OK;
+    }
+    Ctx::NsKey key;
+    key.n = n;
+    key.A = A;
+    key.X = X;
+    key.work = c.d_tcw;
+    key.err = c.d_err;
+    key.wait_ns = wait_ns;
+    key.s = c.stream;
+    if (!c.ns_exec || !(key == c.ns_key)) {
+        drop_ns_graph(c);
+        GW_CUDA(ns_prepare(c.d_tcw, n, nsm, c.stream), "Newton tables");
+        // captured on a private stream (the caller's may be the legacy default stream, which
+        // cannot be captured); the graph is then launched on the caller's stream
+        if (!c.ns_cap_stream)
+            GW_CUDA(cudaStreamCreateWithFlags(&c.ns_cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (cudaStreamBeginCapture(c.ns_cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GW_E_CUDA, "stream capture of the Newton inverse could not start");
+        }
+        const unsigned long long counted = g_launches.load();
+        const cudaError_t eq =
+            ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.ns_cap_stream, true);
+        g_launches.store(counted);  // captured launches run at replay time, where they are counted
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c.ns_cap_stream, &g);
+        if (eq != cudaSuccess || ec != cudaSuccess || !g) {
+            cudaGetLastError();
+            if (g)
+                cudaGraphDestroy(g);
+            return fail(c, GW_E_CUDA, "stream capture of the Newton inverse failed");
+        }
+        c.ns_graph = g;
+        if (cudaGraphInstantiate(&c.ns_exec, c.ns_graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            drop_ns_graph(c);
+            return fail(c, GW_E_CUDA, "instantiation of the Newton graph failed");
+        }
+        size_t nn = 0;
+        c.ns_graph_kernels = 0;
+        if (cudaGraphGetNodes(c.ns_graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(c.ns_graph, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                        ++c.ns_graph_kernels;
+                }
+        }
+        cudaGetLastError();
+        c.ns_key = key;
+    }
+    GW_CUDA(cudaGraphLaunch(c.ns_exec, c.stream), "Newton graph launch");
+    count_launches(static_cast<int>(c.ns_graph_kernels));
     return GW_OK;
 }
 
@@ -502,6 +586,10 @@ void Ctx::release()
     dfree(d_eps);
     dfree(d_epsinv);
     dfree(d_work);
+    drop_ns_graph(*this);
+    if (ns_cap_stream)
+        cudaStreamDestroy(ns_cap_stream);
+    ns_cap_stream = nullptr;
     dfree(d_scal);
     dfree(d_tcw);
     dfree(d_PGsum);
@@ -1043,7 +1131,7 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     else if (method == GW_INV_NEWTON)
         GW_TRY(inverse_newton(c));
     else
-        GW_TRY(inverse_newton_tc(c, c.d_eps, ng, c.d_epsinv));
+        GW_TRY(inverse_newton_tc(c, c.d_eps, ng, c.d_epsinv, true));
     record(c, 8);
     if (eps_out)
         GW_CUDA(cudaMemcpyAsync(eps_out, c.d_eps, bytes, cudaMemcpyDefault, s), "copy eps out");

@@ -122,6 +122,22 @@ struct Ctx {
     bool eps_ready = false;
     int newton_iters = 0;
     double tc_report[4] = {-1, -1, -1, -1};  // last tensor-core Newton inverse (gw_newton_tc_report)
+    // gw_eps_inv's tensor-core inverse as a captured CUDA graph, valid for the key below
+    cudaGraph_t ns_graph = nullptr;
+    cudaGraphExec_t ns_exec = nullptr;
+    cudaStream_t ns_cap_stream = nullptr;  // private stream the graph is captured on (never runs work)
+    unsigned long long ns_graph_kernels = 0;
+    struct NsKey {
+        int n = 0;
+        const void *A = nullptr, *X = nullptr, *work = nullptr, *err = nullptr;
+        uint64_t wait_ns = 0;
+        cudaStream_t s = nullptr;
+        bool operator==(const NsKey &o) const
+        {
+            return n == o.n && A == o.A && X == o.X && work == o.work && err == o.err && wait_ns == o.wait_ns &&
+                   s == o.s;
+        }
+    } ns_key;
     void *d_ppw = nullptr;          // plasmon-pole workspace
     PPWork pp = {};                 // its pieces (valid while pp_ready)
     int pp_b = 0, pp_nmodes = 0;

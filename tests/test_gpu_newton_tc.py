@@ -168,3 +168,32 @@ def test_eps_inv_newton_tc_matches_cholesky(w, route):
     assert np.max(np.abs(inv_t - inv_c)) <= 1e-12
     assert res_t <= 1e-12
     assert 0 <= iters < 16
+
+
+def test_eps_inv_graph_replay_matches_eager():
+    """gw_eps_inv replays its tensor-core inverse from a captured CUDA graph (graph-safe steps,
+    device flags) and recaptures when the order changes; gw_zinv_tc queues the same kernels
+    eagerly with host reads of the convergence flag (and, for another order, drops the graph,
+    whose tables it overwrites).  The kernels that run are the same, so the results agree bit for
+    bit."""
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    dims = (w.n,) * 3
+    with gw.Context(0) as ctx:
+        ctx.load_states(torch.from_numpy(psi.astype(np.complex64)).to(DEV), E, dims, w.nv)
+        for gcut in (w.gcut, w.gcut - 2, w.gcut):
+            g = ctx.build_PG(gcut)
+            ng = len(g)
+            eps = torch.empty((ng, ng), dtype=torch.complex128, device=DEV)
+            first = torch.empty_like(eps)
+            ctx.eps_inv("newton_tc", eps_out=eps, epsinv_out=first)          # capture
+            again = torch.empty_like(eps)
+            ctx.eps_inv("newton_tc", epsinv_out=again)                      # replay
+            eager = ctx.zinv_tc(eps)
+            other = ctx.zinv_tc(torch.eye(5, dtype=torch.complex128, device=DEV) * 2.0)  # another order
+            last = torch.empty_like(eps)
+            ctx.eps_inv("newton_tc", epsinv_out=last)                       # recapture
+            a, b, c, d, e = (t.cpu().numpy() for t in (first, again, eager, last, eps))
+            assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+            assert np.max(np.abs(a - O.inverse_cholesky(e))) <= 1e-12
+            assert np.allclose(other.cpu().numpy(), np.eye(5) * 0.5, rtol=0, atol=1e-15)

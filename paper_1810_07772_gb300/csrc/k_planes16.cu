@@ -75,6 +75,25 @@ __device__ __forceinline__ float from16(uint16_t u)
     }
 }
 
+// hi = rn16(x), lo = rn16(x - hi) for two values at once, packed two per word (x0 in the low half)
+template <bool BF16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    if (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
 // The 16-bit operand planes of the pair densities.  blockIdx.y is one 16-wide chunk of k, whose
 // (v, c) pairs and weights are resolved once in shared memory; threads run over the chunk in the
 // order it is stored (32-bit index arithmetic, no division per element), so every warp writes
@@ -162,27 +181,32 @@ __global__ void __launch_bounds__(256) pair_density16_rows_kernel(const float2 *
     for (int kc = blockIdx.y * per_part + warp; kc < kc_end; kc += 8) {
         const int k0 = kc * KC16 + kk0;
         int v = k0 / nc, c = k0 - v * nc;
-        uint32_t p[4][2];  // planes Re hi, Re lo, Im hi, Im lo: two 16-bit values per word
+        float fr[4], fi[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int k = k0 + i;
-            float fr = 0.f, fi = 0.f;
+            fr[i] = 0.f;
+            fi[i] = 0.f;
             const float w = k < nk ? sw[k] * s : 0.f;  // padding k: zero operand
             if (live && w != 0.f) {
                 const float2 a = row[v];
                 const float2 b = row[nv + c];
-                fr = fmaf(a.x, b.x, a.y * b.y) * w;   // conj(psi_v) psi_c
-                fi = fmaf(a.x, b.y, -a.y * b.x) * w;
+                fr[i] = fmaf(a.x, b.x, a.y * b.y) * w;   // conj(psi_v) psi_c
+                fi[i] = fmaf(a.x, b.y, -a.y * b.x) * w;
             }
             if (++c == nc) {
                 c = 0;
                 ++v;
             }
-            const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi), il = to16<BF16>(fi - from16<BF16>(ih));
-            const uint32_t h[4] = {rh, to16<BF16>(fr - from16<BF16>(rh)), ih, il};
+        }
+        // planes Re hi, Re lo, Im hi, Im lo, two elements per word (element i in the low half):
+        // the paired conversions round each value as the single ones do
+        uint32_t p[4][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                p[q][i >> 1] = (i & 1) ? (p[q][i >> 1] | (h[q] << 16)) : h[q];
+        for (int j = 0; j < 2; ++j) {
+            const int i = 2 * j;
+            split2<BF16>(fr[i], fr[i + 1], p[0][j], p[1][j]);
+            split2<BF16>(fi[i], fi[i + 1], p[2][j], p[3][j]);
         }
         uint16_t *dst = F + (size_t)kc * NPL * per_chunk + (size_t)grp * 128 + rem;
 #pragma unroll

@@ -208,7 +208,7 @@ def test_learned_correction_gain_24cubed():
                     ctx.eps_inv("cholesky", eps_out=eps, epsinv_out=inv)
                     I = torch.eye(ng, dtype=torch.complex128, device=dev)
                     assert float((inv @ eps - I).abs().max()) <= 1e-12
-                    # the judge, P~ of the full sum, against the FP64 oracle at sampled entries
+                    # the reference of the learned form, P~ of the full sum, against the FP64 oracle at sampled entries
                     sel = np.array([0, 1, 7, 100, 350, 690])
                     ref = O.P_gspace_entries(psi.cpu().numpy().astype(np.complex128), E, nv, dims, d["gvec"][sel])
                     sub = d["PG_all"][sel][:, sel].cpu().numpy()

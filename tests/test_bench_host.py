@@ -63,3 +63,14 @@ def test_default_arguments():
     a = bench.parse_args([])
     assert a.gpus == 1 and a.warmup >= 3 and a.impl == "gw" and a.workload == "plain"
     assert bench.WORKLOADS["plain"].n == 24
+
+
+def test_workload_precision_and_error_target():
+    """The 24^3 path runs FP16X3 with the library's default window; the 36^3 split configuration,
+    stated with BF16 hi+lo operands and a 1e-4 target on P~, runs BF16X3 under that target; an
+    explicit --precision wins."""
+    a = bench.parse_args([])
+    assert a.precision == "fp16x3" and bench.ERROR_TARGET.get(a.workload) is None
+    s = bench.parse_args(["--workload", "split"])
+    assert s.precision == "bf16x3" and bench.ERROR_TARGET["split"] == 1e-4
+    assert bench.parse_args(["--workload", "split", "--precision", "fp16x3"]).precision == "fp16x3"

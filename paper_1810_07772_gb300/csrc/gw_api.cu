@@ -442,6 +442,24 @@ int sm_count(int device)
 }
 
 // The tensor-core Newton iteration (Sec. 5.1) for the inverse of A (n x n, device) into X.
+// Kernel nodes of a captured graph: its launches, added to the launch counter on every replay.
+unsigned long long kernel_nodes(cudaGraph_t g)
+{
+    unsigned long long k = 0;
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+            for (size_t i = 0; i < nn; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                    ++k;
+            }
+    }
+    cudaGetLastError();
+    return k;
+}
+
 void drop_ns_graph(Ctx &c)
 {
     if (c.ns_exec)
@@ -518,18 +536,7 @@ gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X, bool us
             drop_ns_graph(c);
             return fail(c, GW_E_CUDA, "instantiation of the Newton graph failed");
         }
-        size_t nn = 0;
-        c.ns_graph_kernels = 0;
-        if (cudaGraphGetNodes(c.ns_graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-            std::vector<cudaGraphNode_t> nodes(nn);
-            if (cudaGraphGetNodes(c.ns_graph, nodes.data(), &nn) == cudaSuccess)
-                for (size_t i = 0; i < nn; ++i) {
-                    cudaGraphNodeType t;
-                    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
-                        ++c.ns_graph_kernels;
-                }
-        }
-        cudaGetLastError();
+        c.ns_graph_kernels = kernel_nodes(c.ns_graph);
         c.ns_key = key;
     }
     GW_CUDA(cudaGraphLaunch(c.ns_exec, c.stream), "Newton graph launch");
@@ -1812,18 +1819,7 @@ gw_status gw_batch_run(gw_batch *b, int use_graph)
                 drop_graph(bb);
                 return bfail(bb, GW_E_CUDA, "graph instantiation failed");
             }
-            size_t nn = 0;
-            bb.graph_kernels = 0;
-            if (cudaGraphGetNodes(bb.graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-                std::vector<cudaGraphNode_t> nodes(nn);
-                if (cudaGraphGetNodes(bb.graph, nodes.data(), &nn) == cudaSuccess)
-                    for (size_t i = 0; i < nn; ++i) {
-                        cudaGraphNodeType t;
-                        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
-                            ++bb.graph_kernels;
-                    }
-            }
-            cudaGetLastError();
+            bb.graph_kernels = static_cast<int>(kernel_nodes(bb.graph));
         }
         GW_BCUDA(cudaGraphLaunch(bb.exec, bb.stream), "graph launch");
         count_launches(bb.graph_kernels);

@@ -57,9 +57,12 @@ typedef enum gw_status {
 
 /* Arithmetic used for the Hermitian rank-k update P = -F^T conj(F).                         */
 typedef enum gw_precision {
-    GW_PREC_TF32X3 = 0,    /* tcgen05 kind::tf32; every FP32 operand split x = hi + lo, both   */
-                           /* rounded to TF32; hi*hi + hi*lo + lo*hi, one TMEM accumulation over */
-                           /* all k (its truncating FP32 sum limits accuracy to ~1e-8 * k/8)    */
+    GW_PREC_TF32X3 = 0,    /* DIAGNOSTIC, not a plain-FP32 mode: tcgen05 kind::tf32, every FP32 */
+                           /* operand split x = hi + lo, both rounded to TF32, hi*hi + hi*lo +   */
+                           /* lo*hi, one TMEM accumulation over all k.  The truncating FP32 sum  */
+                           /* of that one accumulation limits accuracy to ~1e-8 * k/8 (2.2e-4 on */
+                           /* P~ at k = 15360), so it misses a 1e-6 target; GW_PREC_FP16X3 is the */
+                           /* mode that meets it.  Kept to measure what window promotion buys.    */
     GW_PREC_BF16X3 = 1,    /* tcgen05 kind::f16 (BF16); same split and promotion as FP16X3       */
     GW_PREC_TF32X1 = 2,    /* tcgen05 kind::tf32, one product (diagnostic, ~1e-4 relative)      */
     GW_PREC_FP32_SIMT = 3, /* plain FP32 FMA on the CUDA cores (the same-GPU FP32 comparison)   */
@@ -271,19 +274,23 @@ GW_API gw_status gw_batch_last_error(const gw_batch *batch, char *buf, size_t n)
 /*
  * Allocation-free inverse of a Hermitian positive-definite complex128 matrix, by the same FP64
  * blocked Cholesky that gw_eps_inv uses.  The paper has no counterpart: this entry point exists for
- * callers that cannot allocate device memory -- code running while a stream is captured into a
- * CUDA graph, applications whose device memory belongs to another allocator, and loops that must
- * not pay cudaFree's device-wide synchronisation.
+ * callers that cannot allocate device memory -- applications whose device memory belongs to another
+ * allocator (a framework's caching pool or an arena sized at start-up, where a raw cudaMalloc
+ * fragments the pool or fails once it has claimed everything), and loops that must not pay
+ * cudaFree's device-wide synchronisation.
  *   eps     device pointer, n x n complex128, row-major (only its lower triangle is read)
  *   n       1 <= n <= 512; larger orders return GW_E_INVALID
  *   epsinv  device pointer, n x n complex128, receives eps^-1 (both triangles written)
- *   stream  cudaStream_t to enqueue on (NULL = legacy default stream); the call synchronises it
- *           and returns GW_E_NUMERIC if a Cholesky pivot was <= 0
- * Both pointers must be on the calling thread's current device.  No context is needed and no
- * device memory is allocated: the workspace is one static device array of 12.9 MB, which every
- * GPU that loads the library keeps until the process exits.  The first call on a device looks up
- * that array's device address; make that first call before any stream capture.  All calls share
- * the array, so calls that overlap on the GPU (other threads, other streams) race: serialise them.
+ *   stream  cudaStream_t to enqueue on (NULL = legacy default stream)
+ * The call reads its status word back to the host and synchronises `stream` before it returns, so
+ * the calling thread blocks until the inverse is done; it returns GW_E_NUMERIC if a Cholesky pivot
+ * was <= 0.  Both pointers must be device memory of the calling thread's current device, else
+ * GW_E_INVALID.  No context is needed and no device memory is allocated: the workspace is one
+ * static device array of 12.9 MB, which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's contents (the
+ * call clears what must start at zero), so calls that overlap on the GPU (other threads, other
+ * streams) race: serialise them.
  */
 GW_API gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, void *stream);
 

@@ -319,15 +319,6 @@ def P_gspace_entries(psi, E_eV, nv, dims, gsel):
     return out
 
 
-def P_gspace_truncated(psi, E_eV, nv, nc_keep, dims, gvec):
-    """Eq. (gpsaceP) with the unoccupied sum cut to the nc_keep lowest states (band truncation)."""
-    psi = np.asarray(psi)
-    keep = np.concatenate([psi[:nv], psi[nv:nv + nc_keep]])
-    E = np.asarray(E_eV)
-    Ek = np.concatenate([E[:nv], E[nv:nv + nc_keep]])
-    return P_gspace(keep, Ek, nv, dims, gvec)
-
-
 # ----------------------------------------------------------------------------- eps
 
 

@@ -2,14 +2,14 @@
 // device memory.
 //
 // Who cannot allocate, and why:
-//  * code that runs while a stream is being captured into a CUDA graph: cudaMalloc and cudaFree
-//    are not captured and would break or silently escape the graph;
-//  * applications whose memory is owned by another allocator (a framework's caching pool, an
-//    arena sized at start-up): a raw cudaMalloc fragments that memory or fails when the pool has
-//    claimed it all;
-//  * latency-sensitive loops: cudaFree synchronises the whole device.
+//  * applications whose device memory is owned by another allocator (a framework's caching pool,
+//    an arena sized at start-up): a raw cudaMalloc fragments that memory, or fails once the pool
+//    has claimed it all;
+//  * latency-sensitive loops: cudaFree synchronises the whole device, stalling every stream.
 // This entry point therefore keeps its workspace in one file-scope static device array of a
 // fixed maximum size, which every GPU that loads the library holds until the process exits.
+// The call reads its status word back to the host and synchronises the given stream before it
+// returns, so it blocks the calling thread until the inverse is done.
 #include <mutex>
 
 #include "gw_internal.cuh"
@@ -68,6 +68,14 @@ extern "C" gw_status gw_eps_inv_noalloc(const void *eps, int n, void *epsinv, vo
         return GW_E_INVALID;  // the static workspace holds matrices of order <= 512
     int device = 0;
     NA_CUDA(cudaGetDevice(&device));
+    // Both matrices must live on the current device: the kernels run there, and a pointer to
+    // another GPU's memory would make them read or write that GPU's memory.
+    for (const void *p : {eps, static_cast<const void *>(epsinv)}) {
+        cudaPointerAttributes attr{};
+        NA_CUDA(cudaPointerGetAttributes(&attr, p));
+        if (attr.type != cudaMemoryTypeDevice || attr.device != device)
+            return GW_E_INVALID;
+    }
     double2 *base = nullptr;
     const gw_status st = scratch_address(device, &base);
     if (st != GW_OK)

@@ -1,6 +1,7 @@
 """Pins for the oracle of the learned truncation correction: the analytic gradient against central
-finite differences, a one-layer case against the closed-form least-squares gradient, and the
-features against a hand-made 2-vector system."""
+finite differences, a one-layer case against the closed-form least-squares gradient, the
+features against a hand-made 2-vector system, the kept/omitted energy weights against hand sums,
+and the FP16 weight copy against hand-known FP16 values at hand-counted offsets."""
 import numpy as np
 
 from oracle import mlp as M
@@ -93,3 +94,45 @@ def test_f16_activation_forward_equals_forward_when_activations_are_exact():
     params = M.unpack(rng.standard_normal(M.n_params(n_in, hidden)) * 0.3, n_in, hidden)
     a, b = M.forward_f16act(params, X), M.forward(params, X)[0]
     assert 0 < np.abs(a - b).max() <= 2.0 ** -9 * np.abs(b).max()
+
+
+HA = 27.211386245988   # eV per Hartree
+
+
+def test_omitted_weights_by_hand():
+    """One occupied state at -1 Ha, four unoccupied at +1, +2, +3, +4 Ha, the sum cut after two of
+    them: kept = 2/2 + 2/3, omitted = 2/4 + 2/5 (weights 2 / (E_c - E_v) in 1/Hartree, inputs in
+    eV).  A second occupied state at -2 Ha adds 2/3 + 2/4 to the kept and 2/5 + 2/6 to the omitted
+    sum: the sum runs over v as well, and swapping kept and omitted fails both cases."""
+    E = np.array([-1.0, 1.0, 2.0, 3.0, 4.0]) * HA
+    om, kept = M.omitted_weights(E, 1, 2)
+    assert abs(kept - (1.0 + 2.0 / 3.0)) < 1e-14
+    assert abs(om - (0.5 + 0.4)) < 1e-14
+    E2 = np.array([-2.0, -1.0, 1.0, 2.0, 3.0, 4.0]) * HA
+    om2, kept2 = M.omitted_weights(E2, 2, 2)
+    assert abs(kept2 - (1.0 + 2.0 / 3.0 + 2.0 / 3.0 + 0.5)) < 1e-14
+    assert abs(om2 - (0.5 + 0.4 + 0.4 + 2.0 / 6.0)) < 1e-14
+    # nothing omitted: the whole sum is kept
+    om3, kept3 = M.omitted_weights(E, 1, 4)
+    assert om3 == 0.0 and abs(kept3 - (1.0 + 2.0 / 3.0 + 0.5 + 0.4)) < 1e-14
+
+
+def test_to_fp16_weights_rounds_weights_and_keeps_biases():
+    """A 2 -> 3 -> 3 -> 3 -> 2 network has 41 parameters laid out as W1 [0, 6), b1 [6, 9),
+    W2 [9, 18), b2 [18, 21), W3 [21, 30), b3 [30, 33), W4 [33, 39), b4 [39, 41).  With every
+    parameter 1/3, the weights must become FP16's nearest value 0.333251953125 (0x3555) and the
+    biases stay 1/3 bit for bit; 2049 rounds to 2048 (FP16 spacing 2 there, tie to even) and 0.1
+    to 0.0999755859375 (0x2E66)."""
+    assert M.n_params(2, 3) == 41
+    theta = np.full(41, 1.0 / 3.0)
+    theta[0], theta[40] = 2049.0, 2049.0        # a weight of W1 and the last bias of b4
+    theta[33], theta[8] = 0.1, 0.1              # the first weight of W4 and the last bias of b1
+    out = M.to_fp16_weights(theta, 2, 3)
+    weight = np.zeros(41, dtype=bool)
+    for a, b in [(0, 6), (9, 18), (21, 30), (33, 39)]:
+        weight[a:b] = True
+    want = np.where(weight, 0.333251953125, 1.0 / 3.0)
+    want[0], want[40] = 2048.0, 2049.0
+    want[33], want[8] = 0.0999755859375, 0.1
+    assert np.array_equal(out, want)
+    assert np.array_equal(theta[~weight], out[~weight])    # biases untouched, bit for bit

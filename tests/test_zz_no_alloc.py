@@ -1,5 +1,5 @@
 """gw_eps_inv_noalloc: the allocation-free FP64 inverse for callers that cannot call cudaMalloc
-(stream capture, memory owned by another allocator, no device-wide sync from cudaFree).
+(device memory owned by another allocator, loops that must not pay cudaFree's device-wide sync).
 
 It must agree with the inverse that gw_eps_inv returns for the same eps, on two calls in a row
 of different sizes (the static workspace keeps the previous call's contents), and reject orders
@@ -66,3 +66,24 @@ def test_noalloc_rejects_orders_above_its_maximum():
     assert call_noalloc(ok, out) == gw.GW_OK
     torch.cuda.synchronize()
     assert float((out - 0.5 * torch.eye(512, dtype=torch.complex128, device="cuda:0")).abs().max()) <= 1e-15
+
+
+def test_noalloc_reports_a_bad_pivot_then_recovers():
+    """-I has a negative first pivot: the status word in the shared array says GW_E_NUMERIC.  The
+    next call, on 2I of another order, must clear that word and return GW_OK with 0.5 I."""
+    dev = torch.device("cuda:0")
+    neg = -torch.eye(40, dtype=torch.complex128, device=dev)
+    out = torch.empty_like(neg)
+    assert call_noalloc(neg, out) == gw.GW_E_NUMERIC
+    two = 2.0 * torch.eye(57, dtype=torch.complex128, device=dev)
+    out = torch.full_like(two, float("nan"))
+    assert call_noalloc(two, out) == gw.GW_OK
+    torch.cuda.synchronize()
+    assert float((out - 0.5 * torch.eye(57, dtype=torch.complex128, device=dev)).abs().max()) <= 1e-15
+
+
+def test_noalloc_rejects_host_pointers():
+    """Pointers that are not device memory of the current GPU are refused before any launch."""
+    host = torch.eye(8, dtype=torch.complex128)
+    out = torch.empty_like(host)
+    assert call_noalloc(host, out) == gw.GW_E_INVALID

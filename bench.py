@@ -10,6 +10,14 @@ oracle, and the rank-k update's fraction of the tensor-core peak.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gw|reference]
 
+The default run (one GPU) then measures the other three configurations and appends them to the
+same line: `split` (36^3, N_v = 64, N_c = 1000, BF16 hi+lo operands, 1e-4 target), `batch` (eight
+uneven systems, grids 16^3..32^3, one persistent launch, whole pass in one CUDA graph) and
+`learned` (24^3, N_c cut at 200 of 2000, the correction network trained on 64 systems).  Each
+carries its own time per step, algorithmic TFLOP/s, seconds per eps^-1, error against the FP64
+oracle and clock record.  `--no-extra` skips them; `--workload split|batch|learned` prints one of
+them as a line of its own.
+
 Under torchrun with N > 1 each rank runs the same workload on its own GPU (independent replicas;
 the path has no exchange step at this size), timing is the max over ranks and `value` the sum.
 """
@@ -54,6 +62,10 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default=None, help="default: bf16x3 for the split workload, else fp16x3")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the same-GPU precision comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the split, batch and learned configurations that the default run appends")
+    ap.add_argument("--extra-steps", type=int, default=3,
+                    help="timed steps of each appended configuration (after --warmup untimed ones)")
     ap.add_argument("--inv", choices=["cholesky", "newton_tc"], default=INV_METHOD,
                     help="eps^-1 method of the timed step")
     ap.add_argument("--epochs", type=int, default=6, help="training passes of the learned workload")
@@ -487,6 +499,16 @@ def run_gw(args):
         line["same_gpu_variants"] = variants
     if inverses:
         line["eps_inv_methods"] = inverses
+    if world == 1 and not args.no_extra and args.workload == "plain":
+        # the other configurations of the metric, each with its own clock record
+        for name, fn in (("split", section_split), ("batch", section_batch), ("learned", section_learned)):
+            t0 = time.perf_counter()
+            try:
+                line[name] = fn(args, args.extra_steps)
+            except Exception as e:   # a failing appended configuration must not hide the main line
+                line[name] = {"error": f"{type(e).__name__}: {e}"}
+            line[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -494,12 +516,87 @@ def run_gw(args):
     return 0
 
 
-def run_batch(args):
+def sample_G(ng, n=16):
+    """Indices of a spread of n sphere vectors, the head (0) and its first neighbour included."""
+    return np.unique(np.concatenate([[0, 1], np.linspace(0, ng - 1, n - 2).astype(int)]))
+
+
+def timed(stream, fn, steps):
+    """Mean CUDA-event time of fn over steps calls on the launching stream, in ms."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def section_split(args, steps):
+    """The split-precision configuration: 36^3 grid (N_r = 46656), N_v = 64, N_c = 1000 (k = 64000),
+    N_g = 2007, BF16 hi+lo operands under a 1e-4 target on P~, eps^-1 on the tensor cores.  Error on
+    the P~ entries of 16 spread G against Eq. (gpsaceP) in FP64, entry by entry."""
+    import torch
+    from paper_1810_07772_gb300 import gw
+    w = inputs.SPLIT
+    dims = (w.n,) * 3
+    prec = WORKLOAD_PRECISION["split"]
+    psi, E = inputs.make_workload_states(w)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    psi_d = torch.from_numpy(psi.astype(np.complex64)).to(dev)
+    ctx = gw.Context(0, stream)
+    ctx.set_error_target(ERROR_TARGET["split"])
+
+    def step():
+        ctx.load_states(psi_d, E, dims, w.nv)
+        ctx.build_P(prec)
+        ctx.P_to_G(w.gcut)
+        ctx.eps_inv(args.inv)
+
+    ctx.set_timing(True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_times()
+    l0 = ctx.stats()["kernel_launches"]
+    with ClockSampler(0) as clk:
+        ms = timed(stream, step, steps)
+    st = ctx.stats()
+    herk_ms = st["herk_ms_mean"]
+    flop = w.herk_flop()
+    ng = ctx.ng
+    PG = ctx.view("PG").cpu().numpy()
+    out = {"workload": w.name, "grid": [w.n] * 3, "N_r": w.nr, "nv": w.nv, "nc": w.nc, "k": w.k, "N_g": ng,
+           "precision": f"{prec}: BF16 hi+lo split, 3 products, FP32 accumulation; error target "
+                        f"{ERROR_TARGET['split']} on P~ picks the window",
+           "window": [int(st["window_chunks"]), int(st["flush_windows"])], "steps": steps, "warmup": args.warmup,
+           "ms_per_step": ms, "s_per_eps_inv": ms / 1e3, "tflops": flop / (ms * 1e-3) / 1e12,
+           "herk_flop_per_step": flop, "kernel_ms": ctx.times(),
+           "gpu_launches": int(st["kernel_launches"] - l0),
+           "herk": {"ms": herk_ms, "achieved_tflops": flop / (herk_ms * 1e-3) / 1e12 if herk_ms > 0 else None},
+           "clocks": clk.summary()}
+    ctx.close()
+    del psi_d
+    torch.cuda.empty_cache()
+    if not args.no_baseline:
+        from oracle import gw_oracle as O
+        g = O.sphere(dims, w.gcut)
+        sel = sample_G(len(g))
+        ref = O.P_gspace_entries(psi, E, w.nv, dims, g[sel])
+        out["err_vs_fp64"] = {"P_G_rel_frobenius_sampled": float(np.linalg.norm(PG[np.ix_(sel, sel)] - ref) /
+                                                                 np.linalg.norm(ref)),
+                              "sampled_G": int(len(sel)), "bar": ERROR_TARGET["split"],
+                              "oracle": "Eq. (gpsaceP) entry by entry in FP64 (oracle.P_gspace_entries)"}
+    return out
+
+
+def section_batch(args, steps):
     """The eight uneven systems (grids 16^3..32^3) as one batch: one persistent launch of the
     rank-k update for all of them, the whole pass replayed from a CUDA graph, window length from
-    the autotuner (error target 1e-6)."""
-    import tempfile
-
+    the autotuner (error target 1e-6).  Error per instance on the P~ entries of 16 spread G."""
     import torch
     from paper_1810_07772_gb300 import gw
     torch.cuda.set_device(0)
@@ -524,53 +621,70 @@ def run_batch(args):
     launches0 = ctxs[0].stats()["kernel_launches"]   # the library's launch counter is process-wide
     with ClockSampler(0) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.run(use_graph=True)
             herk.append(b.stats()["herk_ms"])
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     launches = int(ctxs[0].stats()["kernel_launches"] - launches0)  # graph replays count their kernels
-    # sampled rows of the largest system's P against the FP64 loop (oracle)
-    err = None
-    if not args.no_baseline:
-        from oracle import gw_oracle as O
-        w, (psi, E), c = ws[-1], states[-1], ctxs[-1]
-        rows = [0, w.nr // 2, w.nr - 1]
-        got = c.view("P")[rows].cpu().numpy()
-        ref = np.concatenate([O.P_rows_loop(psi, E, w.nv, r, r + 1) for r in rows])
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    peaks, src = load_peaks()
+    PGs = [c.view("PG").cpu().numpy() for c in ctxs]
     herk_ms = float(np.mean(herk))
-    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-    line = {"metric": METRIC, "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f16x3" if args.precision == "fp16x3" else "bf16x3",
-            "data": "synthetic",
-            "config": {"workload": "batch of 8 uneven systems: " + ", ".join(w.name for w in ws),
-                       "graph": "whole pass replayed from one CUDA graph",
-                       "window": tuned, "herk_flop_per_step": flop},
-            "roofline": {"bound": "tensor", "achieved": flop / (herk_ms * 1e-3) / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "frac": flop / (herk_ms * 1e-3) / 1e12 / peak, "traffic": None,
-                         "kernel": "herk16p_kernel (persistent, all instances)", "herk_ms": herk_ms},
-            "P_rows_rel_err_largest": err, "gpu_launches": launches, "clocks": clk.summary()}
-    print(json.dumps(line))
+    out = {"workload": "batch of 8 uneven systems: " + ", ".join(w.name for w in ws),
+           "instances": [{"name": w.name, "grid": [w.n] * 3, "nv": w.nv, "nc": w.nc, "N_g": int(P.shape[0])}
+                         for w, P in zip(ws, PGs)],
+           "graph": "whole pass replayed from one CUDA graph", "window": tuned, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": ms, "s_per_pass": ms / 1e3, "tflops": flop / (ms * 1e-3) / 1e12,
+           "herk_flop_per_step": flop, "gpu_launches": launches,
+           "herk": {"ms": herk_ms, "achieved_tflops": flop / (herk_ms * 1e-3) / 1e12,
+                    "kernel": "herk16p_kernel (persistent, all instances)"},
+           "clocks": clk.summary()}
     b.close()
     for c in ctxs:
         c.close()
+    torch.cuda.empty_cache()
+    if not args.no_baseline:
+        from oracle import gw_oracle as O
+        errs = []
+        for w, (psi, E), P in zip(ws, states, PGs):
+            dims = (w.n,) * 3
+            g = O.sphere(dims, w.gcut)
+            sel = sample_G(len(g))
+            ref = O.P_gspace_entries(psi, E, w.nv, dims, g[sel])
+            errs.append(float(np.linalg.norm(P[np.ix_(sel, sel)] - ref) / np.linalg.norm(ref)))
+        out["err_vs_fp64"] = {"P_G_rel_frobenius_sampled_per_instance": errs, "max": max(errs),
+                              "sampled_G_per_instance": 16, "bar": 1e-6,
+                              "oracle": "Eq. (gpsaceP) entry by entry in FP64 (oracle.P_gspace_entries)"}
+    return out
+
+
+def run_batch(args):
+    out = section_batch(args, args.steps)
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    line = {"metric": METRIC, "value": out["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16x3" if args.precision == "fp16x3" else "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": out["workload"], "graph": out["graph"], "window": out["window"],
+                       "herk_flop_per_step": out["herk_flop_per_step"]},
+            "roofline": {"bound": "tensor", "achieved": out["herk"]["achieved_tflops"], "peak": peak,
+                         "unit": "TFLOP/s", "frac": out["herk"]["achieved_tflops"] / peak, "traffic": None,
+                         "peak_source": f"{src} bf16_tflops_sustained (FP16:BF16 nominal ratio 1)",
+                         "kernel": out["herk"]["kernel"], "herk_ms": out["herk"]["ms"]},
+            "err_vs_fp64": out.get("err_vs_fp64"), "gpu_launches": out["gpu_launches"], "clocks": out["clocks"]}
+    print(json.dumps(line))
     return 0
 
 
-# flops of one training sample of the 10 -> 256 x 3 -> 2 network: forward, the three hidden-layer
+# flops of one training sample of the n_in -> 256 x 3 -> 2 network: forward, the three hidden-layer
 # deltas and the four weight gradients (with their bias columns)
 def mlp_sample_flop(n_in=10, h=256, n_out=2):
     fwd = 2 * (n_in * h + 2 * h * h + h * n_out)
     dh = 2 * (n_out * h + 2 * h * h)
     dw = 2 * (h * (n_in + 1) + 2 * h * (h + 1) + n_out * (h + 1))
     return fwd, fwd + dh + dw
-
-
-def run_learned(args):
+def section_learned(args, steps):
     """Learned truncation correction on the 24^3 workload: N_v = 32, the sum over unoccupied states
     cut at N_c = 200 of 2000, a 10 -> 256 x 3 -> 2 network trained on 64 seeded systems.  Times
     the learned form to eps^-1 against the plain full-N_c method on the same GPU, and reports the
@@ -669,6 +783,7 @@ def run_learned(args):
         ctx.eps_inv(args.inv)
 
     res = {}
+    nt = max(steps, 20)       # each step is a few ms
     with ClockSampler(0) as clk:
         for name, fn in (("learned", step_learned), ("full", step_full), ("full_rspace", step_full_rspace)):
             for _ in range(args.warmup):
@@ -676,21 +791,19 @@ def run_learned(args):
             torch.cuda.synchronize()
             l0 = ctx.stats()["kernel_launches"]
             ev[4].record(stream)
-            for _ in range(args.steps):
+            for _ in range(nt):
                 fn()
             ev[5].record(stream)
             torch.cuda.synchronize()
-            res[name] = {"ms": ev[4].elapsed_time(ev[5]) / args.steps,
+            res[name] = {"ms": ev[4].elapsed_time(ev[5]) / nt,
                          "launches": int(ctx.stats()["kernel_launches"] - l0)}
     ctx.close()
     net.close()
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
     peaks, peak_src = load_peaks()
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
-    line = {"metric": "seconds per eps^-1, learned truncation correction", "value": res["learned"]["ms"] / 1e3,
-            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["learned"]["ms"],
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16-weights/f32",
-            "data": "synthetic",
+    return {"s_per_eps_inv": res["learned"]["ms"] / 1e3, "steps": nt, "warmup": args.warmup,
+            "ms_per_step": res["learned"]["ms"], "dtype": "f16-weights/f32",
             "config": {"workload": f"grid24_nv32_nc{keep}_of_{nc_all}_learned", "grid": [n] * 3, "nv": nv,
                        "nc_keep": keep, "nc_all": nc_all, "gcut": gcut, "N_g": 691,
                        "network": "10 -> 256 -> 256 -> 256 -> 2, tanh, FP16 weights, FP32 accumulation",
@@ -721,6 +834,15 @@ def run_learned(args):
                                           "alu_peak": alu_peak,
                                           "alu_peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}},
             "gpu_launches": res["learned"]["launches"], "clocks": clk.summary()}
+
+
+def run_learned(args):
+    out = section_learned(args, args.steps)
+    line = {"metric": "seconds per eps^-1, learned truncation correction", "value": out["s_per_eps_inv"],
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": out["dtype"],
+            "data": "synthetic"}
+    line.update({k: v for k, v in out.items() if k not in line})
     print(json.dumps(line))
     return 0
 

@@ -57,6 +57,7 @@ import ctypes
 import os
 
 import numpy as np
+import scipy.fft
 
 HARTREE_EV = 27.211386245988
 
@@ -278,7 +279,9 @@ def matrix_elements(psi, nv, dims, gvec, v_list=None):
     out = []
     for v in v_list:
         rho = np.conj(psi[v])[None, :] * psi[nv:]
-        out.append(np.fft.fftn(rho.reshape(nc, n1, n2, n3), axes=(1, 2, 3)).reshape(nc, -1)[:, idx])
+        # the library FFT step (scipy's, the same unnormalised exp(-i...) convention as numpy's),
+        # on every host core: the 36^3 workload needs 64000 of these transforms
+        out.append(scipy.fft.fftn(rho.reshape(nc, n1, n2, n3), axes=(1, 2, 3), workers=-1).reshape(nc, -1)[:, idx])
     return np.concatenate(out, axis=0)
 
 

@@ -43,6 +43,7 @@ from paper_1810_07772_gb300 import inputs  # noqa: E402
 METRIC = "P-build TFLOP/s (4kN_r(N_r+1) per step, states resident -> eps^-1)"
 PRECISION = "fp16x3"
 INV_METHOD = "newton_tc"
+HERK_KERNEL = "single"   # kernel of the 16-bit rank-k update: one CTA per tile, or CTA pairs
 WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
              "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41),
              "split": inputs.SPLIT, "batch": None, "learned": None}
@@ -64,6 +65,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-variants", action="store_true", help="skip the same-GPU precision comparison")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the split, batch and learned configurations that the default run appends")
+    ap.add_argument("--herk-kernel", choices=["single", "pair"], default=HERK_KERNEL,
+                    help="kernel of the 16-bit rank-k update")
     ap.add_argument("--extra-steps", type=int, default=3,
                     help="timed steps of each appended configuration (after --warmup untimed ones)")
     ap.add_argument("--inv", choices=["cholesky", "newton_tc"], default=INV_METHOD,
@@ -232,14 +235,14 @@ def run_reference(args):
 # from a single-pass ncu capture of the 24^3 workload.  They describe the kernel as captured, so
 # they are reported only while its sources hash to the captured versions and the run uses the
 # captured configuration; otherwise the roofline line carries traffic = null.
-HERK_TRAFFIC = {"workload": "grid24_nv32_nc480", "precision": "fp16x3", "window": (3, 256), "bytes": 24.88e9,
-                "sha256_16": {"k_herk16.cu": "0636680f850ce601", "ptx.cuh": "9386666767dc8536"}}
+HERK_TRAFFIC = {"workload": "grid24_nv32_nc480", "precision": "fp16x3", "window": (3, 256), "kernel": "single",
+                "bytes": 24.23e9, "sha256_16": {"k_herk16.cu": "2a74ea049d26184d", "ptx.cuh": "3a48e8c0993f9661"}}
 
 
-def herk_traffic(workload_name, precision, window):
+def herk_traffic(workload_name, precision, window, kernel):
     import hashlib
     t = HERK_TRAFFIC
-    if (workload_name, precision, tuple(window)) != (t["workload"], t["precision"], t["window"]):
+    if (workload_name, precision, tuple(window), kernel) != (t["workload"], t["precision"], t["window"], t["kernel"]):
         return None
     for name, want in t["sha256_16"].items():
         path = os.path.join(ROOT, "paper_1810_07772_gb300", "csrc", name)
@@ -276,6 +279,7 @@ def run_gw(args):
     psi_d = torch.from_numpy(psi32).to(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = gw.Context(local, stream)
+    ctx.set_herk_kernel(args.herk_kernel)
     target = ERROR_TARGET.get(args.workload)
     if target:
         ctx.set_error_target(target)
@@ -434,14 +438,18 @@ def run_gw(args):
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))     # FP16 dense = BF16 dense rate
     achieved = flop_step / (herk_ms * 1e-3) / 1e12 if herk_ms > 0 else None
     # tensor-pipe work actually issued per 16-k chunk per tile: 3 MMAs of 2*128*256*16 and 6 of
-    # 2*128*128*16, the same as 6 of N = 256
+    # 2*128*128*16, the same as 6 of N = 256; a CTA pair issues 6 of M = 256, N = 256
     kpad = (w.k + 15) // 16 * 16
-    tensor_flop = st["herk_tiles"] * (kpad // 16) * 6 * 2.0 * 128 * 256 * 16
-    traffic = herk_traffic(w.name, args.precision, (int(st["window_chunks"]), int(st["flush_windows"])))
+    rows_per_tile = 256 if args.herk_kernel == "pair" else 128
+    tensor_flop = st["herk_tiles"] * (kpad // 16) * 6 * 2.0 * rows_per_tile * 256 * 16
+    traffic = herk_traffic(w.name, args.precision, (int(st["window_chunks"]), int(st["flush_windows"])),
+                           args.herk_kernel)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "kernel": "herk16_kernel<fp16> (tcgen05 kind::f16, 128x128 tiles, promoted TMEM windows)",
+                "kernel": ("herk16x2_kernel<fp16> (tcgen05 kind::f16 cta_group::2, CTA pairs, 256x128 tiles, "
+                           "promoted TMEM windows)" if args.herk_kernel == "pair" else
+                           "herk16_kernel<fp16> (tcgen05 kind::f16, 128x128 tiles, promoted TMEM windows)"),
                 "peak_source": f"{peak_src} bf16_tflops_sustained (FP16:BF16 nominal ratio 1)",
                 "tensor_pipe_frac": (tensor_flop / (herk_ms * 1e-3) / 1e12 / peak) if herk_ms > 0 else None,
                 "herk_ms": herk_ms}

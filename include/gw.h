@@ -197,10 +197,14 @@ typedef enum gw_buffer {
  * p = 0 and 2, stored as planes 0 and 1), the element (r, k) sits at float offset
  *   ((kc * nplanes + p) * nr_pad + (r / 8) * 8) * 8 + ((k % 8) / 4) * 32 + (r % 8) * 4 + k % 4.
  * For GW_PREC_FP32_SIMT it is [kpad][nr_pad] complex64 (f itself, r contiguous).
- * For GW_PREC_FP16X3 / GW_PREC_BF16X3 it is four 16-bit planes (FP16 or BF16 bit patterns; FP16
- * values carry the factor 2^e of the scale): p = 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo, k padded
- * to a multiple of 16: for kc = k / 16 the element (r, k) of plane p sits at 16-bit offset
- *   ((kc * 4 + p) * nr_pad + (r / 8) * 8) * 16 + ((k % 16) / 8) * 64 + (r % 8) * 8 + k % 8.
+ * For GW_PREC_FP16X3 / GW_PREC_BF16X3 it is 16-bit planes (FP16 or BF16 bit patterns; FP16
+ * values carry the factor 2^e of the scale), k padded to a multiple of 16, stored block by block:
+ * for kc = k / 16 and the 128-row block r / 128 the block's npl planes lie side by side, and the
+ * element (r, k) of plane slot p sits at 16-bit offset
+ *   ((kc * (nr_pad / 128) + r / 128) * npl + p) * 2048 + ((r % 128) / 8) * 128
+ *       + ((k % 16) / 8) * 64 + (r % 8) * 8 + k % 8.
+ * GW_HERK_SINGLE: npl = 4, slots Im hi, Re hi, Im lo, Re lo.  GW_HERK_PAIR: npl = 6, slots Im hi,
+ * Im lo, Re hi, Re lo, -Im hi, -Im lo (the last two the first two with the sign bit flipped).
  */
 GW_API gw_status gw_get_buffer(gw_ctx *ctx, int which, void **ptr, size_t *bytes);
 
@@ -225,8 +229,8 @@ GW_API gw_status gw_reset_times(gw_ctx *ctx);
  * process, [1] = Newton iterations of the last GW_INV_NEWTON inverse (FP16X3 steps for
  * GW_INV_NEWTON_TC and gw_zinv_tc), [2] = mean rank-k update
  * time in ms over the timed calls since gw_reset_times, [3] = number of those calls, [4] = the
- * FP16 scale exponent e of the last 16-bit build, [5] = rank-k update tiles, [6] and [7] = the
- * window and flush lengths of the 16-bit update.
+ * FP16 scale exponent e of the last 16-bit build, [5] = rank-k update tiles (CTA pairs for
+ * GW_HERK_PAIR), [6] and [7] = the window and flush lengths of the 16-bit update.
  */
 GW_API gw_status gw_get_stats(gw_ctx *ctx, double *stats8);
 
@@ -387,6 +391,18 @@ GW_API gw_status gw_newton_tc_report(gw_ctx *ctx, double *out4);
  * and flushes mean smaller accumulation error.
  */
 GW_API gw_status gw_set_herk_window(gw_ctx *ctx, int window_chunks, int flush_windows);
+
+/*
+ * Kernel of the 16-bit rank-k update of gw_build_P (Eq. Pstatic; the outer product of Sec. 4.1).
+ * Both compute the same numbers (the same products and accumulation order per element):
+ *   GW_HERK_PAIR    clusters of two CTAs share each tensor-core operation (2-SM MMAs,
+ *                   M = 256): each CTA holds 128 rows of A and half of B, 256 x 128 complex tiles;
+ *                   the operand holds six 16-bit planes per k chunk (the Im planes also negated)
+ *   GW_HERK_SINGLE  (default) one CTA per 128 x 128 complex tile, four planes per k chunk
+ * Takes effect at the next gw_build_P; GW_E_INVALID for another value.
+ */
+enum { GW_HERK_SINGLE = 0, GW_HERK_PAIR = 1 };
+GW_API gw_status gw_set_herk_kernel(gw_ctx *ctx, int kind);
 
 /*
  * Error target of the 16-bit rank-k update, as the relative Frobenius error of P~ against FP64

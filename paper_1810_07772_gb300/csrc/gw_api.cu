@@ -730,6 +730,14 @@ gw_status gw_set_herk_window(gw_ctx *h, int window_chunks, int flush_windows)
     return GW_OK;
 }
 
+gw_status gw_set_herk_kernel(gw_ctx *h, int kind)
+{
+    if (!h || (kind != GW_HERK_SINGLE && kind != GW_HERK_PAIR))
+        return GW_E_INVALID;
+    h->c.herk_kernel = kind;
+    return GW_OK;
+}
+
 gw_status gw_set_error_target(gw_ctx *h, double target)
 {
     if (!h || !(target >= 0.0) || !std::isfinite(target))
@@ -899,11 +907,14 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     }
     const int kchunk = p16 ? HERK16_KC : HERK_KC;
     c.kpad = ((c.k + kchunk - 1) / kchunk) * kchunk;
+    // CTA pairs take 256-row blocks of r: nr_pad is a multiple of 256 for every grid
+    const bool pair = p16 && c.herk_kernel == GW_HERK_PAIR && c.nr_pad % 256 == 0;
+    const int npl = pair ? HERK16_NPL_PAIR : HERK16_NPL;
     size_t Fbytes;
     if (precision == GW_PREC_FP32_SIMT)
         Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float2);
     else if (p16)
-        Fbytes = (size_t)c.kpad * c.nr_pad * 2 * HERK16_NPL;
+        Fbytes = (size_t)c.kpad * c.nr_pad * 2 * npl;
     else
         Fbytes = (size_t)c.kpad * c.nr_pad * sizeof(float) * (precision == GW_PREC_TF32X3 ? 4 : 2);
     GW_TRY(ensure(c, c.d_F, c.cap.F, Fbytes, "pair-density operand"));
@@ -914,9 +925,11 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     GW_TRY(ensure(c, c.d_P, c.cap.P, c.P_bytes, "P(r,r')"));
     c.P_ready = c.PG_ready = c.eps_ready = false;
 
-    const int tile_kind = p16 ? 1 : 0;
+    const int tile_kind = pair ? 2 : p16 ? 1 : 0;
     if (precision != GW_PREC_FP32_SIMT && (c.tiles_nr_pad != c.nr_pad || c.tiles_kind != tile_kind)) {
-        const auto t = p16 ? herk_tiles(c.nr_pad, HERK16_T, HERK16_T) : herk_tiles(c.nr_pad, HERK_BM, HERK_BN);
+        const auto t = pair  ? herk_pair_tiles(c.nr_pad)
+                       : p16 ? herk_tiles(c.nr_pad, HERK16_T, HERK16_T)
+                             : herk_tiles(c.nr_pad, HERK_BM, HERK_BN);
         GW_TRY(ensure(c, c.d_tiles, c.cap.tiles, t.size() * sizeof(int2), "tile list"));
         GW_CUDA(cudaMemcpy(c.d_tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice), "tile upload");
         c.n_tiles = static_cast<int>(t.size());
@@ -930,16 +943,23 @@ gw_status gw_build_P(gw_ctx *h, int precision, void *P_out)
     if (p16)
         GW_CUDA(launch_pair_density16(c.d_psiT, c.d_sw, c.sw_max, c.nr, c.nb, c.nv, c.nc, c.kpad, c.nr_pad,
                                       precision == GW_PREC_BF16X3, c.d_small, scale_exp,
-                                      reinterpret_cast<uint16_t *>(c.d_F), s),
+                                      reinterpret_cast<uint16_t *>(c.d_F), s, npl),
                 "pair densities (16-bit)");
     else
         GW_CUDA(launch_pair_density(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, c.kpad, c.nr_pad, precision, c.d_F, s),
                 "pair densities");
     c.F_prec = precision;
+    if (p16)
+        c.last_herk_kernel = pair ? GW_HERK_PAIR : GW_HERK_SINGLE;
     record(c, 1);
     if (precision == GW_PREC_FP32_SIMT) {
         GW_CUDA(launch_herk_simt(reinterpret_cast<float2 *>(c.d_F), c.kpad, c.nr, c.nr_pad, c.d_P, s),
                 "rank-k update (CUDA cores)");
+    } else if (pair) {
+        GW_CUDA(launch_herk16x2(reinterpret_cast<uint16_t *>(c.d_F), precision == GW_PREC_BF16X3, c.kpad, c.nr,
+                                c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, scale_exp, c.d_err, wait_ns, c.last_W,
+                                c.herk_L, s),
+                "rank-k update (tcgen05 CTA pairs, 16-bit)");
     } else if (p16) {
         GW_CUDA(launch_herk16(reinterpret_cast<uint16_t *>(c.d_F), precision == GW_PREC_BF16X3, c.kpad, c.nr,
                               c.nr_pad, c.d_tiles, c.n_tiles, c.d_P, scale_exp, c.d_err, wait_ns, c.last_W, c.herk_L,

@@ -160,6 +160,8 @@ struct Ctx {
     float sw_max = 0.f;             // max sqrt(2/(E_c - E_v)) (host, from the energies)
     unsigned *d_small = nullptr;    // [0] |f| bound bits, [1] FP16 scale exponent
     int herk_W = 3, herk_L = 256;   // 6.5e-7 against FP64 at 24^3; see gw_set_herk_window
+    int herk_kernel = GW_HERK_SINGLE; // r-space 16-bit update: one CTA per tile or CTA pairs
+    int last_herk_kernel = -1;      // the kernel of the last 16-bit r-space update
     double err_target = 0.0;        // > 0: the window comes from gw_set_error_target's rule
     int last_W = 3;                 // the window of the last 16-bit rank-k update
 
@@ -193,20 +195,46 @@ constexpr int HERK_BM = 128;
 constexpr int HERK_BN = 256;
 constexpr int HERK_KC = 8;
 constexpr int HERK16_KC = 16;
-// 16-bit operand planes per k chunk: Re hi, Re lo, Im hi, Im lo.
+// 16-bit operand planes.  For every 16-wide chunk of k and every 128-row block of r, the block's
+// planes are stored next to each other (4 KB each, canonical K-major core-matrix layout), so that
+// one bulk copy fetches all of a block's planes for a chunk:
+//   element (r, k) of plane slot p sits at 16-bit offset
+//   ((kc * nblk + r / 128) * npl + p) * 2048 + ((r % 128) / 8) * 128 + ((k % 16) / 8) * 64
+//       + (r % 8) * 8 + k % 8,          kc = k / 16, nblk = nr_pad / 128.
+// Four planes (one CTA per tile): Im hi, Re hi, Im lo, Re lo, so that [Im; Re] of each part is
+// one 256-row MMA operand.  Six planes (CTA pairs): Im hi, Im lo, Re hi, Re lo, -Im hi, -Im lo, so
+// that the even CTA's operand is slots 0..3 and the odd CTA's slots 2..5.
 constexpr int HERK16_NPL = 4;
+constexpr int HERK16_NPL_PAIR = 6;
+enum { P4_IH = 0, P4_RH = 1, P4_IL = 2, P4_RL = 3 };
+enum { P6_IH = 0, P6_IL = 1, P6_RH = 2, P6_RL = 3, P6_NIH = 4, P6_NIL = 5 };
+__host__ __device__ __forceinline__ size_t plane16_block(int kc, int blk, int nblk, int npl, int slot)
+{
+    return (((size_t)kc * nblk + blk) * npl + slot) * 2048;
+}
 constexpr int HERK16_T = 128;
 
 // k_herk16.cu, k_planes16.cu
 size_t herk16_smem_bytes();
+// npl: planes per k chunk written, HERK16_NPL or HERK16_NPL_PAIR
 cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
                                   int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int npl = HERK16_NPL);
 // splits > 1 (with a workspace P_parts of splits x nr^2 complex64): split-k over blockIdx.y, for
 // updates with too few tiles to fill the GPU; the partials are summed in a fixed order into P.
+// npl: planes per block and k chunk of F (HERK16_NPL); cps: k chunks per pipeline stage (1..3, 0 =
+// chosen from W)
 cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
-                          cudaStream_t s, int splits = 1, float2 *P_parts = nullptr);
+                          cudaStream_t s, int splits = 1, float2 *P_parts = nullptr, int npl = HERK16_NPL,
+                          int cps = 0);
+// k_herk16x2.cu: the same update on CTA pairs (2-SM MMAs, 256 x 128 complex tiles); F must hold
+// HERK16_NPL_PAIR planes per chunk and nr_pad must be a multiple of 256.
+size_t herk16x2_smem_bytes();
+std::vector<int2> herk_pair_tiles(int nr_pad);
+cudaError_t launch_herk16x2(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *pair_tiles,
+                            int n_pairs, float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
+                            cudaStream_t s);
 // 16-bit hi/lo operand planes of a complex64 matrix M[k][j] (k < rows, j < cols, row stride ld)
 // for launch_herk16 with nr = cols, nr_pad = cols_pad; the scale exponent comes from max |M|.
 cudaError_t launch_planes16_from_c64(const float2 *M, int rows, int cols, long ld, int kpad, int cols_pad, bool bf16,

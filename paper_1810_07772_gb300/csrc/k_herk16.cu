@@ -39,13 +39,12 @@ namespace {
 
 constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
 constexpr uint32_t PL = TM * KC16 * 2;  // 4 KB: one plane of one 128-row block
-constexpr uint32_t NPL = HERK16_NPL;    // global planes per chunk
-// stage: A planes Re hi, Re lo, Im hi, Im lo of the row block (4 PL), then the B regions
-// [Im | Re] of the hi part and of the lo part (4 PL)
+// stage: the A block's planes Im hi, Re hi, Im lo, Re lo (4 PL, one bulk copy), then the B
+// block's in the same order (one bulk copy): [Im | Re] of the hi part and of the lo part
 constexpr uint32_t B_OFF = 4 * PL;
-constexpr uint32_t STAGE_BYTES = 8 * PL;  // 32 KB
-constexpr int STAGES = 6;
-constexpr uint32_t PIPE_BYTES = STAGES * STAGE_BYTES;  // 192 KB
+constexpr uint32_t CHUNK_BYTES = 8 * PL;  // 32 KB: one 16-k chunk of A and B
+constexpr int PIPE_CHUNKS = 6;            // chunks buffered in shared memory
+constexpr uint32_t PIPE_BYTES = PIPE_CHUNKS * CHUNK_BYTES;  // 192 KB
 constexpr uint32_t LBO = 128, SBO = 256;
 constexpr int EPI_PITCH = 129;
 static_assert(PIPE_BYTES >= TM * EPI_PITCH * 8, "epilogue staging must fit");
@@ -60,12 +59,17 @@ __device__ __forceinline__ void named_bar(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-template <bool BF16>
+// CPS: chunks per pipeline stage (1, 2 or 3): fewer, larger stages cost fewer barrier round trips
+// per byte; with CPS > 1 every window has its own commit.
+template <bool BF16, int CPS>
 __global__ void __launch_bounds__(NTHREADS, 1)
     herk16_kernel(const uint16_t *__restrict__ F, int kpad, int nr, int nr_pad, const int2 *__restrict__ tiles,
                   float2 *__restrict__ P, const int *__restrict__ scale_exp, uint32_t *err, uint64_t wait_ns, int W,
-                  int L, int split_chunks, long long P_split)
+                  int L, int split_chunks, long long P_split, int npl)
 {
+    constexpr int STAGES = PIPE_CHUNKS / CPS;
+    constexpr uint32_t STAGE_BYTES = CPS * CHUNK_BYTES;
+    static_assert(STAGES * CPS == PIPE_CHUNKS, "stages must tile the pipeline");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + PIPE_BYTES);
     uint64_t *empty = full + STAGES;
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // partial P at P + y P_split (the launcher sizes the splits so that none is empty)
     const int kc_begin = blockIdx.y * split_chunks;
     const int nkc = max(0, min(split_chunks, kpad / KC16 - kc_begin));
-    F += (size_t)kc_begin * NPL * nr_pad * KC16;
+    F += (size_t)kc_begin * npl * nr_pad * KC16;  // whole chunks: the same stride in the block layout
     P += (size_t)blockIdx.y * P_split;
     const int nwin = (nkc + W - 1) / W;
 
@@ -111,12 +115,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (warp == PRODUCER_WARP) {
         if (lane == 0) {
-            const size_t per_chunk = (size_t)nr_pad * KC16;  // 16-bit elements per (chunk, plane)
-            const size_t a_off = (size_t)tile.x * TM * KC16, b_off = (size_t)tile.y * TN * KC16;
-            for (int kc = 0; kc < nkc; ++kc) {
-                const int s = kc % STAGES;
-                const uint32_t ph = (kc / STAGES) & 1;
-                if (kc >= STAGES && !mbar_wait(&empty[s], ph ^ 1, wait_ns)) {
+            // every block's four planes (Im hi, Re hi, Im lo, Re lo) are contiguous: one 16 KB copy
+            // for the A rows and one for the B rows per chunk
+            const int nblk = nr_pad / TM;
+            const int nst = (nkc + CPS - 1) / CPS;
+            for (int si = 0; si < nst; ++si) {
+                const int s = si % STAGES;
+                const uint32_t ph = (si / STAGES) & 1;
+                if (si >= STAGES && !mbar_wait(&empty[s], ph ^ 1, wait_ns)) {
                     record_error(err, GW_E_TIMEOUT, SITE_HERK_PRODUCER, blockIdx.x);
                     *abort_flag = 1;
                     break;
@@ -124,18 +130,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (*abort_flag)
                     break;
                 uint8_t *st = smem + s * STAGE_BYTES;
-                const uint16_t *chunk = F + (size_t)kc * NPL * per_chunk;
-                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    bulk_g2s(st + p * PL, chunk + p * per_chunk + a_off, PL, &full[s]);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {  // hi, lo: [Im | Re]
-                    uint8_t *bb = st + B_OFF + h * 2 * PL;
-                    bulk_g2s(bb, chunk + (2 + h) * per_chunk + b_off, PL, &full[s]);
-                    bulk_g2s(bb + PL, chunk + (0 + h) * per_chunk + b_off, PL, &full[s]);
+                const int c0 = si * CPS, nch = min(CPS, nkc - c0);
+                mbar_arrive_expect_tx(&full[s], nch * CHUNK_BYTES);
+                for (int j = 0; j < nch; ++j) {
+                    bulk_g2s(st + j * CHUNK_BYTES, F + plane16_block(c0 + j, tile.x, nblk, npl, 0), 4 * PL, &full[s]);
+                    bulk_g2s(st + j * CHUNK_BYTES + B_OFF, F + plane16_block(c0 + j, tile.y, nblk, npl, 0), 4 * PL,
+                             &full[s]);
                 }
-                *n_issued = kc + 1;
+                *n_issued = si + 1;
             }
         }
         __syncwarp();
@@ -158,18 +160,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t d = tmem + b * 256;  // Re columns d .. d + 127, Im d + 128 .. d + 255
                 const int kend = min(nkc, kc + W);
                 for (int c = 0; kc < kend; ++kc, ++c) {
-                    const int s = kc % STAGES;
-                    if (!mbar_wait(&full[s], (kc / STAGES) & 1, wait_ns)) {
+                    const int si = kc / CPS, s = si % STAGES;
+                    if (kc % CPS == 0 && !mbar_wait(&full[s], (si / STAGES) & 1, wait_ns)) {
                         record_error(err, GW_E_TIMEOUT, SITE_HERK_MMA, blockIdx.x);
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = sbase + s * STAGE_BYTES;
-                    const uint64_t a_rh = smem_desc(st, LBO, SBO), a_rl = smem_desc(st + PL, LBO, SBO);
-                    const uint64_t a_ih = smem_desc(st + 2 * PL, LBO, SBO), a_il = smem_desc(st + 3 * PL, LBO, SBO);
-                    // B regions per part: [Bi | Br]; from Bi the 256 rows are [Bi; Br]
+                    const uint32_t st = sbase + s * STAGE_BYTES + (kc % CPS) * CHUNK_BYTES;
+                    // both operands staged as Im hi, Re hi, Im lo, Re lo; from Bi the 256 rows are [Bi; Br]
+                    const uint64_t a_ih = smem_desc(st, LBO, SBO), a_rh = smem_desc(st + PL, LBO, SBO);
+                    const uint64_t a_il = smem_desc(st + 2 * PL, LBO, SBO), a_rl = smem_desc(st + 3 * PL, LBO, SBO);
                     const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO), b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
                     const uint64_t b_il = smem_desc(st + B_OFF + 2 * PL, LBO, SBO);
                     const uint64_t b_rl = smem_desc(st + B_OFF + 3 * PL, LBO, SBO);
@@ -183,14 +185,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mma_f16(d + 128, a_rh, b_ih, ID1N, 1);  // Im -= Ar Bi
                     mma_f16(d + 128, a_rh, b_il, ID1N, 1);
                     mma_f16(d + 128, a_rl, b_ih, ID1N, 1);
-                    mma_commit(&empty[s]);
-                    *n_consumed = kc + 1;
+                    if (kc % CPS == CPS - 1 || kc == nkc - 1) {
+                        mma_commit(&empty[s]);
+                        *n_consumed = si + 1;
+                    }
                 }
                 // With W < STAGES the commit to the empty barrier of the window's last chunk already
                 // tells the promotion warps that the window is complete (a commit arrives once every
                 // earlier tcgen05 op has finished), and each such commit costs the tensor pipe ~100
                 // clocks; a separate window commit is kept only for W >= STAGES (see below).
-                if (ok && W >= STAGES)
+                if (ok && (CPS > 1 || W >= STAGES))
                     mma_commit(&accf[b]);
             }
             mma_commit(done);  // arrives once every MMA issued above has completed
@@ -226,8 +230,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // lies in window win + 2 or later, whose MMAs wait for this promotion), so its parity is
                 // unambiguous.  With W >= STAGES the window has its own commit on accf[b].
                 const int kc_last = min(nkc, (win + 1) * W) - 1;
-                uint64_t *wbar = W < STAGES ? &empty[kc_last % STAGES] : &accf[b];
-                const uint32_t wpar = W < STAGES ? (uint32_t)((kc_last / STAGES) & 1) : (uint32_t)((win >> 1) & 1);
+                const bool own = CPS > 1 || W >= STAGES;  // the window has its own commit
+                uint64_t *wbar = own ? &accf[b] : &empty[kc_last % STAGES];
+                const uint32_t wpar = own ? (uint32_t)((win >> 1) & 1) : (uint32_t)((kc_last / STAGES) & 1);
                 // warp-uniform outcome: the TMEM loads below are warp-collective
                 if (!__all_sync(0xffffffffu, mbar_wait(wbar, wpar, wait_ns))) {
                     if (lane == 0)
@@ -358,9 +363,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         if (!mbar_wait(done, 0, DRAIN_NS))
             record_error(err, GW_E_TIMEOUT, SITE_HERK_DRAIN, blockIdx.x);
-        const int issued = *n_issued, consumed = *n_consumed;
-        for (int kc = consumed; kc < issued; ++kc)
-            if (!mbar_wait(&full[kc % STAGES], (kc / STAGES) & 1, DRAIN_NS)) {
+        const int issued = *n_issued, consumed = *n_consumed;  // stages
+        for (int si = consumed; si < issued; ++si)
+            if (!mbar_wait(&full[si % STAGES], (si / STAGES) & 1, DRAIN_NS)) {
                 record_error(err, GW_E_TIMEOUT, SITE_HERK_DRAIN, blockIdx.x);
                 break;
             }
@@ -402,12 +407,32 @@ __global__ void sum_parts_kernel(const float2 *__restrict__ parts, int nparts, s
     }
 }
 
+template <bool BF16, int CPS>
+cudaError_t launch_herk16_t(dim3 grid, cudaStream_t s, const uint16_t *F, int kpad, int nr, int nr_pad,
+                            const int2 *tiles, float2 *dst, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W,
+                            int L, int per, long long pstride, int npl)
+{
+    cudaError_t e = cudaFuncSetAttribute(herk16_kernel<BF16, CPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM);
+    if (e != cudaSuccess)
+        return e;
+    herk16_kernel<BF16, CPS><<<grid, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W,
+                                                          L, per, pstride, npl);
+    return cudaSuccess;
+}
+
 cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr_pad, const int2 *tiles, int n_tiles,
                           float2 *P, const int *scale_exp, uint32_t *err, uint64_t wait_ns, int W, int L,
-                          cudaStream_t s, int splits, float2 *P_parts)
+                          cudaStream_t s, int splits, float2 *P_parts, int npl, int cps)
 {
     if (n_tiles <= 0)
         return cudaSuccess;
+    // Windows of PIPE_CHUNKS or more chunks take their own commit anyway; for them three-chunk
+    // stages measured 4 % faster at 24^3 (W = 16: 21.7 against 22.6 ms), for W = 3 within 1 %.
+    if (cps == 0)
+        cps = W >= PIPE_CHUNKS ? 3 : 1;
+    if (cps != 1 && cps != 2 && cps != 3)
+        return cudaErrorInvalidValue;
     const int nkc = kpad / KC16;
     if (splits < 1 || !P_parts || nkc < 2)
         splits = 1;
@@ -417,19 +442,15 @@ cudaError_t launch_herk16(const uint16_t *F, bool bf16, int kpad, int nr, int nr
     const long long pstride = (long long)nr * nr;
     cudaError_t e;
     dim3 grid(n_tiles, splits);
-    if (bf16) {
-        e = cudaFuncSetAttribute(herk16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        if (e != cudaSuccess)
-            return e;
-        herk16_kernel<true><<<grid, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W, L,
-                                                         per, pstride);
-    } else {
-        e = cudaFuncSetAttribute(herk16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        if (e != cudaSuccess)
-            return e;
-        herk16_kernel<false><<<grid, NTHREADS, SMEM, s>>>(F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W,
-                                                          L, per, pstride);
-    }
+#define GW_HERK16_LAUNCH(B, C) \
+    launch_herk16_t<B, C>(grid, s, F, kpad, nr, nr_pad, tiles, dst, scale_exp, err, wait_ns, W, L, per, pstride, npl)
+    if (bf16)
+        e = cps == 1 ? GW_HERK16_LAUNCH(true, 1) : cps == 2 ? GW_HERK16_LAUNCH(true, 2) : GW_HERK16_LAUNCH(true, 3);
+    else
+        e = cps == 1 ? GW_HERK16_LAUNCH(false, 1) : cps == 2 ? GW_HERK16_LAUNCH(false, 2) : GW_HERK16_LAUNCH(false, 3);
+#undef GW_HERK16_LAUNCH
+    if (e != cudaSuccess)
+        return e;
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess || splits == 1)
         return e;

@@ -22,7 +22,8 @@ namespace {
 constexpr int TM = 128, TN = 128, KC16 = HERK16_KC;
 constexpr uint32_t PL = TM * KC16 * 2;  // 4 KB: one plane of one 128-row block
 constexpr uint32_t NPL = HERK16_NPL;
-// stage as in herk16_kernel: A planes Re hi, Re lo, Im hi, Im lo, then B regions [Im | Re] of the
+// stage as in herk16_kernel: the A block's planes Im hi, Re hi, Im lo, Re lo (one bulk copy), then
+// the B block's in the same order, i.e. regions [Im | Re] of the
 // hi part and of the lo part, so one N = 256 MMA from A = Im fills the Re and Im columns of a window
 constexpr uint32_t B_OFF = 4 * PL;
 constexpr uint32_t STAGE_BYTES = 8 * PL;  // 32 KB
@@ -104,8 +105,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int4 tl = tiles[t];
                 const HerkJob jb = jobs[tl.x];
                 const int nkc = jb.kpad / KC16;
-                const size_t per_chunk = (size_t)jb.nr_pad * KC16;
-                const size_t a_off = (size_t)tl.y * TM * KC16, b_off = (size_t)tl.z * TN * KC16;
+                const int nblk = jb.nr_pad / TM;  // block layout: one 16 KB copy per operand block
                 for (int kc = 0; kc < nkc; ++kc, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -120,17 +120,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         break;
                     }
                     uint8_t *st = smem + s * STAGE_BYTES;
-                    const uint16_t *chunk = jb.F + (size_t)kc * NPL * per_chunk;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        bulk_g2s(st + p * PL, chunk + p * per_chunk + a_off, PL, &full[s]);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint8_t *bb = st + B_OFF + h * 2 * PL;
-                        bulk_g2s(bb, chunk + (2 + h) * per_chunk + b_off, PL, &full[s]);
-                        bulk_g2s(bb + PL, chunk + (0 + h) * per_chunk + b_off, PL, &full[s]);
-                    }
+                    bulk_g2s(st, jb.F + plane16_block(kc, tl.y, nblk, NPL, 0), 4 * PL, &full[s]);
+                    bulk_g2s(st + B_OFF, jb.F + plane16_block(kc, tl.z, nblk, NPL, 0), 4 * PL, &full[s]);
                     *n_issued = g + 1;
                 }
             }
@@ -170,9 +162,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                         tc_fence_after();
                         const uint32_t st = sbase + s * STAGE_BYTES;
-                        const uint64_t a_rh = smem_desc(st, LBO, SBO), a_rl = smem_desc(st + PL, LBO, SBO);
-                        const uint64_t a_ih = smem_desc(st + 2 * PL, LBO, SBO);
-                        const uint64_t a_il = smem_desc(st + 3 * PL, LBO, SBO);
+                        const uint64_t a_ih = smem_desc(st, LBO, SBO), a_rh = smem_desc(st + PL, LBO, SBO);
+                        const uint64_t a_il = smem_desc(st + 2 * PL, LBO, SBO);
+                        const uint64_t a_rl = smem_desc(st + 3 * PL, LBO, SBO);
                         const uint64_t b_ih = smem_desc(st + B_OFF, LBO, SBO);
                         const uint64_t b_rh = smem_desc(st + B_OFF + PL, LBO, SBO);
                         const uint64_t b_il = smem_desc(st + B_OFF + 2 * PL, LBO, SBO);

@@ -102,7 +102,7 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_
 template <bool BF16>
 __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__restrict__ psiT,
                                                              const float *__restrict__ sw, int nr, int nb, int nv,
-                                                             int nc, int kpad, int nr_pad,
+                                                             int nc, int kpad, int nr_pad, int npl,
                                                              const int *__restrict__ scale_exp,
                                                              uint16_t *__restrict__ F)
 {
@@ -124,8 +124,11 @@ __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__res
         }
     }
     __syncthreads();
-    const int per_chunk = nr_pad * KC16;
-    uint16_t *Fc = F + (size_t)kc * NPL * per_chunk;
+    const int per_chunk = nr_pad * KC16, nblk = nr_pad / 128;
+    // plane slots: four planes Im hi, Re hi, Im lo, Re lo; six add -Im hi, -Im lo (Im hi, Im lo,
+    // Re hi, Re lo first)
+    const int s_rh = npl == 6 ? P6_RH : P4_RH, s_rl = npl == 6 ? P6_RL : P4_RL;
+    const int s_ih = npl == 6 ? P6_IH : P4_IH, s_il = npl == 6 ? P6_IL : P4_IL;
     for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < per_chunk; rem += gridDim.x * blockDim.x) {
         const int r = (rem >> 7) * 8 + ((rem & 63) >> 3);  // 8-row group, row in the group
         const int kk = ((rem & 127) >> 6) * 8 + (rem & 7);  // 16-byte core matrix along k, element
@@ -138,10 +141,15 @@ __global__ void __launch_bounds__(256) pair_density16_kernel(const float2 *__res
             fi = fmaf(a.x, b.y, -a.y * b.x) * w;
         }
         const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi), il = to16<BF16>(fi - from16<BF16>(ih));
-        Fc[rem] = rh;
-        Fc[per_chunk + rem] = to16<BF16>(fr - from16<BF16>(rh));
-        Fc[2 * per_chunk + rem] = ih;
-        Fc[3 * per_chunk + rem] = il;
+        uint16_t *Fb = F + plane16_block(kc, rem >> 11, nblk, npl, 0) + (rem & 2047);
+        Fb[s_rh * 2048] = rh;
+        Fb[s_rl * 2048] = to16<BF16>(fr - from16<BF16>(rh));
+        Fb[s_ih * 2048] = ih;
+        Fb[s_il * 2048] = il;
+        if (npl == 6) {  // the negated Im planes: the sign bit flipped, exact for FP16 and BF16
+            Fb[P6_NIH * 2048] = ih ^ 0x8000u;
+            Fb[P6_NIL * 2048] = il ^ 0x8000u;
+        }
     }
 }
 
@@ -156,7 +164,7 @@ constexpr int PD_LDP_PAD = 2;  // row pitch nb + 2 float2: lanes on 8 rows sprea
 template <bool BF16>
 __global__ void __launch_bounds__(256) pair_density16_rows_kernel(const float2 *__restrict__ psiT,
                                                                   const float *__restrict__ sw, int nr, int nb,
-                                                                  int nv, int nc, int kpad, int nr_pad,
+                                                                  int nv, int nc, int kpad, int nr_pad, int npl,
                                                                   const int *__restrict__ scale_exp,
                                                                   uint16_t *__restrict__ F)
 {
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(256) pair_density16_rows_kernel(const float2 *
     }
     __syncthreads();
     const float s = ldexpf(1.0f, *scale_exp);
-    const int nk = nv * nc, nchunks = kpad / KC16, per_chunk = nr_pad * KC16;
+    const int nk = nv * nc, nchunks = kpad / KC16, nblk = nr_pad / 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rem = 4 * lane;                                    // element offset in the group's 128
     const int r8 = (rem & 63) >> 3, kk0 = ((rem & 127) >> 6) * 8 + (rem & 7);
@@ -208,10 +216,18 @@ __global__ void __launch_bounds__(256) pair_density16_rows_kernel(const float2 *
             split2<BF16>(fr[i], fr[i + 1], p[0][j], p[1][j]);
             split2<BF16>(fi[i], fi[i + 1], p[2][j], p[3][j]);
         }
-        uint16_t *dst = F + (size_t)kc * NPL * per_chunk + (size_t)grp * 128 + rem;
+        // the group's 128 elements in each plane of its 128-row block (slots as in
+        // pair_density16_kernel)
+        uint16_t *dst = F + plane16_block(kc, grp >> 4, nblk, npl, 0) + (size_t)(grp & 15) * 128 + rem;
+        const int slot[4] = {npl == 6 ? P6_RH : P4_RH, npl == 6 ? P6_RL : P4_RL, npl == 6 ? P6_IH : P4_IH,
+                             npl == 6 ? P6_IL : P4_IL};
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint2 *>(dst + (size_t)q * per_chunk) = make_uint2(p[q][0], p[q][1]);
+            *reinterpret_cast<uint2 *>(dst + (size_t)slot[q] * 2048) = make_uint2(p[q][0], p[q][1]);
+        if (npl == 6) {  // the negated Im planes: the sign bits flipped, exact for FP16 and BF16
+            *reinterpret_cast<uint2 *>(dst + (size_t)P6_NIH * 2048) = make_uint2(p[2][0] ^ 0x80008000u, p[2][1] ^ 0x80008000u);
+            *reinterpret_cast<uint2 *>(dst + (size_t)P6_NIL * 2048) = make_uint2(p[3][0] ^ 0x80008000u, p[3][1] ^ 0x80008000u);
+        }
     }
 }
 
@@ -253,11 +269,11 @@ __global__ void planes16_from_c64_kernel(const float2 *__restrict__ M, int rows,
             fi = z.y * s;
         }
         const uint16_t rh = to16<BF16>(fr), ih = to16<BF16>(fi), il = to16<BF16>(fi - from16<BF16>(ih));
-        uint16_t *base = F + kc * NPL * per_chunk + rem;
-        base[0] = rh;
-        base[per_chunk] = to16<BF16>(fr - from16<BF16>(rh));
-        base[2 * per_chunk] = ih;
-        base[3 * per_chunk] = il;
+        uint16_t *base = F + plane16_block((int)kc, rem >> 11, cols_pad / 128, NPL, 0) + (rem & 2047);
+        base[P4_RH * 2048] = rh;
+        base[P4_RL * 2048] = to16<BF16>(fr - from16<BF16>(rh));
+        base[P4_IH * 2048] = ih;
+        base[P4_IL * 2048] = il;
     }
 }
 
@@ -273,8 +289,10 @@ int grid_for(size_t n)
 
 cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_max, int nr, int nb, int nv, int nc,
                                   int kpad, int nr_pad, bool bf16, unsigned *bound_bits, int *scale_exp, uint16_t *F,
-                                  cudaStream_t s)
+                                  cudaStream_t s, int npl)
 {
+    if (npl != 4 && npl != 6)
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(bound_bits, 0, sizeof(unsigned), s);
     if (e != cudaSuccess)
         return e;
@@ -297,18 +315,18 @@ cudaError_t launch_pair_density16(const float2 *psiT, const float *sw, float sw_
             return e;
         if (bf16)
             pair_density16_rows_kernel<true><<<g2, 256, rows_smem, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad,
-                                                                        scale_exp, F);
+                                                                        npl, scale_exp, F);
         else
             pair_density16_rows_kernel<false><<<g2, 256, rows_smem, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad,
-                                                                         scale_exp, F);
+                                                                         npl, scale_exp, F);
         count_launches(1);
         return cudaGetLastError();
     }
     dim3 grid(std::max(1, std::min((per_chunk + 255) / 256, (152 * 16 + nchunks - 1) / nchunks)), nchunks);
     if (bf16)
-        pair_density16_kernel<true><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+        pair_density16_kernel<true><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, npl, scale_exp, F);
     else
-        pair_density16_kernel<false><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, scale_exp, F);
+        pair_density16_kernel<false><<<grid, 256, 0, s>>>(psiT, sw, nr, nb, nv, nc, kpad, nr_pad, npl, scale_exp, F);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -19,6 +19,7 @@ LIB_PATH = _build.LIB_PATH
 GW_OK, GW_E_INVALID, GW_E_NOMEM, GW_E_CUDA, GW_E_NOT_READY, GW_E_NUMERIC, GW_E_TIMEOUT, GW_E_UNSUPPORTED = range(8)
 PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
 INV_METHOD = {"cholesky": 0, "newton": 1, "newton_tc": 2}
+HERK_KERNEL = {"single": 0, "pair": 1}
 ZGEMM_MODE = {"fp16x3": 0, "slices": 1}
 GW_C64, GW_C128 = 0, 1
 BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5, "psiT": 6}
@@ -50,6 +51,7 @@ SIGNATURES = {
     "gw_set_wait_limit": (_i, [_vp, _d]),
     "gw_set_q": (_i, [_vp, _c.POINTER(_d)]),
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
+    "gw_set_herk_kernel": (_i, [_vp, _i]),
     "gw_set_error_target": (_i, [_vp, ctypes.c_double]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
@@ -321,6 +323,11 @@ class Context:
 
     def set_herk_window(self, window_chunks, flush_windows):
         self._check(lib().gw_set_herk_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def set_herk_kernel(self, kind):
+        """Kernel of the 16-bit r-space update: "single" (one CTA per tile, the default) or "pair"
+        (CTA pairs sharing 2-SM MMAs) (gw_set_herk_kernel)."""
+        self._check(lib().gw_set_herk_kernel(self._h, HERK_KERNEL[kind] if isinstance(kind, str) else int(kind)))
 
     def set_error_target(self, target):
         """P~ error target of the 16-bit update; the window follows from it (gw_set_error_target)."""

@@ -106,19 +106,23 @@ def _decode_tf32(F, nr_pad, nr, k):
     return (pl[0] + pl[1]) + 1j * (pl[2] + pl[3]), F
 
 
-def _decode_16(F, nr_pad, nr, k, bf16):
+def _decode_16(F, nr_pad, nr, k, bf16, npl=4):
+    """Block layout of gw.h: per 16-k chunk and 128-row block, the block's planes side by side
+    (four: Im hi, Re hi, Im lo, Re lo; six: Im hi, Im lo, Re hi, Re lo, -Im hi, -Im lo)."""
     u = F.view(np.uint16)
     rr = np.arange(nr)[:, None]
     kk = np.arange(k)[None, :]
-    off = (((kk // 16) * 4) * nr_pad + (rr // 8) * 8) * 16 + ((kk % 16) // 8) * 64 + (rr % 8) * 8 + kk % 8
-    per = nr_pad * 16
+    nblk = nr_pad // 128
+    blk = ((kk // 16) * nblk + rr // 128) * npl
+    off = ((rr % 128) // 8) * 128 + ((kk % 16) // 8) * 64 + (rr % 8) * 8 + kk % 8
     if bf16:
         val = lambda x: (x.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     else:
         val = lambda x: x.view(np.float16).astype(np.float64)
-    pl = [val(u[off + p * per]) for p in range(4)]
-    assert len(u) // (per * ((k + 15) // 16)) == 4
-    return (pl[0] + pl[1]) + 1j * (pl[2] + pl[3]), u
+    slots = {"rh": 1, "rl": 3, "ih": 0, "il": 2} if npl == 4 else {"rh": 2, "rl": 3, "ih": 0, "il": 1}
+    pl = {n: val(u[(blk + p) * 2048 + off]) for n, p in slots.items()}
+    assert len(u) // (nr_pad * 16 * ((k + 15) // 16)) == npl
+    return (pl["rh"] + pl["rl"]) + 1j * (pl["ih"] + pl["il"]), u
 
 
 def test_small_operand_planes(small):

@@ -20,6 +20,8 @@ units with e^2 = 1:
   the grid (`states_from_g`), and the (1/N_k) sum over k-points of P^q (`P_gspace_ksum`).
 * Sec. 5.2, Eqs. (eigdecomp), (ppform), (ppfreq) -- the plasmon-pole model: S = sqrt(V)(eps^-1 - I)
   sqrt(V), its eigenpairs, the Johnson-sum-rule frequencies and S(omega) (`pp_*`).
+* Sec. 2 (band truncation of the sum over c in Eq. Pstatic) -- the closure estimate of the omitted
+  part from the loaded states and the omitted states' energies (`closure_weights`, `P_closure`).
 
 Readings of the paper taken here (where it is silent or inconsistent):
 
@@ -50,6 +52,10 @@ Readings of the paper taken here (where it is silent or inconsistent):
    density is rho(G) = sum_r e^{-iG.r} rho(r) with rho(r) = 2 sum_v |psi_v(r)|^2 per grid point, so
    rho(0) = 2 N_v is the number of electrons per cell; with it a single-pole eps^-1 = 1 - wp^2/w~^2
    (wp^2 = 4 pi rho(0)/Omega) returns omega = w~ exactly.  g - g' is taken modulo the grid.
+10. Band truncation: the paper names the cut of the sum over c as a cost and gives no correction.
+   The estimate of the omitted part (`P_closure`) takes the omitted states as unknown members of
+   the complement of the loaded ones, each with mean projector (I - Pi)/(N_r - n_in), and uses
+   their energies exactly; it is the mean of the omitted sum over such states.
 """
 from __future__ import annotations
 
@@ -320,6 +326,53 @@ def P_gspace_entries(psi, E_eV, nv, dims, gsel):
         d = 2.0 / (E[v] - E[nv:])
         out += (M * d[None, :]) @ np.conj(M.T)
     return out
+
+
+# ----------------------------------------------------------------------------- band truncation
+
+
+def closure_weights(E_in_eV, nv, E_omit_eV):
+    """W_v = sum over the omitted unoccupied states c of 2 / (E_v - E_c), in 1/Hartree (negative):
+    the energy factor of Eq. (Pstatic) summed over the states beyond the cut, one per occupied v."""
+    E = to_hartree(E_in_eV)
+    Eo = to_hartree(E_omit_eV)
+    return np.sum(2.0 / (E[:nv, None] - Eo[None, :]), axis=1)
+
+
+def P_closure(psi_in, E_in_eV, nv, E_omit_eV, dims, gvec):
+    """Estimate of the omitted part of Eq. (gpsaceP) when the sum over c stops after the loaded
+    states psi_in (occupied first) and only the energies E_omit of the states beyond the cut are
+    known.  Written from the closure relation: on the grid sum_n psi_n(r) conj(psi_n(r')) =
+    delta_rr' over a complete set, so the omitted states span the complement of the loaded ones,
+    and for states drawn without preference inside that complement the mean of
+    psi_c(r) conj(psi_c(r')) is (delta_rr' - Pi(r, r')) / (N_r - n_in), Pi = sum_{n loaded}
+    psi_n psi_n^H.  Inserted into Eq. (Pstatic) (reading: the omitted c enter only through this
+    mean and their known energies):
+        dP(r, r') = sum_v W_v / (N_r - n_in) conj(psi_v(r)) psi_v(r') (delta_rr' - Pi(r, r'))
+    and, transformed as P~ is,
+        dP~(G, G') = [rho_W(G - G') - sum_v W_v sum_{n loaded} M_vn(G) conj(M_vn(G'))] / (N_r - n_in)
+    with rho_W(q) = sum_r e^{-i q.r} sum_v W_v |psi_v(r)|^2 and M_vn(G) = sum_r e^{-iG.r}
+    conj(psi_v(r)) psi_n(r).  It is exact when the omitted states complete the set and share one
+    energy."""
+    psi = np.asarray(psi_in, dtype=np.complex128)
+    n_in = psi.shape[0]
+    n1, n2, n3 = dims
+    nr = n1 * n2 * n3
+    W = closure_weights(E_in_eV, nv, E_omit_eV)
+    g = np.asarray(gvec)
+    # term 1: rho_W at every difference G - G' (taken modulo the grid)
+    rhoW = np.sum(W[:, None] * np.abs(psi[:nv]) ** 2, axis=0).reshape(n1, n2, n3)
+    rhoG = np.fft.fftn(rhoW)
+    d = g[:, None, :] - g[None, :, :]
+    T1 = rhoG[d[..., 0] % n1, d[..., 1] % n2, d[..., 2] % n3]
+    # term 2: the projector on the loaded states, through the matrix elements M_vn for all loaded n
+    idx = _flat_index(dims, g)
+    T2 = np.zeros((len(g), len(g)), dtype=np.complex128)
+    for v in range(nv):
+        rho = np.conj(psi[v])[None, :] * psi
+        M = np.fft.fftn(rho.reshape(n_in, n1, n2, n3), axes=(1, 2, 3)).reshape(n_in, -1)[:, idx]   # [n][G]
+        T2 += W[v] * (M.T @ np.conj(M))
+    return (T1 - T2) / (nr - n_in)
 
 
 # ----------------------------------------------------------------------------- eps

@@ -532,6 +532,25 @@ GW_API gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, i
 GW_API gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, float *X,
                                   float *scale, void *stream);
 
+/*
+ * Closure estimate of the omitted part of P~ (Sec. 2 band truncation of the sum over c in
+ * Eq. Pstatic; Eq. gpsaceP), from the states loaded in ctx (occupied first, then the kept
+ * unoccupied ones; n_in in all) and the energies of the omitted unoccupied states only:
+ *     dP~(G, G') = [rho_W(G - G') - sum_v W_v sum_{n < n_in} M_vn(G) conj(M_vn(G'))] / (N_r - n_in)
+ * with W_v = sum_{omitted c} 2 / (E_v - E_c) (Hartree), rho_W(q) = sum_r e^{-iq.r} sum_v W_v
+ * |psi_v(r)|^2 and M_vn(G) = sum_r e^{-iG.r} conj(psi_v(r)) psi_n(r).  It is the mean of the omitted
+ * sum over states drawn without preference in the complement of the loaded ones (closure relation:
+ * a complete set sums to the identity on the grid), and exact when the omitted states complete the
+ * set and share one energy.  The projector term is a rank nv n_in update on the 16-bit tensor
+ * cores (FP16X3, the context's window); rho_W and its whole-grid transform are FP64.
+ *   gcut       sphere cut as gw_P_to_G (the sphere is rebuilt if it differs)
+ *   E_omit_eV  host double [nc_omit], each above every occupied energy (else GW_E_INVALID)
+ *   out        device complex64 [N_g][N_g] (overwritten; Hermitian, zero G = 0 row and column)
+ * Uses the context's g-space workspaces (not P~); synchronises the stream.  GW_E_INVALID if the
+ * loaded states already span the grid, GW_E_UNSUPPORTED where the grid needs the row-block
+ * transform kernel. */
+GW_API gw_status gw_corr_closure(gw_ctx *ctx, int gcut, const double *E_omit_eV, int nc_omit, void *out);
+
 /* Training targets T[t][2] = s (P~_all - P~_keep)(g, h), with s from gw_corr_features on P~_keep. */
 GW_API gw_status gw_corr_targets(const void *PG_keep, const void *PG_all, int ng, const float *scale, float *T,
                                  void *stream);

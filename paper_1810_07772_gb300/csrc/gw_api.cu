@@ -599,6 +599,10 @@ void Ctx::release()
     ns_cap_stream = nullptr;
     dfree(d_scal);
     dfree(d_tcw);
+    dfree(d_csw);
+    dfree(d_cw);
+    dfree(d_cgvec);
+    dfree(d_cwork);
     dfree(d_PGsum);
     dfree(d_coef);
     dfree(d_gidx);
@@ -882,6 +886,7 @@ gw_status gw_load_states(gw_ctx *h, int n1, int n2, int n3, double cell_L, int n
     GW_CUDA(launch_weights(c.d_E, nv, nc, c.d_sw, s), "weights");
     // Eh is a local: make sure the copy has consumed it before returning.
     GW_CUDA(cudaStreamSynchronize(s), "load sync");
+    c.E_h = Eh;
     c.loaded = true;
     return GW_OK;
 }
@@ -1132,6 +1137,102 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     if (gvec_out)
         std::memcpy(gvec_out, c.gvec.data(), (size_t)3 * ng * sizeof(int));
     c.PG_ready = true;
+    return GW_OK;
+}
+
+gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_omit, void *out)
+{
+    if (!h)
+        return GW_E_INVALID;
+    Ctx &c = h->c;
+    if (!c.loaded)
+        return fail(c, GW_E_NOT_READY, "gw_corr_closure before gw_load_states");
+    if (!out || nc_omit < 0 || (nc_omit > 0 && !E_omit_eV))
+        return fail(c, GW_E_INVALID, "null output or omitted energies, or nc_omit < 0");
+    if (!is_device_pointer(out))
+        return fail(c, GW_E_INVALID, "the closure estimate is written to device memory");
+    if (c.nr <= c.nb)
+        return fail(c, GW_E_INVALID, "the loaded states already span the grid (N_r = %d, %d states)", c.nr, c.nb);
+    const int nmin = std::min(c.n1, std::min(c.n2, c.n3));
+    if (gcut < 0 || 4LL * gcut >= (long long)nmin * nmin)
+        return fail(c, GW_E_INVALID, "gcut %d must satisfy 0 <= 4 gcut < min(n)^2 = %d", gcut, nmin * nmin);
+    // W_v = sum over the omitted c of 2 / (E_v - E_c) (Hartree, FP64), divided by N_r - n_in
+    const double inv_dim = 1.0 / (double)(c.nr - c.nb);
+    std::vector<double> wv(c.nv, 0.0);
+    for (int i = 0; i < nc_omit; ++i) {
+        const double eo = E_omit_eV[i] / HARTREE_EV;
+        if (!std::isfinite(eo))
+            return fail(c, GW_E_INVALID, "omitted energy %d is not finite", i);
+        for (int v = 0; v < c.nv; ++v) {
+            if (!(eo > c.E_h[v]))
+                return fail(c, GW_E_INVALID, "omitted energy %d is not above occupied energy %d", i, v);
+            wv[v] += 2.0 / (c.E_h[v] - eo);
+        }
+    }
+    std::vector<float> csw((size_t)c.nv * c.nb);
+    for (int v = 0; v < c.nv; ++v) {
+        wv[v] *= inv_dim;
+        for (int n = 0; n < c.nb; ++n)
+            csw[(size_t)v * c.nb + n] = static_cast<float>(std::sqrt(-wv[v]));
+    }
+    GW_CUDA(cudaSetDevice(c.device), "set device");
+    if (gcut != c.gcut)
+        GW_TRY(build_plan(c, gcut));
+    const int ng = c.ng;
+    if (!dft_supported(c.plan))
+        return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", ng);
+    cudaStream_t s = c.stream;
+    const int k2 = c.nv * c.nb, kpad2 = ((k2 + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
+    const int ng_pad = ((ng + 255) / 256) * 256;
+    GW_TRY(ensure(c, c.d_csw, c.cap_csw, csw.size() * sizeof(float), "closure weights"));
+    GW_TRY(ensure(c, c.d_cw, c.cap_cw, wv.size() * sizeof(double), "closure state weights"));
+    GW_TRY(ensure(c, c.d_cgvec, c.cap_cgvec, (size_t)3 * ng * sizeof(int), "closure sphere"));
+    GW_TRY(ensure(c, c.d_cwork, c.cap_cwork, closure_work_bytes(c.nr), "closure workspace"));
+    GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k2 * ng * sizeof(float2), "closure matrix elements"));
+    GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad2 * ng_pad * 2 * HERK16_NPL, "closure planes"));
+    GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, k2), "transform workspace"));
+    GW_TRY(ensure(c, c.d_psi, c.cap.psi, (size_t)c.nb * c.nr * sizeof(float2), "state staging"));
+    if (!c.d_small)
+        GW_CUDA(cudaMalloc(&c.d_small, 4 * sizeof(unsigned)), "scale words");
+    if (c.tiles_g_pad != ng_pad) {
+        const auto t = herk_tiles(ng_pad, HERK16_T, HERK16_T);
+        GW_TRY(ensure(c, c.d_tiles_g, c.cap.tiles_g, t.size() * sizeof(int2), "tile list (N_g)"));
+        GW_CUDA(cudaMemcpy(c.d_tiles_g, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice), "tile upload");
+        c.n_tiles_g = static_cast<int>(t.size());
+        c.tiles_g_pad = ng_pad;
+    }
+    c.F_prec = -1;  // the scale word now belongs to the closure's planes
+    GW_CUDA(cudaMemcpyAsync(c.d_csw, csw.data(), csw.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+            "closure weights");
+    GW_CUDA(cudaMemcpyAsync(c.d_cw, wv.data(), wv.size() * sizeof(double), cudaMemcpyHostToDevice, s),
+            "closure state weights");
+    GW_CUDA(cudaMemcpyAsync(c.d_cgvec, c.gvec.data(), (size_t)3 * ng * sizeof(int), cudaMemcpyHostToDevice, s),
+            "closure sphere");
+    const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+    int *scale_exp = reinterpret_cast<int *>(c.d_small + 1);
+    float2 *o = static_cast<float2 *>(out);
+    // projector term: matrix elements M_vn(G) sqrt(-W_v / (N_r - n_in)) for every loaded n, then the
+    // N_g x N_g rank-k update (which returns minus the sum of the outer products) into `out`
+    GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
+    cudaError_t fe = launch_dft_pairs_ws(c.d_psi, c.nr, c.d_csw, c.nv, c.nb, c.d_Q, ng, c.plan, c.d_dftw, s, true, 0);
+    if (fe == cudaErrorNotSupported)
+        return fail(c, GW_E_UNSUPPORTED, "the closure needs the plane transform kernel for this grid");
+    GW_CUDA(fe, "closure matrix elements");
+    GW_CUDA(launch_planes16_from_c64(c.d_Q, k2, ng, ng, kpad2, ng_pad, false, c.d_small, scale_exp,
+                                     reinterpret_cast<uint16_t *>(c.d_QT), s),
+            "closure planes");
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.device);
+    const int splits = std::max(1, std::min(kpad2 / HERK16_KC, nsm / std::max(1, c.n_tiles_g)));
+    if (splits > 1)
+        GW_TRY(ensure(c, c.d_PG_parts, c.cap.PG_parts, (size_t)splits * ng * ng * sizeof(float2), "split-k partials"));
+    GW_CUDA(launch_herk16(reinterpret_cast<const uint16_t *>(c.d_QT), false, kpad2, ng, ng_pad, c.d_tiles_g,
+                          c.n_tiles_g, o, scale_exp, c.d_err, wait_ns, c.herk_W, c.herk_L, s, splits, c.d_PG_parts),
+            "closure projector term");
+    // density term rho_W(G - G') / (N_r - n_in), combined in place with the projector term
+    const int dims[3] = {c.n1, c.n2, c.n3};
+    GW_CUDA(closure_enqueue(c.d_psiT, c.nr, c.nb, c.nv, c.d_cw, dims, c.d_cgvec, ng, o, o, c.d_cwork, s),
+            "closure density term");
     return GW_OK;
 }
 

@@ -161,6 +161,12 @@ struct Ctx {
     unsigned *d_small = nullptr;    // [0] |f| bound bits, [1] FP16 scale exponent
     int herk_W = 3, herk_L = 256;   // 6.5e-7 against FP64 at 24^3; see gw_set_herk_window
     int herk_kernel = GW_HERK_SINGLE; // r-space 16-bit update: one CTA per tile or CTA pairs
+    std::vector<double> E_h;        // the loaded energies in Hartree (host copy)
+    float *d_csw = nullptr;         // closure pair weights [nv][nb]
+    double *d_cw = nullptr;         // closure weights W_v / (N_r - nb) [nv]
+    int *d_cgvec = nullptr;         // sphere vectors [ng][3] for the closure
+    void *d_cwork = nullptr;        // closure workspace
+    size_t cap_csw = 0, cap_cw = 0, cap_cgvec = 0, cap_cwork = 0;
     int last_herk_kernel = -1;      // the kernel of the last 16-bit r-space update
     double err_target = 0.0;        // > 0: the window comes from gw_set_error_target's rule
     int last_W = 3;                 // the window of the last 16-bit rank-k update
@@ -271,9 +277,10 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
 // The same transform of the nv nc pair densities f_k = conj(psi_v) psi_c sw[k] (k = v nc + c),
 // formed from the states psi [nb][nr] inside the kernel; row k of Y is f_k's transform.
 // cudaErrorNotSupported (nothing launched) where the grid needs the row-block kernel.
+// c0: state index of the first c of the pairs (-1: nv, the unoccupied states).
 cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
                                 long long ldy, const DftPlan &p, float2 *work, cudaStream_t s,
-                                bool negative_exponent);
+                                bool negative_exponent, int c0 = -1);
 // negative_exponent: exp(-iG.r) instead of exp(+iG.r) (the conjugated twiddle table)
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                             const DftPlan &p, cudaStream_t s, bool negative_exponent = false);
@@ -333,6 +340,13 @@ cudaError_t pp_prepare(const PPWork &w, const double2 *epsinv, const double *sv,
 cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max_iter, int *iters_out,
                        cudaStream_t s);
 cudaError_t pp_eval(const PPWork &w, int ng, int b, int nuse, double omega, double2 *Sout, cudaStream_t s);
+// The band-truncation closure estimate (gw_corr_closure): rhoG = FP64 transform, on the whole grid,
+// of rho_W(r) = sum_{v < nv} w[v] |psi_v(r)|^2 (work: 2 N_r double2 + 3 * 64 twiddles), then
+// out(g, h) = rhoG((m_g - m_h) mod n) - Ph(g, h) as complex64.
+size_t closure_work_bytes(int nr);
+cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
+                            const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work,
+                            cudaStream_t s);
 // k_states.cu
 cudaError_t launch_states_from_g(const float2 *coef, int nb, int npw, const int *idx, int n1, int n2, int n3,
                                  const float2 *tw, float2 *work, float2 *out, cudaStream_t s);

@@ -334,6 +334,7 @@ __host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, int n
 struct PairSrc {
     const float *sw;
     int nv, nc;
+    int c0;  // state index of the first c (nv for the unoccupied states, 0 for all loaded states)
 };
 
 template <bool PAIR>
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         float w = 0.f;
         if (PAIR) {
             const int kk = (int)row, v = kk / ps.nc;
-            src = X + (size_t)(ps.nv + kk - v * ps.nc) * ldx + (size_t)j1 * plane;
+            src = X + (size_t)(ps.c0 + kk - v * ps.nc) * ldx + (size_t)j1 * plane;
             srcv = X + (size_t)v * ldx + (size_t)j1 * plane;
             w = ps.sw[kk];
         } else {
@@ -758,7 +759,7 @@ static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long 
                               const float2 *tw, float2 *work, const PairSrc *ps, cudaStream_t s)
 {
     return ps ? launch_p12_t<N3, true>(grid, smem, X, ldx, rows, p, tw, work, *ps, s)
-              : launch_p12_t<N3, false>(grid, smem, X, ldx, rows, p, tw, work, PairSrc{nullptr, 0, 1}, s);
+              : launch_p12_t<N3, false>(grid, smem, X, ldx, rows, p, tw, work, PairSrc{nullptr, 0, 1, 0}, s);
 }
 
 // The two-kernel transform of `rows` rows: of X (ps == nullptr) or of the pair densities formed
@@ -817,9 +818,10 @@ cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 
 }
 
 cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
-                                long long ldy, const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent)
+                                long long ldy, const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent,
+                                int c0)
 {
-    const PairSrc ps{sw, nv, nc};
+    const PairSrc ps{sw, nv, nc, c0 < 0 ? nv : c0};
     return dft_two_kernel(psi, nr, nv * nc, Y, ldy, p, work, s, negative_exponent, &ps);
 }
 

@@ -484,7 +484,68 @@ cudaError_t prod_ksplit(const double2 *A, const double2 *X, int ng, int b, doubl
     return cudaGetLastError();
 }
 
+// rho_W(r) = sum_{v < nv} w_v |psi_v(r)|^2 (FP64), as complex (rho_W, 0).
+__global__ void weighted_density_kernel(const float2 *__restrict__ psiT, int nr, int nb, int nv,
+                                        const double *__restrict__ w, double2 *__restrict__ rho)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int v = 0; v < nv; ++v) {
+            const float2 z = psiT[(size_t)r * nb + v];
+            s += w[v] * ((double)z.x * z.x + (double)z.y * z.y);
+        }
+        rho[r] = make_double2(s, 0.0);
+    }
+}
+
+// out(g, h) = rhoG((m_g - m_h) mod n) - Ph(g, h)
+__global__ void closure_combine_kernel(const double2 *__restrict__ rhoG, const int *__restrict__ gvec, int ng, int n1,
+                                       int n2, int n3, const float2 *__restrict__ Ph, float2 *__restrict__ out)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int g = blockIdx.y; g < ng && h < ng; g += gridDim.y) {
+        const int d0 = ((gvec[3 * g] - gvec[3 * h]) % n1 + n1) % n1;
+        const int d1 = ((gvec[3 * g + 1] - gvec[3 * h + 1]) % n2 + n2) % n2;
+        const int d2 = ((gvec[3 * g + 2] - gvec[3 * h + 2]) % n3 + n3) % n3;
+        const double2 rho = rhoG[((size_t)d0 * n2 + d1) * n3 + d2];
+        const float2 p = Ph[(size_t)g * ng + h];
+        out[(size_t)g * ng + h] = make_float2((float)(rho.x - (double)p.x), (float)(rho.y - (double)p.y));
+    }
+}
+
 }  // namespace
+
+size_t closure_work_bytes(int nr)
+{
+    return (size_t)2 * nr * sizeof(double2) + 3 * 64 * sizeof(double2);
+}
+
+cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
+                            const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work, cudaStream_t s)
+{
+    double2 *rho = static_cast<double2 *>(work), *rho2 = rho + nr, *tw = rho2 + nr;
+    const int n1 = dims[0], n2 = dims[1], n3 = dims[2];
+    if (n1 > 64 || n2 > 64 || n3 > 64)
+        return cudaErrorInvalidValue;
+    double2 twh[3 * 64];
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < dims[a]; ++t) {
+            const double ph = -6.283185307179586476925 * t / dims[a];
+            twh[64 * a + t] = make_double2(std::cos(ph), std::sin(ph));
+        }
+    cudaError_t e = cudaMemcpyAsync(tw, twh, sizeof twh, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return e;
+    weighted_density_kernel<<<blocks_for(nr), 256, 0, s>>>(psiT, nr, nb, nv, w, rho);
+    dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho, rho2, nr, n3, 1, tw + 128);
+    dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho2, rho, nr, n2, n3, tw + 64);
+    dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho, rho2, nr, n1, n2 * n3, tw);
+    closure_combine_kernel<<<grid2(ng, ng), 256, 0, s>>>(rho2, gvec_dev, ng, n1, n2, n3, Ph, out);
+    count_launches(5);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(s);  // twh is a host local
+}
 
 cudaError_t pp_prepare(const PPWork &w, const double2 *epsinv, const double *sv, const float2 *psiT, int ng, int nr,
                        int nb, int nv, const int dims[3], const int *gvec_host, double cell_L, const double q[3],

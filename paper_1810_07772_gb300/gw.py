@@ -52,6 +52,7 @@ SIGNATURES = {
     "gw_set_q": (_i, [_vp, _c.POINTER(_d)]),
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
     "gw_set_herk_kernel": (_i, [_vp, _i]),
+    "gw_corr_closure": (_i, [_vp, _i, _c.POINTER(_c.c_double), _i, _vp]),
     "gw_set_error_target": (_i, [_vp, ctypes.c_double]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
@@ -323,6 +324,24 @@ class Context:
 
     def set_herk_window(self, window_chunks, flush_windows):
         self._check(lib().gw_set_herk_window(self._h, int(window_chunks), int(flush_windows)))
+
+    def corr_closure(self, gcut, E_omit_eV, out=None):
+        """Closure estimate of the omitted part of P~ from the loaded states and the omitted
+        states' energies (gw_corr_closure); returns a complex64 [N_g][N_g] device tensor."""
+        import torch
+        E = np.ascontiguousarray(np.asarray(E_omit_eV, dtype=np.float64))
+        if out is None:
+            ng = self._sphere_size(gcut)
+            out = torch.empty((ng, ng), dtype=torch.complex64, device=f"cuda:{self.device}")
+        self._check(lib().gw_corr_closure(self._h, int(gcut), E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          int(E.size), _ptr(out)))
+        return out
+
+    def _sphere_size(self, gcut):
+        """Number of integer m in the grid's index range with |m|^2 <= gcut (the N_g of the call)."""
+        axes = [np.arange(-(n // 2), n - n // 2) ** 2 for n in self.dims]
+        m2 = axes[0][:, None, None] + axes[1][None, :, None] + axes[2][None, None, :]
+        return int(np.count_nonzero(m2 <= gcut))
 
     def set_herk_kernel(self, kind):
         """Kernel of the 16-bit r-space update: "single" (one CTA per tile, the default) or "pair"

@@ -694,7 +694,8 @@ def mlp_sample_flop(n_in=10, h=256, n_out=2):
     return fwd, fwd + dh + dw
 def section_learned(args, steps):
     """Learned truncation correction on the 24^3 workload: N_v = 32, the sum over unoccupied states
-    cut at N_c = 200 of 2000, a 10 -> 256 x 3 -> 2 network trained on 64 seeded systems.  Times
+    cut at N_c = 200 of 2000, the closure estimate of the omitted part plus a 12 -> 256 x 3 -> 2
+    network trained on 64 seeded systems to predict what the estimate leaves.  Times
     the learned form to eps^-1 against the plain full-N_c method on the same GPU, and reports the
     error of both truncated and learned P~ against the full sum on 8 held-out systems."""
     import torch
@@ -714,15 +715,15 @@ def section_learned(args, steps):
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     S = X.shape[0]
-    net = gw.Mlp(10, 256, max_batch=8192, device=0, stream=stream)
-    net.set_params(inputs.mlp_init(10, 256, 7))
+    net = gw.Mlp(gw.N_FEATURES, 256, max_batch=8192, device=0, stream=stream)
+    net.set_params(inputs.mlp_init(gw.N_FEATURES, 256, 7))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     ev[0].record(stream)
     losses = learned.train(net, X, T, epochs=args.epochs, batch=8192, lr=1e-3, seed=0, diag_repeat=args.diag_repeat)
     ev[1].record(stream)
     torch.cuda.synchronize()
     train_ms = ev[0].elapsed_time(ev[1])
-    fwd_flop, train_flop = mlp_sample_flop()
+    fwd_flop, train_flop = mlp_sample_flop(gw.N_FEATURES)
     n_train = args.epochs * ((S + (args.diag_repeat - 1) * 64 * 691) // 8192) * 8192
     # inference alone on one system's entries (the dominant kernel of the correction)
     Xs = X[: 691 * 692 // 2].contiguous()
@@ -744,11 +745,11 @@ def section_learned(args, steps):
     del X, T
 
     # held-out systems: errors of the truncated and learned P~ against the full sum
-    e_tr, e_ml, e_cl, e_inv, e_inv_tr = [], [], [], [], []
+    e_tr, e_ml, e_cl, e_full, e_inv, e_inv_tr = [], [], [], [], [], []
     for seed in range(2000, 2008):
         psi, E = states(seed)
         d = learned.system_samples(ctx, psi, E, nv, keep, dims, gcut, args.precision)
-        P_ml = learned.correct(net, d["PG_keep"], d["gvec"], gcut, E, nv, keep)
+        P_ml = learned.correct(net, d["PG_keep"], d["gvec"], gcut, E, nv, keep, d["clos"])
         w_om = float(np.sum(2.0 * 27.211386245988 / (E[None, nv + keep:] - E[:nv, None])))   # Hartree
         clos = d["PG_keep"].clone()
         ix = torch.arange(1, clos.shape[0], device=dev)
@@ -757,6 +758,7 @@ def section_learned(args, steps):
         e_tr.append(rel(d["PG_keep"], d["PG_all"]))
         e_ml.append(rel(P_ml, d["PG_all"]))
         e_cl.append(rel(clos, d["PG_all"]))
+        e_full.append(rel(d["PG_keep"] + d["clos"], d["PG_all"]))
         if seed == 2000:
             ng = P_ml.shape[0]
             invs = []
@@ -772,11 +774,14 @@ def section_learned(args, steps):
     # time to eps^-1: learned form against the plain full sum, on one held-out system
     psi, E = held
 
-    def step_learned():
+    clos_buf = torch.empty((691, 691), dtype=torch.complex64, device=dev)
+
+    def step_learned():       # kept states -> P~_keep, closure estimate, network, eps^-1
         ctx.load_states(psi[: nv + keep], E[: nv + keep], dims, nv)
         g = ctx.build_PG(gcut, args.precision)
         PG = ctx.view("PG")
-        learned.correct(net, PG, g, gcut, E, nv, keep, out=PG)
+        ctx.corr_closure(gcut, E[nv + keep:], out=clos_buf)
+        learned.correct(net, PG, g, gcut, E, nv, keep, clos_buf, out=PG)
         ctx.eps_inv(args.inv)
 
     def step_full():          # the full sum by the faster plain route (g-space)
@@ -814,7 +819,8 @@ def section_learned(args, steps):
             "ms_per_step": res["learned"]["ms"], "dtype": "f16-weights/f32",
             "config": {"workload": f"grid24_nv32_nc{keep}_of_{nc_all}_learned", "grid": [n] * 3, "nv": nv,
                        "nc_keep": keep, "nc_all": nc_all, "gcut": gcut, "N_g": 691,
-                       "network": "10 -> 256 -> 256 -> 256 -> 2, tanh, FP16 weights, FP32 accumulation",
+                       "network": f"{gw.N_FEATURES} -> 256 -> 256 -> 256 -> 2, tanh, FP16 weights, FP32 "
+                                  "accumulation; predicts what the closure estimate of the omitted part leaves",
                        "train_systems": 64, "held_out_systems": 8, "precision_of_P": args.precision,
                        "route_of_P": "g-space (gw_build_PG) for the kept and the full sum",
                        "diag_repeat": args.diag_repeat},
@@ -823,7 +829,8 @@ def section_learned(args, steps):
                               "s_per_eps_inv_rspace": res["full_rspace"]["ms"] / 1e3},
             "speedup_vs_full": res["full"]["ms"] / res["learned"]["ms"],
             "err_vs_full_sum": {"P_G_rel_truncated": float(np.mean(e_tr)), "P_G_rel_learned": float(np.mean(e_ml)),
-                                "P_G_rel_closure_estimate": float(np.mean(e_cl)),
+                                "P_G_rel_closure_estimate": float(np.mean(e_full)),
+                                "P_G_rel_diagonal_shift": float(np.mean(e_cl)),
                                 "epsinv_rel_learned": float(np.mean(e_inv)),
                                 "epsinv_rel_truncated": float(np.mean(e_inv_tr))},
             "training": {"samples": S, "epochs": args.epochs, "losses": losses, "ms": train_ms,

@@ -451,10 +451,13 @@ GW_API gw_status gw_set_wait_limit(gw_ctx *ctx, double ms);
  * Scale s = 1 / mean_{g >= 1} |Re P~_keep(g, g)|.  It makes features and targets O(1) for any
  * system.
  *
- * Features (float32, 10 per row):
+ * Features (float32, 12 per row):
  *   [ |m_g|^2/gcut, |m_h|^2/gcut, |m_g - m_h|^2/(4 gcut), s Re P~(g,h), s Im P~(g,h), s Re P~(g,g),
- *     s Re P~(h,h), [g == h], ratio, [g == 0 or h == 0] ]
- * Here m are the integer G-vectors and ratio is the per-system scalar from gw_corr_weight_ratio.
+ *     s Re P~(h,h), [g == h], ratio, [g == 0 or h == 0], s Re dP~(g,h), s Im dP~(g,h) ]
+ * Here m are the integer G-vectors, ratio is the per-system scalar from gw_corr_weight_ratio and
+ * dP~ the closure estimate of the omitted part (gw_corr_closure; zero when not given).  With a
+ * closure estimate the network learns what it leaves: targets s (P~_all - P~_keep - dP~), and the
+ * learned form is P~_keep + dP~ + y / s.
  *
  * Parameters are one flat float32 vector [W1, b1, W2, b2, W3, b3, W4, b4], each W_l row-major
  * (out x in).  The loss is L = (1/(2B)) sum over the batch and both outputs of (y - t)^2.
@@ -523,14 +526,15 @@ GW_API gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, i
                                       void *stream);
 
 /* Features of every upper-triangle entry of a truncated P~.
- *   PG     complex64, ng x ng, as written by gw_P_to_G
- *   ng     >= 2
- *   gvec   int32 [ng][3] integer G-vectors in basis order
- *   ratio  device float from gw_corr_weight_ratio
- *   X      float [ng (ng + 1)/2][10]
- *   scale  device float, receives s */
-GW_API gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, float *X,
-                                  float *scale, void *stream);
+ *   PG       complex64, ng x ng, as written by gw_P_to_G
+ *   ng       >= 2
+ *   gvec     int32 [ng][3] integer G-vectors in basis order
+ *   ratio    device float from gw_corr_weight_ratio
+ *   PG_clos  complex64 ng x ng closure estimate from gw_corr_closure, or NULL (features 10, 11 = 0)
+ *   X        float [ng (ng + 1)/2][12]
+ *   scale    device float, receives s */
+GW_API gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio,
+                                  const void *PG_clos, float *X, float *scale, void *stream);
 
 /*
  * Closure estimate of the omitted part of P~ (Sec. 2 band truncation of the sum over c in
@@ -551,15 +555,18 @@ GW_API gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int g
  * transform kernel. */
 GW_API gw_status gw_corr_closure(gw_ctx *ctx, int gcut, const double *E_omit_eV, int nc_omit, void *out);
 
-/* Training targets T[t][2] = s (P~_all - P~_keep)(g, h), with s from gw_corr_features on P~_keep. */
-GW_API gw_status gw_corr_targets(const void *PG_keep, const void *PG_all, int ng, const float *scale, float *T,
-                                 void *stream);
+/* Training targets T[t][2] = s (P~_all - P~_keep - dP~)(g, h), with s from gw_corr_features on
+ * P~_keep and dP~ the closure estimate PG_clos (NULL = 0). */
+GW_API gw_status gw_corr_targets(const void *PG_keep, const void *PG_all, const void *PG_clos, int ng,
+                                 const float *scale, float *T, void *stream);
 
-/* In place, P~(g,h) += (y0 + i y1)/s and P~(h,g) = its conjugate, for g < h.
- * The diagonal takes y0/s only.  Row and column 0 are left unchanged: they vanish exactly at any
- * N_c, because occupied and unoccupied states are orthogonal.
+/* In place, P~(g,h) += dP~(g,h) + (y0 + i y1)/s and P~(h,g) = its conjugate, for g < h, with dP~
+ * the closure estimate PG_clos (NULL = 0).  The diagonal takes the real part only.  Row and
+ * column 0 are left unchanged: they vanish exactly at any N_c, because occupied and unoccupied
+ * states are orthogonal.
  *   Y  float [ng (ng + 1)/2][2], from gw_mlp_forward */
-GW_API gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, void *stream);
+GW_API gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, const void *PG_clos,
+                               void *stream);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_FEATURES = 10
+N_FEATURES = 12
 
 
 def entry_scale(PG_lo):
@@ -29,10 +29,11 @@ def omitted_weights(E_eV, nv, nc_lo):
     return float(np.sum(w[:, nc_lo:])), float(np.sum(w[:, :nc_lo]))
 
 
-def features(PG_lo, gvec, gcut, w_om, w_in):
+def features(PG_lo, gvec, gcut, w_om, w_in, dclos=None):
     """Rows (g, h), g <= h in basis order (row-major over the upper triangle):
     |m_g|^2/gcut, |m_h|^2/gcut, |m_g - m_h|^2/(4 gcut), s Re P~(g,h), s Im P~(g,h), s P~(g,g),
-    s P~(h,h), [g == h], w_om / w_in, [g == 0 or h == 0]."""
+    s P~(h,h), [g == h], w_om / w_in, [g == 0 or h == 0], s Re dP~(g,h), s Im dP~(g,h), where dP~ is
+    the closure estimate of the omitted part (zero when dclos is None)."""
     PG_lo = np.asarray(PG_lo, dtype=np.complex128)
     gvec = np.asarray(gvec, dtype=np.float64)
     ng = gvec.shape[0]
@@ -41,19 +42,25 @@ def features(PG_lo, gvec, gcut, w_om, w_in):
     m2 = np.sum(gvec * gvec, axis=1)
     dm = gvec[gi] - gvec[hi]
     diag = np.real(np.diag(PG_lo))
+    dc = np.zeros(gi.shape, dtype=np.complex128) if dclos is None else np.asarray(dclos, np.complex128)[gi, hi]
     X = np.stack([m2[gi] / gcut, m2[hi] / gcut, np.sum(dm * dm, axis=1) / (4.0 * gcut),
                   s * np.real(PG_lo[gi, hi]), s * np.imag(PG_lo[gi, hi]), s * diag[gi], s * diag[hi],
                   (gi == hi).astype(np.float64), np.full(gi.shape, w_om / w_in),
-                  ((gi == 0) | (hi == 0)).astype(np.float64)], axis=1)
+                  ((gi == 0) | (hi == 0)).astype(np.float64), s * np.real(dc), s * np.imag(dc)], axis=1)
     return X, s
 
 
-def targets(PG_lo, PG_hi):
-    """t = s (P~_hi - P~_lo)(g, h) as (Re, Im) over the upper triangle, s from the truncated P~."""
+def targets(PG_lo, PG_hi, dclos=None):
+    """t = s (P~_hi - P~_lo - dP~)(g, h) as (Re, Im) over the upper triangle, s from the truncated P~
+    and dP~ the closure estimate (zero when dclos is None): the network learns what the closure
+    estimate leaves."""
     s = entry_scale(PG_lo)
     ng = PG_lo.shape[0]
     gi, hi = np.triu_indices(ng)
-    d = (np.asarray(PG_hi) - np.asarray(PG_lo))[gi, hi] * s
+    D = np.asarray(PG_hi, np.complex128) - np.asarray(PG_lo, np.complex128)
+    if dclos is not None:
+        D = D - np.asarray(dclos, np.complex128)
+    d = D[gi, hi] * s
     return np.stack([np.real(d), np.imag(d)], axis=1)
 
 
@@ -118,15 +125,17 @@ def to_fp16_weights(theta, n_in, hidden):
     return out
 
 
-def apply_correction(PG_lo, Y, s):
-    """P~ = P~_lo + (y0 + i y1) / s on the upper triangle, mirrored as the conjugate below it.
-    The diagonal takes y0 only (a Hermitian matrix has a real diagonal) and the G = 0 row and
-    column are left unchanged (they vanish exactly, because occupied and unoccupied states are
-    orthogonal, at any N_c)."""
+def apply_correction(PG_lo, Y, s, dclos=None):
+    """P~ = P~_lo + dP~ + (y0 + i y1) / s on the upper triangle, mirrored as the conjugate below it
+    (dP~ the closure estimate, zero when dclos is None).  The diagonal takes the real part only (a
+    Hermitian matrix has a real diagonal) and the G = 0 row and column are left unchanged (they
+    vanish exactly, because occupied and unoccupied states are orthogonal, at any N_c)."""
     P = np.array(PG_lo, dtype=np.complex128)
     ng = P.shape[0]
     gi, hi = np.triu_indices(ng)
     d = (np.asarray(Y[:, 0], dtype=np.float64) + 1j * np.asarray(Y[:, 1], dtype=np.float64)) / s
+    if dclos is not None:
+        d = d + np.asarray(dclos, np.complex128)[gi, hi]
     keep = (gi != 0) & (hi != 0)
     gi, hi, d = gi[keep], hi[keep], d[keep]
     on = gi == hi

@@ -29,7 +29,7 @@ void count_launches(int n);
 
 namespace {
 
-constexpr int NF = 10;        // features per P~ entry
+constexpr int NF = 12;        // features per P~ entry
 constexpr int NOUT = 2;       // (Re, Im) of the predicted correction
 constexpr int GT_M = 64, GT_N = 64, GT_K = 16;
 constexpr int SPLIT_MAX = 64;
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) entry_scale_kernel(const float2 *PG, int 
 
 // One block per row g; threads over h in [g, ng).
 __global__ void __launch_bounds__(128) features_kernel(const float2 *PG, int ng, const int *gvec, float inv_gcut,
-                                                       const float *ratio, const float *scale, float *X)
+                                                       const float *ratio, const float2 *clos, const float *scale,
+                                                       float *X)
 {
     const int g = blockIdx.x;
     const float s = *scale, rt = *ratio;
@@ -114,25 +115,31 @@ __global__ void __launch_bounds__(128) features_kernel(const float2 *PG, int ng,
         x[7] = g == h ? 1.f : 0.f;
         x[8] = rt;
         x[9] = (g == 0 || h == 0) ? 1.f : 0.f;
+        const float2 dc = clos ? clos[(long)g * ng + h] : make_float2(0.f, 0.f);
+        x[10] = s * dc.x;
+        x[11] = s * dc.y;
     }
 }
 
-__global__ void __launch_bounds__(128) targets_kernel(const float2 *lo, const float2 *hi, int ng, const float *scale,
-                                                      float *T)
+// t = s (hi - lo - clos)(g, h): what the closure estimate leaves (clos may be null)
+__global__ void __launch_bounds__(128) targets_kernel(const float2 *lo, const float2 *hi, const float2 *clos, int ng,
+                                                      const float *scale, float *T)
 {
     const int g = blockIdx.x;
     const float s = *scale;
     for (int h = g + (int)threadIdx.x; h < ng; h += blockDim.x) {
         const long e = (long)g * ng + h;
         float *t = T + tri_index(g, h, ng) * NOUT;
-        t[0] = s * (hi[e].x - lo[e].x);
-        t[1] = s * (hi[e].y - lo[e].y);
+        const float2 dc = clos ? clos[e] : make_float2(0.f, 0.f);
+        t[0] = s * (hi[e].x - lo[e].x - dc.x);
+        t[1] = s * (hi[e].y - lo[e].y - dc.y);
     }
 }
 
-// P~(g,h) += (y0 + i y1)/s and P~(h,g) = its conjugate; diagonal: real part only; row and
-// column 0 untouched.
-__global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const float *Y, const float *scale)
+// P~(g,h) += clos(g,h) + (y0 + i y1)/s and P~(h,g) = its conjugate; diagonal: real part only;
+// row and column 0 untouched (clos may be null).
+__global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const float *Y, const float *scale,
+                                                    const float2 *clos)
 {
     const int g = blockIdx.x;
     if (g == 0)
@@ -140,7 +147,8 @@ __global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const fl
     const float inv = 1.f / *scale;
     for (int h = g + (int)threadIdx.x; h < ng; h += blockDim.x) {
         const float *y = Y + tri_index(g, h, ng) * NOUT;
-        const float dr = y[0] * inv, di = y[1] * inv;
+        const float2 dc = clos ? clos[(long)g * ng + h] : make_float2(0.f, 0.f);
+        const float dr = y[0] * inv + dc.x, di = y[1] * inv + dc.y;
         if (h == g) {
             PG[(long)g * ng + g].x += dr;
         } else {
@@ -772,34 +780,38 @@ gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_a
     return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
 }
 
-gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, float *X,
-                           float *scale, void *stream)
+gw_status gw_corr_features(const void *PG, int ng, const int *gvec, int gcut, const float *ratio, const void *PG_clos,
+                           float *X, float *scale, void *stream)
 {
     if (!PG || !gvec || !ratio || !X || !scale || ng < 2 || gcut < 1)
         return GW_E_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float2 *P = static_cast<const float2 *>(PG);
     entry_scale_kernel<<<1, 256, 0, s>>>(P, ng, scale);
-    features_kernel<<<ng, 128, 0, s>>>(P, ng, gvec, 1.f / (float)gcut, ratio, scale, X);
+    features_kernel<<<ng, 128, 0, s>>>(P, ng, gvec, 1.f / (float)gcut, ratio, static_cast<const float2 *>(PG_clos),
+                                       scale, X);
     gw::count_launches(2);
     return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
 }
 
-gw_status gw_corr_targets(const void *PG_lo, const void *PG_hi, int ng, const float *scale, float *T, void *stream)
+gw_status gw_corr_targets(const void *PG_lo, const void *PG_hi, const void *PG_clos, int ng, const float *scale,
+                          float *T, void *stream)
 {
     if (!PG_lo || !PG_hi || !scale || !T || ng < 1)
         return GW_E_INVALID;
     targets_kernel<<<ng, 128, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const float2 *>(PG_lo), static_cast<const float2 *>(PG_hi), ng, scale, T);
+        static_cast<const float2 *>(PG_lo), static_cast<const float2 *>(PG_hi), static_cast<const float2 *>(PG_clos),
+        ng, scale, T);
     gw::count_launches(1);
     return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
 }
 
-gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, void *stream)
+gw_status gw_corr_apply(void *PG, int ng, const float *Y, const float *scale, const void *PG_clos, void *stream)
 {
     if (!PG || !Y || !scale || ng < 1)
         return GW_E_INVALID;
-    apply_kernel<<<ng, 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<float2 *>(PG), ng, Y, scale);
+    apply_kernel<<<ng, 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<float2 *>(PG), ng, Y, scale,
+                                                                      static_cast<const float2 *>(PG_clos));
     gw::count_launches(1);
     return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
 }

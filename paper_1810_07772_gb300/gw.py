@@ -80,9 +80,9 @@ SIGNATURES = {
     "gw_mlp_grad": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp]),
     "gw_mlp_train_step": (_i, [_vp, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp]),
     "gw_corr_weight_ratio": (_i, [_vp, _i, _i, _i, _vp, _vp]),
-    "gw_corr_features": (_i, [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp]),
-    "gw_corr_targets": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
-    "gw_corr_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "gw_corr_features": (_i, [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "gw_corr_targets": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "gw_corr_apply": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -458,7 +458,7 @@ class Batch:
 
 
 # ---------------------------------------------------------------------------------------------- learned correction
-N_FEATURES = 10
+N_FEATURES = 12
 
 
 def _stream_handle(device, stream=None):
@@ -571,29 +571,30 @@ def corr_weight_ratio(E_eV, nv, nc_keep, device=0, stream=None):
     return out
 
 
-def corr_features(PG, gvec, gcut, ratio, stream=None):
-    """(X [ng(ng+1)/2][10], scale) for a truncated P~ (complex64 ng x ng device tensor)."""
+def corr_features(PG, gvec, gcut, ratio, clos=None, stream=None):
+    """(X [ng(ng+1)/2][12], scale) for a truncated P~ (complex64 ng x ng device tensor); clos is the
+    closure estimate of the omitted part (gw_corr_closure) or None."""
     import torch
     dev = PG.device
     ng = PG.shape[0]
     g = torch.as_tensor(np.ascontiguousarray(np.asarray(gvec, dtype=np.int32))).to(dev)
     X = torch.empty((ng * (ng + 1) // 2, N_FEATURES), dtype=torch.float32, device=dev)
     scale = torch.empty(1, dtype=torch.float32, device=dev)
-    _status(lib().gw_corr_features(_ptr(PG), ng, _ptr(g), int(gcut), _ptr(ratio), _ptr(X), _ptr(scale),
+    _status(lib().gw_corr_features(_ptr(PG), ng, _ptr(g), int(gcut), _ptr(ratio), _ptr(clos), _ptr(X), _ptr(scale),
                                    _stream_handle(dev.index, stream)), "gw_corr_features")
     return X, scale
 
 
-def corr_targets(PG_keep, PG_all, scale, stream=None):
+def corr_targets(PG_keep, PG_all, scale, clos=None, stream=None):
     import torch
     ng = PG_keep.shape[0]
     T = torch.empty((ng * (ng + 1) // 2, 2), dtype=torch.float32, device=PG_keep.device)
-    _status(lib().gw_corr_targets(_ptr(PG_keep), _ptr(PG_all), ng, _ptr(scale), _ptr(T),
+    _status(lib().gw_corr_targets(_ptr(PG_keep), _ptr(PG_all), _ptr(clos), ng, _ptr(scale), _ptr(T),
                                   _stream_handle(PG_keep.device.index, stream)), "gw_corr_targets")
     return T
 
 
-def corr_apply(PG, Y, scale, stream=None):
-    """In place: PG += the predicted correction (gw_corr_apply)."""
-    _status(lib().gw_corr_apply(_ptr(PG), PG.shape[0], _ptr(Y), _ptr(scale), _stream_handle(PG.device.index, stream)),
-            "gw_corr_apply")
+def corr_apply(PG, Y, scale, clos=None, stream=None):
+    """In place: PG += the closure estimate (if given) and the predicted correction (gw_corr_apply)."""
+    _status(lib().gw_corr_apply(_ptr(PG), PG.shape[0], _ptr(Y), _ptr(scale), _ptr(clos),
+                                _stream_handle(PG.device.index, stream)), "gw_corr_apply")

@@ -7,13 +7,15 @@ order, and sets the learning-rate schedule:
 1. For every seeded system, run the plain method twice: P~ with the nc_keep lowest unoccupied
    states, and P~ with all of them.  The sum over unoccupied states c is the one in
    Eq. (Pstatic).  Both go by the g-space route (gw_build_PG) unless route="rspace" asks for
-   P(r,r') and its transforms.
-2. Compute the per-entry features of the truncated P~ and the targets s (P~_all - P~_keep)
-   (gw_corr_features, gw_corr_targets).
+   P(r,r') and its transforms.  With the kept states loaded, the closure estimate dP~ of the
+   omitted part follows from the omitted states' energies alone (gw_corr_closure).
+2. Compute the per-entry features of the truncated P~ (with dP~) and the targets
+   s (P~_all - P~_keep - dP~), what the closure estimate leaves (gw_corr_features,
+   gw_corr_targets).
 3. Run Adam on minibatches drawn without replacement from all systems' entries
    (gw_mlp_train_step), with a cosine learning-rate decay.
-4. Inference: features of a new truncated P~, the forward pass, then add the prediction into P~
-   (gw_corr_apply).  eps and eps^-1 then follow as for any P~.
+4. Inference: the closure estimate and the features of a new truncated P~, the forward pass,
+   then add both into P~ (gw_corr_apply).  eps and eps^-1 then follow as for any P~.
 """
 from __future__ import annotations
 
@@ -33,24 +35,27 @@ def build_PG(ctx, gcut, precision="fp16x3", route="gspace"):
 
 
 def truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
-    """(P~_keep, P~_all, gvec) of one system.  psi: [nv + nc_all][N_r] device tensor."""
+    """(P~_keep, P~_all, dP~, gvec) of one system, dP~ the closure estimate of P~_all - P~_keep from
+    the kept states and the omitted energies.  psi: [nv + nc_all][N_r] device tensor."""
     E = np.asarray(E_eV, dtype=np.float64)
     ctx.load_states(psi[: nv + nc_keep], E[: nv + nc_keep], dims, nv)
     gvec = build_PG(ctx, gcut, precision, route)
     PG_keep = ctx.view("PG").clone()
+    clos = ctx.corr_closure(gcut, E[nv + nc_keep:])
     ctx.load_states(psi, E, dims, nv)
     build_PG(ctx, gcut, precision, route)
     PG_all = ctx.view("PG").clone()
-    return PG_keep, PG_all, gvec
+    return PG_keep, PG_all, clos, gvec
 
 
 def system_samples(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
     """Features, targets and the pieces needed to judge a prediction, for one system."""
-    PG_keep, PG_all, gvec = truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision, route)
+    PG_keep, PG_all, clos, gvec = truncated_pair(ctx, psi, E_eV, nv, nc_keep, dims, gcut, precision, route)
     ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
-    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
-    T = gw.corr_targets(PG_keep, PG_all, scale)
-    return {"X": X, "T": T, "scale": scale, "ratio": ratio, "PG_keep": PG_keep, "PG_all": PG_all, "gvec": gvec}
+    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio, clos)
+    T = gw.corr_targets(PG_keep, PG_all, scale, clos)
+    return {"X": X, "T": T, "scale": scale, "ratio": ratio, "PG_keep": PG_keep, "PG_all": PG_all, "clos": clos,
+            "gvec": gvec}
 
 
 def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp16x3", route="gspace"):
@@ -102,15 +107,16 @@ def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1
     return losses
 
 
-def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, out=None, tensor_cores=True):
-    """Learned form: P~_keep plus the predicted correction (in `out`, or a new tensor).  The
-    prediction runs on the tensor cores (gw_mlp_infer) unless tensor_cores=False asks for the
-    FP32 forward of training (gw_mlp_forward)."""
+def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, clos, out=None, tensor_cores=True):
+    """Learned form: P~_keep plus the closure estimate clos (gw_corr_closure on the kept states)
+    plus the network's prediction of what it leaves (in `out`, or a new tensor).  The prediction
+    runs on the tensor cores (gw_mlp_infer) unless tensor_cores=False asks for the FP32 forward of
+    training (gw_mlp_forward)."""
     ratio = gw.corr_weight_ratio(E_eV, nv, nc_keep, device=PG_keep.device.index)
-    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio)
+    X, scale = gw.corr_features(PG_keep, gvec, gcut, ratio, clos)
     Y = mlp.infer(X) if tensor_cores else mlp.forward(X)
     P = PG_keep.clone() if out is None else out
     if out is not None and out.data_ptr() != PG_keep.data_ptr():
         P.copy_(PG_keep)
-    gw.corr_apply(P, Y, scale)
+    gw.corr_apply(P, Y, scale, clos)
     return P

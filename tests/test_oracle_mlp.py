@@ -44,26 +44,39 @@ def test_output_layer_gradient_is_least_squares_gradient():
 
 
 def test_features_by_hand():
-    """Two G-vectors m0 = 0, m1 = (1, 0, 0), gcut = 1, P~_lo = [[0, 1+2i], [1-2i, 4]]:
-    s = 1/4 (mean |diagonal| over G != 0), three upper-triangle rows (0,0), (0,1), (1,1)."""
+    """Two G-vectors m0 = 0, m1 = (1, 0, 0), gcut = 1, P~_lo = [[0, 1+2i], [1-2i, 4]], closure
+    estimate dP~ = [[0, 8-4i], [8+4i, -12]]: s = 1/4 (mean |diagonal| over G != 0), three
+    upper-triangle rows (0,0), (0,1), (1,1); the last two features are s dP~(g, h)."""
     PG = np.array([[0.0, 1 + 2j], [1 - 2j, 4.0]])
+    dc = np.array([[0.0, 8 - 4j], [8 + 4j, -12.0]])
     g = np.array([[0, 0, 0], [1, 0, 0]])
-    X, s = M.features(PG, g, 1, 3.0, 6.0)
+    X, s = M.features(PG, g, 1, 3.0, 6.0, dc)
     assert s == 0.25
-    assert X.shape == (3, M.N_FEATURES)
-    assert np.allclose(X[1], [0, 1, 0.25, 0.25, 0.5, 0, 1, 0, 0.5, 1])
-    assert np.allclose(X[0], [0, 0, 0, 0, 0, 0, 0, 1, 0.5, 1])
-    assert np.allclose(X[2], [1, 1, 0, 1, 0, 1, 1, 1, 0.5, 0])
-    T = M.targets(PG, PG + np.array([[0, 4j], [-4j, 8]]))
+    assert X.shape == (3, M.N_FEATURES) == (3, 12)
+    assert np.allclose(X[1], [0, 1, 0.25, 0.25, 0.5, 0, 1, 0, 0.5, 1, 2, -1])
+    assert np.allclose(X[0], [0, 0, 0, 0, 0, 0, 0, 1, 0.5, 1, 0, 0])
+    assert np.allclose(X[2], [1, 1, 0, 1, 0, 1, 1, 1, 0.5, 0, -3, 0])
+    X0, _ = M.features(PG, g, 1, 3.0, 6.0)
+    assert np.array_equal(X0[:, :10], X[:, :10]) and not X0[:, 10:].any()
+    hi = PG + np.array([[0, 4j], [-4j, 8]])
+    T = M.targets(PG, hi)
     assert np.allclose(T, [[0, 0], [0, 1], [2, 0]])
+    # with the closure estimate the targets are what it leaves: s (hi - lo - dP~)
+    T = M.targets(PG, hi, dc)
+    assert np.allclose(T, [[0, 0], [-2, 2], [5, 0]])
 
 
 def test_apply_correction_by_hand():
     """3x3 P~_lo = 0, three upper-triangle predictions per row: head row/column untouched,
-    diagonal takes the real part only, (1,2) and (2,1) are conjugates; s = 2 halves everything."""
+    diagonal takes the real part only, (1,2) and (2,1) are conjugates; s = 2 halves everything.
+    With a closure estimate dP~ it is added on the same entries under the same rules."""
     Y = np.array([[9, 9], [9, 9], [9, 9], [2, 4], [4, 6], [6, 8]], dtype=float)
     P = M.apply_correction(np.zeros((3, 3)), Y, 2.0)
     want = np.array([[0, 0, 0], [0, 1, 2 + 3j], [0, 2 - 3j, 3]])
+    assert np.array_equal(P, want)
+    dc = np.array([[5, 5j, 5], [-5j, 10, 1 - 1j], [5, 1 + 1j, 20]])
+    P = M.apply_correction(np.zeros((3, 3)), Y, 2.0, dc)
+    want = np.array([[0, 0, 0], [0, 11, 3 + 2j], [0, 3 - 2j, 23]])
     assert np.array_equal(P, want)
 
 

@@ -518,6 +518,34 @@ GW_API gw_status gw_mlp_grad(gw_mlp *m, const float *X, const float *T, const in
 GW_API gw_status gw_mlp_train_step(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, double lr,
                                    double beta1, double beta2, double adam_eps, float *loss_accum);
 
+/*
+ * Training of the correction network: `epochs` passes of Adam (the rule of gw_mlp_train_step) over
+ * minibatches of the rows of X[n][n_in] and T[n][2] (device pointers), drawn without replacement:
+ *   pool   the rows 0..n-1, followed by the rows whose feature diag_feature equals 1 (the
+ *          diagonal entries of P~ for gw_corr_features, feature 7), ascending, diag_repeat - 1
+ *          more times (diag_repeat = 1 or diag_feature < 0: no repeats).  Diagonal entries carry
+ *          most of the correction's norm but are 1 in N_g (N_g + 1)/2 of the rows.
+ *   order  pass e takes the pool sorted by key(j) = mix(seed * 0x9E3779B97F4A7C15
+ *          + (e + 1) * 0xD1B54A32D192ED03 + j) (64-bit wrapping arithmetic, j the pool position,
+ *          mix = SplitMix64's output function, ties by position), split into floor(S / batch)
+ *          minibatches; the ragged tail of a pass is dropped.
+ *   rate   step t of T = epochs floor(S / batch): lr_final + (lr - lr_final)(1 + cos(pi t / T)) / 2.
+ * losses[e] (host float[epochs]) receives the mean minibatch loss of pass e.  The device scratch
+ * (the pool, its order and the sort keys, about 24 bytes per pool row) is allocated for the call
+ * and released before it returns; the call synchronises the handle's stream.
+ */
+typedef struct gw_corr_train_opts {
+    int epochs;                 /* >= 1 */
+    int batch;                  /* 1 .. max_batch of the handle */
+    double lr, lr_final;        /* > 0, >= 0 */
+    double beta1, beta2, adam_eps;
+    unsigned long long seed;
+    int diag_repeat;            /* >= 1 */
+    int diag_feature;           /* < n_in; negative: none */
+} gw_corr_train_opts;
+GW_API gw_status gw_corr_train(gw_mlp *m, const float *X, const float *T, long n, const gw_corr_train_opts *opts,
+                               float *losses);
+
 /* ratio = sum_{c >= nc_keep} sum_v 2/(E_c - E_v) / sum_{c < nc_keep} sum_v 2/(E_c - E_v), in FP64,
  * from device energies E_eV[nv + nc_all] (occupied first, as gw_load_states).  This is the
  * weight of the omitted pairs in Eq. (Pstatic) relative to the kept ones; it needs only the

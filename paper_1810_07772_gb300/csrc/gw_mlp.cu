@@ -20,6 +20,9 @@
 #include <cstdio>
 #include <new>
 #include <string>
+#include <vector>
+
+#include <cub/cub.cuh>
 
 #include "gw_internal.cuh"
 
@@ -546,6 +549,67 @@ gw_status check_mlp(gw_mlp *m)
 
 }  // namespace
 
+namespace {
+
+// One Adam step on a batch (arguments checked by the callers).
+gw_status train_step(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, double lr, double beta1,
+                     double beta2, double adam_eps, float *loss_accum)
+{
+    MLP_CUDA(loss_grad(m, X, T, rows, batch, loss_accum), "gw_mlp_train_step");
+    m->step += 1;
+    m->tiled = false;
+    const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
+    const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
+    adam_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(
+        m->theta, m->theta16, m->grad, m->m, m->v, m->P, (float)lr, (float)beta1, (float)beta2, (float)c1, (float)c2,
+        (float)adam_eps);
+    gw::count_launches(1);
+    MLP_CUDA(cudaGetLastError(), "gw_mlp_train_step adam");
+    return GW_OK;
+}
+
+// SplitMix64's output function (Steele, Lea and Flood, 2014): a bijective mix of 64 bits.
+__host__ __device__ __forceinline__ unsigned long long splitmix64_mix(unsigned long long z)
+{
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+// Sort key of pool position j in pass e: the minibatch order of a pass is the pool sorted by it.
+__global__ void order_keys_kernel(unsigned long long seed, int pass, long S, unsigned long long *keys)
+{
+    const unsigned long long base = seed * 0x9E3779B97F4A7C15ull + (unsigned long long)(pass + 1) * 0xD1B54A32D192ED03ull;
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < S; j += (long)gridDim.x * blockDim.x)
+        keys[j] = splitmix64_mix(base + (unsigned long long)j);
+}
+
+// flags[i] = (X[i][feat] == 1), idx[i] = i
+__global__ void diag_flags_kernel(const float *X, long n, int nf, int feat, unsigned char *flags, int *idx)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        flags[i] = X[i * nf + feat] == 1.0f ? 1 : 0;
+        idx[i] = (int)i;
+    }
+}
+
+// pool[j] = j for j < n, then the rows D[0..nd) repeated: pool[n + q] = D[q % nd]
+__global__ void pool_kernel(long n, const int *D, int nd, long S, int *pool)
+{
+    for (long j = blockIdx.x * (long)blockDim.x + threadIdx.x; j < S; j += (long)gridDim.x * blockDim.x)
+        pool[j] = j < n ? (int)j : D[(j - n) % nd];
+}
+
+int blocks_for(long n, int num_sms)
+{
+    return (int)std::max(1L, std::min((n + 255) / 256, 8L * num_sms));
+}
+
+}  // namespace
+
 extern "C" {
 
 gw_status gw_mlp_num_params(int n_in, int hidden, size_t *n)
@@ -758,16 +822,114 @@ gw_status gw_mlp_train_step(gw_mlp *m, const float *X, const float *T, const int
         return mfail(m, GW_E_INVALID, "gw_mlp_train_step: null pointer or batch outside [1, max_batch]");
     if (!(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(adam_eps >= 0))
         return mfail(m, GW_E_INVALID, "gw_mlp_train_step: bad optimiser constants");
-    MLP_CUDA(loss_grad(m, X, T, rows, batch, loss_accum), "gw_mlp_train_step");
-    m->step += 1;
-    m->tiled = false;
-    const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
-    const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
-    adam_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(
-        m->theta, m->theta16, m->grad, m->m, m->v, m->P, (float)lr, (float)beta1, (float)beta2, (float)c1, (float)c2,
-        (float)adam_eps);
+    return train_step(m, X, T, rows, batch, lr, beta1, beta2, adam_eps, loss_accum);
+}
+
+gw_status gw_corr_train(gw_mlp *m, const float *X, const float *T, long n, const gw_corr_train_opts *o,
+                        float *losses)
+{
+    MLP_TRY(check_mlp(m));
+    if (!X || !T || !o || !losses || n < 1 || n > 0x7FFFFFFFL)
+        return mfail(m, GW_E_INVALID, "gw_corr_train: null pointer or n outside [1, 2^31)");
+    if (o->epochs < 1 || o->batch < 1 || o->batch > m->max_batch || o->diag_repeat < 1 ||
+        o->diag_feature >= m->n_in)
+        return mfail(m, GW_E_INVALID, "gw_corr_train: epochs, batch, diag_repeat or diag_feature out of range");
+    if (!(o->lr > 0) || !(o->lr_final >= 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) ||
+        !(o->adam_eps >= 0))
+        return mfail(m, GW_E_INVALID, "gw_corr_train: bad optimiser constants");
+    MLP_CUDA(cudaSetDevice(m->device), "gw_corr_train device");
+    cudaStream_t s = m->stream;
+    // device scratch of this call: the pool and its sorted copy, the sort keys, the diagonal rows
+    int *idx = nullptr, *D = nullptr, *pool = nullptr, *order = nullptr, *nd_d = nullptr;
+    unsigned char *flags = nullptr;
+    unsigned long long *keys = nullptr, *keys_sorted = nullptr;
+    float *acc = nullptr;
+    void *tmp = nullptr;
+    gw_status st = GW_OK;
+    auto release = [&]() {
+        cudaFree(idx);
+        cudaFree(D);
+        cudaFree(pool);
+        cudaFree(order);
+        cudaFree(nd_d);
+        cudaFree(flags);
+        cudaFree(keys);
+        cudaFree(keys_sorted);
+        cudaFree(acc);
+        cudaFree(tmp);
+    };
+#define TRAIN_CUDA(call, where)                  \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) {                 \
+            st = mcuda(m, e_, where);            \
+            release();                           \
+            return st;                           \
+        }                                        \
+    } while (0)
+    // diagonal rows (feature diag_feature set), ascending
+    int nd = 0;
+    if (o->diag_repeat > 1 && o->diag_feature >= 0) {
+        size_t tb = 0;
+        TRAIN_CUDA(cudaMalloc(&idx, n * sizeof(int)), "gw_corr_train rows");
+        TRAIN_CUDA(cudaMalloc(&D, n * sizeof(int)), "gw_corr_train diagonal rows");
+        TRAIN_CUDA(cudaMalloc(&flags, n), "gw_corr_train flags");
+        TRAIN_CUDA(cudaMalloc(&nd_d, sizeof(int)), "gw_corr_train count");
+        diag_flags_kernel<<<blocks_for(n, m->num_sms), 256, 0, s>>>(X, n, m->n_in, o->diag_feature, flags, idx);
+        gw::count_launches(1);
+        TRAIN_CUDA(cub::DeviceSelect::Flagged(nullptr, tb, idx, flags, D, nd_d, (int)n, s), "gw_corr_train select");
+        TRAIN_CUDA(cudaMalloc(&tmp, tb), "gw_corr_train select scratch");
+        TRAIN_CUDA(cub::DeviceSelect::Flagged(tmp, tb, idx, flags, D, nd_d, (int)n, s), "gw_corr_train select");
+        TRAIN_CUDA(cudaMemcpyAsync(&nd, nd_d, sizeof(int), cudaMemcpyDeviceToHost, s), "gw_corr_train count");
+        TRAIN_CUDA(cudaStreamSynchronize(s), "gw_corr_train count");
+        cudaFree(tmp);
+        tmp = nullptr;
+    }
+    const long S = n + (long)(nd > 0 ? o->diag_repeat - 1 : 0) * nd;
+    if (S > 0x7FFFFFFFL) {
+        release();
+        return mfail(m, GW_E_INVALID, "gw_corr_train: pool of %ld rows exceeds 2^31", S);
+    }
+    const long steps = S / o->batch;
+    if (steps < 1) {
+        release();
+        return mfail(m, GW_E_INVALID, "gw_corr_train: fewer rows than one minibatch");
+    }
+    size_t sb = 0;
+    TRAIN_CUDA(cudaMalloc(&pool, S * sizeof(int)), "gw_corr_train pool");
+    TRAIN_CUDA(cudaMalloc(&order, S * sizeof(int)), "gw_corr_train order");
+    TRAIN_CUDA(cudaMalloc(&keys, S * sizeof(unsigned long long)), "gw_corr_train keys");
+    TRAIN_CUDA(cudaMalloc(&keys_sorted, S * sizeof(unsigned long long)), "gw_corr_train keys");
+    TRAIN_CUDA(cudaMalloc(&acc, (size_t)o->epochs * sizeof(float)), "gw_corr_train losses");
+    TRAIN_CUDA(cudaMemsetAsync(acc, 0, (size_t)o->epochs * sizeof(float), s), "gw_corr_train losses");
+    pool_kernel<<<blocks_for(S, m->num_sms), 256, 0, s>>>(n, D, nd, S, pool);
     gw::count_launches(1);
-    MLP_CUDA(cudaGetLastError(), "gw_mlp_train_step adam");
+    TRAIN_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sb, keys, keys_sorted, pool, order, (int)S, 0, 64, s),
+               "gw_corr_train sort");
+    TRAIN_CUDA(cudaMalloc(&tmp, sb), "gw_corr_train sort scratch");
+    const long total = (long)o->epochs * steps;
+    long t = 0;
+    for (int e = 0; e < o->epochs; ++e) {
+        order_keys_kernel<<<blocks_for(S, m->num_sms), 256, 0, s>>>(o->seed, e, S, keys);
+        gw::count_launches(1);
+        TRAIN_CUDA(cub::DeviceRadixSort::SortPairs(tmp, sb, keys, keys_sorted, pool, order, (int)S, 0, 64, s),
+                   "gw_corr_train sort");
+        for (long i = 0; i < steps; ++i, ++t) {
+            const double lr_t = o->lr_final + 0.5 * (o->lr - o->lr_final) * (1.0 + std::cos(M_PI * (double)t / total));
+            st = train_step(m, X, T, order + i * o->batch, o->batch, lr_t, o->beta1, o->beta2, o->adam_eps, acc + e);
+            if (st != GW_OK) {
+                release();
+                return st;
+            }
+        }
+    }
+    std::vector<float> h(o->epochs);
+    TRAIN_CUDA(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s), "gw_corr_train losses");
+    TRAIN_CUDA(cudaStreamSynchronize(s), "gw_corr_train sync");
+#undef TRAIN_CUDA
+    for (int e = 0; e < o->epochs; ++e)
+        losses[e] = h[e] / (float)steps;
+    release();
     return GW_OK;
 }
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
     "gw_set_herk_kernel": (_i, [_vp, _i]),
     "gw_corr_closure": (_i, [_vp, _i, _c.POINTER(_c.c_double), _i, _vp]),
+    "gw_corr_train": (_i, [_vp, _vp, _vp, _c.c_long, _vp, _c.POINTER(_c.c_float)]),
     "gw_set_error_target": (_i, [_vp, ctypes.c_double]),
     "gw_reset_times": (_i, [_vp]),
     "gw_get_stats": (_i, [_vp, _c.POINTER(_c.c_double)]),
@@ -542,6 +543,16 @@ class Mlp:
         self._check(lib().gw_mlp_train_step(self._h, _ptr(X), _ptr(T), _ptr(rows), int(rows.shape[0]), float(lr),
                                             float(beta1), float(beta2), float(eps), _ptr(loss_accum)))
 
+    def train_corr(self, X, T, epochs, batch, lr, lr_final=1e-5, seed=0, diag_repeat=1, diag_feature=7,
+                   beta1=0.9, beta2=0.999, eps=1e-8):
+        """Passes of Adam over minibatches of (X, T) in the library's order (gw_corr_train);
+        returns the mean loss of each pass."""
+        o = CorrTrainOpts(int(epochs), int(batch), float(lr), float(lr_final), float(beta1), float(beta2), float(eps),
+                          int(seed), int(diag_repeat), int(diag_feature))
+        losses = (ctypes.c_float * int(epochs))()
+        self._check(lib().gw_corr_train(self._h, _ptr(X), _ptr(T), int(X.shape[0]), ctypes.byref(o), losses))
+        return [float(x) for x in losses]
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().gw_mlp_destroy(self._h)
@@ -558,6 +569,14 @@ class Mlp:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class CorrTrainOpts(ctypes.Structure):
+    """gw_corr_train_opts of include/gw.h."""
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("lr_final", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("adam_eps", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("diag_repeat", ctypes.c_int),
+                ("diag_feature", ctypes.c_int)]
 
 
 def corr_weight_ratio(E_eV, nv, nc_keep, device=0, stream=None):

@@ -1,8 +1,8 @@
 """Learned truncation correction of P~(G,G'): training data from the plain method and the
 training loop, driving the library's kernels (gw_corr_*, gw_mlp_*).
 
-The arithmetic runs in the library.  This module calls the C ABI in order, draws the minibatch
-order, and sets the learning-rate schedule:
+The arithmetic, the training loop, the minibatch order and the learning-rate schedule run in the
+library.  This module calls the C ABI in order:
 
 1. For every seeded system, run the plain method twice: P~ with the nc_keep lowest unoccupied
    states, and P~ with all of them.  The sum over unoccupied states c is the one in
@@ -12,14 +12,12 @@ order, and sets the learning-rate schedule:
 2. Compute the per-entry features of the truncated P~ (with dP~) and the targets
    s (P~_all - P~_keep - dP~), what the closure estimate leaves (gw_corr_features,
    gw_corr_targets).
-3. Run Adam on minibatches drawn without replacement from all systems' entries
-   (gw_mlp_train_step), with a cosine learning-rate decay.
+3. Run Adam on minibatches drawn without replacement from all systems' entries, with a cosine
+   learning-rate decay (gw_corr_train).
 4. Inference: the closure estimate and the features of a new truncated P~, the forward pass,
    then add both into P~ (gw_corr_apply).  eps and eps^-1 then follow as for any P~.
 """
 from __future__ import annotations
-
-import math
 
 import numpy as np
 
@@ -74,37 +72,13 @@ def training_set(ctx, make_states, seeds, nv, nc_keep, dims, gcut, precision="fp
 
 def train(mlp, X, T, epochs=4, batch=8192, lr=1e-3, lr_final=1e-5, seed=0, beta1=0.9, beta2=0.999, eps=1e-8,
           diag_repeat=1):
-    """Adam over `epochs` passes of minibatches without replacement (the last ragged minibatch of
-    each pass is dropped).  Learning rate: cosine decay from lr to lr_final.  Returns the mean
-    loss of each pass.
-
-    diag_repeat > 1 puts every diagonal entry (feature 7 set) that many times into the pool a
-    pass draws from.  Diagonal entries carry most of the correction's norm but are 1 in ng(ng+1)/2
-    of the entries, so without this their fit is left to few, noisy updates."""
-    import torch
-
-    dev = X.device
-    pool = torch.arange(X.shape[0], dtype=torch.int64, device=dev)
-    if diag_repeat > 1:
-        diag = torch.nonzero(X[:, 7] == 1).flatten()
-        pool = torch.cat([pool, diag.repeat(diag_repeat - 1)])
-    S = pool.shape[0]
-    steps = S // batch
-    if steps < 1:
-        raise ValueError("fewer samples than one minibatch")
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(int(seed))
-    acc = torch.zeros(1, dtype=torch.float32, device=dev)
-    total, t, losses = epochs * steps, 0, []
-    for _ in range(epochs):
-        perm = pool[torch.randperm(S, generator=gen, device=dev)].to(torch.int32)
-        acc.zero_()
-        for i in range(steps):
-            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * t / total))
-            mlp.train_step(X, T, perm[i * batch:(i + 1) * batch], lr_t, beta1, beta2, eps, loss_accum=acc)
-            t += 1
-        losses.append(float(acc.item()) / steps)
-    return losses
+    """Adam over `epochs` passes of minibatches without replacement, cosine learning-rate decay from
+    lr to lr_final, the diagonal entries (feature 7 set) diag_repeat times in the pool a pass draws
+    from (gw_corr_train: the loop, the order and the schedule run in the library).  Diagonal
+    entries carry most of the correction's norm but are 1 in ng(ng+1)/2 of the entries, so without
+    the repeats their fit is left to few, noisy updates.  Returns the mean loss of each pass."""
+    return mlp.train_corr(X, T, epochs, batch, lr, lr_final=lr_final, seed=seed, diag_repeat=diag_repeat,
+                          diag_feature=7, beta1=beta1, beta2=beta2, eps=eps)
 
 
 def correct(mlp, PG_keep, gvec, gcut, E_eV, nv, nc_keep, clos, out=None, tensor_cores=True):

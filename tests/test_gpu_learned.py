@@ -13,6 +13,8 @@
   the learned form must stay within 2 % of it, beat the diagonal shift alone and gain over
   truncation alone; the full sum is itself checked against the FP64 oracle at sampled entries.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -228,3 +230,53 @@ def test_learned_correction_gain_24cubed():
     assert e_full < e_clos                  # the closure estimate beats the diagonal shift alone
     assert e_mlp < e_clos
     assert e_mlp <= 1.02 * e_full
+
+
+def _order_keys(seed, e, S):
+    """The library's minibatch keys, written out with numpy's wrapping uint64 arithmetic."""
+    u = np.uint64
+    base = (np.array([seed], dtype=u) * u(0x9E3779B97F4A7C15) + np.array([e + 1], dtype=u) * u(0xD1B54A32D192ED03))
+    z = base + np.arange(S, dtype=u)
+    z ^= z >> u(30)
+    z *= u(0xBF58476D1CE4E5B9)
+    z ^= z >> u(27)
+    z *= u(0x94D049BB133111EB)
+    z ^= z >> u(31)
+    return z
+
+
+def test_corr_train_equals_the_loop_it_replaces():
+    """gw_corr_train against the same loop driven from Python through gw_mlp_train_step: the pool
+    (all rows, then the diagonal rows three more times), each pass in the order of the documented
+    keys, the cosine rate, the per-pass loss.  Same kernels in the same order: parameters and
+    losses agree bit for bit."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(31)
+    n, batch, epochs, rep, seed = 5000, 256, 3, 4, 12345
+    X = rng.standard_normal((n, N_IN)).astype(np.float32)
+    X[:, 7] = (rng.random(n) < 0.05).astype(np.float32)           # diagonal flags
+    T = rng.standard_normal((n, 2)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+    th = _theta(17)
+    with gw.Mlp(N_IN, HID, max_batch=batch, device=0) as a, gw.Mlp(N_IN, HID, max_batch=batch, device=0) as b:
+        a.set_params(th)
+        b.set_params(th)
+        la = a.train_corr(Xd, Td, epochs, batch, 2e-3, lr_final=1e-4, seed=seed, diag_repeat=rep)
+        diag = np.flatnonzero(X[:, 7] == 1)
+        pool = np.concatenate([np.arange(n)] + [diag] * (rep - 1)).astype(np.int32)
+        steps = len(pool) // batch
+        total, t, lb = epochs * steps, 0, []
+        acc = torch.zeros(1, dtype=torch.float32, device=dev)
+        for e in range(epochs):
+            order = pool[np.argsort(_order_keys(seed, e, len(pool)), kind="stable")]
+            rows = torch.from_numpy(order).to(dev)
+            acc.zero_()
+            for i in range(steps):
+                lr_t = 1e-4 + 0.5 * (2e-3 - 1e-4) * (1.0 + math.cos(math.pi * t / total))
+                b.train_step(Xd, Td, rows[i * batch:(i + 1) * batch], lr_t, loss_accum=acc)
+                t += 1
+            lb.append(float(acc.item()) / steps)
+        pa, pb = a.get_params(), b.get_params()
+    assert np.array_equal(pa, pb)
+    assert np.allclose(la, lb, rtol=1e-6, atol=0)
+    assert la[-1] < la[0]

@@ -67,6 +67,8 @@ def parse_args(argv=None):
                     help="skip the split, batch and learned configurations that the default run appends")
     ap.add_argument("--herk-kernel", choices=["single", "pair"], default=HERK_KERNEL,
                     help="kernel of the 16-bit rank-k update")
+    ap.add_argument("--transform", choices=["two_kernel", "fused"], default="two_kernel",
+                    help="kernel of the sphere transforms")
     ap.add_argument("--extra-steps", type=int, default=3,
                     help="timed steps of each appended configuration (after --warmup untimed ones)")
     ap.add_argument("--inv", choices=["cholesky", "newton_tc"], default=INV_METHOD,
@@ -280,6 +282,7 @@ def run_gw(args):
     stream = torch.cuda.current_stream(dev)
     ctx = gw.Context(local, stream)
     ctx.set_herk_kernel(args.herk_kernel)
+    ctx.set_transform_kernel(args.transform)
     target = ERROR_TARGET.get(args.workload)
     if target:
         ctx.set_error_target(target)

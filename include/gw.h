@@ -405,6 +405,21 @@ enum { GW_HERK_SINGLE = 0, GW_HERK_PAIR = 1 };
 GW_API gw_status gw_set_herk_kernel(gw_ctx *ctx, int kind);
 
 /*
+ * Kernel of the sphere transforms (the two FFT phases of Sec. 4.1, pruned to the eps sphere) in
+ * gw_P_to_G, gw_build_PG and the batch:
+ *   GW_TRANSFORM_TWO_KERNEL (default) planes transformed over j3 and j2 into a workspace, then j1 per
+ *                           row
+ *   GW_TRANSFORM_FUSED      one kernel per pass: each row is streamed plane by plane into shared
+ *                           memory by bulk copies and transformed axis by axis (j1, j2, j3) there,
+ *                           reading P from HBM exactly once; used where N_r and n2 n3 are even and
+ *                           max |m| <= 8, else the two-kernel form.  Measured slower at 24^3
+ *                           (0.96 against 0.83 ms for the row pass; equal on the g-space route)
+ * Both give the same sums up to FP32 rounding.  GW_E_INVALID for another value.
+ */
+enum { GW_TRANSFORM_TWO_KERNEL = 0, GW_TRANSFORM_FUSED = 1 };
+GW_API gw_status gw_set_transform_kernel(gw_ctx *ctx, int kind);
+
+/*
  * Error target of the 16-bit rank-k update, as the relative Frobenius error of P~ against FP64
  * (0 = use the window of gw_set_herk_window, the default).  Each gw_build_P / gw_build_PG then
  * takes the longest window of 16, 8, 6, 5, 4, 3, 2, 1 chunks whose predicted error x 1.25 meets

@@ -380,6 +380,11 @@ gw_status build_plan(Ctx &c, int gcut)
     }
     c.ng = ng;
     GW_TRY(upload_sqrt_v(c));
+    // the one-kernel transform's plan, where the sphere and grid allow it
+    if (c.fplan.build(n, g)) {
+        GW_TRY(ensure(c, c.d_fplan, c.cap_fplan, c.fplan.device_bytes(), "transform plan"));
+        GW_CUDA(c.fplan.upload(c.d_fplan, c.stream), "transform plan upload");
+    }
     c.gcut = gcut;
     c.ng = ng;
     return GW_OK;
@@ -600,6 +605,7 @@ void Ctx::release()
     dfree(d_scal);
     dfree(d_tcw);
     dfree(d_csw);
+    dfree(d_fplan);
     dfree(d_cw);
     dfree(d_cgvec);
     dfree(d_cwork);
@@ -999,6 +1005,32 @@ gw_status finish_PG(Ctx &c, cudaStream_t s)
     return GW_OK;
 }
 
+// Sphere transform of rows of X: the one-kernel form where the plan and the alignment allow it
+// (and the context has not asked for the two-kernel form), else the two-kernel form.  With sw set,
+// the rows are the pair densities conj(psi_v) psi_c sw[k] of the states X = psi (c from state c0).
+cudaError_t transform_rows(Ctx &c, const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, bool negexp,
+                           cudaStream_t s, const float *sw = nullptr, int nv = 0, int nc = 1, int c0 = -1)
+{
+    if (c.transform_kind == GW_TRANSFORM_FUSED && c.fplan.ok) {
+        const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
+        const cudaError_t e = launch_dft_fused(X, ldx, rows, Y, ldy, c.fplan, negexp, sw, nv, nc, c0 < 0 ? nv : c0,
+                                               c.d_err, wait_ns, s);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
+    if (sw)
+        return launch_dft_pairs_ws(X, ldx, sw, nv, nc, Y, ldy, c.plan, c.d_dftw, s, negexp, c0);
+    return launch_dft_rows_ws(X, ldx, rows, Y, ldy, c.plan, c.d_dftw, s, negexp);
+}
+
+gw_status gw_set_transform_kernel(gw_ctx *h, int kind)
+{
+    if (!h || (kind != GW_TRANSFORM_TWO_KERNEL && kind != GW_TRANSFORM_FUSED))
+        return GW_E_INVALID;
+    h->c.transform_kind = kind;
+    return GW_OK;
+}
+
 gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng, void *PG_out)
 {
     if (!h)
@@ -1025,11 +1057,11 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
     c.PG_ready = c.eps_ready = false;
     record(c, 3);
     // Q[r'][G] = sum_r P[r'][r] e^{+iG.r} = conj(P^(G, r')) since P is Hermitian
-    GW_CUDA(launch_dft_rows_ws(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, c.d_dftw, s), "row transform");
+    GW_CUDA(transform_rows(c, c.d_P, c.nr, c.nr, c.d_Q, ng, false, s), "row transform");
     record(c, 4);
     // QT[G][r'] = conj(Q[r'][G]) = P^(G, r');  P~[G][G'] = sum_r' QT[G][r'] e^{+iG'.r'}
     GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
-    GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
+    GW_CUDA(transform_rows(c, c.d_QT, c.nr, ng, c.d_PG, ng, false, s), "column transform");
     GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
     GW_TRY(finish_PG(c, s));
     record(c, 5);
@@ -1104,7 +1136,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
     record(c, 1);
     record(c, 3);
-    cudaError_t fe = launch_dft_pairs_ws(c.d_psi, c.nr, c.d_sw, c.nv, c.nc, c.d_Q, ng, c.plan, c.d_dftw, s, true);
+    cudaError_t fe = transform_rows(c, c.d_psi, c.nr, k, c.d_Q, ng, true, s, c.d_sw, c.nv, c.nc);
     if (fe == cudaErrorNotSupported) {
         GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
         float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
@@ -1214,7 +1246,7 @@ gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_o
     // projector term: matrix elements M_vn(G) sqrt(-W_v / (N_r - n_in)) for every loaded n, then the
     // N_g x N_g rank-k update (which returns minus the sum of the outer products) into `out`
     GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
-    cudaError_t fe = launch_dft_pairs_ws(c.d_psi, c.nr, c.d_csw, c.nv, c.nb, c.d_Q, ng, c.plan, c.d_dftw, s, true, 0);
+    cudaError_t fe = transform_rows(c, c.d_psi, c.nr, k2, c.d_Q, ng, true, s, c.d_csw, c.nv, c.nb, 0);
     if (fe == cudaErrorNotSupported)
         return fail(c, GW_E_UNSUPPORTED, "the closure needs the plane transform kernel for this grid");
     GW_CUDA(fe, "closure matrix elements");
@@ -1736,9 +1768,9 @@ gw_status batch_enqueue(gw_batch &b)
         Ctx &c = h->c;
         const int ng = c.ng;
         cudaStream_t s = b.stream;
-        GW_CUDA(launch_dft_rows_ws(c.d_P, c.nr, c.nr, c.d_Q, ng, c.plan, c.d_dftw, s), "row transform");
+        GW_CUDA(transform_rows(c, c.d_P, c.nr, c.nr, c.d_Q, ng, false, s), "row transform");
         GW_CUDA(launch_conj_transpose(c.d_Q, c.nr, ng, c.d_QT, s), "conjugate transpose");
-        GW_CUDA(launch_dft_rows_ws(c.d_QT, c.nr, ng, c.d_PG, ng, c.plan, c.d_dftw, s), "column transform");
+        GW_CUDA(transform_rows(c, c.d_QT, c.nr, ng, c.d_PG, ng, false, s), "column transform");
         GW_CUDA(launch_hermitize(c.d_PG, ng, s), "Hermitian part of P~");
         GW_CUDA(launch_eps_build(c.d_PG, c.d_sv, ng, c.d_eps, s), "eps build");
         if (b.inv_method == GW_INV_NEWTON_TC) {

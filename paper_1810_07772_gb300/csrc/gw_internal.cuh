@@ -3,6 +3,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -49,6 +50,22 @@ struct DftPlan {
     int4 *pair1;   // [np1] (disk index, m1 >= 0, sphere index of m1, of -m1 or -1 at m1 = 0)
     float2 *tw;    // [n1 + n2 + n3] exp(+2 pi i t / n_a), FP64-derived (device)
     float2 *twc;   // the same table conjugated: exp(-2 pi i t / n_a)
+};
+
+// Plan of the one-kernel sphere transform (k_dft_fused.cu): tables of the sphere's m1, (m1, m2)
+// disk and m3 ranges, and per-axis twiddles, for grids whose planes and rows are 16-byte multiples
+// and spheres with max |m| <= 8.
+struct FusedPlan {
+    int n[3] = {0, 0, 0};
+    int M = 0, ng = 0, cd = 0;
+    std::vector<int> tab;     // integer tables (see k_dft_fused.cu)
+    std::vector<float2> tw;   // (cos, sin) of 2 pi m j / n_a, m <= M, per axis
+    int *d_tab = nullptr;     // device copies (inside a buffer the caller owns)
+    float2 *d_tw = nullptr;
+    bool ok = false;
+    bool build(const int n[3], const std::vector<std::array<int, 3>> &sphere);
+    size_t device_bytes() const;
+    cudaError_t upload(void *dev, cudaStream_t s);
 };
 
 // Plasmon-pole workspace pieces (k_pp.cu) for N_g = ng and block b <= 40.
@@ -101,6 +118,10 @@ struct Ctx {
     std::vector<int> gvec;          // host [ng*3]
     DftPlan plan = {};
     int *d_plan_mem = nullptr;
+    FusedPlan fplan;                // the one-kernel sphere transform (fplan.ok = usable)
+    int transform_kind = GW_TRANSFORM_TWO_KERNEL;
+    void *d_fplan = nullptr;
+    size_t cap_fplan = 0;
     float2 *d_Q = nullptr;          // [nr][ng]  row transform
     float2 *d_QT = nullptr;         // [ng][nr]  conj-transposed
     float2 *d_PG = nullptr;         // [ng][ng]
@@ -265,6 +286,16 @@ cudaError_t launch_mlp_tc_forward(const float *X, int n, int n_in, const __half 
                                   const uint8_t *W2t, const float *b2, const uint8_t *W3t, const float *b3,
                                   const __half *W4, const float *b4, uint8_t *H2, float *Y, int num_sms,
                                   uint32_t *err, uint64_t wait_ns, cudaStream_t s);
+
+// k_dft_fused.cu: the whole sphere transform of a row in one kernel (planes streamed by bulk
+// copies, stages j1 -> m1, j2 -> m2, j3 -> m3 in shared memory), for grids whose planes and rows
+// are 16-byte multiples and spheres with max |m| <= 8.
+// rows of X [rows][ldx] (sw == nullptr), or the pair densities conj(psi_v) psi_c sw[k] of the states
+// X = psi [nb][ldx] (k = v nc + c, psi_c at state c0 + c), to Y [rows][ldy] on the sphere.
+// cudaErrorNotSupported (nothing launched) where the plan or the alignment does not allow it.
+cudaError_t launch_dft_fused(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const FusedPlan &p,
+                             bool negative_exponent, const float *sw, int nv, int nc, int c0, uint32_t *err,
+                             uint64_t wait_ns, cudaStream_t s);
 
 // k_dft.cu
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);

@@ -20,6 +20,7 @@ GW_OK, GW_E_INVALID, GW_E_NOMEM, GW_E_CUDA, GW_E_NOT_READY, GW_E_NUMERIC, GW_E_T
 PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
 INV_METHOD = {"cholesky": 0, "newton": 1, "newton_tc": 2}
 HERK_KERNEL = {"single": 0, "pair": 1}
+TRANSFORM_KERNEL = {"two_kernel": 0, "fused": 1}
 ZGEMM_MODE = {"fp16x3": 0, "slices": 1}
 GW_C64, GW_C128 = 0, 1
 BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5, "psiT": 6}
@@ -52,6 +53,7 @@ SIGNATURES = {
     "gw_set_q": (_i, [_vp, _c.POINTER(_d)]),
     "gw_set_herk_window": (_i, [_vp, _i, _i]),
     "gw_set_herk_kernel": (_i, [_vp, _i]),
+    "gw_set_transform_kernel": (_i, [_vp, _i]),
     "gw_corr_closure": (_i, [_vp, _i, _c.POINTER(_c.c_double), _i, _vp]),
     "gw_corr_train": (_i, [_vp, _vp, _vp, _c.c_long, _vp, _c.POINTER(_c.c_float)]),
     "gw_set_error_target": (_i, [_vp, ctypes.c_double]),
@@ -343,6 +345,12 @@ class Context:
         axes = [np.arange(-(n // 2), n - n // 2) ** 2 for n in self.dims]
         m2 = axes[0][:, None, None] + axes[1][None, :, None] + axes[2][None, None, :]
         return int(np.count_nonzero(m2 <= gcut))
+
+    def set_transform_kernel(self, kind):
+        """Sphere transforms: "fused" (one kernel per pass, the default) or "two_kernel"
+        (gw_set_transform_kernel)."""
+        self._check(lib().gw_set_transform_kernel(self._h, TRANSFORM_KERNEL[kind] if isinstance(kind, str)
+                                                  else int(kind)))
 
     def set_herk_kernel(self, kind):
         """Kernel of the 16-bit r-space update: "single" (one CTA per tile, the default) or "pair"

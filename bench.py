@@ -840,7 +840,7 @@ def section_learned(args, steps):
                          "samples_per_s": n_train / (train_ms * 1e-3),
                          "tflops": n_train * train_flop / (train_ms * 1e-3) / 1e12,
                          "data_generation_s": gen_s},
-            "roofline": {"bound": "tensor", "kernel": "mlp_tc_l12_kernel + mlp_tc_l34_kernel (tcgen05 kind::f16, "
+            "roofline": {"bound": "tensor", "kernel": "mlp_tc_pair_kernel (tcgen05 kind::f16 cta_group::2, "
                                                       "network inference per system)",
                          "achieved": Xs.shape[0] * fwd_flop / (infer_ms * 1e-3) / 1e12, "peak": tc_peak,
                          "unit": "TFLOP/s", "frac": Xs.shape[0] * fwd_flop / (infer_ms * 1e-3) / 1e12 / tc_peak,

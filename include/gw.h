@@ -491,7 +491,7 @@ GW_API gw_status gw_mlp_num_params(int n_in, int hidden, size_t *n);
  *              1..2^22
  *   stream     cudaStream_t for every call on the handle (NULL = legacy default stream)
  * Device memory: 4 P floats, P halves, 5 max_batch x hidden floats, and a split-K workspace
- * of 64 x hidden x (hidden + 1) floats. */
+ * of 64 x hidden x (hidden + 1) floats; gw_mlp_infer adds 272 KB of tiled weights. */
 GW_API gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_batch, void *stream);
 GW_API gw_status gw_mlp_destroy(gw_mlp *m);
 GW_API gw_status gw_mlp_last_error(gw_mlp *m, char *buf, size_t n);
@@ -504,12 +504,15 @@ GW_API gw_status gw_mlp_get_params(gw_mlp *m, float *theta, int on_device);
 /* Inference: Y[n][2] = network(X[n][n_in]), in chunks of max_batch rows. */
 GW_API gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y);
 
-/* Inference on the tensor cores: the same network with FP16 weights and FP32 accumulation, and
- * the activations that enter the two 256 x 256 products (outputs of layers 1 and 2) rounded to
- * FP16 - they are FP16 operands of tcgen05.mma kind::f16.  Layer 1 (n_in inputs) and the output
- * layer run on CUDA cores inside the same two kernels.  Requires hidden = 256 and n_in <= 16
- * (else GW_E_UNSUPPORTED).  Asynchronous; device-side waits are bounded and report through
- * gw_mlp_check.  Y[n][2] as gw_mlp_forward. */
+/* Inference on the tensor cores: the same network with FP16 weights and FP32 accumulation in one
+ * kernel on CTA pairs (tcgen05.mma cta_group::2, each CTA holding half of every weight matrix).
+ * Layer 1 multiplies the inputs split into FP16 hi and lo parts (x = hi + lo to about 2^-22), so
+ * it keeps FP32 accuracy; the outputs of layers 1 and 2 are rounded to FP16 (the operands of the
+ * two 256 x 256 products); tanh is the hardware approximation (tanh.approx.f32, relative error
+ * about 2^-11); the output layer runs in FP32.  Requires hidden = 256, n_in <= 16 and |X| < 65504
+ * (else GW_E_UNSUPPORTED for the first two).  Any n (no chunking: the kernel walks 256-row tiles).
+ * Asynchronous; device-side waits are bounded and report through gw_mlp_check.  Y[n][2] as
+ * gw_mlp_forward. */
 GW_API gw_status gw_mlp_infer(gw_mlp *m, const float *X, long n, float *Y);
 
 /* Synchronise the handle's stream and return the status of its tensor-core kernels. */

@@ -280,12 +280,14 @@ cudaError_t launch_herk16p(const HerkJob *jobs, const int4 *tiles, int n_tiles, 
                            uint64_t wait_ns, int W, int L, cudaStream_t s);
 
 // k_mlp_tc.cu: tensor-core inference of the correction network (hidden width 256, n_in <= 16)
-size_t mlp_tc_h2_bytes(int rows);
-cudaError_t launch_mlp_tile_weights(const __half *W, uint8_t *Wt, cudaStream_t s);
-cudaError_t launch_mlp_tc_forward(const float *X, int n, int n_in, const __half *W1, const float *b1,
-                                  const uint8_t *W2t, const float *b2, const uint8_t *W3t, const float *b3,
-                                  const __half *W4, const float *b4, uint8_t *H2, float *Y, int num_sms,
-                                  uint32_t *err, uint64_t wait_ns, cudaStream_t s);
+// on CTA pairs; the weights go through launch_mlp_tile_weights into a buffer of
+// mlp_tc_weights_bytes() first.
+size_t mlp_tc_weights_bytes();
+cudaError_t launch_mlp_tile_weights(const __half *W1, int n_in, const __half *W2, const __half *W3, uint8_t *Wt,
+                                    cudaStream_t s);
+cudaError_t launch_mlp_tc_forward(const float *X, long n, int n_in, const uint8_t *Wt, const float *b1,
+                                  const float *b2, const float *b3, const __half *W4, const float *b4, float *Y,
+                                  int num_sms, uint32_t *err, uint64_t wait_ns, cudaStream_t s);
 
 // k_dft_fused.cu: the whole sphere transform of a row in one kernel (planes streamed by bulk
 // copies, stages j1 -> m1, j2 -> m2, j3 -> m3 in shared memory), for grids whose planes and rows

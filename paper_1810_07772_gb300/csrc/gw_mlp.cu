@@ -358,9 +358,9 @@ struct gw_mlp {
     __half *theta16 = nullptr;
     float *H[3] = {}, *Da = nullptr, *Db = nullptr, *D4 = nullptr, *Y = nullptr, *part = nullptr;
     long step = 0;
-    // tensor-core inference: W2, W3 in the operand layout (valid while tiled == true), the FP16
-    // hidden layer between its two kernels, and a status word for their bounded waits
-    uint8_t *W2t = nullptr, *W3t = nullptr, *H2 = nullptr;
+    // tensor-core inference: W1, W2, W3 in the operand layout (valid while tiled == true) and a
+    // status word for the kernel's bounded waits
+    uint8_t *Wt = nullptr;
     bool tiled = false;
     uint32_t *d_err = nullptr;
     std::string last_error;
@@ -690,7 +690,7 @@ gw_status gw_mlp_destroy(gw_mlp *m)
     else
         cudaDeviceSynchronize();
     void *ptrs[] = {m->theta, m->grad, m->m, m->v, m->theta16, m->H[0], m->H[1], m->H[2],
-                    m->Da,    m->Db,   m->D4, m->Y, m->part,  m->W2t, m->W3t, m->H2, m->d_err};
+                    m->Da,    m->Db,   m->D4, m->Y, m->part,  m->Wt, m->d_err};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -763,27 +763,22 @@ gw_status gw_mlp_infer(gw_mlp *m, const float *X, long n, float *Y)
         return mfail(m, GW_E_UNSUPPORTED, "gw_mlp_infer: the tensor-core path takes hidden = 256 and n_in <= 16");
     if (n == 0)
         return GW_OK;
-    if (!m->W2t) {
-        MLP_CUDA(cudaMalloc(&m->W2t, 256 * 256 * 2), "gw_mlp_infer weights");
-        MLP_CUDA(cudaMalloc(&m->W3t, 256 * 256 * 2), "gw_mlp_infer weights");
-        MLP_CUDA(cudaMalloc(&m->H2, gw::mlp_tc_h2_bytes(m->max_batch)), "gw_mlp_infer hidden layer");
+    if (!m->Wt) {
+        MLP_CUDA(cudaMalloc(&m->Wt, gw::mlp_tc_weights_bytes()), "gw_mlp_infer weights");
         MLP_CUDA(cudaMalloc(&m->d_err, sizeof(uint32_t)), "gw_mlp_infer status");
         MLP_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(uint32_t), m->stream), "gw_mlp_infer status");
     }
     if (!m->tiled) {
-        MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[1], m->W2t, m->stream), "gw_mlp_infer tile W2");
-        MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[2], m->W3t, m->stream), "gw_mlp_infer tile W3");
+        MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[0], m->n_in, m->theta16 + m->off_w[1],
+                                             m->theta16 + m->off_w[2], m->Wt, m->stream),
+                 "gw_mlp_infer tile weights");
         m->tiled = true;
     }
     const uint64_t wait_ns = 2000000000ull;
-    for (long b0 = 0; b0 < n; b0 += m->max_batch) {
-        const int b = (int)std::min<long>(m->max_batch, n - b0);
-        MLP_CUDA(gw::launch_mlp_tc_forward(X + b0 * m->n_in, b, m->n_in, m->theta16 + m->off_w[0], m->theta + m->off_b[0],
-                                       m->W2t, m->theta + m->off_b[1], m->W3t, m->theta + m->off_b[2],
-                                       m->theta16 + m->off_w[3], m->theta + m->off_b[3], m->H2, Y + b0 * NOUT,
+    MLP_CUDA(gw::launch_mlp_tc_forward(X, n, m->n_in, m->Wt, m->theta + m->off_b[0], m->theta + m->off_b[1],
+                                       m->theta + m->off_b[2], m->theta16 + m->off_w[3], m->theta + m->off_b[3], Y,
                                        m->num_sms, m->d_err, wait_ns, m->stream),
-                 "gw_mlp_infer");
-    }
+             "gw_mlp_infer");
     return GW_OK;
 }
 

@@ -75,10 +75,11 @@ def test_gradient_and_forward_match_oracle():
 
 
 def test_tensor_core_inference_matches_oracle():
-    """gw_mlp_infer (tcgen05 kind::f16, FP16 activations into the 256-wide products) against the
-    oracle forward with the same roundings; 1000 rows = several 128-row tiles, a ragged last tile,
-    and three chunks of 384 rows.  Tolerance: FP32 accumulation plus the odd activation that lands
-    on the other side of an FP16 rounding boundary (2^-11 of one term)."""
+    """gw_mlp_infer (tcgen05 kind::f16 on CTA pairs, FP16 activations into the 256-wide products)
+    against the oracle forward with the same FP16 roundings; 1000 rows = several 256-row tiles and
+    a ragged last tile.  Tolerance: the kernel's tanh is the hardware approximation (relative error
+    about 2^-11 per activation, against exact tanh in the oracle), which with the FP16 roundings
+    moves the output by about 1e-4 relative (measured 9.6e-5 on these inputs); 1e-3 bounds it."""
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(13)
     X = rng.standard_normal((1000, N_IN)).astype(np.float32)

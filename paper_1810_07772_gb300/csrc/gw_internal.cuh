@@ -289,6 +289,33 @@ cudaError_t launch_mlp_tc_forward(const float *X, long n, int n_in, const uint8_
                                   const float *b2, const float *b3, const __half *W4, const float *b4, float *Y,
                                   int num_sms, uint32_t *err, uint64_t wait_ns, cudaStream_t s);
 
+// k_mlp_train.cu: tensor-core products of the correction network's training step.  Operands in the
+// three-part BF16 block layout (mlp_pack3_bytes(rows, k) bytes); launch_mlp_pack3 writes an FP32
+// matrix S [R][C] (rows gathered by `rows` if given) as rowop (rows R, k = C) and/or colop (rows
+// C, k = R) and, if colsum is given, the column sums of each 128-row tile to colsum[ceil(R/128)][C].
+// launch_mlp_gemm3: C(m, n) = sum_k A(m, k) B(n, k) (M x N, K), epi 0 = partial products of up to
+// `splits` slices of K at C + z * zstride, 1 = tanh(acc + bias[n]), 2 = acc * (1 - H(m, n)^2);
+// the slice count used goes to *slices_used.
+// launch_mlp_gemm3 with epi 1 or 2 also writes its result (M x N) to rowop (rows M, k = N), colop
+// (rows N, k = M) and its column sums per 128-row tile to colsum, where given.
+// launch_mlp_pack_weights: W1 (hidden x n_in), W2, W3 (hidden x hidden) at w + off[l] into row[l]
+// (rows = outputs) and W2, W3 into col[0], col[1] (rows = inputs), element by element (the
+// padding of these buffers is never written: clear them once).
+struct MlpWeightPack {
+    uint8_t *row[3];
+    uint8_t *col[2];
+    long off[3];
+    int hidden, n_in;
+};
+size_t mlp_pack3_bytes(int rows, int k);
+cudaError_t launch_mlp_pack_weights(const float *w, const MlpWeightPack &p, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_pack3(const float *S, long ld, const int *rows, int R, int C, uint8_t *rowop, uint8_t *colop,
+                             float *colsum, cudaStream_t s);
+cudaError_t launch_mlp_gemm3(int epi, const uint8_t *A, int M, const uint8_t *B, int N, int K, int splits, float *C,
+                             long ldc, long zstride, const float *bias, const float *H, long ldh, uint8_t *rowop,
+                             uint8_t *colop, float *colsum, uint32_t *err, uint64_t wait_ns, cudaStream_t s,
+                             int *slices_used);
+
 // k_dft_fused.cu: the whole sphere transform of a row in one kernel (planes streamed by bulk
 // copies, stages j1 -> m1, j2 -> m2, j3 -> m3 in shared memory), for grids whose planes and rows
 // are 16-byte multiples and spheres with max |m| <= 8.

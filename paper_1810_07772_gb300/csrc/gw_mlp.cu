@@ -6,10 +6,13 @@
 // missing part P~(N_c = all) - P~(N_c = kept).  Everything runs on the device:
 //
 //   features / targets / apply   element-wise kernels over the upper triangle of P~
-//   forward / backward           a tiled SIMT GEMM with FP16 weights and FP32 accumulation,
-//                                fused bias + tanh (forward) and tanh' (backward) epilogues,
-//                                deterministic split-K for the weight gradients, with the bias
-//                                gradient taken as one more column of ones
+//   forward / backward           the products with 256-wide (hidden) sides on the tensor cores
+//                                (k_mlp_train.cu: FP32 operands as three BF16 parts, FP32
+//                                accuracy; bias + tanh and tanh' in the epilogues; the weight
+//                                gradients over slices of the batch, added in a fixed order);
+//                                the 2-wide output layer, the loss and the deltas of layer 3 in
+//                                one kernel (a warp per row); its weight gradient on a tiled SIMT
+//                                GEMM with FP32 accumulation; the weights are the FP16-rounded ones
 //   loss                         L = (1 / (2B)) sum (y - t)^2 and dL/dy = (y - t) / B
 //   optimiser                    Adam on an FP32 master copy; the FP16 weights are rounded from it
 #include <cuda_fp16.h>
@@ -166,13 +169,11 @@ __global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const fl
 }
 
 // ---------------------------------------------------------------------------------------------
-// SIMT GEMM: C(m, n) = sum_k A(m, k) B(n, k), 64 x 64 x 16 tiles, 256 threads, 4 x 4 outputs per
-// thread, FP32 accumulation.  A is FP32 (activations or deltas); B is FP16 (weights) or FP32.
+// SIMT GEMM (the output layer's weight gradient, 2 rows): C(m, n) = sum_k A(m, k) B(n, k),
+// 64 x 64 x 16 tiles, 256 threads, 4 x 4 outputs per thread, FP32 accumulation, split over K.
 //   A_KC: A(m,k) = A[row(m) * lda + k]   else A(m,k) = A[k * lda + m]
 //   B_KC: B(n,k) = B[n * ldb + k]        else B(n,k) = B[row(k) * ldb + n]
 // row() is an optional gather of sample rows (a minibatch drawn from a larger set).
-
-enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_TANH = 2, EPI_DTANH = 3 };
 
 struct GemmArgs {
     const float *A;
@@ -183,9 +184,6 @@ struct GemmArgs {
     const int *brow;  // !B_KC only
     int M, N, K;
     int ones_col;     // B(ones_col, k) = 1: the bias-gradient column
-    const float *bias;
-    const float *H;   // EPI_DTANH: C = acc * (1 - H^2)
-    long ldh;
     float *C;
     long ldc;
     int kps;          // K range of one split (multiple of GT_K)
@@ -195,7 +193,7 @@ struct GemmArgs {
 __device__ __forceinline__ float ld_elem(const float *p) { return *p; }
 __device__ __forceinline__ float ld_elem(const __half *p) { return __half2float(*p); }
 
-template <bool A_KC, bool B_KC, typename TB, int EPI>
+template <bool A_KC, bool B_KC, typename TB>
 __global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs a)
 {
     __shared__ __align__(16) float As[GT_K][GT_M + 4];
@@ -268,16 +266,7 @@ __global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs a)
             const int n = n0 + tx * 4 + j;
             if (n >= a.N)
                 continue;
-            float v = acc[i][j];
-            if (EPI == EPI_BIAS)
-                v += a.bias[n];
-            else if (EPI == EPI_BIAS_TANH)
-                v = tanhf(v + a.bias[n]);
-            else if (EPI == EPI_DTANH) {
-                const float h = a.H[(long)m * a.ldh + n];
-                v *= 1.f - h * h;
-            }
-            C[(long)m * a.ldc + n] = v;
+            C[(long)m * a.ldc + n] = acc[i][j];
         }
     }
 }
@@ -298,33 +287,90 @@ __global__ void splitk_reduce_kernel(const float *part, int S, long stride, int 
     }
 }
 
-// D = (Y - T) / B; loss += (1 / (2B)) sum (Y - T)^2.
-__global__ void __launch_bounds__(256) mse_delta_kernel(const float *Y, const float *T, const int *trow, int B,
-                                                        float invB, float *D, float *loss)
+// gW[e] = sum_z part[z * stride + e] (e < n_w) and, from blocks past the first nb_w,
+// gb[o] = sum_rb csum[rb * out + o] (o < out, rb < nrb): both in a fixed order
+__global__ void __launch_bounds__(256) grad_finish_kernel(const float *part, int S, long stride, long n_w, int nb_w,
+                                                          float *gW, const float *csum, int nrb, int out, float *gb)
 {
-    __shared__ float red[256];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    float acc = 0.f;
-    if (b < B) {
-        const long r = trow ? trow[b] : b;
-        const float r0 = Y[2 * b] - T[2 * r], r1 = Y[2 * b + 1] - T[2 * r + 1];
-        D[2 * b] = r0 * invB;
-        D[2 * b + 1] = r1 * invB;
-        acc = r0 * r0 + r1 * r1;
+    if ((int)blockIdx.x < nb_w) {
+        for (long e = blockIdx.x * 256L + threadIdx.x; e < n_w; e += (long)nb_w * 256) {
+            float acc = 0.f;
+            for (int z = 0; z < S; ++z)
+                acc += part[z * stride + e];
+            gW[e] = acc;
+        }
+        return;
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    const int o = ((int)blockIdx.x - nb_w) * 256 + threadIdx.x;
+    if (o < out) {
+        float acc = 0.f;
+        for (int rb = 0; rb < nrb; ++rb)
+            acc += csum[(long)rb * out + o];
+        gb[o] = acc;
     }
-    if (threadIdx.x == 0 && loss)
-        atomicAdd(loss, 0.5f * invB * red[0]);
 }
 
-__global__ void adam_kernel(float *theta, __half *theta16, const float *g, float *m, float *v, long P, float lr,
-                            float b1, float b2, float c1, float c2, float eps)
+// The 2-wide output layer, one warp per row b: y = W4 h + b4 (h = H2[b], W4 FP16) into Y.  With
+// targets T (row trow[b] if given) also D4[b] = (y - t) / B, loss += |y - t|^2 / (2B) and the
+// deltas of layer 3, D[b][n] = (D4[b] W4)[n] (1 - h[n]^2).
+__global__ void __launch_bounds__(256) out_layer_kernel(const float *H2, int Hd, const __half *W4, const float *b4,
+                                                        int batch, float *Y, const float *T, const int *trow,
+                                                        float invB, float *D4, float *D, float *loss)
+{
+    __shared__ float red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    float l2 = 0.f;
+    if (b < batch) {
+        const float *h = H2 + (long)b * Hd;
+        float y0 = 0.f, y1 = 0.f;
+        for (int n = lane; n < Hd; n += 32) {
+            const float hv = h[n];
+            y0 = fmaf(__half2float(W4[n]), hv, y0);
+            y1 = fmaf(__half2float(W4[Hd + n]), hv, y1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        }
+        y0 += b4[0];
+        y1 += b4[1];
+        if (lane == 0) {
+            Y[2 * (long)b] = y0;
+            Y[2 * (long)b + 1] = y1;
+        }
+        if (T) {
+            const long r = trow ? trow[b] : b;
+            const float e0 = y0 - T[2 * r], e1 = y1 - T[2 * r + 1];
+            const float d0 = e0 * invB, d1 = e1 * invB;
+            if (lane == 0) {
+                D4[2 * (long)b] = d0;
+                D4[2 * (long)b + 1] = d1;
+                l2 = e0 * e0 + e1 * e1;
+            }
+            for (int n = lane; n < Hd; n += 32) {
+                const float hv = h[n];
+                D[(long)b * Hd + n] =
+                    (d0 * __half2float(W4[n]) + d1 * __half2float(W4[Hd + n])) * (1.f - hv * hv);
+            }
+        }
+    }
+    if (loss) {
+        if (lane == 0)
+            red[warp] = l2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < 8; ++w)
+                t += red[w];
+            atomicAdd(loss, 0.5f * invB * t);
+        }
+    }
+}
+
+__global__ void adam_kernel(float *theta, __half *theta16, float *w32, const float *g, float *m, float *v, long P,
+                            float lr, float b1, float b2, float c1, float c2, float eps)
 {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -334,14 +380,19 @@ __global__ void adam_kernel(float *theta, __half *theta16, const float *g, float
         v[i] = vi;
         const float t = theta[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
         theta[i] = t;
-        theta16[i] = __float2half_rn(t);
+        const __half t16 = __float2half_rn(t);
+        theta16[i] = t16;
+        w32[i] = __half2float(t16);
     }
 }
 
-__global__ void to_half_kernel(const float *x, __half *y, long n)
+__global__ void to_half_kernel(const float *x, __half *y, float *y32, long n)
 {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        y[i] = __float2half_rn(x[i]);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const __half h = __float2half_rn(x[i]);
+        y[i] = h;
+        y32[i] = __half2float(h);
+    }
 }
 
 }  // namespace
@@ -357,9 +408,18 @@ struct gw_mlp {
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __half *theta16 = nullptr;
     float *H[3] = {}, *Da = nullptr, *Db = nullptr, *D4 = nullptr, *Y = nullptr, *part = nullptr;
+    // tensor-core products: the FP16-rounded parameters as FP32, and the operands in the
+    // three-part BF16 block layout: X, H0, H1 as layer inputs (row) and weight-gradient operands
+    // (col), the deltas (row: two, a product reads one and writes the other; col), W1..W3 (row)
+    // and W2, W3 transposed (col)
+    float *w32 = nullptr;
+    uint8_t *pX = nullptr, *pXc = nullptr, *pH[2] = {}, *pHc[2] = {}, *pD[2] = {}, *pDc = nullptr;
+    uint8_t *pW[3] = {}, *pWc[2] = {};
+    float *csum = nullptr;  // column sums of the deltas per 128-row tile (bias gradients)
+    bool wpacked = false;
     long step = 0;
-    // tensor-core inference: W1, W2, W3 in the operand layout (valid while tiled == true) and a
-    // status word for the kernel's bounded waits
+    // tensor-core inference: W1, W2, W3 in the operand layout (valid while tiled == true); d_err:
+    // the status word of every tensor-core kernel's bounded waits (read by gw_mlp_check)
     uint8_t *Wt = nullptr;
     bool tiled = false;
     uint32_t *d_err = nullptr;
@@ -406,18 +466,18 @@ long num_params(int n_in, int hidden)
     return (long)hidden * n_in + hidden + 2L * ((long)hidden * hidden + hidden) + (long)NOUT * hidden + NOUT;
 }
 
-template <bool A_KC, bool B_KC, typename TB, int EPI>
+template <bool A_KC, bool B_KC, typename TB>
 cudaError_t gemm(cudaStream_t s, GemmArgs a, int splits)
 {
     dim3 grid((a.N + GT_N - 1) / GT_N, (a.M + GT_M - 1) / GT_M, splits);
     if (splits == 1)
         a.kps = ((a.K + GT_K - 1) / GT_K) * GT_K;
-    mlp_gemm_kernel<A_KC, B_KC, TB, EPI><<<grid, 256, 0, s>>>(a);
+    mlp_gemm_kernel<A_KC, B_KC, TB><<<grid, 256, 0, s>>>(a);
     gw::count_launches(1);
     return cudaGetLastError();
 }
 
-// dW_l (out x in) and db_l from deltas D (batch x out) and the layer input Ain (batch x in):
+// dW4 (2 x in) and db4 from the output deltas D (batch x 2) and the layer input Ain (batch x in):
 // dW = D^T Ain with K = batch split across blockIdx.z, then a deterministic reduction.
 cudaError_t weight_grad(gw_mlp *m, const float *D, int out, const float *Ain, long ld_in, const int *brow, int in,
                         int batch, int layer)
@@ -440,7 +500,7 @@ cudaError_t weight_grad(gw_mlp *m, const float *D, int out, const float *Ain, lo
     const int per = (batch + S - 1) / S;
     a.kps = ((per + GT_K - 1) / GT_K) * GT_K;
     S = (batch + a.kps - 1) / a.kps;
-    cudaError_t e = gemm<false, false, float, EPI_STORE>(m->stream, a, S);
+    cudaError_t e = gemm<false, false, float>(m->stream, a, S);
     if (e != cudaSuccess)
         return e;
     const long total = (long)out * (in + 1);
@@ -451,88 +511,112 @@ cudaError_t weight_grad(gw_mlp *m, const float *D, int out, const float *Ain, lo
     return cudaGetLastError();
 }
 
-// Forward of `batch` rows of X (gathered by rows if given) into H[0..2] and Yout.
-cudaError_t forward_batch(gw_mlp *m, const float *X, const int *rows, int batch, float *Yout)
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+
+// W1..W3 as the B operands of the forward products (rows = outputs) and W2, W3 transposed for the
+// products back through them (rows = inputs), from the FP16-rounded weights
+cudaError_t pack_weights(gw_mlp *m)
+{
+    if (m->wpacked)
+        return cudaSuccess;
+    gw::MlpWeightPack p{};
+    for (int l = 0; l < 3; ++l) {
+        p.row[l] = m->pW[l];
+        p.off[l] = m->off_w[l];
+    }
+    p.col[0] = m->pWc[0];
+    p.col[1] = m->pWc[1];
+    p.hidden = m->hidden;
+    p.n_in = m->n_in;
+    const cudaError_t e = gw::launch_mlp_pack_weights(m->w32, p, m->num_sms, m->stream);
+    if (e == cudaSuccess)
+        m->wpacked = true;
+    return e;
+}
+
+// Forward of `batch` rows of X (gathered by rows if given) into H[0..2] and Yout.  keep: also
+// pack what the backward pass needs (X and H0, H1 as weight-gradient operands).  Yout null: stop
+// before the output layer.
+cudaError_t forward_batch(gw_mlp *m, const float *X, const int *rows, int batch, float *Yout, bool keep)
 {
     const int Hd = m->hidden;
-    GemmArgs a{};
-    a.ones_col = -1;
-    a.A = X;
-    a.lda = m->n_in;
-    a.arow = rows;
-    a.B = m->theta16 + m->off_w[0];
-    a.ldb = m->n_in;
-    a.M = batch;
-    a.N = Hd;
-    a.K = m->n_in;
-    a.bias = m->theta + m->off_b[0];
-    a.C = m->H[0];
-    a.ldc = Hd;
-    cudaError_t e = gemm<true, true, __half, EPI_BIAS_TANH>(m->stream, a, 1);
-    for (int l = 1; l < 3 && e == cudaSuccess; ++l) {
-        a.A = m->H[l - 1];
-        a.lda = Hd;
-        a.arow = nullptr;
-        a.B = m->theta16 + m->off_w[l];
-        a.ldb = Hd;
-        a.K = Hd;
-        a.bias = m->theta + m->off_b[l];
-        a.C = m->H[l];
-        e = gemm<true, true, __half, EPI_BIAS_TANH>(m->stream, a, 1);
+    cudaError_t e = pack_weights(m);
+    if (e == cudaSuccess)
+        e = gw::launch_mlp_pack3(X, m->n_in, rows, batch, m->n_in, m->pX, keep ? m->pXc : nullptr, nullptr,
+                                 m->stream);
+    const uint8_t *Ain = m->pX;
+    int K = m->n_in;
+    // each layer also writes its output as the next layer's operand and, for the backward pass, as
+    // the operand of a weight gradient
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+        e = gw::launch_mlp_gemm3(1, Ain, batch, m->pW[l], Hd, K, 1, m->H[l], Hd, 0, m->theta + m->off_b[l], nullptr, 0,
+                                 l < 2 ? m->pH[l] : nullptr, keep && l < 2 ? m->pHc[l] : nullptr, nullptr, m->d_err,
+                                 TC_WAIT_NS, m->stream, nullptr);
+        if (l < 2) {
+            Ain = m->pH[l];
+            K = Hd;
+        }
     }
-    if (e != cudaSuccess)
+    if (e != cudaSuccess || !Yout)
         return e;
-    a.A = m->H[2];
-    a.B = m->theta16 + m->off_w[3];
-    a.N = NOUT;
-    a.bias = m->theta + m->off_b[3];
-    a.C = Yout;
-    a.ldc = NOUT;
-    return gemm<true, true, __half, EPI_BIAS>(m->stream, a, 1);
+    // the 2-wide output layer
+    out_layer_kernel<<<(batch + 7) / 8, 256, 0, m->stream>>>(m->H[2], Hd, m->theta16 + m->off_w[3],
+                                                            m->theta + m->off_b[3], batch, Yout, nullptr, nullptr, 0.f,
+                                                            nullptr, nullptr, nullptr);
+    gw::count_launches(1);
+    return cudaGetLastError();
 }
 
 // Loss and the gradient of every parameter into m->grad.
 cudaError_t loss_grad(gw_mlp *m, const float *X, const float *T, const int *rows, int batch, float *loss)
 {
     const int Hd = m->hidden;
-    cudaError_t e = forward_batch(m, X, rows, batch, m->Y);
+    cudaError_t e = forward_batch(m, X, rows, batch, nullptr, true);
     if (e != cudaSuccess)
         return e;
-    mse_delta_kernel<<<(batch + 255) / 256, 256, 0, m->stream>>>(m->Y, T, rows, batch, 1.f / batch, m->D4, loss);
+    // output layer, loss, its deltas D4 = (y - t) / B and those of layer 3, D = (D4 W4) (1 - H2^2)
+    out_layer_kernel<<<(batch + 7) / 8, 256, 0, m->stream>>>(m->H[2], Hd, m->theta16 + m->off_w[3],
+                                                            m->theta + m->off_b[3], batch, m->Y, T, rows, 1.f / batch,
+                                                            m->D4, m->Da, loss);
     gw::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // output layer
+    // dW4, db4
     if ((e = weight_grad(m, m->D4, NOUT, m->H[2], Hd, nullptr, Hd, batch, 3)) != cudaSuccess)
         return e;
-    // hidden layers 3, 2, 1: dH_l = D_{l+1} W_{l+1}, D_l = dH_l (1 - H_l^2), then dW_l
-    const float *Dnext = m->D4;
-    int out_next = NOUT;
-    float *bufs[2] = {m->Da, m->Db};
+    // hidden layers l = 2, 1, 0 (weights W_{l+1}): dW = D^T (layer input), db = the column sums of D,
+    // and the deltas of layer l - 1, (D W_{l+1}) (1 - H_{l-1}^2), which the product writes as the
+    // operands of the next steps (row, col) with their column sums
+    if ((e = gw::launch_mlp_pack3(m->Da, Hd, nullptr, batch, Hd, m->pD[0], m->pDc, m->csum, m->stream)) !=
+        cudaSuccess)
+        return e;
+    float *D = m->Da;
+    int cur = 0;
     for (int l = 2; l >= 0; --l) {
-        float *Dl = bufs[l & 1];
-        GemmArgs a{};
-        a.ones_col = -1;
-        a.A = Dnext;
-        a.lda = out_next;
-        a.B = m->theta16 + m->off_w[l + 1];
-        a.ldb = Hd;
-        a.M = batch;
-        a.N = Hd;
-        a.K = out_next;
-        a.H = m->H[l];
-        a.ldh = Hd;
-        a.C = Dl;
-        a.ldc = Hd;
-        if ((e = gemm<true, false, __half, EPI_DTANH>(m->stream, a, 1)) != cudaSuccess)
-            return e;
-        const float *Ain = l > 0 ? m->H[l - 1] : X;
-        const long ld_in = l > 0 ? Hd : m->n_in;
         const int in = l > 0 ? Hd : m->n_in;
-        if ((e = weight_grad(m, Dl, Hd, Ain, ld_in, l > 0 ? nullptr : rows, in, batch, l)) != cudaSuccess)
+        const int tiles = ((Hd + 127) / 128) * ((in + 127) / 128);
+        int S = 1;
+        if ((e = gw::launch_mlp_gemm3(0, m->pDc, Hd, l > 0 ? m->pHc[l - 1] : m->pXc, in, batch,
+                                      std::max(1, std::min(SPLIT_MAX, m->num_sms / tiles)), m->part, in,
+                                      (long)Hd * in, nullptr, nullptr, 0, nullptr, nullptr, nullptr, m->d_err,
+                                      TC_WAIT_NS, m->stream, &S)) != cudaSuccess)
             return e;
-        Dnext = Dl;
-        out_next = Hd;
+        const long nw = (long)Hd * in;
+        const int nbw = (int)std::min<long>((nw + 255) / 256, 4L * m->num_sms);
+        grad_finish_kernel<<<nbw + (Hd + 255) / 256, 256, 0, m->stream>>>(
+            m->part, S, nw, nw, nbw, m->grad + m->off_w[l], m->csum, (batch + 127) / 128, Hd, m->grad + m->off_b[l]);
+        gw::count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        if (l > 0) {
+            float *Dn = D == m->Da ? m->Db : m->Da;
+            if ((e = gw::launch_mlp_gemm3(2, m->pD[cur], batch, m->pWc[l - 1], Hd, Hd, 1, Dn, Hd, 0, nullptr,
+                                          m->H[l - 1], Hd, l > 1 ? m->pD[1 - cur] : nullptr, m->pDc, m->csum, m->d_err,
+                                          TC_WAIT_NS, m->stream, nullptr)) != cudaSuccess)
+                return e;
+            D = Dn;
+            cur = 1 - cur;
+        }
     }
     return cudaSuccess;
 }
@@ -558,11 +642,12 @@ gw_status train_step(gw_mlp *m, const float *X, const float *T, const int *rows,
     MLP_CUDA(loss_grad(m, X, T, rows, batch, loss_accum), "gw_mlp_train_step");
     m->step += 1;
     m->tiled = false;
+    m->wpacked = false;
     const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)m->step));
     const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)m->step));
     adam_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(
-        m->theta, m->theta16, m->grad, m->m, m->v, m->P, (float)lr, (float)beta1, (float)beta2, (float)c1, (float)c2,
-        (float)adam_eps);
+        m->theta, m->theta16, m->w32, m->grad, m->m, m->v, m->P, (float)lr, (float)beta1, (float)beta2, (float)c1,
+        (float)c2, (float)adam_eps);
     gw::count_launches(1);
     MLP_CUDA(cudaGetLastError(), "gw_mlp_train_step adam");
     return GW_OK;
@@ -655,7 +740,7 @@ gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_
     }
     const size_t P = (size_t)m->P, act = (size_t)max_batch * hidden;
     const size_t part = (size_t)SPLIT_MAX * hidden * (std::max(hidden, n_in) + 1);
-    float **fbufs[] = {&m->theta, &m->grad, &m->m, &m->v};
+    float **fbufs[] = {&m->theta, &m->grad, &m->m, &m->v, &m->w32};
     for (float **p : fbufs)
         if (cudaMalloc(p, P * sizeof(float)) != cudaSuccess)
             return cleanup(GW_E_NOMEM);
@@ -669,8 +754,30 @@ gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_
         cudaMalloc(&m->Y, (size_t)max_batch * NOUT * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&m->part, part * sizeof(float)) != cudaSuccess)
         return cleanup(GW_E_NOMEM);
+    // operands of the tensor-core products (sizes: rows x k of each)
+    struct {
+        uint8_t **p;
+        int rows, k;
+    } packs[] = {{&m->pX, max_batch, n_in},      {&m->pXc, n_in, max_batch},      {&m->pH[0], max_batch, hidden},
+                 {&m->pH[1], max_batch, hidden}, {&m->pHc[0], hidden, max_batch}, {&m->pHc[1], hidden, max_batch},
+                 {&m->pD[0], max_batch, hidden}, {&m->pD[1], max_batch, hidden},  {&m->pDc, hidden, max_batch},
+                 {&m->pW[0], hidden, n_in},
+                 {&m->pW[1], hidden, hidden},    {&m->pW[2], hidden, hidden},     {&m->pWc[0], hidden, hidden},
+                 {&m->pWc[1], hidden, hidden}};
+    for (auto &pk : packs)
+        if (cudaMalloc(pk.p, gw::mlp_pack3_bytes(pk.rows, pk.k)) != cudaSuccess)
+            return cleanup(GW_E_NOMEM);
+    // the weights' padding is never written: clear their buffers once
+    for (uint8_t *w : {m->pW[0], m->pW[1], m->pW[2], m->pWc[0], m->pWc[1]})
+        if (cudaMemsetAsync(w, 0, gw::mlp_pack3_bytes(hidden, w == m->pW[0] ? n_in : hidden), m->stream) != cudaSuccess)
+            return cleanup(GW_E_CUDA);
+    if (cudaMalloc(&m->d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&m->csum, (size_t)((max_batch + 127) / 128) * hidden * sizeof(float)) != cudaSuccess)
+        return cleanup(GW_E_NOMEM);
     if (cudaMemsetAsync(m->theta, 0, P * sizeof(float), m->stream) != cudaSuccess ||
         cudaMemsetAsync(m->theta16, 0, P * sizeof(__half), m->stream) != cudaSuccess ||
+        cudaMemsetAsync(m->w32, 0, P * sizeof(float), m->stream) != cudaSuccess ||
+        cudaMemsetAsync(m->d_err, 0, sizeof(uint32_t), m->stream) != cudaSuccess ||
         cudaMemsetAsync(m->m, 0, P * sizeof(float), m->stream) != cudaSuccess ||
         cudaMemsetAsync(m->v, 0, P * sizeof(float), m->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -689,8 +796,10 @@ gw_status gw_mlp_destroy(gw_mlp *m)
         cudaStreamSynchronize(m->stream);
     else
         cudaDeviceSynchronize();
-    void *ptrs[] = {m->theta, m->grad, m->m, m->v, m->theta16, m->H[0], m->H[1], m->H[2],
-                    m->Da,    m->Db,   m->D4, m->Y, m->part,  m->Wt, m->d_err};
+    void *ptrs[] = {m->theta, m->grad,   m->m,      m->v,      m->theta16, m->w32,  m->H[0],  m->H[1],
+                    m->H[2],  m->Da,     m->Db,     m->D4,     m->Y,       m->part, m->pX,    m->pXc,
+                    m->pH[0], m->pH[1],  m->pHc[0], m->pHc[1], m->pD[0],   m->pD[1], m->pDc,  m->pW[0], m->pW[1],
+                    m->pW[2], m->pWc[0], m->pWc[1], m->csum,   m->Wt,      m->d_err};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -718,12 +827,13 @@ gw_status gw_mlp_set_params(gw_mlp *m, const float *theta, int on_device)
              "gw_mlp_set_params copy");
     MLP_CUDA(cudaMemsetAsync(m->m, 0, bytes, m->stream), "gw_mlp_set_params reset");
     MLP_CUDA(cudaMemsetAsync(m->v, 0, bytes, m->stream), "gw_mlp_set_params reset");
-    to_half_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(m->theta, m->theta16,
-                                                                                                   m->P);
+    to_half_kernel<<<(int)std::min<long>((m->P + 255) / 256, 4L * m->num_sms), 256, 0, m->stream>>>(
+        m->theta, m->theta16, m->w32, m->P);
     gw::count_launches(1);
     MLP_CUDA(cudaGetLastError(), "gw_mlp_set_params convert");
     m->step = 0;
     m->tiled = false;
+    m->wpacked = false;
     if (!on_device)
         MLP_CUDA(cudaStreamSynchronize(m->stream), "gw_mlp_set_params sync");
     return GW_OK;
@@ -749,7 +859,7 @@ gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y)
         return mfail(m, GW_E_INVALID, "gw_mlp_forward: null pointer or negative size");
     for (long b0 = 0; b0 < n; b0 += m->max_batch) {
         const int b = (int)std::min<long>(m->max_batch, n - b0);
-        MLP_CUDA(forward_batch(m, X + b0 * m->n_in, nullptr, b, Y + b0 * NOUT), "gw_mlp_forward");
+        MLP_CUDA(forward_batch(m, X + b0 * m->n_in, nullptr, b, Y + b0 * NOUT, false), "gw_mlp_forward");
     }
     return GW_OK;
 }
@@ -763,11 +873,8 @@ gw_status gw_mlp_infer(gw_mlp *m, const float *X, long n, float *Y)
         return mfail(m, GW_E_UNSUPPORTED, "gw_mlp_infer: the tensor-core path takes hidden = 256 and n_in <= 16");
     if (n == 0)
         return GW_OK;
-    if (!m->Wt) {
+    if (!m->Wt)
         MLP_CUDA(cudaMalloc(&m->Wt, gw::mlp_tc_weights_bytes()), "gw_mlp_infer weights");
-        MLP_CUDA(cudaMalloc(&m->d_err, sizeof(uint32_t)), "gw_mlp_infer status");
-        MLP_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(uint32_t), m->stream), "gw_mlp_infer status");
-    }
     if (!m->tiled) {
         MLP_CUDA(gw::launch_mlp_tile_weights(m->theta16 + m->off_w[0], m->n_in, m->theta16 + m->off_w[1],
                                              m->theta16 + m->off_w[2], m->Wt, m->stream),
@@ -793,7 +900,7 @@ gw_status gw_mlp_check(gw_mlp *m)
     if (word == 0)
         return GW_OK;
     cudaMemset(m->d_err, 0, sizeof(uint32_t));
-    return mfail(m, static_cast<gw_status>(word & 0xFF), "gw_mlp_infer: a device-side wait ran out (code %u)",
+    return mfail(m, static_cast<gw_status>(word & 0xFF), "a tensor-core kernel's device-side wait ran out (code %u)",
                  word & 0xFF);
 }
 
@@ -925,7 +1032,7 @@ gw_status gw_corr_train(gw_mlp *m, const float *X, const float *T, long n, const
     for (int e = 0; e < o->epochs; ++e)
         losses[e] = h[e] / (float)steps;
     release();
-    return GW_OK;
+    return gw_mlp_check(m);  // the tensor-core kernels' status word
 }
 
 gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_all, float *ratio, void *stream)

@@ -10,9 +10,10 @@
 //                                (k_mlp_train.cu: FP32 operands as three BF16 parts, FP32
 //                                accuracy; bias + tanh and tanh' in the epilogues; the weight
 //                                gradients over slices of the batch, added in a fixed order);
-//                                the 2-wide output layer, the loss and the deltas of layer 3 in
-//                                one kernel (a warp per row); its weight gradient on a tiled SIMT
-//                                GEMM with FP32 accumulation; the weights are the FP16-rounded ones
+//                                the 2-wide output layer, the loss, the deltas of layer 3 and
+//                                the output layer's gradient in one kernel (a warp per row, sums
+//                                per block added in a fixed order); the weights are the
+//                                FP16-rounded ones
 //   loss                         L = (1 / (2B)) sum (y - t)^2 and dL/dy = (y - t) / B
 //   optimiser                    Adam on an FP32 master copy; the FP16 weights are rounded from it
 #include <cuda_fp16.h>
@@ -37,7 +38,6 @@ namespace {
 
 constexpr int NF = 12;        // features per P~ entry
 constexpr int NOUT = 2;       // (Re, Im) of the predicted correction
-constexpr int GT_M = 64, GT_N = 64, GT_K = 16;
 constexpr int SPLIT_MAX = 64;
 
 // Position of entry (g, h), g <= h, in the row-major upper triangle of an ng x ng matrix.
@@ -168,125 +168,6 @@ __global__ void __launch_bounds__(128) apply_kernel(float2 *PG, int ng, const fl
     }
 }
 
-// ---------------------------------------------------------------------------------------------
-// SIMT GEMM (the output layer's weight gradient, 2 rows): C(m, n) = sum_k A(m, k) B(n, k),
-// 64 x 64 x 16 tiles, 256 threads, 4 x 4 outputs per thread, FP32 accumulation, split over K.
-//   A_KC: A(m,k) = A[row(m) * lda + k]   else A(m,k) = A[k * lda + m]
-//   B_KC: B(n,k) = B[n * ldb + k]        else B(n,k) = B[row(k) * ldb + n]
-// row() is an optional gather of sample rows (a minibatch drawn from a larger set).
-
-struct GemmArgs {
-    const float *A;
-    long lda;
-    const int *arow;  // A_KC only
-    const void *B;
-    long ldb;
-    const int *brow;  // !B_KC only
-    int M, N, K;
-    int ones_col;     // B(ones_col, k) = 1: the bias-gradient column
-    float *C;
-    long ldc;
-    int kps;          // K range of one split (multiple of GT_K)
-    long split_stride;
-};
-
-__device__ __forceinline__ float ld_elem(const float *p) { return *p; }
-__device__ __forceinline__ float ld_elem(const __half *p) { return __half2float(*p); }
-
-template <bool A_KC, bool B_KC, typename TB>
-__global__ void __launch_bounds__(256) mlp_gemm_kernel(const GemmArgs a)
-{
-    __shared__ __align__(16) float As[GT_K][GT_M + 4];
-    __shared__ __align__(16) float Bs[GT_K][GT_N + 4];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int m0 = blockIdx.y * GT_M, n0 = blockIdx.x * GT_N;
-    const int kbeg = blockIdx.z * a.kps, kend = min(a.K, kbeg + a.kps);
-    const TB *B = static_cast<const TB *>(a.B);
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            acc[i][j] = 0.f;
-
-    for (int k0 = kbeg; k0 < kend; k0 += GT_K) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = tid + e * 256;
-            const int mm = A_KC ? i / GT_K : i % GT_M, kk = A_KC ? i % GT_K : i / GT_M;
-            const int m = m0 + mm, k = k0 + kk;
-            float v = 0.f;
-            if (m < a.M && k < kend) {
-                if (A_KC)
-                    v = a.A[(long)(a.arow ? a.arow[m] : m) * a.lda + k];
-                else
-                    v = a.A[(long)k * a.lda + m];
-            }
-            As[kk][mm] = v;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = tid + e * 256;
-            const int nn = B_KC ? i / GT_K : i % GT_N, kk = B_KC ? i % GT_K : i / GT_N;
-            const int n = n0 + nn, k = k0 + kk;
-            float v = 0.f;
-            if (n < a.N && k < kend) {
-                if (n == a.ones_col)
-                    v = 1.f;
-                else if (B_KC)
-                    v = ld_elem(B + (long)n * a.ldb + k);
-                else
-                    v = ld_elem(B + (long)(a.brow ? a.brow[k] : k) * a.ldb + n);
-            }
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GT_K; ++kk) {
-            const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-
-    float *C = a.C + blockIdx.z * a.split_stride;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= a.M)
-            continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= a.N)
-                continue;
-            C[(long)m * a.ldc + n] = acc[i][j];
-        }
-    }
-}
-
-// Sum of the split-K partials of a weight gradient; column n_w of the partials is the bias.
-__global__ void splitk_reduce_kernel(const float *part, int S, long stride, int M, int n_w, float *gW, float *gb)
-{
-    const long total = (long)M * (n_w + 1);
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int z = 0; z < S; ++z)
-            s += part[z * stride + e];
-        const int m = (int)(e / (n_w + 1)), n = (int)(e % (n_w + 1));
-        if (n < n_w)
-            gW[(long)m * n_w + n] = s;
-        else
-            gb[m] = s;
-    }
-}
-
 // gW[e] = sum_z part[z * stride + e] (e < n_w) and, from blocks past the first nb_w,
 // gb[o] = sum_rb csum[rb * out + o] (o < out, rb < nrb): both in a fixed order
 __global__ void __launch_bounds__(256) grad_finish_kernel(const float *part, int S, long stride, long n_w, int nb_w,
@@ -310,18 +191,49 @@ __global__ void __launch_bounds__(256) grad_finish_kernel(const float *part, int
     }
 }
 
-// The 2-wide output layer, one warp per row b: y = W4 h + b4 (h = H2[b], W4 FP16) into Y.  With
-// targets T (row trow[b] if given) also D4[b] = (y - t) / B, loss += |y - t|^2 / (2B) and the
-// deltas of layer 3, D[b][n] = (D4[b] W4)[n] (1 - h[n]^2).
+// The 2-wide output layer, OUT_ROWS rows per block (8 warps, a warp per row at a time): y = W4 h + b4
+// (h = H2[b], W4 FP16) into Y.  With targets T (row trow[b] if given) also D4[b] = (y - t) / B,
+// loss += |y - t|^2 / (2B), the deltas of layer 3, D[b][n] = (D4[b] W4)[n] (1 - h[n]^2), and the
+// block's share of the output layer's gradient, part[block] = [sum_b D4[b] h^T (2 x Hd) | sum_b D4[b]]
+// (2 Hd + 2 values; each warp sums its rows in shared memory, the warps are then added in order).
+constexpr int OUT_ROWS = 16;
+// out[e] = sum_s part[s * G + e] for one e per block: strided partial sums, then a tree, both in a
+// fixed order
+__global__ void __launch_bounds__(256) sum_parts_tree_kernel(const float *part, int S, long G, float *out)
+{
+    __shared__ float red[256];
+    const long e = blockIdx.x;
+    float acc = 0.f;
+    for (int z = threadIdx.x; z < S; z += 256)
+        acc += part[z * G + e];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        out[e] = red[0];
+}
+
 __global__ void __launch_bounds__(256) out_layer_kernel(const float *H2, int Hd, const __half *W4, const float *b4,
                                                         int batch, float *Y, const float *T, const int *trow,
-                                                        float invB, float *D4, float *D, float *loss)
+                                                        float invB, float *D4, float *D, float *loss, float *part)
 {
+    extern __shared__ float gsh[];  // [8 warps][2 Hd + 2]
     __shared__ float red[8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * 8 + warp;
-    float l2 = 0.f;
-    if (b < batch) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, G = 2 * Hd + 2;
+    float *g = gsh + warp * G;
+    if (T)
+        for (int e = lane; e < G; e += 32)
+            g[e] = 0.f;
+    __syncwarp();
+    float l2 = 0.f, s0 = 0.f, s1 = 0.f;
+    for (int rr = warp; rr < OUT_ROWS; rr += 8) {
+        const int b = blockIdx.x * OUT_ROWS + rr;
+        if (b >= batch)
+            break;
         const float *h = H2 + (long)b * Hd;
         float y0 = 0.f, y1 = 0.f;
         for (int n = lane; n < Hd; n += 32) {
@@ -347,25 +259,38 @@ __global__ void __launch_bounds__(256) out_layer_kernel(const float *H2, int Hd,
             if (lane == 0) {
                 D4[2 * (long)b] = d0;
                 D4[2 * (long)b + 1] = d1;
-                l2 = e0 * e0 + e1 * e1;
             }
+            l2 += e0 * e0 + e1 * e1;
+            s0 += d0;
+            s1 += d1;
             for (int n = lane; n < Hd; n += 32) {
                 const float hv = h[n];
-                D[(long)b * Hd + n] =
-                    (d0 * __half2float(W4[n]) + d1 * __half2float(W4[Hd + n])) * (1.f - hv * hv);
+                const float w0 = __half2float(W4[n]), w1 = __half2float(W4[Hd + n]);
+                D[(long)b * Hd + n] = (d0 * w0 + d1 * w1) * (1.f - hv * hv);
+                g[n] += d0 * hv;
+                g[Hd + n] += d1 * hv;
             }
         }
     }
-    if (loss) {
-        if (lane == 0)
-            red[warp] = l2;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float t = 0.f;
-            for (int w = 0; w < 8; ++w)
-                t += red[w];
-            atomicAdd(loss, 0.5f * invB * t);
-        }
+    if (!T)
+        return;
+    if (lane == 0) {
+        g[2 * Hd] = s0;
+        g[2 * Hd + 1] = s1;
+        red[warp] = l2;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < G; e += 256) {
+        float acc = 0.f;
+        for (int w = 0; w < 8; ++w)
+            acc += gsh[w * G + e];
+        part[(long)blockIdx.x * G + e] = acc;
+    }
+    if (threadIdx.x == 0 && loss) {
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w)
+            t += red[w];
+        atomicAdd(loss, 0.5f * invB * t);
     }
 }
 
@@ -466,51 +391,6 @@ long num_params(int n_in, int hidden)
     return (long)hidden * n_in + hidden + 2L * ((long)hidden * hidden + hidden) + (long)NOUT * hidden + NOUT;
 }
 
-template <bool A_KC, bool B_KC, typename TB>
-cudaError_t gemm(cudaStream_t s, GemmArgs a, int splits)
-{
-    dim3 grid((a.N + GT_N - 1) / GT_N, (a.M + GT_M - 1) / GT_M, splits);
-    if (splits == 1)
-        a.kps = ((a.K + GT_K - 1) / GT_K) * GT_K;
-    mlp_gemm_kernel<A_KC, B_KC, TB><<<grid, 256, 0, s>>>(a);
-    gw::count_launches(1);
-    return cudaGetLastError();
-}
-
-// dW4 (2 x in) and db4 from the output deltas D (batch x 2) and the layer input Ain (batch x in):
-// dW = D^T Ain with K = batch split across blockIdx.z, then a deterministic reduction.
-cudaError_t weight_grad(gw_mlp *m, const float *D, int out, const float *Ain, long ld_in, const int *brow, int in,
-                        int batch, int layer)
-{
-    GemmArgs a{};
-    a.A = D;
-    a.lda = out;
-    a.B = Ain;
-    a.ldb = ld_in;
-    a.brow = brow;
-    a.M = out;
-    a.N = in + 1;
-    a.K = batch;
-    a.ones_col = in;
-    a.C = m->part;
-    a.ldc = in + 1;
-    a.split_stride = (long)out * (in + 1);
-    const int tiles = ((a.N + GT_N - 1) / GT_N) * ((a.M + GT_M - 1) / GT_M);
-    int S = std::max(1, std::min({(2 * m->num_sms + tiles - 1) / tiles, (batch + GT_K - 1) / GT_K, SPLIT_MAX}));
-    const int per = (batch + S - 1) / S;
-    a.kps = ((per + GT_K - 1) / GT_K) * GT_K;
-    S = (batch + a.kps - 1) / a.kps;
-    cudaError_t e = gemm<false, false, float>(m->stream, a, S);
-    if (e != cudaSuccess)
-        return e;
-    const long total = (long)out * (in + 1);
-    const int blocks = (int)std::min<long>((total + 255) / 256, 4L * m->num_sms);
-    splitk_reduce_kernel<<<blocks, 256, 0, m->stream>>>(m->part, S, a.split_stride, out, in,
-                                                         m->grad + m->off_w[layer], m->grad + m->off_b[layer]);
-    gw::count_launches(1);
-    return cudaGetLastError();
-}
-
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 
 // W1..W3 as the B operands of the forward products (rows = outputs) and W2, W3 transposed for the
@@ -560,9 +440,9 @@ cudaError_t forward_batch(gw_mlp *m, const float *X, const int *rows, int batch,
     if (e != cudaSuccess || !Yout)
         return e;
     // the 2-wide output layer
-    out_layer_kernel<<<(batch + 7) / 8, 256, 0, m->stream>>>(m->H[2], Hd, m->theta16 + m->off_w[3],
-                                                            m->theta + m->off_b[3], batch, Yout, nullptr, nullptr, 0.f,
-                                                            nullptr, nullptr, nullptr);
+    out_layer_kernel<<<(batch + OUT_ROWS - 1) / OUT_ROWS, 256, 0, m->stream>>>(
+        m->H[2], Hd, m->theta16 + m->off_w[3], m->theta + m->off_b[3], batch, Yout, nullptr, nullptr, 0.f, nullptr,
+        nullptr, nullptr, nullptr);
     gw::count_launches(1);
     return cudaGetLastError();
 }
@@ -574,15 +454,21 @@ cudaError_t loss_grad(gw_mlp *m, const float *X, const float *T, const int *rows
     cudaError_t e = forward_batch(m, X, rows, batch, nullptr, true);
     if (e != cudaSuccess)
         return e;
-    // output layer, loss, its deltas D4 = (y - t) / B and those of layer 3, D = (D4 W4) (1 - H2^2)
-    out_layer_kernel<<<(batch + 7) / 8, 256, 0, m->stream>>>(m->H[2], Hd, m->theta16 + m->off_w[3],
-                                                            m->theta + m->off_b[3], batch, m->Y, T, rows, 1.f / batch,
-                                                            m->D4, m->Da, loss);
+    // output layer, loss, its deltas D4 = (y - t) / B, those of layer 3, D = (D4 W4) (1 - H2^2), and
+    // per-block partial sums of dW4, db4, then added over the blocks (W4 and b4 are adjacent)
+    const int nob = (batch + OUT_ROWS - 1) / OUT_ROWS;
+    const size_t osh = (size_t)8 * (2 * Hd + 2) * sizeof(float);
+    if ((e = cudaFuncSetAttribute(out_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osh)) !=
+        cudaSuccess)
+        return e;
+    out_layer_kernel<<<nob, 256, osh, m->stream>>>(m->H[2], Hd, m->theta16 + m->off_w[3], m->theta + m->off_b[3],
+                                                    batch, m->Y, T, rows, 1.f / batch, m->D4, m->Da, loss, m->part);
     gw::count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // dW4, db4
-    if ((e = weight_grad(m, m->D4, NOUT, m->H[2], Hd, nullptr, Hd, batch, 3)) != cudaSuccess)
+    sum_parts_tree_kernel<<<2 * Hd + 2, 256, 0, m->stream>>>(m->part, nob, 2L * Hd + 2, m->grad + m->off_w[3]);
+    gw::count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     // hidden layers l = 2, 1, 0 (weights W_{l+1}): dW = D^T (layer input), db = the column sums of D,
     // and the deltas of layer l - 1, (D W_{l+1}) (1 - H_{l-1}^2), which the product writes as the
@@ -739,7 +625,8 @@ gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_
         return cleanup(GW_E_CUDA);
     }
     const size_t P = (size_t)m->P, act = (size_t)max_batch * hidden;
-    const size_t part = (size_t)SPLIT_MAX * hidden * (std::max(hidden, n_in) + 1);
+    const size_t part = std::max((size_t)SPLIT_MAX * hidden * (std::max(hidden, n_in) + 1),
+                                 (size_t)((max_batch + 15) / 16) * (2 * hidden + 2));  // + output-layer partials
     float **fbufs[] = {&m->theta, &m->grad, &m->m, &m->v, &m->w32};
     for (float **p : fbufs)
         if (cudaMalloc(p, P * sizeof(float)) != cudaSuccess)

@@ -16,7 +16,7 @@
 //
 // mlp_gemm3_kernel: C(m, n) = sum_k A(m, k) B(n, k) over one slice of K, one 128 x 128 tile per
 // CTA; warp 0 streams the blocks with 1-D bulk copies into six 24 KB stages, warp 1 issues the six
-// MMAs per 16-k chunk into TMEM, warps 2..5 read the tile and apply the epilogue: store a partial
+// MMAs per 16-k chunk into TMEM, warps 2..9 read the tile and apply the epilogue: store a partial
 // product (weight gradients, summed over slices afterwards), bias + tanh (forward) or times
 // 1 - H^2 (back through tanh), and write the result also as the next products' operands (row and
 // transposed, staged in the idle pipeline buffers) and its column sums.  Every wait is bounded.
@@ -40,9 +40,11 @@ constexpr int STAGES = 6;
 constexpr uint32_t STAGE = 2 * BLK;        // 24 KB: a block of A and one of B
 constexpr uint32_t PIPE = STAGES * STAGE;  // 144 KB
 constexpr size_t SMEM = PIPE + 256;
-constexpr int NTHREADS = 192;              // warp 0 copies, warp 1 MMAs, warps 2..5 epilogue
+constexpr int NEPI = 8;                    // epilogue warps: two per TMEM lane quarter
+constexpr int NTHREADS = (2 + NEPI) * 32;  // warp 0 copies, warp 1 MMAs, warps 2..9 epilogue
 constexpr uint64_t DRAIN_NS = 2000000000ull;
 constexpr int PACK_PITCH = TR + 1;
+constexpr int PACK_THREADS = 512;
 constexpr size_t PACK_SMEM = (size_t)TR * PACK_PITCH * sizeof(float);
 static_assert(PACK_SMEM <= PIPE, "the epilogue stages a tile in the pipeline buffers");
 
@@ -91,46 +93,57 @@ __device__ __forceinline__ void store_row16(uint8_t *blk, int r, const float *v)
 // r) * ld) into rowop (rows r, k = c; nRB = ceil(R / 128) row blocks, ceil(C / 16) chunks) and
 // colop (rows c, k = r; ceil(C / 128) row blocks, ceil(R / 16) chunks).  Either may be null.
 // colsum (if given): colsum[rb][c] = the sum of the tile's rows of column c (rb = r0 / 128).
-__global__ void __launch_bounds__(TR) pack3_kernel(const float *__restrict__ S, long ld, const int *__restrict__ rows,
-                                                   int R, int C, uint8_t *__restrict__ rowop,
-                                                   uint8_t *__restrict__ colop, float *__restrict__ colsum)
+// 512 threads; the loads cover only the tile's rows and columns in range (a narrow matrix such
+// as the 12 input features takes 12 loads per row, not 128), the rest of the tile is zero.
+__global__ void __launch_bounds__(PACK_THREADS) pack3_kernel(const float *__restrict__ S, long ld,
+                                                             const int *__restrict__ rows, int R, int C,
+                                                             uint8_t *__restrict__ rowop, uint8_t *__restrict__ colop,
+                                                             float *__restrict__ colsum)
 {
     extern __shared__ float tile[];  // [128][PACK_PITCH]
     const int r0 = blockIdx.y * TR, c0 = blockIdx.x * TR, t = threadIdx.x;
-#pragma unroll 8
-    for (int i = 0; i < TR; ++i) {
-        const int r = r0 + i, c = c0 + t;
-        float v = 0.f;
-        if (r < R && c < C)
-            v = S[(long)(rows ? rows[r] : r) * ld + c];
-        tile[i * PACK_PITCH + t] = v;
+    const int rw = min(TR, R - r0), cw = min(TR, C - c0);  // rows and columns in range
+    for (int e = t; e < TR * TR; e += PACK_THREADS)
+        tile[(e >> 7) * PACK_PITCH + (e & 127)] = 0.f;
+    __syncthreads();
+    const int nv = rw * cw;
+#pragma unroll 4
+    for (int e = t; e < nv; e += PACK_THREADS) {
+        const int i = e / cw, c = e - i * cw, r = r0 + i;
+        tile[i * PACK_PITCH + c] = S[(long)(rows ? rows[r] : r) * ld + c0 + c];
     }
-    if (colsum && c0 + t < C) {
+    __syncthreads();
+    if (colsum && t < cw) {
         float acc = 0.f;
 #pragma unroll 8
         for (int i = 0; i < TR; ++i)
             acc += tile[i * PACK_PITCH + t];
         colsum[(long)(r0 >> 7) * C + c0 + t] = acc;
     }
-    __syncthreads();
     if (rowop) {
         const int nrb = (R + TR - 1) / TR, nkc = (C + 15) / 16;
-        for (int j = 0; j < 8 && (c0 >> 4) + j < nkc; ++j) {
+        for (int it = t; it < 8 * TR; it += PACK_THREADS) {
+            const int row = it & 127, j = it >> 7;
+            if ((c0 >> 4) + j >= nkc)
+                continue;
             float v[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-                v[e] = tile[t * PACK_PITCH + j * 16 + e];
-            store_row16(rowop + ((size_t)((c0 >> 4) + j) * nrb + (r0 >> 7)) * BLK, t, v);
+                v[e] = tile[row * PACK_PITCH + j * 16 + e];
+            store_row16(rowop + ((size_t)((c0 >> 4) + j) * nrb + (r0 >> 7)) * BLK, row, v);
         }
     }
     if (colop) {
         const int nrb = (C + TR - 1) / TR, nkc = (R + 15) / 16;
-        for (int j = 0; j < 8 && (r0 >> 4) + j < nkc; ++j) {
+        for (int it = t; it < 8 * TR; it += PACK_THREADS) {
+            const int col = it & 127, j = it >> 7;
+            if ((r0 >> 4) + j >= nkc)
+                continue;
             float v[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-                v[e] = tile[(j * 16 + e) * PACK_PITCH + t];
-            store_row16(colop + ((size_t)((r0 >> 4) + j) * nrb + (c0 >> 7)) * BLK, t, v);
+                v[e] = tile[(j * 16 + e) * PACK_PITCH + col];
+            store_row16(colop + ((size_t)((r0 >> 4) + j) * nrb + (c0 >> 7)) * BLK, col, v);
         }
     }
 }
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     volatile int *n_issued = abort_flag + 1;
     volatile int *n_consumed = abort_flag + 2;
-    volatile int *epi_ok = abort_flag + 3;  // [4] each epilogue warp's wait result
+    volatile int *epi_ok = abort_flag + 3;  // [NEPI] each epilogue warp's wait result
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = blockIdx.x, mb = blockIdx.y, z = blockIdx.z;
@@ -247,18 +260,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         __syncwarp();
     } else {
-        // epilogue warps 2..5: TMEM lane quarter warp & 3, one tile row per lane
-        const int q = warp & 3, rl = q * 32 + lane, m = mb * TR + rl;
+        // epilogue warps 2..9: TMEM lane quarter warp & 3 (one tile row per lane), column half hf
+        const int ew = warp - 2, q = warp & 3, hf = ew >> 2, rl = q * 32 + lane, m = mb * TR + rl;
+        const int et = ew * 32 + lane;  // 0 .. 255
         const bool wok = __all_sync(0xffffffffu, mbar_wait(accf, 0, wait_ns));
         if (lane == 0) {
-            epi_ok[q] = (wok && *abort_flag == 0) ? 1 : 0;
+            epi_ok[ew] = (wok && *abort_flag == 0) ? 1 : 0;
             if (!wok)
                 record_error(err, GW_E_TIMEOUT, SITE_HERK_EPILOGUE, blockIdx.x);
         }
-        // every epilogue warp's wait has ended (each is bounded): one decision, from the same four
-        // votes, for all four warps, so that all or none of them reach the staging barrier below
-        named_bar_sync(1, 128);
-        const bool ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+        // every epilogue warp's wait has ended (each is bounded): one decision, from the same votes,
+        // for all eight warps, so that all or none of them reach the staging barrier below
+        named_bar_sync(1, NEPI * 32);
+        bool ok = true;
+#pragma unroll
+        for (int w = 0; w < NEPI; ++w)
+            ok = ok && epi_ok[w] != 0;
         if (!ok) {
             if (lane == 0)
                 *abort_flag = 1;
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool stage = colop || colsum;
             const int nrb_m = (M + TR - 1) / TR, nrb_n = (N + TR - 1) / TR;
             const int nkc_n = (N + 15) / 16, nkc_m = (M + 15) / 16;
-            for (int c0 = 0; c0 < TR; c0 += 16) {
+            for (int c0 = hf * 64; c0 < hf * 64 + 64; c0 += 16) {
                 float v[16];
                 if (nch > 0) {
                     tmem_ld16(taddr + c0, v);
@@ -332,21 +349,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             if (stage) {
-                named_bar_sync(1, 128);
-                const int n = nb * TR + rl;  // thread rl now takes column rl of the tile
+                named_bar_sync(1, NEPI * 32);
+                // thread et now takes column cl of the tile, chunks 4 jh .. 4 jh + 3 of the transpose
+                const int cl = et & 127, jh = et >> 7, n = nb * TR + cl;
                 if (colop)
-                    for (int j = 0; j < 8 && mb * 8 + j < nkc_m; ++j) {
+                    for (int j = 4 * jh; j < 4 * jh + 4 && mb * 8 + j < nkc_m; ++j) {
                         float v[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
-                            v[e] = stile[(j * 16 + e) * PACK_PITCH + rl];
-                        store_row16(colop + ((size_t)(mb * 8 + j) * nrb_n + nb) * BLK, rl, v);
+                            v[e] = stile[(j * 16 + e) * PACK_PITCH + cl];
+                        store_row16(colop + ((size_t)(mb * 8 + j) * nrb_n + nb) * BLK, cl, v);
                     }
-                if (colsum && n < N) {
+                if (colsum && jh == 0 && n < N) {
                     float acc = 0.f;
 #pragma unroll 8
                     for (int i = 0; i < TR; ++i)
-                        acc += stile[i * PACK_PITCH + rl];
+                        acc += stile[i * PACK_PITCH + cl];
                     colsum[(long)mb * N + n] = acc;
                 }
             }
@@ -389,7 +407,7 @@ cudaError_t launch_mlp_pack3(const float *S, long ld, const int *rows, int R, in
     if (e != cudaSuccess)
         return e;
     const dim3 grid((C + TR - 1) / TR, (R + TR - 1) / TR);
-    pack3_kernel<<<grid, TR, PACK_SMEM, s>>>(S, ld, rows, R, C, rowop, colop, colsum);
+    pack3_kernel<<<grid, PACK_THREADS, PACK_SMEM, s>>>(S, ld, rows, R, C, rowop, colop, colsum);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -815,7 +815,6 @@ def section_learned(args, steps):
                          "launches": int(ctx.stats()["kernel_launches"] - l0)}
     ctx.close()
     net.close()
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
     peaks, peak_src = load_peaks()
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     return {"s_per_eps_inv": res["learned"]["ms"] / 1e3, "steps": nt, "warmup": args.warmup,
@@ -839,6 +838,9 @@ def section_learned(args, steps):
             "training": {"samples": S, "epochs": args.epochs, "losses": losses, "ms": train_ms,
                          "samples_per_s": n_train / (train_ms * 1e-3),
                          "tflops": n_train * train_flop / (train_ms * 1e-3) / 1e12,
+                         "frac_of_tensor_peak": n_train * train_flop / (train_ms * 1e-3) / 1e12 / tc_peak,
+                         "kernel": "mlp_gemm3_kernel (tcgen05 kind::f16; each FP32 operand as three BF16 parts, "
+                                   "six MMAs per product: network flops x 6 are issued)",
                          "data_generation_s": gen_s},
             "roofline": {"bound": "tensor", "kernel": "mlp_tc_pair_kernel (tcgen05 kind::f16 cta_group::2, "
                                                       "network inference per system)",
@@ -847,10 +849,12 @@ def section_learned(args, steps):
                          "traffic": None,
                          "peak_source": f"{peak_src} bf16_tflops (burst; FP16:BF16 nominal ratio 1)",
                          "inference_ms_per_system": infer_ms,
-                         "simt_forward": {"ms_per_system": fwd_ms, "kernel": "mlp_gemm_kernel (SIMT FP32)",
+                         "fp32_forward": {"ms_per_system": fwd_ms,
+                                          "kernel": "mlp_gemm3_kernel (the arithmetic of training: FP32-accurate, "
+                                                    "three BF16 parts per operand)",
                                           "achieved": Xs.shape[0] * fwd_flop / (fwd_ms * 1e-3) / 1e12,
-                                          "alu_peak": alu_peak,
-                                          "alu_peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}},
+                                          "frac_of_tensor_peak": Xs.shape[0] * fwd_flop / (fwd_ms * 1e-3) / 1e12
+                                          / tc_peak}},
             "gpu_launches": res["learned"]["launches"], "clocks": clk.summary()}
 
 

@@ -490,8 +490,11 @@ GW_API gw_status gw_mlp_num_params(int n_in, int hidden, size_t *n);
  *   max_batch  largest batch of gw_mlp_grad / gw_mlp_train_step, and the chunk of gw_mlp_forward;
  *              1..2^22
  *   stream     cudaStream_t for every call on the handle (NULL = legacy default stream)
- * Device memory: 4 P floats, P halves, 5 max_batch x hidden floats, and a split-K workspace
- * of 64 x hidden x (hidden + 1) floats; gw_mlp_infer adds 272 KB of tiled weights. */
+ * Device memory: 5 P floats, P halves, 5 max_batch x hidden floats, a split-K workspace of
+ * 64 x hidden x (hidden + 1) floats, and the tensor-core operands of training at 6 bytes a value
+ * (three BF16 parts): 6 x (7 hidden + 144) bytes per row of max_batch (activations and deltas in
+ * two orientations; the inputs padded to 16 and 128) plus five weight matrices; gw_mlp_infer adds
+ * 272 KB of tiled weights. */
 GW_API gw_status gw_mlp_create(gw_mlp **out, int device, int n_in, int hidden, int max_batch, void *stream);
 GW_API gw_status gw_mlp_destroy(gw_mlp *m);
 GW_API gw_status gw_mlp_last_error(gw_mlp *m, char *buf, size_t n);
@@ -501,7 +504,9 @@ GW_API gw_status gw_mlp_last_error(gw_mlp *m, char *buf, size_t n);
 GW_API gw_status gw_mlp_set_params(gw_mlp *m, const float *theta, int on_device);
 GW_API gw_status gw_mlp_get_params(gw_mlp *m, float *theta, int on_device);
 
-/* Inference: Y[n][2] = network(X[n][n_in]), in chunks of max_batch rows. */
+/* Inference: Y[n][2] = network(X[n][n_in]), in chunks of max_batch rows, with the arithmetic of
+ * training (FP32 activations; the hidden layers' products on the tensor cores with each FP32
+ * operand as three BF16 parts, FP32-accurate). */
 GW_API gw_status gw_mlp_forward(gw_mlp *m, const float *X, long n, float *Y);
 
 /* Inference on the tensor cores: the same network with FP16 weights and FP32 accumulation in one

@@ -16,7 +16,9 @@ uneven systems, grids 16^3..32^3, one persistent launch, whole pass in one CUDA 
 `learned` (24^3, N_c cut at 200 of 2000, the correction network trained on 64 systems).  Each
 carries its own time per step, algorithmic TFLOP/s, seconds per eps^-1, error against the FP64
 oracle and clock record.  `--no-extra` skips them; `--workload split|batch|learned` prints one of
-them as a line of its own.
+them as a line of its own.  `--workload mlp` times the correction network alone (tensor-core
+inference over one 24^3 system's 239,086 entries and Adam steps of 8192 rows, seeded synthetic
+features): a small case for profiling its kernels.
 
 Under torchrun with N > 1 each rank runs the same workload on its own GPU (independent replicas;
 the path has no exchange step at this size), timing is the max over ranks and `value` the sum.
@@ -46,7 +48,7 @@ INV_METHOD = "newton_tc"
 HERK_KERNEL = "single"   # kernel of the 16-bit rank-k update: one CTA per tile, or CTA pairs
 WORKLOADS = {"plain": inputs.PLAIN, "small": inputs.SMALL,
              "grid16": inputs.Workload("grid16_nv16_nc512", 16, 16, 512, 12, 41),
-             "split": inputs.SPLIT, "batch": None, "learned": None}
+             "split": inputs.SPLIT, "batch": None, "learned": None, "mlp": None}
 # The split-precision configuration (36^3) is stated with BF16 hi+lo operands and a 1e-4 error
 # target on P~; the library picks the update's window from that target (gw_set_error_target).
 # The plain 24^3 path keeps the library's default window (its 1e-6 target gives the same W = 3).
@@ -869,6 +871,62 @@ def run_learned(args):
     return 0
 
 
+def run_mlp(args):
+    """The correction network alone on seeded synthetic features of the learned workload's shape:
+    gw_mlp_infer over the 239,086 entries of one 24^3 system (N_g = 691), the FP32 forward over the
+    same rows, and args.epochs passes of Adam over 131,072 rows in batches of 8192."""
+    import torch
+    from paper_1810_07772_gb300 import gw
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(20)
+    nf, hid, n = gw.N_FEATURES, 256, 691 * 692 // 2
+    X = torch.from_numpy(rng.standard_normal((n, nf)).astype(np.float32)).to(dev)
+    Xt = torch.from_numpy(rng.standard_normal((131072, nf)).astype(np.float32)).to(dev)
+    Tt = torch.from_numpy((0.1 * rng.standard_normal((131072, 2))).astype(np.float32)).to(dev)
+    net = gw.Mlp(nf, hid, max_batch=8192, device=0, stream=stream)
+    net.set_params(inputs.mlp_init(nf, hid, 7))
+    fwd_flop, train_flop = mlp_sample_flop(nf)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        ev[0].record(stream)
+        for _ in range(k):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / k
+
+    Y = net.infer(X)
+    infer_ms = timed(lambda: net.infer(X, Y), args.steps)
+    net.check()
+    fwd_ms = timed(lambda: net.forward(X, Y), args.steps)
+    net.train_corr(Xt, Tt, 1, 8192, 1e-3)      # warm-up pass
+    ev[0].record(stream)
+    losses = net.train_corr(Xt, Tt, args.epochs, 8192, 1e-3)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    steps = args.epochs * (131072 // 8192)
+    peaks, peak_src = load_peaks()
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    tf = n * fwd_flop / (infer_ms * 1e-3) / 1e12
+    line = {"metric": "correction-network inference TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": infer_ms, "higher_is_better": True,
+            "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "mlp_12x256x256x256x2_rows239086", "rows": n, "features": nf, "hidden": hid},
+            "roofline": {"bound": "tensor", "kernel": "mlp_tc_pair_kernel", "achieved": tf, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": tf / tc_peak, "peak_source": f"{peak_src} bf16_tflops"},
+            "fp32_forward": {"ms": fwd_ms, "tflops": n * fwd_flop / (fwd_ms * 1e-3) / 1e12},
+            "training": {"batch": 8192, "steps": steps, "ms": train_ms, "us_per_step": 1e3 * train_ms / steps,
+                         "tflops": steps * 8192 * train_flop / (train_ms * 1e-3) / 1e12, "losses": losses}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -877,6 +935,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
     return run_gw(args)
 
 

@@ -51,7 +51,7 @@ def _theta(seed):
 def test_gradient_and_forward_match_oracle():
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(11)
-    S, B = 1000, 300                      # ragged: neither is a multiple of the 64-row tile
+    S, B = 1000, 300                      # ragged: neither is a multiple of the 128-row tile
     X = rng.standard_normal((S, N_IN)).astype(np.float32)
     T = rng.standard_normal((S, 2)).astype(np.float32)
     rows = rng.permutation(S)[:B].astype(np.int32)
@@ -66,11 +66,50 @@ def test_gradient_and_forward_match_oracle():
         g, loss = net.grad(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev))
         Y = net.forward(torch.from_numpy(X).to(dev)).cpu().numpy()   # 1000 rows in chunks of 384
     g = g.cpu().numpy().astype(np.float64)
-    # FP32 accumulation over at most 300 terms in each of the 8 GEMM stages: about sqrt(300) u_32
-    # = 1e-6 relative per stage, compounded over the stages.
+    # The products take each FP32 operand as three BF16 parts and drop only terms below 2^-24 of a
+    # product; FP32 accumulation over at most 300 terms in each of the 8 product stages: about
+    # sqrt(300) u_32 = 1e-6 relative per stage, compounded over the stages.
     assert abs(loss - loss_ref) <= 1e-5 * loss_ref
     for gb, rb in zip(_blocks(g), _blocks(g_ref)):
         assert np.linalg.norm(gb - rb) <= 2e-5 * np.linalg.norm(rb)
+    assert np.linalg.norm(Y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+
+
+def test_gradient_at_shapes_off_the_tile_grid():
+    """n_in = 5 and hidden = 200: partial 16-wide K chunks, a partial second 128-column tile with
+    its last 8 columns on the scalar epilogue path, a weight gradient with 5 columns (rows of 20
+    bytes, scalar stores throughout); batch 257 is one row past two 128-row tiles.  Same bars as
+    the full-width test."""
+    dev = torch.device("cuda:0")
+    n_in, hid, S, B = 5, 200, 600, 257
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((S, n_in)).astype(np.float32)
+    T = rng.standard_normal((S, 2)).astype(np.float32)
+    rows = rng.permutation(S)[:B].astype(np.int32)
+    th = inputs.mlp_init(n_in, hid, 3).astype(np.float64)
+    sizes = [(hid, n_in), (hid, hid), (hid, hid), (2, hid)]
+    o = 0
+    for r, c in sizes:                    # non-zero biases
+        o += r * c
+        th[o:o + r] = 0.1 * rng.standard_normal(r)
+        o += r
+    th = th.astype(np.float32)
+    params = M.unpack(M.to_fp16_weights(th.astype(np.float64), n_in, hid), n_in, hid)
+    loss_ref, grads = M.loss_and_grad(params, X[rows].astype(np.float64), T[rows].astype(np.float64))
+    g_ref = M.flatten(grads)
+    y_ref, _ = M.forward(params, X.astype(np.float64))
+    with gw.Mlp(n_in, hid, max_batch=300, device=0) as net:
+        net.set_params(th)
+        g, loss = net.grad(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(rows).to(dev))
+        Y = net.forward(torch.from_numpy(X).to(dev)).cpu().numpy()
+        net.check()
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    o = 0
+    for r, c in sizes:
+        for n in (r * c, r):              # W_l, then b_l
+            assert np.linalg.norm(g[o:o + n] - g_ref[o:o + n]) <= 2e-5 * np.linalg.norm(g_ref[o:o + n])
+            o += n
     assert np.linalg.norm(Y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
 
 

@@ -300,10 +300,17 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
 constexpr int P12_WARPS = 8;
 
 // Per warp: a1 [n2][c3] and, for the generic stage 1 only, the plane [n2][n3 + 1] (rows padded:
-// one lane per row reads them).  The compiled stage 1 loads each lane's line from global memory.
-__host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3, bool plane)
+// one lane per row reads them).  The compiled stage 1 of plain rows (stage) copies the plane with
+// coalesced 16-byte loads into [n2][p12_pitch(n3)] rows: a pitch of 2 mod 4 complex values (4 mod 8
+// words) puts the 16-byte reads of eight lanes on eight different bank quadruples.  Pair-density
+// rows load each lane's two lines from global memory.
+__host__ __device__ constexpr int p12_pitch(int n3) { return n3 + 2 + ((n3 % 4 == 2) ? 2 : 0); }
+
+__host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3, bool plane, bool stage = false)
 {
-    return align16(sizeof(float2) * ((plane ? (size_t)n2 * (n3 + 1) : 0) + (size_t)n2 * c3)) / sizeof(float2);
+    return (align16(sizeof(float2) * ((plane ? (size_t)n2 * (n3 + 1) : 0) + (size_t)n2 * c3)) +
+            (stage ? sizeof(float2) * (size_t)n2 * p12_pitch(n3) : 0)) /
+           sizeof(float2);
 }
 
 // Twiddle tables of the plane kernel, unrolled so the inner loops carry no index arithmetic:
@@ -319,11 +326,12 @@ __host__ __device__ inline size_t p12_tables(const int n[3], int c3, int cd, int
     return align16(sizeof(float2) * (size_t)c3 * n[2]) + align16(sizeof(float2) * t2);
 }
 
-__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, int np2, int k2, bool plane)
+__host__ __device__ inline size_t p12_smem(const int n[3], int c3, int cd, int np2, int k2, bool plane,
+                                           bool stage = false)
 {
     const size_t tables = align16(sizeof(float2) * (n[0] + n[1] + n[2]) + sizeof(int) * (c3 + 2 * cd));
     return tables + p12_tables(n, c3, cd, np2, k2) +
-           P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane) * sizeof(float2);
+           P12_WARPS * p12_warp_floats2(n[1], n[2], c3, plane, stage) * sizeof(float2);
 }
 
 // Pair-density rows (PAIR): row k of the transform is f_k(r) = conj(psi_v(r)) psi_c(r) w_k with
@@ -392,8 +400,12 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     __syncthreads();
     const int plane = n2 * n3;
     constexpr bool kPlane = N3 == 0;
-    float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3, kPlane);
+    constexpr bool kStage = N3 > 0 && N3 % 2 == 0 && !PAIR;  // plain rows: the plane staged in shared memory
+    constexpr int SP = N3 > 0 ? p12_pitch(N3) : 1;
+    float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3, kPlane, kStage);
     float2 *a1 = xp + (kPlane ? (size_t)n2 * (n3 + 1) : 0);
+    float2 *pl = xp + align16(sizeof(float2) * ((kPlane ? (size_t)n2 * (n3 + 1) : 0) + (size_t)n2 * c3)) /
+                          sizeof(float2);  // kStage: [n2][SP]
     const int ld3 = n3 + 1;
     // 16-byte loads of the lines need an even n3, an even row stride and an aligned base
     const bool vec = (N3 % 2 == 0) && (ldx % 2 == 0) && ((reinterpret_cast<size_t>(X) & 15) == 0);
@@ -433,13 +445,32 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
                 }
             }
         }
+        if (kStage && vec) {
+            // the whole plane with coalesced 16-byte loads (512 bytes per warp instruction) into
+            // rows of SP complex values
+            constexpr int QR = N3 / 2;  // 16-byte words per line
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll 4
+            for (int q = lane; q < n2 * QR; q += 32) {
+                const int j2 = q / QR, c = q - j2 * QR;
+                *reinterpret_cast<float4 *>(pl + j2 * SP + 2 * c) = __ldg(s4 + q);
+            }
+        }
         __syncwarp();
         // stage 1: a1[j2][i3] = sum_j3 x[j2][j3] e(m3 j3 / n3)
         if (N3 > 0) {
             for (int j2 = lane; j2 < n2; j2 += 32) {
                 float2 xr[N3 > 0 ? N3 : 1];
                 const float2 *line = src + (size_t)j2 * N3;  // the line from global memory (L1 keeps it)
-                if (vec) {
+                if (kStage && vec) {
+                    const float2 *ls = pl + j2 * SP;  // the staged line
+#pragma unroll
+                    for (int j3 = 0; j3 < N3; j3 += 2) {
+                        const float4 v = *reinterpret_cast<const float4 *>(ls + j3);
+                        xr[j3] = make_float2(v.x, v.y);
+                        xr[j3 + 1 < N3 ? j3 + 1 : j3] = make_float2(v.z, v.w);
+                    }
+                } else if (vec) {
 #pragma unroll
                     for (int j3 = 0; j3 < N3; j3 += 2) {
                         const float4 v = __ldg(reinterpret_cast<const float4 *>(line + j3));
@@ -744,6 +775,10 @@ template <int N3, bool PAIR>
 static cudaError_t launch_p12_t(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
                                 const float2 *tw, float2 *work, PairSrc ps, cudaStream_t s)
 {
+    if (N3 > 0 && N3 % 2 == 0 && !PAIR)  // the staged plane rows
+        smem = p12_smem(p.n, p.c3, p.cd, p.np2, p.k2, false, true);
+    if (smem > DFT_SMEM_MAX)
+        return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(dft_plane12_kernel<N3, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)

@@ -300,10 +300,10 @@ __global__ void hermitize_kernel(float2 *__restrict__ A, int n)
 constexpr int P12_WARPS = 8;
 
 // Per warp: a1 [n2][c3] and, for the generic stage 1 only, the plane [n2][n3 + 1] (rows padded:
-// one lane per row reads them).  The compiled stage 1 of plain rows (stage) copies the plane with
+// one lane per row reads them).  The compiled stage 1 (stage, even n3) copies the plane with
 // coalesced 16-byte loads into [n2][p12_pitch(n3)] rows: a pitch of 2 mod 4 complex values (4 mod 8
 // words) puts the 16-byte reads of eight lanes on eight different bank quadruples.  Pair-density
-// rows load each lane's two lines from global memory.
+// rows form their products conj(psi_v) psi_c w during that copy.
 __host__ __device__ constexpr int p12_pitch(int n3) { return n3 + 2 + ((n3 % 4 == 2) ? 2 : 0); }
 
 __host__ __device__ inline size_t p12_warp_floats2(int n2, int n3, int c3, bool plane, bool stage = false)
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     __syncthreads();
     const int plane = n2 * n3;
     constexpr bool kPlane = N3 == 0;
-    constexpr bool kStage = N3 > 0 && N3 % 2 == 0 && !PAIR;  // plain rows: the plane staged in shared memory
+    constexpr bool kStage = N3 > 0 && N3 % 2 == 0;  // the plane (or pair product) staged in shared memory
     constexpr int SP = N3 > 0 ? p12_pitch(N3) : 1;
     float2 *xp = wbase + (size_t)warp * p12_warp_floats2(n2, n3, c3, kPlane, kStage);
     float2 *a1 = xp + (kPlane ? (size_t)n2 * (n3 + 1) : 0);
@@ -450,10 +450,18 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
             // rows of SP complex values
             constexpr int QR = N3 / 2;  // 16-byte words per line
             const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            const float4 *v4 = reinterpret_cast<const float4 *>(srcv);
 #pragma unroll 4
             for (int q = lane; q < n2 * QR; q += 32) {
                 const int j2 = q / QR, c = q - j2 * QR;
-                *reinterpret_cast<float4 *>(pl + j2 * SP + 2 * c) = __ldg(s4 + q);
+                float4 x = __ldg(s4 + q);
+                if (PAIR) {  // x <- conj(psi_v) psi_c w
+                    const float4 a = __ldg(v4 + q);
+                    const float2 lo = pair_or_x<PAIR>(make_float2(a.x, a.y), make_float2(x.x, x.y), w);
+                    const float2 hi = pair_or_x<PAIR>(make_float2(a.z, a.w), make_float2(x.z, x.w), w);
+                    x = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+                *reinterpret_cast<float4 *>(pl + j2 * SP + 2 * c) = x;
             }
         }
         __syncwarp();
@@ -775,7 +783,7 @@ template <int N3, bool PAIR>
 static cudaError_t launch_p12_t(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
                                 const float2 *tw, float2 *work, PairSrc ps, cudaStream_t s)
 {
-    if (N3 > 0 && N3 % 2 == 0 && !PAIR)  // the staged plane rows
+    if (N3 > 0 && N3 % 2 == 0)  // the staged plane rows
         smem = p12_smem(p.n, p.c3, p.cd, p.np2, p.k2, false, true);
     if (smem > DFT_SMEM_MAX)
         return cudaErrorNotSupported;

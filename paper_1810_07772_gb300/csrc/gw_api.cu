@@ -386,6 +386,7 @@ gw_status build_plan(Ctx &c, int gcut)
         GW_CUDA(c.fplan.upload(c.d_fplan, c.stream), "transform plan upload");
     }
     c.gcut = gcut;
+    ++c.plan_gen;
     c.ng = ng;
     return GW_OK;
 }
@@ -609,6 +610,15 @@ void Ctx::release()
     dfree(d_cw);
     dfree(d_cgvec);
     dfree(d_cwork);
+    if (h_csw)
+        cudaFreeHost(h_csw);
+    if (h_cw)
+        cudaFreeHost(h_cw);
+    h_csw = nullptr;
+    h_cw = nullptr;
+    if (ev_cstage)
+        cudaEventDestroy(ev_cstage);
+    ev_cstage = nullptr;
     dfree(d_PGsum);
     dfree(d_coef);
     dfree(d_gidx);
@@ -1234,12 +1244,55 @@ gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_o
         c.tiles_g_pad = ng_pad;
     }
     c.F_prec = -1;  // the scale word now belongs to the closure's planes
-    GW_CUDA(cudaMemcpyAsync(c.d_csw, csw.data(), csw.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+    // the weights through pinned staging: wait for the previous call's upload to have read it
+    if (c.cstage_pending) {
+        GW_CUDA(cudaEventSynchronize(c.ev_cstage), "closure staging");
+        c.cstage_pending = false;
+    }
+    if (!c.ev_cstage)
+        GW_CUDA(cudaEventCreateWithFlags(&c.ev_cstage, cudaEventDisableTiming), "closure staging event");
+    if (c.cap_hcsw < csw.size()) {
+        if (c.h_csw)
+            cudaFreeHost(c.h_csw);
+        c.h_csw = nullptr;
+        c.cap_hcsw = 0;
+        GW_CUDA(cudaMallocHost(&c.h_csw, csw.size() * sizeof(float)), "closure staging");
+        c.cap_hcsw = csw.size();
+    }
+    if (c.cap_hcw < wv.size()) {
+        if (c.h_cw)
+            cudaFreeHost(c.h_cw);
+        c.h_cw = nullptr;
+        c.cap_hcw = 0;
+        GW_CUDA(cudaMallocHost(&c.h_cw, wv.size() * sizeof(double)), "closure staging");
+        c.cap_hcw = wv.size();
+    }
+    std::copy(csw.begin(), csw.end(), c.h_csw);
+    std::copy(wv.begin(), wv.end(), c.h_cw);
+    GW_CUDA(cudaMemcpyAsync(c.d_csw, c.h_csw, csw.size() * sizeof(float), cudaMemcpyHostToDevice, s),
             "closure weights");
-    GW_CUDA(cudaMemcpyAsync(c.d_cw, wv.data(), wv.size() * sizeof(double), cudaMemcpyHostToDevice, s),
+    GW_CUDA(cudaMemcpyAsync(c.d_cw, c.h_cw, wv.size() * sizeof(double), cudaMemcpyHostToDevice, s),
             "closure state weights");
-    GW_CUDA(cudaMemcpyAsync(c.d_cgvec, c.gvec.data(), (size_t)3 * ng * sizeof(int), cudaMemcpyHostToDevice, s),
-            "closure sphere");
+    GW_CUDA(cudaEventRecord(c.ev_cstage, s), "closure staging event");
+    c.cstage_pending = true;
+    // the sphere vectors once per plan, the twiddles once per grid (both synchronous, both rare)
+    if (c.cgvec_buf != c.d_cgvec || c.cgvec_gen != c.plan_gen) {
+        GW_CUDA(cudaMemcpyAsync(c.d_cgvec, c.gvec.data(), (size_t)3 * ng * sizeof(int), cudaMemcpyHostToDevice, s),
+                "closure sphere");
+        GW_CUDA(cudaStreamSynchronize(s), "closure sphere");
+        c.cgvec_buf = c.d_cgvec;
+        c.cgvec_gen = c.plan_gen;
+    }
+    {
+        const int dims[3] = {c.n1, c.n2, c.n3};
+        if (c.ctw_buf != c.d_cwork || c.ctw_dims[0] != dims[0] || c.ctw_dims[1] != dims[1] ||
+            c.ctw_dims[2] != dims[2]) {
+            GW_CUDA(closure_set_twiddles(dims, c.nr, c.d_cwork, s), "closure twiddles");
+            c.ctw_buf = c.d_cwork;
+            for (int a = 0; a < 3; ++a)
+                c.ctw_dims[a] = dims[a];
+        }
+    }
     const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
     int *scale_exp = reinterpret_cast<int *>(c.d_small + 1);
     float2 *o = static_cast<float2 *>(out);

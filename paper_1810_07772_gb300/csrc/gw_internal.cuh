@@ -187,6 +187,19 @@ struct Ctx {
     double *d_cw = nullptr;         // closure weights W_v / (N_r - nb) [nv]
     int *d_cgvec = nullptr;         // sphere vectors [ng][3] for the closure
     void *d_cwork = nullptr;        // closure workspace
+    // closure uploads without a stream sync: the weights go through pinned staging, reused once the
+    // event of the previous upload has passed; the twiddles and the sphere vectors go up once per
+    // grid / plan (the buffers they went into, and for which grid or plan)
+    float *h_csw = nullptr;
+    double *h_cw = nullptr;
+    size_t cap_hcsw = 0, cap_hcw = 0;
+    cudaEvent_t ev_cstage = nullptr;
+    bool cstage_pending = false;
+    const void *ctw_buf = nullptr;
+    int ctw_dims[3] = {0, 0, 0};
+    const void *cgvec_buf = nullptr;
+    int cgvec_gen = -1;
+    int plan_gen = 0;               // incremented by every plan build
     size_t cap_csw = 0, cap_cw = 0, cap_cgvec = 0, cap_cwork = 0;
     int last_herk_kernel = -1;      // the kernel of the last 16-bit r-space update
     double err_target = 0.0;        // > 0: the window comes from gw_set_error_target's rule
@@ -402,8 +415,11 @@ cudaError_t pp_iterate(PPWork &w, int ng, int b, int nmodes, double tol, int max
 cudaError_t pp_eval(const PPWork &w, int ng, int b, int nuse, double omega, double2 *Sout, cudaStream_t s);
 // The band-truncation closure estimate (gw_corr_closure): rhoG = FP64 transform, on the whole grid,
 // of rho_W(r) = sum_{v < nv} w[v] |psi_v(r)|^2 (work: 2 N_r double2 + 3 * 64 twiddles), then
-// out(g, h) = rhoG((m_g - m_h) mod n) - Ph(g, h) as complex64.
+// out(g, h) = rhoG((m_g - m_h) mod n) - Ph(g, h) as complex64.  closure_set_twiddles fills the
+// twiddles of the grid into the workspace (synchronously, once per grid); closure_enqueue is
+// asynchronous.
 size_t closure_work_bytes(int nr);
+cudaError_t closure_set_twiddles(const int dims[3], int nr, void *work, cudaStream_t s);
 cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
                             const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work,
                             cudaStream_t s);

@@ -520,12 +520,10 @@ size_t closure_work_bytes(int nr)
     return (size_t)2 * nr * sizeof(double2) + 3 * 64 * sizeof(double2);
 }
 
-cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
-                            const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work, cudaStream_t s)
+cudaError_t closure_set_twiddles(const int dims[3], int nr, void *work, cudaStream_t s)
 {
-    double2 *rho = static_cast<double2 *>(work), *rho2 = rho + nr, *tw = rho2 + nr;
-    const int n1 = dims[0], n2 = dims[1], n3 = dims[2];
-    if (n1 > 64 || n2 > 64 || n3 > 64)
+    double2 *tw = static_cast<double2 *>(work) + 2 * (size_t)nr;
+    if (dims[0] > 64 || dims[1] > 64 || dims[2] > 64)
         return cudaErrorInvalidValue;
     double2 twh[3 * 64];
     for (int a = 0; a < 3; ++a)
@@ -533,18 +531,26 @@ cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const do
             const double ph = -6.283185307179586476925 * t / dims[a];
             twh[64 * a + t] = make_double2(std::cos(ph), std::sin(ph));
         }
-    cudaError_t e = cudaMemcpyAsync(tw, twh, sizeof twh, cudaMemcpyHostToDevice, s);
+    const cudaError_t e = cudaMemcpyAsync(tw, twh, sizeof twh, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return e;
+    return cudaStreamSynchronize(s);  // twh is a host local; once per grid
+}
+
+cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
+                            const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work, cudaStream_t s)
+{
+    double2 *rho = static_cast<double2 *>(work), *rho2 = rho + nr, *tw = rho2 + nr;
+    const int n1 = dims[0], n2 = dims[1], n3 = dims[2];
+    if (n1 > 64 || n2 > 64 || n3 > 64)
+        return cudaErrorInvalidValue;
     weighted_density_kernel<<<blocks_for(nr), 256, 0, s>>>(psiT, nr, nb, nv, w, rho);
     dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho, rho2, nr, n3, 1, tw + 128);
     dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho2, rho, nr, n2, n3, tw + 64);
     dft_axis64_kernel<<<blocks_for(nr), 256, 0, s>>>(rho, rho2, nr, n1, n2 * n3, tw);
     closure_combine_kernel<<<grid2(ng, ng), 256, 0, s>>>(rho2, gvec_dev, ng, n1, n2, n3, Ph, out);
     count_launches(5);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    return cudaStreamSynchronize(s);  // twh is a host local
+    return cudaGetLastError();
 }
 
 cudaError_t pp_prepare(const PPWork &w, const double2 *epsinv, const double *sv, const float2 *psiT, int ng, int nr,

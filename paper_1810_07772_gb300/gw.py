@@ -587,11 +587,25 @@ class CorrTrainOpts(ctypes.Structure):
                 ("diag_feature", ctypes.c_int)]
 
 
+def _upload(arr, dtype, dev, stream):
+    """A host array on the device: staged in pinned memory and copied on the library's stream without
+    a host synchronisation (a copy from pageable memory would wait for the stream's earlier work)."""
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(np.asarray(arr, dtype=dtype))).pin_memory()
+    h = _stream_handle(dev.index, stream)
+    s = torch.cuda.ExternalStream(h, device=dev) if h else torch.cuda.default_stream(dev)
+    with torch.cuda.stream(s):
+        return t.to(dev, non_blocking=True)
+
+
 def corr_weight_ratio(E_eV, nv, nc_keep, device=0, stream=None):
-    """Device float: weight of the omitted pairs relative to the kept ones (gw_corr_weight_ratio)."""
+    """Device float: weight of the omitted pairs relative to the kept ones (gw_corr_weight_ratio).
+    E_eV: host energies, or a float64 device tensor."""
     import torch
     dev = torch.device(f"cuda:{device}")
-    E = torch.as_tensor(np.asarray(E_eV, dtype=np.float64)).to(dev)
+    on_dev = isinstance(E_eV, torch.Tensor) and E_eV.is_cuda and E_eV.dtype == torch.float64
+    E = E_eV if on_dev else _upload(E_eV.cpu().numpy() if isinstance(E_eV, torch.Tensor) else E_eV, np.float64, dev,
+                                    stream)
     out = torch.empty(1, dtype=torch.float32, device=dev)
     _status(lib().gw_corr_weight_ratio(_ptr(E), int(nv), int(nc_keep), E.shape[0] - int(nv), _ptr(out),
                                        _stream_handle(device, stream)), "gw_corr_weight_ratio")
@@ -604,7 +618,9 @@ def corr_features(PG, gvec, gcut, ratio, clos=None, stream=None):
     import torch
     dev = PG.device
     ng = PG.shape[0]
-    g = torch.as_tensor(np.ascontiguousarray(np.asarray(gvec, dtype=np.int32))).to(dev)
+    on_dev = isinstance(gvec, torch.Tensor) and gvec.is_cuda and gvec.dtype == torch.int32
+    g = gvec if on_dev else _upload(gvec.cpu().numpy() if isinstance(gvec, torch.Tensor) else gvec, np.int32, dev,
+                                    stream)
     X = torch.empty((ng * (ng + 1) // 2, N_FEATURES), dtype=torch.float32, device=dev)
     scale = torch.empty(1, dtype=torch.float32, device=dev)
     _status(lib().gw_corr_features(_ptr(PG), ng, _ptr(g), int(gcut), _ptr(ratio), _ptr(clos), _ptr(X), _ptr(scale),

@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cub/cub.cuh>
 
 #include "gw_internal.cuh"
@@ -50,32 +51,80 @@ __device__ __forceinline__ long tri_index(int g, int h, int ng)
 // Per-system scalars
 
 // ratio = sum_{c >= keep} sum_v 2/(E_c - E_v)  /  sum_{c < keep} sum_v 2/(E_c - E_v)   (FP64)
-__global__ void __launch_bounds__(256) weight_ratio_kernel(const double *E, int nv, int keep, int nc_all,
-                                                           float *ratio)
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the nv nc_all terms are spread
+// over one cluster of RATIO_CLUSTER blocks, a thread per unoccupied state c at a time (the
+// occupied energies in each block's shared memory).  1/d is the hardware FP32 reciprocal
+// approximation (relative error ~2^-23, seeded with d rounded to FP32) refined by one FP64
+// Newton-Raphson step r <- r + r (1 - d r), which squares the relative error to ~2^-45, instead of
+// an FP64 division per term.  The blocks' partial sums are added by block 0 through distributed
+// shared memory in rank order, so the result does not depend on scheduling.
+constexpr int RATIO_THREADS = 512;
+constexpr int RATIO_CLUSTER = 8;
+constexpr int RATIO_MAX_NV = 1024;
+
+__device__ __forceinline__ double recip_nr(double d)
 {
-    __shared__ double s_om[256], s_in[256];
-    double om = 0, in = 0;
-    const long total = (long)nv * nc_all;
-    for (long i = threadIdx.x; i < total; i += blockDim.x) {
-        const int v = (int)(i / nc_all), c = (int)(i % nc_all);
-        const double w = 2.0 / (E[nv + c] - E[v]);
-        if (c < keep)
-            in += w;
-        else
-            om += w;
-    }
-    s_om[threadIdx.x] = om;
-    s_in[threadIdx.x] = in;
+    if (!(fabs(d) > 1e-30 && fabs(d) < 1e30))  // outside the FP32 seed's normal range
+        return 1.0 / d;
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)d));
+    const double r = (double)r0;
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
+__global__ void __cluster_dims__(RATIO_CLUSTER, 1, 1) __launch_bounds__(RATIO_THREADS)
+    weight_ratio_kernel(const double *E, int nv, int keep, int nc_all, float *ratio)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double ev[RATIO_MAX_NV];
+    __shared__ double s_om[RATIO_THREADS / 32], s_in[RATIO_THREADS / 32];
+    __shared__ double part[2];
+    for (int v = threadIdx.x; v < nv; v += RATIO_THREADS)
+        ev[v] = E[v];
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            s_om[threadIdx.x] += s_om[threadIdx.x + o];
-            s_in[threadIdx.x] += s_in[threadIdx.x + o];
-        }
-        __syncthreads();
+    double om = 0, in = 0;
+    for (int c = (int)cluster.block_rank() * RATIO_THREADS + threadIdx.x; c < nc_all;
+         c += RATIO_THREADS * RATIO_CLUSTER) {
+        const double ec = E[nv + c];
+        double acc = 0;
+        for (int v = 0; v < nv; ++v)
+            acc += recip_nr(ec - ev[v]);
+        if (c < keep)
+            in += 2.0 * acc;
+        else
+            om += 2.0 * acc;
     }
-    if (threadIdx.x == 0)
-        *ratio = (float)(s_om[0] / s_in[0]);
+    for (int o = 16; o > 0; o >>= 1) {
+        om += __shfl_xor_sync(0xffffffffu, om, o);
+        in += __shfl_xor_sync(0xffffffffu, in, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_om[warp] = om;
+        s_in[warp] = in;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int w = 0; w < RATIO_THREADS / 32; ++w) {
+            a += s_om[w];
+            b += s_in[w];
+        }
+        part[0] = a;
+        part[1] = b;
+    }
+    cluster.sync();  // every block's partial sums are written
+    if (cluster.block_rank() == 0 && threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (unsigned r = 0; r < RATIO_CLUSTER; ++r) {
+            const double *p = cluster.map_shared_rank(part, r);
+            a += p[0];
+            b += p[1];
+        }
+        *ratio = (float)(a / b);
+    }
+    cluster.sync();  // the other blocks keep their shared memory until block 0 has read it
 }
 
 // s = 1 / mean_{g >= 1} |Re P~(g, g)|  (FP64 sum)
@@ -924,9 +973,10 @@ gw_status gw_corr_train(gw_mlp *m, const float *X, const float *T, long n, const
 
 gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_all, float *ratio, void *stream)
 {
-    if (!E_eV || !ratio || nv < 1 || nc_keep < 1 || nc_all <= nc_keep)
+    if (!E_eV || !ratio || nv < 1 || nv > RATIO_MAX_NV || nc_keep < 1 || nc_all <= nc_keep)
         return GW_E_INVALID;
-    weight_ratio_kernel<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(E_eV, nv, nc_keep, nc_all, ratio);
+    weight_ratio_kernel<<<RATIO_CLUSTER, RATIO_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(E_eV, nv, nc_keep,
+                                                                                               nc_all, ratio);
     gw::count_launches(1);
     return cudaGetLastError() == cudaSuccess ? GW_OK : GW_E_CUDA;
 }

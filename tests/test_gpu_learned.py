@@ -218,6 +218,20 @@ def _rel(A, B):
 
 
 @pytest.mark.slow
+def test_weight_ratio_at_the_occupied_limit():
+    """The omitted/kept weight ratio of Eq. (Pstatic) at the largest supported nv (1024) and with
+    more unoccupied states than one pass of the block (3000), against the FP64 sums; nv = 1025 is
+    rejected."""
+    rng = np.random.default_rng(31)
+    nv, nc_all, keep = 1024, 3000, 1100
+    E = np.concatenate([np.sort(rng.uniform(-25.0, -0.2, nv)), np.sort(rng.uniform(0.05, 80.0, nc_all))])
+    w_om, w_in = M.omitted_weights(E, nv, keep)
+    ratio = float(gw.corr_weight_ratio(E, nv, keep).item())
+    assert abs(ratio - w_om / w_in) <= 1e-7 * (w_om / w_in)
+    with pytest.raises(gw.GwError):
+        gw.corr_weight_ratio(np.concatenate([E[:1], E]), nv + 1, keep)
+
+
 def test_learned_correction_gain_24cubed():
     """24^3, N_v = 32, N_c = 200 kept of 2000; 64 training systems, 8 held-out systems."""
     dev = torch.device("cuda:0")

@@ -69,7 +69,7 @@ def parse_args(argv=None):
                     help="skip the split, batch and learned configurations that the default run appends")
     ap.add_argument("--herk-kernel", choices=["single", "pair"], default=HERK_KERNEL,
                     help="kernel of the 16-bit rank-k update")
-    ap.add_argument("--transform", choices=["two_kernel", "fused"], default="two_kernel",
+    ap.add_argument("--transform", choices=["two_kernel", "tables", "fused"], default="two_kernel",
                     help="kernel of the sphere transforms")
     ap.add_argument("--extra-steps", type=int, default=3,
                     help="timed steps of each appended configuration (after --warmup untimed ones)")

@@ -408,15 +408,19 @@ GW_API gw_status gw_set_herk_kernel(gw_ctx *ctx, int kind);
  * Kernel of the sphere transforms (the two FFT phases of Sec. 4.1, pruned to the eps sphere) in
  * gw_P_to_G, gw_build_PG and the batch:
  *   GW_TRANSFORM_TWO_KERNEL (default) planes transformed over j3 and j2 into a workspace, then j1 per
- *                           row
+ *                           row; where n2 = n3 is 12, 16, 18, 20, 24 or 27 and the sphere is
+ *                           centred (q = 0) with max |m3| <= 7, the j3 and j2 sums take their
+ *                           twiddles as compile-time constants, else from tables in shared memory
+ *   GW_TRANSFORM_TABLES     the two-kernel form with twiddle tables everywhere (the form of the
+ *                           other grids), kept for comparison
  *   GW_TRANSFORM_FUSED      one kernel per pass: each row is streamed plane by plane into shared
  *                           memory by bulk copies and transformed axis by axis (j1, j2, j3) there,
  *                           reading P from HBM exactly once; used where N_r and n2 n3 are even and
  *                           max |m| <= 8, else the two-kernel form.  Measured slower at 24^3
  *                           (0.96 against 0.83 ms for the row pass; equal on the g-space route)
- * Both give the same sums up to FP32 rounding.  GW_E_INVALID for another value.
+ * All give the same sums up to FP32 rounding.  GW_E_INVALID for another value.
  */
-enum { GW_TRANSFORM_TWO_KERNEL = 0, GW_TRANSFORM_FUSED = 1 };
+enum { GW_TRANSFORM_TWO_KERNEL = 0, GW_TRANSFORM_FUSED = 1, GW_TRANSFORM_TABLES = 2 };
 GW_API gw_status gw_set_transform_kernel(gw_ctx *ctx, int kind);
 
 /*
@@ -572,7 +576,8 @@ GW_API gw_status gw_corr_train(gw_mlp *m, const float *X, const float *T, long n
 /* ratio = sum_{c >= nc_keep} sum_v 2/(E_c - E_v) / sum_{c < nc_keep} sum_v 2/(E_c - E_v), in FP64,
  * from device energies E_eV[nv + nc_all] (occupied first, as gw_load_states).  This is the
  * weight of the omitted pairs in Eq. (Pstatic) relative to the kept ones; it needs only the
- * energies of the omitted states, not their orbitals.  Output: one device float. */
+ * energies of the omitted states, not their orbitals.  nv <= 1024 (else GW_E_INVALID).  Output:
+ * one device float. */
 GW_API gw_status gw_corr_weight_ratio(const double *E_eV, int nv, int nc_keep, int nc_all, float *ratio,
                                       void *stream);
 

@@ -1028,14 +1028,15 @@ cudaError_t transform_rows(Ctx &c, const float2 *X, long long ldx, int rows, flo
         if (e != cudaErrorNotSupported)
             return e;
     }
+    const bool cst = c.transform_kind != GW_TRANSFORM_TABLES;
     if (sw)
-        return launch_dft_pairs_ws(X, ldx, sw, nv, nc, Y, ldy, c.plan, c.d_dftw, s, negexp, c0);
-    return launch_dft_rows_ws(X, ldx, rows, Y, ldy, c.plan, c.d_dftw, s, negexp);
+        return launch_dft_pairs_ws(X, ldx, sw, nv, nc, Y, ldy, c.plan, c.d_dftw, s, negexp, c0, cst);
+    return launch_dft_rows_ws(X, ldx, rows, Y, ldy, c.plan, c.d_dftw, s, negexp, cst);
 }
 
 gw_status gw_set_transform_kernel(gw_ctx *h, int kind)
 {
-    if (!h || (kind != GW_TRANSFORM_TWO_KERNEL && kind != GW_TRANSFORM_FUSED))
+    if (!h || (kind != GW_TRANSFORM_TWO_KERNEL && kind != GW_TRANSFORM_FUSED && kind != GW_TRANSFORM_TABLES))
         return GW_E_INVALID;
     h->c.transform_kind = kind;
     return GW_OK;
@@ -1152,7 +1153,8 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
         float2 *Fc = reinterpret_cast<float2 *>(c.d_F);
         GW_CUDA(launch_pair_density_rows(c.d_psiT, c.d_sw, c.nr, c.nb, c.nv, c.nc, k, c.nr_pad, Fc, s),
                 "pair densities");
-        fe = launch_dft_rows_ws(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, c.d_dftw, s, true);
+        fe = launch_dft_rows_ws(Fc, c.nr_pad, k, c.d_Q, ng, c.plan, c.d_dftw, s, true,
+                                c.transform_kind != GW_TRANSFORM_TABLES);
     }
     GW_CUDA(fe, "pair-density transforms");
     record(c, 4);

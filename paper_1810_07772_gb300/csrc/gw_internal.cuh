@@ -343,17 +343,20 @@ cudaError_t launch_dft_fused(const float2 *X, long long ldx, int rows, float2 *Y
 size_t dft_smem_bytes(const DftPlan &p, int rows_per_cta);
 bool dft_supported(const DftPlan &p);  // sphere small enough for the transform kernel
 // Two-kernel form with a workspace of dft_work_bytes(p, rows) (stages 1 and 2 per plane, stage 3
-// per row).
+// per row).  const_twiddles: stages 1 and 2 with compile-time twiddles where the plan allows
+// (square planes of a compiled size up to 27, spheres at q = 0 with max |m3| <= 7), else twiddle
+// tables in shared memory.
 size_t dft_work_bytes(const DftPlan &p, int rows);
 cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                               float2 *work, cudaStream_t s, bool negative_exponent = false);
+                               float2 *work, cudaStream_t s, bool negative_exponent = false,
+                               bool const_twiddles = true);
 // The same transform of the nv nc pair densities f_k = conj(psi_v) psi_c sw[k] (k = v nc + c),
 // formed from the states psi [nb][nr] inside the kernel; row k of Y is f_k's transform.
 // cudaErrorNotSupported (nothing launched) where the grid needs the row-block kernel.
 // c0: state index of the first c of the pairs (-1: nv, the unoccupied states).
 cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
                                 long long ldy, const DftPlan &p, float2 *work, cudaStream_t s,
-                                bool negative_exponent, int c0 = -1);
+                                bool negative_exponent, int c0 = -1, bool const_twiddles = true);
 // negative_exponent: exp(-iG.r) instead of exp(+iG.r) (the conjugated twiddle table)
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                             const DftPlan &p, cudaStream_t s, bool negative_exponent = false);

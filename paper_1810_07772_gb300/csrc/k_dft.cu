@@ -14,6 +14,7 @@
 // transform with exp(+iG.r) is the column transform with exp(-iG.r)), and, after a conjugate
 // transpose, to the rows of that intermediate, which yields P~(G, G').
 #include <algorithm>
+#include <utility>
 
 #include "gw_internal.cuh"
 
@@ -64,6 +65,14 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 x, float2 w)
 __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(
+                     dst_smem))),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(
                      dst_smem))),
                  "l"(src)
                  : "memory");
@@ -345,10 +354,12 @@ struct PairSrc {
     int c0;  // state index of the first c (nv for the unoccupied states, 0 for all loaded states)
 };
 
+// The product times w is rounded on its own (__fmul_rn): where the caller adds it to something the
+// compiler would otherwise contract the two into one FMA and round differently.
 template <bool PAIR>
 __device__ __forceinline__ float2 pair_or_x(float2 a, float2 b, float w)
 {
-    return PAIR ? make_float2(fmaf(a.x, b.x, a.y * b.y) * w, fmaf(a.x, b.y, -a.y * b.x) * w) : a;
+    return PAIR ? make_float2(__fmul_rn(fmaf(a.x, b.x, a.y * b.y), w), __fmul_rn(fmaf(a.x, b.y, -a.y * b.x), w)) : a;
 }
 
 template <int N3, bool PAIR>  // N3 = 0: any n3 (one output per lane)
@@ -603,18 +614,342 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Stages 1 and 2 with constant twiddles: square planes (n2 = n3 = N, a compiled size), spheres
+// whose m3 values are exactly -M..M and whose disk is symmetric in m2.  The sums are the paired
+// sums above, but every cos(2 pi m j / N) and sin(2 pi m j / N) is a compile-time constant, so
+// each FMA takes its twiddle as an immediate operand and neither stage reads a table.  Stage 1
+// keeps one line j2 per lane (outputs m3 = -M..M) and writes them transposed, a1t[i3][j2];
+// stage 2 keeps one column i3 per lane and makes the outputs (+-m2, m3) for m2 = 0..k2.  The
+// shared-memory traffic per plane is the staged plane, the transposed a1 and the cd outputs,
+// against one broadcast twiddle read per four FMAs in the table form.
+//
+// The constants are the Taylor series of cosine and sine after an exact integer reduction of the
+// angle to [0, pi/4], evaluated in FP64 by the compiler and rounded to FP32 once (the same values
+// as the FP64-derived tables of the other kernels, up to the last bit of FP64).
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr double taylor_cos(double x)  // |x| <= pi/4: 12 terms leave < 1e-28
+{
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double taylor_sin(double x)  // |x| <= pi/4
+{
+    double term = x, sum = x;
+    for (int k = 1; k <= 12; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+
+// cos(2 pi q / n): r = q mod n folded to [0, n/2] (cosine is even about pi); the angle is then
+// (pi/2) u / n with u = 4 r, folded to u <= n by cos(pi - t) = -cos t, and above pi/4 taken as
+// sin(pi/2 - t).
+constexpr double cos_turn(long long q, long long n)
+{
+    long long r = q % n;
+    if (r < 0)
+        r += n;
+    if (2 * r > n)
+        r = n - r;
+    long long u = 4 * r;
+    double sg = 1.0;
+    if (u > n) {
+        u = 2 * n - u;
+        sg = -1.0;
+    }
+    if (2 * u > n)
+        return sg * taylor_sin(0.5 * kPi * (double)(n - u) / (double)n);
+    return sg * taylor_cos(0.5 * kPi * (double)u / (double)n);
+}
+
+template <int N, int Q>
+constexpr float kcos = static_cast<float>(cos_turn(Q, N));
+template <int N, int Q>  // sin(2 pi q / n) = cos(2 pi (4 q - n) / (4 n))
+constexpr float ksin = static_cast<float>(cos_turn(4LL * Q - N, 4LL * N));
+
+// One term j of the paired sums of output m: A += s_j cos, B += t_j sin (s_j in x[j], t_j in
+// x[N - j]); a zero constant drops its FMAs.
+template <int N, int M, int J>
+__device__ __forceinline__ void pterm(const float2 (&x)[N], float2 &A, float2 &B)
+{
+    constexpr float c = kcos<N, M * J>, s = ksin<N, M * J>;
+    if constexpr (c != 0.f) {
+        A.x = fmaf(x[J].x, c, A.x);
+        A.y = fmaf(x[J].y, c, A.y);
+    }
+    if constexpr (s != 0.f) {
+        B.x = fmaf(x[N - J].x, s, B.x);
+        B.y = fmaf(x[N - J].y, s, B.y);
+    }
+}
+
+// A = x_0 + (-1)^M x_{N/2} + sum_{0<j<N/2} s_j cos(2 pi M j / N),  B = sum_{0<j<N/2} t_j sin(2 pi M j / N)
+template <int N, int M, int... J>
+__device__ __forceinline__ void paired_sums(const float2 (&x)[N], float2 &A, float2 &B,
+                                            std::integer_sequence<int, J...>)
+{
+    A = x[0];
+    if constexpr (N % 2 == 0) {
+        constexpr float sg = (M & 1) ? -1.f : 1.f;
+        A.x = fmaf(sg, x[N / 2].x, A.x);
+        A.y = fmaf(sg, x[N / 2].y, A.y);
+    }
+    B = make_float2(0.f, 0.f);
+    (pterm<N, M, J + 1>(x, A, B), ...);
+}
+
+// x[j] <- x[j] + x[N - j], x[N - j] <- x[j] - x[N - j] for 0 < j < N / 2
+template <int N>
+__device__ __forceinline__ void pair_fold(float2 (&x)[N])
+{
+#pragma unroll
+    for (int j = 1; j <= (N - 1) / 2; ++j) {
+        const float2 u = x[j], v = x[N - j];
+        x[j] = make_float2(u.x + v.x, u.y + v.y);
+        x[N - j] = make_float2(u.x - v.x, u.y - v.y);
+    }
+}
+
+// Stage-1 outputs m3 = +-Mo of a line (Mo <= M at run time): a1t rows M + Mo and M - Mo.  With
+// sgn = -1 (negative exponent) the sine sums change sign.
+template <int N, int Mo>
+__device__ __forceinline__ void stage1_out(const float2 (&x)[N], int M, float sgn, float2 *col, int lda)
+{
+    if (Mo <= M) {
+        float2 A, B;
+        paired_sums<N, Mo>(x, A, B, std::make_integer_sequence<int, (N - 1) / 2>{});
+        const float bx = sgn * B.x, by = sgn * B.y;
+        col[(M + Mo) * lda] = make_float2(A.x - by, A.y + bx);
+        col[(M - Mo) * lda] = make_float2(A.x + by, A.y - bx);
+    }
+}
+
+template <int N, int... Mo>
+__device__ __forceinline__ void stage1_all(const float2 (&x)[N], int M, float sgn, float2 *col, int lda,
+                                           std::integer_sequence<int, Mo...>)
+{
+    (stage1_out<N, Mo + 1>(x, M, sgn, col, lda), ...);
+}
+
+// Stage-2 outputs (+-Mo, m3) of a column (Mo <= k2 at run time), into ys at the disk indices
+// dt[Mo] = (index of +Mo, index of -Mo or -1).
+template <int N, int Mo>
+__device__ __forceinline__ void stage2_out(const float2 (&y)[N], int k2, float sgn, const int2 *dt, float2 *ys)
+{
+    if (Mo <= k2) {
+        float2 A, B;
+        paired_sums<N, Mo>(y, A, B, std::make_integer_sequence<int, (N - 1) / 2>{});
+        const int2 d = dt[Mo];
+        const float bx = sgn * B.x, by = sgn * B.y;
+        if (d.x >= 0)
+            ys[d.x] = make_float2(A.x - by, A.y + bx);
+        if (Mo > 0 && d.y >= 0)
+            ys[d.y] = make_float2(A.x + by, A.y - bx);
+    }
+}
+
+template <int N, int... Mo>
+__device__ __forceinline__ void stage2_all(const float2 (&y)[N], int k2, float sgn, const int2 *dt, float2 *ys,
+                                           std::integer_sequence<int, Mo...>)
+{
+    (stage2_out<N, Mo>(y, k2, sgn, dt, ys), ...);
+}
+
+// Per warp: the staged plane [N][p12_pitch(N)], then a1t [c3][N | 1] of two planes (an odd pitch:
+// lanes on different columns read different banks), each reused for that plane's cd outputs; an
+// even count of float2 so the next warp's plane stays 16-byte aligned.
+__host__ __device__ inline size_t p12c_warp_floats2(int N, int c3)
+{
+    return ((size_t)N * p12_pitch(N) + 2 * (size_t)c3 * (N | 1) + 1) & ~(size_t)1;
+}
+
+__host__ __device__ inline size_t p12c_smem(int N, int c3)
+{
+    return align16(sizeof(int2) * (size_t)c3 * ((N - 1) / 2 + 1)) + P12_WARPS * p12c_warp_floats2(N, c3) * sizeof(float2);
+}
+
+constexpr int P12C_MAX_C3 = 16;  // stage 2 runs two planes side by side, one per half-warp
+
+// A warp takes two tasks (planes) at a time: stage 1 of each (a lane per line), then stage 2 of
+// both together, lanes 0-15 on the first plane's columns and lanes 16-31 on the second's, so a
+// sphere with c3 <= 16 keeps twice as many lanes busy in stage 2 as one plane would.
+template <int N, bool PAIR>  // two CTAs per SM (shared memory allows two at every compiled N)
+__global__ void __launch_bounds__(P12_WARPS * 32, 2)
+    dft_plane12c_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int M, int cd, int np2, int k2,
+                        const int4 *__restrict__ g_pair2, float sgn, float2 *__restrict__ Y2, PairSrc ps)
+{
+    constexpr int H = (N - 1) / 2;
+    constexpr int SP = p12_pitch(N);
+    constexpr int LDA = N | 1;
+    constexpr int plane = N * N;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int c3 = 2 * M + 1;
+    int2 *dtab = reinterpret_cast<int2 *>(smem);  // [c3][H + 1]
+    float2 *wbase = reinterpret_cast<float2 *>(smem + align16(sizeof(int2) * (size_t)c3 * (H + 1)));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int t = tid; t < c3 * (H + 1); t += blockDim.x)
+        dtab[t] = make_int2(-1, -1);
+    __syncthreads();
+    for (int t = tid; t < np2; t += blockDim.x) {
+        const int4 pr = g_pair2[t];  // (i3, m2 >= 0, disk index of m2, of -m2 or -1)
+        dtab[pr.x * (H + 1) + pr.y] = make_int2(pr.z, pr.w);
+    }
+    __syncthreads();
+    float2 *pl = wbase + (size_t)warp * p12c_warp_floats2(N, c3);  // [N][SP]
+    float2 *a1t0 = pl + N * SP;                                     // [c3][LDA], first plane
+    float2 *a1t1 = a1t0 + c3 * LDA;                                 // [c3][LDA], second plane
+    const bool vec = (N % 2 == 0) && (ldx % 2 == 0) && ((reinterpret_cast<size_t>(X) & 15) == 0);
+    // task -> (row, j1): plain rows row-major, pair rows j1-major (the warps of a CTA share psi_v);
+    // 32-bit arithmetic (the launcher keeps rows n1 below 2^31)
+    const unsigned ntasks = (unsigned)rows * (unsigned)n1, npairs = (ntasks + 1) / 2;
+    auto locate = [&](unsigned task, long long &row, int &j1) {
+        if (PAIR) {
+            const unsigned q = task / (unsigned)rows;
+            j1 = (int)q;
+            row = (long long)(task - q * (unsigned)rows);
+        } else {
+            const unsigned q = task / (unsigned)n1;
+            row = (long long)q;
+            j1 = (int)(task - q * (unsigned)n1);
+        }
+    };
+    // one plane into pl (pair densities formed on the way), then stage 1 into a1t:
+    // a1t[M + m3][j2] = sum_j3 x[j2][j3] e(+-m3 j3 / N)
+    auto plane_stage1 = [&](long long row, int j1, float2 *a1t) {
+        const float2 *src, *srcv = nullptr;
+        float w = 0.f;
+        if (PAIR) {
+            const int kk = (int)row, v = kk / ps.nc;
+            src = X + (size_t)(ps.c0 + kk - v * ps.nc) * ldx + (size_t)j1 * plane;
+            srcv = X + (size_t)v * ldx + (size_t)j1 * plane;
+            w = ps.sw[kk];
+        } else {
+            src = X + row * ldx + (size_t)j1 * plane;
+        }
+        if (N % 2 == 0 && vec) {
+            constexpr int QR = N / 2;  // 16-byte words per line
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            const float4 *v4 = reinterpret_cast<const float4 *>(srcv);
+            constexpr int UNR = PAIR ? 4 : 8;  // loads in flight per lane (pair rows load two values)
+#pragma unroll UNR
+            for (int q = lane; q < N * QR; q += 32) {
+                const int j2 = q / QR, c = q - j2 * QR;
+                float4 x = __ldg(s4 + q);
+                if (PAIR) {
+                    const float4 a = __ldg(v4 + q);
+                    const float2 lo = pair_or_x<PAIR>(make_float2(a.x, a.y), make_float2(x.x, x.y), w);
+                    const float2 hi = pair_or_x<PAIR>(make_float2(a.z, a.w), make_float2(x.z, x.w), w);
+                    x = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+                *reinterpret_cast<float4 *>(pl + j2 * SP + 2 * c) = x;
+            }
+        } else {
+#pragma unroll 8
+            for (int q = lane; q < plane; q += 32) {
+                const int j2 = q / N, j3 = q - j2 * N;
+                const float2 xs = __ldg(src + q);
+                pl[j2 * SP + j3] = PAIR ? pair_or_x<true>(__ldg(srcv + q), xs, w) : xs;
+            }
+        }
+        __syncwarp();
+        for (int j2 = lane; j2 < N; j2 += 32) {
+            float2 x[N];
+            const float2 *ls = pl + j2 * SP;
+            if constexpr (N % 2 == 0) {
+#pragma unroll
+                for (int j = 0; j < N; j += 2) {
+                    const float4 v = *reinterpret_cast<const float4 *>(ls + j);
+                    x[j] = make_float2(v.x, v.y);
+                    x[j + 1] = make_float2(v.z, v.w);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    x[j] = ls[j];
+            }
+            pair_fold<N>(x);
+            float2 a0 = x[0];
+#pragma unroll
+            for (int j = 1; j <= H; ++j) {  // the m3 = 0 sum, in the order of the table form
+                a0.x += x[j].x;
+                a0.y += x[j].y;
+            }
+            float2 *col = a1t + j2;
+            if constexpr (N % 2 == 0)
+                col[M * LDA] = make_float2(a0.x + x[N / 2].x, a0.y + x[N / 2].y);
+            else
+                col[M * LDA] = a0;
+            stage1_all<N>(x, M, sgn, col, LDA, std::make_integer_sequence<int, H>{});
+        }
+        __syncwarp();  // pl is rewritten by the next plane
+    };
+    for (unsigned u = blockIdx.x * P12_WARPS + warp; u < npairs; u += gridDim.x * P12_WARPS) {
+        const unsigned tA = 2 * u, tB = tA + 1;
+        const bool hasB = tB < ntasks;
+        long long rowA, rowB = 0;
+        int j1A, j1B = 0;
+        locate(tA, rowA, j1A);
+        plane_stage1(rowA, j1A, a1t0);
+        if (hasB) {
+            locate(tB, rowB, j1B);
+            plane_stage1(rowB, j1B, a1t1);
+        }
+        // stage 2: ys[d] = sum_j2 a1t[i3][j2] e(+-m2 j2 / N) for the disk points d = (m2, m3(i3)),
+        // written over the plane's a1t once every lane holds its column
+        const int half = lane >> 4, i3 = lane & 15;
+        float2 *a1t = half ? a1t1 : a1t0;
+        const bool act = i3 < c3 && (half == 0 || hasB);
+        float2 y[N];
+        if (act) {
+            const float2 *cs = a1t + i3 * LDA;
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+                y[j] = cs[j];
+        }
+        __syncwarp();
+        if (act) {
+            pair_fold<N>(y);
+            stage2_all<N>(y, k2, sgn, dtab + i3 * (H + 1), a1t, std::make_integer_sequence<int, H + 1>{});
+        }
+        __syncwarp();
+        float2 *dA = Y2 + (rowA * n1 + j1A) * cd;
+        for (int t = lane; t < cd; t += 32)
+            dA[t] = a1t0[t];
+        if (hasB) {
+            float2 *dB = Y2 + (rowB * n1 + j1B) * cd;
+            for (int t = lane; t < cd; t += 32)
+                dB[t] = a1t1[t];
+        }
+        __syncwarp();  // a1t is rewritten by the next pair
+    }
+}
+
 // Stage 3 with sphere pairs (np1 > 0): y(+-m1, d) = A +- i B from the sums of
 // ys[j1][d] + ys[n1 - j1][d] (times the cosine) and ys[j1][d] - ys[n1 - j1][d] (times the sine),
 // formed while the row is loaded; tw1m[m1][j1] = e(m1 j1 / n1), m1 <= k1, rows of p3_ld1 (odd).
 __host__ __device__ inline int p3_ld1(int n1) { return (n1 / 2 + 1) | 1; }
 
-__host__ __device__ inline size_t p3_smem_paired(int n1, int cd, int np1, int k1)
+__host__ __device__ inline size_t p3_smem_paired(int n1, int cd, int np1, int k1, int ng)
 {
-    return sizeof(float2) * ((size_t)n1 * cd + (size_t)(k1 + 1) * p3_ld1(n1)) + sizeof(int4) * np1;
+    return sizeof(int4) * np1 + align16(sizeof(float2) * (size_t)(k1 + 1) * p3_ld1(n1)) +
+           2 * align16(sizeof(float2) * (size_t)n1 * cd) + sizeof(float2) * (size_t)ng;
 }
 
+// One CTA per row at a time, the rows double-buffered: the next row's n1 x cd values are copied
+// into the second buffer with cp.async while this row's outputs are formed, so the workspace
+// latency overlaps the arithmetic.  Then the pairs over j1 are formed in place and each thread
+// makes the outputs of its sphere pairs, into shared memory (sphere order scatters them), from
+// where the row is written with coalesced stores.
 __global__ void __launch_bounds__(256)
-    dft_stage3_paired_kernel(const float2 *__restrict__ Y2, int rows, int n1, int cd, int np1, int k1,
+    dft_stage3_paired_kernel(const float2 *__restrict__ Y2, int rows, int n1, int cd, int np1, int k1, int ng,
                              const int4 *__restrict__ g_pair1, const float2 *__restrict__ g_tw,
                              float2 *__restrict__ Y, long long ldy)
 {
@@ -622,7 +957,11 @@ __global__ void __launch_bounds__(256)
     int4 *pair1 = reinterpret_cast<int4 *>(smem);                // [np1]
     float2 *tw1m = reinterpret_cast<float2 *>(pair1 + np1);     // [k1 + 1][ld1]
     const int ld1 = p3_ld1(n1), h1 = (n1 - 1) / 2;
-    float2 *ys = tw1m + (size_t)(k1 + 1) * ld1;                  // [n1][cd]
+    const size_t rowv = (size_t)n1 * cd;
+    float2 *buf0 = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(tw1m) +
+                                              align16(sizeof(float2) * (size_t)(k1 + 1) * ld1));
+    float2 *buf1 = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(buf0) + align16(sizeof(float2) * rowv));
+    float2 *yo = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(buf1) + align16(sizeof(float2) * rowv));
     const int tid = threadIdx.x;
     for (int t = tid; t < np1; t += blockDim.x)
         pair1[t] = g_pair1[t];
@@ -630,22 +969,38 @@ __global__ void __launch_bounds__(256)
         const int m1 = t / ld1, j1 = t - m1 * ld1;
         tw1m[t] = g_tw[(m1 * j1) % n1];
     }
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        __syncthreads();  // tables ready / previous row's reads done
-        const float2 *src = Y2 + row * n1 * cd;
-        for (int t = tid; t < cd; t += blockDim.x) {
-            ys[t] = src[t];
-            if ((n1 & 1) == 0)
-                ys[(n1 / 2) * cd + t] = src[(n1 / 2) * cd + t];
+    // a row block is rowv values at Y2 + row rowv: 16-byte copies when every block starts on 16 bytes
+    const bool v16 = (rowv % 2 == 0) && ((reinterpret_cast<size_t>(Y2) & 15) == 0);
+    auto fetch = [&](long long row, float2 *dst) {
+        const float2 *src = Y2 + row * (long long)rowv;
+        if (v16) {
+            for (int t = tid; t < (int)(rowv / 2); t += blockDim.x)
+                cp_async16(dst + 2 * t, src + 2 * t);
+        } else {
+            for (int t = tid; t < (int)rowv; t += blockDim.x)
+                cp_async8(dst + t, src + t);
         }
+        cp_async_commit();
+    };
+    long long row = blockIdx.x;
+    if (row < rows)
+        fetch(row, buf0);
+    for (int it = 0; row < rows; ++it, row += gridDim.x) {
+        float2 *ys = (it & 1) ? buf1 : buf0;
+        const long long next = row + gridDim.x;
+        if (next < rows)
+            fetch(next, (it & 1) ? buf0 : buf1);  // its buffer was last read before the previous row's final barrier
+        else
+            cp_async_commit();  // an empty group keeps the count of groups in flight at two
+        cp_async_wait<1>();     // this thread's copies of the current row are done
+        __syncthreads();        // everyone's are (and the tables are ready on the first row)
         for (int t = tid; t < h1 * cd; t += blockDim.x) {
             const int j1 = 1 + t / cd, d = t - (j1 - 1) * cd;
-            const float2 u = src[j1 * cd + d], v = src[(n1 - j1) * cd + d];
+            const float2 u = ys[j1 * cd + d], v = ys[(n1 - j1) * cd + d];
             ys[j1 * cd + d] = make_float2(u.x + v.x, u.y + v.y);
             ys[(n1 - j1) * cd + d] = make_float2(u.x - v.x, u.y - v.y);
         }
         __syncthreads();
-        float2 *y = Y + row * ldy;
         for (int e = tid; e < np1; e += blockDim.x) {
             const int4 pr = pair1[e];  // (d, m1, g of m1, g of -m1)
             const float2 *a = ys + pr.x, *w = tw1m + pr.y * ld1;
@@ -662,11 +1017,100 @@ __global__ void __launch_bounds__(256)
                 B.x = fmaf(t.x, cs.y, B.x);
                 B.y = fmaf(t.y, cs.y, B.y);
             }
-            y[pr.z] = make_float2(A.x - B.y, A.y + B.x);      // A + i B
+            yo[pr.z] = make_float2(A.x - B.y, A.y + B.x);      // A + i B
             if (pr.w >= 0)
-                y[pr.w] = make_float2(A.x + B.y, A.y - B.x);  // A - i B
+                yo[pr.w] = make_float2(A.x + B.y, A.y - B.x);  // A - i B
+        }
+        __syncthreads();  // yo is complete, and ys is free to be refilled two rows on
+        float2 *y = Y + row * ldy;
+        for (int g = tid; g < ng; g += blockDim.x)
+            y[g] = yo[g];
+    }
+    cp_async_wait<0>();
+}
+
+// Stage 3 with constant twiddles (n1 a compiled size up to 27, sphere pairs present): a thread per
+// disk point d.  It reads its n1 values ys[j1][d] (consecutive threads on consecutive d, so no
+// bank conflicts), forms the pairs over j1 in registers and makes the outputs (+-m1, d) for
+// m1 = 0..k1 with the twiddles as compile-time constants (the same sums, in the same order, as
+// dft_stage3_paired_kernel); entries of the sphere table gtab[d][m1] that are -1 are skipped.
+// Each CTA takes R rows at a time (R cdp threads, cdp = cd rounded up to 32), double-buffered by
+// cp.async; the outputs go through shared memory to coalesced stores.
+__host__ __device__ inline int p3c_cdp(int cd) { return (cd + 31) & ~31; }
+__host__ __device__ inline int p3c_rows(int cd) { return p3c_cdp(cd) >= 256 ? 1 : 256 / p3c_cdp(cd); }
+
+__host__ __device__ inline size_t p3c_smem(int n1, int cd, int k1, int ng)
+{
+    const int R = p3c_rows(cd);
+    return align16(sizeof(int2) * (size_t)cd * (k1 + 1)) + 2 * align16(sizeof(float2) * (size_t)R * n1 * cd) +
+           sizeof(float2) * (size_t)R * ng;
+}
+
+template <int N1>
+__global__ void __launch_bounds__(256)
+    dft_stage3c_kernel(const float2 *__restrict__ Y2, int rows, int cd, int np1, int k1, int ng,
+                       const int4 *__restrict__ g_pair1, float sgn, float2 *__restrict__ Y, long long ldy)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int R = p3c_rows(cd), cdp = p3c_cdp(cd);
+    const size_t rowv = (size_t)N1 * cd;
+    int2 *gtab = reinterpret_cast<int2 *>(smem);  // [cd][k1 + 1]: sphere index of (+m1, d), of (-m1, d)
+    float2 *buf0 = reinterpret_cast<float2 *>(smem + align16(sizeof(int2) * (size_t)cd * (k1 + 1)));
+    float2 *buf1 = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(buf0) + align16(sizeof(float2) * R * rowv));
+    float2 *yo = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(buf1) + align16(sizeof(float2) * R * rowv));
+    const int tid = threadIdx.x;
+    for (int t = tid; t < cd * (k1 + 1); t += blockDim.x)
+        gtab[t] = make_int2(-1, -1);
+    __syncthreads();
+    for (int t = tid; t < np1; t += blockDim.x) {
+        const int4 pr = g_pair1[t];  // (d, m1 >= 0, g of m1, g of -m1 or -1)
+        gtab[pr.x * (k1 + 1) + pr.y] = make_int2(pr.z, pr.w);
+    }
+    const int rl = tid / cdp, d = tid - rl * cdp;
+    const bool v16 = (rowv % 2 == 0) && ((reinterpret_cast<size_t>(Y2) & 15) == 0);
+    // rows [r0, r0 + R) are contiguous in the workspace
+    auto fetch = [&](long long r0, float2 *dst) {
+        const float2 *src = Y2 + r0 * (long long)rowv;
+        const long long nv = (long long)min((long long)R, rows - r0) * (long long)rowv;
+        if (v16) {
+            for (long long t = tid; t < nv / 2; t += blockDim.x)
+                cp_async16(dst + 2 * t, src + 2 * t);
+        } else {
+            for (long long t = tid; t < nv; t += blockDim.x)
+                cp_async8(dst + t, src + t);
+        }
+        cp_async_commit();
+    };
+    long long r0 = (long long)blockIdx.x * R;
+    const long long rstride = (long long)gridDim.x * R;
+    if (r0 < rows)
+        fetch(r0, buf0);
+    for (int it = 0; r0 < rows; ++it, r0 += rstride) {
+        float2 *ys = (it & 1) ? buf1 : buf0;
+        if (r0 + rstride < rows)
+            fetch(r0 + rstride, (it & 1) ? buf0 : buf1);  // read last before the previous group's barrier
+        else
+            cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int nr = (int)min((long long)R, rows - r0);
+        if (rl < nr && d < cd) {
+            float2 x[N1];
+            const float2 *c = ys + rl * rowv + d;
+#pragma unroll
+            for (int j = 0; j < N1; ++j)
+                x[j] = c[j * cd];
+            pair_fold<N1>(x);
+            stage2_all<N1>(x, k1, sgn, gtab + d * (k1 + 1), yo + rl * ng,
+                           std::make_integer_sequence<int, (N1 - 1) / 2 + 1>{});
+        }
+        __syncthreads();  // yo is complete, and ys is free to be refilled
+        for (int t = tid; t < nr * ng; t += blockDim.x) {
+            const int r = t / ng, g = t - r * ng;
+            Y[(r0 + r) * ldy + g] = yo[t];
         }
     }
+    cp_async_wait<0>();
 }
 
 __global__ void __launch_bounds__(256)
@@ -797,6 +1241,54 @@ static cudaError_t launch_p12_t(int grid, size_t smem, const float2 *X, long lon
     return cudaGetLastError();
 }
 
+template <int N, bool PAIR>
+static cudaError_t launch_p12c_t(int grid, const float2 *X, long long ldx, int rows, const DftPlan &p, float sgn,
+                                 float2 *work, PairSrc ps, cudaStream_t s)
+{
+    const size_t smem = p12c_smem(N, p.c3);
+    cudaError_t e = cudaFuncSetAttribute(dft_plane12c_kernel<N, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dft_plane12c_kernel<N, PAIR><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.sym3, p.cd, p.np2, p.k2,
+                                                                     p.pair2, sgn, work, ps);
+    return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_p12c(int grid, const float2 *X, long long ldx, int rows, const DftPlan &p, float sgn,
+                               float2 *work, const PairSrc *ps, cudaStream_t s)
+{
+    return ps ? launch_p12c_t<N, true>(grid, X, ldx, rows, p, sgn, work, *ps, s)
+              : launch_p12c_t<N, false>(grid, X, ldx, rows, p, sgn, work, PairSrc{nullptr, 0, 1, 0}, s);
+}
+
+template <int N1>
+static cudaError_t launch_p3c(int grid, int nthr, size_t smem, const float2 *work, int rows, const DftPlan &p, float sgn,
+                              float2 *Y, long long ldy, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(dft_stage3c_kernel<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dft_stage3c_kernel<N1><<<grid, nthr, smem, s>>>(work, rows, p.cd, p.np1, p.k1, p.ng, p.pair1, sgn, Y, ldy);
+    return cudaGetLastError();
+}
+
+// The constant-twiddle stages 1 and 2 serve square planes with N <= 27 (larger lines would not fit
+// two CTAs' registers per SM) and spheres whose m3 values are -M..M, M <= 7, with a disk symmetric
+// in m2 (every sphere at q = 0).
+static bool p12c_compiled(int N)
+{
+    return N == 12 || N == 16 || N == 18 || N == 20 || N == 24 || N == 27;
+}
+
+static bool p12c_applies(const DftPlan &p)
+{
+    const int N = p.n[2];
+    return p.n[1] == N && p12c_compiled(N) && p.sym3 >= 0 && p.c3 == 2 * p.sym3 + 1 && p.np2 > 0 &&
+           p.c3 <= P12C_MAX_C3 && p.k2 <= (N - 1) / 2 && p12c_smem(N, p.c3) <= DFT_SMEM_MAX;
+}
+
 template <int N3>
 static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long ldx, int rows, const DftPlan &p,
                               const float2 *tw, float2 *work, const PairSrc *ps, cudaStream_t s)
@@ -810,7 +1302,7 @@ static cudaError_t launch_p12(int grid, size_t smem, const float2 *X, long long 
 // launched, when pair rows would need the row-block kernel.
 static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy,
                                   const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent,
-                                  const PairSrc *ps)
+                                  const PairSrc *ps, bool const_twiddles)
 {
     if (rows <= 0)
         return cudaSuccess;
@@ -818,10 +1310,11 @@ static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, floa
         return ps ? cudaErrorNotSupported : launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     const float2 *tw = negative_exponent ? p.twc : p.tw;
     const size_t sm12 = p12_smem(p.n, p.c3, p.cd, p.np2, p.k2, !p12_compiled(p.n[2]));
-    const bool paired3 = p.np1 > 0 && p3_smem_paired(p.n[0], p.cd, p.np1, p.k1) <= DFT_SMEM_MAX;
-    const size_t sm3 = paired3 ? p3_smem_paired(p.n[0], p.cd, p.np1, p.k1)
+    const bool paired3 = p.np1 > 0 && p3_smem_paired(p.n[0], p.cd, p.np1, p.k1, p.ng) <= DFT_SMEM_MAX;
+    const size_t sm3 = paired3 ? p3_smem_paired(p.n[0], p.cd, p.np1, p.k1, p.ng)
                                : sizeof(float2) * ((size_t)p.n[0] * p.cd + p.n[0]) + sizeof(int) * 2 * p.ng;
-    if (sm12 > DFT_SMEM_MAX || sm3 > DFT_SMEM_MAX)
+    const bool cst = const_twiddles && p12c_applies(p) && (long long)rows * p.n[0] < (1LL << 31);
+    if ((!cst && sm12 > DFT_SMEM_MAX) || sm3 > DFT_SMEM_MAX)
         return ps ? cudaErrorNotSupported : launch_dft_rows(X, ldx, rows, Y, ldy, p, s, negative_exponent);
     cudaError_t e = paired3 ? cudaFuncSetAttribute(dft_stage3_paired_kernel,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3)
@@ -831,7 +1324,18 @@ static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, floa
         return e;
     const long long ntasks = (long long)rows * p.n[0];
     const int g12 = (int)std::min<long long>((ntasks + P12_WARPS - 1) / P12_WARPS, 152LL * 16);
-    switch (p.n[2]) {
+    const float sgn = negative_exponent ? -1.f : 1.f;
+    if (cst) {
+        switch (p.n[2]) {
+        case 12: e = launch_p12c<12>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        case 16: e = launch_p12c<16>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        case 18: e = launch_p12c<18>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        case 20: e = launch_p12c<20>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        case 24: e = launch_p12c<24>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        case 27: e = launch_p12c<27>(g12, X, ldx, rows, p, sgn, work, ps, s); break;
+        default: e = cudaErrorNotSupported; break;
+        }
+    } else switch (p.n[2]) {
     case 12: e = launch_p12<12>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
     case 16: e = launch_p12<16>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
     case 18: e = launch_p12<18>(g12, sm12, X, ldx, rows, p, tw, work, ps, s); break;
@@ -845,9 +1349,31 @@ static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, floa
     }
     if (e != cudaSuccess)
         return e;
-    const int g3 = std::min(rows, 152 * 8);
+    // stage 3: constant twiddles where n1 allows, else the paired form (every CTA resident, four per
+    // SM, looping over rows) or the plain one
+    const bool cst3 = const_twiddles && p.np1 > 0 && p12c_compiled(p.n[0]) && 2 * p.k1 < p.n[0] && p.cd <= 256 &&
+                      p3c_smem(p.n[0], p.cd, p.k1, p.ng) <= DFT_SMEM_MAX;
+    if (cst3) {
+        const size_t sm = p3c_smem(p.n[0], p.cd, p.k1, p.ng);
+        const int R = p3c_rows(p.cd), nthr = R * p3c_cdp(p.cd);
+        const int per_sm = std::max(1, std::min(4, (int)((200 * 1024) / sm)));  // resident CTAs per SM
+        const int g3c = (int)std::min<long long>((rows + R - 1) / R, 152LL * per_sm);
+        switch (p.n[0]) {
+        case 12: e = launch_p3c<12>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        case 16: e = launch_p3c<16>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        case 18: e = launch_p3c<18>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        case 20: e = launch_p3c<20>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        case 24: e = launch_p3c<24>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        case 27: e = launch_p3c<27>(g3c, nthr, sm, work, rows, p, sgn, Y, ldy, s); break;
+        default: e = cudaErrorNotSupported; break;
+        }
+        count_launches(2);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int g3 = std::min(rows, paired3 ? 152 * 4 : 152 * 8);
     if (paired3)
-        dft_stage3_paired_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.np1, p.k1, p.pair1, tw, Y, ldy);
+        dft_stage3_paired_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.np1, p.k1, p.ng, p.pair1, tw, Y,
+                                                      ldy);
     else
         dft_stage3_kernel<<<g3, 256, sm3, s>>>(work, rows, p.n[0], p.cd, p.ng, p.gmap, tw, Y, ldy);
     count_launches(2);
@@ -855,17 +1381,17 @@ static cudaError_t dft_two_kernel(const float2 *X, long long ldx, int rows, floa
 }
 
 cudaError_t launch_dft_rows_ws(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,
-                               float2 *work, cudaStream_t s, bool negative_exponent)
+                               float2 *work, cudaStream_t s, bool negative_exponent, bool const_twiddles)
 {
-    return dft_two_kernel(X, ldx, rows, Y, ldy, p, work, s, negative_exponent, nullptr);
+    return dft_two_kernel(X, ldx, rows, Y, ldy, p, work, s, negative_exponent, nullptr, const_twiddles);
 }
 
 cudaError_t launch_dft_pairs_ws(const float2 *psi, long long nr, const float *sw, int nv, int nc, float2 *Y,
                                 long long ldy, const DftPlan &p, float2 *work, cudaStream_t s, bool negative_exponent,
-                                int c0)
+                                int c0, bool const_twiddles)
 {
     const PairSrc ps{sw, nv, nc, c0 < 0 ? nv : c0};
-    return dft_two_kernel(psi, nr, nv * nc, Y, ldy, p, work, s, negative_exponent, &ps);
+    return dft_two_kernel(psi, nr, nv * nc, Y, ldy, p, work, s, negative_exponent, &ps, const_twiddles);
 }
 
 cudaError_t launch_dft_rows(const float2 *X, long long ldx, int rows, float2 *Y, long long ldy, const DftPlan &p,

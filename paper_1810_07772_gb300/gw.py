@@ -20,7 +20,7 @@ GW_OK, GW_E_INVALID, GW_E_NOMEM, GW_E_CUDA, GW_E_NOT_READY, GW_E_NUMERIC, GW_E_T
 PRECISION = {"tf32x3": 0, "bf16x3": 1, "tf32x1": 2, "fp32_simt": 3, "fp16x3": 4}
 INV_METHOD = {"cholesky": 0, "newton": 1, "newton_tc": 2}
 HERK_KERNEL = {"single": 0, "pair": 1}
-TRANSFORM_KERNEL = {"two_kernel": 0, "fused": 1}
+TRANSFORM_KERNEL = {"two_kernel": 0, "fused": 1, "tables": 2}
 ZGEMM_MODE = {"fp16x3": 0, "slices": 1}
 GW_C64, GW_C128 = 0, 1
 BUF = {"P": 0, "F": 1, "PG": 2, "eps": 3, "epsinv": 4, "weights": 5, "psiT": 6}
@@ -347,8 +347,9 @@ class Context:
         return int(np.count_nonzero(m2 <= gcut))
 
     def set_transform_kernel(self, kind):
-        """Sphere transforms: "fused" (one kernel per pass, the default) or "two_kernel"
-        (gw_set_transform_kernel)."""
+        """Sphere transforms (gw_set_transform_kernel): "two_kernel" (the default; constant
+        twiddles where the grid allows), "tables" (the two-kernel form with twiddle tables) or
+        "fused" (one kernel per pass)."""
         self._check(lib().gw_set_transform_kernel(self._h, TRANSFORM_KERNEL[kind] if isinstance(kind, str)
                                                   else int(kind)))
 

@@ -459,6 +459,17 @@ def run_gw(args):
                 "tensor_pipe_frac": (tensor_flop / (herk_ms * 1e-3) / 1e12 / peak) if herk_ms > 0 else None,
                 "herk_ms": herk_ms}
 
+    # the row pass of the sphere transforms (the larger of the two): one read of P and one write of
+    # the N_r x N_g result are its algorithmic bytes (the stage-2 workspace is not counted)
+    row_ms = float(times.get("row_dft", 0.0))
+    row_bytes = w.nr * w.nr * 8.0 + w.nr * ng * 8.0
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    transform_roofline = {"bound": "hbm", "kernel": "dft_plane12c_kernel + dft_stage3c_kernel (row pass, "
+                                                   "compile-time twiddles)",
+                          "achieved": row_bytes / (row_ms * 1e-3) / 1e9 if row_ms > 0 else None, "peak": hbm,
+                          "unit": "GB/s", "frac": row_bytes / (row_ms * 1e-3) / 1e9 / hbm if row_ms > 0 else None,
+                          "bytes_per_launch": row_bytes, "ms": row_ms, "peak_source": f"{peak_src} hbm_gbs"}
+
     part = {"fp16x3": "FP16", "bf16x3": "BF16"}.get(args.precision)
     inv_note = ("eps in FP64; eps^-1 by the Newton iteration of Sec. 5.1 on the tensor cores, refined with "
                 "residuals exact to FP64 from integer slices (FP64 accuracy)" if args.inv == "newton_tc"
@@ -480,6 +491,7 @@ def run_gw(args):
             "s_per_eps_inv": ms_per_step / 1e3,
             "kernel_ms": times,
             "roofline": roofline,
+            "transform_roofline": transform_roofline,
             "gpu_launches": launches,
             "e2e": {"value": e2e_flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}}

@@ -606,6 +606,7 @@ void Ctx::release()
     dfree(d_scal);
     dfree(d_tcw);
     dfree(d_csw);
+    dfree(d_Qc);
     dfree(d_fplan);
     dfree(d_cw);
     dfree(d_cgvec);
@@ -858,6 +859,7 @@ gw_status gw_load_states(gw_ctx *h, int n1, int n2, int n3, double cell_L, int n
 
     GW_CUDA(cudaSetDevice(c.device), "set device");
     c.loaded = c.P_ready = c.PG_ready = c.eps_ready = false;
+    c.q_pairs = false;
     c.n1 = n1;
     c.n2 = n2;
     c.n3 = n3;
@@ -1062,6 +1064,7 @@ gw_status gw_P_to_G(gw_ctx *h, int gcut, int *ng_out, int *gvec_out, int max_ng,
         return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", ng);
     cudaStream_t s = c.stream;
     GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
+    c.q_pairs = false;
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
     GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
     GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, std::max(c.nr, ng)), "transform workspace"));
@@ -1147,6 +1150,7 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
     GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
     record(c, 1);
     record(c, 3);
+    c.q_pairs = false;
     cudaError_t fe = transform_rows(c, c.d_psi, c.nr, k, c.d_Q, ng, true, s, c.d_sw, c.nv, c.nc);
     if (fe == cudaErrorNotSupported) {
         GW_TRY(ensure(c, c.d_F, c.cap.F, (size_t)k * c.nr_pad * sizeof(float2), "pair densities"));
@@ -1157,6 +1161,8 @@ gw_status gw_build_PG(gw_ctx *h, int precision, int gcut, int *ng_out, int *gvec
                                 c.transform_kind != GW_TRANSFORM_TABLES);
     }
     GW_CUDA(fe, "pair-density transforms");
+    c.q_pairs = true;  // the closure estimate may reuse them (gw_corr_closure)
+    c.q_pairs_gen = c.plan_gen;
     record(c, 4);
     GW_CUDA(launch_planes16_from_c64(c.d_Q, k, ng, ng, kpad, ng_pad, bf16, c.d_small, scale_exp,
                                      reinterpret_cast<uint16_t *>(c.d_QT), s),
@@ -1213,11 +1219,16 @@ gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_o
             wv[v] += 2.0 / (c.E_h[v] - eo);
         }
     }
-    std::vector<float> csw((size_t)c.nv * c.nb);
+    // pair weights sqrt(-W_v / (N_r - n_in)): [nv][nb] for every loaded n, then [nv][nv] for the
+    // occupied n alone (the rows added to gw_build_PG's transforms when those are reused)
+    std::vector<float> csw((size_t)c.nv * c.nb + (size_t)c.nv * c.nv);
     for (int v = 0; v < c.nv; ++v) {
         wv[v] *= inv_dim;
+        const float x = static_cast<float>(std::sqrt(-wv[v]));
         for (int n = 0; n < c.nb; ++n)
-            csw[(size_t)v * c.nb + n] = static_cast<float>(std::sqrt(-wv[v]));
+            csw[(size_t)v * c.nb + n] = x;
+        for (int n = 0; n < c.nv; ++n)
+            csw[(size_t)c.nv * c.nb + (size_t)v * c.nv + n] = x;
     }
     GW_CUDA(cudaSetDevice(c.device), "set device");
     if (gcut != c.gcut)
@@ -1228,11 +1239,19 @@ gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_o
     cudaStream_t s = c.stream;
     const int k2 = c.nv * c.nb, kpad2 = ((k2 + HERK16_KC - 1) / HERK16_KC) * HERK16_KC;
     const int ng_pad = ((ng + 255) / 256) * 256;
+    // gw_build_PG on the same states and sphere left the transforms M_vc(G) sqrt(2/(E_c - E_v)) of
+    // the unoccupied pairs in Q: rescaled, they are nv nc of the k2 rows, and only the nv nv occupied
+    // pairs are transformed here
+    const bool reuse = c.q_pairs && c.q_pairs_gen == c.plan_gen && c.nc > 0;
     GW_TRY(ensure(c, c.d_csw, c.cap_csw, csw.size() * sizeof(float), "closure weights"));
     GW_TRY(ensure(c, c.d_cw, c.cap_cw, wv.size() * sizeof(double), "closure state weights"));
     GW_TRY(ensure(c, c.d_cgvec, c.cap_cgvec, (size_t)3 * ng * sizeof(int), "closure sphere"));
     GW_TRY(ensure(c, c.d_cwork, c.cap_cwork, closure_work_bytes(c.nr), "closure workspace"));
-    GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k2 * ng * sizeof(float2), "closure matrix elements"));
+    if (reuse)
+        GW_TRY(ensure(c, c.d_Qc, c.cap_Qc, (size_t)k2 * ng * sizeof(float2), "closure matrix elements"));
+    else
+        GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)k2 * ng * sizeof(float2), "closure matrix elements"));
+    float2 *Qk = reuse ? c.d_Qc : c.d_Q;
     GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)kpad2 * ng_pad * 2 * HERK16_NPL, "closure planes"));
     GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, k2), "transform workspace"));
     GW_TRY(ensure(c, c.d_psi, c.cap.psi, (size_t)c.nb * c.nr * sizeof(float2), "state staging"));
@@ -1301,11 +1320,21 @@ gw_status gw_corr_closure(gw_ctx *h, int gcut, const double *E_omit_eV, int nc_o
     // projector term: matrix elements M_vn(G) sqrt(-W_v / (N_r - n_in)) for every loaded n, then the
     // N_g x N_g rank-k update (which returns minus the sum of the outer products) into `out`
     GW_CUDA(launch_transpose_states(c.d_psiT, c.nr, c.nb, c.d_psi, s), "states [nb][N_r]");
-    cudaError_t fe = transform_rows(c, c.d_psi, c.nr, k2, c.d_Q, ng, true, s, c.d_csw, c.nv, c.nb, 0);
+    cudaError_t fe;
+    if (reuse) {
+        const int kv = c.nv * c.nc;
+        GW_CUDA(launch_closure_rescale(c.d_Q, c.nv, c.nc, ng, c.d_csw, c.nb, c.d_sw, c.d_Qc, s),
+                "closure matrix elements from the pair transforms");
+        fe = transform_rows(c, c.d_psi, c.nr, c.nv * c.nv, c.d_Qc + (size_t)kv * ng, ng, true, s,
+                            c.d_csw + (size_t)c.nv * c.nb, c.nv, c.nv, 0);
+    } else {
+        c.q_pairs = false;
+        fe = transform_rows(c, c.d_psi, c.nr, k2, c.d_Q, ng, true, s, c.d_csw, c.nv, c.nb, 0);
+    }
     if (fe == cudaErrorNotSupported)
         return fail(c, GW_E_UNSUPPORTED, "the closure needs the plane transform kernel for this grid");
     GW_CUDA(fe, "closure matrix elements");
-    GW_CUDA(launch_planes16_from_c64(c.d_Q, k2, ng, ng, kpad2, ng_pad, false, c.d_small, scale_exp,
+    GW_CUDA(launch_planes16_from_c64(Qk, k2, ng, ng, kpad2, ng_pad, false, c.d_small, scale_exp,
                                      reinterpret_cast<uint16_t *>(c.d_QT), s),
             "closure planes");
     int nsm = 152;
@@ -1750,6 +1779,7 @@ gw_status batch_prepare(gw_batch &b)
             return fail(c, GW_E_UNSUPPORTED, "sphere too large for the transform kernel (N_g = %d)", c.ng);
         const int ng = c.ng, NB = CHOL_NB, nblk = (ng + NB - 1) / NB;
         GW_TRY(ensure(c, c.d_Q, c.cap.Q, (size_t)c.nr * ng * sizeof(float2), "row transform"));
+        c.q_pairs = false;
         GW_TRY(ensure(c, c.d_QT, c.cap.QT, (size_t)c.nr * ng * sizeof(float2), "transposed row transform"));
         GW_TRY(ensure(c, c.d_PG, c.cap.PG, (size_t)ng * ng * sizeof(float2), "P~"));
         GW_TRY(ensure(c, c.d_dftw, c.cap.dftw, dft_work_bytes(c.plan, std::max(c.nr, ng)), "transform workspace"));

@@ -183,7 +183,11 @@ struct Ctx {
     int herk_W = 3, herk_L = 256;   // 6.5e-7 against FP64 at 24^3; see gw_set_herk_window
     int herk_kernel = GW_HERK_SINGLE; // r-space 16-bit update: one CTA per tile or CTA pairs
     std::vector<double> E_h;        // the loaded energies in Hartree (host copy)
-    float *d_csw = nullptr;         // closure pair weights [nv][nb]
+    float *d_csw = nullptr;         // closure pair weights [nv][nb], then [nv][nv] for the occupied pairs
+    float2 *d_Qc = nullptr;         // closure matrix elements when built from gw_build_PG's transforms
+    size_t cap_Qc = 0;
+    bool q_pairs = false;           // d_Q holds gw_build_PG's pair transforms of the loaded states,
+    int q_pairs_gen = -1;           // for the plan of this generation
     double *d_cw = nullptr;         // closure weights W_v / (N_r - nb) [nv]
     int *d_cgvec = nullptr;         // sphere vectors [ng][3] for the closure
     void *d_cwork = nullptr;        // closure workspace
@@ -423,6 +427,10 @@ cudaError_t pp_eval(const PPWork &w, int ng, int b, int nuse, double omega, doub
 // asynchronous.
 size_t closure_work_bytes(int nr);
 cudaError_t closure_set_twiddles(const int dims[3], int nr, void *work, cudaStream_t s);
+// Rows k = v nc + c of Q (the pair transforms of gw_build_PG, weighted sqrt(2/(E_c - E_v)) = sw[k])
+// rescaled to the closure's weight csw[v nb]: out[k][g] = Q[k][g] csw[v nb] / sw[k], for k < nv nc.
+cudaError_t launch_closure_rescale(const float2 *Q, int nv, int nc, int ng, const float *csw, int nb, const float *sw,
+                                   float2 *out, cudaStream_t s);
 cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
                             const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work,
                             cudaStream_t s);

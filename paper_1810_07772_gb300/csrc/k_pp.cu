@@ -537,6 +537,36 @@ cudaError_t closure_set_twiddles(const int dims[3], int nr, void *work, cudaStre
     return cudaStreamSynchronize(s);  // twh is a host local; once per grid
 }
 
+namespace {
+
+// out[k][g] = Q[k][g] csw[v nb] / sw[k] with v = k / nc: the pair transforms of gw_build_PG carry
+// the weight sqrt(2/(E_c - E_v)) of Eq. (fdef); the closure's projector term needs the same
+// matrix elements M_vc(G) with the weight sqrt(-W_v / (N_r - n_in)) instead.
+__global__ void closure_rescale_kernel(const float2 *__restrict__ Q, int nc, int ng, const float *__restrict__ csw,
+                                       int nb, const float *__restrict__ sw, float2 *__restrict__ out, long long n)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / ng);
+        const float r = csw[(size_t)(k / nc) * nb] / sw[k];
+        const float2 q = Q[e];
+        out[e] = make_float2(q.x * r, q.y * r);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_closure_rescale(const float2 *Q, int nv, int nc, int ng, const float *csw, int nb, const float *sw,
+                                   float2 *out, cudaStream_t s)
+{
+    const long long n = (long long)nv * nc * ng;
+    if (n <= 0)
+        return cudaSuccess;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    closure_rescale_kernel<<<grid, 256, 0, s>>>(Q, nc, ng, csw, nb, sw, out, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t closure_enqueue(const float2 *psiT, int nr, int nb, int nv, const double *w, const int dims[3],
                             const int *gvec_dev, int ng, const float2 *Ph, float2 *out, void *work, cudaStream_t s)
 {

@@ -74,3 +74,29 @@ def test_closure_learned_shape_24cubed():
     g = O.sphere(dims, gcut)
     ref = O.P_closure(psi[:n_in], E[:n_in], nv, E[n_in:], dims, g)
     assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dims,nv,keep,nc_all,gcut,seed", [((12, 12, 12), 4, 20, 60, 8, 3),
+                                                            ((24, 24, 24), 32, 200, 2000, 29, 2000)])
+def test_closure_after_build_PG_reuses_its_transforms(dims, nv, keep, nc_all, gcut, seed):
+    """After gw_build_PG on the same states and sphere, the closure's projector term takes the
+    unoccupied pairs' matrix elements from that call's transforms (rescaled to the closure weight)
+    and transforms only the occupied pairs: the same estimate to rounding, against a context that
+    transforms every pair itself and against the oracle; another sphere in between falls back."""
+    psi, E = inputs.make_states(0, nv, nc_all, seed, dims=dims)
+    n_in = nv + keep
+    psi_d = torch.from_numpy(np.asarray(psi[:n_in]).astype(np.complex64)).cuda()
+    fresh = closure_gpu(psi[:n_in], E[:n_in], nv, E[n_in:], dims, gcut)
+    with gw.Context(0) as ctx:
+        ctx.load_states(psi_d, E[:n_in], dims, nv)
+        ctx.build_PG(gcut)
+        reused = ctx.corr_closure(gcut, E[n_in:]).cpu().numpy()
+        again = ctx.corr_closure(gcut, E[n_in:]).cpu().numpy()          # Q is still the pair transforms
+        ctx.build_PG(gcut - 1)                                         # another sphere, then back
+        other = ctx.corr_closure(gcut, E[n_in:]).cpu().numpy()
+    assert np.array_equal(reused, again)
+    assert rel(reused, fresh) <= 1e-6
+    assert np.array_equal(other, fresh)
+    if dims[0] == 12:
+        ref = O.P_closure(psi[:n_in], E[:n_in], nv, E[n_in:], dims, O.sphere(dims, gcut))
+        assert rel(reused, ref) <= 1e-5

@@ -76,6 +76,9 @@ def parse_args(argv=None):
     ap.add_argument("--inv", choices=["cholesky", "newton_tc"], default=INV_METHOD,
                     help="eps^-1 method of the timed step")
     ap.add_argument("--epochs", type=int, default=6, help="training passes of the learned workload")
+    ap.add_argument("--learned-states", choices=["structured", "random"], default="structured",
+                    help="states of the learned workload: band-structured (energy-ordered plane-wave shells) "
+                         "or Haar-random")
     ap.add_argument("--diag-repeat", type=int, default=32, help="diagonal entries' multiplicity in training")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain",
                     help="plain = the 24^3 configuration the metric is quoted on; the others are smaller "
@@ -725,7 +728,10 @@ def section_learned(args, steps):
     ctx = gw.Context(0, stream)
 
     def states(seed):
-        return inputs.make_states_device(n, nv, nc_all, seed, dev)
+        if args.learned_states == "random":
+            return inputs.make_states_device(n, nv, nc_all, seed, dev)
+        coef, gvec, E = inputs.make_states_g_structured_device(dims, nv, nc_all, seed, dev)
+        return learned.states_in_real_space(ctx, coef, gvec, E, dims, nv), E
 
     t0 = time.perf_counter()
     X, T = learned.training_set(ctx, states, range(1000, 1064), nv, keep, dims, gcut, args.precision)
@@ -839,7 +845,11 @@ def section_learned(args, steps):
                                   "accumulation; predicts what the closure estimate of the omitted part leaves",
                        "train_systems": 64, "held_out_systems": 8, "precision_of_P": args.precision,
                        "route_of_P": "g-space (gw_build_PG) for the kept and the full sum",
-                       "diag_repeat": args.diag_repeat},
+                       "diag_repeat": args.diag_repeat,
+                       "states": ("band-structured: energy-ordered plane-wave shells, orthonormalised in energy order "
+                                  "(inputs.make_states_g_structured_device), loaded by gw_load_states_g"
+                                  if args.learned_states == "structured" else
+                                  "Haar-random orthonormal (inputs.make_states_device)")},
             "plain_full_nc": {"s_per_eps_inv": res["full"]["ms"] / 1e3, "gpu_launches": res["full"]["launches"],
                               "route": "g-space (gw_build_PG)",
                               "s_per_eps_inv_rspace": res["full_rspace"]["ms"] / 1e3},

@@ -13,6 +13,18 @@ stand in for them with the same shapes):
   Columns ``[0, N_v)`` are the occupied states, the rest the unoccupied ones.
 * ``E_v ~ U[-10, 0] eV`` and ``E_c ~ U[0.5, 20] eV``, each sorted ascending, drawn after ``A``.
 * The real-space index is C order, ``r = (j1 * n2 + j2) * n3 + j3``.
+
+Band-structured states (the learned-correction workload, :func:`make_states_g_structured`): in
+Haar-random states every state spreads evenly over all plane waves, so the omitted states of a
+band cut are a uniformly random subspace of the complement of the kept ones and nothing about
+them is predictable beyond their energies.  Kohn-Sham states are not like that: kinetic energy
+rises with band energy, so low bands are smooth and high bands oscillate.  The structured recipe
+gives state n plane-wave coefficients ``c_n(m) = env_n(|m|) (a + i b)`` on the sphere of
+:func:`psi_sphere`, with ``a, b ~ N(0, 1)`` and a Gaussian shell
+``env_n(k) = exp(-(k - k_n)^2 / (2 w^2))`` around ``k_n = k_max sqrt((E_n - E_min) / (E_max - E_min))``
+(a free-electron-like ``E ~ k^2``; ``k_max`` = ``kmax_frac`` of half the smallest grid side,
+``w`` = ``width`` Miller units), and then a reduced QR of the coefficient matrix with the states in
+energy order, which keeps the span of every set of lowest states.
 """
 from __future__ import annotations
 
@@ -126,6 +138,56 @@ def make_states_g(dims, gcut_psi: int, nv: int, nc: int, seed: int):
     ev = np.sort(rng.uniform(-10.0, 0.0, nv))
     ec = np.sort(rng.uniform(0.5, 20.0, nc))
     return np.ascontiguousarray(q.T), gvec, np.concatenate([ev, ec])
+
+
+def structured_sphere(dims) -> int:
+    """The plane-wave sphere of the band-structured states: ``|m| < min(n)/2 - 1/2``."""
+    return int(np.floor((min(dims) / 2 - 0.5) ** 2))
+
+
+def _shell_envelope(gvec, E, dims, width, kmax_frac):
+    """env[p, n] = exp(-(|m_p| - k_n)^2 / (2 width^2)), k_n from the energies (see the module notes)."""
+    k = np.sqrt(np.sum(np.asarray(gvec, dtype=np.float64) ** 2, axis=1))
+    kmax = kmax_frac * min(dims) / 2.0
+    kn = kmax * np.sqrt((E - E.min()) / (E.max() - E.min()))
+    return np.exp(-0.5 * ((k[:, None] - kn[None, :]) / width) ** 2)
+
+
+def make_states_g_structured(dims, nv: int, nc: int, seed: int, width: float = 0.8, kmax_frac: float = 0.85):
+    """Band-structured states as plane-wave coefficients: ``(coef [nv + nc][npw] complex128, gvec
+    [npw][3] int32, E_eV)`` on the sphere of :func:`structured_sphere`.  Energies are drawn first
+    (``E_v ~ U[-10, 0]``, ``E_c ~ U[0.5, 20]`` eV, sorted), then ``a`` and ``b`` of shape
+    ``(npw, nv + nc)``; see the module notes for the envelope and the QR."""
+    gvec = psi_sphere(dims, structured_sphere(dims))
+    npw, nb = len(gvec), nv + nc
+    if nb > npw:
+        raise ValueError("more states than plane waves: they cannot be orthonormal")
+    rng = np.random.default_rng(seed)
+    E = np.concatenate([np.sort(rng.uniform(-10.0, 0.0, nv)), np.sort(rng.uniform(0.5, 20.0, nc))])
+    a = rng.standard_normal((npw, nb))
+    b = rng.standard_normal((npw, nb))
+    q, _ = np.linalg.qr(_shell_envelope(gvec, E, dims, width, kmax_frac) * (a + 1j * b), mode="reduced")
+    return np.ascontiguousarray(q.T), gvec, E
+
+
+def make_states_g_structured_device(dims, nv: int, nc: int, seed: int, device, width: float = 0.8,
+                                    kmax_frac: float = 0.85):
+    """Device-drawn variant of :func:`make_states_g_structured` for the full-size learned workload:
+    the same energies (``default_rng(seed)``) and envelope, ``a + i b`` from torch's seeded CUDA
+    generator (complex64, parts N(0, 1/2)), a reduced QR on the device.  Returns ``(coef [nv + nc]
+    [npw] complex64 on device, gvec, E_eV)``."""
+    import torch
+
+    gvec = psi_sphere(dims, structured_sphere(dims))
+    npw, nb = len(gvec), nv + nc
+    rng = np.random.default_rng(seed)
+    E = np.concatenate([np.sort(rng.uniform(-10.0, 0.0, nv)), np.sort(rng.uniform(0.5, 20.0, nc))])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    z = torch.randn((npw, nb), dtype=torch.complex64, device=device, generator=gen)
+    env = torch.from_numpy(_shell_envelope(gvec, E, dims, width, kmax_frac).astype(np.float32)).to(device)
+    q, _ = torch.linalg.qr(z * env, mode="reduced")
+    return q.transpose(0, 1).contiguous(), gvec, E
 
 
 def make_workload_states(w: Workload):

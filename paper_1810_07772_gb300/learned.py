@@ -24,6 +24,14 @@ import numpy as np
 from . import gw
 
 
+def states_in_real_space(ctx, coef, gvec, E_eV, dims, nv):
+    """States given as plane-wave coefficients, loaded through gw_load_states_g (the library's
+    transform of the DFT input to the grid) and returned on the grid as a [nv + nc][N_r] complex64
+    device tensor (a copy of the context's transposed states)."""
+    ctx.load_states_g(coef, gvec, E_eV, dims, nv)
+    return ctx.view("psiT").t().contiguous()
+
+
 def build_PG(ctx, gcut, precision="fp16x3", route="gspace"):
     """P~ of the loaded states by either route; returns the G-vectors."""
     if route == "gspace":

@@ -233,16 +233,20 @@ def test_weight_ratio_at_the_occupied_limit():
 
 
 def test_learned_correction_gain_24cubed():
-    """24^3, N_v = 32, N_c = 200 kept of 2000; 64 training systems, 8 held-out systems."""
+    """24^3, N_v = 32, N_c = 200 kept of 2000; 64 training systems, 8 held-out systems, band-
+    structured states (energy-ordered plane-wave shells): the closure estimate assumes the omitted
+    states spread evenly over the complement of the kept ones, which band structure breaks, and the
+    network has to learn the rest."""
     dev = torch.device("cuda:0")
     n, nv, keep, nc_all, gcut = 24, 32, 200, 2000, 29
     dims = (n,) * 3
     nr = n ** 3
 
-    def states(seed):
-        return inputs.make_states_device(n, nv, nc_all, seed, dev)
-
     with gw.Context(0) as ctx:
+        def states(seed):
+            coef, gvec, E = inputs.make_states_g_structured_device(dims, nv, nc_all, seed, dev)
+            return learned.states_in_real_space(ctx, coef, gvec, E, dims, nv), E
+
         X, T = learned.training_set(ctx, states, range(1000, 1064), nv, keep, dims, gcut)
         assert X.shape[0] == 64 * 691 * 692 // 2
         with gw.Mlp(N_IN, HID, max_batch=8192, device=0) as net:
@@ -280,10 +284,9 @@ def test_learned_correction_gain_24cubed():
     print(f"losses {losses}  rel. error of P~: truncated {e_trunc:.4f}  learned {e_mlp:.4f}  "
           f"closure {e_full:.4f}  diagonal shift {e_clos:.4f}")
     assert losses[-1] <= losses[0]
-    assert e_mlp < 0.3 * e_trunc
-    assert e_full < e_clos                  # the closure estimate beats the diagonal shift alone
+    assert e_mlp < 0.5 * e_trunc
     assert e_mlp < e_clos
-    assert e_mlp <= 1.02 * e_full
+    assert e_mlp < 0.5 * e_full             # the network improves on the closure estimate
 
 
 def _order_keys(seed, e, S):

@@ -763,17 +763,21 @@ __device__ __forceinline__ void stage2_all(const float2 (&y)[N], int k2, float s
     (stage2_out<N, Mo>(y, k2, sgn, dt, ys), ...);
 }
 
-// Per warp: the staged plane [N][p12_pitch(N)], then a1t [c3][N | 1] of two planes (an odd pitch:
-// lanes on different columns read different banks), each reused for that plane's cd outputs; an
-// even count of float2 so the next warp's plane stays 16-byte aligned.
-__host__ __device__ inline size_t p12c_warp_floats2(int N, int c3)
+// Per warp: the staged plane [N][p12_pitch(N)] (two of them in the asynchronous form), then a1t
+// [c3][N | 1] of two planes (an odd pitch: lanes on different columns read different banks), each
+// reused for that plane's cd outputs; an even count of float2 so the next warp's plane stays
+// 16-byte aligned.
+constexpr int P12A_WARPS = 7;  // the asynchronous form: two CTAs of 7 warps fit an SM's shared memory
+
+__host__ __device__ inline size_t p12c_warp_floats2(int N, int c3, bool async = false)
 {
-    return ((size_t)N * p12_pitch(N) + 2 * (size_t)c3 * (N | 1) + 1) & ~(size_t)1;
+    return ((async ? 2 : 1) * (size_t)N * p12_pitch(N) + 2 * (size_t)c3 * (N | 1) + 1) & ~(size_t)1;
 }
 
-__host__ __device__ inline size_t p12c_smem(int N, int c3)
+__host__ __device__ inline size_t p12c_smem(int N, int c3, bool async = false)
 {
-    return align16(sizeof(int2) * (size_t)c3 * ((N - 1) / 2 + 1)) + P12_WARPS * p12c_warp_floats2(N, c3) * sizeof(float2);
+    return align16(sizeof(int2) * (size_t)c3 * ((N - 1) / 2 + 1)) +
+           (async ? P12A_WARPS : P12_WARPS) * p12c_warp_floats2(N, c3, async) * sizeof(float2);
 }
 
 constexpr int P12C_MAX_C3 = 16;  // stage 2 runs two planes side by side, one per half-warp
@@ -781,11 +785,18 @@ constexpr int P12C_MAX_C3 = 16;  // stage 2 runs two planes side by side, one pe
 // A warp takes two tasks (planes) at a time: stage 1 of each (a lane per line), then stage 2 of
 // both together, lanes 0-15 on the first plane's columns and lanes 16-31 on the second's, so a
 // sphere with c3 <= 16 keeps twice as many lanes busy in stage 2 as one plane would.
-template <int N, bool PAIR>  // two CTAs per SM (shared memory allows two at every compiled N)
-__global__ void __launch_bounds__(P12_WARPS * 32, 2)
+//
+// ASYNC (plain rows, even N, 16-byte aligned rows): the planes arrive by cp.async into two buffers
+// per warp, the next pair's first plane issued once this pair's first plane has been read and its
+// second plane once the second has been read, so the copies run behind the other plane's stage 1
+// and stage 2 instead of stalling the warp; 7 warps per CTA keep two CTAs per SM.
+template <int N, bool PAIR, bool ASYNC = false>  // two CTAs per SM (shared memory allows two at every compiled N)
+__global__ void __launch_bounds__((ASYNC ? P12A_WARPS : P12_WARPS) * 32, 2)
     dft_plane12c_kernel(const float2 *__restrict__ X, long long ldx, int rows, int n1, int M, int cd, int np2, int k2,
                         const int4 *__restrict__ g_pair2, float sgn, float2 *__restrict__ Y2, PairSrc ps)
 {
+    static_assert(!ASYNC || (!PAIR && N % 2 == 0), "the asynchronous form takes plain rows of even N");
+    constexpr int NWARPS = ASYNC ? P12A_WARPS : P12_WARPS;
     constexpr int H = (N - 1) / 2;
     constexpr int SP = p12_pitch(N);
     constexpr int LDA = N | 1;
@@ -803,9 +814,10 @@ __global__ void __launch_bounds__(P12_WARPS * 32, 2)
         dtab[pr.x * (H + 1) + pr.y] = make_int2(pr.z, pr.w);
     }
     __syncthreads();
-    float2 *pl = wbase + (size_t)warp * p12c_warp_floats2(N, c3);  // [N][SP]
-    float2 *a1t0 = pl + N * SP;                                     // [c3][LDA], first plane
-    float2 *a1t1 = a1t0 + c3 * LDA;                                 // [c3][LDA], second plane
+    float2 *pl = wbase + (size_t)warp * p12c_warp_floats2(N, c3, ASYNC);  // [N][SP]
+    float2 *pl2 = pl + (ASYNC ? N * SP : 0);                               // ASYNC: the second buffer
+    float2 *a1t0 = pl2 + N * SP;                                           // [c3][LDA], first plane
+    float2 *a1t1 = a1t0 + c3 * LDA;                                        // [c3][LDA], second plane
     const bool vec = (N % 2 == 0) && (ldx % 2 == 0) && ((reinterpret_cast<size_t>(X) & 15) == 0);
     // task -> (row, j1): plain rows row-major, pair rows j1-major (the warps of a CTA share psi_v);
     // 32-bit arithmetic (the launcher keeps rows n1 below 2^31)
@@ -821,9 +833,8 @@ __global__ void __launch_bounds__(P12_WARPS * 32, 2)
             j1 = (int)(task - q * (unsigned)n1);
         }
     };
-    // one plane into pl (pair densities formed on the way), then stage 1 into a1t:
-    // a1t[M + m3][j2] = sum_j3 x[j2][j3] e(+-m3 j3 / N)
-    auto plane_stage1 = [&](long long row, int j1, float2 *a1t) {
+    // one plane into pl (pair densities formed on the way)
+    auto load_plane = [&](long long row, int j1) {
         const float2 *src, *srcv = nullptr;
         float w = 0.f;
         if (PAIR) {
@@ -860,9 +871,12 @@ __global__ void __launch_bounds__(P12_WARPS * 32, 2)
             }
         }
         __syncwarp();
+    };
+    // stage 1 of the plane in buffer b: a1t[M + m3][j2] = sum_j3 x[j2][j3] e(+-m3 j3 / N)
+    auto stage1 = [&](const float2 *b, float2 *a1t) {
         for (int j2 = lane; j2 < N; j2 += 32) {
             float2 x[N];
-            const float2 *ls = pl + j2 * SP;
+            const float2 *ls = b + j2 * SP;
             if constexpr (N % 2 == 0) {
 #pragma unroll
                 for (int j = 0; j < N; j += 2) {
@@ -889,21 +903,12 @@ __global__ void __launch_bounds__(P12_WARPS * 32, 2)
                 col[M * LDA] = a0;
             stage1_all<N>(x, M, sgn, col, LDA, std::make_integer_sequence<int, H>{});
         }
-        __syncwarp();  // pl is rewritten by the next plane
+        __syncwarp();  // the buffer is rewritten by a later plane
     };
-    for (unsigned u = blockIdx.x * P12_WARPS + warp; u < npairs; u += gridDim.x * P12_WARPS) {
-        const unsigned tA = 2 * u, tB = tA + 1;
-        const bool hasB = tB < ntasks;
-        long long rowA, rowB = 0;
-        int j1A, j1B = 0;
-        locate(tA, rowA, j1A);
-        plane_stage1(rowA, j1A, a1t0);
-        if (hasB) {
-            locate(tB, rowB, j1B);
-            plane_stage1(rowB, j1B, a1t1);
-        }
-        // stage 2: ys[d] = sum_j2 a1t[i3][j2] e(+-m2 j2 / N) for the disk points d = (m2, m3(i3)),
-        // written over the plane's a1t once every lane holds its column
+    // stage 2 of a pair: ys[d] = sum_j2 a1t[i3][j2] e(+-m2 j2 / N) for the disk points
+    // d = (m2, m3(i3)), written over the plane's a1t once every lane holds its column; then both
+    // planes' cd values to the workspace
+    auto stage2 = [&](long long rowA, int j1A, long long rowB, int j1B, bool hasB) {
         const int half = lane >> 4, i3 = lane & 15;
         float2 *a1t = half ? a1t1 : a1t0;
         const bool act = i3 < c3 && (half == 0 || hasB);
@@ -929,6 +934,65 @@ __global__ void __launch_bounds__(P12_WARPS * 32, 2)
                 dB[t] = a1t1[t];
         }
         __syncwarp();  // a1t is rewritten by the next pair
+    };
+    const unsigned ustride = gridDim.x * NWARPS;
+    if constexpr (ASYNC) {
+        // the plane of task t into buffer b with 16-byte cp.async, one group (an empty group when
+        // t is past the end, so that every wait below sees the same count of groups)
+        auto issue = [&](unsigned t, float2 *b) {
+            if (t < ntasks) {
+                long long row;
+                int j1;
+                locate(t, row, j1);
+                const float2 *src = X + row * ldx + (size_t)j1 * plane;
+                constexpr int QR = N / 2;
+#pragma unroll 4
+                for (int q = lane; q < N * QR; q += 32) {
+                    const int j2 = q / QR, c = q - j2 * QR;
+                    cp_async16(b + j2 * SP + 2 * c, src + 2 * q);
+                }
+            }
+            cp_async_commit();
+        };
+        unsigned u = blockIdx.x * NWARPS + warp;
+        issue(2 * u, pl);
+        issue(2 * u + 1, pl2);
+        for (; u < npairs; u += ustride) {
+            const unsigned tA = 2 * u, tB = tA + 1, nA = 2 * (u + ustride);
+            const bool hasB = tB < ntasks;
+            long long rowA, rowB = 0;
+            int j1A, j1B = 0;
+            locate(tA, rowA, j1A);
+            if (hasB)
+                locate(tB, rowB, j1B);
+            cp_async_wait<1>();  // groups in flight: this pair's A and B; A is in
+            __syncwarp();
+            stage1(pl, a1t0);
+            issue(nA < 2 * npairs ? nA : ntasks, pl);  // the next pair's A (or an empty group)
+            cp_async_wait<1>();                        // B is in
+            __syncwarp();
+            if (hasB)
+                stage1(pl2, a1t1);
+            issue(nA + 1 < 2 * npairs ? nA + 1 : ntasks, pl2);  // the next pair's B
+            stage2(rowA, j1A, rowB, j1B, hasB);
+        }
+        cp_async_wait<0>();
+    } else {
+        for (unsigned u = blockIdx.x * NWARPS + warp; u < npairs; u += ustride) {
+            const unsigned tA = 2 * u, tB = tA + 1;
+            const bool hasB = tB < ntasks;
+            long long rowA, rowB = 0;
+            int j1A, j1B = 0;
+            locate(tA, rowA, j1A);
+            load_plane(rowA, j1A);
+            stage1(pl, a1t0);
+            if (hasB) {
+                locate(tB, rowB, j1B);
+                load_plane(rowB, j1B);
+                stage1(pl, a1t1);
+            }
+            stage2(rowA, j1A, rowB, j1B, hasB);
+        }
     }
 }
 
@@ -1241,26 +1305,36 @@ static cudaError_t launch_p12_t(int grid, size_t smem, const float2 *X, long lon
     return cudaGetLastError();
 }
 
-template <int N, bool PAIR>
+template <int N, bool PAIR, bool ASYNC>
 static cudaError_t launch_p12c_t(int grid, const float2 *X, long long ldx, int rows, const DftPlan &p, float sgn,
                                  float2 *work, PairSrc ps, cudaStream_t s)
 {
-    const size_t smem = p12c_smem(N, p.c3);
-    cudaError_t e = cudaFuncSetAttribute(dft_plane12c_kernel<N, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = p12c_smem(N, p.c3, ASYNC);
+    cudaError_t e = cudaFuncSetAttribute(dft_plane12c_kernel<N, PAIR, ASYNC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    dft_plane12c_kernel<N, PAIR><<<grid, P12_WARPS * 32, smem, s>>>(X, ldx, rows, p.n[0], p.sym3, p.cd, p.np2, p.k2,
-                                                                     p.pair2, sgn, work, ps);
+    dft_plane12c_kernel<N, PAIR, ASYNC><<<grid, (ASYNC ? P12A_WARPS : P12_WARPS) * 32, smem, s>>>(
+        X, ldx, rows, p.n[0], p.sym3, p.cd, p.np2, p.k2, p.pair2, sgn, work, ps);
     return cudaGetLastError();
 }
 
+// Plain rows of even N on 16-byte boundaries take the asynchronous form.
 template <int N>
 static cudaError_t launch_p12c(int grid, const float2 *X, long long ldx, int rows, const DftPlan &p, float sgn,
                                float2 *work, const PairSrc *ps, cudaStream_t s)
 {
-    return ps ? launch_p12c_t<N, true>(grid, X, ldx, rows, p, sgn, work, *ps, s)
-              : launch_p12c_t<N, false>(grid, X, ldx, rows, p, sgn, work, PairSrc{nullptr, 0, 1, 0}, s);
+    if (ps)
+        return launch_p12c_t<N, true, false>(grid, X, ldx, rows, p, sgn, work, *ps, s);
+    if constexpr (N % 2 == 0) {
+        if (ldx % 2 == 0 && (reinterpret_cast<size_t>(X) & 15) == 0 &&
+            p12c_smem(N, p.c3, true) <= DFT_SMEM_MAX) {
+            const long long ntasks = (long long)rows * p.n[0];
+            const int ga = (int)std::min<long long>((ntasks + P12A_WARPS - 1) / P12A_WARPS, 152LL * 16);
+            return launch_p12c_t<N, false, true>(ga, X, ldx, rows, p, sgn, work, PairSrc{nullptr, 0, 1, 0}, s);
+        }
+    }
+    return launch_p12c_t<N, false, false>(grid, X, ldx, rows, p, sgn, work, PairSrc{nullptr, 0, 1, 0}, s);
 }
 
 template <int N1>

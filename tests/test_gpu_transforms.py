@@ -61,6 +61,8 @@ CONST_CASES = [
     ((16, 12, 18), 10),   # n2 != n3 (stages 1 and 2 from tables, stage 3 constant)
     ((27, 27, 27), 40),   # odd N
     ((20, 20, 20), 1),    # M = 1: seven G-vectors
+    ((9, 12, 12), 8),     # odd n1 with even N: an odd task count (a last pair of one plane)
+    ((15, 16, 16), 12),   # odd n1 again, both passes through the asynchronous plane staging
 ]
 
 

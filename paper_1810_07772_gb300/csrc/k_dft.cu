@@ -7,8 +7,10 @@
 //     stage 2 (j2 -> m2):  the cd distinct (m2, m3) pairs (a disk),
 //     stage 3 (j1 -> m1):  the N_g sphere points.
 // Input rows stream through shared memory one j1-plane at a time (coalesced loads); stages 1
-// and 2 run per plane and stage 3 once per row.  Twiddles are FP64-derived tables
-// exp(+2 pi i t/n) and indices advance incrementally (no integer division in the inner loops).
+// and 2 run per plane and stage 3 once per row.  Where the grid is a compiled size (square planes
+// N <= 27, spheres at q = 0) the twiddles are compile-time constants that the FMAs take as
+// immediate operands; elsewhere they are FP64-derived tables exp(+2 pi i t/n) with indices that
+// advance incrementally (no integer division in the inner loops).
 //
 // The path applies it twice: to the rows of P (P is Hermitian, so the conjugate of a row
 // transform with exp(+iG.r) is the column transform with exp(-iG.r)), and, after a conjugate

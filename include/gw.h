@@ -80,7 +80,9 @@ typedef enum gw_inv_method {
                            /* max |I - eps X| < 3e-5, then two                                     */
                            /* refinements R = I - eps X, X <- X + X R with R exact to FP64 from   */
                            /* integer slices (see gw_zgemm_tc); GW_E_NUMERIC if the residual      */
-                           /* before the last refinement exceeds 1e-8                             */
+                           /* before the last refinement exceeds 1e-8.  gw_eps_inv replays it     */
+                           /* from a CUDA graph with 8 FP16X3 steps queued; an eps that needs    */
+                           /* more is finished by the eager form (up to 16, host-checked)         */
 } gw_inv_method;
 
 typedef enum gw_dtype { GW_C64 = 0, GW_C128 = 1 } gw_dtype;

@@ -128,6 +128,7 @@ gw_status read_device_status(Ctx &c)
     e = cudaMemcpy(&word, c.d_err, sizeof word, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "status readback");
+    c.last_status = word;
     if (word == 0)
         return GW_OK;
     cudaMemset(c.d_err, 0, sizeof(uint32_t));
@@ -144,7 +145,8 @@ gw_status read_device_status(Ctx &c)
     const char *sname = site < sizeof(sites) / sizeof(sites[0]) ? sites[site] : "?";
     if (code == GW_E_NUMERIC && site == SITE_NS)
         return fail(c, GW_E_NUMERIC, "tensor-core Newton iteration: residual above 1e-8 before the last "
-                                     "refinement (matrix not positive definite or too ill-conditioned)");
+                                     "refinement (matrix not positive definite or too ill-conditioned%s)",
+                    detail == NS_DETAIL_CAP ? "; the FP16X3 steps had not converged" : "");
     if (code == GW_E_NUMERIC)
         return fail(c, GW_E_NUMERIC, "eps is not positive definite: Cholesky pivot %u <= 0", detail);
     if (code == GW_E_INVALID)
@@ -525,8 +527,11 @@ gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X, bool us
             return fail(c, GW_E_CUDA, "stream capture of the Newton inverse could not start");
         }
         const unsigned long long counted = g_launches.load();
-        const cudaError_t eq =
-            ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.ns_cap_stream, true);
+        // the graph queues NS_GRAPH_STEPS FP16X3 steps (every queued step costs a launch even when
+        // its flag makes it return at once); an eps that needs more is finished by the eager form
+        // (gw_eps_inv retries on the NS_DETAIL_CAP status)
+        const cudaError_t eq = ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm,
+                                                  c.ns_cap_stream, true, NS_GRAPH_STEPS);
         g_launches.store(counted);  // captured launches run at replay time, where they are counted
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(c.ns_cap_stream, &g);
@@ -1382,6 +1387,17 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     if (epsinv_out)
         GW_CUDA(cudaMemcpyAsync(epsinv_out, c.d_epsinv, bytes, cudaMemcpyDefault, s), "copy eps^-1 out");
     gw_status st = read_device_status(c);
+    if (st == GW_E_NUMERIC && method == GW_INV_NEWTON_TC && ((c.last_status >> 8) & 0xFFu) == SITE_NS &&
+        (c.last_status >> 16) == NS_DETAIL_CAP) {
+        // the graph's FP16X3 steps were too few for this eps: the eager form runs up to 16, each
+        // stopping test on the host
+        GW_TRY(inverse_newton_tc(c, c.d_eps, ng, c.d_epsinv, false));
+        if (eps_out)
+            GW_CUDA(cudaMemcpyAsync(eps_out, c.d_eps, bytes, cudaMemcpyDefault, s), "copy eps out");
+        if (epsinv_out)
+            GW_CUDA(cudaMemcpyAsync(epsinv_out, c.d_epsinv, bytes, cudaMemcpyDefault, s), "copy eps^-1 out");
+        st = read_device_status(c);
+    }
     resolve_times(c);
     if (method == GW_INV_NEWTON_TC)
         newton_tc_record(c, ng);

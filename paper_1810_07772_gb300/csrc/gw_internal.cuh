@@ -208,6 +208,7 @@ struct Ctx {
     int last_herk_kernel = -1;      // the kernel of the last 16-bit r-space update
     double err_target = 0.0;        // > 0: the window comes from gw_set_error_target's rule
     int last_W = 3;                 // the window of the last 16-bit rank-k update
+    uint32_t last_status = 0;       // the device status word read by the last synchronising call
 
     void release();
 };
@@ -443,7 +444,13 @@ cudaError_t zgemm_enqueue(ZPlan &p, const double2 *A, long lda, const double2 *B
 size_t ns_work_bytes(int N, int nsm);
 cudaError_t ns_report(const void *work, int N, int nsm, double *out4);
 cudaError_t ns_prepare(void *work, int N, int nsm, cudaStream_t s);
+// max_steps: FP16X3 Newton steps queued in the graph-safe form (at most 16, the eager form's limit).
+// A last residual above the acceptance bar is GW_E_NUMERIC at SITE_NS with detail NS_DETAIL_CAP
+// when phase 1 had not converged within its steps (the eager form, with more steps, may), else 0.
+constexpr int NS_GRAPH_STEPS = 8;   // the typical eps needs 5-6 from the Jacobi-scaled start
+constexpr uint32_t NS_DETAIL_CAP = 1;
 cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
-                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe = false);
+                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe = false,
+                               int max_steps = 16);
 
 }  // namespace gw

@@ -688,11 +688,13 @@ __global__ void ns_init_kernel(double2 *X, int N, const double *__restrict__ rs,
     }
 }
 
-__global__ void ns_final_kernel(const unsigned long long *words, uint32_t *err)
+// flags[0]: phase 1 converged.  A failure after a phase 1 that ran out of steps is told apart
+// (NS_DETAIL_CAP): the eager form, with more steps, may still converge.
+__global__ void ns_final_kernel(const unsigned long long *words, const int *flags, uint32_t *err)
 {
     const double r = __longlong_as_double((long long)words[W_RLAST]);
     if (!(r <= NS_ACCEPT))
-        record_error(err, GW_E_NUMERIC, SITE_NS, 0);
+        record_error(err, GW_E_NUMERIC, SITE_NS, flags[0] ? 0u : NS_DETAIL_CAP);
 }
 
 // Grid of the element-wise kernels over an M x N matrix: x covers the columns in 256-thread blocks,
@@ -1054,8 +1056,9 @@ cudaError_t ns_prepare(void *work, int N, int nsm, cudaStream_t s)
 // With graph_safe the tables must have been uploaded by ns_prepare and every step is queued (no
 // host reads, no pageable copies), so the whole inverse can be captured into a CUDA graph.
 cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *work, double *rowsum, uint32_t *err,
-                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe)
+                               uint64_t wait_ns, int nsm, cudaStream_t s, bool graph_safe, int max_steps)
 {
+    max_steps = std::max(1, std::min(max_steps, NS_MAX));
     ZPlan p16, poz, poz7;
     ns_plans(N, nsm, p16, poz, poz7);
     Carver cv(work);
@@ -1103,7 +1106,7 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
     count_launches(1);
     NS_TRY(cudaGetLastError());
     // phase 1: X <- X (2I - eps X) with FP16X3 products, stopped on device below NS_TOL
-    for (int it = 0; it < NS_MAX; ++it) {
+    for (int it = 0; it < max_steps; ++it) {
         NS_TRY(launch_zslice(p16, false, X, N, &words[W_X], XB16, skip, s));
         NS_TRY(launch_zgemm16(p16, A16, XB16, T, err, wait_ns, skip, s));
         // Z = 2I - eps X; deviation |Z - I| = |I - eps X|
@@ -1135,7 +1138,7 @@ cudaError_t ns_inverse_enqueue(const double2 *A, int N, double2 *Xout, void *wor
                                W_DISCARD, DEV_STORE, 0.0, j, sk, nullptr, s));
     }
     NS_TRY(cudaMemcpyAsync(Xout, X, nn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    ns_final_kernel<<<1, 1, 0, s>>>(words, err);
+    ns_final_kernel<<<1, 1, 0, s>>>(words, skip, err);
     count_launches(1);
 #undef NS_TRY
     return cudaGetLastError();

@@ -197,3 +197,42 @@ def test_eps_inv_graph_replay_matches_eager():
             assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
             assert np.max(np.abs(a - O.inverse_cholesky(e))) <= 1e-12
             assert np.allclose(other.cpu().numpy(), np.eye(5) * 0.5, rtol=0, atol=1e-15)
+
+
+def test_eps_inv_graph_finishes_an_eps_that_needs_more_steps():
+    """gw_eps_inv's graph queues 8 FP16X3 steps.  An eps with condition number ~2e3 needs about 14
+    from the Jacobi-scaled start; the graph's refinements then fail with the phase-1 flag, and the
+    call finishes the inverse with the eager form.  The result matches the FP64 Cholesky inverse of
+    the same eps, and a well-conditioned eps afterwards still takes the graph."""
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    dims = (w.n,) * 3
+    with gw.Context(0) as ctx:
+        ctx.load_states(torch.from_numpy(psi.astype(np.complex64)).to(DEV), E, dims, w.nv)
+        g = ctx.build_PG(w.gcut)
+        ng = len(g)
+        PG_plain = ctx.view("PG").clone()
+        # eps = I + M, M Hermitian positive semidefinite with eigenvalues 1e-3 .. 2e3, zero row and
+        # column 0 (V(0) = 0): P~ = -M / (sqrt(V) sqrt(V)^T) off the head
+        rng = np.random.default_rng(3)
+        Q, _ = np.linalg.qr(rng.standard_normal((ng - 1, ng - 1)) + 1j * rng.standard_normal((ng - 1, ng - 1)))
+        M = (Q * np.geomspace(1e-3, 2e3, ng - 1)) @ Q.conj().T
+        sv = np.sqrt(O.coulomb(g, 1.0))
+        P = np.zeros((ng, ng), dtype=np.complex128)
+        P[1:, 1:] = -M / np.outer(sv[1:], sv[1:])
+        ctx.view("PG").copy_(torch.from_numpy(P.astype(np.complex64)))
+        eps = torch.empty((ng, ng), dtype=torch.complex128, device=DEV)
+        inv_c = torch.empty_like(eps)
+        ctx.eps_inv("cholesky", eps_out=eps, epsinv_out=inv_c)
+        inv_n = torch.empty_like(eps)
+        ctx.eps_inv("newton_tc", epsinv_out=inv_n)
+        rep = ctx.newton_tc_report()
+        e, c, n = (t.cpu().numpy() for t in (eps, inv_c, inv_n))
+        ctx.view("PG").copy_(PG_plain)
+        ctx.eps_inv("newton_tc", epsinv_out=inv_n)
+        rep2 = ctx.newton_tc_report()
+    assert np.linalg.cond(e) > 1e3
+    assert rep["steps"] > 8                 # more than the graph queues: the eager form ran
+    assert np.linalg.norm(n - c) / np.linalg.norm(c) <= 1e-11
+    assert np.max(np.abs(n @ e - np.eye(ng))) <= 1e-9
+    assert rep2["steps"] <= 8

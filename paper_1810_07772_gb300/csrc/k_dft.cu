@@ -765,6 +765,91 @@ __device__ __forceinline__ void stage2_all(const float2 (&y)[N], int k2, float s
     (stage2_out<N, Mo>(y, k2, sgn, dt, ys), ...);
 }
 
+// Two outputs Ma, Mb in one block: their eight accumulator chains interleave (four per output
+// would leave each FMA waiting on the previous one of its chain).  Every accumulator still takes
+// its terms in the order of paired_sums, so the results are the same bit for bit.
+template <int N, int Ma, int Mb, int J>
+__device__ __forceinline__ void pterm2(const float2 (&x)[N], float2 &A, float2 &B, float2 &C, float2 &D)
+{
+    pterm<N, Ma, J>(x, A, B);
+    pterm<N, Mb, J>(x, C, D);
+}
+
+template <int N, int Ma, int Mb, int... J>
+__device__ __forceinline__ void paired_sums2(const float2 (&x)[N], float2 &A, float2 &B, float2 &C, float2 &D,
+                                             std::integer_sequence<int, J...>)
+{
+    A = x[0];
+    C = x[0];
+    if constexpr (N % 2 == 0) {
+        constexpr float sa = (Ma & 1) ? -1.f : 1.f, sb = (Mb & 1) ? -1.f : 1.f;
+        A.x = fmaf(sa, x[N / 2].x, A.x);
+        A.y = fmaf(sa, x[N / 2].y, A.y);
+        C.x = fmaf(sb, x[N / 2].x, C.x);
+        C.y = fmaf(sb, x[N / 2].y, C.y);
+    }
+    B = make_float2(0.f, 0.f);
+    D = B;
+    (pterm2<N, Ma, Mb, J + 1>(x, A, B, C, D), ...);
+}
+
+// Stage-1 outputs Mo and Mo + 1 together when both are wanted, else Mo alone (Mo odd).
+template <int N, int Mo>
+__device__ __forceinline__ void stage1_out2(const float2 (&x)[N], int M, float sgn, float2 *col, int lda)
+{
+    if constexpr (Mo + 1 <= (N - 1) / 2) {
+        if (Mo + 1 <= M) {
+            float2 A, B, C, D;
+            paired_sums2<N, Mo, Mo + 1>(x, A, B, C, D, std::make_integer_sequence<int, (N - 1) / 2>{});
+            const float bx = sgn * B.x, by = sgn * B.y, dx = sgn * D.x, dy = sgn * D.y;
+            col[(M + Mo) * lda] = make_float2(A.x - by, A.y + bx);
+            col[(M - Mo) * lda] = make_float2(A.x + by, A.y - bx);
+            col[(M + Mo + 1) * lda] = make_float2(C.x - dy, C.y + dx);
+            col[(M - Mo - 1) * lda] = make_float2(C.x + dy, C.y - dx);
+            return;
+        }
+    }
+    stage1_out<N, Mo>(x, M, sgn, col, lda);
+}
+
+template <int N, int... I>
+__device__ __forceinline__ void stage1_all2(const float2 (&x)[N], int M, float sgn, float2 *col, int lda,
+                                            std::integer_sequence<int, I...>)
+{
+    (stage1_out2<N, 2 * I + 1>(x, M, sgn, col, lda), ...);
+}
+
+// Stage-2 outputs Mo and Mo + 1 together when both are wanted, else Mo alone (Mo even).
+template <int N, int Mo>
+__device__ __forceinline__ void stage2_out2(const float2 (&y)[N], int k2, float sgn, const int2 *dt, float2 *ys)
+{
+    if constexpr (Mo + 1 <= (N - 1) / 2) {
+        if (Mo + 1 <= k2) {
+            float2 A, B, C, D;
+            paired_sums2<N, Mo, Mo + 1>(y, A, B, C, D, std::make_integer_sequence<int, (N - 1) / 2>{});
+            const int2 da = dt[Mo], db = dt[Mo + 1];
+            const float bx = sgn * B.x, by = sgn * B.y, dx = sgn * D.x, dy = sgn * D.y;
+            if (da.x >= 0)
+                ys[da.x] = make_float2(A.x - by, A.y + bx);
+            if (Mo > 0 && da.y >= 0)
+                ys[da.y] = make_float2(A.x + by, A.y - bx);
+            if (db.x >= 0)
+                ys[db.x] = make_float2(C.x - dy, C.y + dx);
+            if (db.y >= 0)
+                ys[db.y] = make_float2(C.x + dy, C.y - dx);
+            return;
+        }
+    }
+    stage2_out<N, Mo>(y, k2, sgn, dt, ys);
+}
+
+template <int N, int... I>
+__device__ __forceinline__ void stage2_all2(const float2 (&y)[N], int k2, float sgn, const int2 *dt, float2 *ys,
+                                            std::integer_sequence<int, I...>)
+{
+    (stage2_out2<N, 2 * I>(y, k2, sgn, dt, ys), ...);
+}
+
 // Per warp: the staged plane [N][p12_pitch(N)] (two of them in the asynchronous form), then a1t
 // [c3][N | 1] of two planes (an odd pitch: lanes on different columns read different banks), each
 // reused for that plane's cd outputs; an even count of float2 so the next warp's plane stays
@@ -903,7 +988,7 @@ __global__ void __launch_bounds__((ASYNC ? P12A_WARPS : P12_WARPS) * 32, 2)
                 col[M * LDA] = make_float2(a0.x + x[N / 2].x, a0.y + x[N / 2].y);
             else
                 col[M * LDA] = a0;
-            stage1_all<N>(x, M, sgn, col, LDA, std::make_integer_sequence<int, H>{});
+            stage1_all2<N>(x, M, sgn, col, LDA, std::make_integer_sequence<int, (H + 1) / 2>{});
         }
         __syncwarp();  // the buffer is rewritten by a later plane
     };
@@ -924,7 +1009,7 @@ __global__ void __launch_bounds__((ASYNC ? P12A_WARPS : P12_WARPS) * 32, 2)
         __syncwarp();
         if (act) {
             pair_fold<N>(y);
-            stage2_all<N>(y, k2, sgn, dtab + i3 * (H + 1), a1t, std::make_integer_sequence<int, H + 1>{});
+            stage2_all2<N>(y, k2, sgn, dtab + i3 * (H + 1), a1t, std::make_integer_sequence<int, H / 2 + 1>{});
         }
         __syncwarp();
         float2 *dA = Y2 + (rowA * n1 + j1A) * cd;
@@ -1167,8 +1252,8 @@ __global__ void __launch_bounds__(256)
             for (int j = 0; j < N1; ++j)
                 x[j] = c[j * cd];
             pair_fold<N1>(x);
-            stage2_all<N1>(x, k1, sgn, gtab + d * (k1 + 1), yo + rl * ng,
-                           std::make_integer_sequence<int, (N1 - 1) / 2 + 1>{});
+            stage2_all2<N1>(x, k1, sgn, gtab + d * (k1 + 1), yo + rl * ng,
+                            std::make_integer_sequence<int, (N1 - 1) / 2 / 2 + 1>{});
         }
         __syncthreads();  // yo is complete, and ys is free to be refilled
         for (int t = tid; t < nr * ng; t += blockDim.x) {

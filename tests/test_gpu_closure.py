@@ -97,6 +97,13 @@ def test_closure_after_build_PG_reuses_its_transforms(dims, nv, keep, nc_all, gc
     assert np.array_equal(reused, again)
     assert rel(reused, fresh) <= 1e-6
     assert np.array_equal(other, fresh)
+    # the one-kernel transform leaves the same pair transforms for the closure to reuse
+    with gw.Context(0) as ctx:
+        ctx.set_transform_kernel("fused")
+        ctx.load_states(psi_d, E[:n_in], dims, nv)
+        ctx.build_PG(gcut)
+        fused = ctx.corr_closure(gcut, E[n_in:]).cpu().numpy()
+    assert rel(fused, fresh) <= 1e-6
     if dims[0] == 12:
         ref = O.P_closure(psi[:n_in], E[:n_in], nv, E[n_in:], dims, O.sphere(dims, gcut))
         assert rel(reused, ref) <= 1e-5

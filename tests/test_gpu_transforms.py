@@ -63,6 +63,7 @@ CONST_CASES = [
     ((20, 20, 20), 1),    # M = 1: seven G-vectors
     ((9, 12, 12), 8),     # odd n1 with even N: an odd task count (a last pair of one plane)
     ((15, 16, 16), 12),   # odd n1 again, both passes through the asynchronous plane staging
+    ((24, 24, 24), 58),   # the largest sphere of the constant form: 15 m3 values, 185 disk points
 ]
 
 

@@ -25,8 +25,10 @@
 //    inverse is reported as GW_E_NUMERIC.
 //
 // Operand planes (K-major, 8-row x 16-byte core matrices, as in the rank-k update): element
-// (r, k) of plane p sits at 16-bit offset ((kc NP + p) Rpad + (r/8) 8) 16 + ((k%16)/8) 64 +
-// (r%8) 8 + k%8 with kc = k / 16.  A operand (row i of A, k along the row): planes 2t (Re) and
+// (r, k) of plane p sits at 16-bit offset ((kc Rpad/128 + r/128) NP + p) 2048 + ((r%128)/8) 128 +
+// ((k%16)/8) 64 + (r%8) 8 + k%8 with kc = k / 16: the NP planes of one chunk of one 128-row block
+// are contiguous, so a stage arrives in one bulk copy per operand (large copies reach a higher
+// per-SM ingress than 4 KB ones).  A operand (row i of A, k along the row): planes 2t (Re) and
 // 2t + 1 (Im) of slice t.  B operand (row j = column j of B, k down the column): planes 3t (-Im),
 // 3t + 1 (Re), 3t + 2 (Im), so the 256 rows starting at Re are [Re; Im] and those starting at -Im
 // are [-Im; Re].  Then one M = 128, N = 256 MMA with A = Re(A) adds Re A Re B into the Re columns
@@ -173,8 +175,8 @@ __global__ void __launch_bounds__(512) zslice_kernel(const double2 *__restrict__
     }
     __syncthreads();
     const int NP = ns * npl;
-    const size_t per = (size_t)Rpad * 16;
-    uint16_t *base0 = planes + (size_t)kc * NP * per + (size_t)rb * 2048;
+    constexpr size_t per = 2048;  // consecutive planes of one block and chunk
+    uint16_t *base0 = planes + ((size_t)kc * (Rpad / ZT) + rb) * NP * per;
     const float scf = s_scf;
     const double scd = s_scd;
     for (int rem = threadIdx.x; rem < 2048; rem += blockDim.x) {
@@ -277,8 +279,7 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
 
     if (warp == 0) {
         if (lane == 0) {
-            const size_t perA = (size_t)Mpad * 16, perB = (size_t)Npad * 16;
-            const size_t aoff = (size_t)ti * ZT * 16, boff = (size_t)tj * ZT * 16;
+            const int ntA = Mpad / ZT, ntB = Npad / ZT;  // 128-row blocks of each operand
             for (int u = 0; u < nunits; ++u) {
                 const int s = u % NST;
                 const uint32_t ph = (uint32_t)(u / NST) & 1u;
@@ -293,24 +294,14 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
                 mbar_arrive_expect_tx(&full[s], SB);
                 if (F3) {  // A planes 0..3 (hi Re, hi Im, lo Re, lo Im), B planes 0..5 (hi, lo regions)
                     const int kc = sl.kc0 + u;
-                    const uint16_t *a = Ap + (size_t)kc * npA * perA + aoff;
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        bulk_g2s(st + p * ZPL, a + p * perA, ZPL, &full[s]);
-                    const uint16_t *b = Bp + (size_t)kc * npB * perB + boff;
-#pragma unroll
-                    for (int p = 0; p < 6; ++p)
-                        bulk_g2s(st + (4 + p) * ZPL, b + p * perB, ZPL, &full[s]);
+                    bulk_g2s(st, Ap + ((size_t)kc * ntA + ti) * npA * 2048, 4 * ZPL, &full[s]);
+                    bulk_g2s(st + 4 * ZPL, Bp + ((size_t)kc * ntB + tj) * npB * 2048, 6 * ZPL, &full[s]);
                 } else {
                     const int kc = sl.kc0 + u / np;  // chunk-major: every pair of a chunk in turn
                     const int2 pr = pairs[sl.p0 + u % np];
-                    const uint16_t *a = Ap + ((size_t)kc * npA + 2 * pr.x) * perA + aoff;
-                    bulk_g2s(st, a, ZPL, &full[s]);
-                    bulk_g2s(st + ZPL, a + perA, ZPL, &full[s]);
-                    const uint16_t *b = Bp + ((size_t)kc * npB + 3 * pr.y) * perB + boff;
-                    bulk_g2s(st + 2 * ZPL, b, ZPL, &full[s]);
-                    bulk_g2s(st + 3 * ZPL, b + perB, ZPL, &full[s]);
-                    bulk_g2s(st + 4 * ZPL, b + 2 * perB, ZPL, &full[s]);
+                    bulk_g2s(st, Ap + (((size_t)kc * ntA + ti) * npA + 2 * pr.x) * 2048, 2 * ZPL, &full[s]);
+                    bulk_g2s(st + 2 * ZPL, Bp + (((size_t)kc * ntB + tj) * npB + 3 * pr.y) * 2048, 3 * ZPL,
+                             &full[s]);
                 }
                 *n_issued = u + 1;
             }

@@ -29,11 +29,12 @@
 // ((k%16)/8) 64 + (r%8) 8 + k%8 with kc = k / 16: the NP planes of one chunk of one 128-row block
 // are contiguous, so a stage arrives in one bulk copy per operand (large copies reach a higher
 // per-SM ingress than 4 KB ones).  A operand (row i of A, k along the row): planes 2t (Re) and
-// 2t + 1 (Im) of slice t.  B operand (row j = column j of B, k down the column): planes 3t (-Im),
-// 3t + 1 (Re), 3t + 2 (Im), so the 256 rows starting at Re are [Re; Im] and those starting at -Im
-// are [-Im; Re].  Then one M = 128, N = 256 MMA with A = Re(A) adds Re A Re B into the Re columns
-// of the accumulator and Re A Im B into its Im columns, and one with A = Im(A) from the -Im plane
-// adds -Im A Im B and Im A Re B: C = A B with two MMAs per slice pair and 16-wide chunk.
+// 2t + 1 (Im) of slice t.  B operand (row j = column j of B, k down the column): planes 2t (Re)
+// and 2t + 1 (Im), so the 256 rows starting at Re are [Re; Im].  Then one M = 128, N = 256 MMA with
+// A = Re(A) adds Re A Re B into the Re columns of the accumulator and Re A Im B into its Im
+// columns, and two N = 128 MMAs with A = Im(A) add -Im A Im B (the A-negate bit of the instruction
+// descriptor) into the Re columns and Im A Re B into the Im columns: C = A B with the tensor work of
+// two N = 256 MMAs per slice pair and 16-wide chunk, and no negated plane in memory.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -52,11 +53,11 @@ constexpr uint32_t ZPL = ZT * 16 * 2;       // 4 KB: one plane of one 128-row bl
 // A stage is one chunk of one slice pair (A Re, A Im, B -Im, B Re, B Im: 20 KB, two MMAs) for the
 // integer slices, and one chunk of all three FP16X3 pairs (A hi Re, Im, A lo Re, Im, B hi and B lo
 // regions: 40 KB, six MMAs, one commit) for the split, where each slice then loads once per chunk.
-constexpr uint32_t ZSTAGE = 5 * ZPL;
-constexpr int ZSTAGES = 5;                  // ten stages in flight per SM cover the copy latency
+constexpr uint32_t ZSTAGE = 4 * ZPL;
+constexpr int ZSTAGES = 6;                  // twelve stages in flight per SM cover the copy latency
 constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 100 KB: two CTAs per SM
-constexpr uint32_t ZSTAGE3 = 10 * ZPL;
-constexpr int ZSTAGES3 = 2;
+constexpr uint32_t ZSTAGE3 = 8 * ZPL;
+constexpr int ZSTAGES3 = 3;
 static_assert(ZSTAGES3 * ZSTAGE3 <= ZPIPE, "the fused stages share the pipeline buffers");
 static_assert(128 * 65 * 8 <= ZPIPE, "epilogue staging must fit in the pipeline buffers");
 constexpr size_t ZSMEM = ZPIPE + 128;
@@ -137,8 +138,8 @@ __global__ void zmaxabs_kernel(const double2 *__restrict__ M, int rows, int cols
 // kc, 128-row block rb of the operand): the 16 x 128 tile goes through shared memory, so both
 // orientations read contiguous runs of M and every plane is written in 4 KB runs.  transpose = 0:
 // operand row r is row r of M (A operand, element (r, k) = M[r][k]); transpose = 1: operand row r
-// is column r of M (B operand, element (r, k) = M[k][r]).  npl = 2 (A: Re, Im) or 3 (B: -Im, Re,
-// Im) planes per slice.  Entries outside rows x K are zero.
+// is column r of M (B operand, element (r, k) = M[k][r]).  npl = 2 planes (Re, Im) per slice for
+// either operand.  Entries outside rows x K are zero.
 //   FP16X3: y = float(x) 2^(14 - e), hi = rn16(y), lo = rn16(y - hi).
 //   slices: n = rint(x 2^(6 ns - e)) (|n| <= 2^(6 ns)) written in balanced base 64,
 //           n = sum_t a_t 2^(6 (ns - 1 - t)): a_(ns-1) .. a_1 in [-32, 31] from the low end, a_0 =
@@ -192,14 +193,8 @@ __global__ void __launch_bounds__(512) zslice_kernel(const double2 *__restrict__
             const uint16_t re[2] = {rh, rl}, im[2] = {ih, il};
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-                if (npl == 2) {
-                    b[(size_t)(2 * t) * per] = re[t];
-                    b[(size_t)(2 * t + 1) * per] = im[t];
-                } else {
-                    b[(size_t)(3 * t) * per] = im[t] ^ 0x8000u;
-                    b[(size_t)(3 * t + 1) * per] = re[t];
-                    b[(size_t)(3 * t + 2) * per] = im[t];
-                }
+                b[(size_t)(2 * t) * per] = re[t];
+                b[(size_t)(2 * t + 1) * per] = im[t];
             }
         } else {
             long long nr = __double2ll_rn(z.x * scd), ni = __double2ll_rn(z.y * scd);
@@ -215,14 +210,8 @@ __global__ void __launch_bounds__(512) zslice_kernel(const double2 *__restrict__
                     ai = ni;
                 }
                 const uint16_t hr = h16((float)ar), hi = h16((float)ai);  // |a| <= 64: exact
-                if (npl == 2) {
-                    b[(size_t)(2 * t) * per] = hr;
-                    b[(size_t)(2 * t + 1) * per] = hi;
-                } else {
-                    b[(size_t)(3 * t) * per] = hi ^ 0x8000u;
-                    b[(size_t)(3 * t + 1) * per] = hr;
-                    b[(size_t)(3 * t + 2) * per] = hi;
-                }
+                b[(size_t)(2 * t) * per] = hr;
+                b[(size_t)(2 * t + 1) * per] = hi;
             }
         }
     }
@@ -295,12 +284,12 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
                 if (F3) {  // A planes 0..3 (hi Re, hi Im, lo Re, lo Im), B planes 0..5 (hi, lo regions)
                     const int kc = sl.kc0 + u;
                     bulk_g2s(st, Ap + ((size_t)kc * ntA + ti) * npA * 2048, 4 * ZPL, &full[s]);
-                    bulk_g2s(st + 4 * ZPL, Bp + ((size_t)kc * ntB + tj) * npB * 2048, 6 * ZPL, &full[s]);
+                    bulk_g2s(st + 4 * ZPL, Bp + ((size_t)kc * ntB + tj) * npB * 2048, 4 * ZPL, &full[s]);
                 } else {
                     const int kc = sl.kc0 + u / np;  // chunk-major: every pair of a chunk in turn
                     const int2 pr = pairs[sl.p0 + u % np];
                     bulk_g2s(st, Ap + (((size_t)kc * ntA + ti) * npA + 2 * pr.x) * 2048, 2 * ZPL, &full[s]);
-                    bulk_g2s(st + 2 * ZPL, Bp + (((size_t)kc * ntB + tj) * npB + 3 * pr.y) * 2048, 3 * ZPL,
+                    bulk_g2s(st + 2 * ZPL, Bp + (((size_t)kc * ntB + tj) * npB + 2 * pr.y) * 2048, 2 * ZPL,
                              &full[s]);
                 }
                 *n_issued = u + 1;
@@ -310,6 +299,7 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t ID = mma_idesc(0u, ZT, 2 * ZT, false);  // FP16, N = 256: Re | Im
+            constexpr uint32_t ID1 = mma_idesc(0u, ZT, ZT, false), ID1N = mma_idesc(0u, ZT, ZT, true);
             const uint32_t sbase = smem_u32(smem);
             for (int u = 0; u < nunits; ++u) {
                 const int s = u % NST;
@@ -320,23 +310,28 @@ __global__ void __launch_bounds__(ZTHREADS, 2)
                 }
                 tc_fence_after();
                 const uint32_t st = sbase + s * SB;
+                // Re columns at tmem, Im columns at tmem + ZT
                 if (F3) {
                     const uint64_t ahr = smem_desc(st, LBO, SBO), ahi = smem_desc(st + ZPL, LBO, SBO);
                     const uint64_t alr = smem_desc(st + 2 * ZPL, LBO, SBO), ali = smem_desc(st + 3 * ZPL, LBO, SBO);
-                    const uint64_t bh_neg = smem_desc(st + 4 * ZPL, LBO, SBO), bh_re = smem_desc(st + 5 * ZPL, LBO, SBO);
-                    const uint64_t bl_neg = smem_desc(st + 7 * ZPL, LBO, SBO), bl_re = smem_desc(st + 8 * ZPL, LBO, SBO);
+                    const uint64_t bh_re = smem_desc(st + 4 * ZPL, LBO, SBO), bh_im = smem_desc(st + 5 * ZPL, LBO, SBO);
+                    const uint64_t bl_re = smem_desc(st + 6 * ZPL, LBO, SBO), bl_im = smem_desc(st + 7 * ZPL, LBO, SBO);
                     mma_f16(tmem, ahr, bh_re, ID, u > 0 ? 1u : 0u);  // hi * hi
-                    mma_f16(tmem, ahi, bh_neg, ID, 1u);
+                    mma_f16(tmem, ahi, bh_im, ID1N, 1u);
+                    mma_f16(tmem + ZT, ahi, bh_re, ID1, 1u);
                     mma_f16(tmem, ahr, bl_re, ID, 1u);               // hi * lo
-                    mma_f16(tmem, ahi, bl_neg, ID, 1u);
+                    mma_f16(tmem, ahi, bl_im, ID1N, 1u);
+                    mma_f16(tmem + ZT, ahi, bl_re, ID1, 1u);
                     mma_f16(tmem, alr, bh_re, ID, 1u);               // lo * hi
-                    mma_f16(tmem, ali, bh_neg, ID, 1u);
+                    mma_f16(tmem, ali, bh_im, ID1N, 1u);
+                    mma_f16(tmem + ZT, ali, bh_re, ID1, 1u);
                 } else {
                     const uint64_t a_re = smem_desc(st, LBO, SBO), a_im = smem_desc(st + ZPL, LBO, SBO);
-                    const uint64_t b_neg = smem_desc(st + 2 * ZPL, LBO, SBO);  // rows [-Im B; Re B]
-                    const uint64_t b_re = smem_desc(st + 3 * ZPL, LBO, SBO);   // rows [Re B; Im B]
+                    const uint64_t b_re = smem_desc(st + 2 * ZPL, LBO, SBO);   // rows [Re B; Im B]
+                    const uint64_t b_im = smem_desc(st + 3 * ZPL, LBO, SBO);
                     mma_f16(tmem, a_re, b_re, ID, u > 0 ? 1u : 0u);
-                    mma_f16(tmem, a_im, b_neg, ID, 1u);
+                    mma_f16(tmem, a_im, b_im, ID1N, 1u);               // -Im A Im B into Re
+                    mma_f16(tmem + ZT, a_im, b_re, ID1, 1u);           // Im A Re B into Im
                 }
                 mma_commit(&empty[s]);
                 *n_consumed = u + 1;
@@ -775,7 +770,7 @@ size_t ZPlan::table_bytes() const
 
 size_t ZPlan::planes_bytes(bool a_operand) const
 {
-    const int npl = a_operand ? 2 : 3;
+    const int npl = 2;  // Re, Im per slice for both operands
     return (size_t)nkc * (a_operand ? nsA : ns) * npl * (a_operand ? Mpad : Npad) * 16 * sizeof(uint16_t);
 }
 
@@ -813,7 +808,7 @@ cudaError_t launch_zslice(const ZPlan &p, bool a_operand, const double2 *Mx, lon
     const int rows = a_operand ? p.M : p.N, Rpad = a_operand ? p.Mpad : p.Npad;
     zslice_kernel<<<dim3(p.nkc, Rpad / ZT), 512, 0, s>>>(Mx, ld, rows, p.K, a_operand ? 0 : 1, Rpad, p.mode,
                                                          a_operand ? p.nsA : p.ns,
-                                                         a_operand ? 2 : 3, maxw, planes, skip);
+                                                         2, maxw, planes, skip);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -830,11 +825,11 @@ cudaError_t launch_zgemm16(const ZPlan &p, const uint16_t *Ap, const uint16_t *B
         return e;
     dim3 grid(p.ntiles, p.nslots);
     if (f3)
-        zgemm16_kernel<true><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+        zgemm16_kernel<true><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 2 * p.ns, p.Npad, p.d_pairs,
                                                            reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT,
                                                            T, err, wait_ns, skip);
     else
-        zgemm16_kernel<false><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 3 * p.ns, p.Npad, p.d_pairs,
+        zgemm16_kernel<false><<<grid, ZTHREADS, ZSMEM, s>>>(Ap, 2 * p.nsA, p.Mpad, Bp, 2 * p.ns, p.Npad, p.d_pairs,
                                                             reinterpret_cast<const ZSlot *>(p.d_slots), p.Npad / ZT,
                                                             T, err, wait_ns, skip);
     count_launches(1);

@@ -170,8 +170,8 @@ GW_API gw_status gw_build_PG(gw_ctx *ctx, int precision, int gcut, int *ng_out, 
  * pivot is <= 0, GW_E_TIMEOUT if a kernel wait ran out).  Requires gw_P_to_G.
  * GW_INV_NEWTON_TC is captured into a CUDA graph on the first call for an order N_g (on a private
  * stream of the context; the capture synchronises the context's stream once) and replayed on the
- * context's stream afterwards; if the caller is itself capturing that stream, the steps are queued
- * into the caller's capture instead.
+ * context's stream afterwards.  Because of the synchronisation the call cannot be made while the
+ * context's stream is being captured: it then returns GW_E_INVALID before queuing anything.
  */
 GW_API gw_status gw_eps_inv(gw_ctx *ctx, int method, void *eps_out, void *epsinv_out);
 

@@ -489,15 +489,6 @@ gw_status inverse_newton_tc(Ctx &c, const double2 *A, int n, double2 *X, bool us
     GW_TRY(ensure(c, c.d_tcw, c.cap.tcw, ns_work_bytes(n, nsm), "tensor-core Newton workspace"));
     GW_TRY(ensure(c, c.d_scal, c.cap.scal, 4 * sizeof(double), "Newton scalars"));
     const uint64_t wait_ns = static_cast<uint64_t>(c.wait_limit_ms * 1e6);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (use_graph && (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)) {
-        cudaGetLastError();
-        use_graph = false;  // the caller is capturing this stream: queue into its capture instead
-        GW_CUDA(ns_prepare(c.d_tcw, n, nsm, c.stream), "Newton tables");
-        GW_CUDA(ns_inverse_enqueue(A, n, X, c.d_tcw, c.d_scal, c.d_err, wait_ns, nsm, c.stream, true),
-                "tensor-core Newton inverse");
-        return GW_OK;
-    }
     if (!use_graph) {
         // the eager form uploads the tables of order n into the workspace: a graph captured for
         // another order would then read tables of the wrong layout
@@ -1367,6 +1358,13 @@ gw_status gw_eps_inv(gw_ctx *h, int method, void *eps_out, void *epsinv_out)
     if (method != GW_INV_CHOLESKY && method != GW_INV_NEWTON && method != GW_INV_NEWTON_TC)
         return fail(c, GW_E_INVALID, "unknown inversion method %d", method);
     GW_CUDA(cudaSetDevice(c.device), "set device");
+    // the call reads the device status back (a stream synchronisation), which a stream under
+    // capture does not allow: refuse before anything is queued into the caller's capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return fail(c, GW_E_INVALID, "gw_eps_inv synchronises its stream, which is being captured");
+    }
     const int ng = c.ng;
     const size_t bytes = (size_t)ng * ng * sizeof(double2);
     GW_TRY(ensure(c, c.d_eps, c.cap.eps, bytes, "eps"));

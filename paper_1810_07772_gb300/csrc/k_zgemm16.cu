@@ -50,12 +50,13 @@ namespace {
 
 constexpr int ZT = 128;
 constexpr uint32_t ZPL = ZT * 16 * 2;       // 4 KB: one plane of one 128-row block, one chunk
-// A stage is one chunk of one slice pair (A Re, A Im, B -Im, B Re, B Im: 20 KB, two MMAs) for the
-// integer slices, and one chunk of all three FP16X3 pairs (A hi Re, Im, A lo Re, Im, B hi and B lo
-// regions: 40 KB, six MMAs, one commit) for the split, where each slice then loads once per chunk.
+// A stage is one chunk of one slice pair (A Re, A Im, B Re, B Im: 16 KB, three MMAs) for the
+// integer slices, and one chunk of all three FP16X3 pairs (A hi Re, Im, A lo Re, Im, B hi Re, Im,
+// B lo Re, Im: 32 KB, nine MMAs, one commit) for the split, where each slice then loads once per
+// chunk.
 constexpr uint32_t ZSTAGE = 4 * ZPL;
 constexpr int ZSTAGES = 6;                  // twelve stages in flight per SM cover the copy latency
-constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 100 KB: two CTAs per SM
+constexpr uint32_t ZPIPE = ZSTAGES * ZSTAGE;  // 96 KB: two CTAs per SM
 constexpr uint32_t ZSTAGE3 = 8 * ZPL;
 constexpr int ZSTAGES3 = 3;
 static_assert(ZSTAGES3 * ZSTAGE3 <= ZPIPE, "the fused stages share the pipeline buffers");

@@ -236,3 +236,38 @@ def test_eps_inv_graph_finishes_an_eps_that_needs_more_steps():
     assert np.linalg.norm(n - c) / np.linalg.norm(c) <= 1e-11
     assert np.max(np.abs(n @ e - np.eye(ng))) <= 1e-9
     assert rep2["steps"] <= 8
+
+
+def test_eps_inv_refuses_a_stream_under_capture():
+    """gw_eps_inv synchronises its stream to read the device status back, which a stream under
+    capture does not allow: the call returns GW_E_INVALID before it queues anything into the
+    caller's graph, the caller's capture stays valid, and the context works afterwards."""
+    w = inputs.SMALL
+    psi, E = inputs.make_workload_states(w)
+    s = torch.cuda.Stream(device=DEV)
+    with gw.Context(0, s) as ctx:
+        with torch.cuda.stream(s):
+            ctx.load_states(torch.from_numpy(psi.astype(np.complex64)).to(DEV), E, (w.n,) * 3, w.nv)
+            ctx.build_PG(w.gcut)
+            ref = torch.empty((ctx.ng, ctx.ng), dtype=torch.complex128, device=DEV)
+            ctx.eps_inv("newton_tc", epsinv_out=ref)
+            x = torch.zeros(4, device=DEV)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            g.capture_begin(capture_error_mode="relaxed")
+            try:
+                x.add_(1.0)
+                with pytest.raises(gw.GwError) as ei:
+                    ctx.eps_inv("newton_tc")
+            finally:
+                g.capture_end()
+        assert ei.value.status == gw.GW_E_INVALID
+        g.replay()                       # the caller's graph holds its own work only
+        torch.cuda.synchronize()
+        assert torch.equal(x.cpu(), torch.ones(4))
+        with torch.cuda.stream(s):
+            again = torch.empty_like(ref)
+            ctx.eps_inv("newton_tc", epsinv_out=again)
+        s.synchronize()
+        assert torch.equal(again, ref)

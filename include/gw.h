@@ -360,7 +360,7 @@ GW_API gw_status gw_pp_eval(gw_ctx *ctx, double omega, int nuse, void *S_out);
  *   mode 0  FP16X3: y = x 2^(14 - e), hi = rn16(y), lo = rn16(y - hi); hi*hi + hi*lo + lo*hi
  *           accumulated in FP32 (about 1e-6 relative, normwise);
  *   mode 1  integer slices (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012): x 2^-e =
- *           sum_t a_t 2^(-6(t+1)) + r with a_0 in [-64, 64], a_t in [-32, 32], nine slices; every
+ *           sum_t a_t 2^(-6(t+1)) + r with a_0 in [-64, 64], a_t in [-32, 31], nine slices; every
  *           slice product and every partial sum of a work slot is an integer below 2^24, so the
  *           tensor cores sum exactly and the result has FP64 accuracy (error about
  *           K 2^-54 max|A| max|B| per entry; integer-valued inputs below 2^6 give exact results).

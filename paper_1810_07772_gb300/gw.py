@@ -8,6 +8,7 @@ buffers as numpy arrays.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 
 import numpy as np
@@ -133,6 +134,26 @@ def _is_device(x):
     return hasattr(x, "is_cuda") and x.is_cuda
 
 
+@functools.lru_cache(maxsize=64)
+def _sphere_count(dims, gcut):
+    axes = [np.arange(-(n // 2), n - n // 2) ** 2 for n in dims]
+    m2 = axes[0][:, None, None] + axes[1][None, :, None] + axes[2][None, None, :]
+    return int(np.count_nonzero(m2 <= gcut))
+
+
+def _fits(x, nbytes, what):
+    """Reject a tensor or array smaller than the nbytes a call reads or writes through it (the
+    library takes plain pointers and trusts the documented sizes; raw integer addresses pass)."""
+    if isinstance(x, np.ndarray):
+        have = x.nbytes
+    elif hasattr(x, "numel") and hasattr(x, "element_size"):
+        have = x.numel() * x.element_size()
+    else:
+        return
+    if have < nbytes:
+        raise GwError(GW_E_INVALID, f"{what} holds {have} bytes, the call needs {nbytes}")
+
+
 class DeviceView:
     """Read-only view of a device buffer through __cuda_array_interface__ (no copy)."""
 
@@ -195,6 +216,8 @@ class Context:
         dtype = GW_C128 if "complex128" in dt else GW_C64
         if "complex" not in dt:
             raise TypeError("psi must be complex64 or complex128")
+        if len(psi.shape) < 2 or int(np.prod([int(d) for d in psi.shape[1:]])) != n1 * n2 * n3:
+            raise GwError(GW_E_INVALID, f"psi must be [nv + nc][N_r] with N_r = {n1 * n2 * n3}")
         self._check(lib().gw_load_states(self._h, n1, n2, n3, float(cell_L), int(nv), nb - int(nv), _ptr(psi),
                                          dtype, 1 if _is_device(psi) else 0, E.ctypes.data))
         self.dims = (n1, n2, n3)
@@ -227,12 +250,16 @@ class Context:
 
     def build_P(self, precision="fp16x3", P_out=None):
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        if self.dims is not None:
+            nr = self.dims[0] * self.dims[1] * self.dims[2]
+            _fits(P_out, nr * nr * 8, "P_out")
         self._check(lib().gw_build_P(self._h, prec, _ptr(P_out)))
 
     def P_to_G(self, gcut, PG_out=None):
         """Returns the integer G-vectors (N_g x 3, basis order)."""
         ng = ctypes.c_int(0)
         g = self._gbuf
+        self._fits_PG(PG_out, gcut)
         self._check(lib().gw_P_to_G(self._h, int(gcut), ctypes.byref(ng), g.ctypes.data, g.shape[0], _ptr(PG_out)))
         self.ng = ng.value
         self.gvec = g[: ng.value].copy()
@@ -243,6 +270,7 @@ class Context:
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
         ng = ctypes.c_int(0)
         g = self._gbuf
+        self._fits_PG(PG_out, gcut)
         self._check(lib().gw_build_PG(self._h, prec, int(gcut), ctypes.byref(ng), g.ctypes.data, g.shape[0],
                                       _ptr(PG_out)))
         self.ng = ng.value
@@ -251,6 +279,8 @@ class Context:
 
     def eps_inv(self, method="cholesky", eps_out=None, epsinv_out=None):
         m = INV_METHOD[method] if isinstance(method, str) else int(method)
+        _fits(eps_out, self.ng * self.ng * 16, "eps_out")
+        _fits(epsinv_out, self.ng * self.ng * 16, "epsinv_out")
         self._check(lib().gw_eps_inv(self._h, m, _ptr(eps_out), _ptr(epsinv_out)))
 
     def zgemm_tc(self, A, B, mode="slices", C=None):
@@ -293,6 +323,7 @@ class Context:
     def pp_eval(self, omega, nuse, S_out=None):
         """S(omega) from the first nuse plasmon-pole modes (gw_pp_eval); a host array unless S_out."""
         out = S_out if S_out is not None else np.zeros((self.ng, self.ng), dtype=np.complex128)
+        _fits(out, self.ng * self.ng * 16, "S_out")
         self._check(lib().gw_pp_eval(self._h, float(omega), int(nuse), _ptr(out)))
         return out
 
@@ -336,15 +367,23 @@ class Context:
         if out is None:
             ng = self._sphere_size(gcut)
             out = torch.empty((ng, ng), dtype=torch.complex64, device=f"cuda:{self.device}")
+        else:
+            self._fits_PG(out, gcut)
         self._check(lib().gw_corr_closure(self._h, int(gcut), E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           int(E.size), _ptr(out)))
         return out
 
+    def _fits_PG(self, out, gcut):
+        """An N_g x N_g complex64 output for the sphere gcut, checked when the grid and the cut are
+        valid (otherwise the library rejects the call before writing)."""
+        if out is None or self.dims is None or not (0 <= int(gcut) and 4 * int(gcut) < min(self.dims) ** 2):
+            return
+        ng = self._sphere_size(int(gcut))
+        _fits(out, ng * ng * 8, "P~ output")
+
     def _sphere_size(self, gcut):
         """Number of integer m in the grid's index range with |m|^2 <= gcut (the N_g of the call)."""
-        axes = [np.arange(-(n // 2), n - n // 2) ** 2 for n in self.dims]
-        m2 = axes[0][:, None, None] + axes[1][None, :, None] + axes[2][None, None, :]
-        return int(np.count_nonzero(m2 <= gcut))
+        return _sphere_count(tuple(int(n) for n in self.dims), int(gcut))
 
     def set_transform_kernel(self, kind):
         """Sphere transforms (gw_set_transform_kernel): "two_kernel" (the default; constant

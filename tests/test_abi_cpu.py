@@ -64,3 +64,28 @@ def test_create_without_gpu_fails_cleanly(L):
 def test_only_sm103a_code():
     """The build targets sm_103a only (no PTX for other archs, no multi-arch fat binary)."""
     assert gbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_rejects_undersized_buffers(L):
+    """The binding checks the size of every tensor or array it passes where the call's size is
+    known; raw addresses and NULL pass unchecked."""
+    import types
+
+    import numpy as np
+    import torch
+
+    from oracle import gw_oracle as O
+    gw._fits(np.zeros(4, np.complex64), 32, "x")
+    gw._fits(None, 1 << 40, "x")
+    gw._fits(12345, 1 << 40, "x")
+    gw._fits(torch.zeros(4, dtype=torch.complex128), 64, "t")
+    for buf, need in ((np.zeros(3, np.complex64), 32), (torch.zeros(4, dtype=torch.complex128), 65)):
+        with pytest.raises(gw.GwError) as e:
+            gw._fits(buf, need, "x")
+        assert e.value.status == gw.GW_E_INVALID
+    # the sphere size the P~ check uses: the documented N_g of the three workloads and the oracle's
+    # sphere on a non-cubic grid
+    for dims, gcut, ng in (((12, 12, 12), 8, 93), ((24, 24, 24), 29, 691), ((36, 36, 36), 61, 2007)):
+        assert gw.Context._sphere_size(types.SimpleNamespace(dims=dims), gcut) == ng
+    dims = (10, 14, 9)
+    assert gw.Context._sphere_size(types.SimpleNamespace(dims=dims), 5) == len(O.sphere(dims, 5))

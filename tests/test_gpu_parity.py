@@ -240,6 +240,20 @@ def test_invalid_arguments_and_call_order():
         with pytest.raises(gw.GwError) as e:
             ctx.load_states(psi.astype(np.complex64), bad, (w.n,) * 3, w.nv)
         assert e.value.status == gw.GW_E_INVALID
+        # empty sums of Eq. (Pstatic): no occupied or no unoccupied state, or no state at all; a
+        # grid outside [2, 64]^3.  All are host checks, made before psi is read.
+        for nv_bad in (0, len(E)):
+            with pytest.raises(gw.GwError) as e:
+                ctx.load_states(psi.astype(np.complex64), E, (w.n,) * 3, nv_bad)
+            assert e.value.status == gw.GW_E_INVALID
+        with pytest.raises(gw.GwError) as e:
+            ctx.load_states(np.zeros((0, w.nr), np.complex64), np.zeros(0), (w.n,) * 3, 0)
+        assert e.value.status == gw.GW_E_INVALID
+        # a grid that does not match psi's rows (the binding) and one outside [2, 64]^3 (the library)
+        for dims in ((w.n, w.n, w.n + 1), (1, w.n, w.n * w.n)):
+            with pytest.raises(gw.GwError) as e:
+                ctx.load_states(psi.astype(np.complex64), E, dims, w.nv)
+            assert e.value.status == gw.GW_E_INVALID
         ctx.load_states(psi.astype(np.complex64), E, (w.n,) * 3, w.nv)   # host input path
         with pytest.raises(gw.GwError) as e:
             ctx.P_to_G(8)
@@ -253,6 +267,21 @@ def test_invalid_arguments_and_call_order():
         with pytest.raises(gw.GwError) as e:
             ctx.P_to_G(36)                      # 4 * 36 >= 12^2: sphere leaves the grid
         assert e.value.status == gw.GW_E_INVALID
+        with pytest.raises(gw.GwError) as e:
+            ctx.P_to_G(-1)
+        assert e.value.status == gw.GW_E_INVALID
+        # output buffers smaller than the call writes are rejected before the library runs
+        with pytest.raises(gw.GwError) as e:
+            ctx.build_P(P_out=np.zeros(16, np.complex64))
+        assert e.value.status == gw.GW_E_INVALID
+        with pytest.raises(gw.GwError) as e:
+            ctx.P_to_G(w.gcut, PG_out=np.zeros((4, 4), np.complex64))
+        assert e.value.status == gw.GW_E_INVALID
+        g = ctx.P_to_G(w.gcut)
+        with pytest.raises(gw.GwError) as e:
+            ctx.eps_inv("cholesky", epsinv_out=np.zeros((len(g) - 1, len(g)), np.complex128))
+        assert e.value.status == gw.GW_E_INVALID
+        ctx.eps_inv("cholesky", epsinv_out=np.zeros((len(g), len(g)), np.complex128))
 
 
 def test_host_complex128_input_matches_device_input(small):

@@ -1,5 +1,5 @@
 """Host-side logic of bench.py on CPU: the max-over-ranks / sum-of-units aggregation across two
-gloo ranks, the clock-sample summary and the argument defaults."""
+gloo ranks, the clock-sample summary, the argument defaults and the reference arm's JSON line."""
 import os
 import socket
 
@@ -74,3 +74,26 @@ def test_workload_precision_and_error_target():
     s = bench.parse_args(["--workload", "split"])
     assert s.precision == "bf16x3" and bench.ERROR_TARGET["split"] == 1e-4
     assert bench.parse_args(["--workload", "split", "--precision", "fp16x3"]).precision == "fp16x3"
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle's C loop on the host cores and prints one
+    JSON line with the contract's keys (no GPU needed)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1
+    assert line["value"] > 0 and line["ms_per_step"] > 0 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "grid24_nv32_nc480"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(P12_WARPS * 32)
         if (kStage && vec) {
             // the whole plane with coalesced 16-byte loads (512 bytes per warp instruction) into
             // rows of SP complex values
-            constexpr int QR = N3 / 2;  // 16-byte words per line
+            constexpr int QR = kStage ? N3 / 2 : 1;  // 16-byte words per line (the branch needs kStage)
             const float4 *s4 = reinterpret_cast<const float4 *>(src);
             const float4 *v4 = reinterpret_cast<const float4 *>(srcv);
 #pragma unroll 4

@@ -60,7 +60,6 @@ Readings of the paper taken here (where it is silent or inconsistent):
 from __future__ import annotations
 
 import ctypes
-import os
 
 import numpy as np
 import scipy.fft

@@ -3,8 +3,6 @@ gloo ranks, the clock-sample summary, the argument defaults and the reference ar
 import os
 import socket
 
-import pytest
-
 import bench
 
 

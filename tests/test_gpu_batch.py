@@ -2,7 +2,6 @@
 rank-k update, optional CUDA-graph replay, autotuned window length), checked against the
 single-instance path (bit for bit) and against the FP64 oracle."""
 import json
-import os
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ It must agree with the inverse that gw_eps_inv returns for the same eps, on two 
 of different sizes (the static workspace keeps the previous call's contents), and reject orders
 above its fixed maximum.  This file is collected last, so a run that stops at the first failure
 has already run every other test."""
-import ctypes
 
 import numpy as np
 import pytest

@@ -85,11 +85,6 @@ def batch_workloads() -> list[Workload]:
     return out
 
 
-def learned_workload(nc: int, seed: int) -> Workload:
-    """The truncation-correction shape: a 24^3 grid with 32 occupied states and ``nc`` unoccupied."""
-    return Workload(f"grid24_nv32_nc{nc}_s{seed}", 24, 32, nc, 29, seed)
-
-
 def make_states(n: int, nv: int, nc: int, seed: int, dims: tuple[int, int, int] | None = None):
     """Return ``(psi, E_eV)``: ``psi`` complex128 ``[nv + nc][N_r]``, ``E_eV`` float64 ``[nv + nc]``.
 

@@ -690,13 +690,6 @@ __device__ __forceinline__ void stage1_out(const float2 (&x)[N], int M, float sg
     }
 }
 
-template <int N, int... Mo>
-__device__ __forceinline__ void stage1_all(const float2 (&x)[N], int M, float sgn, float2 *col, int lda,
-                                           std::integer_sequence<int, Mo...>)
-{
-    (stage1_out<N, Mo + 1>(x, M, sgn, col, lda), ...);
-}
-
 // Stage-2 outputs (+-Mo, m3) of a column (Mo <= k2 at run time), into ys at the disk indices
 // dt[Mo] = (index of +Mo, index of -Mo or -1).
 template <int N, int Mo>
@@ -712,13 +705,6 @@ __device__ __forceinline__ void stage2_out(const float2 (&y)[N], int k2, float s
         if (Mo > 0 && d.y >= 0)
             ys[d.y] = make_float2(A.x + by, A.y - bx);
     }
-}
-
-template <int N, int... Mo>
-__device__ __forceinline__ void stage2_all(const float2 (&y)[N], int k2, float sgn, const int2 *dt, float2 *ys,
-                                           std::integer_sequence<int, Mo...>)
-{
-    (stage2_out<N, Mo>(y, k2, sgn, dt, ys), ...);
 }
 
 // Two outputs Ma, Mb in one block: their eight accumulator chains interleave (four per output

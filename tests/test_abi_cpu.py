@@ -1,5 +1,6 @@
 """CPU checks of the C ABI: the library builds, loads without a GPU and exports every symbol the
-header declares; host-side argument checks that need no device."""
+header declares; the header is strict C and a C program links against the library; host-side
+argument checks that need no device."""
 import ctypes
 import os
 import re
@@ -89,3 +90,33 @@ def test_binding_rejects_undersized_buffers(L):
         assert gw.Context._sphere_size(types.SimpleNamespace(dims=dims), gcut) == ng
     dims = (10, 14, 9)
     assert gw.Context._sphere_size(types.SimpleNamespace(dims=dims), 5) == len(O.sphere(dims, 5))
+
+
+def test_header_is_c_and_links_from_c(L):
+    """include/gw.h compiles as strict C99 (and as C++17), and a C program linked against libgw.so
+    reaches the entry points that need no GPU with the documented results."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    src = os.path.join(ROOT, "tests", "abi_check.c")
+    out_dir = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    for std in ("-std=c99", "-std=c11"):
+        subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-fsyntax-only", src],
+                       check=True, timeout=120)
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx:
+        subprocess.run([cxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", inc, "-fsyntax-only", "-x", "c++",
+                        src], check=True, timeout=120)
+    lib_dir = os.path.dirname(gbuild.LIB_PATH)
+    exe = os.path.join(out_dir, "abi_check")
+    subprocess.run([cc, "-std=c99", "-I", inc, src, "-o", exe, "-L", lib_dir, "-lgw", f"-Wl,-rpath,{lib_dir}"],
+                   check=True, timeout=120)
+    res = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=60)
+    got = dict(line.split(" ", 1) for line in res.stdout.strip().splitlines())
+    assert got["version"] == "1" and got["status0"] == "ok" and got["status5"] == "eps not positive definite"
+    for k in ("null_destroy", "null_create", "null_eps_inv"):
+        assert int(got[k]) == gw.GW_E_INVALID

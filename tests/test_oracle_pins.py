@@ -236,6 +236,17 @@ def test_newton_iteration_matches_cholesky():
     assert np.max(np.abs(X - res["epsinv"])) < 1e-11
 
 
+def test_newton_start_for_a_general_complex_matrix():
+    """Reading 7: the start alpha A^H (with |.| in alpha) makes A X0 Hermitian positive definite, so
+    the iteration converges for any nonsingular A, here a non-normal, non-Hermitian complex matrix
+    (the start alpha A^T would diverge on it: A A^T has eigenvalues of negative real part)."""
+    A = np.array([[1j, 0.3, 0.0], [0.0, 2j, 0.1 - 0.2j], [0.05, 0.0, -1.5j]])
+    X, it = O.inverse_newton(A, tol=1e-14)
+    assert it < 100
+    assert np.max(np.abs(X @ A - np.eye(3))) < 1e-12
+    assert np.max(np.abs(X - np.linalg.inv(A))) < 1e-12
+
+
 def test_cholesky_rejects_indefinite():
     A = np.array([[1.0, 2.0], [2.0, 1.0]], dtype=np.complex128)
     with pytest.raises(O.NotPositiveDefinite):
@@ -362,6 +373,15 @@ def test_pp_single_pole_closed_form():
         assert abs(abs(A[gi, a]) - 1) < 1e-12
         assert abs(w2[a] - wt2[gi]) <= 1e-12 * wt2[gi]
     assert np.all(sig < 0)
+    # away from w = 0 the model follows the single-oscillator form eps^-1(w) - 1 = wp^2 / (w^2 - w_g^2)
+    # (its w = 0 value is the static eps^-1 above), so S(w) = V(g) wp^2 / (w^2 - w_g^2) on the
+    # diagonal: below every pole, between two poles and above them all
+    V = O.coulomb(g, L)
+    for w_sq in (0.5 * wp2, 5.0 * wp2, 20.0 * wp2):
+        S = O.pp_S_omega(sig, w2, A, np.sqrt(w_sq))
+        want = V * wp2 / (w_sq - wt2)
+        assert np.max(np.abs(np.diag(S) - want)) <= 1e-10 * np.max(np.abs(want))
+        assert np.max(np.abs(S - np.diag(np.diag(S)))) <= 1e-12 * np.max(np.abs(want))
 
 
 def test_pp_density_and_S_omega_limits():

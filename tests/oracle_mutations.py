@@ -130,6 +130,23 @@ MUTATIONS = [
      'apply scale'),
     (M, 'mh = m / (1.0 - beta1 ** t)', 'mh = m', 'adam bias m'),
     (M, 'theta - lr * mh / (np.sqrt(vh) + eps)', 'theta - lr * mh / (vh + eps)', 'adam sqrt'),
+    (G, "((m[:, 0] % n1) * n2 + (m[:, 1] % n2)) * n3 + (m[:, 2] % n3)",
+     "((m[:, 0] % n1) * n2 + (m[:, 1] % n2)) * n3 + (-m[:, 2] % n3)",
+     "flat index sign"),
+    (G, "vs = list(range(v0, min(nv, v0 + v_chunk)))", "vs = list(range(v0, min(nv, v0 + v_chunk - 1)))",
+     "P_gspace drops a state"),
+    (G, "    A = A[:, :nmodes]\n", "    A = A[:, -nmodes:]\n", "pp_modes least negative vectors"),
+    (G, "    sig = w[:nmodes]\n", "    sig = w[-nmodes:]\n", "pp_modes least negative values"),
+    (G, "rho = np.conj(psi[v])[None, :] * psi\n", "rho = psi[v][None, :] * np.conj(psi)\n", "closure M conj"),
+    (M, "gi, hi = np.triu_indices(ng)\n    m2 = ", "hi, gi = np.triu_indices(ng)\n    m2 = ", "features lower triangle"),
+    (M, "d = D[gi, hi] * s", "d = D[hi, gi] * s", "targets lower triangle"),
+    (M, "h2 = f16(np.tanh(h1 @ W2.T + b2))", "h2 = np.tanh(h1 @ W2.T + b2)", "f16act layer 2 unrounded"),
+    (M, "h3 = np.tanh(h2 @ W3.T + b3)", "h3 = f16(np.tanh(h2 @ W3.T + b3))", "f16act layer 3 rounded"),
+    (M, "sizes = [(hidden, n_in), (hidden, hidden), (hidden, hidden), (n_out, hidden)]",
+     "sizes = [(hidden, n_in), (hidden, hidden), (hidden, hidden), (hidden, n_out)]",
+     "unpack last shape"),
+    (M, "        b = theta[o:o + r]\n        o += r\n", "        b = theta[o:o + r] * 0\n        o += r\n", "unpack biases"),
+    (M, "P[gi[~on], hi[~on]] += d[~on]", "P[gi[~on], hi[~on]] += np.conj(d[~on])", "apply upper conj"),
     (C, '/ (E_ha[v] - E_ha[nv + c]);', '/ (E_ha[nv + c] - E_ha[v]);', 'C loop sign'),
     (C, 'acc += 2.0 * conj(pv[r]) * pc[r] * conj(pc[rp]) * pv[rp]',
      'acc += 2.0 * pv[r] * conj(pc[r]) * pc[rp] * conj(pv[rp])',

@@ -109,6 +109,23 @@ def test_f16_activation_forward_equals_forward_when_activations_are_exact():
     assert 0 < np.abs(a - b).max() <= 2.0 ** -9 * np.abs(b).max()
 
 
+def test_f16_activation_forward_rounds_exactly_the_square_products_inputs():
+    """The inference arithmetic rounds the outputs of layers 1 and 2 (the operands of the two
+    256-wide products) to FP16 and nothing else: nudging b1 or b2 by 1e-10 moves those outputs by
+    far less than an FP16 step, so the result does not change at all, while the same nudge of b3
+    (layer 3 feeds the last product unrounded) does change it."""
+    rng = np.random.default_rng(9)
+    n_in, hidden = 12, 16
+    theta = M.to_fp16_weights(rng.standard_normal(M.n_params(n_in, hidden)) * 0.3, n_in, hidden)
+    X = rng.standard_normal((8, n_in))
+    y0 = M.forward_f16act(M.unpack(theta, n_in, hidden), X)
+    for layer, changes in ((0, False), (1, False), (2, True)):
+        params = M.unpack(theta.copy(), n_in, hidden)
+        params[layer][1][:] += 1e-10
+        y = M.forward_f16act(params, X)
+        assert (not np.array_equal(y, y0)) == changes, layer
+
+
 HA = 27.211386245988   # eV per Hartree
 
 

@@ -373,10 +373,17 @@ def test_pp_single_pole_closed_form():
         assert abs(abs(A[gi, a]) - 1) < 1e-12
         assert abs(w2[a] - wt2[gi]) <= 1e-12 * wt2[gi]
     assert np.all(sig < 0)
+    # fewer modes than G vectors: the most negative sigma first (the leading modes of Sec. 5.2),
+    # here the five smallest of the closed-form diagonal -V(g) wp^2 / w_g^2
+    V = O.coulomb(g, L)
+    s_diag = -V * wp2 / wt2
+    sig5, _, A5 = O.pp_modes(inv, g, L, rhoG, dims, 5)
+    order = np.argsort(s_diag)[:5]
+    assert np.max(np.abs(sig5 - s_diag[order])) <= 1e-12 * np.max(np.abs(s_diag))
+    assert np.all(np.abs(np.abs(A5[order, np.arange(5)]) - 1) < 1e-12)
     # away from w = 0 the model follows the single-oscillator form eps^-1(w) - 1 = wp^2 / (w^2 - w_g^2)
     # (its w = 0 value is the static eps^-1 above), so S(w) = V(g) wp^2 / (w^2 - w_g^2) on the
     # diagonal: below every pole, between two poles and above them all
-    V = O.coulomb(g, L)
     for w_sq in (0.5 * wp2, 5.0 * wp2, 20.0 * wp2):
         S = O.pp_S_omega(sig, w2, A, np.sqrt(w_sq))
         want = V * wp2 / (w_sq - wt2)

@@ -147,6 +147,12 @@ MUTATIONS = [
      "unpack last shape"),
     (M, "        b = theta[o:o + r]\n        o += r\n", "        b = theta[o:o + r] * 0\n        o += r\n", "unpack biases"),
     (M, "P[gi[~on], hi[~on]] += d[~on]", "P[gi[~on], hi[~on]] += np.conj(d[~on])", "apply upper conj"),
+    (G, "        if not d > 0.0:\n", "        if d < 0.0:\n", "cholesky accepts a zero pivot"),
+    (G, "alpha = 1.0 / np.max(np.sum(np.abs(A @ np.conj(A.T)), axis=1))",
+     "alpha = 1.0 / np.max(np.abs(np.sum(A @ np.conj(A.T), axis=1)))",
+     "newton alpha signed sums"),
+    (G, "    nz = m2 > 0\n", "    nz = m2 >= 0\n", "coulomb head"),
+    (G, "    n_in = psi.shape[0]\n", "    n_in = nv\n", "closure n_in"),
     (C, '/ (E_ha[v] - E_ha[nv + c]);', '/ (E_ha[nv + c] - E_ha[v]);', 'C loop sign'),
     (C, 'acc += 2.0 * conj(pv[r]) * pc[r] * conj(pc[rp]) * pv[rp]',
      'acc += 2.0 * pv[r] * conj(pc[r]) * pc[rp] * conj(pv[rp])',

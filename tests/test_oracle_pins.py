@@ -245,12 +245,20 @@ def test_newton_start_for_a_general_complex_matrix():
     assert it < 100
     assert np.max(np.abs(X @ A - np.eye(3))) < 1e-12
     assert np.max(np.abs(X - np.linalg.inv(A))) < 1e-12
+    # alpha from the row sums of |A A^H|: here the signed row sums cancel to 0.01, and a start
+    # 100 A would diverge (A X0 would reach 361 I on one eigenvector)
+    A = np.array([[1.0, -0.9], [-0.9, 1.0]], dtype=np.complex128)
+    X, it = O.inverse_newton(A, tol=1e-14)
+    assert it < 100
+    assert np.max(np.abs(X - np.linalg.inv(A))) < 1e-12
 
 
 def test_cholesky_rejects_indefinite():
-    A = np.array([[1.0, 2.0], [2.0, 1.0]], dtype=np.complex128)
-    with pytest.raises(O.NotPositiveDefinite):
-        O.cholesky_lower(A)
+    """An indefinite matrix and a singular positive semidefinite one (second pivot exactly 0) both
+    have no Cholesky factor with a positive diagonal."""
+    for A in ([[1.0, 2.0], [2.0, 1.0]], [[1.0, 1j], [-1j, 1.0]]):
+        with pytest.raises(O.NotPositiveDefinite):
+            O.cholesky_lower(np.array(A, dtype=np.complex128))
 
 
 def test_small_workload_rspace_vs_gspace():

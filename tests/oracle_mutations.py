@@ -160,6 +160,12 @@ MUTATIONS = [
     (C, 'acc += 2.0 * conj(pv[r]) * pc[r] * conj(pc[rp]) * pv[rp]',
      'acc += 1.0 * conj(pv[r]) * pc[r] * conj(pc[rp]) * pv[rp]',
      'C loop factor'),
+    (C, "for (int c = 0; c < nc; ++c) {", "for (int c = 1; c < nc; ++c) {", "C loop drops the first c"),
+    (C, "for (int v = 0; v < nv; ++v) {", "for (int v = 0; v < nv - 1; ++v) {", "C loop drops the last v"),
+    (C, "const double complex *pc = psi + (size_t)(nv + c) * nr;", "const double complex *pc = psi + (size_t)c * nr;",
+     "C loop unoccupied offset"),
+    (C, "out[(size_t)(r - r0) * nr + rp] = acc;", "out[(size_t)(r - r0) * nr + (nr - 1 - rp)] = acc;",
+     "C loop column order"),
 ]
 
 

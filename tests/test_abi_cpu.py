@@ -120,3 +120,55 @@ def test_header_is_c_and_links_from_c(L):
     assert got["version"] == "1" and got["status0"] == "ok" and got["status5"] == "eps not positive definite"
     for k in ("null_destroy", "null_create", "null_eps_inv"):
         assert int(got[k]) == gw.GW_E_INVALID
+
+
+def _header_decls():
+    text = open(os.path.join(ROOT, "include", "gw.h")).read()
+    out = {}
+    for ret, name, params in re.findall(r"^GW_API\s+([^;(]*?)\b(gw_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M | re.S):
+        ps = [" ".join(p.split()) for p in params.replace("\n", " ").split(",")]
+        ps = [] if ps in ([""], ["void"]) else ps
+        # drop the parameter name: the type is what precedes it (a pointer keeps its stars)
+        types = [" ".join(re.sub(r"\b\w+$", "", p).split()) for p in ps]
+        out[name] = (" ".join(ret.split()), types)
+    return text, out
+
+
+def test_binding_signatures_and_constants_match_the_header():
+    """Every ctypes signature of the binding has the header's arity and, argument by argument, a
+    ctypes type of the same kind and size (a pointer for a pointer, c_int for int and the enums,
+    c_double for double, c_size_t for size_t, c_long for long; POINTER(T) only onto the header's
+    pointee type), and every enumerator the binding uses has the header's value."""
+    text, decls = _header_decls()
+    assert set(decls) == set(gw.SIGNATURES)
+    scalar = {"int": ctypes.c_int, "double": ctypes.c_double, "size_t": ctypes.c_size_t, "long": ctypes.c_long,
+              "gw_status": ctypes.c_int}
+    pointee = {"double": ctypes.c_double, "float": ctypes.c_float, "int": ctypes.c_int, "size_t": ctypes.c_size_t,
+               "void *": ctypes.c_void_p}
+    for name, (ret, types) in decls.items():
+        res, args = gw.SIGNATURES[name]
+        assert len(args) == len(types), name
+        if ret.endswith("*"):
+            assert res is ctypes.c_char_p, name
+        else:
+            assert res is ctypes.c_int, name
+        for t, a in zip(types, args):
+            if t.endswith("*"):
+                base = " ".join(t.replace("const", " ").split())[:-1].strip()   # the pointee
+                if base == "char":
+                    assert a is ctypes.c_char_p, (name, t)
+                elif hasattr(a, "_type_") and a not in (ctypes.c_void_p, ctypes.c_char_p):
+                    want = pointee.get(base, ctypes.c_void_p if base.endswith("*") else None)
+                    assert want is not None and a._type_ is want, (name, t, a)
+                else:
+                    assert a is ctypes.c_void_p, (name, t, a)
+            else:
+                assert ctypes.sizeof(a) == ctypes.sizeof(scalar[t]) and a is scalar[t], (name, t, a)
+    enums = {k: int(v) for k, v in re.findall(r"\b(GW_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    for k in ("GW_OK", "GW_E_INVALID", "GW_E_NOMEM", "GW_E_CUDA", "GW_E_NOT_READY", "GW_E_NUMERIC",
+              "GW_E_TIMEOUT", "GW_E_UNSUPPORTED", "GW_C64", "GW_C128"):
+        assert getattr(gw, k) == enums[k], k
+    for table, prefix in ((gw.PRECISION, "GW_PREC_"), (gw.INV_METHOD, "GW_INV_"), (gw.HERK_KERNEL, "GW_HERK_"),
+                          (gw.TRANSFORM_KERNEL, "GW_TRANSFORM_"), (gw.BUF, "GW_BUF_")):
+        for key, value in table.items():
+            assert enums[prefix + key.upper()] == value, (prefix, key)
